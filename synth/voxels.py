@@ -1,0 +1,169 @@
+"""Seeded voxel workloads shaped like the paper's pore-scale, continuum and
+fractured domains (Section 5, Table "settings"): binary porous solids, a
+log-normal modulus field, stiffness contrast and thin compliant slits.
+
+Every array is indexed [z][y][x] (x fastest), matching the voxel numbering
+v = x + nx*(y + ny*z) used throughout the library.  Moduli are float32, the
+type the library's C interface takes, so both consumers see identical values.
+"""
+from __future__ import annotations
+
+import dataclasses
+from typing import Dict, Tuple
+
+import numpy as np
+from scipy import ndimage
+
+FACES = ("x0", "x1", "y0", "y1", "z0", "z1")
+
+
+@dataclasses.dataclass
+class Problem:
+    """A voxel elasticity problem: geometry, material, subdomains and loads."""
+    name: str
+    mask: np.ndarray            # uint8 [nz, ny, nx], 1 = solid
+    E: np.ndarray               # float32 [nz, ny, nx], Young's modulus per voxel
+    nu: float                   # Poisson ratio (global)
+    grains: Tuple[int, int, int]  # Cartesian subdomain counts (px, py, pz)
+    bcs: Dict[str, dict]        # face -> {"fix": (bx,by,bz), "value": (ux,uy,uz), "traction": (tx,ty,tz)}
+    n_mortar: int = 4           # maximum mortar nodes per interface
+    seed: int = 0
+
+    @property
+    def shape(self):
+        return self.mask.shape
+
+
+def _empty_face():
+    return {"fix": (False, False, False), "value": (0.0, 0.0, 0.0), "traction": (0.0, 0.0, 0.0)}
+
+
+def bcs_clamped_traction(traction=(0.0, 0.0, 1.0), clamp_face="z0", load_face="z1"):
+    """Clamp every component on `clamp_face`; uniform traction on `load_face`."""
+    bcs = {f: _empty_face() for f in FACES}
+    bcs[clamp_face] = {"fix": (True, True, True), "value": (0.0, 0.0, 0.0), "traction": (0.0, 0.0, 0.0)}
+    bcs[load_face] = {"fix": (False, False, False), "value": (0.0, 0.0, 0.0),
+                      "traction": tuple(float(t) for t in traction)}
+    return bcs
+
+
+def bcs_dict_to_arrays(bcs):
+    """Face dictionary -> (fix uint8[6,3], value float64[6,3], traction float64[6,3])."""
+    fix = np.zeros((6, 3), np.uint8)
+    val = np.zeros((6, 3), np.float64)
+    tra = np.zeros((6, 3), np.float64)
+    for f, face in enumerate(FACES):
+        d = bcs.get(face, _empty_face())
+        fix[f] = [1 if b else 0 for b in d["fix"]]
+        val[f] = d["value"]
+        tra[f] = d["traction"]
+    return fix, val, tra
+
+
+def _largest_component_touching_bottom(solid):
+    """Keep the largest 6-connected solid component that touches the z=0 face."""
+    lab, n = ndimage.label(solid, structure=ndimage.generate_binary_structure(3, 1))
+    if n == 0:
+        return np.zeros_like(solid, dtype=np.uint8)
+    sizes = np.bincount(lab.ravel(), minlength=n + 1)
+    bottom = np.unique(lab[0][lab[0] > 0])
+    if bottom.size == 0:
+        return np.zeros_like(solid, dtype=np.uint8)
+    best = bottom[np.argmax(sizes[bottom])]
+    return (lab == best).astype(np.uint8)
+
+
+def _filtered_noise(rng, shape, sigma):
+    noise = rng.standard_normal(shape)
+    return ndimage.gaussian_filter(noise, sigma=sigma, mode="reflect", truncate=4.0)
+
+
+def porous_mask(shape, porosity, sigma, rng):
+    """Gaussian-filtered white noise thresholded at the porosity quantile.
+
+    Voxels whose filtered value ranks in the lowest `porosity` fraction become
+    void (ties broken by a stable sort), then the largest 6-connected solid
+    component touching z=0 is kept so that the clamped problem is nonsingular.
+    """
+    f = _filtered_noise(rng, shape, sigma).ravel()
+    order = np.argsort(f, kind="stable")
+    n_void = int(round(porosity * f.size))
+    solid = np.ones(f.size, dtype=bool)
+    solid[order[:n_void]] = False
+    return _largest_component_touching_bottom(solid.reshape(shape))
+
+
+def lognormal_modulus(shape, sigma_corr, rng, mu=0.0, sigma=1.0):
+    """E = exp(mu + sigma*g), g a Gaussian-filtered field rescaled to zero mean, unit variance."""
+    g = _filtered_noise(rng, shape, sigma_corr)
+    g = (g - g.mean()) / g.std()
+    return np.exp(mu + sigma * g).astype(np.float32)
+
+
+def _slits_and_voronoi(shape, rng, n_slits=20, radius=32.0, n_seeds=64, contrast=1e-4, phases=(1.0, 10.0)):
+    nz, ny, nx = shape
+    zz, yy, xx = np.meshgrid(np.arange(nz) + 0.5, np.arange(ny) + 0.5, np.arange(nx) + 0.5, indexing="ij")
+    pts = np.stack([xx.ravel(), yy.ravel(), zz.ravel()], axis=1)
+    seeds = rng.uniform(0.0, 1.0, size=(n_seeds, 3)) * np.array([nx, ny, nz])
+    phase = rng.integers(0, 2, size=n_seeds)
+    E = np.empty(pts.shape[0], np.float64)
+    chunk = 1 << 20
+    for s in range(0, pts.shape[0], chunk):
+        p = pts[s:s + chunk]
+        d2 = ((p[:, None, :] - seeds[None, :, :]) ** 2).sum(axis=2)
+        E[s:s + chunk] = np.where(phase[np.argmin(d2, axis=1)] == 0, phases[0], phases[1])
+    for _ in range(n_slits):
+        c = rng.uniform(0.0, 1.0, size=3) * np.array([nx, ny, nz])
+        nrm = rng.standard_normal(3)
+        nrm /= np.linalg.norm(nrm)
+        rel = pts - c
+        dn = rel @ nrm
+        dt2 = (rel * rel).sum(axis=1) - dn * dn
+        hit = (np.abs(dn) <= 0.5) & (dt2 <= radius * radius)
+        E[hit] *= contrast
+    return E.reshape(shape).astype(np.float32)
+
+
+def make_workload(name, seed=0):
+    """Build one of the named workloads (see WORKLOADS for the recipes)."""
+    rng = np.random.default_rng(seed)
+    if name == "cube16":
+        shape = (16, 16, 16)
+        mask = np.ones(shape, np.uint8)
+        E = np.ones(shape, np.float32)
+        return Problem(name, mask, E, 0.25, (2, 2, 2), bcs_clamped_traction(), 4, seed)
+    if name in ("porous64", "porous32", "porous24", "porous48"):
+        n = int(name[len("porous"):])
+        shape = (n, n, n)
+        mask = porous_mask(shape, 0.3, 2.0, rng)
+        E = lognormal_modulus(shape, 2.0, rng)
+        p = n // 16
+        return Problem(name, mask, E, 0.3, (p, p, p), bcs_clamped_traction(), 4, seed)
+    if name == "porous128":
+        shape = (128, 128, 128)
+        mask = porous_mask(shape, 0.4, 3.0, rng)
+        E = lognormal_modulus(shape, 3.0, rng)
+        return Problem(name, mask, E, 0.3, (8, 8, 8), bcs_clamped_traction(), 4, seed)
+    if name == "fractured256":
+        shape = (256, 256, 256)
+        mask = porous_mask(shape, 0.25, 2.0, rng)
+        E = _slits_and_voronoi(shape, rng)
+        return Problem(name, mask, E, 0.25, (16, 16, 16), bcs_clamped_traction(), 2, seed)
+    if name.startswith("tiny"):
+        # tiny<n>: porous n^3 block with 2x2x2 subdomains, small enough for dense checks
+        n = int(name[4:])
+        shape = (n, n, n)
+        mask = porous_mask(shape, 0.2, 1.0, rng)
+        E = lognormal_modulus(shape, 1.0, rng)
+        return Problem(name, mask, E, 0.3, (2, 2, 2), bcs_clamped_traction(), 2, seed)
+    raise KeyError(name)
+
+
+WORKLOADS = {
+    "cube16": "16^3 all-solid block, E=1, nu=0.25, 2x2x2 subdomains, z=0 clamped, unit +z traction on z=16",
+    "porous64": "64^3 porous block: white noise -> Gaussian sigma=2 -> porosity 0.3 -> largest 6-connected "
+                "component touching z=0; log-normal E (mu=0, sigma=1, same filter); nu=0.3; 4x4x4 subdomains",
+    "porous128": "128^3 porous block, porosity 0.4, sigma=3, log-normal E, nu=0.3, 8x8x8 subdomains",
+    "fractured256": "256^3 porous block (porosity 0.25, sigma=2), 64-seed Voronoi two-phase E in {1,10}, "
+                    "20 planar 1-voxel slits of radius 32 with E x 1e-4, nu=0.25, 16x16x16 subdomains",
+}

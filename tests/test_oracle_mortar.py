@@ -1,0 +1,108 @@
+"""Pins for oracle/mortar.py: mortar placement (Section 3.3, Eq. node_init)
+and Gaussian mortars (Eq. gauss)."""
+import itertools
+
+import numpy as np
+import pytest
+
+from oracle.mortar import gaussian_mortars, place_mortars
+
+
+def _energy(coords, sel):
+    X = coords[list(sel)].astype(float)
+    e = 0.0
+    for a, b in itertools.combinations(range(len(sel)), 2):
+        e += 1.0 / np.linalg.norm(X[a] - X[b])
+    return e
+
+
+def test_line_two_mortars_are_endpoints():
+    coords = np.array([[3, k, 7] for k in range(11)])
+    assert sorted(place_mortars(coords, 2)) == [0, 10]
+
+
+def test_square_face_four_mortars_are_corners():
+    coords = np.array([[i, j, 5] for j in range(5) for i in range(5)])     # x fastest, like node ids
+    sel = place_mortars(coords, 4)
+    got = sorted(tuple(coords[s][:2]) for s in sel)
+    assert got == [(0, 0), (0, 4), (4, 0), (4, 4)]
+
+
+def test_line_three_mortars_endpoints_and_middle():
+    coords = np.array([[k, 0, 0] for k in range(9)])
+    assert sorted(place_mortars(coords, 3)) == [0, 4, 8]
+
+
+def test_all_nodes_when_n_exceeds_size():
+    coords = np.array([[0, 0, 0], [1, 0, 0], [1, 1, 0]])
+    assert place_mortars(coords, 4) == [0, 1, 2]
+    assert place_mortars(coords, 3) == [0, 1, 2]
+
+
+def test_single_mortar_nearest_centroid():
+    coords = np.array([[k, 0, 0] for k in range(7)])
+    assert place_mortars(coords, 1) == [3]
+    coords = np.array([[k, 0, 0] for k in range(6)])       # tie between 2 and 3 -> smaller id
+    assert place_mortars(coords, 1) == [2]
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_coordinatewise_optimum(seed):
+    # after the sweeps stop, no single mortar can move to another free node and lower the energy
+    rng = np.random.default_rng(seed)
+    pts = {(int(a), int(b), 0) for a, b in rng.integers(0, 7, size=(40, 2))}
+    coords = np.array(sorted(pts, key=lambda p: (p[2], p[1], p[0])))
+    for n in (2, 3, 4, 5):
+        sel = place_mortars(coords, n)
+        e0 = _energy(coords, sel)
+        for i in range(n):
+            for y in range(len(coords)):
+                if y in sel:
+                    continue
+                trial = list(sel)
+                trial[i] = y
+                assert _energy(coords, trial) >= e0 - 1e-12
+
+
+def test_brute_force_report_small_interfaces():
+    # the greedy + sweep placement is a local method; on tiny interfaces it matches the global optimum
+    hits = 0
+    total = 0
+    for seed in range(8):
+        rng = np.random.default_rng(100 + seed)
+        pts = {(int(a), int(b), 0) for a, b in rng.integers(0, 5, size=(12, 2))}
+        coords = np.array(sorted(pts, key=lambda p: (p[2], p[1], p[0])))
+        if len(coords) < 4:
+            continue
+        sel = place_mortars(coords, 3)
+        best = min(_energy(coords, c) for c in itertools.combinations(range(len(coords)), 3))
+        total += 1
+        hits += abs(_energy(coords, sel) - best) < 1e-12
+    assert total > 0 and hits >= total // 2
+
+
+@pytest.mark.parametrize("beta", [1.0, 4.0, 16.0])
+def test_gaussian_partition_of_unity_and_peaks(beta):
+    rng = np.random.default_rng(1)
+    pts = {(int(a), int(b), int(c)) for a, b, c in rng.integers(0, 9, size=(60, 3))}
+    coords = np.array(sorted(pts, key=lambda p: (p[2], p[1], p[0])))
+    sel = place_mortars(coords, 4)
+    eta = gaussian_mortars(coords, sel, beta)
+    assert np.abs(eta.sum(axis=1) - 1.0).max() < 1e-15
+    assert (eta > 0).all()
+    for i, m in enumerate(sel):
+        assert np.argmax(eta[m]) == i          # mortar i dominates at its own node
+
+
+def test_gaussian_closed_form_two_mortars():
+    # two mortars 4 apart on a line, beta = 4, min spacing^2 = 16: at the midpoint both weights
+    # are 1/2; at node 1: a_0 = -1/64, a_1 = -9/64 -> eta_0 = 1/(1+exp(-1/8))
+    coords = np.array([[k, 0, 0] for k in range(5)])
+    eta = gaussian_mortars(coords, [0, 4], 4.0)
+    assert eta[2, 0] == pytest.approx(0.5, abs=1e-15)
+    assert eta[1, 0] == pytest.approx(1.0 / (1.0 + np.exp(-0.125)), rel=1e-15)
+
+
+def test_single_mortar_is_constant_one():
+    coords = np.array([[k, 1, 2] for k in range(5)])
+    assert np.array_equal(gaussian_mortars(coords, [2]), np.ones((5, 1)))
