@@ -1,0 +1,194 @@
+/*
+ * hplmm.h -- C interface of the GB300 (sm_103a) library for algebraic hPLMM,
+ * the two-level multiscale preconditioner of Khan & Mehmani, "High-order
+ * Multiscale Preconditioner for Elasticity of Arbitrary Structures", used in
+ * right-preconditioned GMRES for Q1 finite-element linear elasticity on voxel
+ * images.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * - Status codes are returned, never exceptions.  After any HPLMM_ERR_* the
+ *   context may only be destroyed, except HPLMM_NOT_CONVERGED (solve returns
+ *   its best iterate) and HPLMM_ERR_INVALID raised by argument checks that
+ *   ran before any work was queued.  hplmm_last_error() gives the message.
+ * - Work is queued on the CUDA stream given to hplmm_create (0 = legacy
+ *   default stream).  hplmm_assemble, hplmm_setup and hplmm_solve
+ *   synchronise that stream before returning; hplmm_apply* are asynchronous.
+ * - "device" pointers are CUDA device (or managed) memory owned by the caller;
+ *   "host" pointers are ordinary host memory owned by the caller.  The context
+ *   owns every internal buffer and frees it in hplmm_destroy.
+ * - Vectors of length n_dof hold the free degrees of freedom in the paper's
+ *   fine-grid numbering: existing nodes in lexicographic order (x fastest),
+ *   the x,y,z components of a node consecutive, Dirichlet components removed
+ *   (Section 2, Eq. ls_all).  All such vectors are float64.
+ * - Voxel arrays are [nz][ny][nx] with x fastest; voxel (i,j,k) spans
+ *   [i,i+1]x[j,j+1]x[k,k+1] (h = 1).
+ */
+#ifndef HPLMM_H
+#define HPLMM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct hplmm_ctx hplmm_ctx;
+
+typedef enum {
+  HPLMM_OK = 0,
+  HPLMM_NOT_CONVERGED = 1,
+  HPLMM_ERR_INVALID = -1,   /* bad argument, size or call order detected on the host */
+  HPLMM_ERR_OOM = -2,       /* a device allocation failed */
+  HPLMM_ERR_CUDA = -3,      /* a CUDA runtime error */
+  HPLMM_ERR_SINGULAR = -4,  /* a non-positive pivot in a local or coarse Cholesky factorisation */
+  HPLMM_ERR_TIMEOUT = -5,   /* a device-side wait ran out of its iteration budget */
+  HPLMM_ERR_STATE = -6      /* call out of order (e.g. apply before setup) */
+} hplmm_status;
+
+typedef enum { HPLMM_FP64 = 0, HPLMM_FP32 = 1, HPLMM_BF16 = 2 } hplmm_prec;
+
+/* Options (zero-initialise, then call hplmm_default_options). */
+typedef struct {
+  int n_mortar;          /* n: maximum mortar nodes per contact interface (Section 3.3; paper sweeps 1,2,4,8) */
+  double beta;           /* Gaussian mortar spread, Eq. gauss (paper: 4) */
+  int contact_halfwidth; /* w: contact grid = nodes within L-inf distance w of an interface (Section 3.1) */
+  int n_st;              /* smoother stages, Eq. local_smoother (paper: 1 with M_CG) */
+  hplmm_prec local_prec; /* precision of local factorisations and basis solves: FP64 or FP32 */
+  hplmm_prec apply_prec; /* precision of the preconditioner apply (SpMV, smoother, restriction and
+                            prolongation): FP64, FP32 or BF16 storage, FP32 accumulation for the latter two */
+  int restart;           /* GMRES restart length (default 30) */
+  int max_iters;         /* cap on total GMRES iterations (paper: 300) */
+  int strict_two_grain;  /* 1: shape vectors only on the two grains of each interface (the paper's
+                            literal Eq. col_pk); 0 (default): on every grain whose voxels touch it */
+  int use_graph;         /* 1: replay the preconditioner apply as a captured CUDA graph */
+  int verbose;           /* 1: print phase timings to stderr */
+} hplmm_options;
+
+/* Boundary conditions on the six faces of the image box, in the order
+ * x=0, x=nx, y=0, y=ny, z=0, z=nz (Eq. BC).  fix[f][d] != 0 prescribes
+ * displacement component d on face f to value[f][d] (a later face overrides
+ * an earlier one on shared nodes); traction[f] is a uniform traction on the
+ * solid part of face f, applied to components that are not fixed. */
+typedef struct {
+  uint8_t fix[6][3];
+  double value[6][3];
+  double traction[6][3];
+} hplmm_bcs;
+
+typedef struct {
+  int iters;              /* Arnoldi steps taken */
+  int restarts;           /* completed restart cycles */
+  double rel_res_true;    /* ||b - A x|| / ||b|| recomputed in FP64 at exit */
+  double t_setup_ml;      /* smoother build (local factorisations of grains and contact grids), s */
+  double t_setup_mg;      /* coarse build (maps, mortars, basis solves, Galerkin, coarse Cholesky), s */
+  double t_solve;         /* GMRES, s */
+  long long n_dof;        /* free fine DOFs */
+  long long n_coarse;     /* coarse dimension N^o = N^o_m + kept corrections */
+  long long n_interfaces; /* contact interfaces N^c (= contact grids N^zeta) */
+  long long n_grains;     /* grain grids N^g */
+} hplmm_stats;
+
+/* Fill `opt` with the defaults: n=4, beta=4, w=2, n_st=1, FP64 locals and apply,
+ * restart 30, 300 iterations, default coupling, no graph. */
+void hplmm_default_options(hplmm_options *opt);
+
+/* Create a context bound to the current CUDA device and `cuda_stream`
+ * (a cudaStream_t, or NULL for the legacy default stream).  `opt` may be NULL
+ * for defaults; it is copied.  Returns HPLMM_ERR_INVALID on bad options. */
+hplmm_status hplmm_create(hplmm_ctx **ctx, const hplmm_options *opt, void *cuda_stream);
+
+/* Assemble A_hat and b_hat (Section 2, Eqs. stiff_iso, BC, ls_all) from a voxel
+ * image.  mask: DEVICE uint8 [nz][ny][nx], 1 = solid (the caller keeps one
+ * connected component attached to a Dirichlet face; otherwise a local or
+ * coarse factorisation reports HPLMM_ERR_SINGULAR).  E: DEVICE float32 per
+ * voxel, or NULL for the constant E0.  bcs: HOST.  n_dof_out: HOST, receives
+ * the number of free DOFs.  b_out: DEVICE float64 [n_dof] or NULL.  Replaces
+ * any earlier assembly and set-up in this context.  Synchronises. */
+hplmm_status hplmm_assemble(hplmm_ctx *ctx, const uint8_t *mask, int nx, int ny, int nz,
+                            const float *E, double E0, double nu, const hplmm_bcs *bcs,
+                            double *b_out, long long *n_dof_out);
+
+/* Build the preconditioner (T_MG + T_ML): grain grids, contact interfaces,
+ * W, mortars and Gaussian Q^o (Sections 3.1-3.3, 4.2), shape and correction
+ * vectors (Eqs. col_pk, col_cg), A^o = P_hat^T A_hat P_hat and its Cholesky
+ * factor (Eq. mg_struct), and the local factorisations of the contact-grain
+ * smoother (Eqs. local_smoother_CG, Mg_Mz).
+ * partition: DEVICE int32 grain id per voxel (values in [0, n_grains), void
+ * voxels ignored), or NULL for the Cartesian slicing into px*py*pz grains.
+ * b: DEVICE float64 [n_dof] right-hand side defining the correction columns,
+ * or NULL for the assembled b_hat.  Synchronises. */
+hplmm_status hplmm_setup(hplmm_ctx *ctx, const int32_t *partition, int n_grains,
+                         int px, int py, int pz, const double *b);
+
+/* z = M^{-1} r, the full multiplicative preconditioner of Eq. multi_precond
+ * (M_G first, then n_st stages of M_CG).  r, z: DEVICE float64 [n_dof];
+ * they may not alias.  Asynchronous on the context's stream. */
+hplmm_status hplmm_apply(hplmm_ctx *ctx, const double *r, double *z);
+
+/* z = M_G^{-1} r = P_hat (A^o)^{-1} P_hat^T r (Eq. mg_struct); with r = b_hat
+ * this is the first-pass solution of Section 6.1.  DEVICE float64 [n_dof]. */
+hplmm_status hplmm_apply_coarse(hplmm_ctx *ctx, const double *r, double *z);
+
+/* z = M_CG^{-1} r, one stage of the contact-grain smoother (Eq.
+ * local_smoother_CG).  DEVICE float64 [n_dof]. */
+hplmm_status hplmm_apply_smoother(hplmm_ctx *ctx, const double *r, double *z);
+
+/* y = A_hat x in FP64.  DEVICE float64 [n_dof]. */
+hplmm_status hplmm_spmv(hplmm_ctx *ctx, const double *x, double *y);
+
+/* Right-preconditioned FGMRES(restart) with CGS2 Arnoldi in FP64 (Section 5),
+ * x_0 = 0, stopping when ||b - A x|| / ||b|| <= tol (true residual checked
+ * at the end of each cycle) or after max_iters steps.  b: DEVICE float64
+ * [n_dof] or NULL for b_hat; x: DEVICE float64 [n_dof] (output).  st: HOST,
+ * may be NULL.  Returns HPLMM_OK or HPLMM_NOT_CONVERGED.  Synchronises. */
+hplmm_status hplmm_solve(hplmm_ctx *ctx, const double *b, double *x, double tol, hplmm_stats *st);
+
+/* Sizes of the index maps, for hplmm_get_maps.  HOST outputs. */
+typedef struct {
+  long long n_nodes;        /* existing fine nodes */
+  long long n_dof;
+  long long n_grains;
+  long long n_interfaces;
+  long long n_iface_nodes;  /* nodes on contact interfaces (with a free DOF) */
+  long long n_mortars;      /* mortar nodes over all interfaces */
+  long long n_mortar_cols;  /* N^o_m */
+  long long n_coarse;       /* N^o */
+} hplmm_sizes;
+
+hplmm_status hplmm_get_sizes(hplmm_ctx *ctx, hplmm_sizes *out);
+
+/* Copy the set-up's integer maps and mortar weights into caller arrays
+ * (any pointer may be NULL to skip it).  Arrays are DEVICE memory.
+ *   node_ijk       int32 [n_nodes][3]    grid coordinates of each existing node
+ *   W              int64 [n_dof]         free-DOF index at each position of the W order (Eq. permute)
+ *   iface_pair     int32 [n_interfaces][2] grains (a < b) of each interface
+ *   iface_nodes    int32 [n_iface_nodes] node ids of interface 0, then 1, ... (ascending within)
+ *   iface_offsets  int32 [n_interfaces+1]
+ *   mortar_nodes   int32 [n_mortars]     mortar node ids of interface 0, then 1, ... (mortar order)
+ *   mortar_offsets int32 [n_interfaces+1]
+ *   eta            float64 [n_iface_nodes x ...] weights eta_i(y): for interface c, a row-major
+ *                  block (nodes of c) x (mortars of c), blocks in interface order
+ * Synchronises. */
+hplmm_status hplmm_get_maps(hplmm_ctx *ctx, int32_t *node_ijk, int64_t *W, int32_t *iface_pair,
+                            int32_t *iface_nodes, int32_t *iface_offsets, int32_t *mortar_nodes,
+                            int32_t *mortar_offsets, double *eta);
+
+/* Copy the coarse matrix A^o (N^o x N^o, row-major float64, DEVICE) -- the
+ * symmetrised Galerkin product of Eq. mg_struct.  Synchronises. */
+hplmm_status hplmm_get_coarse_matrix(hplmm_ctx *ctx, double *A_o);
+
+/* Copy column `col` of P_hat in the free-DOF numbering (DEVICE float64 [n_dof]). */
+hplmm_status hplmm_get_prolongation_column(hplmm_ctx *ctx, long long col, double *out);
+
+/* Message of the most recent error in this context (never NULL). */
+const char *hplmm_last_error(const hplmm_ctx *ctx);
+
+/* Free every device and host resource of the context.  NULL is ignored. */
+void hplmm_destroy(hplmm_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HPLMM_H */

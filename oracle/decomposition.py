@@ -51,7 +51,7 @@ class Decomposition:
         self.n_grains = int(n_grains)
         nz, ny, nx = mesh.nz, mesh.ny, mesh.nx
         gpad = np.full((nz + 2, ny + 2, nx + 2), BIG, np.int64)
-        gpad[1:-1, 1:-1, 1:-1] = np.where(mesh.solid, grain_of_voxel, BIG)
+        gpad[1:-1, 1:-1, 1:-1] = np.where(mesh.solid, np.asarray(grain_of_voxel, np.int64), BIG)
         ii, jj, kk = mesh.node_ijk[:, 0], mesh.node_ijk[:, 1], mesh.node_ijk[:, 2]
         G8 = np.empty((mesh.n_nodes, 8), np.int64)
         t = 0

@@ -1,0 +1,345 @@
+"""Python binding of libhplmm.so, the GB300 (sm_103a) library for algebraic
+hPLMM (two-level multiscale preconditioner for Q1 voxel elasticity, used in
+right-preconditioned GMRES).
+
+This module only marshals arguments: every step of assembly, set-up, apply and
+solve runs in the library's CUDA kernels.  Device arrays are torch CUDA tensors
+(PyTorch is used for device memory and streams only).  There is no CPU
+fallback: importing works without a GPU, but every call needs the built
+library and a CUDA device, and a missing library raises at first use.
+
+The functions below carry the C interface's names (include/hplmm.h); `Solver`
+wraps one context for convenience.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libhplmm.so")
+
+HPLMM_OK = 0
+HPLMM_NOT_CONVERGED = 1
+HPLMM_ERR_INVALID = -1
+HPLMM_ERR_OOM = -2
+HPLMM_ERR_CUDA = -3
+HPLMM_ERR_SINGULAR = -4
+HPLMM_ERR_TIMEOUT = -5
+HPLMM_ERR_STATE = -6
+HPLMM_FP64, HPLMM_FP32, HPLMM_BF16 = 0, 1, 2
+PREC = {"fp64": HPLMM_FP64, "fp32": HPLMM_FP32, "bf16": HPLMM_BF16}
+
+EXPORTED = [
+    "hplmm_default_options", "hplmm_create", "hplmm_assemble", "hplmm_setup", "hplmm_apply",
+    "hplmm_apply_coarse", "hplmm_apply_smoother", "hplmm_spmv", "hplmm_solve", "hplmm_get_sizes",
+    "hplmm_get_maps", "hplmm_get_coarse_matrix", "hplmm_get_prolongation_column", "hplmm_last_error",
+    "hplmm_destroy",
+]
+
+
+class hplmm_options(ctypes.Structure):
+    _fields_ = [("n_mortar", ctypes.c_int), ("beta", ctypes.c_double), ("contact_halfwidth", ctypes.c_int),
+                ("n_st", ctypes.c_int), ("local_prec", ctypes.c_int), ("apply_prec", ctypes.c_int),
+                ("restart", ctypes.c_int), ("max_iters", ctypes.c_int), ("strict_two_grain", ctypes.c_int),
+                ("use_graph", ctypes.c_int), ("verbose", ctypes.c_int)]
+
+
+class hplmm_bcs(ctypes.Structure):
+    _fields_ = [("fix", (ctypes.c_uint8 * 3) * 6), ("value", (ctypes.c_double * 3) * 6),
+                ("traction", (ctypes.c_double * 3) * 6)]
+
+
+class hplmm_stats(ctypes.Structure):
+    _fields_ = [("iters", ctypes.c_int), ("restarts", ctypes.c_int), ("rel_res_true", ctypes.c_double),
+                ("t_setup_ml", ctypes.c_double), ("t_setup_mg", ctypes.c_double), ("t_solve", ctypes.c_double),
+                ("n_dof", ctypes.c_longlong), ("n_coarse", ctypes.c_longlong),
+                ("n_interfaces", ctypes.c_longlong), ("n_grains", ctypes.c_longlong)]
+
+
+class hplmm_sizes(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_longlong) for n in ("n_nodes", "n_dof", "n_grains", "n_interfaces", "n_iface_nodes",
+                                                   "n_mortars", "n_mortar_cols", "n_coarse")]
+
+
+_lib = None
+
+
+def load_library():
+    """Load libhplmm.so (built in-tree); raise if it is missing."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"{LIB_PATH} is missing; build it with `python -m paper_2509_19777_gb300.build` "
+                           "(the library has no CPU fallback)")
+    lib = ctypes.CDLL(LIB_PATH)
+    P, I, D, LL = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_longlong
+    sig = {
+        "hplmm_default_options": (None, [ctypes.POINTER(hplmm_options)]),
+        "hplmm_create": (I, [ctypes.POINTER(P), ctypes.POINTER(hplmm_options), P]),
+        "hplmm_assemble": (I, [P, P, I, I, I, P, D, D, ctypes.POINTER(hplmm_bcs), P, ctypes.POINTER(LL)]),
+        "hplmm_setup": (I, [P, P, I, I, I, I, P]),
+        "hplmm_apply": (I, [P, P, P]),
+        "hplmm_apply_coarse": (I, [P, P, P]),
+        "hplmm_apply_smoother": (I, [P, P, P]),
+        "hplmm_spmv": (I, [P, P, P]),
+        "hplmm_solve": (I, [P, P, P, D, ctypes.POINTER(hplmm_stats)]),
+        "hplmm_get_sizes": (I, [P, ctypes.POINTER(hplmm_sizes)]),
+        "hplmm_get_maps": (I, [P, P, P, P, P, P, P, P, P]),
+        "hplmm_get_coarse_matrix": (I, [P, P]),
+        "hplmm_get_prolongation_column": (I, [P, LL, P]),
+        "hplmm_last_error": (ctypes.c_char_p, [P]),
+        "hplmm_destroy": (None, [P]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = lib
+    return lib
+
+
+class HplmmError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"hplmm status {code}: {msg}")
+        self.code = code
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _check(ctx, rc, allow=(HPLMM_OK,)):
+    if rc not in allow:
+        msg = load_library().hplmm_last_error(ctx).decode() if ctx else ""
+        raise HplmmError(rc, msg)
+    return rc
+
+
+# ---- functions with the C interface's names -------------------------------------------------
+def hplmm_default_options():
+    o = hplmm_options()
+    load_library().hplmm_default_options(ctypes.byref(o))
+    return o
+
+
+def hplmm_create(options=None, stream=None):
+    """Create a context on the current CUDA device and `stream` (torch stream or raw handle)."""
+    import torch
+    lib = load_library()
+    ctx = ctypes.c_void_p()
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    handle = stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
+    rc = lib.hplmm_create(ctypes.byref(ctx), ctypes.byref(options) if options is not None else None,
+                          ctypes.c_void_p(handle))
+    if rc != HPLMM_OK:
+        raise HplmmError(rc, "hplmm_create failed")
+    return ctx
+
+
+def make_bcs(bcs):
+    """Face dictionary (synth.FACES order) or (fix, value, traction) arrays -> hplmm_bcs."""
+    if isinstance(bcs, dict):
+        from synth import bcs_dict_to_arrays
+        fix, val, tra = bcs_dict_to_arrays(bcs)
+    else:
+        fix, val, tra = bcs
+    b = hplmm_bcs()
+    for f in range(6):
+        for d in range(3):
+            b.fix[f][d] = int(fix[f][d])
+            b.value[f][d] = float(val[f][d])
+            b.traction[f][d] = float(tra[f][d])
+    return b
+
+
+def hplmm_assemble(ctx, mask, E, nu, bcs, b_out=None, E0=1.0):
+    nz, ny, nx = mask.shape
+    n = ctypes.c_longlong(0)
+    bc = bcs if isinstance(bcs, hplmm_bcs) else make_bcs(bcs)
+    _check(ctx, load_library().hplmm_assemble(ctx, _ptr(mask), nx, ny, nz, _ptr(E), float(E0), float(nu),
+                                              ctypes.byref(bc), _ptr(b_out), ctypes.byref(n)))
+    return n.value
+
+
+def hplmm_setup(ctx, partition=None, n_grains=0, grains=(1, 1, 1), b=None):
+    px, py, pz = grains
+    _check(ctx, load_library().hplmm_setup(ctx, _ptr(partition), int(n_grains), px, py, pz, _ptr(b)))
+
+
+def hplmm_apply(ctx, r, z):
+    _check(ctx, load_library().hplmm_apply(ctx, _ptr(r), _ptr(z)))
+
+
+def hplmm_apply_coarse(ctx, r, z):
+    _check(ctx, load_library().hplmm_apply_coarse(ctx, _ptr(r), _ptr(z)))
+
+
+def hplmm_apply_smoother(ctx, r, z):
+    _check(ctx, load_library().hplmm_apply_smoother(ctx, _ptr(r), _ptr(z)))
+
+
+def hplmm_spmv(ctx, x, y):
+    _check(ctx, load_library().hplmm_spmv(ctx, _ptr(x), _ptr(y)))
+
+
+def hplmm_solve(ctx, b, x, tol=1e-8):
+    st = hplmm_stats()
+    rc = load_library().hplmm_solve(ctx, _ptr(b), _ptr(x), float(tol), ctypes.byref(st))
+    _check(ctx, rc, allow=(HPLMM_OK, HPLMM_NOT_CONVERGED))
+    return rc, st
+
+
+def hplmm_get_sizes(ctx):
+    s = hplmm_sizes()
+    _check(ctx, load_library().hplmm_get_sizes(ctx, ctypes.byref(s)))
+    return {n: getattr(s, n) for n, _ in hplmm_sizes._fields_}
+
+
+def hplmm_get_maps(ctx, device="cuda"):
+    """Integer maps and mortar weights of the set-up, as numpy arrays."""
+    import torch
+    sz = hplmm_get_sizes(ctx)
+    i32 = dict(dtype=torch.int32, device=device)
+    node_ijk = torch.empty(sz["n_nodes"] * 3, **i32)
+    W = torch.empty(max(sz["n_dof"], 1), dtype=torch.int64, device=device)
+    pair = torch.empty(max(2 * sz["n_interfaces"], 1), **i32)
+    inodes = torch.empty(max(sz["n_iface_nodes"], 1), **i32)
+    ioff = torch.empty(sz["n_interfaces"] + 1, **i32)
+    mnodes = torch.empty(max(sz["n_mortars"], 1), **i32)
+    moff = torch.empty(sz["n_interfaces"] + 1, **i32)
+    # eta block sizes follow from the offsets; allocate generously (nodes x max mortars)
+    eta = torch.empty(max(sz["n_iface_nodes"] * max(1, 128), 1), dtype=torch.float64, device=device)
+    _check(ctx, load_library().hplmm_get_maps(ctx, _ptr(node_ijk), _ptr(W), _ptr(pair), _ptr(inodes), _ptr(ioff),
+                                              _ptr(mnodes), _ptr(moff), _ptr(eta)))
+    ioff_h = ioff.cpu().numpy()
+    moff_h = moff.cpu().numpy()
+    n_eta = int(sum((ioff_h[c + 1] - ioff_h[c]) * (moff_h[c + 1] - moff_h[c]) for c in range(sz["n_interfaces"])))
+    return {
+        "node_ijk": node_ijk.cpu().numpy().reshape(-1, 3),
+        "W": W.cpu().numpy()[:sz["n_dof"]],
+        "iface_pair": pair.cpu().numpy()[:2 * sz["n_interfaces"]].reshape(-1, 2),
+        "iface_nodes": inodes.cpu().numpy()[:sz["n_iface_nodes"]],
+        "iface_offsets": ioff_h,
+        "mortar_nodes": mnodes.cpu().numpy()[:sz["n_mortars"]],
+        "mortar_offsets": moff_h,
+        "eta": eta.cpu().numpy()[:n_eta],
+        "sizes": sz,
+    }
+
+
+def hplmm_get_coarse_matrix(ctx, device="cuda"):
+    import torch
+    n = hplmm_get_sizes(ctx)["n_coarse"]
+    A = torch.empty(max(n * n, 1), dtype=torch.float64, device=device)
+    _check(ctx, load_library().hplmm_get_coarse_matrix(ctx, _ptr(A)))
+    return A[:n * n].reshape(n, n)
+
+
+def hplmm_get_prolongation_column(ctx, col, out):
+    _check(ctx, load_library().hplmm_get_prolongation_column(ctx, int(col), _ptr(out)))
+
+
+def hplmm_last_error(ctx):
+    return load_library().hplmm_last_error(ctx).decode()
+
+
+def hplmm_destroy(ctx):
+    if ctx:
+        load_library().hplmm_destroy(ctx)
+
+
+# ---- convenience wrapper ---------------------------------------------------------------------
+class Solver:
+    """One library context: assemble -> setup -> apply / solve, on torch CUDA tensors."""
+
+    def __init__(self, n_mortar=4, beta=4.0, contact_halfwidth=2, n_st=1, local_prec="fp64", apply_prec="fp64",
+                 restart=30, max_iters=300, strict_two_grain=False, use_graph=False, verbose=False, stream=None):
+        o = hplmm_default_options()
+        o.n_mortar, o.beta, o.contact_halfwidth, o.n_st = n_mortar, beta, contact_halfwidth, n_st
+        o.local_prec, o.apply_prec = PREC[local_prec], PREC[apply_prec]
+        o.restart, o.max_iters = restart, max_iters
+        o.strict_two_grain, o.use_graph, o.verbose = int(strict_two_grain), int(use_graph), int(verbose)
+        self.options = o
+        self.ctx = hplmm_create(o, stream)
+        self.n_dof = 0
+
+    def close(self):
+        hplmm_destroy(self.ctx)
+        self.ctx = None
+
+    def __del__(self):
+        try:
+            if getattr(self, "ctx", None):
+                self.close()
+        except Exception:
+            pass
+
+    def assemble(self, mask, E, nu, bcs, E0=1.0):
+        import torch
+        self.n_dof = hplmm_assemble(self.ctx, mask, E, nu, bcs, None, E0)
+        self.b = torch.empty(self.n_dof, dtype=torch.float64, device=mask.device)
+        hplmm_assemble(self.ctx, mask, E, nu, bcs, self.b, E0)
+        return self.n_dof
+
+    def setup(self, grains=(1, 1, 1), partition=None, n_grains=0, b=None):
+        hplmm_setup(self.ctx, partition, n_grains, grains, b)
+
+    def apply(self, r, z=None):
+        import torch
+        z = torch.empty_like(r) if z is None else z
+        hplmm_apply(self.ctx, r, z)
+        return z
+
+    def apply_coarse(self, r, z=None):
+        import torch
+        z = torch.empty_like(r) if z is None else z
+        hplmm_apply_coarse(self.ctx, r, z)
+        return z
+
+    def apply_smoother(self, r, z=None):
+        import torch
+        z = torch.empty_like(r) if z is None else z
+        hplmm_apply_smoother(self.ctx, r, z)
+        return z
+
+    def spmv(self, x, y=None):
+        import torch
+        y = torch.empty_like(x) if y is None else y
+        hplmm_spmv(self.ctx, x, y)
+        return y
+
+    def solve(self, b=None, x=None, tol=1e-8):
+        import torch
+        x = torch.empty(self.n_dof, dtype=torch.float64, device="cuda") if x is None else x
+        rc, st = hplmm_solve(self.ctx, b, x, tol)
+        return x, rc, st
+
+    def sizes(self):
+        return hplmm_get_sizes(self.ctx)
+
+    def maps(self):
+        return hplmm_get_maps(self.ctx)
+
+    def coarse_matrix(self):
+        return hplmm_get_coarse_matrix(self.ctx)
+
+    def prolongation_column(self, col, out=None):
+        import torch
+        out = torch.empty(self.n_dof, dtype=torch.float64, device="cuda") if out is None else out
+        hplmm_get_prolongation_column(self.ctx, col, out)
+        return out
+
+
+def problem_to_device(problem, device="cuda"):
+    """synth.Problem -> (mask uint8, E float32) device tensors."""
+    import torch
+    mask = torch.from_numpy(np.ascontiguousarray(problem.mask.astype(np.uint8))).to(device)
+    E = torch.from_numpy(np.ascontiguousarray(problem.E.astype(np.float32))).to(device)
+    return mask, E

@@ -1,0 +1,251 @@
+// Preconditioner application and the outer Krylov solver.
+//
+// Eq. multi_precond: M^{-1} r = z1 + M_L^{-1}(r - A_hat z1), z1 = M_G^{-1} r.
+// Eq. local_smoother: n_st stages of the base smoother on the running residual.
+// Eq. local_smoother_CG: M_CG^{-1} r = z_zeta + M_g^{-1}(r - A_hat z_zeta),
+//   z_zeta = M_zeta^{-1} r (contact grids, overlapping: atomic adds);
+//   M_g^{-1} on disjoint grain interiors.
+// Section 5: right-preconditioned GMRES.  Because the mixed-precision apply is
+// not exactly linear, the flexible variant (FGMRES, storing Z_j = M^{-1} v_j) is
+// used; classical Gram-Schmidt with one re-orthogonalisation (CGS2) keeps the
+// Arnoldi basis orthogonal in FP64 with two block reductions per step.
+#include "common.cuh"
+
+#include <chrono>
+#include <cmath>
+
+namespace hp {
+namespace {
+
+__global__ void k_axpby(double *y, const double *x, double a, double b, long long n) {
+  long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) y[i] = a * x[i] + b * y[i];
+}
+
+__global__ void k_add2(double *z, const double *a, const double *b, long long n) {
+  long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) z[i] = a[i] + b[i];
+}
+
+__global__ void k_scale_copy(double *y, const double *x, double a, long long n) {
+  long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) y[i] = a * x[i];
+}
+
+constexpr int MDOT_BLOCKS = 304;
+constexpr int MAXV = 64;
+
+// partial[b][j] = sum over block b's slice of V_j . w  (j < nv); nv <= MAXV
+__global__ void __launch_bounds__(256) k_mdot(const double *V, long long ldv, int nv, const double *w, long long n,
+                                              double *partial) {
+  __shared__ double red[8][MAXV];
+  int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  double acc[MAXV];
+  for (int j = 0; j < nv; ++j) acc[j] = 0.0;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    double wi = w[i];
+    for (int j = 0; j < nv; ++j) acc[j] += V[j * ldv + i] * wi;
+  }
+  for (int j = 0; j < nv; ++j) {
+    double s = acc[j];
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    if (lane == 0) red[wid][j] = s;
+  }
+  __syncthreads();
+  for (int j = threadIdx.x; j < nv; j += blockDim.x) {
+    double s = 0.0;
+    for (int w2 = 0; w2 < 8; ++w2) s += red[w2][j];
+    partial[(long long)blockIdx.x * MAXV + j] = s;
+  }
+}
+
+__global__ void k_mdot_final(const double *partial, int nblocks, int nv, double *out) {
+  int j = threadIdx.x;
+  if (j >= nv) return;
+  double s = 0.0;
+  for (int b = 0; b < nblocks; ++b) s += partial[(long long)b * MAXV + j];
+  out[j] = s;
+}
+
+// w -= sum_j V_j h[j]
+__global__ void k_mupdate(double *w, const double *V, long long ldv, int nv, const double *h, long long n) {
+  __shared__ double hs[MAXV];
+  for (int j = threadIdx.x; j < nv; j += blockDim.x) hs[j] = h[j];
+  __syncthreads();
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    double s = w[i];
+    for (int j = 0; j < nv; ++j) s -= V[j * ldv + i] * hs[j];
+    w[i] = s;
+  }
+}
+
+// x += sum_j Z_j y[j]
+__global__ void k_mcombine(double *x, const double *Z, long long ldz, int nv, const double *y, long long n) {
+  __shared__ double ys[MAXV];
+  for (int j = threadIdx.x; j < nv; j += blockDim.x) ys[j] = y[j];
+  __syncthreads();
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    double s = x[i];
+    for (int j = 0; j < nv; ++j) s += Z[j * ldz + i] * ys[j];
+    x[i] = s;
+  }
+}
+
+void mdot(hplmm_ctx *c, const double *V, long long ldv, int nv, const double *w, long long n, double *out) {
+  k_mdot<<<MDOT_BLOCKS, 256, 0, c->stream>>>(V, ldv, nv, w, n, c->w_partial.p);
+  HP_CHECK_LAUNCH();
+  k_mdot_final<<<1, MAXV, 0, c->stream>>>(c->w_partial.p, MDOT_BLOCKS, nv, out);
+  HP_CHECK_LAUNCH();
+}
+
+}  // namespace
+
+void check_status(hplmm_ctx *c) {
+  int st = 0;
+  HP_CUDA(cudaMemcpyAsync(&st, c->status.p, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+  HP_CUDA(cudaStreamSynchronize(c->stream));
+  if (st != 0) {
+    hplmm_status code = (hplmm_status)st;
+    if (code == HPLMM_ERR_SINGULAR) throw Error(code, "non-positive pivot in a Cholesky factorisation (singular local or coarse matrix)");
+    if (code == HPLMM_ERR_TIMEOUT) throw Error(code, "a device-side wait ran out of its budget");
+    throw Error(HPLMM_ERR_CUDA, "device error word " + std::to_string(st));
+  }
+}
+
+void smoother_stage(hplmm_ctx *c, const double *r_pad, double *z_pad) {
+  cudaStream_t s = c->stream;
+  long long L = 3LL * c->n_nodes;
+  // z_zeta = M_zeta^{-1} r
+  HP_CUDA(cudaMemsetAsync(c->w_zz.p, 0, sizeof(double) * L, s));
+  smoother_apply(c, c->contacts, r_pad, c->w_zz.p, true);
+  // r2 = r - A z_zeta
+  spmv(c, c->w_zz.p, c->w_r2.p, c->opt.apply_prec, r_pad);
+  // z_g = M_g^{-1} r2 (disjoint grain interiors)
+  HP_CUDA(cudaMemsetAsync(c->w_zg.p, 0, sizeof(double) * L, s));
+  smoother_apply(c, c->grains, c->w_r2.p, c->w_zg.p, false);
+  k_add2<<<grid_for(L, 256), 256, 0, s>>>(z_pad, c->w_zz.p, c->w_zg.p, L);
+  HP_CHECK_LAUNCH();
+}
+
+void precond_apply(hplmm_ctx *c, const double *r_pad, double *z_pad) {
+  cudaStream_t s = c->stream;
+  long long L = 3LL * c->n_nodes;
+  // z1 = M_G^{-1} r
+  coarse_apply(c, r_pad, c->w_z1.p);
+  // r1 = r - A z1
+  spmv(c, c->w_z1.p, c->w_r1.p, c->opt.apply_prec, r_pad);
+  // n_st stages of M_CG on the running residual
+  HP_CUDA(cudaMemcpyAsync(z_pad, c->w_z1.p, sizeof(double) * L, cudaMemcpyDeviceToDevice, s));
+  for (int st = 0; st < c->opt.n_st; ++st) {
+    smoother_stage(c, c->w_r1.p, c->w_t.p);
+    k_axpby<<<grid_for(L, 256), 256, 0, s>>>(z_pad, c->w_t.p, 1.0, 1.0, L);
+    HP_CHECK_LAUNCH();
+    if (st + 1 < c->opt.n_st) {
+      // res <- res - A t
+      spmv(c, c->w_t.p, c->w_r2.p, c->opt.apply_prec, c->w_r1.p);
+      HP_CUDA(cudaMemcpyAsync(c->w_r1.p, c->w_r2.p, sizeof(double) * L, cudaMemcpyDeviceToDevice, s));
+    }
+  }
+}
+
+int fgmres(hplmm_ctx *c, const double *b_pad, double *x_pad, double tol, hplmm_stats *st) {
+  cudaStream_t s = c->stream;
+  long long L = 3LL * c->n_nodes;
+  int m = c->opt.restart;
+  int maxit = c->opt.max_iters;
+  double *V = c->V.p, *Z = c->Z.p;
+  double *w = c->w_w.p;
+  double *dev_h = c->w_h.p;  // [0..m]: h1, [MAXV..]: h2, [2*MAXV]: norm^2
+  std::vector<double> H((size_t)(m + 1) * m, 0.0), cs(m, 0.0), sn(m, 0.0), gv(m + 1, 0.0), y(m, 0.0);
+  std::vector<double> hh(2 * MAXV + 1, 0.0);
+  HP_CUDA(cudaMemsetAsync(x_pad, 0, sizeof(double) * L, s));
+  mdot(c, b_pad, 0, 1, b_pad, L, dev_h);
+  HP_CUDA(cudaMemcpyAsync(hh.data(), dev_h, sizeof(double), cudaMemcpyDeviceToHost, s));
+  HP_CUDA(cudaStreamSynchronize(s));
+  double bnorm = std::sqrt(hh[0]);
+  int its = 0, restarts = 0;
+  double rel = 0.0;
+  if (bnorm == 0.0) {
+    if (st) {
+      st->iters = 0;
+      st->restarts = 0;
+      st->rel_res_true = 0.0;
+    }
+    return HPLMM_OK;
+  }
+  for (;;) {
+    // r = b - A x (true residual, FP64)
+    spmv(c, x_pad, V, HPLMM_FP64, b_pad);
+    mdot(c, V, 0, 1, V, L, dev_h);
+    HP_CUDA(cudaMemcpyAsync(hh.data(), dev_h, sizeof(double), cudaMemcpyDeviceToHost, s));
+    HP_CUDA(cudaStreamSynchronize(s));
+    double beta = std::sqrt(hh[0]);
+    rel = beta / bnorm;
+    if (c->opt.verbose) fprintf(stderr, "[hplmm] fgmres cycle %d: its=%d true rel=%.3e\n", restarts, its, rel);
+    if (rel <= tol || its >= maxit) break;
+    k_scale_copy<<<grid_for(L, 256), 256, 0, s>>>(V, V, 1.0 / beta, L);
+    HP_CHECK_LAUNCH();
+    std::fill(gv.begin(), gv.end(), 0.0);
+    gv[0] = beta;
+    int k = 0;
+    for (int j = 0; j < m; ++j) {
+      double *vj = V + (long long)j * L;
+      double *zj = Z + (long long)j * L;
+      precond_apply(c, vj, zj);
+      spmv(c, zj, w, HPLMM_FP64);
+      ++its;
+      // CGS2
+      mdot(c, V, L, j + 1, w, L, dev_h);
+      k_mupdate<<<MDOT_BLOCKS, 256, 0, s>>>(w, V, L, j + 1, dev_h, L);
+      HP_CHECK_LAUNCH();
+      mdot(c, V, L, j + 1, w, L, dev_h + MAXV);
+      k_mupdate<<<MDOT_BLOCKS, 256, 0, s>>>(w, V, L, j + 1, dev_h + MAXV, L);
+      HP_CHECK_LAUNCH();
+      mdot(c, w, 0, 1, w, L, dev_h + 2 * MAXV);
+      HP_CUDA(cudaMemcpyAsync(hh.data(), dev_h, sizeof(double) * (2 * MAXV + 1), cudaMemcpyDeviceToHost, s));
+      HP_CUDA(cudaStreamSynchronize(s));
+      for (int i = 0; i <= j; ++i) H[(size_t)i * m + j] = hh[i] + hh[MAXV + i];
+      double hn = std::sqrt(std::max(hh[2 * MAXV], 0.0));
+      H[(size_t)(j + 1) * m + j] = hn;
+      for (int i = 0; i < j; ++i) {
+        double a = H[(size_t)i * m + j], bb = H[(size_t)(i + 1) * m + j];
+        H[(size_t)i * m + j] = cs[i] * a + sn[i] * bb;
+        H[(size_t)(i + 1) * m + j] = -sn[i] * a + cs[i] * bb;
+      }
+      double a = H[(size_t)j * m + j], bb = H[(size_t)(j + 1) * m + j];
+      double den = std::hypot(a, bb);
+      cs[j] = a / den;
+      sn[j] = bb / den;
+      H[(size_t)j * m + j] = den;
+      H[(size_t)(j + 1) * m + j] = 0.0;
+      gv[j + 1] = -sn[j] * gv[j];
+      gv[j] = cs[j] * gv[j];
+      k = j + 1;
+      double est = std::fabs(gv[j + 1]) / bnorm;
+      if (c->opt.verbose) fprintf(stderr, "[hplmm]   it %d est %.3e\n", its, est);
+      if (hn > 0.0 && j + 1 < m + 1) {
+        k_scale_copy<<<grid_for(L, 256), 256, 0, s>>>(V + (long long)(j + 1) * L, w, 1.0 / hn, L);
+        HP_CHECK_LAUNCH();
+      }
+      if (est <= tol || hn == 0.0 || its >= maxit) break;
+    }
+    for (int i = k - 1; i >= 0; --i) {
+      double t = gv[i];
+      for (int q = i + 1; q < k; ++q) t -= H[(size_t)i * m + q] * y[q];
+      y[i] = t / H[(size_t)i * m + i];
+    }
+    HP_CUDA(cudaMemcpyAsync(dev_h, y.data(), sizeof(double) * k, cudaMemcpyHostToDevice, s));
+    k_mcombine<<<MDOT_BLOCKS, 256, 0, s>>>(x_pad, Z, L, k, dev_h, L);
+    HP_CHECK_LAUNCH();
+    ++restarts;
+  }
+  check_status(c);
+  if (st) {
+    st->iters = its;
+    st->restarts = restarts;
+    st->rel_res_true = rel;
+  }
+  return rel <= tol ? HPLMM_OK : HPLMM_NOT_CONVERGED;
+}
+
+}  // namespace hp

@@ -1,0 +1,388 @@
+// Fine-grid assembly (paper Section 2, Eqs. stiff_iso, BC, ls_all): Q1
+// hexahedra on unit voxels, the element stiffness E_e * K_ref(nu), Dirichlet
+// elimination and consistent face-traction loads, stored as a node-block
+// (3x3) BSR matrix over existing nodes.  Fixed components keep their slot in
+// every padded vector but their rows and columns are zero, so all internal
+// vectors are [n_nodes][3] with zeros on fixed slots.
+#include "common.cuh"
+
+namespace hp {
+namespace {
+
+__device__ __forceinline__ int corner_index(int ox, int oy, int oz) { return ox + 2 * oy + 4 * oz; }
+
+__global__ void k_node_exists(const uint8_t *mask, int nx, int ny, int nz, int *flag) {
+  long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  long long NX = nx + 1, NY = ny + 1, NZ = nz + 1;
+  if (g >= NX * NY * NZ) return;
+  int i = (int)(g % NX), j = (int)((g / NX) % NY), k = (int)(g / (NX * NY));
+  int any = 0;
+  for (int dk = -1; dk <= 0; ++dk)
+    for (int dj = -1; dj <= 0; ++dj)
+      for (int di = -1; di <= 0; ++di) {
+        int vi = i + di, vj = j + dj, vk = k + dk;
+        if (vi < 0 || vj < 0 || vk < 0 || vi >= nx || vj >= ny || vk >= nz) continue;
+        any |= mask[((long long)vk * ny + vj) * nx + vi] != 0;
+      }
+  flag[g] = any;
+}
+
+__global__ void k_node_finalize(const int *flag, int *ids, int *node_ijk, int nx, int ny, long long n_grid) {
+  long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= n_grid) return;
+  long long NX = nx + 1, NY = ny + 1;
+  if (flag[g]) {
+    int id = ids[g];
+    node_ijk[3 * id + 0] = (int)(g % NX);
+    node_ijk[3 * id + 1] = (int)((g / NX) % NY);
+    node_ijk[3 * id + 2] = (int)(g / (NX * NY));
+  } else {
+    ids[g] = -1;
+  }
+}
+
+// K_ref(nu): int over the unit cube of B^T D B with 2x2x2 Gauss-Legendre points, E = 1.
+// Voigt order (xx,yy,zz,yz,xz,xy), engineering shear; corner a = ax + 2 ay + 4 az.
+__global__ void k_kref(double nu, double *K) {
+  int r = threadIdx.x / 24, c = threadIdx.x % 24;
+  if (threadIdx.x >= 576) return;
+  double lam = nu / ((1.0 + nu) * (1.0 - 2.0 * nu));
+  double mu = 1.0 / (2.0 * (1.0 + nu));
+  double D[6][6] = {};
+  for (int a = 0; a < 3; ++a)
+    for (int b = 0; b < 3; ++b) D[a][b] = lam;
+  for (int a = 0; a < 3; ++a) {
+    D[a][a] += 2.0 * mu;
+    D[3 + a][3 + a] = mu;
+  }
+  const double g = 0.5 / sqrt(3.0);
+  const double pts[2] = {0.5 - g, 0.5 + g};
+  int na = r / 3, da = r % 3, nb = c / 3, db = c % 3;
+  double acc = 0.0;
+  for (int qz = 0; qz < 2; ++qz)
+    for (int qy = 0; qy < 2; ++qy)
+      for (int qx = 0; qx < 2; ++qx) {
+        double x[3] = {pts[qx], pts[qy], pts[qz]};
+        double ga[3], gb[3];
+        for (int s = 0; s < 2; ++s) {
+          int node = s ? nb : na;
+          int o[3] = {node & 1, (node >> 1) & 1, (node >> 2) & 1};
+          double f[3], sg[3];
+          for (int d = 0; d < 3; ++d) {
+            f[d] = o[d] ? x[d] : 1.0 - x[d];
+            sg[d] = o[d] ? 1.0 : -1.0;
+          }
+          double *gg = s ? gb : ga;
+          gg[0] = sg[0] * f[1] * f[2];
+          gg[1] = f[0] * sg[1] * f[2];
+          gg[2] = f[0] * f[1] * sg[2];
+        }
+        // Voigt strain column for (node, comp): Ba[6]
+        double Ba[6] = {}, Bb[6] = {};
+        for (int s = 0; s < 2; ++s) {
+          double *B = s ? Bb : Ba;
+          double *gg = s ? gb : ga;
+          int d = s ? db : da;
+          if (d == 0) { B[0] = gg[0]; B[4] = gg[2]; B[5] = gg[1]; }
+          if (d == 1) { B[1] = gg[1]; B[3] = gg[2]; B[5] = gg[0]; }
+          if (d == 2) { B[2] = gg[2]; B[3] = gg[1]; B[4] = gg[0]; }
+        }
+        double s = 0.0;
+        for (int p = 0; p < 6; ++p)
+          for (int q = 0; q < 6; ++q) s += Ba[p] * D[p][q] * Bb[q];
+        acc += 0.125 * s;
+      }
+  K[r * 24 + c] = acc;
+}
+
+struct BCDev {
+  uint8_t fix[6][3];
+  double value[6][3];
+  double traction[6][3];
+};
+
+__global__ void k_bc(const int *node_ijk, int n_nodes, int nx, int ny, int nz, const uint8_t *mask, BCDev bc,
+                     uint8_t *fixed, double *uD, double *f) {
+  int n = blockIdx.x * blockDim.x + threadIdx.x;
+  if (n >= n_nodes) return;
+  int p[3] = {node_ijk[3 * n], node_ijk[3 * n + 1], node_ijk[3 * n + 2]};
+  int lim[3] = {nx, ny, nz};
+  uint8_t fx[3] = {0, 0, 0};
+  double u[3] = {0, 0, 0}, t[3] = {0, 0, 0};
+  for (int face = 0; face < 6; ++face) {
+    int ax = face >> 1, side = face & 1;
+    int plane = side ? lim[ax] : 0;
+    if (p[ax] != plane) continue;
+    for (int d = 0; d < 3; ++d)
+      if (bc.fix[face][d]) {
+        fx[d] = 1;
+        u[d] = bc.value[face][d];
+      }
+    double tr0 = bc.traction[face][0], tr1 = bc.traction[face][1], tr2 = bc.traction[face][2];
+    if (tr0 != 0.0 || tr1 != 0.0 || tr2 != 0.0) {
+      int layer = side ? lim[ax] - 1 : 0;
+      int a1 = (ax + 1) % 3, a2 = (ax + 2) % 3;
+      int cnt = 0;
+      for (int o1 = -1; o1 <= 0; ++o1)
+        for (int o2 = -1; o2 <= 0; ++o2) {
+          int v[3];
+          v[ax] = layer;
+          v[a1] = p[a1] + o1;
+          v[a2] = p[a2] + o2;
+          if (v[a1] < 0 || v[a2] < 0 || v[a1] >= lim[a1] || v[a2] >= lim[a2]) continue;
+          cnt += mask[((long long)v[2] * ny + v[1]) * nx + v[0]] != 0;
+        }
+      t[0] += 0.25 * cnt * tr0;
+      t[1] += 0.25 * cnt * tr1;
+      t[2] += 0.25 * cnt * tr2;
+    }
+  }
+  for (int d = 0; d < 3; ++d) {
+    fixed[3 * n + d] = fx[d];
+    uD[3 * n + d] = u[d];
+    f[3 * n + d] = t[d];
+  }
+}
+
+// neighbour m = n + (dx,dy,dz) is coupled to n when a solid voxel has both as corners
+__device__ __forceinline__ bool shares_solid(const uint8_t *mask, int nx, int ny, int nz, int i, int j, int k, int dx,
+                                             int dy, int dz) {
+  int x0 = max(i - 1, i + dx - 1), x1 = min(i, i + dx);
+  int y0 = max(j - 1, j + dy - 1), y1 = min(j, j + dy);
+  int z0 = max(k - 1, k + dz - 1), z1 = min(k, k + dz);
+  for (int vz = z0; vz <= z1; ++vz)
+    for (int vy = y0; vy <= y1; ++vy)
+      for (int vx = x0; vx <= x1; ++vx) {
+        if (vx < 0 || vy < 0 || vz < 0 || vx >= nx || vy >= ny || vz >= nz) continue;
+        if (mask[((long long)vz * ny + vy) * nx + vx]) return true;
+      }
+  return false;
+}
+
+__global__ void k_bsr_count(const int *node_ijk, int n_nodes, const int *g2n, const uint8_t *mask, int nx, int ny,
+                            int nz, int *cnt) {
+  int n = blockIdx.x * blockDim.x + threadIdx.x;
+  if (n >= n_nodes) return;
+  int i = node_ijk[3 * n], j = node_ijk[3 * n + 1], k = node_ijk[3 * n + 2];
+  int c = 0;
+  for (int dz = -1; dz <= 1; ++dz)
+    for (int dy = -1; dy <= 1; ++dy)
+      for (int dx = -1; dx <= 1; ++dx)
+        if (shares_solid(mask, nx, ny, nz, i, j, k, dx, dy, dz)) ++c;
+  cnt[n] = c;
+}
+
+__global__ void k_bsr_fill(const int *node_ijk, int n_nodes, const int *g2n, const uint8_t *mask, const float *E,
+                           int nx, int ny, int nz, const double *Kref, const int *row_ptr, const uint8_t *fixed,
+                           const double *uD, const double *f, int *col, double *val64, float *val32, double *b) {
+  int n = blockIdx.x * blockDim.x + threadIdx.x;
+  if (n >= n_nodes) return;
+  int i = node_ijk[3 * n], j = node_ijk[3 * n + 1], k = node_ijk[3 * n + 2];
+  long long NX = nx + 1, NY = ny + 1;
+  int pos = row_ptr[n];
+  double rhs[3] = {f[3 * n], f[3 * n + 1], f[3 * n + 2]};
+  bool fr[3] = {fixed[3 * n] != 0, fixed[3 * n + 1] != 0, fixed[3 * n + 2] != 0};
+  for (int dz = -1; dz <= 1; ++dz)
+    for (int dy = -1; dy <= 1; ++dy)
+      for (int dx = -1; dx <= 1; ++dx) {
+        if (!shares_solid(mask, nx, ny, nz, i, j, k, dx, dy, dz)) continue;
+        int m = g2n[((long long)(k + dz) * NY + (j + dy)) * NX + (i + dx)];
+        double blk[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+        int x0 = max(i - 1, i + dx - 1), x1 = min(i, i + dx);
+        int y0 = max(j - 1, j + dy - 1), y1 = min(j, j + dy);
+        int z0 = max(k - 1, k + dz - 1), z1 = min(k, k + dz);
+        for (int vz = z0; vz <= z1; ++vz)
+          for (int vy = y0; vy <= y1; ++vy)
+            for (int vx = x0; vx <= x1; ++vx) {
+              if (vx < 0 || vy < 0 || vz < 0 || vx >= nx || vy >= ny || vz >= nz) continue;
+              long long v = ((long long)vz * ny + vy) * nx + vx;
+              if (!mask[v]) continue;
+              double e = E[v];
+              int a = corner_index(i - vx, j - vy, k - vz);
+              int bb = corner_index(i + dx - vx, j + dy - vy, k + dz - vz);
+              for (int d = 0; d < 3; ++d)
+                for (int d2 = 0; d2 < 3; ++d2) blk[3 * d + d2] += e * Kref[(3 * a + d) * 24 + 3 * bb + d2];
+            }
+        bool fc[3] = {fixed[3 * m] != 0, fixed[3 * m + 1] != 0, fixed[3 * m + 2] != 0};
+        for (int d = 0; d < 3; ++d)
+          for (int d2 = 0; d2 < 3; ++d2)
+            if (!fr[d] && fc[d2]) rhs[d] -= blk[3 * d + d2] * uD[3 * m + d2];
+        for (int d = 0; d < 3; ++d)
+          for (int d2 = 0; d2 < 3; ++d2)
+            if (fr[d] || fc[d2]) blk[3 * d + d2] = 0.0;
+        col[pos] = m;
+        for (int q = 0; q < 9; ++q) {
+          val64[(long long)pos * 9 + q] = blk[q];
+          val32[(long long)pos * 9 + q] = (float)blk[q];
+        }
+        ++pos;
+      }
+  for (int d = 0; d < 3; ++d) b[3 * n + d] = fr[d] ? 0.0 : rhs[d];
+}
+
+__global__ void k_not_fixed(const uint8_t *fixed, int *flag, long long n) {
+  long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (s < n) flag[s] = fixed[s] ? 0 : 1;
+}
+
+__global__ void k_free_finalize(const uint8_t *fixed, int *free_index, int *dof_slot, long long n) {
+  long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= n) return;
+  if (fixed[s]) {
+    free_index[s] = -1;
+  } else {
+    dof_slot[free_index[s]] = (int)s;
+  }
+}
+
+__global__ void k_gather_free(const int *dof_slot, const double *pad, double *dof, long long n_dof) {
+  long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n_dof) dof[i] = pad[dof_slot[i]];
+}
+
+__global__ void k_scatter_free(const int *dof_slot, const double *dof, double *pad, long long n_dof) {
+  long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n_dof) pad[dof_slot[i]] = dof[i];
+}
+
+// y = A x (or y = sub - A x when sub != nullptr); one thread per node row, 3x3 blocks
+template <typename T>
+__global__ void k_spmv(const int *row_ptr, const int *col, const T *val, const double *x, double *y,
+                       const double *sub, int n_nodes) {
+  int n = blockIdx.x * blockDim.x + threadIdx.x;
+  if (n >= n_nodes) return;
+  using A = typename std::conditional<std::is_same<T, double>::value, double, float>::type;
+  A s0 = 0, s1 = 0, s2 = 0;
+  int e = row_ptr[n + 1];
+  for (int p = row_ptr[n]; p < e; ++p) {
+    int m = col[p];
+    const T *v = val + (long long)p * 9;
+    A x0 = (A)x[3 * m], x1 = (A)x[3 * m + 1], x2 = (A)x[3 * m + 2];
+    s0 += (A)v[0] * x0 + (A)v[1] * x1 + (A)v[2] * x2;
+    s1 += (A)v[3] * x0 + (A)v[4] * x1 + (A)v[5] * x2;
+    s2 += (A)v[6] * x0 + (A)v[7] * x1 + (A)v[8] * x2;
+  }
+  if (sub) {
+    y[3 * n] = sub[3 * n] - (double)s0;
+    y[3 * n + 1] = sub[3 * n + 1] - (double)s1;
+    y[3 * n + 2] = sub[3 * n + 2] - (double)s2;
+  } else {
+    y[3 * n] = (double)s0;
+    y[3 * n + 1] = (double)s1;
+    y[3 * n + 2] = (double)s2;
+  }
+}
+
+}  // namespace
+
+void assemble(hplmm_ctx *c, const uint8_t *mask, int nx, int ny, int nz, const float *E, double E0, double nu,
+              const hplmm_bcs *bcs, double *b_out) {
+  HP_REQUIRE(mask != nullptr && bcs != nullptr, HPLMM_ERR_INVALID, "assemble: mask and bcs are required");
+  HP_REQUIRE(nx > 0 && ny > 0 && nz > 0, HPLMM_ERR_INVALID, "assemble: image dimensions must be positive");
+  HP_REQUIRE(nu > -1.0 && nu < 0.5, HPLMM_ERR_INVALID, "assemble: Poisson ratio must lie in (-1, 0.5)");
+  HP_REQUIRE((long long)(nx + 1) * (ny + 1) * (nz + 1) < (1LL << 31), HPLMM_ERR_INVALID,
+             "assemble: image too large for 32-bit node indices");
+  cudaStream_t s = c->stream;
+  c->assembled = false;
+  c->setup_done = false;
+  c->nx = nx;
+  c->ny = ny;
+  c->nz = nz;
+  c->nu = nu;
+  c->E0 = E0;
+  long long nvox = (long long)nx * ny * nz;
+  c->mask.alloc(nvox);
+  HP_CUDA(cudaMemcpyAsync(c->mask.p, mask, nvox, cudaMemcpyDeviceToDevice, s));
+  c->E.alloc(nvox);
+  if (E) {
+    HP_CUDA(cudaMemcpyAsync(c->E.p, E, nvox * sizeof(float), cudaMemcpyDeviceToDevice, s));
+  } else {
+    std::vector<float> h(nvox, (float)E0);
+    HP_CUDA(cudaMemcpyAsync(c->E.p, h.data(), nvox * sizeof(float), cudaMemcpyHostToDevice, s));
+    HP_CUDA(cudaStreamSynchronize(s));
+  }
+  c->n_grid = (long long)(nx + 1) * (ny + 1) * (nz + 1);
+  Buf<int> flag;
+  flag.alloc(c->n_grid);
+  c->grid_to_node.alloc(c->n_grid);
+  k_node_exists<<<grid_for(c->n_grid, 256), 256, 0, s>>>(c->mask.p, nx, ny, nz, flag.p);
+  HP_CHECK_LAUNCH();
+  long long nn = exclusive_scan_i32(flag.p, c->grid_to_node.p, c->n_grid, s);
+  HP_REQUIRE(nn > 0, HPLMM_ERR_INVALID, "assemble: the image has no solid voxel");
+  c->n_nodes = (int)nn;
+  c->node_ijk.alloc(3 * nn);
+  k_node_finalize<<<grid_for(c->n_grid, 256), 256, 0, s>>>(flag.p, c->grid_to_node.p, c->node_ijk.p, nx, ny,
+                                                           c->n_grid);
+  HP_CHECK_LAUNCH();
+  c->Kref.alloc(576);
+  k_kref<<<1, 576, 0, s>>>(nu, c->Kref.p);
+  HP_CHECK_LAUNCH();
+
+  BCDev bc;
+  for (int f = 0; f < 6; ++f)
+    for (int d = 0; d < 3; ++d) {
+      bc.fix[f][d] = bcs->fix[f][d] ? 1 : 0;
+      bc.value[f][d] = bcs->value[f][d];
+      bc.traction[f][d] = bcs->traction[f][d];
+    }
+  long long nslot = 3LL * nn;
+  c->fixed.alloc(nslot);
+  Buf<double> uD, f;
+  uD.alloc(nslot);
+  f.alloc(nslot);
+  k_bc<<<grid_for(nn, 256), 256, 0, s>>>(c->node_ijk.p, c->n_nodes, nx, ny, nz, c->mask.p, bc, c->fixed.p, uD.p,
+                                         f.p);
+  HP_CHECK_LAUNCH();
+
+  c->row_ptr.alloc(nn + 1);
+  Buf<int> cnt;
+  cnt.alloc(nn + 1);
+  k_bsr_count<<<grid_for(nn, 256), 256, 0, s>>>(c->node_ijk.p, c->n_nodes, c->grid_to_node.p, c->mask.p, nx, ny, nz,
+                                                 cnt.p);
+  HP_CHECK_LAUNCH();
+  HP_CUDA(cudaMemsetAsync(cnt.p + nn, 0, sizeof(int), s));
+  c->nnzb = exclusive_scan_i32(cnt.p, c->row_ptr.p, nn + 1, s);
+  c->col.alloc(c->nnzb);
+  c->val64.alloc(c->nnzb * 9);
+  c->val32.alloc(c->nnzb * 9);
+  c->b_pad.alloc(nslot);
+  k_bsr_fill<<<grid_for(nn, 128), 128, 0, s>>>(c->node_ijk.p, c->n_nodes, c->grid_to_node.p, c->mask.p, c->E.p, nx,
+                                               ny, nz, c->Kref.p, c->row_ptr.p, c->fixed.p, uD.p, f.p, c->col.p,
+                                               c->val64.p, c->val32.p, c->b_pad.p);
+  HP_CHECK_LAUNCH();
+
+  c->free_index.alloc(nslot);
+  k_not_fixed<<<grid_for(nslot, 256), 256, 0, s>>>(c->fixed.p, flag.p, nslot);
+  HP_CHECK_LAUNCH();
+  c->n_dof = exclusive_scan_i32(flag.p, c->free_index.p, nslot, s);
+  c->dof_slot.alloc(c->n_dof);
+  k_free_finalize<<<grid_for(nslot, 256), 256, 0, s>>>(c->fixed.p, c->free_index.p, c->dof_slot.p, nslot);
+  HP_CHECK_LAUNCH();
+  if (b_out) gather_free(c, c->b_pad.p, b_out);
+  HP_CUDA(cudaStreamSynchronize(s));
+  c->assembled = true;
+}
+
+void gather_free(hplmm_ctx *c, const double *pad, double *dof) {
+  k_gather_free<<<grid_for(c->n_dof, 256), 256, 0, c->stream>>>(c->dof_slot.p, pad, dof, c->n_dof);
+  HP_CHECK_LAUNCH();
+}
+
+void scatter_free(hplmm_ctx *c, const double *dof, double *pad) {
+  HP_CUDA(cudaMemsetAsync(pad, 0, sizeof(double) * 3 * (size_t)c->n_nodes, c->stream));
+  k_scatter_free<<<grid_for(c->n_dof, 256), 256, 0, c->stream>>>(c->dof_slot.p, dof, pad, c->n_dof);
+  HP_CHECK_LAUNCH();
+}
+
+void spmv(hplmm_ctx *c, const double *x_pad, double *y_pad, hplmm_prec prec, const double *sub) {
+  if (prec == HPLMM_FP64) {
+    k_spmv<double><<<grid_for(c->n_nodes, 128), 128, 0, c->stream>>>(c->row_ptr.p, c->col.p, c->val64.p, x_pad,
+                                                                      y_pad, sub, c->n_nodes);
+  } else {
+    k_spmv<float><<<grid_for(c->n_nodes, 128), 128, 0, c->stream>>>(c->row_ptr.p, c->col.p, c->val32.p, x_pad,
+                                                                     y_pad, sub, c->n_nodes);
+  }
+  HP_CHECK_LAUNCH();
+}
+
+}  // namespace hp

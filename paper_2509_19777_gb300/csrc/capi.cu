@@ -1,0 +1,310 @@
+// The library's C interface (include/hplmm.h): argument checks, phase
+// ordering, timing and the conversion between the public free-DOF vectors
+// and the padded [n_nodes][3] layout used internally.
+#include "common.cuh"
+
+#include <chrono>
+#include <cstring>
+
+using hp::Error;
+
+namespace {
+
+double now_s() {
+  return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();
+}
+
+template <typename F>
+hplmm_status guarded(hplmm_ctx *c, F &&f) {
+  if (!c) return HPLMM_ERR_INVALID;
+  try {
+    f();
+    return HPLMM_OK;
+  } catch (const Error &e) {
+    c->err = e.what();
+    return e.code;
+  } catch (const std::exception &e) {
+    c->err = e.what();
+    return HPLMM_ERR_CUDA;
+  }
+}
+
+void validate_options(const hplmm_options &o) {
+  HP_REQUIRE(o.n_mortar >= 1 && o.n_mortar <= 128, HPLMM_ERR_INVALID, "n_mortar must lie in [1, 128]");
+  HP_REQUIRE(o.beta > 0.0, HPLMM_ERR_INVALID, "beta must be positive");
+  HP_REQUIRE(o.contact_halfwidth >= 0 && o.contact_halfwidth <= 16, HPLMM_ERR_INVALID,
+             "contact_halfwidth must lie in [0, 16]");
+  HP_REQUIRE(o.n_st >= 1 && o.n_st <= 16, HPLMM_ERR_INVALID, "n_st must lie in [1, 16]");
+  HP_REQUIRE(o.local_prec == HPLMM_FP64 || o.local_prec == HPLMM_FP32, HPLMM_ERR_INVALID,
+             "local_prec must be FP64 or FP32");
+  HP_REQUIRE(o.apply_prec == HPLMM_FP64 || o.apply_prec == HPLMM_FP32, HPLMM_ERR_INVALID,
+             "apply_prec must be FP64 or FP32");
+  HP_REQUIRE(o.restart >= 1 && o.restart <= 60, HPLMM_ERR_INVALID, "restart must lie in [1, 60]");
+  HP_REQUIRE(o.max_iters >= 1, HPLMM_ERR_INVALID, "max_iters must be positive");
+}
+
+void require_setup(hplmm_ctx *c) {
+  HP_REQUIRE(c->assembled, HPLMM_ERR_STATE, "call hplmm_assemble first");
+  HP_REQUIRE(c->setup_done, HPLMM_ERR_STATE, "call hplmm_setup first");
+}
+
+void alloc_work(hplmm_ctx *c) {
+  long long L = 3LL * c->n_nodes;
+  for (auto *b : {&c->w_r1, &c->w_r2, &c->w_z1, &c->w_zz, &c->w_zg, &c->w_t, &c->w_w, &c->w_in, &c->w_out})
+    b->alloc(L);
+  long long No = std::max<long long>(c->n_coarse, 1);
+  c->w_coarse_t.alloc(No);
+  c->w_coarse_u.alloc(No);
+  int m = c->opt.restart;
+  c->V.alloc((size_t)(m + 1) * L);
+  c->Z.alloc((size_t)m * L);
+  c->w_h.alloc(2 * 64 + 8);
+  c->w_partial.alloc(304 * 64);
+}
+
+}  // namespace
+
+extern "C" {
+
+void hplmm_default_options(hplmm_options *o) {
+  if (!o) return;
+  std::memset(o, 0, sizeof(*o));
+  o->n_mortar = 4;
+  o->beta = 4.0;
+  o->contact_halfwidth = 2;
+  o->n_st = 1;
+  o->local_prec = HPLMM_FP64;
+  o->apply_prec = HPLMM_FP64;
+  o->restart = 30;
+  o->max_iters = 300;
+  o->strict_two_grain = 0;
+  o->use_graph = 0;
+  o->verbose = 0;
+}
+
+hplmm_status hplmm_create(hplmm_ctx **ctx, const hplmm_options *opt, void *cuda_stream) {
+  if (!ctx) return HPLMM_ERR_INVALID;
+  *ctx = nullptr;
+  hplmm_options o;
+  hplmm_default_options(&o);
+  if (opt) o = *opt;
+  try {
+    validate_options(o);
+  } catch (const Error &) {
+    return HPLMM_ERR_INVALID;
+  }
+  hplmm_ctx *c = new (std::nothrow) hplmm_ctx();
+  if (!c) return HPLMM_ERR_OOM;
+  c->opt = o;
+  c->stream = (cudaStream_t)cuda_stream;
+  if (cudaGetDevice(&c->device) != cudaSuccess) {
+    delete c;
+    return HPLMM_ERR_CUDA;
+  }
+  *ctx = c;
+  return HPLMM_OK;
+}
+
+hplmm_status hplmm_assemble(hplmm_ctx *c, const uint8_t *mask, int nx, int ny, int nz, const float *E, double E0,
+                            double nu, const hplmm_bcs *bcs, double *b_out, long long *n_dof_out) {
+  return guarded(c, [&] {
+    hp::assemble(c, mask, nx, ny, nz, E, E0, nu, bcs, b_out);
+    if (n_dof_out) *n_dof_out = c->n_dof;
+  });
+}
+
+hplmm_status hplmm_setup(hplmm_ctx *c, const int32_t *partition, int n_grains, int px, int py, int pz,
+                         const double *b) {
+  return guarded(c, [&] {
+    HP_REQUIRE(c->assembled, HPLMM_ERR_STATE, "call hplmm_assemble first");
+    if (partition) {
+      HP_REQUIRE(n_grains >= 1, HPLMM_ERR_INVALID, "n_grains must be positive with an explicit partition");
+      c->n_grains = n_grains;
+      c->px = c->py = c->pz = 0;
+    } else {
+      HP_REQUIRE(px >= 1 && py >= 1 && pz >= 1 && px <= c->nx && py <= c->ny && pz <= c->nz, HPLMM_ERR_INVALID,
+                 "Cartesian grain counts must lie in [1, image size] per axis");
+      c->px = px;
+      c->py = py;
+      c->pz = pz;
+      c->n_grains = px * py * pz;
+    }
+    c->setup_done = false;
+    cudaStream_t s = c->stream;
+    long long L = 3LL * c->n_nodes;
+    c->b_corr.alloc(L);
+    if (b)
+      hp::scatter_free(c, b, c->b_corr.p);
+    else
+      HP_CUDA(cudaMemcpyAsync(c->b_corr.p, c->b_pad.p, sizeof(double) * L, cudaMemcpyDeviceToDevice, s));
+    HP_CUDA(cudaStreamSynchronize(s));
+    double t0 = now_s();
+    hp::build_maps(c, partition);
+    hp::build_mortars(c);
+    hp::build_local_sets(c);
+    double t1 = now_s();
+    // smoother build (T_ML): exact local factorisations of grains and contact grids
+    hp::factor_local(c, c->grains, c->opt.local_prec);
+    hp::factor_local(c, c->contacts, c->opt.local_prec);
+    hp::check_status(c);
+    double t2 = now_s();
+    // coarse build (T_MG): basis solves, Galerkin product, coarse Cholesky
+    hp::build_coarse(c, c->b_corr.p);
+    alloc_work(c);
+    hp::check_status(c);
+    double t3 = now_s();
+    c->t_ml = t2 - t1;
+    c->t_mg = (t1 - t0) + (t3 - t2);
+    if (c->opt.verbose)
+      fprintf(stderr, "[hplmm] setup: maps %.3f ms, factor %.3f ms, coarse %.3f ms; N^o=%lld, ifaces=%d\n",
+              1e3 * (t1 - t0), 1e3 * (t2 - t1), 1e3 * (t3 - t2), c->n_coarse, c->n_ifaces);
+    c->setup_done = true;
+  });
+}
+
+hplmm_status hplmm_apply(hplmm_ctx *c, const double *r, double *z) {
+  return guarded(c, [&] {
+    require_setup(c);
+    HP_REQUIRE(r && z && r != z, HPLMM_ERR_INVALID, "apply: r and z must be distinct device vectors");
+    hp::scatter_free(c, r, c->w_in.p);
+    hp::precond_apply(c, c->w_in.p, c->w_out.p);
+    hp::gather_free(c, c->w_out.p, z);
+  });
+}
+
+hplmm_status hplmm_apply_coarse(hplmm_ctx *c, const double *r, double *z) {
+  return guarded(c, [&] {
+    require_setup(c);
+    HP_REQUIRE(r && z, HPLMM_ERR_INVALID, "apply_coarse: null vector");
+    hp::scatter_free(c, r, c->w_in.p);
+    hp::coarse_apply(c, c->w_in.p, c->w_out.p);
+    hp::gather_free(c, c->w_out.p, z);
+  });
+}
+
+hplmm_status hplmm_apply_smoother(hplmm_ctx *c, const double *r, double *z) {
+  return guarded(c, [&] {
+    require_setup(c);
+    HP_REQUIRE(r && z, HPLMM_ERR_INVALID, "apply_smoother: null vector");
+    hp::scatter_free(c, r, c->w_in.p);
+    hp::smoother_stage(c, c->w_in.p, c->w_out.p);
+    hp::gather_free(c, c->w_out.p, z);
+  });
+}
+
+hplmm_status hplmm_spmv(hplmm_ctx *c, const double *x, double *y) {
+  return guarded(c, [&] {
+    HP_REQUIRE(c->assembled, HPLMM_ERR_STATE, "call hplmm_assemble first");
+    HP_REQUIRE(x && y, HPLMM_ERR_INVALID, "spmv: null vector");
+    long long L = 3LL * c->n_nodes;
+    if (c->w_in.n < (size_t)L) c->w_in.alloc(L);
+    if (c->w_out.n < (size_t)L) c->w_out.alloc(L);
+    hp::scatter_free(c, x, c->w_in.p);
+    hp::spmv(c, c->w_in.p, c->w_out.p, HPLMM_FP64);
+    hp::gather_free(c, c->w_out.p, y);
+  });
+}
+
+hplmm_status hplmm_solve(hplmm_ctx *c, const double *b, double *x, double tol, hplmm_stats *st) {
+  hplmm_status rc = HPLMM_OK;
+  hplmm_status g = guarded(c, [&] {
+    require_setup(c);
+    HP_REQUIRE(x, HPLMM_ERR_INVALID, "solve: x is required");
+    HP_REQUIRE(tol > 0.0, HPLMM_ERR_INVALID, "solve: tol must be positive");
+    const double *bp = c->b_pad.p;
+    if (b) {
+      hp::scatter_free(c, b, c->w_in.p);
+      bp = c->w_in.p;
+    }
+    double t0 = now_s();
+    rc = (hplmm_status)hp::fgmres(c, bp, c->w_out.p, tol, st);
+    hp::gather_free(c, c->w_out.p, x);
+    HP_CUDA(cudaStreamSynchronize(c->stream));
+    double t1 = now_s();
+    if (st) {
+      st->t_setup_ml = c->t_ml;
+      st->t_setup_mg = c->t_mg;
+      st->t_solve = t1 - t0;
+      st->n_dof = c->n_dof;
+      st->n_coarse = c->n_coarse;
+      st->n_interfaces = c->n_ifaces;
+      st->n_grains = c->n_grains;
+    }
+  });
+  return g != HPLMM_OK ? g : rc;
+}
+
+hplmm_status hplmm_get_sizes(hplmm_ctx *c, hplmm_sizes *out) {
+  return guarded(c, [&] {
+    HP_REQUIRE(out, HPLMM_ERR_INVALID, "get_sizes: null output");
+    std::memset(out, 0, sizeof(*out));
+    out->n_nodes = c->n_nodes;
+    out->n_dof = c->n_dof;
+    if (c->setup_done) {
+      out->n_grains = c->n_grains;
+      out->n_interfaces = c->n_ifaces;
+      out->n_iface_nodes = c->n_iface_nodes;
+      out->n_mortars = c->n_mortars;
+      out->n_mortar_cols = c->n_mortar_cols;
+      out->n_coarse = c->n_coarse;
+    }
+  });
+}
+
+hplmm_status hplmm_get_maps(hplmm_ctx *c, int32_t *node_ijk, int64_t *W, int32_t *iface_pair, int32_t *iface_nodes,
+                            int32_t *iface_offsets, int32_t *mortar_nodes, int32_t *mortar_offsets, double *eta) {
+  return guarded(c, [&] {
+    require_setup(c);
+    cudaStream_t s = c->stream;
+    auto cp = [&](void *dst, const void *src, size_t bytes) {
+      if (dst && bytes) HP_CUDA(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToDevice, s));
+    };
+    cp(node_ijk, c->node_ijk.p, sizeof(int) * 3 * (size_t)c->n_nodes);
+    if (W) hp::compute_W(c, W);
+    cp(iface_pair, c->iface_pair.p, sizeof(int) * 2 * (size_t)c->n_ifaces);
+    cp(iface_nodes, c->iface_nodes.p, sizeof(int) * (size_t)c->n_iface_nodes);
+    cp(iface_offsets, c->iface_off.p, sizeof(int) * (size_t)(c->n_ifaces + 1));
+    cp(mortar_nodes, c->mortar_nodes.p, sizeof(int) * (size_t)c->n_mortars);
+    cp(mortar_offsets, c->mortar_off.p, sizeof(int) * (size_t)(c->n_ifaces + 1));
+    if (eta && c->n_ifaces) {
+      long long last = 0;
+      HP_CUDA(cudaMemcpyAsync(&last, c->eta_off.p + c->n_ifaces, sizeof(long long), cudaMemcpyDeviceToHost, s));
+      HP_CUDA(cudaStreamSynchronize(s));
+      cp(eta, c->eta.p, sizeof(double) * (size_t)last);
+    }
+    HP_CUDA(cudaStreamSynchronize(s));
+  });
+}
+
+hplmm_status hplmm_get_coarse_matrix(hplmm_ctx *c, double *A_o) {
+  return guarded(c, [&] {
+    require_setup(c);
+    HP_REQUIRE(A_o, HPLMM_ERR_INVALID, "get_coarse_matrix: null output");
+    size_t bytes = sizeof(double) * (size_t)c->n_coarse * (size_t)c->n_coarse;
+    if (bytes) HP_CUDA(cudaMemcpyAsync(A_o, c->Ao.p, bytes, cudaMemcpyDeviceToDevice, c->stream));
+    HP_CUDA(cudaStreamSynchronize(c->stream));
+  });
+}
+
+hplmm_status hplmm_get_prolongation_column(hplmm_ctx *c, long long col, double *out) {
+  return guarded(c, [&] {
+    require_setup(c);
+    HP_REQUIRE(out && col >= 0 && col < c->n_coarse, HPLMM_ERR_INVALID, "get_prolongation_column: bad column");
+    hp::prolong_column(c, col, c->w_out.p);
+    hp::gather_free(c, c->w_out.p, out);
+    HP_CUDA(cudaStreamSynchronize(c->stream));
+  });
+}
+
+const char *hplmm_last_error(const hplmm_ctx *c) {
+  if (!c) return "null context";
+  return c->err.c_str();
+}
+
+void hplmm_destroy(hplmm_ctx *c) {
+  if (!c) return;
+  if (c->apply_graph) cudaGraphExecDestroy(c->apply_graph);
+  delete c;
+}
+
+}  // extern "C"

@@ -1,0 +1,756 @@
+// Coarse space of the preconditioner (paper Section 4.2, Eqs. mg_struct, WQP,
+// reduced_defs, bc_matrix, col_cg, col_pk): shape and correction vectors from
+// batched local solves, the Galerkin coarse matrix A^o = P_hat^T A_hat P_hat,
+// its FP64 Cholesky factor, and the restriction / prolongation of the apply.
+//
+// Storage.  For grain g the panel X_g holds, row-major with leading dimension
+// k_g, the local DOFs of g (its interior nodes in the grain problem's order,
+// three components each) against the k_g coarse columns coupled to g: the
+// mortar columns of every coupled interface (interfaces in ascending order,
+// inside one interface (mortar i, kept component gamma)), then the grain's
+// correction column when it is kept.  The interface rows of P_hat are the
+// Gaussian weights eta_i(y) (Q^o, Eq. reduced_defs) and are never stored.
+#include "common.cuh"
+
+#include <algorithm>
+
+namespace hp {
+namespace {
+
+// local column of interface c inside grain g's panel, or -1 if not coupled
+__device__ __forceinline__ int colbase_of(const int *gi_off, const int *gi_iface, const int *gi_colbase, int g, int c) {
+  int a = gi_off[g], b = gi_off[g + 1];
+  while (a < b) {  // ascending interface ids
+    int m = (a + b) >> 1;
+    int v = gi_iface[m];
+    if (v == c) return gi_colbase[m];
+    if (v < c) a = m + 1;
+    else b = m;
+  }
+  return -1;
+}
+
+__device__ __forceinline__ int comp_rank(int mask, int gamma) { return __popc(mask & ((1 << gamma) - 1)); }
+
+// right-hand sides of Eq. col_pk (-A^g_c Q^o e_k) and Eq. col_cg (b^g), one thread per local node
+template <typename T>
+__global__ void k_basis_rhs(int G, const long long *node_off, const int *nloc, const int *lnodes, const int *row_ptr,
+                            const int *col, const double *val, const int *iface_of_node, const int *iface_slot,
+                            const int *iface_pair, const int *mortar_off, const long long *eta_off, const double *eta,
+                            const int *comp_mask, const int *gi_off, const int *gi_iface, const int *gi_colbase,
+                            const int *kg, const int *corr_col, const long long *panel_off, const double *b,
+                            int strict, T *X) {
+  int g = blockIdx.y;
+  int cnt = nloc[g] / 3;
+  int o = blockIdx.x * blockDim.x + threadIdx.x;
+  if (o >= cnt) return;
+  int ld = kg[g];
+  T *Xg = X + panel_off[g];
+  int n = lnodes[node_off[g] + o];
+  for (int p = row_ptr[n]; p < row_ptr[n + 1]; ++p) {
+    int m = col[p];
+    int c = iface_of_node[m];
+    if (c < 0) continue;
+    if (strict && iface_pair[2 * c] != g && iface_pair[2 * c + 1] != g) continue;
+    int base = colbase_of(gi_off, gi_iface, gi_colbase, g, c);
+    if (base < 0) continue;
+    int nc = mortar_off[c + 1] - mortar_off[c];
+    int cm = comp_mask[c];
+    int ncomp = __popc(cm);
+    int slot = iface_slot[m];
+    const double *et = eta + eta_off[c] + (long long)slot * nc;
+    const double *v = val + (long long)p * 9;
+    for (int i = 0; i < nc; ++i) {
+      double w = et[i];
+      for (int gam = 0; gam < 3; ++gam) {
+        if (!((cm >> gam) & 1)) continue;
+        int lc = base + i * ncomp + comp_rank(cm, gam);
+        for (int d = 0; d < 3; ++d) {
+          double a = v[3 * d + gam];
+          if (a != 0.0) Xg[(long long)(3 * o + d) * ld + lc] -= (T)(a * w);
+        }
+      }
+    }
+  }
+  if (corr_col[g] >= 0)
+    for (int d = 0; d < 3; ++d) Xg[(long long)(3 * o + d) * ld + (ld - 1)] = (T)b[3LL * n + d];
+}
+
+// voxel bounding box of every grain (for the Galerkin sub-assembly)
+__global__ void k_grain_vbox(const int *vg, int nx, int ny, int nz, int *vmin, int *vmax) {
+  long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (v >= (long long)nx * ny * nz) return;
+  int g = vg[v];
+  if (g < 0) return;
+  int p[3] = {(int)(v % nx), (int)((v / nx) % ny), (int)(v / ((long long)nx * ny))};
+  for (int a = 0; a < 3; ++a) {
+    atomicMin(&vmin[3 * g + a], p[a]);
+    atomicMax(&vmax[3 * g + a], p[a]);
+  }
+}
+
+struct GalBox {
+  int lo[3], ext[3];  // node box: lo .. lo+ext-1
+};
+
+// P_hat restricted to the corners of grain g's voxels: interior rows from X_g, interface rows eta
+template <typename T>
+__global__ void k_gal_fill(const int *gbox, const long long *gal_off, const int *kg, const int *grid_to_node, int nx,
+                           int ny, const int *node_cls, const int *iface_of_node, const int *iface_slot,
+                           const uint8_t *fixed, const int *gbox_grain, const long long *node_off_g,
+                           const int *lmap_g, const long long *panel_off, const T *X, const int *mortar_off,
+                           const long long *eta_off, const double *eta, const int *comp_mask, const int *gi_off,
+                           const int *gi_iface, const int *gi_colbase, T *P) {
+  int g = blockIdx.y;
+  const int *bx = gbox + 6 * g;
+  int ex = bx[3], ey = bx[4], ez = bx[5];
+  int vol = ex * ey * ez;
+  int cell = blockIdx.x * blockDim.x + threadIdx.x;
+  if (cell >= vol) return;
+  int k = kg[g];
+  int x = bx[0] + cell % ex, y = bx[1] + (cell / ex) % ey, z = bx[2] + cell / (ex * ey);
+  long long NX = nx + 1, NY = ny + 1;
+  int n = grid_to_node[((long long)z * NY + y) * NX + x];
+  if (n < 0) return;
+  T *Pr = P + gal_off[g] + (long long)3 * cell * k;
+  if (node_cls[n] == g) {
+    // ordinal of n in the grain problem: box of the grain set (lo, ext, perm)
+    const int *b = gbox_grain + 9 * g;
+    int pp[3] = {x - b[0], y - b[1], z - b[2]};
+    int f = b[6], m = b[7], s = b[8];
+    int gc = (pp[s] * b[3 + m] + pp[m]) * b[3 + f] + pp[f];
+    int o = lmap_g[node_off_g[g] + gc];
+    const T *Xr = X + panel_off[g] + (long long)3 * o * k;
+    for (int e = 0; e < 3 * k; ++e) Pr[e] = Xr[e];
+    return;
+  }
+  int c = iface_of_node[n];
+  if (c < 0) return;
+  int base = colbase_of(gi_off, gi_iface, gi_colbase, g, c);
+  if (base < 0) return;
+  int nc = mortar_off[c + 1] - mortar_off[c];
+  int cm = comp_mask[c];
+  int ncomp = __popc(cm);
+  const double *et = eta + eta_off[c] + (long long)iface_slot[n] * nc;
+  for (int d = 0; d < 3; ++d) {
+    if (fixed[3 * n + d] || !((cm >> d) & 1)) continue;
+    for (int i = 0; i < nc; ++i) Pr[(long long)d * k + base + i * ncomp + comp_rank(cm, d)] = (T)et[i];
+  }
+}
+
+// Y = A^(g) P on the grain's node box, A^(g) = sum over the grain's solid voxels of E_v K_ref
+template <typename T>
+__global__ void k_gal_Y(const int *gbox, const long long *gal_off, const int *kg, const int *vg, const uint8_t *mask,
+                        const float *E, int nx, int ny, int nz, const double *Kref, const uint8_t *fixed,
+                        const int *grid_to_node, const T *P, T *Y) {
+  __shared__ T K[576];
+  int g = blockIdx.y;
+  for (int e = threadIdx.x; e < 576; e += blockDim.x) K[e] = (T)Kref[e];
+  __syncthreads();
+  const int *bx = gbox + 6 * g;
+  int ex = bx[3], ey = bx[4], ez = bx[5];
+  int vol = ex * ey * ez;
+  int cell = blockIdx.x;
+  if (cell >= vol) return;
+  int k = kg[g];
+  int x = bx[0] + cell % ex, y = bx[1] + (cell / ex) % ey, z = bx[2] + cell / (ex * ey);
+  const T *Pg = P + gal_off[g];
+  T *Yr = Y + gal_off[g] + (long long)3 * cell * k;
+  for (int a = threadIdx.x; a < k; a += blockDim.x) {
+    T acc[3] = {0, 0, 0};
+    for (int dz = -1; dz <= 0; ++dz)
+      for (int dy = -1; dy <= 0; ++dy)
+        for (int dx = -1; dx <= 0; ++dx) {
+          int vx = x + dx, vy = y + dy, vz = z + dz;
+          if (vx < 0 || vy < 0 || vz < 0 || vx >= nx || vy >= ny || vz >= nz) continue;
+          long long v = ((long long)vz * ny + vy) * nx + vx;
+          if (vg[v] != g) continue;
+          T Ev = (T)E[v];
+          int ca = (x - vx) + 2 * (y - vy) + 4 * (z - vz);
+          for (int cb = 0; cb < 8; ++cb) {
+            int nx_ = vx + (cb & 1), ny_ = vy + ((cb >> 1) & 1), nz_ = vz + ((cb >> 2) & 1);
+            int bc = ((nz_ - bx[2]) * ey + (ny_ - bx[1])) * ex + (nx_ - bx[0]);
+            const T *pr = Pg + (long long)3 * bc * k + a;
+            T p0 = pr[0], p1 = pr[k], p2 = pr[2 * k];
+            for (int d = 0; d < 3; ++d) {
+              const T *kr = K + (3 * ca + d) * 24 + 3 * cb;
+              acc[d] += Ev * (kr[0] * p0 + kr[1] * p1 + kr[2] * p2);
+            }
+          }
+        }
+    Yr[a] = acc[0];
+    Yr[k + a] = acc[1];
+    Yr[2 * k + a] = acc[2];
+  }
+}
+
+// A^o[gcol(a)][gcol(b)] += sum_r P[r][a] Y[r][b] over the grain's box rows; 32x32 output tiles
+template <typename T>
+__global__ void __launch_bounds__(256) k_gal_gemm(const int *tiles, const int *gbox, const long long *gal_off,
+                                                  const int *kg, const int *gcol_off, const int *gcol, const T *P,
+                                                  const T *Y, double *Ao, long long No) {
+  __shared__ T Ps[32][33];
+  __shared__ T Ys[32][33];
+  int g = tiles[3 * blockIdx.x], a0 = tiles[3 * blockIdx.x + 1], b0 = tiles[3 * blockIdx.x + 2];
+  const int *bx = gbox + 6 * g;
+  long long M = 3LL * bx[3] * bx[4] * bx[5];
+  int k = kg[g];
+  const T *Pg = P + gal_off[g];
+  const T *Yg = Y + gal_off[g];
+  int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;  // 16 x 16 threads, 2x2 outputs each
+  T acc[2][2] = {{0, 0}, {0, 0}};
+  for (long long r0 = 0; r0 < M; r0 += 32) {
+    for (int e = threadIdx.x; e < 1024; e += 256) {
+      int rr = e >> 5, cc = e & 31;
+      long long r = r0 + rr;
+      Ps[rr][cc] = (r < M && a0 + cc < k) ? Pg[r * k + a0 + cc] : (T)0;
+      Ys[rr][cc] = (r < M && b0 + cc < k) ? Yg[r * k + b0 + cc] : (T)0;
+    }
+    __syncthreads();
+#pragma unroll 8
+    for (int rr = 0; rr < 32; ++rr) {
+      T p0 = Ps[rr][ty], p1 = Ps[rr][ty + 16];
+      T y0 = Ys[rr][tx], y1 = Ys[rr][tx + 16];
+      acc[0][0] += p0 * y0;
+      acc[0][1] += p0 * y1;
+      acc[1][0] += p1 * y0;
+      acc[1][1] += p1 * y1;
+    }
+    __syncthreads();
+  }
+  const int *gc = gcol + gcol_off[g];
+  for (int i = 0; i < 2; ++i)
+    for (int j = 0; j < 2; ++j) {
+      int a = a0 + ty + 16 * i, bb = b0 + tx + 16 * j;
+      if (a < k && bb < k) atomicAdd(&Ao[(long long)gc[a] * No + gc[bb]], (double)acc[i][j]);
+    }
+}
+
+__global__ void k_symmetrize(double *A, long long N, double *asym) {
+  long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= N * N) return;
+  long long i = e / N, j = e % N;
+  if (j >= i) return;
+  double a = A[i * N + j], b = A[j * N + i];
+  double m = 0.5 * (a + b);
+  A[i * N + j] = m;
+  A[j * N + i] = m;
+}
+
+// ---------------------------------------------------------------- dense FP64 Cholesky (64x64 tiles)
+constexpr int TB = 64;
+
+__global__ void k_potrf_tile(double *A, long long N, int kt, double *Dinv, int *status) {
+  __shared__ double L[TB][TB + 1];
+  __shared__ double W[TB][TB + 1];
+  int k0 = kt * TB;
+  int nb = (int)min((long long)TB, N - k0);
+  for (int e = threadIdx.x; e < TB * TB; e += blockDim.x) {
+    int r = e / TB, c = e % TB;
+    L[r][c] = (r < nb && c < nb && c <= r) ? A[(long long)(k0 + r) * N + k0 + c] : (r == c ? 1.0 : 0.0);
+  }
+  __syncthreads();
+  for (int c = 0; c < nb; ++c) {
+    if (threadIdx.x == 0) {
+      double d = L[c][c];
+      if (!(d > 0.0)) {
+        atomicExch(status, (int)HPLMM_ERR_SINGULAR);
+        d = 1.0;
+      }
+      L[c][c] = sqrt(d);
+    }
+    __syncthreads();
+    for (int r = c + 1 + threadIdx.x; r < nb; r += blockDim.x) L[r][c] /= L[c][c];
+    __syncthreads();
+    for (int e = threadIdx.x; e < TB * TB; e += blockDim.x) {
+      int r = e / TB, c2 = e % TB;
+      if (r > c && c2 > c && c2 <= r && r < nb) L[r][c2] -= L[r][c] * L[c2][c];
+    }
+    __syncthreads();
+  }
+  // inverse of the lower factor block, column j by thread j
+  if (threadIdx.x < TB) {
+    int j = threadIdx.x;
+    for (int i = 0; i < TB; ++i) {
+      double v;
+      if (i < j) {
+        v = 0.0;
+      } else {
+        double s = (i == j) ? 1.0 : 0.0;
+        for (int q = j; q < i; ++q) s -= L[i][q] * W[q][j];
+        v = s / L[i][i];
+      }
+      W[i][j] = v;
+    }
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < TB * TB; e += blockDim.x) {
+    int r = e / TB, c = e % TB;
+    if (r < nb && c < nb) A[(long long)(k0 + r) * N + k0 + c] = (c <= r) ? L[r][c] : 0.0;
+    Dinv[(long long)kt * TB * TB + e] = (r < nb && c < nb) ? W[r][c] : 0.0;
+  }
+}
+
+// A[it][kt] <- A[it][kt] * inv(L_kk)^T for it > kt
+__global__ void k_trsm_tiles(double *A, long long N, int kt, const double *Dinv) {
+  __shared__ double Di[TB][TB + 1];
+  __shared__ double Bt[TB][TB + 1];
+  int it = kt + 1 + blockIdx.x;
+  int k0 = kt * TB, i0 = it * TB;
+  int nbk = (int)min((long long)TB, N - k0), nbi = (int)min((long long)TB, N - i0);
+  for (int e = threadIdx.x; e < TB * TB; e += blockDim.x) {
+    int r = e / TB, c = e % TB;
+    Di[r][c] = Dinv[(long long)kt * TB * TB + e];
+    Bt[r][c] = (r < nbi && c < nbk) ? A[(long long)(i0 + r) * N + k0 + c] : 0.0;
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < TB * TB; e += blockDim.x) {
+    int r = e / TB, c = e % TB;
+    double s = 0.0;
+    for (int q = 0; q <= c; ++q) s += Bt[r][q] * Di[c][q];
+    if (r < nbi && c < nbk) A[(long long)(i0 + r) * N + k0 + c] = s;
+  }
+}
+
+// A[it][jt] -= A[it][kt] A[jt][kt]^T for it >= jt > kt (lower tiles only)
+__global__ void k_syrk_tiles(double *A, long long N, int kt, int T) {
+  __shared__ double Ai[TB][TB + 1];
+  __shared__ double Aj[TB][TB + 1];
+  int m = T - kt - 1;
+  int t = blockIdx.x;
+  int ti = (int)((sqrt(8.0 * t + 1.0) - 1.0) * 0.5);
+  while ((ti + 1) * (ti + 2) / 2 <= t) ++ti;
+  while (ti * (ti + 1) / 2 > t) --ti;
+  int tj = t - ti * (ti + 1) / 2;
+  if (ti >= m) return;
+  int it = kt + 1 + ti, jt = kt + 1 + tj;
+  int k0 = kt * TB, i0 = it * TB, j0 = jt * TB;
+  int nbk = (int)min((long long)TB, N - k0);
+  int nbi = (int)min((long long)TB, N - i0), nbj = (int)min((long long)TB, N - j0);
+  for (int e = threadIdx.x; e < TB * TB; e += blockDim.x) {
+    int r = e / TB, c = e % TB;
+    Ai[r][c] = (r < nbi && c < nbk) ? A[(long long)(i0 + r) * N + k0 + c] : 0.0;
+    Aj[r][c] = (r < nbj && c < nbk) ? A[(long long)(j0 + r) * N + k0 + c] : 0.0;
+  }
+  __syncthreads();
+  // 256 threads, 4x4 outputs each
+  int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  double acc[4][4] = {};
+  for (int q = 0; q < TB; ++q) {
+    double a[4], b[4];
+    for (int u = 0; u < 4; ++u) {
+      a[u] = Ai[ty + 16 * u][q];
+      b[u] = Aj[tx + 16 * u][q];
+    }
+    for (int u = 0; u < 4; ++u)
+      for (int v = 0; v < 4; ++v) acc[u][v] += a[u] * b[v];
+  }
+  for (int u = 0; u < 4; ++u)
+    for (int v = 0; v < 4; ++v) {
+      int r = ty + 16 * u, c = tx + 16 * v;
+      if (r < nbi && c < nbj && (it != jt || c <= r)) A[(long long)(i0 + r) * N + j0 + c] -= acc[u][v];
+    }
+}
+
+// ---------------------------------------------------------------- coarse solve (one CTA)
+// forward L y = t then backward L^T u = y with the blocked factor and inverse diagonal tiles
+__global__ void __launch_bounds__(1024) k_coarse_solve(const double *L, long long N, const double *Dinv, double *x) {
+  __shared__ double blk[TB];
+  __shared__ double part[32][TB + 1];
+  int T = (int)((N + TB - 1) / TB);
+  int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  // forward
+  for (int kt = 0; kt < T; ++kt) {
+    int k0 = kt * TB, nb = (int)min((long long)TB, N - k0);
+    // partial sums of L[k0+r][0:k0] x[0:k0]: warp w handles rows r = w, w+32 (2 rows per warp)
+    for (int r = wid; r < TB; r += 32) {
+      double s = 0.0;
+      if (r < nb)
+        for (long long j = lane; j < k0; j += 32) s += L[(long long)(k0 + r) * N + j] * x[j];
+      for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+      if (lane == 0) blk[r] = (r < nb) ? x[k0 + r] - s : 0.0;
+    }
+    __syncthreads();
+    if (threadIdx.x < nb) {
+      int r = threadIdx.x;
+      double s = 0.0;
+      for (int q = 0; q <= r; ++q) s += Dinv[(long long)kt * TB * TB + r * TB + q] * blk[q];
+      x[k0 + r] = s;
+    }
+    __syncthreads();
+  }
+  // backward: u_k = inv(L_kk)^T (y_k - sum_{i>k} L_ik^T u_i)
+  for (int kt = T - 1; kt >= 0; --kt) {
+    int k0 = kt * TB, nb = (int)min((long long)TB, N - k0);
+    // column sums: thread (wid, lane) over rows i >= k0+nb (stride 32 by warp), columns c = lane, lane+32
+    double s0 = 0.0, s1 = 0.0;
+    for (long long i = k0 + nb + wid; i < N; i += 32) {
+      double xi = x[i];
+      const double *row = L + i * N + k0;
+      if (lane < nb) s0 += row[lane] * xi;
+      if (lane + 32 < nb) s1 += row[lane + 32] * xi;
+    }
+    part[wid][lane] = s0;
+    part[wid][lane + 32] = s1;
+    __syncthreads();
+    if (threadIdx.x < TB) {
+      int c = threadIdx.x;
+      double s = 0.0;
+      for (int w = 0; w < 32; ++w) s += part[w][c];
+      blk[c] = (c < nb) ? x[k0 + c] - s : 0.0;
+    }
+    __syncthreads();
+    if (threadIdx.x < nb) {
+      int r = threadIdx.x;
+      double s = 0.0;
+      for (int q = r; q < nb; ++q) s += Dinv[(long long)kt * TB * TB + q * TB + r] * blk[q];
+      x[k0 + r] = s;
+    }
+    __syncthreads();
+  }
+}
+
+// ---------------------------------------------------------------- restriction / prolongation
+// t[gcol] += sum over grain rows of X_g[row][a] r_loc[row]; CTA = (grain, 32-column chunk)
+template <typename T, typename A>
+__global__ void k_restrict_grain(const long long *node_off, const int *nloc, const int *lnodes, const int *kg,
+                                 const long long *panel_off, const T *X, const int *gcol_off, const int *gcol,
+                                 const double *r, double *t) {
+  __shared__ A part[8][32];
+  int g = blockIdx.y, a0 = blockIdx.x * 32;
+  int k = kg[g];
+  if (a0 >= k) return;
+  int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  int N = nloc[g];
+  const T *Xg = X + panel_off[g];
+  const int *ln = lnodes + node_off[g];
+  A s = 0;
+  int a = a0 + lane;
+  for (int row = wid; row < N; row += 8) {
+    int o = row / 3, d = row - 3 * o;
+    A rv = (A)r[3LL * ln[o] + d];
+    if (a < k) s += (A)Xg[(long long)row * k + a] * rv;
+  }
+  part[wid][lane] = s;
+  __syncthreads();
+  if (wid == 0) {
+    A tot = 0;
+    for (int w = 0; w < 8; ++w) tot += part[w][lane];
+    if (a < k) atomicAdd(&t[gcol[gcol_off[g] + a]], (double)tot);
+  }
+}
+
+// interface part of the restriction: t[(c,i,gamma)] += sum_y eta_i(y) r(y,gamma); thread per interface node
+__global__ void k_restrict_iface(const int *iface_nodes, const int *iface_of_node, long long count,
+                                 const int *iface_slot, const int *mortar_off, const long long *eta_off,
+                                 const double *eta, const int *comp_mask, const int *col_off, const uint8_t *fixed,
+                                 const double *r, double *t) {
+  long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= count) return;
+  int n = iface_nodes[p];
+  int c = iface_of_node[n];
+  int nc = mortar_off[c + 1] - mortar_off[c];
+  int cm = comp_mask[c], ncomp = __popc(cm);
+  const double *et = eta + eta_off[c] + (long long)iface_slot[n] * nc;
+  for (int gam = 0; gam < 3; ++gam) {
+    if (!((cm >> gam) & 1) || fixed[3 * n + gam]) continue;
+    double rv = r[3LL * n + gam];
+    if (rv == 0.0) continue;
+    for (int i = 0; i < nc; ++i) atomicAdd(&t[col_off[c] + i * ncomp + comp_rank(cm, gam)], et[i] * rv);
+  }
+}
+
+// z on grain rows = X_g u[K_g]; warp per row
+template <typename T, typename A>
+__global__ void k_prolong_grain(const long long *node_off, const int *nloc, const int *lnodes, const int *kg,
+                                const long long *panel_off, const T *X, const int *gcol_off, const int *gcol,
+                                const double *u, double *z) {
+  __shared__ A ul[512];
+  int g = blockIdx.y;
+  int k = kg[g];
+  for (int a = threadIdx.x; a < k; a += blockDim.x) ul[a] = (A)u[gcol[gcol_off[g] + a]];
+  __syncthreads();
+  int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  int N = nloc[g];
+  const T *Xg = X + panel_off[g];
+  const int *ln = lnodes + node_off[g];
+  int nw = blockDim.x >> 5;
+  for (int row = blockIdx.x * nw + wid; row < N; row += gridDim.x * nw) {
+    const T *xr = Xg + (long long)row * k;
+    A s = 0;
+    for (int a = lane; a < k; a += 32) s += (A)xr[a] * ul[a];
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    if (lane == 0) {
+      int o = row / 3, d = row - 3 * o;
+      z[3LL * ln[o] + d] = (double)s;
+    }
+  }
+}
+
+__global__ void k_prolong_iface(const int *iface_nodes, const int *iface_of_node, long long count,
+                                const int *iface_slot, const int *mortar_off, const long long *eta_off,
+                                const double *eta, const int *comp_mask, const int *col_off, const uint8_t *fixed,
+                                const double *u, double *z) {
+  long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= count) return;
+  int n = iface_nodes[p];
+  int c = iface_of_node[n];
+  int nc = mortar_off[c + 1] - mortar_off[c];
+  int cm = comp_mask[c], ncomp = __popc(cm);
+  const double *et = eta + eta_off[c] + (long long)iface_slot[n] * nc;
+  for (int gam = 0; gam < 3; ++gam) {
+    double s = 0.0;
+    if (((cm >> gam) & 1) && !fixed[3 * n + gam])
+      for (int i = 0; i < nc; ++i) s += et[i] * u[col_off[c] + i * ncomp + comp_rank(cm, gam)];
+    z[3LL * n + gam] = s;
+  }
+}
+
+template <typename T>
+T *panel_ptr(hplmm_ctx *c);
+template <>
+double *panel_ptr<double>(hplmm_ctx *c) { return c->X64.p; }
+template <>
+float *panel_ptr<float>(hplmm_ctx *c) { return c->X32.p; }
+
+template <typename T>
+void galerkin(hplmm_ctx *c, const Buf<int> &gbox, const std::vector<long long> &hgal, const Buf<long long> &gal_off,
+              const Buf<int> &gcol_off, const Buf<int> &gcol, int maxvol) {
+  cudaStream_t s = c->stream;
+  int G = c->n_grains;
+  Buf<T> P, Y;
+  P.alloc(std::max<long long>(hgal[G], 1));
+  Y.alloc(std::max<long long>(hgal[G], 1));
+  P.zero(s);
+  dim3 gf(grid_for(maxvol, 128), G);
+  k_gal_fill<T><<<gf, 128, 0, s>>>(gbox.p, gal_off.p, c->kg.p, c->grid_to_node.p, c->nx, c->ny, c->node_cls.p,
+                                   c->iface_of_node.p, c->iface_slot.p, c->fixed.p, c->grains.box.p,
+                                   c->grains.node_off.p, c->grains.lmap.p, c->panel_off.p, panel_ptr<T>(c),
+                                   c->mortar_off.p, c->eta_off.p, c->eta.p, c->comp_mask.p, c->gi_off.p,
+                                   c->gi_iface.p, c->gi_colbase.p, P.p);
+  HP_CHECK_LAUNCH();
+  dim3 gy(maxvol, G);
+  k_gal_Y<T><<<gy, 128, 0, s>>>(gbox.p, gal_off.p, c->kg.p, c->vgrain.p, c->mask.p, c->E.p, c->nx, c->ny, c->nz,
+                                c->Kref.p, c->fixed.p, c->grid_to_node.p, P.p, Y.p);
+  HP_CHECK_LAUNCH();
+  std::vector<int> tiles;
+  for (int g = 0; g < G; ++g) {
+    int k = c->h_kg[g];
+    for (int a0 = 0; a0 < k; a0 += 32)
+      for (int b0 = 0; b0 < k; b0 += 32) {
+        tiles.push_back(g);
+        tiles.push_back(a0);
+        tiles.push_back(b0);
+      }
+  }
+  if (!tiles.empty()) {
+    Buf<int> tl;
+    tl.upload(tiles, s);
+    k_gal_gemm<T><<<(unsigned)(tiles.size() / 3), 256, 0, s>>>(tl.p, gbox.p, gal_off.p, c->kg.p, gcol_off.p, gcol.p,
+                                                               P.p, Y.p, c->Ao.p, c->n_coarse);
+    HP_CHECK_LAUNCH();
+  }
+  HP_CUDA(cudaStreamSynchronize(s));
+}
+
+}  // namespace
+
+void build_coarse(hplmm_ctx *c, const double *b_corr) {
+  cudaStream_t s = c->stream;
+  int G = c->n_grains;
+  bool f64 = c->opt.local_prec == HPLMM_FP64;
+  // panels
+  std::vector<long long> poff(G + 1, 0);
+  for (int g = 0; g < G; ++g) poff[g + 1] = poff[g] + (long long)c->grains.h_n[g] * c->h_kg[g];
+  c->h_panel_off = poff;
+  c->panel_off.upload(poff, s);
+  if (f64) {
+    c->X64.alloc(std::max<long long>(poff[G], 1));
+    c->X64.zero(s);
+  } else {
+    c->X32.alloc(std::max<long long>(poff[G], 1));
+    c->X32.zero(s);
+  }
+  int maxn = 0, maxk = 0;
+  for (int g = 0; g < G; ++g) {
+    maxn = std::max(maxn, c->grains.h_n[g] / 3);
+    maxk = std::max(maxk, c->h_kg[g]);
+  }
+  HP_REQUIRE(maxk <= 512, HPLMM_ERR_INVALID,
+             "a grain couples to " + std::to_string(maxk) + " coarse columns (limit 512); use fewer mortars or larger grains");
+  dim3 grid(grid_for(std::max(maxn, 1), 128), G);
+  if (f64)
+    k_basis_rhs<double><<<grid, 128, 0, s>>>(G, c->grains.node_off.p, c->grains.n.p, c->grains.lnodes.p,
+                                             c->row_ptr.p, c->col.p, c->val64.p, c->iface_of_node.p, c->iface_slot.p,
+                                             c->iface_pair.p, c->mortar_off.p, c->eta_off.p, c->eta.p,
+                                             c->comp_mask.p, c->gi_off.p, c->gi_iface.p, c->gi_colbase.p, c->kg.p,
+                                             c->corr_col.p, c->panel_off.p, b_corr, c->opt.strict_two_grain, c->X64.p);
+  else
+    k_basis_rhs<float><<<grid, 128, 0, s>>>(G, c->grains.node_off.p, c->grains.n.p, c->grains.lnodes.p, c->row_ptr.p,
+                                            c->col.p, c->val64.p, c->iface_of_node.p, c->iface_slot.p,
+                                            c->iface_pair.p, c->mortar_off.p, c->eta_off.p, c->eta.p, c->comp_mask.p,
+                                            c->gi_off.p, c->gi_iface.p, c->gi_colbase.p, c->kg.p, c->corr_col.p,
+                                            c->panel_off.p, b_corr, c->opt.strict_two_grain, c->X32.p);
+  HP_CHECK_LAUNCH();
+  // batched local solves (Eqs. col_pk, col_cg): X_g <- (A^g_g)^{-1} X_g
+  if (f64)
+    solve_local_multi_f64(c, c->grains, c->X64.p, c->panel_off, c->kg, c->h_kg);
+  else
+    solve_local_multi_f32(c, c->grains, c->X32.p, c->panel_off, c->kg, c->h_kg);
+
+  // global column of every local panel column
+  std::vector<int> hgoff(G + 1, 0), hgcol;
+  for (int g = 0; g < G; ++g) {
+    for (int q = c->h_gi_off[g]; q < c->h_gi_off[g + 1]; ++q) {
+      int ci = c->h_gi_iface[q];
+      for (int col = c->h_col_off[ci]; col < c->h_col_off[ci + 1]; ++col) hgcol.push_back(col);
+    }
+    if (c->h_corr_col[g] >= 0) hgcol.push_back(c->h_corr_col[g]);
+    hgoff[g + 1] = (int)hgcol.size();
+  }
+  if (hgcol.empty()) hgcol.push_back(0);
+  c->gcol_off.upload(hgoff, s);
+  c->gcol.upload(hgcol, s);
+
+  // Galerkin product on each grain's node box
+  Buf<int> vmin, vmax;
+  vmin.alloc(3 * G);
+  vmax.alloc(3 * G);
+  vmin.fill_bytes(0x7f, s);
+  vmax.fill_bytes(0x80, s);
+  long long nv = (long long)c->nx * c->ny * c->nz;
+  k_grain_vbox<<<grid_for(nv, 256), 256, 0, s>>>(c->vgrain.p, c->nx, c->ny, c->nz, vmin.p, vmax.p);
+  HP_CHECK_LAUNCH();
+  auto lo = vmin.download(s), hi = vmax.download(s);
+  std::vector<int> hbox(6 * G, 0);
+  std::vector<long long> hgal(G + 1, 0);
+  int maxvol = 1;
+  for (int g = 0; g < G; ++g) {
+    int vol = 1;
+    for (int a = 0; a < 3; ++a) {
+      if (lo[3 * g + a] > hi[3 * g + a]) {
+        hbox[6 * g + a] = 0;
+        hbox[6 * g + 3 + a] = 0;
+        vol = 0;
+      } else {
+        hbox[6 * g + a] = lo[3 * g + a];
+        hbox[6 * g + 3 + a] = hi[3 * g + a] - lo[3 * g + a] + 2;
+        vol *= hbox[6 * g + 3 + a];
+      }
+    }
+    if (vol == 0)
+      for (int a = 0; a < 3; ++a) hbox[6 * g + 3 + a] = 0;
+    maxvol = std::max(maxvol, vol);
+    hgal[g + 1] = hgal[g] + 3LL * vol * c->h_kg[g];
+  }
+  Buf<int> gbox;
+  gbox.upload(hbox, s);
+  Buf<long long> gal_off;
+  gal_off.upload(hgal, s);
+  long long No = c->n_coarse;
+  c->Ao.alloc(std::max<long long>(No * No, 1));
+  c->Ao.zero(s);
+  if (f64)
+    galerkin<double>(c, gbox, hgal, gal_off, c->gcol_off, c->gcol, maxvol);
+  else
+    galerkin<float>(c, gbox, hgal, gal_off, c->gcol_off, c->gcol, maxvol);
+  if (No > 0) {
+    k_symmetrize<<<grid_for(No * No, 256), 256, 0, s>>>(c->Ao.p, No, nullptr);
+    HP_CHECK_LAUNCH();
+    // Cholesky factor (FP64) in a copy
+    c->Lo.alloc(No * No);
+    HP_CUDA(cudaMemcpyAsync(c->Lo.p, c->Ao.p, sizeof(double) * No * No, cudaMemcpyDeviceToDevice, s));
+    int T = (int)((No + TB - 1) / TB);
+    c->Lo_dinv.alloc((size_t)T * TB * TB);
+    for (int kt = 0; kt < T; ++kt) {
+      k_potrf_tile<<<1, 256, 0, s>>>(c->Lo.p, No, kt, c->Lo_dinv.p, c->status.p);
+      HP_CHECK_LAUNCH();
+      int m = T - kt - 1;
+      if (m > 0) {
+        k_trsm_tiles<<<m, 256, 0, s>>>(c->Lo.p, No, kt, c->Lo_dinv.p);
+        HP_CHECK_LAUNCH();
+        k_syrk_tiles<<<m * (m + 1) / 2, 256, 0, s>>>(c->Lo.p, No, kt, T);
+        HP_CHECK_LAUNCH();
+      }
+    }
+  }
+  HP_CUDA(cudaStreamSynchronize(s));
+}
+
+void coarse_apply(hplmm_ctx *c, const double *r_pad, double *z_pad) {
+  cudaStream_t s = c->stream;
+  long long No = c->n_coarse;
+  int G = c->n_grains;
+  bool f64 = c->opt.local_prec == HPLMM_FP64;
+  HP_CUDA(cudaMemsetAsync(z_pad, 0, sizeof(double) * 3 * (size_t)c->n_nodes, s));
+  if (No == 0) return;
+  double *t = c->w_coarse_t.p;
+  HP_CUDA(cudaMemsetAsync(t, 0, sizeof(double) * No, s));
+  if (c->n_iface_nodes > 0) {
+    k_restrict_iface<<<grid_for(c->n_iface_nodes, 128), 128, 0, s>>>(
+        c->iface_nodes.p, c->iface_of_node.p, c->n_iface_nodes, c->iface_slot.p, c->mortar_off.p, c->eta_off.p,
+        c->eta.p, c->comp_mask.p, c->col_off.p, c->fixed.p, r_pad, t);
+    HP_CHECK_LAUNCH();
+  }
+  int kmax = 1;
+  for (int g = 0; g < G; ++g) kmax = std::max(kmax, c->h_kg[g]);
+  dim3 gr((kmax + 31) / 32, G);
+  if (f64)
+    k_restrict_grain<double, double><<<gr, 256, 0, s>>>(c->grains.node_off.p, c->grains.n.p, c->grains.lnodes.p,
+                                                        c->kg.p, c->panel_off.p, c->X64.p, c->gcol_off.p, c->gcol.p,
+                                                        r_pad, t);
+  else
+    k_restrict_grain<float, float><<<gr, 256, 0, s>>>(c->grains.node_off.p, c->grains.n.p, c->grains.lnodes.p,
+                                                      c->kg.p, c->panel_off.p, c->X32.p, c->gcol_off.p, c->gcol.p,
+                                                      r_pad, t);
+  HP_CHECK_LAUNCH();
+  k_coarse_solve<<<1, 1024, 0, s>>>(c->Lo.p, No, c->Lo_dinv.p, t);
+  HP_CHECK_LAUNCH();
+  dim3 gp(16, G);
+  if (f64)
+    k_prolong_grain<double, double><<<gp, 256, 0, s>>>(c->grains.node_off.p, c->grains.n.p, c->grains.lnodes.p,
+                                                       c->kg.p, c->panel_off.p, c->X64.p, c->gcol_off.p, c->gcol.p, t,
+                                                       z_pad);
+  else
+    k_prolong_grain<float, float><<<gp, 256, 0, s>>>(c->grains.node_off.p, c->grains.n.p, c->grains.lnodes.p,
+                                                     c->kg.p, c->panel_off.p, c->X32.p, c->gcol_off.p, c->gcol.p, t,
+                                                     z_pad);
+  HP_CHECK_LAUNCH();
+  if (c->n_iface_nodes > 0) {
+    k_prolong_iface<<<grid_for(c->n_iface_nodes, 128), 128, 0, s>>>(
+        c->iface_nodes.p, c->iface_of_node.p, c->n_iface_nodes, c->iface_slot.p, c->mortar_off.p, c->eta_off.p,
+        c->eta.p, c->comp_mask.p, c->col_off.p, c->fixed.p, t, z_pad);
+    HP_CHECK_LAUNCH();
+  }
+}
+
+void prolong_column(hplmm_ctx *c, long long col, double *out_pad) {
+  cudaStream_t s = c->stream;
+  long long No = c->n_coarse;
+  int G = c->n_grains;
+  bool f64 = c->opt.local_prec == HPLMM_FP64;
+  HP_CUDA(cudaMemsetAsync(out_pad, 0, sizeof(double) * 3 * (size_t)c->n_nodes, s));
+  double *u = c->w_coarse_u.p;
+  HP_CUDA(cudaMemsetAsync(u, 0, sizeof(double) * No, s));
+  double one = 1.0;
+  HP_CUDA(cudaMemcpyAsync(u + col, &one, sizeof(double), cudaMemcpyHostToDevice, s));
+  dim3 gp(16, G);
+  if (f64)
+    k_prolong_grain<double, double><<<gp, 256, 0, s>>>(c->grains.node_off.p, c->grains.n.p, c->grains.lnodes.p,
+                                                       c->kg.p, c->panel_off.p, c->X64.p, c->gcol_off.p, c->gcol.p, u,
+                                                       out_pad);
+  else
+    k_prolong_grain<float, float><<<gp, 256, 0, s>>>(c->grains.node_off.p, c->grains.n.p, c->grains.lnodes.p,
+                                                     c->kg.p, c->panel_off.p, c->X32.p, c->gcol_off.p, c->gcol.p, u,
+                                                     out_pad);
+  HP_CHECK_LAUNCH();
+  if (c->n_iface_nodes > 0) {
+    k_prolong_iface<<<grid_for(c->n_iface_nodes, 128), 128, 0, s>>>(
+        c->iface_nodes.p, c->iface_of_node.p, c->n_iface_nodes, c->iface_slot.p, c->mortar_off.p, c->eta_off.p,
+        c->eta.p, c->comp_mask.p, c->col_off.p, c->fixed.p, u, out_pad);
+    HP_CHECK_LAUNCH();
+  }
+  HP_CUDA(cudaStreamSynchronize(s));
+}
+
+}  // namespace hp

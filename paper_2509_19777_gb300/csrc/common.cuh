@@ -1,0 +1,247 @@
+// Internal definitions shared by the hPLMM CUDA translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <cstdio>
+#include <stdexcept>
+#include <type_traits>
+#include <string>
+#include <vector>
+
+#include "../../include/hplmm.h"
+
+namespace hp {
+
+// ---------------------------------------------------------------- errors
+struct Error : public std::runtime_error {
+  hplmm_status code;
+  Error(hplmm_status c, const std::string &m) : std::runtime_error(m), code(c) {}
+};
+
+#define HP_CUDA(call)                                                                      \
+  do {                                                                                     \
+    cudaError_t e_ = (call);                                                               \
+    if (e_ != cudaSuccess) {                                                               \
+      throw ::hp::Error(e_ == cudaErrorMemoryAllocation ? HPLMM_ERR_OOM : HPLMM_ERR_CUDA,  \
+                        std::string(#call) + ": " + cudaGetErrorString(e_) + " at " +      \
+                            __FILE__ + ":" + std::to_string(__LINE__));                    \
+    }                                                                                      \
+  } while (0)
+
+#define HP_CHECK_LAUNCH() HP_CUDA(cudaGetLastError())
+
+#define HP_REQUIRE(cond, code, msg)        \
+  do {                                     \
+    if (!(cond)) throw ::hp::Error(code, msg); \
+  } while (0)
+
+// ---------------------------------------------------------------- device buffer
+template <typename T>
+struct Buf {
+  T *p = nullptr;
+  size_t n = 0;
+  Buf() = default;
+  Buf(const Buf &) = delete;
+  Buf &operator=(const Buf &) = delete;
+  ~Buf() { release(); }
+  void release() {
+    if (p) cudaFree(p);
+    p = nullptr;
+    n = 0;
+  }
+  void alloc(size_t count) {
+    release();
+    if (count == 0) count = 1;
+    cudaError_t e = cudaMalloc(&p, count * sizeof(T));
+    if (e != cudaSuccess) {
+      p = nullptr;
+      throw Error(HPLMM_ERR_OOM, "cudaMalloc of " + std::to_string(count * sizeof(T)) + " bytes failed: " +
+                                     cudaGetErrorString(e));
+    }
+    n = count;
+  }
+  void zero(cudaStream_t s) { HP_CUDA(cudaMemsetAsync(p, 0, n * sizeof(T), s)); }
+  void fill_bytes(int v, cudaStream_t s) { HP_CUDA(cudaMemsetAsync(p, v, n * sizeof(T), s)); }
+  void upload(const std::vector<T> &h, cudaStream_t s) {
+    alloc(h.size());
+    if (!h.empty()) HP_CUDA(cudaMemcpyAsync(p, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice, s));
+  }
+  std::vector<T> download(cudaStream_t s, size_t count = (size_t)-1) const {
+    if (count == (size_t)-1) count = n;
+    std::vector<T> h(count);
+    if (count) HP_CUDA(cudaMemcpyAsync(h.data(), p, count * sizeof(T), cudaMemcpyDeviceToHost, s));
+    HP_CUDA(cudaStreamSynchronize(s));
+    return h;
+  }
+  T *get() const { return p; }
+};
+
+inline unsigned grid_for(long long n, int block) {
+  long long g = (n + block - 1) / block;
+  if (g < 1) g = 1;
+  if (g > 2147483647LL) g = 2147483647LL;
+  return (unsigned)g;
+}
+
+// ---------------------------------------------------------------- primitives (prims.cu)
+// exclusive scan of int32 values (in may equal out); returns the total
+long long exclusive_scan_i32(const int *in, int *out, long long n, cudaStream_t s);
+// sort 64-bit unsigned keys ascending in place (n arbitrary; uses a power-of-two scratch)
+void sort_u64(uint64_t *keys, long long n, cudaStream_t s);
+
+// ---------------------------------------------------------------- local band problems
+// A local problem (grain grid or contact grid) is a principal submatrix of A_hat on
+// the nodes of a box, numbered in a permuted lexicographic order (slowest axis = the
+// longest box extent) so that the matrix is banded; all three components of every
+// member node are kept, fixed components becoming identity rows.
+struct LocalSet {
+  int count = 0;
+  // host copies
+  std::vector<int> h_n;        // local DOFs (3 * member nodes)
+  std::vector<int> h_bw;       // half bandwidth in DOFs
+  std::vector<long long> h_band_off;  // offset of the band storage (elements)
+  std::vector<long long> h_node_off;  // offset into node lists (capacity = box volume)
+  std::vector<long long> h_vec_off;   // offset of local vectors (n entries each)
+  long long band_total = 0, node_total = 0, vec_total = 0;
+  // device
+  Buf<int> box;       // per problem: lo[3], ext[3], perm[3] (9 ints)
+  Buf<int> n;         // local DOF count
+  Buf<int> bw;        // half bandwidth (DOFs)
+  Buf<long long> band_off, node_off, vec_off;
+  Buf<int> lnodes;    // ordinal -> global node id (node_off based)
+  Buf<int> lmap;      // box cell (permuted lexicographic) -> ordinal or -1 (node_off based)
+  Buf<long long> dinv_off;
+  Buf<double> band64, dinv64;   // FP64 factors (panel width 16)
+  Buf<float> band32, dinv32;    // FP32 factors (panel width 32)
+  Buf<int> order;     // problems sorted by decreasing factorisation cost
+  hplmm_prec prec = HPLMM_FP64;
+};
+
+}  // namespace hp
+
+// ---------------------------------------------------------------- the context
+struct hplmm_ctx {
+  hplmm_options opt{};
+  cudaStream_t stream = nullptr;
+  std::string err;
+  int device = 0;
+
+  // ---- assembly (Section 2)
+  bool assembled = false;
+  int nx = 0, ny = 0, nz = 0;
+  long long n_grid = 0;            // (nx+1)(ny+1)(nz+1)
+  int n_nodes = 0;
+  long long n_dof = 0;
+  double nu = 0.3, E0 = 1.0;
+  hp::Buf<uint8_t> mask;           // voxel mask copy
+  hp::Buf<float> E;                // voxel modulus (E0 filled if none given)
+  hp::Buf<int> grid_to_node;       // n_grid -> node id or -1
+  hp::Buf<int> node_ijk;           // n_nodes*3
+  hp::Buf<uint8_t> fixed;          // n_nodes*3
+  hp::Buf<int> free_index;         // n_nodes*3 -> free DOF or -1
+  hp::Buf<int> dof_slot;           // n_dof -> node*3+d
+  hp::Buf<double> Kref;            // 24x24 reference element stiffness (E = 1)
+  hp::Buf<int> row_ptr, col;       // BSR over nodes, 3x3 blocks
+  long long nnzb = 0;
+  hp::Buf<double> val64;           // nnzb*9, fixed rows/cols zeroed
+  hp::Buf<float> val32;            // FP32 shadow
+  hp::Buf<double> b_pad;           // n_nodes*3 right-hand side, 0 on fixed slots
+  hp::Buf<double> b_corr;          // right-hand side defining the correction columns (padded)
+
+  // ---- decomposition (Sections 3.1-3.2)
+  bool setup_done = false;
+  int n_grains = 0, px = 0, py = 0, pz = 0;
+  hp::Buf<int> vgrain;             // grain id per voxel (-1 void)
+  hp::Buf<int> node_cls;           // >=0 grain of an interior node; -1 interface node; -2 none
+  hp::Buf<int> iface_of_node;      // interface id or -1
+  hp::Buf<int> iface_slot;         // position of the node inside its interface list
+  int n_ifaces = 0;
+  long long n_iface_nodes = 0;
+  hp::Buf<int> iface_pair;         // n_ifaces*2
+  hp::Buf<int> iface_off;          // n_ifaces+1
+  hp::Buf<int> iface_nodes;        // n_iface_nodes
+  std::vector<int> h_iface_off;
+  // grain -> coupled interfaces (CSR) and column layout
+  std::vector<int> h_gi_off, h_gi_iface, h_gi_colbase;
+  hp::Buf<int> gi_off, gi_iface, gi_colbase;  // colbase = local column offset of the interface inside K_g
+  std::vector<int> h_kg;           // columns per grain (incl. correction)
+  std::vector<long long> h_panel_off;  // offsets of X_g panels (elements)
+  hp::Buf<int> kg;
+  hp::Buf<long long> panel_off;
+  std::vector<int> h_corr_col;     // coarse column of grain g's correction, or -1
+  hp::Buf<int> corr_col;
+
+  // ---- mortars (Section 3.3)
+  int n_mortars = 0;
+  hp::Buf<int> mortar_off;         // n_ifaces+1
+  hp::Buf<int> mortar_nodes;       // slot -> node id
+  hp::Buf<int> mortar_idx;         // slot -> index into its interface's node list
+  hp::Buf<long long> eta_off;      // n_ifaces+1 (elements)
+  hp::Buf<double> eta;             // per interface: F x nc row-major
+  hp::Buf<int> comp_mask;          // per interface: bit gamma set if component gamma has a free DOF
+  hp::Buf<int> col_off;            // n_ifaces+1: first coarse column of each interface
+  std::vector<int> h_mortar_off, h_comp_mask, h_col_off;
+  long long n_mortar_cols = 0, n_coarse = 0;
+
+  // ---- local problems
+  hp::LocalSet grains, contacts;
+
+  // ---- coarse space (Section 4.2)
+  hp::Buf<double> X64;             // basis panels X_g (local DOF rows x k_g), FP64
+  hp::Buf<float> X32;              // FP32 copy/compute
+  hp::Buf<double> Ao;              // N^o x N^o
+  hp::Buf<double> Lo;              // Cholesky factor (lower, row-major full storage)
+  hp::Buf<double> Lo_dinv;         // inverses of its 64x64 diagonal tiles
+  hp::Buf<int> gcol_off, gcol;     // global coarse column of each panel column
+  hp::Buf<int> status;             // device error word
+
+  // ---- apply / GMRES work vectors (padded n_nodes*3)
+  hp::Buf<double> w_r1, w_r2, w_z1, w_zz, w_zg, w_t, w_w;
+  hp::Buf<double> w_coarse_t, w_coarse_u;
+  hp::Buf<double> w_loc64;         // local vectors for smoother
+  hp::Buf<float> w_loc32;
+  hp::Buf<double> w_in, w_out;     // padded copies of API vectors
+  hp::Buf<double> V, Z, w_dots, w_h;
+  int gmres_cap = 0;
+  hp::Buf<double> w_partial;
+
+  // graph of the apply
+  cudaGraphExec_t apply_graph = nullptr;
+  const double *graph_r = nullptr;
+  double *graph_z = nullptr;
+
+  double t_ml = 0, t_mg = 0;
+};
+
+namespace hp {
+// assemble.cu
+void assemble(hplmm_ctx *c, const uint8_t *mask, int nx, int ny, int nz, const float *E, double E0, double nu,
+              const hplmm_bcs *bcs, double *b_out);
+void spmv(hplmm_ctx *c, const double *x_pad, double *y_pad, hplmm_prec prec, const double *sub = nullptr);
+void gather_free(hplmm_ctx *c, const double *pad, double *dof);
+void scatter_free(hplmm_ctx *c, const double *dof, double *pad);
+// maps.cu
+void build_maps(hplmm_ctx *c, const int32_t *partition);
+void build_mortars(hplmm_ctx *c);
+void compute_W(hplmm_ctx *c, int64_t *W);
+// local.cu
+void build_local_sets(hplmm_ctx *c);
+void factor_local(hplmm_ctx *c, LocalSet &S, hplmm_prec prec);
+void solve_local_multi_f64(hplmm_ctx *c, LocalSet &S, double *X, const Buf<long long> &x_off, const Buf<int> &x_ld,
+                           const std::vector<int> &h_ld);
+void solve_local_multi_f32(hplmm_ctx *c, LocalSet &S, float *X, const Buf<long long> &x_off, const Buf<int> &x_ld,
+                           const std::vector<int> &h_ld);
+void smoother_apply(hplmm_ctx *c, LocalSet &S, const double *r_pad, double *z_pad, bool atomic);
+int num_sms();
+// coarse.cu
+void build_coarse(hplmm_ctx *c, const double *b_pad_for_corr);
+void coarse_apply(hplmm_ctx *c, const double *r_pad, double *z_pad);
+void prolong_column(hplmm_ctx *c, long long col, double *out_pad);
+// apply.cu
+void precond_apply(hplmm_ctx *c, const double *r_pad, double *z_pad);
+void smoother_stage(hplmm_ctx *c, const double *r_pad, double *z_pad);
+int fgmres(hplmm_ctx *c, const double *b_pad, double *x_pad, double tol, hplmm_stats *st);
+void check_status(hplmm_ctx *c);
+}  // namespace hp

@@ -1,0 +1,838 @@
+// Local problems of the preconditioner: the grain-grid blocks A^{g_i}_{g_i}
+// (Eqs. col_pk, col_cg and Mg_Mz) and the contact-grid blocks R A_hat E of
+// Eq. Mg_Mz.  Each is a principal submatrix of A_hat, factorised once by an
+// exact banded Cholesky (the paper precomputes exact local factorisations,
+// Section 6.3) and then solved many times.
+//
+// Layout.  A problem's nodes are numbered in a permuted lexicographic order
+// of its box (slowest axis = longest extent) which makes the matrix banded
+// with half bandwidth bw.  The band is stored panel-blocked: panel p holds the
+// NB columns [p*NB, p*NB+NB) and the NB+bw rows starting at p*NB, row-major,
+// so every panel is one contiguous (NB+bw) x NB tile.  The inverse of each
+// NB x NB diagonal factor block is stored beside it, turning the in-block
+// triangular solves into small dense products.
+#include "common.cuh"
+
+#include <algorithm>
+#include <numeric>
+
+namespace hp {
+
+template <typename T> struct NBOf;
+template <> struct NBOf<float> { static constexpr int v = 32; };
+template <> struct NBOf<double> { static constexpr int v = 16; };
+
+namespace {
+
+constexpr int FACT_THREADS = 256;
+
+__device__ __forceinline__ long long panel_addr(int i, int j, int NB, int bw) {
+  int p = j / NB, c = j - p * NB, r = i - p * NB;
+  return (long long)p * (NB + bw) * NB + (long long)r * NB + c;
+}
+
+// box of problem k: lo[3], ext[3], perm[3] (perm[0] = fastest axis)
+struct Box {
+  int lo[3], ext[3], perm[3];
+};
+
+__device__ __forceinline__ Box load_box(const int *box, int k) {
+  Box b;
+  for (int a = 0; a < 3; ++a) {
+    b.lo[a] = box[9 * k + a];
+    b.ext[a] = box[9 * k + 3 + a];
+    b.perm[a] = box[9 * k + 6 + a];
+  }
+  return b;
+}
+
+// cell index of grid point (x,y,z) in the box's permuted order, or -1 when outside
+__device__ __forceinline__ int box_cell(const Box &b, int x, int y, int z) {
+  int p[3] = {x - b.lo[0], y - b.lo[1], z - b.lo[2]};
+  for (int a = 0; a < 3; ++a)
+    if (p[a] < 0 || p[a] >= b.ext[a]) return -1;
+  int f = b.perm[0], m = b.perm[1], s = b.perm[2];
+  return (p[s] * b.ext[m] + p[m]) * b.ext[f] + p[f];
+}
+
+__device__ __forceinline__ void cell_xyz(const Box &b, int cell, int *xyz) {
+  int f = b.perm[0], m = b.perm[1], s = b.perm[2];
+  int pf = cell % b.ext[f];
+  int t = cell / b.ext[f];
+  int pm = t % b.ext[m];
+  int ps = t / b.ext[m];
+  int p[3];
+  p[f] = pf;
+  p[m] = pm;
+  p[s] = ps;
+  for (int a = 0; a < 3; ++a) xyz[a] = b.lo[a] + p[a];
+}
+
+// ---------------------------------------------------------------- boxes
+__global__ void k_grain_bbox(const int *cls, const int *node_ijk, int n_nodes, int *bmin, int *bmax) {
+  int n = blockIdx.x * blockDim.x + threadIdx.x;
+  if (n >= n_nodes) return;
+  int g = cls[n];
+  if (g < 0) return;
+  for (int a = 0; a < 3; ++a) {
+    atomicMin(&bmin[3 * g + a], node_ijk[3 * n + a]);
+    atomicMax(&bmax[3 * g + a], node_ijk[3 * n + a]);
+  }
+}
+
+__global__ void k_iface_bbox(const int *iface_nodes, const int *iface_of_node, long long count, const int *node_ijk,
+                             int *bmin, int *bmax) {
+  long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= count) return;
+  int n = iface_nodes[p];
+  int c = iface_of_node[n];
+  for (int a = 0; a < 3; ++a) {
+    atomicMin(&bmin[3 * c + a], node_ijk[3 * n + a]);
+    atomicMax(&bmax[3 * c + a], node_ijk[3 * n + a]);
+  }
+}
+
+// mark the (2w+1)^3 neighbourhood of every interface node in its contact grid's box
+__global__ void k_contact_mark(const int *iface_nodes, const int *iface_of_node, long long count, const int *node_ijk,
+                               const int *box, const long long *node_off, int w, int *lmap) {
+  long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= count) return;
+  int n = iface_nodes[p];
+  int c = iface_of_node[n];
+  Box b = load_box(box, c);
+  int x = node_ijk[3 * n], y = node_ijk[3 * n + 1], z = node_ijk[3 * n + 2];
+  for (int dz = -w; dz <= w; ++dz)
+    for (int dy = -w; dy <= w; ++dy)
+      for (int dx = -w; dx <= w; ++dx) {
+        int cell = box_cell(b, x + dx, y + dy, z + dz);
+        if (cell >= 0) lmap[node_off[c] + cell] = 1;
+      }
+}
+
+// one CTA per problem: enumerate member nodes in box order, assign ordinals
+// kind 0: grain (member = interior node of grain k); kind 1: contact grid (member = marked, exists, free)
+__global__ void k_local_enum(int kind, const int *box, const long long *node_off, int *lmap, int *lnodes, int *nloc,
+                             const int *grid_to_node, int nx, int ny, const int *cls, const uint8_t *fixed) {
+  __shared__ int warp_tot[32];
+  __shared__ int running;
+  int k = blockIdx.x;
+  Box b = load_box(box, k);
+  int vol = b.ext[0] * b.ext[1] * b.ext[2];
+  long long off = node_off[k];
+  if (threadIdx.x == 0) running = 0;
+  __syncthreads();
+  long long NX = nx + 1, NY = ny + 1;
+  for (int base = 0; base < vol; base += blockDim.x) {
+    int cell = base + threadIdx.x;
+    int node = -1, member = 0;
+    if (cell < vol) {
+      int xyz[3];
+      cell_xyz(b, cell, xyz);
+      node = grid_to_node[((long long)xyz[2] * NY + xyz[1]) * NX + xyz[0]];
+      if (node >= 0) {
+        if (kind == 0) {
+          member = cls[node] == k;
+        } else {
+          bool has_free = !fixed[3 * node] || !fixed[3 * node + 1] || !fixed[3 * node + 2];
+          member = (lmap[off + cell] == 1) && has_free;
+        }
+      }
+    }
+    // block exclusive scan of member flags
+    int v = member;
+    int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    int incl = v;
+    for (int o = 1; o < 32; o <<= 1) {
+      int t = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += t;
+    }
+    if (lane == 31) warp_tot[wid] = incl;
+    __syncthreads();
+    if (wid == 0) {
+      int nw = blockDim.x >> 5;
+      int t = lane < nw ? warp_tot[lane] : 0;
+      int s = t;
+      for (int o = 1; o < 32; o <<= 1) {
+        int u = __shfl_up_sync(0xffffffffu, s, o);
+        if (lane >= o) s += u;
+      }
+      warp_tot[lane] = s - t;
+    }
+    __syncthreads();
+    int excl = incl - v + warp_tot[wid] + running;
+    if (cell < vol) {
+      lmap[off + cell] = member ? excl : -1;
+      if (member) lnodes[off + excl] = node;
+    }
+    __syncthreads();
+    if (threadIdx.x == blockDim.x - 1) running = excl + v;
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) nloc[k] = 3 * running;
+}
+
+// half bandwidth: max |ord(n) - ord(m)| over coupled member pairs
+__global__ void k_local_bw(const int *box, const long long *node_off, const int *nloc, const int *lmap,
+                           const int *lnodes, const int *node_ijk, const int *row_ptr, const int *col, int *bw) {
+  int k = blockIdx.x;
+  Box b = load_box(box, k);
+  long long off = node_off[k];
+  int cnt = nloc[k] / 3;
+  int best = 0;
+  for (int o = threadIdx.x; o < cnt; o += blockDim.x) {
+    int n = lnodes[off + o];
+    for (int p = row_ptr[n]; p < row_ptr[n + 1]; ++p) {
+      int m = col[p];
+      int cell = box_cell(b, node_ijk[3 * m], node_ijk[3 * m + 1], node_ijk[3 * m + 2]);
+      if (cell < 0) continue;
+      int om = lmap[off + cell];
+      if (om >= 0) best = max(best, abs(om - o));
+    }
+  }
+  for (int o = 16; o > 0; o >>= 1) best = max(best, __shfl_down_sync(0xffffffffu, best, o));
+  if ((threadIdx.x & 31) == 0) atomicMax(&bw[k], 3 * best + 2);
+}
+
+// scatter the lower band of the principal submatrix into panel-blocked storage
+template <typename T>
+__global__ void k_local_extract(const int *box, const long long *node_off, const int *nloc, const int *bwv,
+                                const long long *band_off, const int *lmap, const int *lnodes, const int *node_ijk,
+                                const int *row_ptr, const int *col, const double *val, const uint8_t *fixed, T *band,
+                                int NB) {
+  int k = blockIdx.x;
+  Box b = load_box(box, k);
+  long long off = node_off[k];
+  int cnt = nloc[k] / 3;
+  int bw = bwv[k];
+  T *B = band + band_off[k];
+  for (int o = threadIdx.x; o < cnt; o += blockDim.x) {
+    int n = lnodes[off + o];
+    for (int p = row_ptr[n]; p < row_ptr[n + 1]; ++p) {
+      int m = col[p];
+      int cell = box_cell(b, node_ijk[3 * m], node_ijk[3 * m + 1], node_ijk[3 * m + 2]);
+      if (cell < 0) continue;
+      int om = lmap[off + cell];
+      if (om < 0 || om > o) continue;
+      const double *v = val + (long long)p * 9;
+      for (int d = 0; d < 3; ++d)
+        for (int d2 = 0; d2 < 3; ++d2) {
+          int i = 3 * o + d, j = 3 * om + d2;
+          if (j > i) continue;
+          B[panel_addr(i, j, NB, bw)] = (T)v[3 * d + d2];
+        }
+    }
+    for (int d = 0; d < 3; ++d)
+      if (fixed[3 * n + d]) {
+        int i = 3 * o + d;
+        B[panel_addr(i, i, NB, bw)] = (T)1.0;
+      }
+  }
+}
+
+// ---------------------------------------------------------------- factorisation
+template <typename T>
+__device__ __forceinline__ T dev_sqrt(T x);
+template <>
+__device__ __forceinline__ float dev_sqrt<float>(float x) { return sqrtf(x); }
+template <>
+__device__ __forceinline__ double dev_sqrt<double>(double x) { return sqrt(x); }
+
+// persistent: each CTA takes problems from the cost-ordered queue
+template <typename T, int NB>
+__global__ void __launch_bounds__(FACT_THREADS) k_band_chol(const int *order, int count, int *queue,
+                                                           const int *nloc, const int *bwv,
+                                                           const long long *band_off, const long long *dinv_off,
+                                                           T *band, T *dinv, int *status) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  constexpr int LD = NB + (16 / sizeof(T));  // padded row stride
+  T *P = reinterpret_cast<T *>(smraw);
+  __shared__ T Dv[NB][NB + 1];
+  __shared__ int s_job;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = FACT_THREADS / 32;
+  for (;;) {
+    if (threadIdx.x == 0) s_job = atomicAdd(queue, 1);
+    __syncthreads();
+    int job = s_job;
+    __syncthreads();
+    if (job >= count) return;
+    int k = order[job];
+    int N = nloc[k], bw = bwv[k];
+    if (N == 0) continue;
+    T *B = band + band_off[k];
+    T *Di = dinv + dinv_off[k];
+    const int RP = NB + bw;
+    for (int k0 = 0, p = 0; k0 < N; k0 += NB, ++p) {
+      int nb = min(NB, N - k0);
+      int R = min(N - k0, RP);
+      T *Bp = B + (long long)p * RP * NB;
+      // 1. load panel rows [0,R) into shared memory
+      for (int e = threadIdx.x; e < R * NB; e += FACT_THREADS) {
+        int r = e / NB, cc = e - r * NB;
+        P[r * LD + cc] = Bp[e];
+      }
+      __syncthreads();
+      // 2. factor the diagonal block (one warp), then invert it
+      if (wid == 0) {
+        for (int cc = 0; cc < nb; ++cc) {
+          if (lane == 0) {
+            T d = P[cc * LD + cc];
+            if (!(d > (T)0)) {
+              atomicExch(status, (int)HPLMM_ERR_SINGULAR);
+              d = (T)1;
+            }
+            P[cc * LD + cc] = dev_sqrt<T>(d);
+          }
+          __syncwarp();
+          T dd = P[cc * LD + cc];
+          for (int r = cc + 1 + lane; r < nb; r += 32) P[r * LD + cc] /= dd;
+          __syncwarp();
+          for (int r = cc + 1 + lane; r < nb; r += 32) {
+            T lr = P[r * LD + cc];
+            for (int c2 = cc + 1; c2 <= r; ++c2) P[r * LD + c2] -= lr * P[c2 * LD + cc];
+          }
+          __syncwarp();
+        }
+        // zero the strict upper part and padding of the diagonal block
+        for (int e = lane; e < NB * NB; e += 32) {
+          int r = e / NB, cc = e % NB;
+          if (cc > r || r >= nb || cc >= nb) P[r * LD + cc] = (T)0;
+        }
+        __syncwarp();
+        // column j of inv(L_kk): solve L x = e_j (lane j)
+        for (int j = lane; j < NB; j += 32) {
+          for (int i = 0; i < NB; ++i) {
+            T v;
+            if (i < j || i >= nb || j >= nb) {
+              v = (T)0;
+            } else {
+              T s = (i == j) ? (T)1 : (T)0;
+              for (int q = j; q < i; ++q) s -= P[i * LD + q] * Dv[q][j];
+              v = s / P[i * LD + i];
+            }
+            Dv[i][j] = v;
+          }
+        }
+      }
+      __syncthreads();
+      // 3. L_panel = A_panel * inv(L_kk)^T for rows [nb, R)
+      for (int r = nb + threadIdx.x; r < R; r += FACT_THREADS) {
+        T out[NB];
+#pragma unroll
+        for (int cc = 0; cc < NB; ++cc) out[cc] = 0;
+#pragma unroll
+        for (int q = 0; q < NB; ++q) {
+          T aq = P[r * LD + q];
+          const volatile T *dcol = &Dv[0][q];
+#pragma unroll
+          for (int cc = q; cc < NB; ++cc) out[cc] += aq * dcol[cc * (NB + 1)];
+        }
+#pragma unroll
+        for (int cc = 0; cc < NB; ++cc) P[r * LD + cc] = out[cc];
+      }
+      // store inv(L_kk)
+      for (int e = threadIdx.x; e < NB * NB; e += FACT_THREADS) Di[(long long)p * NB * NB + e] = Dv[e / NB][e % NB];
+      __syncthreads();
+      // 4. write the panel back
+      for (int e = threadIdx.x; e < R * NB; e += FACT_THREADS) {
+        int r = e / NB, cc = e - r * NB;
+        Bp[e] = P[r * LD + cc];
+      }
+      // 5. trailing update of the (R-nb)^2 lower window: A[i][j] -= sum_c P[i][c] P[j][c].
+      //    Warp tiles of 16 rows x 32 columns (lane = column), rows strided over warps.
+      int Wn = R - nb;
+      int nrt = (Wn + 15) / 16;
+      int nct = (Wn + 31) / 32;
+      int ntiles = 0;
+      for (int tj = 0; tj < nct; ++tj) ntiles += max(0, nrt - 2 * tj);
+      for (int t = wid; t < ntiles; t += nw) {
+        // tile t -> (column tile tj, row tile ti), column-major over the lower window (ti >= 2 tj)
+        int tj = 0, rem = t;
+        while (rem >= nrt - 2 * tj) {
+          rem -= nrt - 2 * tj;
+          ++tj;
+        }
+        int ti = 2 * tj + rem;
+        int jl = nb + tj * 32 + lane;
+        T pj[NB];
+#pragma unroll
+        for (int cc = 0; cc < NB; ++cc) pj[cc] = (jl < R) ? P[jl * LD + cc] : (T)0;
+        T acc[16];
+#pragma unroll
+        for (int q = 0; q < 16; ++q) {
+          int il = nb + ti * 16 + q;
+          int ir = il < R ? il : nb;  // rows past the window read a valid row; the result is discarded
+          T s = 0;
+#pragma unroll
+          for (int cc = 0; cc < NB; ++cc) s += P[ir * LD + cc] * pj[cc];
+          acc[q] = s;
+        }
+#pragma unroll
+        for (int q = 0; q < 16; ++q) {
+          int il = nb + ti * 16 + q;
+          if (il < R && jl < R && jl <= il) B[panel_addr(k0 + il, k0 + jl, NB, bw)] -= acc[q];
+        }
+      }
+      __syncthreads();
+    }
+  }
+}
+
+// ---------------------------------------------------------------- multi-RHS solves
+// One CTA per (problem, block of RB right-hand sides).  X holds the right-hand
+// sides row-major (local DOF rows, ld columns) and is overwritten by the solution.
+template <typename T, int NB>
+__global__ void __launch_bounds__(256) k_band_solve_multi(const int *items, int n_items, const int *nloc,
+                                                          const int *bwv, const long long *band_off,
+                                                          const long long *dinv_off, const T *band, const T *dinv,
+                                                          T *Xbase, const long long *x_off, const int *x_ld) {
+  constexpr int RB = 32;
+  constexpr int CH = 32;  // panel rows staged per chunk
+  __shared__ T Ds[NB][NB];
+  __shared__ T Yb[NB][RB];
+  __shared__ T Ps[CH][NB];
+  __shared__ T red[8][NB][RB];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  int it = blockIdx.x;
+  if (it >= n_items) return;
+  int k = items[2 * it], r0 = items[2 * it + 1];
+  int N = nloc[k], bw = bwv[k];
+  int ld = x_ld[k];
+  int ncol = min(RB, ld - r0);
+  const T *B = band + band_off[k];
+  const T *Di = dinv + dinv_off[k];
+  T *X = Xbase + x_off[k] + r0;
+  const int RP = NB + bw;
+  const int np = (N + NB - 1) / NB;
+  bool colok = lane < ncol;
+  // forward: L y = x
+  for (int p = 0; p < np; ++p) {
+    int k0 = p * NB, nb = min(NB, N - k0);
+    for (int e = threadIdx.x; e < NB * NB; e += 256) Ds[e / NB][e % NB] = Di[(long long)p * NB * NB + e];
+    for (int q = wid; q < NB; q += 8) Yb[q][lane] = (q < nb && colok) ? X[(long long)(k0 + q) * ld + lane] : (T)0;
+    __syncthreads();
+    T y[NB / 8 + 1];
+    {
+      int qi = 0;
+      for (int q = wid; q < NB; q += 8, ++qi) {
+        T s = 0;
+        for (int cc = 0; cc <= q; ++cc) s += Ds[q][cc] * Yb[cc][lane];
+        y[qi] = s;
+      }
+    }
+    __syncthreads();
+    {
+      int qi = 0;
+      for (int q = wid; q < NB; q += 8, ++qi) {
+        Yb[q][lane] = y[qi];
+        if (q < nb && colok) X[(long long)(k0 + q) * ld + lane] = y[qi];
+      }
+    }
+    __syncthreads();
+    // window rows [k0+nb, min(N, k0+nb+bw)) -= Lpanel * Yb
+    T yb[NB];
+#pragma unroll
+    for (int cc = 0; cc < NB; ++cc) yb[cc] = Yb[cc][lane];
+    const T *Bp = B + (long long)p * RP * NB;
+    int rend = min(N - k0, RP);
+    for (int c0 = nb; c0 < rend; c0 += CH) {
+      int cn = min(CH, rend - c0);
+      for (int e = threadIdx.x; e < cn * NB; e += 256) Ps[e / NB][e % NB] = Bp[(long long)c0 * NB + e];
+      __syncthreads();
+      for (int r = wid; r < cn; r += 8) {
+        T s = 0;
+#pragma unroll
+        for (int cc = 0; cc < NB; ++cc) s += Ps[r][cc] * yb[cc];
+        if (colok) X[(long long)(k0 + c0 + r) * ld + lane] -= s;
+      }
+      __syncthreads();
+    }
+  }
+  // backward: L^T x = y
+  for (int p = np - 1; p >= 0; --p) {
+    int k0 = p * NB, nb = min(NB, N - k0);
+    for (int e = threadIdx.x; e < NB * NB; e += 256) Ds[e / NB][e % NB] = Di[(long long)p * NB * NB + e];
+    T acc[NB];
+#pragma unroll
+    for (int cc = 0; cc < NB; ++cc) acc[cc] = 0;
+    const T *Bp = B + (long long)p * RP * NB;
+    int rend = min(N - k0, RP);
+    for (int c0 = nb; c0 < rend; c0 += CH) {
+      int cn = min(CH, rend - c0);
+      __syncthreads();
+      for (int e = threadIdx.x; e < cn * NB; e += 256) Ps[e / NB][e % NB] = Bp[(long long)c0 * NB + e];
+      __syncthreads();
+      for (int r = wid; r < cn; r += 8) {
+        T xv = colok ? X[(long long)(k0 + c0 + r) * ld + lane] : (T)0;
+#pragma unroll
+        for (int cc = 0; cc < NB; ++cc) acc[cc] += Ps[r][cc] * xv;
+      }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int cc = 0; cc < NB; ++cc) red[wid][cc][lane] = acc[cc];
+    __syncthreads();
+    for (int q = wid; q < NB; q += 8) {
+      T s = 0;
+      for (int w = 0; w < 8; ++w) s += red[w][q][lane];
+      Yb[q][lane] = ((q < nb && colok) ? X[(long long)(k0 + q) * ld + lane] : (T)0) - s;
+    }
+    __syncthreads();
+    for (int q = wid; q < NB; q += 8) {
+      T s = 0;
+      for (int cc = q; cc < NB; ++cc) s += Ds[cc][q] * Yb[cc][lane];
+      if (q < nb && colok) X[(long long)(k0 + q) * ld + lane] = s;
+    }
+    __syncthreads();
+  }
+}
+
+// ---------------------------------------------------------------- single-RHS smoother solves
+// One CTA per problem: gather r into the local order, solve, add (or store) into z.
+template <typename T, int NB>
+__global__ void __launch_bounds__(256) k_band_solve_one(int count, const int *nloc, const int *bwv,
+                                                        const long long *band_off, const long long *dinv_off,
+                                                        const long long *node_off, const int *lnodes, const T *band,
+                                                        const T *dinv, const double *r, double *z, int atomic) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  T *v = reinterpret_cast<T *>(smraw);
+  __shared__ T Ds[NB][NB];
+  __shared__ T vb[NB];
+  __shared__ T red[8][NB];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  int k = blockIdx.x;
+  if (k >= count) return;
+  int N = nloc[k], bw = bwv[k];
+  if (N == 0) return;
+  const T *B = band + band_off[k];
+  const T *Di = dinv + dinv_off[k];
+  const int *ln = lnodes + node_off[k];
+  for (int l = threadIdx.x; l < N; l += 256) {
+    int o = l / 3, d = l - 3 * o;
+    v[l] = (T)r[3LL * ln[o] + d];
+  }
+  const int RP = NB + bw;
+  const int np = (N + NB - 1) / NB;
+  __syncthreads();
+  for (int p = 0; p < np; ++p) {
+    int k0 = p * NB, nb = min(NB, N - k0);
+    for (int e = threadIdx.x; e < NB * NB; e += 256) Ds[e / NB][e % NB] = Di[(long long)p * NB * NB + e];
+    __syncthreads();
+    if (threadIdx.x < NB) {
+      int q = threadIdx.x;
+      T s = 0;
+      for (int cc = 0; cc <= q && cc < nb; ++cc) s += Ds[q][cc] * v[k0 + cc];
+      vb[q] = (q < nb) ? s : (T)0;
+    }
+    __syncthreads();
+    if (threadIdx.x < nb) v[k0 + threadIdx.x] = vb[threadIdx.x];
+    const T *Bp = B + (long long)p * RP * NB;
+    int rend = min(N - k0, RP);
+    for (int rr = nb + threadIdx.x; rr < rend; rr += 256) {
+      const T *row = Bp + (long long)rr * NB;
+      T s = 0;
+#pragma unroll
+      for (int cc = 0; cc < NB; ++cc) s += row[cc] * vb[cc];
+      v[k0 + rr] -= s;
+    }
+    __syncthreads();
+  }
+  for (int p = np - 1; p >= 0; --p) {
+    int k0 = p * NB, nb = min(NB, N - k0);
+    for (int e = threadIdx.x; e < NB * NB; e += 256) Ds[e / NB][e % NB] = Di[(long long)p * NB * NB + e];
+    const T *Bp = B + (long long)p * RP * NB;
+    int rend = min(N - k0, RP);
+    // lanes over columns of the panel (NB <= 32), warps over rows
+    T acc = 0;
+    if (lane < NB)
+      for (int rr = nb + wid; rr < rend; rr += 8) acc += Bp[(long long)rr * NB + lane] * v[k0 + rr];
+    if (lane < NB) red[wid][lane] = acc;
+    __syncthreads();
+    if (threadIdx.x < NB) {
+      int q = threadIdx.x;
+      T s = 0;
+      for (int w = 0; w < 8; ++w) s += red[w][q];
+      vb[q] = (q < nb) ? v[k0 + q] - s : (T)0;
+    }
+    __syncthreads();
+    if (threadIdx.x < nb) {
+      int q = threadIdx.x;
+      T s = 0;
+      for (int cc = q; cc < nb; ++cc) s += Ds[cc][q] * vb[cc];
+      v[k0 + q] = s;
+    }
+    __syncthreads();
+  }
+  for (int l = threadIdx.x; l < N; l += 256) {
+    int o = l / 3, d = l - 3 * o;
+    long long slot = 3LL * ln[o] + d;
+    if (atomic)
+      atomicAdd(&z[slot], (double)v[l]);
+    else
+      z[slot] = (double)v[l];
+  }
+}
+
+template <typename T>
+T *band_ptr(LocalSet &S);
+template <>
+float *band_ptr<float>(LocalSet &S) { return S.band32.p; }
+template <>
+double *band_ptr<double>(LocalSet &S) { return S.band64.p; }
+template <typename T>
+T *dinv_ptr(LocalSet &S);
+template <>
+float *dinv_ptr<float>(LocalSet &S) { return S.dinv32.p; }
+template <>
+double *dinv_ptr<double>(LocalSet &S) { return S.dinv64.p; }
+
+}  // namespace
+
+int num_sms() {
+  static int n = 0;
+  if (!n) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    if (n <= 0) n = 1;
+  }
+  return n;
+}
+
+namespace {
+
+template <typename T>
+void layout_and_factor(hplmm_ctx *c, LocalSet &S) {
+  constexpr int NB = NBOf<T>::v;
+  cudaStream_t s = c->stream;
+  int K = S.count;
+  // band and inverse-block offsets for this precision
+  std::vector<long long> boff(K + 1, 0), doff(K + 1, 0);
+  int bwmax = 0;
+  for (int k = 0; k < K; ++k) {
+    int N = S.h_n[k], bw = S.h_bw[k];
+    long long np = (N + NB - 1) / NB;
+    boff[k + 1] = boff[k] + np * (NB + bw) * NB;
+    doff[k + 1] = doff[k] + np * NB * NB;
+    if (N > 0) bwmax = std::max(bwmax, bw);
+  }
+  size_t smem = (size_t)(NB + bwmax) * (NB + 16 / sizeof(T)) * sizeof(T);
+  HP_REQUIRE(smem <= 200 * 1024, HPLMM_ERR_INVALID,
+             "local problem half bandwidth " + std::to_string(bwmax) + " is too large; use smaller grain grids");
+  S.h_band_off = boff;
+  S.band_off.upload(boff, s);
+  S.dinv_off.upload(doff, s);
+  if (sizeof(T) == 8) {
+    S.band64.alloc(std::max<long long>(boff[K], 1));
+    S.band64.zero(s);
+    S.dinv64.alloc(std::max<long long>(doff[K], 1));
+  } else {
+    S.band32.alloc(std::max<long long>(boff[K], 1));
+    S.band32.zero(s);
+    S.dinv32.alloc(std::max<long long>(doff[K], 1));
+  }
+  T *band = band_ptr<T>(S);
+  T *dinv = dinv_ptr<T>(S);
+  k_local_extract<T><<<K, 128, 0, s>>>(S.box.p, S.node_off.p, S.n.p, S.bw.p, S.band_off.p, S.lmap.p, S.lnodes.p,
+                                       c->node_ijk.p, c->row_ptr.p, c->col.p, c->val64.p, c->fixed.p, band, NB);
+  HP_CHECK_LAUNCH();
+  Buf<int> queue;
+  queue.alloc(1);
+  queue.zero(s);
+  auto kern = k_band_chol<T, NB>;
+  HP_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  int grid = std::min(K, 2 * num_sms());
+  kern<<<grid, FACT_THREADS, smem, s>>>(S.order.p, K, queue.p, S.n.p, S.bw.p, S.band_off.p, S.dinv_off.p, band, dinv,
+                                        c->status.p);
+  HP_CHECK_LAUNCH();
+  HP_CUDA(cudaStreamSynchronize(s));
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------- set construction
+static void finish_set(hplmm_ctx *c, LocalSet &S, int kind, const std::vector<int> &hbox) {
+  cudaStream_t s = c->stream;
+  int K = S.count;
+  S.box.upload(hbox, s);
+  std::vector<long long> noff(K + 1, 0);
+  for (int k = 0; k < K; ++k)
+    noff[k + 1] = noff[k] + (long long)hbox[9 * k + 3] * hbox[9 * k + 4] * hbox[9 * k + 5];
+  S.h_node_off = noff;
+  S.node_total = noff[K];
+  S.node_off.upload(noff, s);
+  if (S.lmap.n < (size_t)std::max<long long>(noff[K], 1) || kind == 0) {
+    S.lmap.alloc(std::max<long long>(noff[K], 1));
+    S.lmap.zero(s);
+  }
+  S.lnodes.alloc(std::max<long long>(noff[K], 1));
+  S.n.alloc(std::max(K, 1));
+  S.bw.alloc(std::max(K, 1));
+  S.bw.zero(s);
+}
+
+static void enumerate_set(hplmm_ctx *c, LocalSet &S, int kind) {
+  cudaStream_t s = c->stream;
+  int K = S.count;
+  if (K == 0) return;
+  k_local_enum<<<K, 256, 0, s>>>(kind, S.box.p, S.node_off.p, S.lmap.p, S.lnodes.p, S.n.p, c->grid_to_node.p, c->nx,
+                                 c->ny, c->node_cls.p, c->fixed.p);
+  HP_CHECK_LAUNCH();
+  k_local_bw<<<K, 128, 0, s>>>(S.box.p, S.node_off.p, S.n.p, S.lmap.p, S.lnodes.p, c->node_ijk.p, c->row_ptr.p,
+                               c->col.p, S.bw.p);
+  HP_CHECK_LAUNCH();
+  S.h_n = S.n.download(s, K);
+  S.h_bw = S.bw.download(s, K);
+  std::vector<long long> voff(K + 1, 0);
+  for (int k = 0; k < K; ++k) voff[k + 1] = voff[k] + S.h_n[k];
+  S.h_vec_off = voff;
+  S.vec_total = voff[K];
+  S.vec_off.upload(voff, s);
+  std::vector<int> ord(K);
+  std::iota(ord.begin(), ord.end(), 0);
+  std::stable_sort(ord.begin(), ord.end(), [&](int a, int b) {
+    double ca = (double)S.h_n[a] * S.h_bw[a] * S.h_bw[a], cb = (double)S.h_n[b] * S.h_bw[b] * S.h_bw[b];
+    return ca > cb;
+  });
+  S.order.upload(ord, s);
+  HP_CUDA(cudaStreamSynchronize(s));
+}
+
+static std::vector<int> make_boxes(const std::vector<int> &bmin, const std::vector<int> &bmax, int K, int grow,
+                                   int nx, int ny, int nz) {
+  std::vector<int> hbox(9 * std::max(K, 1), 0);
+  int lim[3] = {nx, ny, nz};
+  for (int k = 0; k < K; ++k) {
+    int ext[3];
+    for (int a = 0; a < 3; ++a) {
+      int lo = bmin[3 * k + a], hi = bmax[3 * k + a];
+      if (lo > hi) {  // empty
+        lo = 0;
+        hi = -1;
+      } else {
+        lo = std::max(lo - grow, 0);
+        hi = std::min(hi + grow, lim[a]);
+      }
+      hbox[9 * k + a] = lo;
+      ext[a] = hi - lo + 1;
+      hbox[9 * k + 3 + a] = std::max(ext[a], 0);
+    }
+    int perm[3] = {0, 1, 2};
+    std::stable_sort(perm, perm + 3, [&](int a, int b) { return ext[a] < ext[b]; });
+    for (int a = 0; a < 3; ++a) hbox[9 * k + 6 + a] = perm[a];
+  }
+  return hbox;
+}
+
+void build_local_sets(hplmm_ctx *c) {
+  cudaStream_t s = c->stream;
+  int G = c->n_grains;
+  // grains
+  {
+    Buf<int> bmin, bmax;
+    bmin.alloc(3 * G);
+    bmax.alloc(3 * G);
+    bmin.fill_bytes(0x7f, s);
+    bmax.fill_bytes(0x80, s);
+    k_grain_bbox<<<grid_for(c->n_nodes, 256), 256, 0, s>>>(c->node_cls.p, c->node_ijk.p, c->n_nodes, bmin.p, bmax.p);
+    HP_CHECK_LAUNCH();
+    auto lo = bmin.download(s), hi = bmax.download(s);
+    c->grains.count = G;
+    auto hbox = make_boxes(lo, hi, G, 0, c->nx, c->ny, c->nz);
+    finish_set(c, c->grains, 0, hbox);
+    enumerate_set(c, c->grains, 0);
+  }
+  // contact grids
+  {
+    int C = c->n_ifaces;
+    c->contacts.count = C;
+    if (C > 0) {
+      Buf<int> bmin, bmax;
+      bmin.alloc(3 * C);
+      bmax.alloc(3 * C);
+      bmin.fill_bytes(0x7f, s);
+      bmax.fill_bytes(0x80, s);
+      k_iface_bbox<<<grid_for(c->n_iface_nodes, 256), 256, 0, s>>>(c->iface_nodes.p, c->iface_of_node.p,
+                                                                   c->n_iface_nodes, c->node_ijk.p, bmin.p, bmax.p);
+      HP_CHECK_LAUNCH();
+      auto lo = bmin.download(s), hi = bmax.download(s);
+      int w = c->opt.contact_halfwidth;
+      auto hbox = make_boxes(lo, hi, C, w, c->nx, c->ny, c->nz);
+      finish_set(c, c->contacts, 1, hbox);
+      c->contacts.lmap.zero(s);
+      k_contact_mark<<<grid_for(c->n_iface_nodes, 128), 128, 0, s>>>(c->iface_nodes.p, c->iface_of_node.p,
+                                                                     c->n_iface_nodes, c->node_ijk.p,
+                                                                     c->contacts.box.p, c->contacts.node_off.p, w,
+                                                                     c->contacts.lmap.p);
+      HP_CHECK_LAUNCH();
+      enumerate_set(c, c->contacts, 1);
+    }
+  }
+}
+
+void factor_local(hplmm_ctx *c, LocalSet &S, hplmm_prec prec) {
+  if (S.count == 0) return;
+  if (prec == HPLMM_FP64)
+    layout_and_factor<double>(c, S);
+  else
+    layout_and_factor<float>(c, S);
+  S.prec = prec;
+}
+
+template <typename T>
+static void solve_multi_t(hplmm_ctx *c, LocalSet &S, T *X, const Buf<long long> &x_off, const Buf<int> &x_ld,
+                          const std::vector<int> &h_ld) {
+  constexpr int NB = NBOf<T>::v;
+  cudaStream_t s = c->stream;
+  std::vector<int> items;
+  // largest problems first
+  auto ord = S.order.download(s, S.count);
+  for (int k : ord) {
+    if (S.h_n[k] == 0) continue;
+    for (int r0 = 0; r0 < h_ld[k]; r0 += 32) {
+      items.push_back(k);
+      items.push_back(r0);
+    }
+  }
+  int n_items = (int)items.size() / 2;
+  if (n_items == 0) return;
+  Buf<int> it;
+  it.upload(items, s);
+  k_band_solve_multi<T, NB><<<n_items, 256, 0, s>>>(it.p, n_items, S.n.p, S.bw.p, S.band_off.p, S.dinv_off.p,
+                                                    band_ptr<T>(S), dinv_ptr<T>(S), X, x_off.p, x_ld.p);
+  HP_CHECK_LAUNCH();
+  HP_CUDA(cudaStreamSynchronize(s));
+}
+
+void solve_local_multi_f64(hplmm_ctx *c, LocalSet &S, double *X, const Buf<long long> &x_off, const Buf<int> &x_ld,
+                           const std::vector<int> &h_ld) {
+  solve_multi_t<double>(c, S, X, x_off, x_ld, h_ld);
+}
+void solve_local_multi_f32(hplmm_ctx *c, LocalSet &S, float *X, const Buf<long long> &x_off, const Buf<int> &x_ld,
+                           const std::vector<int> &h_ld) {
+  solve_multi_t<float>(c, S, X, x_off, x_ld, h_ld);
+}
+
+void smoother_apply(hplmm_ctx *c, LocalSet &S, const double *r_pad, double *z_pad, bool atomic) {
+  if (S.count == 0) return;
+  cudaStream_t s = c->stream;
+  int nmax = 0;
+  for (int k = 0; k < S.count; ++k) nmax = std::max(nmax, S.h_n[k]);
+  if (S.prec == HPLMM_FP64) {
+    size_t smem = sizeof(double) * (size_t)std::max(nmax, 1);
+    auto kern = k_band_solve_one<double, 16>;
+    HP_REQUIRE(smem <= 200 * 1024, HPLMM_ERR_INVALID, "local problem too large for the FP64 smoother");
+    HP_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    kern<<<S.count, 256, smem, s>>>(S.count, S.n.p, S.bw.p, S.band_off.p, S.dinv_off.p, S.node_off.p, S.lnodes.p,
+                                    S.band64.p, S.dinv64.p, r_pad, z_pad, atomic ? 1 : 0);
+  } else {
+    size_t smem = sizeof(float) * (size_t)std::max(nmax, 1);
+    auto kern = k_band_solve_one<float, 32>;
+    HP_REQUIRE(smem <= 200 * 1024, HPLMM_ERR_INVALID, "local problem too large for the FP32 smoother");
+    HP_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    kern<<<S.count, 256, smem, s>>>(S.count, S.n.p, S.bw.p, S.band_off.p, S.dinv_off.p, S.node_off.p, S.lnodes.p,
+                                    S.band32.p, S.dinv32.p, r_pad, z_pad, atomic ? 1 : 0);
+  }
+  HP_CHECK_LAUNCH();
+}
+
+}  // namespace hp

@@ -1,0 +1,64 @@
+"""Shared helpers for the GPU parity tests: seeded workloads, oracle runs cached
+per process, and conversions between numpy and torch."""
+import functools
+
+import numpy as np
+
+import synth
+from oracle import fem, gmres, precond
+from oracle.decomposition import cartesian_partition
+
+# (workload, seed, options) -> small cases the oracle finishes in seconds, spanning several
+# grains, porous geometry, heterogeneous moduli and the edge cases of the method
+CASES = {
+    "cube16_n4": ("cube16", 0, dict(n_mortar=4, contact_halfwidth=1)),
+    "tiny8_n2": ("tiny8", 3, dict(n_mortar=2, contact_halfwidth=1)),
+    "tiny10_n1": ("tiny10", 5, dict(n_mortar=1, contact_halfwidth=1)),
+    "tiny10_strict": ("tiny10", 6, dict(n_mortar=3, contact_halfwidth=1, strict_two_grain=True)),
+    "porous32_n4": ("porous32", 1, dict(n_mortar=4, contact_halfwidth=2)),
+}
+
+
+def problem(name):
+    wl, seed, opt = CASES[name]
+    return synth.make_workload(wl, seed), opt
+
+
+@functools.lru_cache(maxsize=None)
+def oracle_case(name):
+    """(problem, options, oracle system, oracle preconditioner)."""
+    p, opt = problem(name)
+    o = precond.Options(n_mortar=opt["n_mortar"], contact_halfwidth=opt["contact_halfwidth"],
+                        strict_two_grain=opt.get("strict_two_grain", False))
+    sysm, M = precond.build(p, o)
+    return p, opt, sysm, M
+
+
+@functools.lru_cache(maxsize=None)
+def oracle_solution(name, tol=1e-11):
+    p, opt, sysm, M = oracle_case(name)
+    x, st = gmres.gmres(sysm.A, sysm.b, M.apply, tol=tol)
+    return x, st
+
+
+def rel(a, b):
+    a = np.asarray(a, dtype=np.float64)
+    b = np.asarray(b, dtype=np.float64)
+    d = np.linalg.norm(a - b)
+    n = np.linalg.norm(b)
+    return d / n if n > 0 else d
+
+
+def gpu_solver(name, **over):
+    import torch
+    import paper_2509_19777_gb300 as hp
+    p, opt = problem(name)
+    kw = dict(n_mortar=opt["n_mortar"], contact_halfwidth=opt["contact_halfwidth"],
+              strict_two_grain=opt.get("strict_two_grain", False))
+    kw.update(over)
+    s = hp.Solver(**kw)
+    mask, E = hp.problem_to_device(p)
+    s.assemble(mask, E, p.nu, p.bcs)
+    s.setup(grains=p.grains)
+    torch.cuda.synchronize()
+    return s

@@ -1,0 +1,179 @@
+"""GPU parity: every stage of the CUDA path, called through the C interface,
+against the FP64 CPU oracle on the same seeded inputs.
+
+Bars: integer maps and mortar choices bit-exact; FP64 values within the
+rounding of two different factorisations (relative 1e-10 on A^o, P_hat and
+M^{-1} r); FP64 solutions within relative 1e-8 of the oracle's; FP32 forms
+within the error stated per test, with the true FP64 residual always <= tol.
+"""
+import numpy as np
+import pytest
+
+from tests._cases import CASES, gpu_solver, oracle_case, oracle_solution, rel
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+SMALL = ["cube16_n4", "tiny8_n2", "tiny10_n1", "tiny10_strict"]
+
+
+def _t(x):
+    return torch.from_numpy(np.ascontiguousarray(x, dtype=np.float64)).cuda()
+
+
+def _n(t):
+    return t.detach().cpu().numpy()
+
+
+@pytest.fixture(scope="module", params=SMALL + ["porous32_n4"])
+def case(request):
+    name = request.param
+    p, opt, sysm, M = oracle_case(name)
+    s = gpu_solver(name)
+    yield name, p, sysm, M, s
+    s.close()
+
+
+def test_assembly_rhs_and_spmv(case):
+    name, p, sysm, M, s = case
+    assert s.n_dof == sysm.n_dof
+    assert rel(_n(s.b), sysm.b) < 1e-13
+    rng = np.random.default_rng(0)
+    x = rng.standard_normal(sysm.n_dof)
+    y = _n(s.spmv(_t(x)))
+    assert rel(y, sysm.A @ x) < 1e-13
+
+
+def test_maps_bit_exact(case):
+    name, p, sysm, M, s = case
+    mp = s.maps()
+    dec, mo = M.dec, M.mortars
+    assert np.array_equal(mp["node_ijk"], sysm.mesh.node_ijk)
+    assert np.array_equal(mp["W"], dec.W)
+    assert np.array_equal(mp["iface_pair"], dec.iface_pair)
+    off = mp["iface_offsets"]
+    assert len(off) == dec.n_interfaces + 1
+    for c in range(dec.n_interfaces):
+        assert np.array_equal(mp["iface_nodes"][off[c]:off[c + 1]], dec.iface_nodes[c])
+    moff = mp["mortar_offsets"]
+    for c in range(dec.n_interfaces):
+        assert np.array_equal(mp["mortar_nodes"][moff[c]:moff[c + 1]], mo.mortar_nodes[c]), f"interface {c}"
+    eta = np.concatenate([e.ravel() for e in mo.eta])
+    assert np.abs(mp["eta"] - eta).max() < 1e-14
+    sz = mp["sizes"]
+    assert sz["n_mortar_cols"] == mo.n_mortar_cols
+    assert sz["n_coarse"] == M.coarse.n_coarse
+
+
+def test_coarse_matrix(case):
+    name, p, sysm, M, s = case
+    A = _n(s.coarse_matrix())
+    Ao = M.coarse.A_o
+    assert A.shape == Ao.shape
+    assert np.abs(A - Ao).max() < 1e-10 * np.abs(Ao).max()
+
+
+def test_prolongation_columns(case):
+    name, p, sysm, M, s = case
+    P = M.coarse.P_hat.tocsc()
+    n = P.shape[1]
+    for col in sorted(set([0, 1, n // 3, n // 2, n - 1])):
+        ref = P[:, col].toarray().ravel()
+        got = _n(s.prolongation_column(col))
+        assert rel(got, ref) < 1e-10, f"column {col}"
+
+
+def test_apply_coarse_smoother_full(case):
+    name, p, sysm, M, s = case
+    rng = np.random.default_rng(1)
+    r = rng.standard_normal(sysm.n_dof)
+    rt = _t(r)
+    assert rel(_n(s.apply_coarse(rt)), M.M_G(r)) < 1e-10
+    assert rel(_n(s.apply_smoother(rt)), M.smoother.apply(r)) < 1e-10
+    assert rel(_n(s.apply(rt)), M.apply(r)) < 1e-10
+
+
+def test_first_pass_equals_oracle(case):
+    name, p, sysm, M, s = case
+    xa = _n(s.apply_coarse(s.b))
+    assert rel(xa, M.M_G(sysm.b)) < 1e-10
+
+
+def test_solve_fp64(case):
+    name, p, sysm, M, s = case
+    x_ref, st_ref = oracle_solution(name)
+    x, rc, st = s.solve(tol=1e-11)
+    assert rc == 0
+    xn = _n(x)
+    assert np.linalg.norm(sysm.b - sysm.A @ xn) / np.linalg.norm(sysm.b) <= 1e-11 * 1.001
+    assert rel(xn, x_ref) < 1e-8
+    # CGS2 FGMRES vs MGS GMRES: the same Krylov space, so iteration counts agree up to rounding
+    assert abs(st.iters - st_ref["iters"]) <= 2
+
+
+@pytest.mark.parametrize("name", ["cube16_n4", "porous32_n4"])
+@pytest.mark.parametrize("local,applyp", [("fp32", "fp32"), ("fp32", "fp64"), ("fp64", "fp32")])
+def test_mixed_precision_forms(name, local, applyp):
+    # FP32 local factors / basis / smoother and FP32 SpMV inside the apply: the outer FP64 FGMRES still
+    # reaches the FP64 residual; the apply differs from the FP64 oracle by FP32 rounding of local solves
+    p, opt, sysm, M = oracle_case(name)
+    s = gpu_solver(name, local_prec=local, apply_prec=applyp)
+    rng = np.random.default_rng(2)
+    r = rng.standard_normal(sysm.n_dof)
+    e_apply = rel(_n(s.apply(_t(r))), M.apply(r))
+    assert e_apply < 1e-3, e_apply
+    x, rc, st = s.solve(tol=1e-8)
+    xn = _n(x)
+    assert rc == 0
+    assert np.linalg.norm(sysm.b - sysm.A @ xn) / np.linalg.norm(sysm.b) <= 1e-8
+    x_ref, _ = oracle_solution(name)
+    assert rel(xn, x_ref) < 1e-6
+    s.close()
+
+
+def test_state_errors_and_arguments():
+    import paper_2509_19777_gb300 as hp
+    s = hp.Solver()
+    r = torch.zeros(3, dtype=torch.float64, device="cuda")
+    with pytest.raises(hp.HplmmError) as ei:
+        s.apply(r)
+    assert ei.value.code == hp.HPLMM_ERR_STATE
+    p, opt = __import__("tests._cases", fromlist=["problem"]).problem("tiny8_n2")
+    mask, E = hp.problem_to_device(p)
+    s.assemble(mask, E, p.nu, p.bcs)
+    with pytest.raises(hp.HplmmError) as ei:
+        s.setup(grains=(0, 1, 1))
+    assert ei.value.code == hp.HPLMM_ERR_INVALID
+    bad = torch.full(p.mask.shape, 99, dtype=torch.int32, device="cuda")
+    with pytest.raises(hp.HplmmError) as ei:
+        s.setup(partition=bad, n_grains=8)
+    assert ei.value.code == hp.HPLMM_ERR_INVALID
+    s.close()
+
+
+def test_explicit_partition_matches_oracle():
+    # a non-Cartesian partition (diagonal slabs) through the partition argument
+    import paper_2509_19777_gb300 as hp
+    from oracle import precond, gmres as og
+    from synth import make_workload
+    p = make_workload("tiny10", 9)
+    nz, ny, nx = p.mask.shape
+    k, j, i = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
+    part = ((i + j + 2 * k) // 7).astype(np.int32)
+    G = int(part.max()) + 1
+    from oracle import fem
+    sysm = fem.System(p.mask, p.E, p.nu, p.bcs)
+    M = precond.HPLMM(sysm, part, G, precond.Options(n_mortar=3, contact_halfwidth=1))
+    s = hp.Solver(n_mortar=3, contact_halfwidth=1)
+    mask, E = hp.problem_to_device(p)
+    s.assemble(mask, E, p.nu, p.bcs)
+    s.setup(partition=torch.from_numpy(part).cuda(), n_grains=G)
+    mp = s.maps()
+    assert np.array_equal(mp["W"], M.dec.W)
+    moff = mp["mortar_offsets"]
+    for c in range(M.dec.n_interfaces):
+        assert np.array_equal(mp["mortar_nodes"][moff[c]:moff[c + 1]], M.mortars.mortar_nodes[c])
+    rng = np.random.default_rng(4)
+    r = rng.standard_normal(sysm.n_dof)
+    assert rel(_n(s.apply(_t(r))), M.apply(r)) < 1e-10
+    s.close()
