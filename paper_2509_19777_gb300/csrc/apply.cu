@@ -101,12 +101,18 @@ void mdot(hplmm_ctx *c, const double *V, long long ldv, int nv, const double *w,
 }  // namespace
 
 void check_status(hplmm_ctx *c) {
-  int st = 0;
-  HP_CUDA(cudaMemcpyAsync(&st, c->status.p, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+  int w[4] = {0, 0, 0, 0};
+  HP_CUDA(cudaMemcpyAsync(w, c->status.p, sizeof(w), cudaMemcpyDeviceToHost, c->stream));
   HP_CUDA(cudaStreamSynchronize(c->stream));
+  int st = w[0];
   if (st != 0) {
     hplmm_status code = (hplmm_status)st;
-    if (code == HPLMM_ERR_SINGULAR) throw Error(code, "non-positive pivot in a Cholesky factorisation (singular local or coarse matrix)");
+    if (code == HPLMM_ERR_SINGULAR) {
+      static const char *where[] = {"?", "grain-grid", "contact-grid", "coarse"};
+      throw Error(code, std::string("non-positive pivot in the ") + where[(w[1] >= 1 && w[1] <= 3) ? w[1] : 0] +
+                            " Cholesky factorisation (problem " + std::to_string(w[2]) + ", row " +
+                            std::to_string(w[3]) + "): the matrix is singular or not positive definite");
+    }
     if (code == HPLMM_ERR_TIMEOUT) throw Error(code, "a device-side wait ran out of its budget");
     throw Error(HPLMM_ERR_CUDA, "device error word " + std::to_string(st));
   }

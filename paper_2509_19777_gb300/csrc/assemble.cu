@@ -352,9 +352,11 @@ void assemble(hplmm_ctx *c, const uint8_t *mask, int nx, int ny, int nz, const f
   HP_CHECK_LAUNCH();
 
   c->free_index.alloc(nslot);
-  k_not_fixed<<<grid_for(nslot, 256), 256, 0, s>>>(c->fixed.p, flag.p, nslot);
+  Buf<int> freeflag;
+  freeflag.alloc(nslot);
+  k_not_fixed<<<grid_for(nslot, 256), 256, 0, s>>>(c->fixed.p, freeflag.p, nslot);
   HP_CHECK_LAUNCH();
-  c->n_dof = exclusive_scan_i32(flag.p, c->free_index.p, nslot, s);
+  c->n_dof = exclusive_scan_i32(freeflag.p, c->free_index.p, nslot, s);
   c->dof_slot.alloc(c->n_dof);
   k_free_finalize<<<grid_for(nslot, 256), 256, 0, s>>>(c->fixed.p, c->free_index.p, c->dof_slot.p, nslot);
   HP_CHECK_LAUNCH();

@@ -254,7 +254,11 @@ __global__ void k_potrf_tile(double *A, long long N, int kt, double *Dinv, int *
     if (threadIdx.x == 0) {
       double d = L[c][c];
       if (!(d > 0.0)) {
-        atomicExch(status, (int)HPLMM_ERR_SINGULAR);
+        if (atomicCAS(status, 0, (int)HPLMM_ERR_SINGULAR) == 0) {
+          status[1] = 3;
+          status[2] = 0;
+          status[3] = k0 + c;
+        }
         d = 1.0;
       }
       L[c][c] = sqrt(d);

@@ -242,7 +242,7 @@ template <typename T, int NB>
 __global__ void __launch_bounds__(FACT_THREADS) k_band_chol(const int *order, int count, int *queue,
                                                            const int *nloc, const int *bwv,
                                                            const long long *band_off, const long long *dinv_off,
-                                                           T *band, T *dinv, int *status) {
+                                                           T *band, T *dinv, int *status, int where) {
   extern __shared__ __align__(16) unsigned char smraw[];
   constexpr int LD = NB + (16 / sizeof(T));  // padded row stride
   T *P = reinterpret_cast<T *>(smraw);
@@ -277,7 +277,11 @@ __global__ void __launch_bounds__(FACT_THREADS) k_band_chol(const int *order, in
           if (lane == 0) {
             T d = P[cc * LD + cc];
             if (!(d > (T)0)) {
-              atomicExch(status, (int)HPLMM_ERR_SINGULAR);
+              if (atomicCAS(status, 0, (int)HPLMM_ERR_SINGULAR) == 0) {
+                status[1] = where;
+                status[2] = k;
+                status[3] = k0 + cc;
+              }
               d = (T)1;
             }
             P[cc * LD + cc] = dev_sqrt<T>(d);
@@ -601,7 +605,7 @@ int num_sms() {
 namespace {
 
 template <typename T>
-void layout_and_factor(hplmm_ctx *c, LocalSet &S) {
+void layout_and_factor(hplmm_ctx *c, LocalSet &S, int where) {
   constexpr int NB = NBOf<T>::v;
   cudaStream_t s = c->stream;
   int K = S.count;
@@ -642,7 +646,7 @@ void layout_and_factor(hplmm_ctx *c, LocalSet &S) {
   HP_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   int grid = std::min(K, 2 * num_sms());
   kern<<<grid, FACT_THREADS, smem, s>>>(S.order.p, K, queue.p, S.n.p, S.bw.p, S.band_off.p, S.dinv_off.p, band, dinv,
-                                        c->status.p);
+                                        c->status.p, where);
   HP_CHECK_LAUNCH();
   HP_CUDA(cudaStreamSynchronize(s));
 }
@@ -771,10 +775,11 @@ void build_local_sets(hplmm_ctx *c) {
 
 void factor_local(hplmm_ctx *c, LocalSet &S, hplmm_prec prec) {
   if (S.count == 0) return;
+  int where = (&S == &c->grains) ? 1 : 2;
   if (prec == HPLMM_FP64)
-    layout_and_factor<double>(c, S);
+    layout_and_factor<double>(c, S, where);
   else
-    layout_and_factor<float>(c, S);
+    layout_and_factor<float>(c, S, where);
   S.prec = prec;
 }
 
