@@ -1,0 +1,449 @@
+#!/usr/bin/env python
+"""Benchmark: set-up + FGMRES time-to-solution at relative residual 1e-8 for
+algebraic hPLMM on one GB300, plain FP64 against the chosen mixed-precision
+form, on the 64^3 porous log-normal workload (4x4x4 grains of 16^3 voxels).
+
+One step = the whole hot path over one synthetic image: preconditioner set-up
+(maps, mortars, local factorisations, basis solves, Galerkin product, coarse
+Cholesky) and the right-preconditioned FGMRES solve to 1e-8, with the
+assembled system resident in HBM.  `e2e` repeats the step through the C
+interface from pinned host buffers (image upload, assembly, set-up, solve,
+solution download inside the timed region).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl hplmm|reference]
+
+Under torchrun each rank solves its own seeded replica (replicas only) and
+rank 0 prints one JSON line with the maximum time over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "setup+GMRES time-to-solution at rel. residual 1e-8, plain FP64 vs chosen form"
+WORKLOAD = "porous64"
+TOL = 1e-8
+CHOSEN = dict(local_prec="fp32", apply_prec="fp32")
+PLAIN = dict(local_prec="fp64", apply_prec="fp64")
+METHOD = dict(n_mortar=4, contact_halfwidth=2, n_st=1, restart=30, max_iters=300)
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="hplmm", choices=["hplmm", "reference"])
+    ap.add_argument("--seed", type=int, default=0)
+    ap.add_argument("--no-plain", action="store_true", help="skip the plain FP64 comparison run")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    return ap.parse_args()
+
+
+# ------------------------------------------------------------------ distributed plumbing
+def dist_init(n):
+    import torch
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        if torch.cuda.is_available():
+            torch.cuda.set_device(local)
+        dist.init_process_group(backend=backend)
+    return rank, world, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def reduce_max(x, world):
+    if world <= 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda" if torch.cuda.is_available() else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ------------------------------------------------------------------ clocks during the timed region
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except (FileNotFoundError, OSError):
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax = float(parts[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": smax, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ------------------------------------------------------------------ the GPU arm
+def run_form(hp, problem, form, steps, warmup, flush, stream, profile=False):
+    """Time `steps` set-up + solve steps of one form; returns per-step ms and the last stats."""
+    import torch
+    s = hp.Solver(**METHOD, **form, profile=profile, stream=stream)
+    mask, E = hp.problem_to_device(problem)
+    s.assemble(mask, E, problem.nu, problem.bcs)
+    x = torch.empty(s.n_dof, dtype=torch.float64, device="cuda")
+    times, st = [], None
+    launches0 = None
+    for it in range(warmup + steps):
+        if it == warmup:
+            if profile:
+                s.reset_profile()
+            launches0 = hp.hplmm_kernel_launches()
+        flush.zero_()  # evict L2 between steps (outside the timed window)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        s.setup(grains=problem.grains)
+        _, rc, st = s.solve(None, x, TOL)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        if rc != 0 or st.rel_res_true > TOL:
+            raise RuntimeError(f"solve did not reach {TOL}: rc={rc} rel={st.rel_res_true}")
+        if it >= warmup:
+            times.append(e0.elapsed_time(e1))
+    launches = hp.hplmm_kernel_launches() - launches0
+    prof = s.profile() if profile else None
+    costs = s.costs()
+    sizes = s.sizes()
+    return s, x, times, st, prof, costs, sizes, launches
+
+
+def run_e2e(hp, problem, form, steps, warmup, flush, stream):
+    """The same step through the C interface from pinned host buffers, copies inside the timed region."""
+    import numpy as np
+    import torch
+    s = hp.Solver(**METHOD, **form, stream=stream)
+    mask_h = torch.from_numpy(np.ascontiguousarray(problem.mask.astype(np.uint8))).pin_memory()
+    E_h = torch.from_numpy(np.ascontiguousarray(problem.E.astype(np.float32))).pin_memory()
+    mask_d = torch.empty_like(mask_h, device="cuda")
+    E_d = torch.empty_like(E_h, device="cuda")
+    times = []
+    x_h = None
+    bcs = hp.make_bcs(problem.bcs)
+    for it in range(warmup + steps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        with torch.cuda.stream(stream):
+            mask_d.copy_(mask_h, non_blocking=True)
+            E_d.copy_(E_h, non_blocking=True)
+        n = hp.hplmm_assemble(s.ctx, mask_d, E_d, problem.nu, bcs)
+        s.n_dof = n
+        s.setup(grains=problem.grains)
+        x, rc, st = s.solve(None, None, TOL)
+        if x_h is None:
+            x_h = torch.empty(n, dtype=torch.float64).pin_memory()
+        with torch.cuda.stream(stream):
+            x_h.copy_(x, non_blocking=True)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        if rc != 0:
+            raise RuntimeError("e2e solve did not converge")
+        if it >= warmup:
+            times.append(e0.elapsed_time(e1))
+    h2d = mask_h.numel() * mask_h.element_size() + E_h.numel() * E_h.element_size()
+    d2h = x_h.numel() * 8
+    s.close()
+    return times, h2d, d2h
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2509_19777_gb300", "csrc")
+    for f in sorted(os.listdir(csrc)):
+        if f.endswith((".cu", ".cuh")):
+            h.update(open(os.path.join(csrc, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        d = json.load(open(path))
+        return d.get("hbm_gbs", 6800.0), d.get("sm_max_mhz", 2070.0), "measured"
+    return 6800.0, 2070.0, "fallback"
+
+
+def roofline(prof, costs, sizes, steps, problem_nodes, clock_mhz):
+    """Roofline of the dominant phase of the timed steps (algorithmic units / measured phase time)."""
+    hbm, smax, src = measured_peaks()
+    # FP32 CUDA-core peak from unit counts: 152 SMs x 128 FP32 lanes x 2 flops x clock
+    alu_peak = 152 * 128 * 2 * (smax * 1e6) / 1e12
+    eb = costs["local_elem_bytes"]
+    cand = {}
+    for ph, (ms, launches) in prof.items():
+        if ms <= 0:
+            continue
+        cand[ph] = (ms, launches)
+    dom = max(cand, key=lambda k: cand[k][0])
+    ms, launches = cand[dom]
+    per_step_ms = ms / steps
+    per_launch_ms = ms / max(launches, 1)
+    launches_per_step = launches / steps
+    out = {"kernel_phase": dom, "ms_per_step": per_step_ms, "launches_per_step": launches_per_step}
+    if dom == "factor_grains":
+        work = costs["grain_chol_flops"]
+        out.update(bound="alu", achieved=work / (per_step_ms * 1e-3) / 1e12, peak=alu_peak, unit="TFLOP/s")
+    elif dom == "factor_contacts":
+        work = costs["contact_chol_flops"]
+        out.update(bound="alu", achieved=work / (per_step_ms * 1e-3) / 1e12, peak=alu_peak, unit="TFLOP/s")
+    elif dom == "basis_solve":
+        work = costs["basis_solve_flops"]
+        out.update(bound="alu", achieved=work / (per_step_ms * 1e-3) / 1e12, peak=alu_peak, unit="TFLOP/s")
+    elif dom in ("apply_grains", "apply_contacts"):
+        elems = costs["grain_band_elems"] if dom == "apply_grains" else costs["contact_band_elems"]
+        dofs = costs["grain_dofs"] if dom == "apply_grains" else costs["contact_dofs"]
+        # per launch: the factor is read twice (forward and backward sweep), plus gather/scatter of vectors
+        bytes_per_launch = 2 * elems * eb + dofs * (8 + 8 + 4)
+        out.update(bound="hbm", achieved=bytes_per_launch / (per_launch_ms * 1e-3) / 1e9, peak=hbm, unit="GB/s")
+    elif dom == "spmv":
+        bytes_per_launch = costs["nnzb"] * (9 * 4 + 4) + problem_nodes * 3 * 8 * 3
+        out.update(bound="hbm", achieved=bytes_per_launch / (per_launch_ms * 1e-3) / 1e9, peak=hbm, unit="GB/s")
+    else:
+        out.update(bound="hbm", achieved=None, peak=hbm, unit="GB/s")
+    out["frac"] = (out["achieved"] / out["peak"]) if out.get("achieved") else None
+    out["peak_source"] = src
+    return out
+
+
+def traffic_for(phase):
+    """DRAM bytes per launch of the phase's kernel from the committed ncu summary, if still current."""
+    path = os.path.join(ROOT, "profiles", "dram_traffic.json")
+    if not os.path.exists(path):
+        return None
+    try:
+        d = json.load(open(path))
+    except (OSError, ValueError):
+        return None
+    ent = d.get(phase)
+    if not ent or ent.get("kernel_source_hash") != kernel_source_hash():
+        return None
+    return ent.get("dram_bytes_per_launch_full_workload")
+
+
+# ------------------------------------------------------------------ the CPU oracle sample
+def oracle_sample(seed):
+    """Time the CPU oracle on a bounded sample of the workload.
+
+    Sample: the 32x32x16 corner (x, y, z) of the 64^3 image -- 4 of its 64 grains at the same 16^3 grain
+    size, re-filtered to the solid component touching z=0 -- with the oracle's full set-up and its
+    GMRES(30) to 1e-8, single-threaded."""
+    import synth
+    from oracle import gmres as og
+    from oracle import precond
+    from synth.voxels import _largest_component_touching_bottom
+    p = synth.make_workload(WORKLOAD, seed)
+    sub = _largest_component_touching_bottom(p.mask[:16, :32, :32].astype(bool))
+    q = synth.Problem("porous64_corner", sub, p.E[:16, :32, :32].copy(), p.nu, (2, 2, 1), p.bcs, 4, seed)
+    t0 = time.perf_counter()
+    sysm, M = precond.build(q, precond.Options(n_mortar=4, contact_halfwidth=2))
+    t1 = time.perf_counter()
+    x, st = og.gmres(sysm.A, sysm.b, M.apply, tol=TOL)
+    t2 = time.perf_counter()
+    return {"setup_s": t1 - t0, "solve_s": t2 - t1, "iters": st["iters"], "grains": 4, "n_dof": sysm.n_dof}
+
+
+def cpu_baseline_json(sample, full_grains, full_iters):
+    """Extrapolate the sample to the full image: set-up scales with the grain count; the solve with the
+    grain count times the iteration ratio (the GPU run's count on the full image, when known)."""
+    scale = full_grains / sample["grains"]
+    its_ratio = (full_iters / sample["iters"]) if (full_iters and sample["iters"]) else 1.0
+    value = sample["setup_s"] * scale + sample["solve_s"] * scale * its_ratio
+    return {"value": value, "unit": "s", "cores": 1, "kind": "oracle",
+            "sample": (f"oracle (numpy/scipy, 1 thread) set-up + GMRES(30) to 1e-8 on the 32x32x16 corner of the "
+                       f"64^3 image ({sample['n_dof']} DOF, 4 of the 64 grains): set-up {sample['setup_s']:.2f} s, "
+                       f"solve {sample['solve_s']:.2f} s in {sample['iters']} its; extrapolated x{scale:.0f} grains "
+                       f"and x{its_ratio:.2f} iterations to the full image")}
+
+
+def _oracle_subprocess(seed):
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    code = ("import json,sys; sys.path.insert(0, %r); import bench; "
+            "print(json.dumps(bench.oracle_sample(%d)))") % (ROOT, seed)
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, timeout=900)
+    if r.returncode != 0:
+        raise RuntimeError(r.stderr[-2000:])
+    return json.loads(r.stdout.strip().splitlines()[-1])
+
+
+def reference_arm(args, rank, world):
+    if rank != 0:
+        return
+    t0 = time.perf_counter()
+    times = []
+    sample = None
+    for it in range(args.warmup + args.steps):
+        ts = time.perf_counter()
+        sample = _oracle_subprocess(args.seed)
+        te = time.perf_counter()
+        if it >= args.warmup:
+            times.append(te - ts)
+    cb = cpu_baseline_json(sample, 64, None)
+    line = {"impl": "reference", "metric": METRIC, "value": cb["value"], "unit": "s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * cb["value"],
+            "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "grains": [4, 4, 4], "n_mortar": 4, "contact_halfwidth": 2,
+                       "tol": TOL, "l2": "n/a (CPU)"},
+            "cpu_baseline": cb,
+            "e2e": {"value": cb["value"], "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+            "sample_wall_s": statistics.mean(times)}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    rank, world, local = dist_init(args.gpus)
+    if args.impl == "reference":
+        reference_arm(args, rank, world)
+        return
+    import numpy as np
+    import torch
+    import paper_2509_19777_gb300 as hp
+    import synth
+    from paper_2509_19777_gb300.build import build_library
+    build_library()
+    torch.cuda.set_device(local)
+    stream = torch.cuda.current_stream()
+    problem = synth.make_workload(WORKLOAD, args.seed + rank)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")   # 256 MiB > 129 MB L2
+
+    # plain FP64 form (comparison)
+    plain = None
+    if not args.no_plain:
+        sp, xp, tp, stp, _, _, _, _ = run_form(hp, problem, PLAIN, max(1, min(args.steps, 3)), 1, flush, stream)
+        plain = {"value": statistics.mean(tp) / 1e3, "iters": stp.iters, "rel_res": stp.rel_res_true,
+                 "t_setup_ml": stp.t_setup_ml, "t_setup_mg": stp.t_setup_mg, "t_solve": stp.t_solve}
+        xp_h = xp.cpu().numpy()
+        sp.close()
+
+    # chosen form: timed steps with clocks sampled, then the same steps with phase profiling
+    barrier(world)
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        sc, xc, tc, stc, _, costs, sizes, launches = run_form(hp, problem, CHOSEN, args.steps, args.warmup, flush,
+                                                              stream)
+    barrier(world)
+    torch.cuda.synchronize()
+    ms_step = statistics.mean(tc)
+    ms_step_max = reduce_max(ms_step, world)
+    xc_h = xc.cpu().numpy()
+    sc.close()
+    # profiled repetition (events around every phase) for the per-phase breakdown and roofline
+    sq, _, tq, _, prof, costs, sizes, _ = run_form(hp, problem, CHOSEN, args.steps, 1, flush, stream, profile=True)
+    sq.close()
+    # end to end through the C interface from host buffers
+    te2e, h2d, d2h = run_e2e(hp, problem, CHOSEN, args.steps, max(1, args.warmup), flush, stream)
+    e2e_ms = reduce_max(statistics.mean(te2e), world)
+
+    clocks = clk.summary()
+    rf = roofline(prof, costs, sizes, args.steps, sizes["n_nodes"], clocks.get("sm_mhz"))
+    rf["traffic"] = traffic_for(rf["kernel_phase"])
+    line = {
+        "metric": METRIC,
+        "value": ms_step_max / 1e3,
+        "unit": "s",
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": ms_step_max,
+        "higher_is_better": False,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32+f64",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "image": [64, 64, 64], "porosity": 0.3, "grains": [4, 4, 4],
+                   "n_mortar": 4, "contact_halfwidth": 2, "tol": TOL, "n_dof": sizes["n_dof"],
+                   "n_coarse": sizes["n_coarse"], "n_interfaces": sizes["n_interfaces"],
+                   "form": "FP32 local factors/basis/smoother/SpMV in the apply, FP64 coarse Cholesky and FGMRES",
+                   "l2": "flushed (256 MiB write) before every step", "parallelism": "replicas"},
+        "iters": stc.iters,
+        "rel_res_true": stc.rel_res_true,
+        "phases_s": {"t_setup_ml": stc.t_setup_ml, "t_setup_mg": stc.t_setup_mg, "t_solve": stc.t_solve},
+        "profile_ms_per_step": {k: v[0] / args.steps for k, v in prof.items()},
+        "plain_fp64": plain,
+        "speedup_vs_plain_fp64": (plain["value"] / (ms_step_max / 1e3)) if plain else None,
+        "rel_diff_vs_plain_fp64": (float(np.linalg.norm(xc_h - xp_h) / np.linalg.norm(xp_h)) if plain else None),
+        "roofline": rf,
+        "e2e": {"value": e2e_ms / 1e3, "unit": "s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "gpu_launches": launches // max(1, args.steps) * args.steps,
+        "gpu_launches_per_step": launches / max(1, args.steps),
+        "clocks": clocks,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu:
+        try:
+            sample = _oracle_subprocess(args.seed)
+            line["cpu_baseline"] = cpu_baseline_json(sample, 64, stc.iters)
+        except Exception as e:  # the baseline is reported, never required
+            line["cpu_baseline"] = {"value": None, "error": str(e)[-300:]}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+if __name__ == "__main__":
+    main()

@@ -63,6 +63,7 @@ typedef struct {
                             literal Eq. col_pk); 0 (default): on every grain whose voxels touch it */
   int use_graph;         /* 1: replay the preconditioner apply as a captured CUDA graph */
   int verbose;           /* 1: print phase timings to stderr */
+  int profile;           /* 1: time every phase with CUDA events on the context's stream (hplmm_get_profile) */
 } hplmm_options;
 
 /* Boundary conditions on the six faces of the image box, in the order
@@ -180,6 +181,47 @@ hplmm_status hplmm_get_coarse_matrix(hplmm_ctx *ctx, double *A_o);
 
 /* Copy column `col` of P_hat in the free-DOF numbering (DEVICE float64 [n_dof]). */
 hplmm_status hplmm_get_prolongation_column(hplmm_ctx *ctx, long long col, double *out);
+
+/* Phases timed when options.profile = 1 (CUDA events around each phase's launches). */
+typedef enum {
+  HPLMM_PH_MAPS = 0,          /* grain/interface maps and mortars (Sections 3.1-3.3) */
+  HPLMM_PH_FACTOR_GRAINS,     /* banded Cholesky of the grain blocks A^g_g */
+  HPLMM_PH_FACTOR_CONTACTS,   /* banded Cholesky of the contact-grid blocks */
+  HPLMM_PH_BASIS_RHS,         /* right-hand sides of Eqs. col_pk and col_cg */
+  HPLMM_PH_BASIS_SOLVE,       /* batched multi-RHS local solves building P */
+  HPLMM_PH_GALERKIN,          /* A^o = P_hat^T A_hat P_hat */
+  HPLMM_PH_COARSE_CHOL,       /* FP64 Cholesky of A^o */
+  HPLMM_PH_APPLY_COARSE,      /* M_G^{-1}: restriction, coarse solve, prolongation */
+  HPLMM_PH_APPLY_CONTACTS,    /* M_zeta^{-1}: contact-grid solves */
+  HPLMM_PH_APPLY_GRAINS,      /* M_g^{-1}: grain-grid solves */
+  HPLMM_PH_SPMV,              /* every A_hat x product */
+  HPLMM_PH_KRYLOV,            /* FGMRES vector work (CGS2 products, updates) */
+  HPLMM_PH_COUNT
+} hplmm_phase;
+
+/* Cumulative milliseconds and kernel launches per phase since the last reset
+ * (arrays of n >= HPLMM_PH_COUNT entries, HOST).  Requires options.profile. */
+hplmm_status hplmm_get_profile(hplmm_ctx *ctx, double *ms, long long *launches, int n);
+hplmm_status hplmm_reset_profile(hplmm_ctx *ctx);
+
+/* Process-wide number of CUDA kernels this library has launched. */
+long long hplmm_kernel_launches(void);
+
+/* Algorithmic sizes of the current set-up, for roofline accounting (HOST output). */
+typedef struct {
+  long long nnzb;                 /* 3x3 blocks of A_hat */
+  long long grain_band_elems;     /* stored factor elements of all grain blocks */
+  long long contact_band_elems;   /* stored factor elements of all contact-grid blocks */
+  double grain_chol_flops;        /* sum N b^2 over grain blocks (banded Cholesky) */
+  double contact_chol_flops;      /* sum N b^2 over contact-grid blocks */
+  double basis_solve_flops;       /* sum 4 N b k over grains (forward + backward, k right-hand sides) */
+  long long grain_dofs;           /* sum of local DOFs of the grain blocks */
+  long long contact_dofs;         /* sum of local DOFs of the contact-grid blocks */
+  long long panel_elems;          /* stored basis-panel elements sum N_g k_g */
+  int local_elem_bytes;           /* bytes per stored local factor / panel element */
+} hplmm_costs;
+
+hplmm_status hplmm_get_costs(hplmm_ctx *ctx, hplmm_costs *out);
 
 /* Message of the most recent error in this context (never NULL). */
 const char *hplmm_last_error(const hplmm_ctx *ctx);

@@ -35,16 +35,18 @@ PREC = {"fp64": HPLMM_FP64, "fp32": HPLMM_FP32, "bf16": HPLMM_BF16}
 EXPORTED = [
     "hplmm_default_options", "hplmm_create", "hplmm_assemble", "hplmm_setup", "hplmm_apply",
     "hplmm_apply_coarse", "hplmm_apply_smoother", "hplmm_spmv", "hplmm_solve", "hplmm_get_sizes",
-    "hplmm_get_maps", "hplmm_get_coarse_matrix", "hplmm_get_prolongation_column", "hplmm_last_error",
-    "hplmm_destroy",
+    "hplmm_get_maps", "hplmm_get_coarse_matrix", "hplmm_get_prolongation_column", "hplmm_get_profile",
+    "hplmm_reset_profile", "hplmm_kernel_launches", "hplmm_get_costs", "hplmm_last_error", "hplmm_destroy",
 ]
+PHASES = ["maps", "factor_grains", "factor_contacts", "basis_rhs", "basis_solve", "galerkin", "coarse_chol",
+          "apply_coarse", "apply_contacts", "apply_grains", "spmv", "krylov"]
 
 
 class hplmm_options(ctypes.Structure):
     _fields_ = [("n_mortar", ctypes.c_int), ("beta", ctypes.c_double), ("contact_halfwidth", ctypes.c_int),
                 ("n_st", ctypes.c_int), ("local_prec", ctypes.c_int), ("apply_prec", ctypes.c_int),
                 ("restart", ctypes.c_int), ("max_iters", ctypes.c_int), ("strict_two_grain", ctypes.c_int),
-                ("use_graph", ctypes.c_int), ("verbose", ctypes.c_int)]
+                ("use_graph", ctypes.c_int), ("verbose", ctypes.c_int), ("profile", ctypes.c_int)]
 
 
 class hplmm_bcs(ctypes.Structure):
@@ -62,6 +64,14 @@ class hplmm_stats(ctypes.Structure):
 class hplmm_sizes(ctypes.Structure):
     _fields_ = [(n, ctypes.c_longlong) for n in ("n_nodes", "n_dof", "n_grains", "n_interfaces", "n_iface_nodes",
                                                    "n_mortars", "n_mortar_cols", "n_coarse")]
+
+
+class hplmm_costs(ctypes.Structure):
+    _fields_ = [("nnzb", ctypes.c_longlong), ("grain_band_elems", ctypes.c_longlong),
+                ("contact_band_elems", ctypes.c_longlong), ("grain_chol_flops", ctypes.c_double),
+                ("contact_chol_flops", ctypes.c_double), ("basis_solve_flops", ctypes.c_double),
+                ("grain_dofs", ctypes.c_longlong), ("contact_dofs", ctypes.c_longlong),
+                ("panel_elems", ctypes.c_longlong), ("local_elem_bytes", ctypes.c_int)]
 
 
 _lib = None
@@ -91,6 +101,10 @@ def load_library():
         "hplmm_get_maps": (I, [P, P, P, P, P, P, P, P, P]),
         "hplmm_get_coarse_matrix": (I, [P, P]),
         "hplmm_get_prolongation_column": (I, [P, LL, P]),
+        "hplmm_get_profile": (I, [P, P, P, I]),
+        "hplmm_reset_profile": (I, [P]),
+        "hplmm_kernel_launches": (LL, []),
+        "hplmm_get_costs": (I, [P, ctypes.POINTER(hplmm_costs)]),
         "hplmm_last_error": (ctypes.c_char_p, [P]),
         "hplmm_destroy": (None, [P]),
     }
@@ -246,6 +260,30 @@ def hplmm_get_prolongation_column(ctx, col, out):
     _check(ctx, load_library().hplmm_get_prolongation_column(ctx, int(col), _ptr(out)))
 
 
+def hplmm_get_profile(ctx):
+    """{phase: (milliseconds, kernel launches)} accumulated since the last reset."""
+    n = len(PHASES)
+    ms = (ctypes.c_double * n)()
+    ln = (ctypes.c_longlong * n)()
+    _check(ctx, load_library().hplmm_get_profile(ctx, ctypes.cast(ms, ctypes.c_void_p),
+                                                 ctypes.cast(ln, ctypes.c_void_p), n))
+    return {PHASES[i]: (ms[i], ln[i]) for i in range(n)}
+
+
+def hplmm_reset_profile(ctx):
+    _check(ctx, load_library().hplmm_reset_profile(ctx))
+
+
+def hplmm_kernel_launches():
+    return int(load_library().hplmm_kernel_launches())
+
+
+def hplmm_get_costs(ctx):
+    c = hplmm_costs()
+    _check(ctx, load_library().hplmm_get_costs(ctx, ctypes.byref(c)))
+    return {n: getattr(c, n) for n, _ in hplmm_costs._fields_}
+
+
 def hplmm_last_error(ctx):
     return load_library().hplmm_last_error(ctx).decode()
 
@@ -260,12 +298,14 @@ class Solver:
     """One library context: assemble -> setup -> apply / solve, on torch CUDA tensors."""
 
     def __init__(self, n_mortar=4, beta=4.0, contact_halfwidth=2, n_st=1, local_prec="fp64", apply_prec="fp64",
-                 restart=30, max_iters=300, strict_two_grain=False, use_graph=False, verbose=False, stream=None):
+                 restart=30, max_iters=300, strict_two_grain=False, use_graph=False, verbose=False, profile=False,
+                 stream=None):
         o = hplmm_default_options()
         o.n_mortar, o.beta, o.contact_halfwidth, o.n_st = n_mortar, beta, contact_halfwidth, n_st
         o.local_prec, o.apply_prec = PREC[local_prec], PREC[apply_prec]
         o.restart, o.max_iters = restart, max_iters
         o.strict_two_grain, o.use_graph, o.verbose = int(strict_two_grain), int(use_graph), int(verbose)
+        o.profile = int(profile)
         self.options = o
         self.ctx = hplmm_create(o, stream)
         self.n_dof = 0
@@ -329,6 +369,15 @@ class Solver:
 
     def coarse_matrix(self):
         return hplmm_get_coarse_matrix(self.ctx)
+
+    def profile(self):
+        return hplmm_get_profile(self.ctx)
+
+    def reset_profile(self):
+        hplmm_reset_profile(self.ctx)
+
+    def costs(self):
+        return hplmm_get_costs(self.ctx)
 
     def prolongation_column(self, col, out=None):
         import torch

@@ -92,6 +92,7 @@ __global__ void k_mcombine(double *x, const double *Z, long long ldz, int nv, co
 }
 
 void mdot(hplmm_ctx *c, const double *V, long long ldv, int nv, const double *w, long long n, double *out) {
+  ProfScope ps(c, HPLMM_PH_KRYLOV);
   k_mdot<<<MDOT_BLOCKS, 256, 0, c->stream>>>(V, ldv, nv, w, n, c->w_partial.p);
   HP_CHECK_LAUNCH();
   k_mdot_final<<<1, MAXV, 0, c->stream>>>(c->w_partial.p, MDOT_BLOCKS, nv, out);
@@ -202,11 +203,17 @@ int fgmres(hplmm_ctx *c, const double *b_pad, double *x_pad, double tol, hplmm_s
       ++its;
       // CGS2
       mdot(c, V, L, j + 1, w, L, dev_h);
-      k_mupdate<<<MDOT_BLOCKS, 256, 0, s>>>(w, V, L, j + 1, dev_h, L);
-      HP_CHECK_LAUNCH();
+      {
+        ProfScope ps(c, HPLMM_PH_KRYLOV);
+        k_mupdate<<<MDOT_BLOCKS, 256, 0, s>>>(w, V, L, j + 1, dev_h, L);
+        HP_CHECK_LAUNCH();
+      }
       mdot(c, V, L, j + 1, w, L, dev_h + MAXV);
-      k_mupdate<<<MDOT_BLOCKS, 256, 0, s>>>(w, V, L, j + 1, dev_h + MAXV, L);
-      HP_CHECK_LAUNCH();
+      {
+        ProfScope ps(c, HPLMM_PH_KRYLOV);
+        k_mupdate<<<MDOT_BLOCKS, 256, 0, s>>>(w, V, L, j + 1, dev_h + MAXV, L);
+        HP_CHECK_LAUNCH();
+      }
       mdot(c, w, 0, 1, w, L, dev_h + 2 * MAXV);
       HP_CUDA(cudaMemcpyAsync(hh.data(), dev_h, sizeof(double) * (2 * MAXV + 1), cudaMemcpyDeviceToHost, s));
       HP_CUDA(cudaStreamSynchronize(s));

@@ -377,6 +377,7 @@ void scatter_free(hplmm_ctx *c, const double *dof, double *pad) {
 }
 
 void spmv(hplmm_ctx *c, const double *x_pad, double *y_pad, hplmm_prec prec, const double *sub) {
+  ProfScope ps(c, HPLMM_PH_SPMV);
   if (prec == HPLMM_FP64) {
     k_spmv<double><<<grid_for(c->n_nodes, 128), 128, 0, c->stream>>>(c->row_ptr.p, c->col.p, c->val64.p, x_pad,
                                                                       y_pad, sub, c->n_nodes);

@@ -3,10 +3,42 @@
 // and the padded [n_nodes][3] layout used internally.
 #include "common.cuh"
 
+#include <atomic>
 #include <chrono>
 #include <cstring>
 
 using hp::Error;
+
+namespace hp {
+static std::atomic<long long> g_launches{0};
+long long note_launch() { return ++g_launches; }
+long long launch_count() { return g_launches.load(); }
+
+cudaEvent_t prof_event(hplmm_ctx *c) {
+  if (!c->ev_pool.empty()) {
+    cudaEvent_t e = c->ev_pool.back();
+    c->ev_pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  HP_CUDA(cudaEventCreate(&e));
+  return e;
+}
+
+void prof_harvest(hplmm_ctx *c) {
+  if (c->prof_pending.empty()) return;
+  HP_CUDA(cudaEventSynchronize(c->prof_pending.back().e1));
+  for (auto &r : c->prof_pending) {
+    float ms = 0.f;
+    HP_CUDA(cudaEventElapsedTime(&ms, r.e0, r.e1));
+    c->prof_ms[r.ph] += ms;
+    c->prof_launches[r.ph] += r.launches;
+    c->ev_pool.push_back(r.e0);
+    c->ev_pool.push_back(r.e1);
+  }
+  c->prof_pending.clear();
+}
+}  // namespace hp
 
 namespace {
 
@@ -80,6 +112,7 @@ void hplmm_default_options(hplmm_options *o) {
   o->strict_two_grain = 0;
   o->use_graph = 0;
   o->verbose = 0;
+  o->profile = 0;
 }
 
 hplmm_status hplmm_create(hplmm_ctx **ctx, const hplmm_options *opt, void *cuda_stream) {
@@ -139,9 +172,12 @@ hplmm_status hplmm_setup(hplmm_ctx *c, const int32_t *partition, int n_grains, i
       HP_CUDA(cudaMemcpyAsync(c->b_corr.p, c->b_pad.p, sizeof(double) * L, cudaMemcpyDeviceToDevice, s));
     HP_CUDA(cudaStreamSynchronize(s));
     double t0 = now_s();
-    hp::build_maps(c, partition);
-    hp::build_mortars(c);
-    hp::build_local_sets(c);
+    {
+      hp::ProfScope ps(c, HPLMM_PH_MAPS);
+      hp::build_maps(c, partition);
+      hp::build_mortars(c);
+      hp::build_local_sets(c);
+    }
     double t1 = now_s();
     // smoother build (T_ML): exact local factorisations of grains and contact grids
     hp::factor_local(c, c->grains, c->opt.local_prec);
@@ -158,6 +194,7 @@ hplmm_status hplmm_setup(hplmm_ctx *c, const int32_t *partition, int n_grains, i
     if (c->opt.verbose)
       fprintf(stderr, "[hplmm] setup: maps %.3f ms, factor %.3f ms, coarse %.3f ms; N^o=%lld, ifaces=%d\n",
               1e3 * (t1 - t0), 1e3 * (t2 - t1), 1e3 * (t3 - t2), c->n_coarse, c->n_ifaces);
+    hp::prof_harvest(c);
     c->setup_done = true;
   });
 }
@@ -220,6 +257,7 @@ hplmm_status hplmm_solve(hplmm_ctx *c, const double *b, double *x, double tol, h
     rc = (hplmm_status)hp::fgmres(c, bp, c->w_out.p, tol, st);
     hp::gather_free(c, c->w_out.p, x);
     HP_CUDA(cudaStreamSynchronize(c->stream));
+    hp::prof_harvest(c);
     double t1 = now_s();
     if (st) {
       st->t_setup_ml = c->t_ml;
@@ -296,6 +334,51 @@ hplmm_status hplmm_get_prolongation_column(hplmm_ctx *c, long long col, double *
   });
 }
 
+hplmm_status hplmm_get_profile(hplmm_ctx *c, double *ms, long long *launches, int n) {
+  return guarded(c, [&] {
+    HP_REQUIRE(n >= HPLMM_PH_COUNT, HPLMM_ERR_INVALID, "get_profile: arrays must hold HPLMM_PH_COUNT entries");
+    hp::prof_harvest(c);
+    for (int i = 0; i < HPLMM_PH_COUNT; ++i) {
+      if (ms) ms[i] = c->prof_ms[i];
+      if (launches) launches[i] = c->prof_launches[i];
+    }
+  });
+}
+
+hplmm_status hplmm_reset_profile(hplmm_ctx *c) {
+  return guarded(c, [&] {
+    hp::prof_harvest(c);
+    for (int i = 0; i < HPLMM_PH_COUNT; ++i) {
+      c->prof_ms[i] = 0.0;
+      c->prof_launches[i] = 0;
+    }
+  });
+}
+
+long long hplmm_kernel_launches(void) { return hp::launch_count(); }
+
+hplmm_status hplmm_get_costs(hplmm_ctx *c, hplmm_costs *out) {
+  return guarded(c, [&] {
+    require_setup(c);
+    HP_REQUIRE(out, HPLMM_ERR_INVALID, "get_costs: null output");
+    std::memset(out, 0, sizeof(*out));
+    out->nnzb = c->nnzb;
+    out->local_elem_bytes = c->opt.local_prec == HPLMM_FP64 ? 8 : 4;
+    auto acc = [&](const hp::LocalSet &S, long long &elems, double &flops, long long &dofs) {
+      elems = S.h_band_off.empty() ? 0 : S.h_band_off.back();
+      for (int k = 0; k < S.count; ++k) {
+        flops += (double)S.h_n[k] * S.h_bw[k] * S.h_bw[k];
+        dofs += S.h_n[k];
+      }
+    };
+    acc(c->grains, out->grain_band_elems, out->grain_chol_flops, out->grain_dofs);
+    acc(c->contacts, out->contact_band_elems, out->contact_chol_flops, out->contact_dofs);
+    for (int g = 0; g < c->grains.count; ++g)
+      out->basis_solve_flops += 4.0 * c->grains.h_n[g] * c->grains.h_bw[g] * c->h_kg[g];
+    out->panel_elems = c->h_panel_off.empty() ? 0 : c->h_panel_off.back();
+  });
+}
+
 const char *hplmm_last_error(const hplmm_ctx *c) {
   if (!c) return "null context";
   return c->err.c_str();
@@ -304,6 +387,12 @@ const char *hplmm_last_error(const hplmm_ctx *c) {
 void hplmm_destroy(hplmm_ctx *c) {
   if (!c) return;
   if (c->apply_graph) cudaGraphExecDestroy(c->apply_graph);
+  cudaStreamSynchronize(c->stream);
+  for (auto &r : c->prof_pending) {
+    cudaEventDestroy(r.e0);
+    cudaEventDestroy(r.e1);
+  }
+  for (auto e : c->ev_pool) cudaEventDestroy(e);
   delete c;
 }
 

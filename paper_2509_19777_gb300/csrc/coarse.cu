@@ -511,6 +511,13 @@ __global__ void k_prolong_iface(const int *iface_nodes, const int *iface_of_node
 }
 
 template <typename T>
+Buf<T> &gal_buf(hplmm_ctx *c);
+template <>
+Buf<double> &gal_buf<double>(hplmm_ctx *c) { return c->gal64; }
+template <>
+Buf<float> &gal_buf<float>(hplmm_ctx *c) { return c->gal32; }
+
+template <typename T>
 T *panel_ptr(hplmm_ctx *c);
 template <>
 double *panel_ptr<double>(hplmm_ctx *c) { return c->X64.p; }
@@ -522,10 +529,13 @@ void galerkin(hplmm_ctx *c, const Buf<int> &gbox, const std::vector<long long> &
               const Buf<int> &gcol_off, const Buf<int> &gcol, int maxvol) {
   cudaStream_t s = c->stream;
   int G = c->n_grains;
-  Buf<T> P, Y;
-  P.alloc(std::max<long long>(hgal[G], 1));
-  Y.alloc(std::max<long long>(hgal[G], 1));
-  P.zero(s);
+  Buf<T> &work = gal_buf<T>(c);
+  long long tot = std::max<long long>(hgal[G], 1);
+  work.alloc(2 * tot);
+  HP_CUDA(cudaMemsetAsync(work.p, 0, sizeof(T) * tot, s));
+  struct {
+    T *p;
+  } P{work.p}, Y{work.p + tot};
   dim3 gf(grid_for(maxvol, 128), G);
   k_gal_fill<T><<<gf, 128, 0, s>>>(gbox.p, gal_off.p, c->kg.p, c->grid_to_node.p, c->nx, c->ny, c->node_cls.p,
                                    c->iface_of_node.p, c->iface_slot.p, c->fixed.p, c->grains.box.p,
@@ -583,6 +593,8 @@ void build_coarse(hplmm_ctx *c, const double *b_corr) {
   HP_REQUIRE(maxk <= 512, HPLMM_ERR_INVALID,
              "a grain couples to " + std::to_string(maxk) + " coarse columns (limit 512); use fewer mortars or larger grains");
   dim3 grid(grid_for(std::max(maxn, 1), 128), G);
+  {
+  ProfScope ps_rhs(c, HPLMM_PH_BASIS_RHS);
   if (f64)
     k_basis_rhs<double><<<grid, 128, 0, s>>>(G, c->grains.node_off.p, c->grains.n.p, c->grains.lnodes.p,
                                              c->row_ptr.p, c->col.p, c->val64.p, c->iface_of_node.p, c->iface_slot.p,
@@ -596,6 +608,7 @@ void build_coarse(hplmm_ctx *c, const double *b_corr) {
                                             c->gi_off.p, c->gi_iface.p, c->gi_colbase.p, c->kg.p, c->corr_col.p,
                                             c->panel_off.p, b_corr, c->opt.strict_two_grain, c->X32.p);
   HP_CHECK_LAUNCH();
+  }
   // batched local solves (Eqs. col_pk, col_cg): X_g <- (A^g_g)^{-1} X_g
   if (f64)
     solve_local_multi_f64(c, c->grains, c->X64.p, c->panel_off, c->kg, c->h_kg);
@@ -654,11 +667,13 @@ void build_coarse(hplmm_ctx *c, const double *b_corr) {
   long long No = c->n_coarse;
   c->Ao.alloc(std::max<long long>(No * No, 1));
   c->Ao.zero(s);
+  ProfScope ps_gal(c, HPLMM_PH_GALERKIN);
   if (f64)
     galerkin<double>(c, gbox, hgal, gal_off, c->gcol_off, c->gcol, maxvol);
   else
     galerkin<float>(c, gbox, hgal, gal_off, c->gcol_off, c->gcol, maxvol);
   if (No > 0) {
+    ProfScope ps_chol(c, HPLMM_PH_COARSE_CHOL);
     k_symmetrize<<<grid_for(No * No, 256), 256, 0, s>>>(c->Ao.p, No, nullptr);
     HP_CHECK_LAUNCH();
     // Cholesky factor (FP64) in a copy
@@ -682,6 +697,7 @@ void build_coarse(hplmm_ctx *c, const double *b_corr) {
 }
 
 void coarse_apply(hplmm_ctx *c, const double *r_pad, double *z_pad) {
+  ProfScope ps(c, HPLMM_PH_APPLY_COARSE);
   cudaStream_t s = c->stream;
   long long No = c->n_coarse;
   int G = c->n_grains;

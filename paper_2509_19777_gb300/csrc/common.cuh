@@ -30,7 +30,13 @@ struct Error : public std::runtime_error {
     }                                                                                      \
   } while (0)
 
-#define HP_CHECK_LAUNCH() HP_CUDA(cudaGetLastError())
+// every kernel launch site checks its launch; the check also counts launches
+long long note_launch();
+#define HP_CHECK_LAUNCH()          \
+  do {                             \
+    ::hp::note_launch();           \
+    HP_CUDA(cudaGetLastError());   \
+  } while (0)
 
 #define HP_REQUIRE(cond, code, msg)        \
   do {                                     \
@@ -41,7 +47,8 @@ struct Error : public std::runtime_error {
 template <typename T>
 struct Buf {
   T *p = nullptr;
-  size_t n = 0;
+  size_t n = 0;    // current size (elements)
+  size_t cap = 0;  // allocated capacity (elements); alloc() keeps the memory when it fits
   Buf() = default;
   Buf(const Buf &) = delete;
   Buf &operator=(const Buf &) = delete;
@@ -49,18 +56,22 @@ struct Buf {
   void release() {
     if (p) cudaFree(p);
     p = nullptr;
-    n = 0;
+    n = cap = 0;
   }
   void alloc(size_t count) {
-    release();
     if (count == 0) count = 1;
+    if (p && count <= cap) {
+      n = count;
+      return;
+    }
+    release();
     cudaError_t e = cudaMalloc(&p, count * sizeof(T));
     if (e != cudaSuccess) {
       p = nullptr;
       throw Error(HPLMM_ERR_OOM, "cudaMalloc of " + std::to_string(count * sizeof(T)) + " bytes failed: " +
                                      cudaGetErrorString(e));
     }
-    n = count;
+    n = cap = count;
   }
   void zero(cudaStream_t s) { HP_CUDA(cudaMemsetAsync(p, 0, n * sizeof(T), s)); }
   void fill_bytes(int v, cudaStream_t s) { HP_CUDA(cudaMemsetAsync(p, v, n * sizeof(T), s)); }
@@ -192,6 +203,8 @@ struct hplmm_ctx {
   hp::Buf<double> X64;             // basis panels X_g (local DOF rows x k_g), FP64
   hp::Buf<float> X32;              // FP32 copy/compute
   hp::Buf<double> Ao;              // N^o x N^o
+  hp::Buf<double> gal64;           // Galerkin work: P and Y on the grains' node boxes (FP64 form)
+  hp::Buf<float> gal32;            // (FP32 form)
   hp::Buf<double> Lo;              // Cholesky factor (lower, row-major full storage)
   hp::Buf<double> Lo_dinv;         // inverses of its 64x64 diagonal tiles
   hp::Buf<int> gcol_off, gcol;     // global coarse column of each panel column
@@ -213,9 +226,44 @@ struct hplmm_ctx {
   double *graph_z = nullptr;
 
   double t_ml = 0, t_mg = 0;
+
+  // ---- phase profiling (options.profile)
+  struct ProfRec {
+    int ph;
+    cudaEvent_t e0, e1;
+    long long launches;
+  };
+  std::vector<cudaEvent_t> ev_pool;
+  std::vector<ProfRec> prof_pending;
+  double prof_ms[HPLMM_PH_COUNT] = {};
+  long long prof_launches[HPLMM_PH_COUNT] = {};
 };
 
 namespace hp {
+long long launch_count();
+cudaEvent_t prof_event(hplmm_ctx *c);
+void prof_harvest(hplmm_ctx *c);
+
+// times the kernels queued on the context's stream between construction and destruction
+struct ProfScope {
+  hplmm_ctx *c;
+  int ph;
+  cudaEvent_t e0 = nullptr;
+  long long l0 = 0;
+  ProfScope(hplmm_ctx *ctx, int phase) : c(ctx), ph(phase) {
+    if (!c->opt.profile) return;
+    e0 = prof_event(c);
+    cudaEventRecord(e0, c->stream);
+    l0 = launch_count();
+  }
+  ~ProfScope() {
+    if (!c->opt.profile || !e0) return;
+    cudaEvent_t e1 = prof_event(c);
+    cudaEventRecord(e1, c->stream);
+    c->prof_pending.push_back({ph, e0, e1, launch_count() - l0});
+  }
+};
+
 // assemble.cu
 void assemble(hplmm_ctx *c, const uint8_t *mask, int nx, int ny, int nz, const float *E, double E0, double nu,
               const hplmm_bcs *bcs, double *b_out);

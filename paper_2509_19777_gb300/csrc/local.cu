@@ -776,6 +776,7 @@ void build_local_sets(hplmm_ctx *c) {
 void factor_local(hplmm_ctx *c, LocalSet &S, hplmm_prec prec) {
   if (S.count == 0) return;
   int where = (&S == &c->grains) ? 1 : 2;
+  ProfScope ps(c, where == 1 ? HPLMM_PH_FACTOR_GRAINS : HPLMM_PH_FACTOR_CONTACTS);
   if (prec == HPLMM_FP64)
     layout_and_factor<double>(c, S, where);
   else
@@ -800,6 +801,7 @@ static void solve_multi_t(hplmm_ctx *c, LocalSet &S, T *X, const Buf<long long> 
   }
   int n_items = (int)items.size() / 2;
   if (n_items == 0) return;
+  ProfScope ps(c, HPLMM_PH_BASIS_SOLVE);
   Buf<int> it;
   it.upload(items, s);
   k_band_solve_multi<T, NB><<<n_items, 256, 0, s>>>(it.p, n_items, S.n.p, S.bw.p, S.band_off.p, S.dinv_off.p,
@@ -819,6 +821,7 @@ void solve_local_multi_f32(hplmm_ctx *c, LocalSet &S, float *X, const Buf<long l
 
 void smoother_apply(hplmm_ctx *c, LocalSet &S, const double *r_pad, double *z_pad, bool atomic) {
   if (S.count == 0) return;
+  ProfScope ps(c, (&S == &c->grains) ? HPLMM_PH_APPLY_GRAINS : HPLMM_PH_APPLY_CONTACTS);
   cudaStream_t s = c->stream;
   int nmax = 0;
   for (int k = 0; k < S.count; ++k) nmax = std::max(nmax, S.h_n[k]);
