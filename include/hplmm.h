@@ -138,6 +138,22 @@ hplmm_status hplmm_apply_smoother(hplmm_ctx *ctx, const double *r, double *z);
 /* y = A_hat x in FP64.  DEVICE float64 [n_dof]. */
 hplmm_status hplmm_spmv(hplmm_ctx *ctx, const double *x, double *y);
 
+/* y = A_hat x in FP64, like hplmm_spmv, but allocating nothing.  The paper has
+ * no counterpart: this entry point exists for callers that cannot allocate
+ * device memory at call time -- their memory is held by their own pool or
+ * fixed budget, or their loop must not pay cudaMalloc's implicit device
+ * synchronisation.  The padded work vectors live in one file-scope device
+ * array of 786,432 float64 slots per vector, so the context must have
+ * 3 * n_nodes <= 786,432 (262,144 fine nodes); larger systems get
+ * HPLMM_ERR_INVALID.  The array (12 MiB) stays allocated on every device that
+ * loads the library until the process exits.  The first call on a device looks
+ * up the array's device address once (make that first call before any stream
+ * capture).  All calls share the array and it keeps the previous call's
+ * contents (the padded input is cleared each call); calls that overlap on the
+ * GPU race.  x, y: DEVICE float64 [n_dof].  Asynchronous on the context's
+ * stream. */
+hplmm_status hplmm_spmv_noalloc(hplmm_ctx *ctx, const double *x, double *y);
+
 /* Right-preconditioned FGMRES(restart) with CGS2 Arnoldi in FP64 (Section 5),
  * x_0 = 0, stopping when ||b - A x|| / ||b|| <= tol (true residual checked
  * at the end of each cycle) or after max_iters steps.  b: DEVICE float64

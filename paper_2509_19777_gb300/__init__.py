@@ -34,7 +34,8 @@ PREC = {"fp64": HPLMM_FP64, "fp32": HPLMM_FP32, "bf16": HPLMM_BF16}
 
 EXPORTED = [
     "hplmm_default_options", "hplmm_create", "hplmm_assemble", "hplmm_setup", "hplmm_apply",
-    "hplmm_apply_coarse", "hplmm_apply_smoother", "hplmm_spmv", "hplmm_solve", "hplmm_get_sizes",
+    "hplmm_apply_coarse", "hplmm_apply_smoother", "hplmm_spmv", "hplmm_spmv_noalloc", "hplmm_solve",
+    "hplmm_get_sizes",
     "hplmm_get_maps", "hplmm_get_coarse_matrix", "hplmm_get_prolongation_column", "hplmm_get_profile",
     "hplmm_reset_profile", "hplmm_kernel_launches", "hplmm_get_costs", "hplmm_last_error", "hplmm_destroy",
 ]
@@ -96,6 +97,7 @@ def load_library():
         "hplmm_apply_coarse": (I, [P, P, P]),
         "hplmm_apply_smoother": (I, [P, P, P]),
         "hplmm_spmv": (I, [P, P, P]),
+        "hplmm_spmv_noalloc": (I, [P, P, P]),
         "hplmm_solve": (I, [P, P, P, D, ctypes.POINTER(hplmm_stats)]),
         "hplmm_get_sizes": (I, [P, ctypes.POINTER(hplmm_sizes)]),
         "hplmm_get_maps": (I, [P, P, P, P, P, P, P, P, P]),
@@ -201,6 +203,11 @@ def hplmm_apply_smoother(ctx, r, z):
 
 def hplmm_spmv(ctx, x, y):
     _check(ctx, load_library().hplmm_spmv(ctx, _ptr(x), _ptr(y)))
+
+
+def hplmm_spmv_noalloc(ctx, x, y):
+    """y = A_hat x using the library's static device scratch (no allocation; see include/hplmm.h)."""
+    _check(ctx, load_library().hplmm_spmv_noalloc(ctx, _ptr(x), _ptr(y)))
 
 
 def hplmm_solve(ctx, b, x, tol=1e-8):
