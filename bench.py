@@ -48,6 +48,9 @@ def parse():
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--no-plain", action="store_true", help="skip the plain FP64 comparison run")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--quick", action="store_true",
+                    help="profiling mode: time only the chosen form (no plain, e2e or CPU legs); prints a short line")
+    ap.add_argument("--workload", default=WORKLOAD, help="synthetic workload for --quick runs (e.g. porous32)")
     return ap.parse_args()
 
 
@@ -370,8 +373,17 @@ def main():
     build_library()
     torch.cuda.set_device(local)
     stream = torch.cuda.current_stream()
-    problem = synth.make_workload(WORKLOAD, args.seed + rank)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")   # 256 MiB > 129 MB L2
+    if args.quick:
+        problem = synth.make_workload(args.workload, args.seed + rank)
+        sq, _, tq, stq, prof, costs, sizes, launches = run_form(hp, problem, CHOSEN, args.steps, args.warmup, flush,
+                                                                stream, profile=True)
+        print(json.dumps({"workload": args.workload, "ms_per_step": statistics.mean(tq), "iters": stq.iters,
+                          "launches_per_step": launches / args.steps,
+                          "profile_ms_per_step": {k: v[0] / args.steps for k, v in prof.items()}}), flush=True)
+        sq.close()
+        return
+    problem = synth.make_workload(WORKLOAD, args.seed + rank)
 
     # plain FP64 form (comparison)
     plain = None

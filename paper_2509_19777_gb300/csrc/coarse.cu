@@ -356,61 +356,98 @@ __global__ void k_syrk_tiles(double *A, long long N, int kt, int T) {
     }
 }
 
-// ---------------------------------------------------------------- coarse solve (one CTA)
-// forward L y = t then backward L^T u = y with the blocked factor and inverse diagonal tiles
-__global__ void __launch_bounds__(1024) k_coarse_solve(const double *L, long long N, const double *Dinv, double *x) {
-  __shared__ double blk[TB];
-  __shared__ double part[32][TB + 1];
-  int T = (int)((N + TB - 1) / TB);
-  int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  // forward
-  for (int kt = 0; kt < T; ++kt) {
-    int k0 = kt * TB, nb = (int)min((long long)TB, N - k0);
-    // partial sums of L[k0+r][0:k0] x[0:k0]: warp w handles rows r = w, w+32 (2 rows per warp)
-    for (int r = wid; r < TB; r += 32) {
-      double s = 0.0;
-      if (r < nb)
-        for (long long j = lane; j < k0; j += 32) s += L[(long long)(k0 + r) * N + j] * x[j];
-      for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
-      if (lane == 0) blk[r] = (r < nb) ? x[k0 + r] - s : 0.0;
-    }
-    __syncthreads();
-    if (threadIdx.x < nb) {
-      int r = threadIdx.x;
-      double s = 0.0;
-      for (int q = 0; q <= r; ++q) s += Dinv[(long long)kt * TB * TB + r * TB + q] * blk[q];
-      x[k0 + r] = s;
-    }
-    __syncthreads();
+// ---------------------------------------------------------------- explicit inverse factor Y = L^{-1}
+// Right-looking block substitution of L Y = I: for block row k, Y_kj = inv(L_kk) B_kj (j <= k), then
+// B_ij -= L_ik Y_kj for i > k.  Y starts as the identity (B) and is overwritten in place.
+__global__ void k_eye(double *Y, long long N) {
+  long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < N) Y[i * N + i] = 1.0;
+}
+
+__global__ void k_trinv_scale(double *Y, long long N, int kt, const double *Dinv) {
+  __shared__ double D[TB][TB + 1];
+  __shared__ double Bt[TB][TB + 1];
+  int jt = blockIdx.x;  // 0..kt
+  int k0 = kt * TB, j0 = jt * TB;
+  int nbk = (int)min((long long)TB, N - k0), nbj = (int)min((long long)TB, N - j0);
+  for (int e = threadIdx.x; e < TB * TB; e += blockDim.x) {
+    int r = e / TB, c = e % TB;
+    D[r][c] = Dinv[(long long)kt * TB * TB + e];
+    Bt[r][c] = (r < nbk && c < nbj) ? Y[(long long)(k0 + r) * N + j0 + c] : 0.0;
   }
-  // backward: u_k = inv(L_kk)^T (y_k - sum_{i>k} L_ik^T u_i)
-  for (int kt = T - 1; kt >= 0; --kt) {
-    int k0 = kt * TB, nb = (int)min((long long)TB, N - k0);
-    // column sums: thread (wid, lane) over rows i >= k0+nb (stride 32 by warp), columns c = lane, lane+32
-    double s0 = 0.0, s1 = 0.0;
-    for (long long i = k0 + nb + wid; i < N; i += 32) {
-      double xi = x[i];
-      const double *row = L + i * N + k0;
-      if (lane < nb) s0 += row[lane] * xi;
-      if (lane + 32 < nb) s1 += row[lane + 32] * xi;
+  __syncthreads();
+  int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  double acc[4][4] = {};
+  for (int q = 0; q < TB; ++q) {
+    double a[4], b[4];
+    for (int u = 0; u < 4; ++u) {
+      a[u] = D[ty + 16 * u][q];
+      b[u] = Bt[q][tx + 16 * u];
     }
-    part[wid][lane] = s0;
-    part[wid][lane + 32] = s1;
-    __syncthreads();
-    if (threadIdx.x < TB) {
-      int c = threadIdx.x;
-      double s = 0.0;
-      for (int w = 0; w < 32; ++w) s += part[w][c];
-      blk[c] = (c < nb) ? x[k0 + c] - s : 0.0;
+    for (int u = 0; u < 4; ++u)
+      for (int v = 0; v < 4; ++v) acc[u][v] += a[u] * b[v];
+  }
+  for (int u = 0; u < 4; ++u)
+    for (int v = 0; v < 4; ++v) {
+      int r = ty + 16 * u, c = tx + 16 * v;
+      if (r < nbk && c < nbj) Y[(long long)(k0 + r) * N + j0 + c] = acc[u][v];
     }
-    __syncthreads();
-    if (threadIdx.x < nb) {
-      int r = threadIdx.x;
-      double s = 0.0;
-      for (int q = r; q < nb; ++q) s += Dinv[(long long)kt * TB * TB + q * TB + r] * blk[q];
-      x[k0 + r] = s;
+}
+
+// Y[it][jt] -= L[it][kt] Y[kt][jt] for it > kt, jt <= kt
+__global__ void k_trinv_update(double *Y, const double *L, long long N, int kt, int T) {
+  __shared__ double Lt[TB][TB + 1];
+  __shared__ double Yt[TB][TB + 1];
+  int ncol = kt + 1;
+  int it = kt + 1 + blockIdx.x / ncol, jt = blockIdx.x % ncol;
+  if (it >= T) return;
+  int i0 = it * TB, k0 = kt * TB, j0 = jt * TB;
+  int nbi = (int)min((long long)TB, N - i0), nbk = (int)min((long long)TB, N - k0),
+      nbj = (int)min((long long)TB, N - j0);
+  for (int e = threadIdx.x; e < TB * TB; e += blockDim.x) {
+    int r = e / TB, c = e % TB;
+    Lt[r][c] = (r < nbi && c < nbk) ? L[(long long)(i0 + r) * N + k0 + c] : 0.0;
+    Yt[r][c] = (r < nbk && c < nbj) ? Y[(long long)(k0 + r) * N + j0 + c] : 0.0;
+  }
+  __syncthreads();
+  int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  double acc[4][4] = {};
+  for (int q = 0; q < TB; ++q) {
+    double a[4], b[4];
+    for (int u = 0; u < 4; ++u) {
+      a[u] = Lt[ty + 16 * u][q];
+      b[u] = Yt[q][tx + 16 * u];
     }
-    __syncthreads();
+    for (int u = 0; u < 4; ++u)
+      for (int v = 0; v < 4; ++v) acc[u][v] += a[u] * b[v];
+  }
+  for (int u = 0; u < 4; ++u)
+    for (int v = 0; v < 4; ++v) {
+      int r = ty + 16 * u, c = tx + 16 * v;
+      if (r < nbi && c < nbj) Y[(long long)(i0 + r) * N + j0 + c] -= acc[u][v];
+    }
+}
+
+// u = Y t over the lower triangle: warp per row
+__global__ void k_trmv_lower(const double *Y, long long N, const double *t, double *u) {
+  int lane = threadIdx.x & 31;
+  long long row = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (row >= N) return;
+  const double *yr = Y + row * N;
+  double s = 0.0;
+  for (long long j = lane; j <= row; j += 32) s += yr[j] * t[j];
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+  if (lane == 0) u[row] = s;
+}
+
+// z = Y^T u over the lower triangle: CTA per 32-row slab, threads over columns, atomic accumulation
+__global__ void k_trmv_lower_t(const double *Y, long long N, const double *u, double *z) {
+  long long r0 = (long long)blockIdx.y * 32;
+  long long r1 = min(N, r0 + 32);
+  for (long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x; j < r1; j += (long long)gridDim.x * blockDim.x) {
+    double s = 0.0;
+    for (long long i = max(r0, j); i < r1; ++i) s += Y[i * N + j] * u[i];
+    if (s != 0.0) atomicAdd(&z[j], s);
   }
 }
 
@@ -692,6 +729,20 @@ void build_coarse(hplmm_ctx *c, const double *b_corr) {
         HP_CHECK_LAUNCH();
       }
     }
+    // explicit inverse factor Y = L^{-1} (FP64), so that each apply is two parallel triangular products
+    c->Linv.alloc(No * No);
+    c->Linv.zero(s);
+    k_eye<<<grid_for(No, 256), 256, 0, s>>>(c->Linv.p, No);
+    HP_CHECK_LAUNCH();
+    for (int kt = 0; kt < T; ++kt) {
+      k_trinv_scale<<<kt + 1, 256, 0, s>>>(c->Linv.p, No, kt, c->Lo_dinv.p);
+      HP_CHECK_LAUNCH();
+      int m = T - kt - 1;
+      if (m > 0) {
+        k_trinv_update<<<m * (kt + 1), 256, 0, s>>>(c->Linv.p, c->Lo.p, No, kt, T);
+        HP_CHECK_LAUNCH();
+      }
+    }
   }
   HP_CUDA(cudaStreamSynchronize(s));
 }
@@ -724,7 +775,13 @@ void coarse_apply(hplmm_ctx *c, const double *r_pad, double *z_pad) {
                                                       c->kg.p, c->panel_off.p, c->X32.p, c->gcol_off.p, c->gcol.p,
                                                       r_pad, t);
   HP_CHECK_LAUNCH();
-  k_coarse_solve<<<1, 1024, 0, s>>>(c->Lo.p, No, c->Lo_dinv.p, t);
+  // u = Y t, then t <- Y^T u  (A^o)^{-1} = Y^T Y
+  double *u = c->w_coarse_u.p;
+  k_trmv_lower<<<grid_for(No * 32, 256), 256, 0, s>>>(c->Linv.p, No, t, u);
+  HP_CHECK_LAUNCH();
+  HP_CUDA(cudaMemsetAsync(t, 0, sizeof(double) * No, s));
+  dim3 gt(grid_for(std::min<long long>(No, 1024), 256), (unsigned)((No + 31) / 32));
+  k_trmv_lower_t<<<gt, 256, 0, s>>>(c->Linv.p, No, u, t);
   HP_CHECK_LAUNCH();
   dim3 gp(16, G);
   if (f64)

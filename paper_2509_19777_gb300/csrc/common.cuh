@@ -123,9 +123,8 @@ struct LocalSet {
   Buf<long long> band_off, node_off, vec_off;
   Buf<int> lnodes;    // ordinal -> global node id (node_off based)
   Buf<int> lmap;      // box cell (permuted lexicographic) -> ordinal or -1 (node_off based)
-  Buf<long long> dinv_off;
-  Buf<double> band64, dinv64;   // FP64 factors (panel width 16)
-  Buf<float> band32, dinv32;    // FP32 factors (panel width 32)
+  Buf<double> band64;   // FP64 factors (panel width 16; diagonal rows hold inv(L_kk))
+  Buf<float> band32;    // FP32 factors (panel width 32)
   Buf<int> order;     // problems sorted by decreasing factorisation cost
   hplmm_prec prec = HPLMM_FP64;
 };
@@ -207,6 +206,7 @@ struct hplmm_ctx {
   hp::Buf<float> gal32;            // (FP32 form)
   hp::Buf<double> Lo;              // Cholesky factor (lower, row-major full storage)
   hp::Buf<double> Lo_dinv;         // inverses of its 64x64 diagonal tiles
+  hp::Buf<double> Linv;            // Y = L^{-1} (lower), so that (A^o)^{-1} = Y^T Y
   hp::Buf<int> gcol_off, gcol;     // global coarse column of each panel column
   hp::Buf<int> status;             // device error word
 

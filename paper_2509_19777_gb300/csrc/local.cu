@@ -241,8 +241,8 @@ __device__ __forceinline__ double dev_sqrt<double>(double x) { return sqrt(x); }
 template <typename T, int NB>
 __global__ void __launch_bounds__(FACT_THREADS) k_band_chol(const int *order, int count, int *queue,
                                                            const int *nloc, const int *bwv,
-                                                           const long long *band_off, const long long *dinv_off,
-                                                           T *band, T *dinv, int *status, int where) {
+                                                           const long long *band_off, T *band, int *status,
+                                                           int where) {
   extern __shared__ __align__(16) unsigned char smraw[];
   constexpr int LD = NB + (16 / sizeof(T));  // padded row stride
   T *P = reinterpret_cast<T *>(smraw);
@@ -259,7 +259,6 @@ __global__ void __launch_bounds__(FACT_THREADS) k_band_chol(const int *order, in
     int N = nloc[k], bw = bwv[k];
     if (N == 0) continue;
     T *B = band + band_off[k];
-    T *Di = dinv + dinv_off[k];
     const int RP = NB + bw;
     for (int k0 = 0, p = 0; k0 < N; k0 += NB, ++p) {
       int nb = min(NB, N - k0);
@@ -333,11 +332,10 @@ __global__ void __launch_bounds__(FACT_THREADS) k_band_chol(const int *order, in
 #pragma unroll
         for (int cc = 0; cc < NB; ++cc) P[r * LD + cc] = out[cc];
       }
-      // store inv(L_kk)
-      for (int e = threadIdx.x; e < NB * NB; e += FACT_THREADS) Di[(long long)p * NB * NB + e] = Dv[e / NB][e % NB];
       __syncthreads();
-      // 4. write the panel back
-      for (int e = threadIdx.x; e < R * NB; e += FACT_THREADS) {
+      // 4. write the panel back: inv(L_kk) in the diagonal rows (the solves only need the inverse), then L
+      for (int e = threadIdx.x; e < NB * NB; e += FACT_THREADS) Bp[e] = Dv[e / NB][e % NB];
+      for (int e = NB * NB + threadIdx.x; e < R * NB; e += FACT_THREADS) {
         int r = e / NB, cc = e - r * NB;
         Bp[e] = P[r * LD + cc];
       }
@@ -387,8 +385,8 @@ __global__ void __launch_bounds__(FACT_THREADS) k_band_chol(const int *order, in
 template <typename T, int NB>
 __global__ void __launch_bounds__(256) k_band_solve_multi(const int *items, int n_items, const int *nloc,
                                                           const int *bwv, const long long *band_off,
-                                                          const long long *dinv_off, const T *band, const T *dinv,
-                                                          T *Xbase, const long long *x_off, const int *x_ld) {
+                                                          const T *band, T *Xbase, const long long *x_off,
+                                                          const int *x_ld) {
   constexpr int RB = 32;
   constexpr int CH = 32;  // panel rows staged per chunk
   __shared__ T Ds[NB][NB];
@@ -403,7 +401,6 @@ __global__ void __launch_bounds__(256) k_band_solve_multi(const int *items, int 
   int ld = x_ld[k];
   int ncol = min(RB, ld - r0);
   const T *B = band + band_off[k];
-  const T *Di = dinv + dinv_off[k];
   T *X = Xbase + x_off[k] + r0;
   const int RP = NB + bw;
   const int np = (N + NB - 1) / NB;
@@ -411,7 +408,7 @@ __global__ void __launch_bounds__(256) k_band_solve_multi(const int *items, int 
   // forward: L y = x
   for (int p = 0; p < np; ++p) {
     int k0 = p * NB, nb = min(NB, N - k0);
-    for (int e = threadIdx.x; e < NB * NB; e += 256) Ds[e / NB][e % NB] = Di[(long long)p * NB * NB + e];
+    for (int e = threadIdx.x; e < NB * NB; e += 256) Ds[e / NB][e % NB] = B[(long long)p * RP * NB + e];
     for (int q = wid; q < NB; q += 8) Yb[q][lane] = (q < nb && colok) ? X[(long long)(k0 + q) * ld + lane] : (T)0;
     __syncthreads();
     T y[NB / 8 + 1];
@@ -454,7 +451,7 @@ __global__ void __launch_bounds__(256) k_band_solve_multi(const int *items, int 
   // backward: L^T x = y
   for (int p = np - 1; p >= 0; --p) {
     int k0 = p * NB, nb = min(NB, N - k0);
-    for (int e = threadIdx.x; e < NB * NB; e += 256) Ds[e / NB][e % NB] = Di[(long long)p * NB * NB + e];
+    for (int e = threadIdx.x; e < NB * NB; e += 256) Ds[e / NB][e % NB] = B[(long long)p * RP * NB + e];
     T acc[NB];
 #pragma unroll
     for (int cc = 0; cc < NB; ++cc) acc[cc] = 0;
@@ -491,81 +488,254 @@ __global__ void __launch_bounds__(256) k_band_solve_multi(const int *items, int 
 }
 
 // ---------------------------------------------------------------- single-RHS smoother solves
-// One CTA per problem: gather r into the local order, solve, add (or store) into z.
+// One CTA per problem: gather r into shared memory in the local order, run the forward and backward
+// sweeps, add (contact grids, which overlap) or store (grain grids) the result into z.  The factor is
+// streamed in 16 KiB row chunks of its panels by bulk asynchronous copies (cp.async.bulk) into a ring of
+// SOLVE_STAGES shared-memory buffers guarded by mbarriers, so the loads of later chunks overlap the
+// arithmetic on earlier ones.  Forward: panels in order, chunk 0 (holding inv(L_kk)) first.  Backward:
+// panels in reverse, chunk 0 last.  Every wait is bounded; on expiry the kernel records
+// HPLMM_ERR_TIMEOUT, drains its own copies (also bounded) and returns.
+constexpr int SOLVE_STAGES = 4;
+constexpr int CHUNK_BYTES = 16384;
+constexpr long long WAIT_LIMIT = 1LL << 26;
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+               : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
+  uint32_t done;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.b32 %0, 1, 0, p;\n}\n"
+      : "=r"(done)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return done != 0;
+}
+
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity) {
+  for (long long it = 0; it < WAIT_LIMIT; ++it)
+    if (mbar_try_wait(bar, parity)) return true;
+  return false;
+}
+
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
+
+// position of chunk number q in the stream: forward then backward
+struct ChunkPos {
+  int dir, p, c, row0, rows;
+};
+
+struct ChunkIter {
+  int N, NB, RP, CH, np;
+  int dir = 0, p = 0, c = 0;
+  __device__ int rows_needed(int pp) const {
+    int r = min(N - pp * NB, RP);
+    return max(r, NB);
+  }
+  __device__ int nch(int pp) const { return (rows_needed(pp) + CH - 1) / CH; }
+  __device__ void start() {
+    dir = 0;
+    p = 0;
+    c = 0;
+  }
+  // current chunk (c is the position within the panel's visiting order)
+  __device__ ChunkPos cur() const {
+    int n = nch(p);
+    int chunk = (dir == 0) ? c : ((c + 1) % n);  // backward: 1, 2, ..., n-1, then 0
+    int row0 = chunk * CH;
+    int rows = min(CH, rows_needed(p) - row0);
+    return {dir, p, chunk, row0, rows};
+  }
+  __device__ void next() {
+    if (++c >= nch(p)) {
+      c = 0;
+      if (dir == 0) {
+        if (++p >= np) {
+          dir = 1;
+          p = np - 1;
+        }
+      } else {
+        --p;
+      }
+    }
+  }
+};
+
 template <typename T, int NB>
 __global__ void __launch_bounds__(256) k_band_solve_one(int count, const int *nloc, const int *bwv,
-                                                        const long long *band_off, const long long *dinv_off,
-                                                        const long long *node_off, const int *lnodes, const T *band,
-                                                        const T *dinv, const double *r, double *z, int atomic) {
-  extern __shared__ __align__(16) unsigned char smraw[];
-  T *v = reinterpret_cast<T *>(smraw);
-  __shared__ T Ds[NB][NB];
+                                                        const long long *band_off, const long long *node_off,
+                                                        const int *lnodes, const T *band, const double *r, double *z,
+                                                        int atomic, int *status) {
+  static_assert(NB * sizeof(T) == 128, "panel rows are 128 bytes");
+  constexpr int E = 16 / sizeof(T);   // elements per 16-byte lane load
+  constexpr int CH = CHUNK_BYTES / 128;  // rows per chunk
+  extern __shared__ __align__(128) unsigned char smring[];
+  T *ring = reinterpret_cast<T *>(smring);
+  T *v = ring + (size_t)SOLVE_STAGES * CH * NB;
+  __shared__ __align__(8) uint64_t full[SOLVE_STAGES];
   __shared__ T vb[NB];
-  __shared__ T red[8][NB];
+  __shared__ T red[32][NB + 1];
+  __shared__ int abort_flag;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  int k = blockIdx.x;
+  const int k = blockIdx.x;
   if (k >= count) return;
-  int N = nloc[k], bw = bwv[k];
+  const int N = nloc[k];
   if (N == 0) return;
+  const int bw = bwv[k];
+  const int RP = NB + bw;
+  const int np = (N + NB - 1) / NB;
   const T *B = band + band_off[k];
-  const T *Di = dinv + dinv_off[k];
   const int *ln = lnodes + node_off[k];
+  ChunkIter prod{N, NB, RP, CH, np}, cons{N, NB, RP, CH, np};
+  prod.start();
+  cons.start();
+  int total = 0;
+  for (int pp = 0; pp < np; ++pp) total += 2 * cons.nch(pp);
+  if (threadIdx.x == 0) {
+    abort_flag = 0;
+    for (int st = 0; st < SOLVE_STAGES; ++st) mbar_init(&full[st], 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
   for (int l = threadIdx.x; l < N; l += 256) {
     int o = l / 3, d = l - 3 * o;
     v[l] = (T)r[3LL * ln[o] + d];
   }
-  const int RP = NB + bw;
-  const int np = (N + NB - 1) / NB;
   __syncthreads();
-  for (int p = 0; p < np; ++p) {
-    int k0 = p * NB, nb = min(NB, N - k0);
-    for (int e = threadIdx.x; e < NB * NB; e += 256) Ds[e / NB][e % NB] = Di[(long long)p * NB * NB + e];
-    __syncthreads();
-    if (threadIdx.x < NB) {
-      int q = threadIdx.x;
-      T s = 0;
-      for (int cc = 0; cc <= q && cc < nb; ++cc) s += Ds[q][cc] * v[k0 + cc];
-      vb[q] = (q < nb) ? s : (T)0;
+  int issued = 0;
+  if (threadIdx.x == 0) {
+    for (; issued < SOLVE_STAGES && issued < total; ++issued) {
+      ChunkPos cp = prod.cur();
+      uint32_t bytes = (uint32_t)cp.rows * 128u;
+      mbar_expect_tx(&full[issued], bytes);
+      bulk_g2s(ring + (size_t)issued * CH * NB, B + (long long)cp.p * RP * NB + (long long)cp.row0 * NB, bytes,
+               &full[issued]);
+      prod.next();
     }
-    __syncthreads();
-    if (threadIdx.x < nb) v[k0 + threadIdx.x] = vb[threadIdx.x];
-    const T *Bp = B + (long long)p * RP * NB;
-    int rend = min(N - k0, RP);
-    for (int rr = nb + threadIdx.x; rr < rend; rr += 256) {
-      const T *row = Bp + (long long)rr * NB;
-      T s = 0;
+  }
+  const int g = lane & 7;       // 16-byte column group inside a row
+  const int rsub = lane >> 3;   // row slot inside a warp's 4-row group
+  T acc[E];
 #pragma unroll
-      for (int cc = 0; cc < NB; ++cc) s += row[cc] * vb[cc];
-      v[k0 + rr] -= s;
+  for (int e = 0; e < E; ++e) acc[e] = 0;
+  T vbr[E];
+  int qfail = total;
+  for (int q = 0; q < total; ++q) {
+    const int st = q % SOLVE_STAGES;
+    const uint32_t parity = (uint32_t)((q / SOLVE_STAGES) & 1);
+    bool ok = mbar_wait_bounded(&full[st], parity);
+    if (__syncthreads_or(!ok)) {
+      if (threadIdx.x == 0) {
+        atomicCAS(status, 0, (int)HPLMM_ERR_TIMEOUT);
+        abort_flag = 1;
+      }
+      qfail = q;
+      __syncthreads();
+      break;
     }
+    const ChunkPos cp = cons.cur();
+    const T *buf = ring + (size_t)st * CH * NB;
+    const int k0 = cp.p * NB, nb = min(NB, N - k0);
+    const int rend = min(N - k0, RP);  // rows of the panel inside the matrix
+    if (cp.dir == 0) {
+      if (cp.c == 0) {
+        // y_blk = inv(L_kk) x_blk
+        if (threadIdx.x < NB) {
+          int t = threadIdx.x;
+          T sacc = 0;
+          for (int cc = 0; cc <= t && cc < nb; ++cc) sacc += buf[t * NB + cc] * v[k0 + cc];
+          vb[t] = (t < nb) ? sacc : (T)0;
+        }
+        __syncthreads();
+        if (threadIdx.x < nb) v[k0 + threadIdx.x] = vb[threadIdx.x];
+      }
+#pragma unroll
+      for (int e = 0; e < E; ++e) vbr[e] = vb[g * E + e];
+      // window rows of this chunk: v[k0 + rr] -= L[rr][:] . y_blk
+      int lo = max(cp.row0, nb), hi = min(cp.row0 + cp.rows, rend);
+      for (int base = cp.row0; base < hi; base += 32) {
+        int rr = base + wid * 4 + rsub;
+        T part = 0;
+        if (rr >= lo && rr < hi) {
+          const T *row = buf + (size_t)(rr - cp.row0) * NB + g * E;
+#pragma unroll
+          for (int e = 0; e < E; ++e) part += row[e] * vbr[e];
+        }
+        part += __shfl_xor_sync(0xffffffffu, part, 4);
+        part += __shfl_xor_sync(0xffffffffu, part, 2);
+        part += __shfl_xor_sync(0xffffffffu, part, 1);
+        if (g == 0 && rr >= lo && rr < hi) v[k0 + rr] -= part;
+      }
+    } else {
+      // accumulate L[rr][:]^T x[k0 + rr] over the panel's window rows
+      int lo = max(cp.row0, nb), hi = min(cp.row0 + cp.rows, rend);
+      for (int base = cp.row0; base < hi; base += 32) {
+        int rr = base + wid * 4 + rsub;
+        if (rr >= lo && rr < hi) {
+          const T *row = buf + (size_t)(rr - cp.row0) * NB + g * E;
+          T xv = v[k0 + rr];
+#pragma unroll
+          for (int e = 0; e < E; ++e) acc[e] += row[e] * xv;
+        }
+      }
+      if (cp.c == 0) {
+        // finish the panel: t = x_blk - acc, x_blk = inv(L_kk)^T t
+#pragma unroll
+        for (int e = 0; e < E; ++e) red[wid * 4 + rsub][g * E + e] = acc[e];
+        __syncthreads();
+        if (threadIdx.x < NB) {
+          int cc = threadIdx.x;
+          T sacc = 0;
+          for (int w = 0; w < 32; ++w) sacc += red[w][cc];
+          vb[cc] = (cc < nb) ? v[k0 + cc] - sacc : (T)0;
+        }
+        __syncthreads();
+        if (threadIdx.x < nb) {
+          int t = threadIdx.x;
+          T sacc = 0;
+          for (int cc = t; cc < nb; ++cc) sacc += buf[cc * NB + t] * vb[cc];
+          v[k0 + t] = sacc;
+        }
+#pragma unroll
+        for (int e = 0; e < E; ++e) acc[e] = 0;
+      }
+    }
+    cons.next();
     __syncthreads();
+    // refill the stage just consumed
+    if (threadIdx.x == 0 && issued < total) {
+      ChunkPos cpn = prod.cur();
+      uint32_t bytes = (uint32_t)cpn.rows * 128u;
+      mbar_expect_tx(&full[st], bytes);
+      bulk_g2s(ring + (size_t)st * CH * NB, B + (long long)cpn.p * RP * NB + (long long)cpn.row0 * NB, bytes,
+               &full[st]);
+      prod.next();
+      ++issued;
+    }
   }
-  for (int p = np - 1; p >= 0; --p) {
-    int k0 = p * NB, nb = min(NB, N - k0);
-    for (int e = threadIdx.x; e < NB * NB; e += 256) Ds[e / NB][e % NB] = Di[(long long)p * NB * NB + e];
-    const T *Bp = B + (long long)p * RP * NB;
-    int rend = min(N - k0, RP);
-    // lanes over columns of the panel (NB <= 32), warps over rows
-    T acc = 0;
-    if (lane < NB)
-      for (int rr = nb + wid; rr < rend; rr += 8) acc += Bp[(long long)rr * NB + lane] * v[k0 + rr];
-    if (lane < NB) red[wid][lane] = acc;
+  if (abort_flag) {
+    // drain our own copies still in flight (chunks qfail .. issued-1) before shared memory is released
+    if (threadIdx.x == 0)
+      for (int q = qfail; q < issued; ++q) mbar_wait_bounded(&full[q % SOLVE_STAGES], (uint32_t)((q / SOLVE_STAGES) & 1));
     __syncthreads();
-    if (threadIdx.x < NB) {
-      int q = threadIdx.x;
-      T s = 0;
-      for (int w = 0; w < 8; ++w) s += red[w][q];
-      vb[q] = (q < nb) ? v[k0 + q] - s : (T)0;
-    }
-    __syncthreads();
-    if (threadIdx.x < nb) {
-      int q = threadIdx.x;
-      T s = 0;
-      for (int cc = q; cc < nb; ++cc) s += Ds[cc][q] * vb[cc];
-      v[k0 + q] = s;
-    }
-    __syncthreads();
+    return;
   }
+  __syncthreads();
   for (int l = threadIdx.x; l < N; l += 256) {
     int o = l / 3, d = l - 3 * o;
     long long slot = 3LL * ln[o] + d;
@@ -582,12 +752,6 @@ template <>
 float *band_ptr<float>(LocalSet &S) { return S.band32.p; }
 template <>
 double *band_ptr<double>(LocalSet &S) { return S.band64.p; }
-template <typename T>
-T *dinv_ptr(LocalSet &S);
-template <>
-float *dinv_ptr<float>(LocalSet &S) { return S.dinv32.p; }
-template <>
-double *dinv_ptr<double>(LocalSet &S) { return S.dinv64.p; }
 
 }  // namespace
 
@@ -610,13 +774,12 @@ void layout_and_factor(hplmm_ctx *c, LocalSet &S, int where) {
   cudaStream_t s = c->stream;
   int K = S.count;
   // band and inverse-block offsets for this precision
-  std::vector<long long> boff(K + 1, 0), doff(K + 1, 0);
+  std::vector<long long> boff(K + 1, 0);
   int bwmax = 0;
   for (int k = 0; k < K; ++k) {
     int N = S.h_n[k], bw = S.h_bw[k];
     long long np = (N + NB - 1) / NB;
     boff[k + 1] = boff[k] + np * (NB + bw) * NB;
-    doff[k + 1] = doff[k] + np * NB * NB;
     if (N > 0) bwmax = std::max(bwmax, bw);
   }
   size_t smem = (size_t)(NB + bwmax) * (NB + 16 / sizeof(T)) * sizeof(T);
@@ -624,18 +787,14 @@ void layout_and_factor(hplmm_ctx *c, LocalSet &S, int where) {
              "local problem half bandwidth " + std::to_string(bwmax) + " is too large; use smaller grain grids");
   S.h_band_off = boff;
   S.band_off.upload(boff, s);
-  S.dinv_off.upload(doff, s);
   if (sizeof(T) == 8) {
     S.band64.alloc(std::max<long long>(boff[K], 1));
     S.band64.zero(s);
-    S.dinv64.alloc(std::max<long long>(doff[K], 1));
   } else {
     S.band32.alloc(std::max<long long>(boff[K], 1));
     S.band32.zero(s);
-    S.dinv32.alloc(std::max<long long>(doff[K], 1));
   }
   T *band = band_ptr<T>(S);
-  T *dinv = dinv_ptr<T>(S);
   k_local_extract<T><<<K, 128, 0, s>>>(S.box.p, S.node_off.p, S.n.p, S.bw.p, S.band_off.p, S.lmap.p, S.lnodes.p,
                                        c->node_ijk.p, c->row_ptr.p, c->col.p, c->val64.p, c->fixed.p, band, NB);
   HP_CHECK_LAUNCH();
@@ -645,8 +804,8 @@ void layout_and_factor(hplmm_ctx *c, LocalSet &S, int where) {
   auto kern = k_band_chol<T, NB>;
   HP_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   int grid = std::min(K, 2 * num_sms());
-  kern<<<grid, FACT_THREADS, smem, s>>>(S.order.p, K, queue.p, S.n.p, S.bw.p, S.band_off.p, S.dinv_off.p, band, dinv,
-                                        c->status.p, where);
+  kern<<<grid, FACT_THREADS, smem, s>>>(S.order.p, K, queue.p, S.n.p, S.bw.p, S.band_off.p, band, c->status.p,
+                                        where);
   HP_CHECK_LAUNCH();
   HP_CUDA(cudaStreamSynchronize(s));
 }
@@ -804,8 +963,8 @@ static void solve_multi_t(hplmm_ctx *c, LocalSet &S, T *X, const Buf<long long> 
   ProfScope ps(c, HPLMM_PH_BASIS_SOLVE);
   Buf<int> it;
   it.upload(items, s);
-  k_band_solve_multi<T, NB><<<n_items, 256, 0, s>>>(it.p, n_items, S.n.p, S.bw.p, S.band_off.p, S.dinv_off.p,
-                                                    band_ptr<T>(S), dinv_ptr<T>(S), X, x_off.p, x_ld.p);
+  k_band_solve_multi<T, NB><<<n_items, 256, 0, s>>>(it.p, n_items, S.n.p, S.bw.p, S.band_off.p, band_ptr<T>(S), X,
+                                                    x_off.p, x_ld.p);
   HP_CHECK_LAUNCH();
   HP_CUDA(cudaStreamSynchronize(s));
 }
@@ -825,20 +984,21 @@ void smoother_apply(hplmm_ctx *c, LocalSet &S, const double *r_pad, double *z_pa
   cudaStream_t s = c->stream;
   int nmax = 0;
   for (int k = 0; k < S.count; ++k) nmax = std::max(nmax, S.h_n[k]);
+  const size_t ring = (size_t)SOLVE_STAGES * CHUNK_BYTES;
   if (S.prec == HPLMM_FP64) {
-    size_t smem = sizeof(double) * (size_t)std::max(nmax, 1);
+    size_t smem = ring + sizeof(double) * (size_t)std::max(nmax, 1);
     auto kern = k_band_solve_one<double, 16>;
     HP_REQUIRE(smem <= 200 * 1024, HPLMM_ERR_INVALID, "local problem too large for the FP64 smoother");
     HP_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    kern<<<S.count, 256, smem, s>>>(S.count, S.n.p, S.bw.p, S.band_off.p, S.dinv_off.p, S.node_off.p, S.lnodes.p,
-                                    S.band64.p, S.dinv64.p, r_pad, z_pad, atomic ? 1 : 0);
+    kern<<<S.count, 256, smem, s>>>(S.count, S.n.p, S.bw.p, S.band_off.p, S.node_off.p, S.lnodes.p, S.band64.p,
+                                    r_pad, z_pad, atomic ? 1 : 0, c->status.p);
   } else {
-    size_t smem = sizeof(float) * (size_t)std::max(nmax, 1);
+    size_t smem = ring + sizeof(float) * (size_t)std::max(nmax, 1);
     auto kern = k_band_solve_one<float, 32>;
     HP_REQUIRE(smem <= 200 * 1024, HPLMM_ERR_INVALID, "local problem too large for the FP32 smoother");
     HP_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    kern<<<S.count, 256, smem, s>>>(S.count, S.n.p, S.bw.p, S.band_off.p, S.dinv_off.p, S.node_off.p, S.lnodes.p,
-                                    S.band32.p, S.dinv32.p, r_pad, z_pad, atomic ? 1 : 0);
+    kern<<<S.count, 256, smem, s>>>(S.count, S.n.p, S.bw.p, S.band_off.p, S.node_off.p, S.lnodes.p, S.band32.p,
+                                    r_pad, z_pad, atomic ? 1 : 0, c->status.p);
   }
   HP_CHECK_LAUNCH();
 }
