@@ -452,32 +452,40 @@ __global__ void k_trmv_lower_t(const double *Y, long long N, const double *u, do
 }
 
 // ---------------------------------------------------------------- restriction / prolongation
-// t[gcol] += sum over grain rows of X_g[row][a] r_loc[row]; CTA = (grain, 32-column chunk)
+// t[gcol] += sum over grain rows of X_g[row][a] r_loc[row]; CTA = (grain, chunk of RCHUNK rows):
+// the chunk's residual entries are gathered once into shared memory, then each thread owns columns and
+// reads the panel rows coalesced.
+constexpr int RCHUNK = 512;
+
 template <typename T, typename A>
-__global__ void k_restrict_grain(const long long *node_off, const int *nloc, const int *lnodes, const int *kg,
-                                 const long long *panel_off, const T *X, const int *gcol_off, const int *gcol,
-                                 const double *r, double *t) {
-  __shared__ A part[8][32];
-  int g = blockIdx.y, a0 = blockIdx.x * 32;
-  int k = kg[g];
-  if (a0 >= k) return;
-  int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+__global__ void __launch_bounds__(256) k_restrict_grain(const long long *node_off, const int *nloc, const int *lnodes,
+                                                        const int *kg, const long long *panel_off, const T *X,
+                                                        const int *gcol_off, const int *gcol, const double *r,
+                                                        double *t) {
+  __shared__ A rl[RCHUNK];
+  int g = blockIdx.y;
   int N = nloc[g];
-  const T *Xg = X + panel_off[g];
+  int row0 = blockIdx.x * RCHUNK;
+  if (row0 >= N) return;
+  int cnt = min(RCHUNK, N - row0);
+  int k = kg[g];
   const int *ln = lnodes + node_off[g];
-  A s = 0;
-  int a = a0 + lane;
-  for (int row = wid; row < N; row += 8) {
+  for (int rr = threadIdx.x; rr < cnt; rr += blockDim.x) {
+    int row = row0 + rr;
     int o = row / 3, d = row - 3 * o;
-    A rv = (A)r[3LL * ln[o] + d];
-    if (a < k) s += (A)Xg[(long long)row * k + a] * rv;
+    rl[rr] = (A)r[3LL * ln[o] + d];
   }
-  part[wid][lane] = s;
   __syncthreads();
-  if (wid == 0) {
-    A tot = 0;
-    for (int w = 0; w < 8; ++w) tot += part[w][lane];
-    if (a < k) atomicAdd(&t[gcol[gcol_off[g] + a]], (double)tot);
+  const T *Xg = X + panel_off[g] + (long long)row0 * k;
+  for (int a = threadIdx.x; a < k; a += blockDim.x) {
+    A s0 = 0, s1 = 0;
+    int rr = 0;
+    for (; rr + 1 < cnt; rr += 2) {
+      s0 += (A)Xg[(long long)rr * k + a] * rl[rr];
+      s1 += (A)Xg[(long long)(rr + 1) * k + a] * rl[rr + 1];
+    }
+    if (rr < cnt) s0 += (A)Xg[(long long)rr * k + a] * rl[rr];
+    atomicAdd(&t[gcol[gcol_off[g] + a]], (double)(s0 + s1));
   }
 }
 
@@ -763,9 +771,9 @@ void coarse_apply(hplmm_ctx *c, const double *r_pad, double *z_pad) {
         c->eta.p, c->comp_mask.p, c->col_off.p, c->fixed.p, r_pad, t);
     HP_CHECK_LAUNCH();
   }
-  int kmax = 1;
-  for (int g = 0; g < G; ++g) kmax = std::max(kmax, c->h_kg[g]);
-  dim3 gr((kmax + 31) / 32, G);
+  int nmax = 1;
+  for (int g = 0; g < G; ++g) nmax = std::max(nmax, c->grains.h_n[g]);
+  dim3 gr((nmax + RCHUNK - 1) / RCHUNK, G);
   if (f64)
     k_restrict_grain<double, double><<<gr, 256, 0, s>>>(c->grains.node_off.p, c->grains.n.p, c->grains.lnodes.p,
                                                         c->kg.p, c->panel_off.p, c->X64.p, c->gcol_off.p, c->gcol.p,

@@ -488,16 +488,17 @@ __global__ void __launch_bounds__(256) k_band_solve_multi(const int *items, int 
 }
 
 // ---------------------------------------------------------------- single-RHS smoother solves
-// One CTA per problem: gather r into shared memory in the local order, run the forward and backward
-// sweeps, add (contact grids, which overlap) or store (grain grids) the result into z.  The factor is
-// streamed in 16 KiB row chunks of its panels by bulk asynchronous copies (cp.async.bulk) into a ring of
-// SOLVE_STAGES shared-memory buffers guarded by mbarriers, so the loads of later chunks overlap the
-// arithmetic on earlier ones.  Forward: panels in order, chunk 0 (holding inv(L_kk)) first.  Backward:
-// panels in reverse, chunk 0 last.  Every wait is bounded; on expiry the kernel records
-// HPLMM_ERR_TIMEOUT, drains its own copies (also bounded) and returns.
-constexpr int SOLVE_STAGES = 4;
-constexpr int CHUNK_BYTES = 16384;
-constexpr long long WAIT_LIMIT = 1LL << 26;
+// One CTA per problem solves L L^T x = r for the gathered local right-hand side (kept in shared memory) and
+// adds (contact grids, which overlap) or stores (grain grids) x into z.
+//
+// The factor is streamed panel by panel in large row chunks (tens of KiB: a bulk copy has a roughly fixed
+// per-operation cost on one SM, so few large copies beat many small ones) by cp.async.bulk into a ring of
+// 2-3 shared-memory stages guarded by mbarriers.  Forward sweep: panels in order, chunk 0 (whose first NB
+// rows hold inv(L_kk)) first; backward sweep: panels in reverse, chunk 0 last.  All waits are bounded; on
+// expiry HPLMM_ERR_TIMEOUT is recorded, in-flight copies are drained (bounded) and the CTA returns.
+constexpr int SOLVE_THREADS = 512;
+constexpr int MAX_STAGES = 4;
+constexpr long long WAIT_LIMIT = 1LL << 28;
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -512,10 +513,11 @@ __device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
                : "memory");
 }
 
-__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
+// non-suspending poll of a phase
+__device__ __forceinline__ bool mbar_test_wait(uint64_t *bar, uint32_t parity) {
   uint32_t done;
   asm volatile(
-      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.b32 %0, 1, 0, p;\n}\n"
+      "{\n .reg .pred p;\n mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.b32 %0, 1, 0, p;\n}\n"
       : "=r"(done)
       : "r"(smem_u32(bar)), "r"(parity)
       : "memory");
@@ -524,7 +526,7 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
 
 __device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity) {
   for (long long it = 0; it < WAIT_LIMIT; ++it)
-    if (mbar_try_wait(bar, parity)) return true;
+    if (mbar_test_wait(bar, parity)) return true;
   return false;
 }
 
@@ -536,31 +538,17 @@ __device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t by
       : "memory");
 }
 
-// position of chunk number q in the stream: forward then backward
-struct ChunkPos {
-  int dir, p, c, row0, rows;
-};
-
+// chunk q of the stream: direction, panel, chunk index inside the panel, first row and row count
 struct ChunkIter {
   int N, NB, RP, CH, np;
   int dir = 0, p = 0, c = 0;
-  __device__ int rows_needed(int pp) const {
-    int r = min(N - pp * NB, RP);
-    return max(r, NB);
-  }
+  __device__ int rows_needed(int pp) const { return max(min(N - pp * NB, RP), NB); }
   __device__ int nch(int pp) const { return (rows_needed(pp) + CH - 1) / CH; }
-  __device__ void start() {
-    dir = 0;
-    p = 0;
-    c = 0;
-  }
-  // current chunk (c is the position within the panel's visiting order)
-  __device__ ChunkPos cur() const {
+  __device__ void cur(int &chunk, int &row0, int &rows) const {
     int n = nch(p);
-    int chunk = (dir == 0) ? c : ((c + 1) % n);  // backward: 1, 2, ..., n-1, then 0
-    int row0 = chunk * CH;
-    int rows = min(CH, rows_needed(p) - row0);
-    return {dir, p, chunk, row0, rows};
+    chunk = (dir == 0) ? c : ((c + 1) % n);  // backward: 1, 2, ..., n-1, then 0
+    row0 = chunk * CH;
+    rows = min(CH, rows_needed(p) - row0);
   }
   __device__ void next() {
     if (++c >= nch(p)) {
@@ -577,21 +565,28 @@ struct ChunkIter {
   }
 };
 
+// one lane per warp polls the phase, then every lane confirms it (each thread observes the completion)
+__device__ __forceinline__ bool warp_wait_phase(uint64_t *bar, uint32_t parity) {
+  int ok = 1;
+  if ((threadIdx.x & 31) == 0) ok = mbar_wait_bounded(bar, parity) ? 1 : 0;
+  ok = __shfl_sync(0xffffffffu, ok, 0);
+  if (!ok) return false;
+  return mbar_wait_bounded(bar, parity);
+}
+
 template <typename T, int NB>
-__global__ void __launch_bounds__(256) k_band_solve_one(int count, const int *nloc, const int *bwv,
-                                                        const long long *band_off, const long long *node_off,
-                                                        const int *lnodes, const T *band, const double *r, double *z,
-                                                        int atomic, int *status) {
+__global__ void __launch_bounds__(SOLVE_THREADS) k_band_solve_one(int count, const int *nloc, const int *bwv,
+                                                                  const long long *band_off,
+                                                                  const long long *node_off, const int *lnodes,
+                                                                  const T *band, const double *r, double *z,
+                                                                  int atomic, int CH, int stages, int *status) {
   static_assert(NB * sizeof(T) == 128, "panel rows are 128 bytes");
-  constexpr int E = 16 / sizeof(T);   // elements per 16-byte lane load
-  constexpr int CH = CHUNK_BYTES / 128;  // rows per chunk
+  constexpr int E = 16 / sizeof(T);  // elements per 16-byte group; 8 groups per row
+  constexpr int NW = SOLVE_THREADS / 32;
   extern __shared__ __align__(128) unsigned char smring[];
-  T *ring = reinterpret_cast<T *>(smring);
-  T *v = ring + (size_t)SOLVE_STAGES * CH * NB;
-  __shared__ __align__(8) uint64_t full[SOLVE_STAGES];
-  __shared__ T vb[NB];
-  __shared__ T red[32][NB + 1];
-  __shared__ int abort_flag;
+  __shared__ __align__(8) uint64_t full[MAX_STAGES];
+  __shared__ __align__(16) T vb[NB];
+  __shared__ T red[NW * 4][NB + 1];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const int k = blockIdx.x;
   if (k >= count) return;
@@ -602,114 +597,126 @@ __global__ void __launch_bounds__(256) k_band_solve_one(int count, const int *nl
   const int np = (N + NB - 1) / NB;
   const T *B = band + band_off[k];
   const int *ln = lnodes + node_off[k];
+  const size_t stage_elems = (size_t)CH * NB;
+  T *ring = reinterpret_cast<T *>(smring);
+  T *v = ring + (size_t)stages * stage_elems;
   ChunkIter prod{N, NB, RP, CH, np}, cons{N, NB, RP, CH, np};
-  prod.start();
-  cons.start();
   int total = 0;
   for (int pp = 0; pp < np; ++pp) total += 2 * cons.nch(pp);
   if (threadIdx.x == 0) {
-    abort_flag = 0;
-    for (int st = 0; st < SOLVE_STAGES; ++st) mbar_init(&full[st], 1);
+    for (int st = 0; st < stages; ++st) mbar_init(&full[st], 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
-  for (int l = threadIdx.x; l < N; l += 256) {
+  for (int l = threadIdx.x; l < N; l += SOLVE_THREADS) {
     int o = l / 3, d = l - 3 * o;
     v[l] = (T)r[3LL * ln[o] + d];
   }
   __syncthreads();
   int issued = 0;
   if (threadIdx.x == 0) {
-    for (; issued < SOLVE_STAGES && issued < total; ++issued) {
-      ChunkPos cp = prod.cur();
-      uint32_t bytes = (uint32_t)cp.rows * 128u;
+    for (; issued < stages && issued < total; ++issued) {
+      int chunk, row0, rows;
+      prod.cur(chunk, row0, rows);
+      uint32_t bytes = (uint32_t)rows * 128u;
       mbar_expect_tx(&full[issued], bytes);
-      bulk_g2s(ring + (size_t)issued * CH * NB, B + (long long)cp.p * RP * NB + (long long)cp.row0 * NB, bytes,
-               &full[issued]);
+      bulk_g2s(ring + (size_t)issued * stage_elems, B + ((long long)prod.p * RP + row0) * NB, bytes, &full[issued]);
       prod.next();
     }
   }
-  const int g = lane & 7;       // 16-byte column group inside a row
-  const int rsub = lane >> 3;   // row slot inside a warp's 4-row group
+  const int g = lane & 7;      // 16-byte column group inside a row (backward)
+  const int rsub = lane >> 3;  // row slot inside a warp's 4-row group (backward)
   T acc[E];
 #pragma unroll
   for (int e = 0; e < E; ++e) acc[e] = 0;
-  T vbr[E];
-  int qfail = total;
+  int qfail = -1;
   for (int q = 0; q < total; ++q) {
-    const int st = q % SOLVE_STAGES;
-    const uint32_t parity = (uint32_t)((q / SOLVE_STAGES) & 1);
-    bool ok = mbar_wait_bounded(&full[st], parity);
+    const int st = q % stages;
+    bool ok = warp_wait_phase(&full[st], (uint32_t)((q / stages) & 1));
     if (__syncthreads_or(!ok)) {
-      if (threadIdx.x == 0) {
-        atomicCAS(status, 0, (int)HPLMM_ERR_TIMEOUT);
-        abort_flag = 1;
-      }
       qfail = q;
-      __syncthreads();
       break;
     }
-    const ChunkPos cp = cons.cur();
-    const T *buf = ring + (size_t)st * CH * NB;
-    const int k0 = cp.p * NB, nb = min(NB, N - k0);
-    const int rend = min(N - k0, RP);  // rows of the panel inside the matrix
-    if (cp.dir == 0) {
-      if (cp.c == 0) {
-        // y_blk = inv(L_kk) x_blk
-        if (threadIdx.x < NB) {
-          int t = threadIdx.x;
+    int chunk, row0, rows;
+    cons.cur(chunk, row0, rows);
+    const T *buf = ring + (size_t)st * stage_elems;
+    const int k0 = cons.p * NB, nb = min(NB, N - k0);
+    const int rend = min(N - k0, RP);  // rows of this panel inside the matrix
+    const int lo = max(row0, nb), hi = min(row0 + rows, rend);
+    if (cons.dir == 0) {
+      if (chunk == 0) {
+        // y_blk = inv(L_kk) x_blk: row t, 16-byte group g2 per thread, reduced over the 8 groups
+        if (threadIdx.x < NB * 8) {
+          int t = threadIdx.x >> 3, g2 = threadIdx.x & 7;
           T sacc = 0;
-          for (int cc = 0; cc <= t && cc < nb; ++cc) sacc += buf[t * NB + cc] * v[k0 + cc];
-          vb[t] = (t < nb) ? sacc : (T)0;
+#pragma unroll
+          for (int e = 0; e < E; ++e) {
+            int cc = g2 * E + e;
+            if (cc <= t && cc < nb) sacc += buf[t * NB + cc] * v[k0 + cc];
+          }
+          sacc += __shfl_xor_sync(0xffffffffu, sacc, 4);
+          sacc += __shfl_xor_sync(0xffffffffu, sacc, 2);
+          sacc += __shfl_xor_sync(0xffffffffu, sacc, 1);
+          if (g2 == 0) vb[t] = (t < nb) ? sacc : (T)0;
         }
         __syncthreads();
         if (threadIdx.x < nb) v[k0 + threadIdx.x] = vb[threadIdx.x];
       }
+      // window rows: one row per thread, 16-byte groups visited in a row-rotated order so that the 8
+      // threads of a shared-memory phase touch 8 different bank groups; 4 partial sums for ILP
+      for (int rr = lo + threadIdx.x; rr < hi; rr += SOLVE_THREADS) {
+        const T *row = buf + (size_t)(rr - row0) * NB;
+        T s0 = 0, s1 = 0, s2 = 0, s3 = 0;
 #pragma unroll
-      for (int e = 0; e < E; ++e) vbr[e] = vb[g * E + e];
-      // window rows of this chunk: v[k0 + rr] -= L[rr][:] . y_blk
-      int lo = max(cp.row0, nb), hi = min(cp.row0 + cp.rows, rend);
-      for (int base = cp.row0; base < hi; base += 32) {
-        int rr = base + wid * 4 + rsub;
-        T part = 0;
-        if (rr >= lo && rr < hi) {
-          const T *row = buf + (size_t)(rr - cp.row0) * NB + g * E;
+        for (int j = 0; j < 8; j += 2) {
+          int ga = (j + rr) & 7, gb = (j + 1 + rr) & 7;
 #pragma unroll
-          for (int e = 0; e < E; ++e) part += row[e] * vbr[e];
+          for (int e = 0; e < E; e += 2) {
+            s0 += row[ga * E + e] * vb[ga * E + e];
+            s1 += row[ga * E + e + 1] * vb[ga * E + e + 1];
+            s2 += row[gb * E + e] * vb[gb * E + e];
+            s3 += row[gb * E + e + 1] * vb[gb * E + e + 1];
+          }
         }
-        part += __shfl_xor_sync(0xffffffffu, part, 4);
-        part += __shfl_xor_sync(0xffffffffu, part, 2);
-        part += __shfl_xor_sync(0xffffffffu, part, 1);
-        if (g == 0 && rr >= lo && rr < hi) v[k0 + rr] -= part;
+        v[k0 + rr] -= (s0 + s1) + (s2 + s3);
       }
     } else {
       // accumulate L[rr][:]^T x[k0 + rr] over the panel's window rows
-      int lo = max(cp.row0, nb), hi = min(cp.row0 + cp.rows, rend);
-      for (int base = cp.row0; base < hi; base += 32) {
+      for (int base = row0; base < hi; base += NW * 4) {
         int rr = base + wid * 4 + rsub;
         if (rr >= lo && rr < hi) {
-          const T *row = buf + (size_t)(rr - cp.row0) * NB + g * E;
+          const T *row = buf + (size_t)(rr - row0) * NB + g * E;
           T xv = v[k0 + rr];
 #pragma unroll
           for (int e = 0; e < E; ++e) acc[e] += row[e] * xv;
         }
       }
-      if (cp.c == 0) {
-        // finish the panel: t = x_blk - acc, x_blk = inv(L_kk)^T t
+      if (chunk == 0) {
+        // finish the panel: t = x_blk - acc (reduced over the 64 row slots), x_blk = inv(L_kk)^T t
 #pragma unroll
         for (int e = 0; e < E; ++e) red[wid * 4 + rsub][g * E + e] = acc[e];
         __syncthreads();
-        if (threadIdx.x < NB) {
-          int cc = threadIdx.x;
+        if (threadIdx.x < NB * 8) {
+          int cc = threadIdx.x >> 3, part = threadIdx.x & 7;
           T sacc = 0;
-          for (int w = 0; w < 32; ++w) sacc += red[w][cc];
-          vb[cc] = (cc < nb) ? v[k0 + cc] - sacc : (T)0;
+          for (int w = part; w < NW * 4; w += 8) sacc += red[w][cc];
+          sacc += __shfl_xor_sync(0xffffffffu, sacc, 4);
+          sacc += __shfl_xor_sync(0xffffffffu, sacc, 2);
+          sacc += __shfl_xor_sync(0xffffffffu, sacc, 1);
+          if (part == 0) vb[cc] = (cc < nb) ? v[k0 + cc] - sacc : (T)0;
         }
         __syncthreads();
-        if (threadIdx.x < nb) {
-          int t = threadIdx.x;
+        if (threadIdx.x < NB * 8) {
+          int t = threadIdx.x >> 3, g2 = threadIdx.x & 7;
           T sacc = 0;
-          for (int cc = t; cc < nb; ++cc) sacc += buf[cc * NB + t] * vb[cc];
-          v[k0 + t] = sacc;
+#pragma unroll
+          for (int e = 0; e < E; ++e) {
+            int cc = g2 * E + e;
+            if (cc >= t && cc < nb) sacc += buf[cc * NB + t] * vb[cc];
+          }
+          sacc += __shfl_xor_sync(0xffffffffu, sacc, 4);
+          sacc += __shfl_xor_sync(0xffffffffu, sacc, 2);
+          sacc += __shfl_xor_sync(0xffffffffu, sacc, 1);
+          if (g2 == 0 && t < nb) v[k0 + t] = sacc;
         }
 #pragma unroll
         for (int e = 0; e < E; ++e) acc[e] = 0;
@@ -719,24 +726,25 @@ __global__ void __launch_bounds__(256) k_band_solve_one(int count, const int *nl
     __syncthreads();
     // refill the stage just consumed
     if (threadIdx.x == 0 && issued < total) {
-      ChunkPos cpn = prod.cur();
-      uint32_t bytes = (uint32_t)cpn.rows * 128u;
+      int chunk2, row02, rows2;
+      prod.cur(chunk2, row02, rows2);
+      uint32_t bytes = (uint32_t)rows2 * 128u;
       mbar_expect_tx(&full[st], bytes);
-      bulk_g2s(ring + (size_t)st * CH * NB, B + (long long)cpn.p * RP * NB + (long long)cpn.row0 * NB, bytes,
-               &full[st]);
+      bulk_g2s(ring + (size_t)st * stage_elems, B + ((long long)prod.p * RP + row02) * NB, bytes, &full[st]);
       prod.next();
       ++issued;
     }
   }
-  if (abort_flag) {
+  if (qfail >= 0) {
     // drain our own copies still in flight (chunks qfail .. issued-1) before shared memory is released
-    if (threadIdx.x == 0)
-      for (int q = qfail; q < issued; ++q) mbar_wait_bounded(&full[q % SOLVE_STAGES], (uint32_t)((q / SOLVE_STAGES) & 1));
+    if (threadIdx.x == 0) {
+      atomicCAS(status, 0, (int)HPLMM_ERR_TIMEOUT);
+      for (int q = qfail; q < issued; ++q) mbar_wait_bounded(&full[q % stages], (uint32_t)((q / stages) & 1));
+    }
     __syncthreads();
     return;
   }
-  __syncthreads();
-  for (int l = threadIdx.x; l < N; l += 256) {
+  for (int l = threadIdx.x; l < N; l += SOLVE_THREADS) {
     int o = l / 3, d = l - 3 * o;
     long long slot = 3LL * ln[o] + d;
     if (atomic)
@@ -984,21 +992,30 @@ void smoother_apply(hplmm_ctx *c, LocalSet &S, const double *r_pad, double *z_pa
   cudaStream_t s = c->stream;
   int nmax = 0;
   for (int k = 0; k < S.count; ++k) nmax = std::max(nmax, S.h_n[k]);
-  const size_t ring = (size_t)SOLVE_STAGES * CHUNK_BYTES;
+  // shared memory: the local vector, then a ring of 2..4 stages of large row chunks (>= NB rows each)
+  const size_t budget = 200 * 1024;
+  int rpmax = 0;
+  for (int k = 0; k < S.count; ++k)
+    if (S.h_n[k] > 0) rpmax = std::max(rpmax, S.h_bw[k] + (S.prec == HPLMM_FP64 ? 16 : 32));
+  const int NBv = S.prec == HPLMM_FP64 ? 16 : 32;
+  const size_t esz = S.prec == HPLMM_FP64 ? 8 : 4;
+  size_t vbytes = ((esz * (size_t)std::max(nmax, 1) + 127) / 128) * 128;
+  HP_REQUIRE(vbytes + 2 * (size_t)NBv * 128 <= budget, HPLMM_ERR_INVALID, "local problem too large for the smoother");
+  size_t ring = budget - vbytes;
+  int stages = ring >= 3 * 40960 ? 3 : 2;
+  int CH = (int)std::min<size_t>(ring / stages / 128, 768);  // rows per chunk (at most 96 KiB)
+  CH = std::max(NBv, std::min(CH, std::max(rpmax, NBv)));
+  size_t smem = (size_t)stages * CH * 128 + vbytes;
   if (S.prec == HPLMM_FP64) {
-    size_t smem = ring + sizeof(double) * (size_t)std::max(nmax, 1);
     auto kern = k_band_solve_one<double, 16>;
-    HP_REQUIRE(smem <= 200 * 1024, HPLMM_ERR_INVALID, "local problem too large for the FP64 smoother");
     HP_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    kern<<<S.count, 256, smem, s>>>(S.count, S.n.p, S.bw.p, S.band_off.p, S.node_off.p, S.lnodes.p, S.band64.p,
-                                    r_pad, z_pad, atomic ? 1 : 0, c->status.p);
+    kern<<<S.count, SOLVE_THREADS, smem, s>>>(S.count, S.n.p, S.bw.p, S.band_off.p, S.node_off.p, S.lnodes.p,
+                                              S.band64.p, r_pad, z_pad, atomic ? 1 : 0, CH, stages, c->status.p);
   } else {
-    size_t smem = ring + sizeof(float) * (size_t)std::max(nmax, 1);
     auto kern = k_band_solve_one<float, 32>;
-    HP_REQUIRE(smem <= 200 * 1024, HPLMM_ERR_INVALID, "local problem too large for the FP32 smoother");
     HP_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    kern<<<S.count, 256, smem, s>>>(S.count, S.n.p, S.bw.p, S.band_off.p, S.node_off.p, S.lnodes.p, S.band32.p,
-                                    r_pad, z_pad, atomic ? 1 : 0, c->status.p);
+    kern<<<S.count, SOLVE_THREADS, smem, s>>>(S.count, S.n.p, S.bw.p, S.band_off.p, S.node_off.p, S.lnodes.p,
+                                              S.band32.p, r_pad, z_pad, atomic ? 1 : 0, CH, stages, c->status.p);
   }
   HP_CHECK_LAUNCH();
 }
