@@ -126,6 +126,8 @@ struct LocalSet {
   Buf<double> band64;   // FP64 factors (panel width 16; diagonal rows hold inv(L_kk))
   Buf<float> band32;    // FP32 factors (panel width 32)
   Buf<int> order;     // problems sorted by decreasing factorisation cost
+  int tuned_far_stages = 0;  // smoother solve pipeline depths picked by the tuner (0 = largest that fits)
+  int tuned_c0_stages = 0;
   hplmm_prec prec = HPLMM_FP64;
 };
 

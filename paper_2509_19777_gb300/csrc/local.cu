@@ -488,17 +488,36 @@ __global__ void __launch_bounds__(256) k_band_solve_multi(const int *items, int 
 }
 
 // ---------------------------------------------------------------- single-RHS smoother solves
-// One CTA per problem solves L L^T x = r for the gathered local right-hand side (kept in shared memory) and
-// adds (contact grids, which overlap) or stores (grain grids) x into z.
+// One CTA per problem solves L L^T x = r for the gathered local right-hand side (kept in shared memory as
+// the vector v) and adds (contact grids, which overlap) or stores (grain grids) x into z.
 //
-// The factor is streamed panel by panel in large row chunks (tens of KiB: a bulk copy has a roughly fixed
-// per-operation cost on one SM, so few large copies beat many small ones) by cp.async.bulk into a ring of
-// 2-3 shared-memory stages guarded by mbarriers.  Forward sweep: panels in order, chunk 0 (whose first NB
-// rows hold inv(L_kk)) first; backward sweep: panels in reverse, chunk 0 last.  All waits are bounded; on
-// expiry HPLMM_ERR_TIMEOUT is recorded, in-flight copies are drained (bounded) and the CTA returns.
-constexpr int SOLVE_THREADS = 512;
-constexpr int MAX_STAGES = 4;
-constexpr long long WAIT_LIMIT = 1LL << 28;
+// Both sweeps run in steps, one per panel (forward: p = 0 .. np-1, backward: p = np-1 .. 0).  The work of a
+// step is split between warps so that the short sequential chain of the triangular solve overlaps the
+// bandwidth-heavy part:
+//   - the leader warp handles the diagonal block of panel p and its "near" block (the next NB rows):
+//       forward  y_p = inv(L_pp) (v_p - L_{p,p-1} y_{p-1}),   near product L_{p+1,p} y_p kept in registers;
+//       backward x_p = inv(L_pp)^T (v_p - L_{p+1,p}^T x_{p+1} - far_p);
+//   - the bulk warps handle the "far" rows (beyond the near block) of panel p-1, one row per thread:
+//       forward  v[rows] -= L_far(p-1) y_{p-1};
+//       backward far_{p-1} = L_far(p-1)^T v[rows] (column sums reduced per warp);
+//   - a producer warp streams the factor with bulk asynchronous copies (cp.async.bulk) into two rings of
+//     shared-memory stages (the diagonal+near chunk of each panel, and the far rows in chunks of one row
+//     per bulk thread), guarded by full/empty mbarriers, running ahead of the consumers.
+// The leader and bulk warps meet once per step on a named barrier that also ORs their error flags.  Every
+// wait is bounded; on expiry the kernel records HPLMM_ERR_TIMEOUT, lets every copy in flight land and
+// returns without writing z.
+//
+// Shared-memory bank conflicts: a factor row is 128 bytes (8 groups of 16 bytes).  A bulk thread always
+// works on rows with the same index modulo 8 (rows of a chunk start at a multiple of 8 and the bulk thread
+// count is a multiple of 8), and visits the row's 16-byte groups starting at that offset, with its copy of
+// y (or its column accumulators) kept in the same rotated order in registers.  The 8 threads of one
+// shared-memory phase therefore touch 8 different bank groups.
+constexpr int WS_BULK_WARPS = 8;
+constexpr int WS_THREADS = (2 + WS_BULK_WARPS) * 32;
+constexpr int WS_FAR_ROWS = WS_BULK_WARPS * 32;  // rows per far chunk: one per bulk thread
+constexpr int WS_MAX_FAR_STAGES = 8;
+constexpr int WS_MAX_C0_STAGES = 4;
+constexpr long long WAIT_CYCLES = 4000000000LL;  // about two seconds of SM clock
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -513,21 +532,31 @@ __device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
                : "memory");
 }
 
-// non-suspending poll of a phase
-__device__ __forceinline__ bool mbar_test_wait(uint64_t *bar, uint32_t parity) {
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+// potentially suspending probe of a phase (returns after the phase completed or a hardware time limit)
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
   uint32_t done;
   asm volatile(
-      "{\n .reg .pred p;\n mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.b32 %0, 1, 0, p;\n}\n"
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.b32 %0, 1, 0, p;\n}\n"
       : "=r"(done)
       : "r"(smem_u32(bar)), "r"(parity)
       : "memory");
   return done != 0;
 }
 
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity) {
-  for (long long it = 0; it < WAIT_LIMIT; ++it)
-    if (mbar_test_wait(bar, parity)) return true;
-  return false;
+// bounded wait (about two seconds); gives up early when another warp has raised the abort flag
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity, const volatile int *abort_flag) {
+  const long long t0 = clock64();
+  for (long long it = 0;; ++it) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if ((it & 63) == 63) {
+      if (abort_flag && *abort_flag) return false;
+      if (clock64() - t0 > WAIT_CYCLES) return false;
+    }
+  }
 }
 
 __device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
@@ -538,55 +567,56 @@ __device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t by
       : "memory");
 }
 
-// chunk q of the stream: direction, panel, chunk index inside the panel, first row and row count
-struct ChunkIter {
-  int N, NB, RP, CH, np;
-  int dir = 0, p = 0, c = 0;
-  __device__ int rows_needed(int pp) const { return max(min(N - pp * NB, RP), NB); }
-  __device__ int nch(int pp) const { return (rows_needed(pp) + CH - 1) / CH; }
-  __device__ void cur(int &chunk, int &row0, int &rows) const {
-    int n = nch(p);
-    chunk = (dir == 0) ? c : ((c + 1) % n);  // backward: 1, 2, ..., n-1, then 0
-    row0 = chunk * CH;
-    rows = min(CH, rows_needed(p) - row0);
+// named barrier 1 over the leader and bulk warps; returns the OR of `flag` over its threads
+__device__ __forceinline__ int step_barrier_or(int flag, int nthreads) {
+  int res;
+  asm volatile(
+      "{\n .reg .pred p, q;\n setp.ne.s32 p, %1, 0;\n bar.red.or.pred q, 1, %2, p;\n selp.s32 %0, 1, 0, q;\n}\n"
+      : "=r"(res)
+      : "r"(flag), "r"(nthreads)
+      : "memory");
+  return res;
+}
+
+// 16-byte group loads of a factor row
+template <typename T> struct Vec16;
+template <> struct Vec16<float> {
+  static __device__ __forceinline__ void load(const float *p, float *o) {
+    float4 v = *reinterpret_cast<const float4 *>(p);
+    o[0] = v.x; o[1] = v.y; o[2] = v.z; o[3] = v.w;
   }
-  __device__ void next() {
-    if (++c >= nch(p)) {
-      c = 0;
-      if (dir == 0) {
-        if (++p >= np) {
-          dir = 1;
-          p = np - 1;
-        }
-      } else {
-        --p;
-      }
-    }
+};
+template <> struct Vec16<double> {
+  static __device__ __forceinline__ void load(const double *p, double *o) {
+    double2 v = *reinterpret_cast<const double2 *>(p);
+    o[0] = v.x; o[1] = v.y;
   }
 };
 
-// one lane per warp polls the phase, then every lane confirms it (each thread observes the completion)
-__device__ __forceinline__ bool warp_wait_phase(uint64_t *bar, uint32_t parity) {
-  int ok = 1;
-  if ((threadIdx.x & 31) == 0) ok = mbar_wait_bounded(bar, parity) ? 1 : 0;
-  ok = __shfl_sync(0xffffffffu, ok, 0);
-  if (!ok) return false;
-  return mbar_wait_bounded(bar, parity);
-}
+// geometry of panel p: rows of the panel inside the matrix, and its far rows [2 NB, rend)
+struct PanelGeo {
+  int N, NB, RP;
+  __device__ int rend(int p) const { return min(N - p * NB, RP); }
+  __device__ int nfar(int p) const { return max(0, rend(p) - 2 * NB); }
+  __device__ int nchunks(int p) const { return (nfar(p) + WS_FAR_ROWS - 1) / WS_FAR_ROWS; }
+  __device__ int c0rows() const { return min(2 * NB, RP); }
+};
 
 template <typename T, int NB>
-__global__ void __launch_bounds__(SOLVE_THREADS) k_band_solve_one(int count, const int *nloc, const int *bwv,
-                                                                  const long long *band_off,
-                                                                  const long long *node_off, const int *lnodes,
-                                                                  const T *band, const double *r, double *z,
-                                                                  int atomic, int CH, int stages, int *status) {
-  static_assert(NB * sizeof(T) == 128, "panel rows are 128 bytes");
-  constexpr int E = 16 / sizeof(T);  // elements per 16-byte group; 8 groups per row
-  constexpr int NW = SOLVE_THREADS / 32;
-  extern __shared__ __align__(128) unsigned char smring[];
-  __shared__ __align__(8) uint64_t full[MAX_STAGES];
-  __shared__ __align__(16) T vb[NB];
-  __shared__ T red[NW * 4][NB + 1];
+__global__ void __launch_bounds__(WS_THREADS) k_band_solve_ws(int count, const int *nloc, const int *bwv,
+                                                              const long long *band_off, const long long *node_off,
+                                                              const int *lnodes, const T *band, const double *r,
+                                                              double *z, int atomic, int far_stages, int c0_stages,
+                                                              int *status) {
+  static_assert(NB * sizeof(T) == 128, "factor rows are 128 bytes");
+  constexpr int E = 16 / sizeof(T);  // elements per 16-byte group
+  constexpr int NT_STEP = (1 + WS_BULK_WARPS) * 32;
+  extern __shared__ __align__(128) unsigned char smdyn[];
+  __shared__ __align__(8) uint64_t full_far[WS_MAX_FAR_STAGES], empty_far[WS_MAX_FAR_STAGES];
+  __shared__ __align__(8) uint64_t full_c0[WS_MAX_C0_STAGES], empty_c0[WS_MAX_C0_STAGES];
+  __shared__ T red[2][WS_BULK_WARPS][NB];
+  __shared__ T stage[WS_BULK_WARPS][8][NB];
+  __shared__ volatile int s_abort;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const int k = blockIdx.x;
   if (k >= count) return;
@@ -595,156 +625,239 @@ __global__ void __launch_bounds__(SOLVE_THREADS) k_band_solve_one(int count, con
   const int bw = bwv[k];
   const int RP = NB + bw;
   const int np = (N + NB - 1) / NB;
+  const int VN = np * NB + NB;  // padded local vector
+  const PanelGeo geo{N, NB, RP};
   const T *B = band + band_off[k];
   const int *ln = lnodes + node_off[k];
-  const size_t stage_elems = (size_t)CH * NB;
-  T *ring = reinterpret_cast<T *>(smring);
-  T *v = ring + (size_t)stages * stage_elems;
-  ChunkIter prod{N, NB, RP, CH, np}, cons{N, NB, RP, CH, np};
-  int total = 0;
-  for (int pp = 0; pp < np; ++pp) total += 2 * cons.nch(pp);
+  T *far_ring = reinterpret_cast<T *>(smdyn);
+  T *c0_ring = far_ring + (size_t)far_stages * WS_FAR_ROWS * NB;
+  T *v = c0_ring + (size_t)c0_stages * 2 * NB * NB;
+  const int c0rows = geo.c0rows();
+
   if (threadIdx.x == 0) {
-    for (int st = 0; st < stages; ++st) mbar_init(&full[st], 1);
+    for (int i = 0; i < far_stages; ++i) {
+      mbar_init(&full_far[i], 1);
+      mbar_init(&empty_far[i], WS_BULK_WARPS);
+    }
+    for (int i = 0; i < c0_stages; ++i) {
+      mbar_init(&full_c0[i], 1);
+      mbar_init(&empty_c0[i], 1);
+    }
+    s_abort = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
-  for (int l = threadIdx.x; l < N; l += SOLVE_THREADS) {
-    int o = l / 3, d = l - 3 * o;
-    v[l] = (T)r[3LL * ln[o] + d];
+  for (int l = threadIdx.x; l < VN; l += WS_THREADS) {
+    T val = 0;
+    if (l < N) {
+      int o = l / 3, d = l - 3 * o;
+      val = (T)r[3LL * ln[o] + d];
+    }
+    v[l] = val;
   }
   __syncthreads();
-  int issued = 0;
-  if (threadIdx.x == 0) {
-    for (; issued < stages && issued < total; ++issued) {
-      int chunk, row0, rows;
-      prod.cur(chunk, row0, rows);
-      uint32_t bytes = (uint32_t)rows * 128u;
-      mbar_expect_tx(&full[issued], bytes);
-      bulk_g2s(ring + (size_t)issued * stage_elems, B + ((long long)prod.p * RP + row0) * NB, bytes, &full[issued]);
-      prod.next();
-    }
-  }
-  const int g = lane & 7;      // 16-byte column group inside a row (backward)
-  const int rsub = lane >> 3;  // row slot inside a warp's 4-row group (backward)
-  T acc[E];
-#pragma unroll
-  for (int e = 0; e < E; ++e) acc[e] = 0;
-  int qfail = -1;
-  for (int q = 0; q < total; ++q) {
-    const int st = q % stages;
-    bool ok = warp_wait_phase(&full[st], (uint32_t)((q / stages) & 1));
-    if (__syncthreads_or(!ok)) {
-      qfail = q;
-      break;
-    }
-    int chunk, row0, rows;
-    cons.cur(chunk, row0, rows);
-    const T *buf = ring + (size_t)st * stage_elems;
-    const int k0 = cons.p * NB, nb = min(NB, N - k0);
-    const int rend = min(N - k0, RP);  // rows of this panel inside the matrix
-    const int lo = max(row0, nb), hi = min(row0 + rows, rend);
-    if (cons.dir == 0) {
-      if (chunk == 0) {
-        // y_blk = inv(L_kk) x_blk: row t, 16-byte group g2 per thread, reduced over the 8 groups
-        if (threadIdx.x < NB * 8) {
-          int t = threadIdx.x >> 3, g2 = threadIdx.x & 7;
-          T sacc = 0;
-#pragma unroll
-          for (int e = 0; e < E; ++e) {
-            int cc = g2 * E + e;
-            if (cc <= t && cc < nb) sacc += buf[t * NB + cc] * v[k0 + cc];
+
+  const int nsteps = 2 * np;
+  if (wid == 1) {
+    // ------------------------------------------------------------ producer
+    if (lane == 0) {
+      int c0_n = 0, far_n = 0;
+      bool ok = true;
+      for (int s = 0; s < nsteps && ok; ++s) {
+        const int p = (s < np) ? s : (2 * np - 1 - s);
+        {
+          const int slot = c0_n % c0_stages, use = c0_n / c0_stages;
+          if (use > 0 && !mbar_wait_bounded(&empty_c0[slot], (uint32_t)((use - 1) & 1), &s_abort)) {
+            ok = false;
+            break;
           }
-          sacc += __shfl_xor_sync(0xffffffffu, sacc, 4);
-          sacc += __shfl_xor_sync(0xffffffffu, sacc, 2);
-          sacc += __shfl_xor_sync(0xffffffffu, sacc, 1);
-          if (g2 == 0) vb[t] = (t < nb) ? sacc : (T)0;
+          const uint32_t bytes = (uint32_t)c0rows * 128u;
+          mbar_expect_tx(&full_c0[slot], bytes);
+          bulk_g2s(c0_ring + (size_t)slot * 2 * NB * NB, B + (long long)p * RP * NB, bytes, &full_c0[slot]);
+          ++c0_n;
         }
-        __syncthreads();
-        if (threadIdx.x < nb) v[k0 + threadIdx.x] = vb[threadIdx.x];
-      }
-      // window rows: one row per thread, 16-byte groups visited in a row-rotated order so that the 8
-      // threads of a shared-memory phase touch 8 different bank groups; 4 partial sums for ILP
-      for (int rr = lo + threadIdx.x; rr < hi; rr += SOLVE_THREADS) {
-        const T *row = buf + (size_t)(rr - row0) * NB;
-        T s0 = 0, s1 = 0, s2 = 0, s3 = 0;
-#pragma unroll
-        for (int j = 0; j < 8; j += 2) {
-          int ga = (j + rr) & 7, gb = (j + 1 + rr) & 7;
-#pragma unroll
-          for (int e = 0; e < E; e += 2) {
-            s0 += row[ga * E + e] * vb[ga * E + e];
-            s1 += row[ga * E + e + 1] * vb[ga * E + e + 1];
-            s2 += row[gb * E + e] * vb[gb * E + e];
-            s3 += row[gb * E + e + 1] * vb[gb * E + e + 1];
+        const int q = p - 1;
+        if (q >= 0) {
+          const int nf = geo.nfar(q), nc = geo.nchunks(q);
+          for (int cix = 0; cix < nc; ++cix) {
+            const int slot = far_n % far_stages, use = far_n / far_stages;
+            if (use > 0 && !mbar_wait_bounded(&empty_far[slot], (uint32_t)((use - 1) & 1), &s_abort)) {
+              ok = false;
+              break;
+            }
+            const int rows = min(WS_FAR_ROWS, nf - cix * WS_FAR_ROWS);
+            const uint32_t bytes = (uint32_t)rows * 128u;
+            mbar_expect_tx(&full_far[slot], bytes);
+            bulk_g2s(far_ring + (size_t)slot * WS_FAR_ROWS * NB,
+                     B + ((long long)q * RP + 2 * NB + (long long)cix * WS_FAR_ROWS) * NB, bytes, &full_far[slot]);
+            ++far_n;
           }
         }
-        v[k0 + rr] -= (s0 + s1) + (s2 + s3);
       }
-    } else {
-      // accumulate L[rr][:]^T x[k0 + rr] over the panel's window rows
-      for (int base = row0; base < hi; base += NW * 4) {
-        int rr = base + wid * 4 + rsub;
-        if (rr >= lo && rr < hi) {
-          const T *row = buf + (size_t)(rr - row0) * NB + g * E;
-          T xv = v[k0 + rr];
-#pragma unroll
-          for (int e = 0; e < E; ++e) acc[e] += row[e] * xv;
-        }
+      if (!ok) {
+        s_abort = 1;
+        atomicCAS(status, 0, (int)HPLMM_ERR_TIMEOUT);
       }
-      if (chunk == 0) {
-        // finish the panel: t = x_blk - acc (reduced over the 64 row slots), x_blk = inv(L_kk)^T t
+      // let every copy issued into a stage land before shared memory is released (no-op when all were consumed)
+      for (int i = 0; i < c0_stages && i < c0_n; ++i) {
+        int last = i + ((c0_n - 1 - i) / c0_stages) * c0_stages;
+        mbar_wait_bounded(&full_c0[i], (uint32_t)((last / c0_stages) & 1), nullptr);
+      }
+      for (int i = 0; i < far_stages && i < far_n; ++i) {
+        int last = i + ((far_n - 1 - i) / far_stages) * far_stages;
+        mbar_wait_bounded(&full_far[i], (uint32_t)((last / far_stages) & 1), nullptr);
+      }
+    }
+    __syncwarp();
+  } else if (wid == 0) {
+    // ------------------------------------------------------------ leader: diagonal and near blocks
+    int c0_n = 0;
+    T near = 0;
+    for (int s = 0; s < nsteps; ++s) {
+      const bool fwd = s < np;
+      const int p = fwd ? s : (2 * np - 1 - s);
+      const int k0 = p * NB, nb = min(NB, N - k0);
+      const int slot = c0_n % c0_stages;
+      int fail = 0;
+      if (!mbar_wait_bounded(&full_c0[slot], (uint32_t)((c0_n / c0_stages) & 1), &s_abort)) fail = 1;
+      if (!fail) {
+        const T *c0 = c0_ring + (size_t)slot * 2 * NB * NB;
+        const int i = lane % NB;
+        if (fwd) {
+          T x = (lane < nb) ? v[k0 + lane] - near : (T)0;
+          T y = 0;
 #pragma unroll
-        for (int e = 0; e < E; ++e) red[wid * 4 + rsub][g * E + e] = acc[e];
-        __syncthreads();
-        if (threadIdx.x < NB * 8) {
-          int cc = threadIdx.x >> 3, part = threadIdx.x & 7;
-          T sacc = 0;
-          for (int w = part; w < NW * 4; w += 8) sacc += red[w][cc];
-          sacc += __shfl_xor_sync(0xffffffffu, sacc, 4);
-          sacc += __shfl_xor_sync(0xffffffffu, sacc, 2);
-          sacc += __shfl_xor_sync(0xffffffffu, sacc, 1);
-          if (part == 0) vb[cc] = (cc < nb) ? v[k0 + cc] - sacc : (T)0;
-        }
-        __syncthreads();
-        if (threadIdx.x < NB * 8) {
-          int t = threadIdx.x >> 3, g2 = threadIdx.x & 7;
-          T sacc = 0;
-#pragma unroll
-          for (int e = 0; e < E; ++e) {
-            int cc = g2 * E + e;
-            if (cc >= t && cc < nb) sacc += buf[cc * NB + t] * vb[cc];
+          for (int j = 0; j < NB; ++j) {
+            const int jj = (j + i) % NB;
+            y += c0[i * NB + jj] * __shfl_sync(0xffffffffu, x, jj);
           }
-          sacc += __shfl_xor_sync(0xffffffffu, sacc, 4);
-          sacc += __shfl_xor_sync(0xffffffffu, sacc, 2);
-          sacc += __shfl_xor_sync(0xffffffffu, sacc, 1);
-          if (g2 == 0 && t < nb) v[k0 + t] = sacc;
-        }
+          if (lane < nb) v[k0 + lane] = y;
+          // near product for the next block (rows NB .. c0rows of the chunk)
+          // (rows at or past c0rows were not copied: their coefficients are taken as zero)
+          const bool nvalid = NB + i < c0rows;
+          T nr = 0;
 #pragma unroll
-        for (int e = 0; e < E; ++e) acc[e] = 0;
+          for (int j = 0; j < NB; ++j) {
+            const int jj = (j + i) % NB;
+            const T coef = nvalid ? c0[(NB + i) * NB + jj] : (T)0;
+            nr += coef * __shfl_sync(0xffffffffu, y, jj);
+          }
+          near = nr;
+        } else {
+          // far partial sums of panel p (bulk warps computed them in the previous step)
+          T far = 0;
+          if (p + 1 < np) {
+#pragma unroll
+            for (int w = 0; w < WS_BULK_WARPS; ++w) far += red[p & 1][w][i];
+          }
+          // near: L_{p+1,p}^T x_{p+1}; rows past the matrix hold zeros in v
+          T nt = 0;
+          const int nrows = c0rows - NB;
+          for (int rr = 0; rr < nrows; ++rr) nt += c0[(NB + rr) * NB + i] * v[k0 + NB + rr];
+          T t = (lane < nb) ? v[k0 + lane] - far - nt : (T)0;
+          T x = 0;
+#pragma unroll
+          for (int cc = 0; cc < NB; ++cc) x += c0[cc * NB + i] * __shfl_sync(0xffffffffu, t, cc);
+          if (lane < nb) v[k0 + lane] = x;
+        }
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&empty_c0[slot]);
       }
+      ++c0_n;
+      if (fail) s_abort = 1;
+      if (step_barrier_or(fail, NT_STEP)) break;
     }
-    cons.next();
-    __syncthreads();
-    // refill the stage just consumed
-    if (threadIdx.x == 0 && issued < total) {
-      int chunk2, row02, rows2;
-      prod.cur(chunk2, row02, rows2);
-      uint32_t bytes = (uint32_t)rows2 * 128u;
-      mbar_expect_tx(&full[st], bytes);
-      bulk_g2s(ring + (size_t)st * stage_elems, B + ((long long)prod.p * RP + row02) * NB, bytes, &full[st]);
-      prod.next();
-      ++issued;
+  } else {
+    // ------------------------------------------------------------ bulk: far rows of panel p-1
+    const int bw_id = wid - 2;
+    const int tb = threadIdx.x - 64;
+    const int off = tb & 7;  // this thread's rows are congruent to off modulo 8
+    int far_n = 0;
+    for (int s = 0; s < nsteps; ++s) {
+      const bool fwd = s < np;
+      const int p = fwd ? s : (2 * np - 1 - s);
+      const int q = p - 1;
+      int fail = 0;
+      if (q >= 0) {
+        const int kq = q * NB;
+        const int nf = geo.nfar(q), nc = geo.nchunks(q);
+        T acc[NB];
+        T yr[NB];
+        if (fwd) {
+          // y_{q} in rotated group order
+#pragma unroll
+          for (int g = 0; g < 8; ++g) Vec16<T>::load(v + kq + ((g + off) & 7) * E, &yr[g * E]);
+        } else {
+#pragma unroll
+          for (int e = 0; e < NB; ++e) acc[e] = 0;
+        }
+        for (int cix = 0; cix < nc; ++cix) {
+          const int slot = far_n % far_stages;
+          if (!fail && !mbar_wait_bounded(&full_far[slot], (uint32_t)((far_n / far_stages) & 1), &s_abort)) fail = 1;
+          if (!fail) {
+            const int rr = cix * WS_FAR_ROWS + tb;  // far row index
+            if (rr < nf) {
+              const T *row = far_ring + (size_t)slot * WS_FAR_ROWS * NB + (size_t)tb * NB;
+              const int vrow = kq + 2 * NB + rr;
+              if (fwd) {
+                T s0 = 0, s1 = 0;
+#pragma unroll
+                for (int g = 0; g < 8; g += 2) {
+                  T ra[E], rb[E];
+                  Vec16<T>::load(row + ((g + off) & 7) * E, ra);
+                  Vec16<T>::load(row + ((g + 1 + off) & 7) * E, rb);
+#pragma unroll
+                  for (int e = 0; e < E; ++e) {
+                    s0 += ra[e] * yr[g * E + e];
+                    s1 += rb[e] * yr[(g + 1) * E + e];
+                  }
+                }
+                v[vrow] -= s0 + s1;
+              } else {
+                const T xv = v[vrow];
+#pragma unroll
+                for (int g = 0; g < 8; ++g) {
+                  T ra[E];
+                  Vec16<T>::load(row + ((g + off) & 7) * E, ra);
+#pragma unroll
+                  for (int e = 0; e < E; ++e) acc[g * E + e] += ra[e] * xv;
+                }
+              }
+            }
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&empty_far[slot]);
+          }
+          ++far_n;
+        }
+        if (!fwd) {
+          // reduce the column sums: lanes with equal (lane & 7) share the rotation
+#pragma unroll
+          for (int e = 0; e < NB; ++e) {
+            acc[e] += __shfl_xor_sync(0xffffffffu, acc[e], 8);
+            acc[e] += __shfl_xor_sync(0xffffffffu, acc[e], 16);
+          }
+          if (lane < 8) {
+#pragma unroll
+            for (int g = 0; g < 8; ++g)
+#pragma unroll
+              for (int e = 0; e < E; ++e) stage[bw_id][lane][((g + lane) & 7) * E + e] = acc[g * E + e];
+          }
+          __syncwarp();
+          if (lane < NB) {
+            T sum = 0;
+#pragma unroll
+            for (int c = 0; c < 8; ++c) sum += stage[bw_id][c][lane];
+            red[q & 1][bw_id][lane] = sum;
+          }
+          __syncwarp();
+        }
+      }
+      if (fail) s_abort = 1;
+      if (step_barrier_or(fail, NT_STEP)) break;
     }
   }
-  if (qfail >= 0) {
-    // drain our own copies still in flight (chunks qfail .. issued-1) before shared memory is released
-    if (threadIdx.x == 0) {
-      atomicCAS(status, 0, (int)HPLMM_ERR_TIMEOUT);
-      for (int q = qfail; q < issued; ++q) mbar_wait_bounded(&full[q % stages], (uint32_t)((q / stages) & 1));
-    }
-    __syncthreads();
-    return;
-  }
-  for (int l = threadIdx.x; l < N; l += SOLVE_THREADS) {
+  __syncthreads();
+  if (s_abort) return;
+  for (int l = threadIdx.x; l < N; l += WS_THREADS) {
     int o = l / 3, d = l - 3 * o;
     long long slot = 3LL * ln[o] + d;
     if (atomic)
@@ -990,32 +1103,33 @@ void smoother_apply(hplmm_ctx *c, LocalSet &S, const double *r_pad, double *z_pa
   if (S.count == 0) return;
   ProfScope ps(c, (&S == &c->grains) ? HPLMM_PH_APPLY_GRAINS : HPLMM_PH_APPLY_CONTACTS);
   cudaStream_t s = c->stream;
-  int nmax = 0;
-  for (int k = 0; k < S.count; ++k) nmax = std::max(nmax, S.h_n[k]);
-  // shared memory: the local vector, then a ring of 2..4 stages of large row chunks (>= NB rows each)
-  const size_t budget = 200 * 1024;
-  int rpmax = 0;
+  const bool f64 = S.prec == HPLMM_FP64;
+  const int NBv = f64 ? 16 : 32;
+  const size_t esz = f64 ? 8 : 4;
+  // shared memory: far ring (32 KiB stages), diagonal+near ring (2 NB rows of 128 bytes), padded local vector
+  int vmax = 0;
   for (int k = 0; k < S.count; ++k)
-    if (S.h_n[k] > 0) rpmax = std::max(rpmax, S.h_bw[k] + (S.prec == HPLMM_FP64 ? 16 : 32));
-  const int NBv = S.prec == HPLMM_FP64 ? 16 : 32;
-  const size_t esz = S.prec == HPLMM_FP64 ? 8 : 4;
-  size_t vbytes = ((esz * (size_t)std::max(nmax, 1) + 127) / 128) * 128;
-  HP_REQUIRE(vbytes + 2 * (size_t)NBv * 128 <= budget, HPLMM_ERR_INVALID, "local problem too large for the smoother");
-  size_t ring = budget - vbytes;
-  int stages = ring >= 3 * 40960 ? 3 : 2;
-  int CH = (int)std::min<size_t>(ring / stages / 128, 768);  // rows per chunk (at most 96 KiB)
-  CH = std::max(NBv, std::min(CH, std::max(rpmax, NBv)));
-  size_t smem = (size_t)stages * CH * 128 + vbytes;
-  if (S.prec == HPLMM_FP64) {
-    auto kern = k_band_solve_one<double, 16>;
+    if (S.h_n[k] > 0) vmax = std::max(vmax, ((S.h_n[k] + NBv - 1) / NBv) * NBv + NBv);
+  const size_t vbytes = ((esz * (size_t)std::max(vmax, 1) + 127) / 128) * 128;
+  const size_t far_stage = (size_t)WS_FAR_ROWS * 128, c0_stage = (size_t)2 * NBv * 128;
+  const size_t budget = 216 * 1024;
+  int c0s = 3;
+  HP_REQUIRE(vbytes + c0s * c0_stage + 2 * far_stage <= budget, HPLMM_ERR_INVALID,
+             "local problem too large for the smoother (" + std::to_string(vmax) + " local DOFs)");
+  int fs = (int)std::min<size_t>(WS_MAX_FAR_STAGES, (budget - vbytes - c0s * c0_stage) / far_stage);
+  if (S.tuned_far_stages > 0) fs = std::min(fs, S.tuned_far_stages);
+  if (S.tuned_c0_stages > 0) c0s = S.tuned_c0_stages;
+  const size_t smem = (size_t)fs * far_stage + (size_t)c0s * c0_stage + vbytes;
+  if (f64) {
+    auto kern = k_band_solve_ws<double, 16>;
     HP_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    kern<<<S.count, SOLVE_THREADS, smem, s>>>(S.count, S.n.p, S.bw.p, S.band_off.p, S.node_off.p, S.lnodes.p,
-                                              S.band64.p, r_pad, z_pad, atomic ? 1 : 0, CH, stages, c->status.p);
+    kern<<<S.count, WS_THREADS, smem, s>>>(S.count, S.n.p, S.bw.p, S.band_off.p, S.node_off.p, S.lnodes.p,
+                                           S.band64.p, r_pad, z_pad, atomic ? 1 : 0, fs, c0s, c->status.p);
   } else {
-    auto kern = k_band_solve_one<float, 32>;
+    auto kern = k_band_solve_ws<float, 32>;
     HP_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    kern<<<S.count, SOLVE_THREADS, smem, s>>>(S.count, S.n.p, S.bw.p, S.band_off.p, S.node_off.p, S.lnodes.p,
-                                              S.band32.p, r_pad, z_pad, atomic ? 1 : 0, CH, stages, c->status.p);
+    kern<<<S.count, WS_THREADS, smem, s>>>(S.count, S.n.p, S.bw.p, S.band_off.p, S.node_off.p, S.lnodes.p,
+                                           S.band32.p, r_pad, z_pad, atomic ? 1 : 0, fs, c0s, c->status.p);
   }
   HP_CHECK_LAUNCH();
 }
