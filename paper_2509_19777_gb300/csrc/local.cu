@@ -500,9 +500,12 @@ __global__ void __launch_bounds__(256) k_band_solve_multi(const int *items, int 
 //   - the bulk warps handle the "far" rows (beyond the near block) of panel p-1, one row per thread:
 //       forward  v[rows] -= L_far(p-1) y_{p-1};
 //       backward far_{p-1} = L_far(p-1)^T v[rows] (column sums reduced per warp);
-//   - a producer warp streams the factor with bulk asynchronous copies (cp.async.bulk) into two rings of
-//     shared-memory stages (the diagonal+near chunk of each panel, and the far rows in chunks of one row
-//     per bulk thread), guarded by full/empty mbarriers, running ahead of the consumers.
+//   - a producer warp streams the far rows with bulk asynchronous copies (cp.async.bulk) into a ring of
+//     shared-memory stages guarded by full/empty mbarriers, running ahead of the consumers.  On this GPU a
+//     bulk copy costs about half a microsecond of serialised copy-engine time per SM almost regardless of
+//     its size up to 64 KiB, so the chunks are large (FAR_ROWS_PER_THREAD rows per bulk thread, 64 KiB);
+//   - the leader warp fetches its own small diagonal+near chunks with coalesced 16-byte cp.async copies a
+//     few steps ahead (a bulk copy of 8 KiB would cost as much engine time as one of 64 KiB).
 // The leader and bulk warps meet once per step on a named barrier that also ORs their error flags.  Every
 // wait is bounded; on expiry the kernel records HPLMM_ERR_TIMEOUT, lets every copy in flight land and
 // returns without writing z.
@@ -514,10 +517,12 @@ __global__ void __launch_bounds__(256) k_band_solve_multi(const int *items, int 
 // shared-memory phase therefore touch 8 different bank groups.
 constexpr int WS_BULK_WARPS = 8;
 constexpr int WS_THREADS = (2 + WS_BULK_WARPS) * 32;
-constexpr int WS_FAR_ROWS = WS_BULK_WARPS * 32;  // rows per far chunk: one per bulk thread
+// far rows per bulk thread per chunk: 2 for FP32 factors (64 KiB chunks), 1 for FP64 (32 KiB chunks, since
+// the FP64 local vector already takes half of the shared memory)
+template <typename T> constexpr int far_rpt() { return sizeof(T) == 4 ? 2 : 1; }
 constexpr int WS_MAX_FAR_STAGES = 8;
-constexpr int WS_MAX_C0_STAGES = 4;
-constexpr long long WAIT_CYCLES = 4000000000LL;  // about two seconds of SM clock
+constexpr int WS_MAX_C0_STAGES = 8;
+constexpr long long WAIT_LIMIT = 1LL << 26;
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -547,16 +552,13 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
   return done != 0;
 }
 
-// bounded wait (about two seconds); gives up early when another warp has raised the abort flag
+// bounded wait; gives up early when another warp has raised the abort flag
 __device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity, const volatile int *abort_flag) {
-  const long long t0 = clock64();
-  for (long long it = 0;; ++it) {
+  for (long long it = 0; it < WAIT_LIMIT; ++it) {
     if (mbar_try_wait(bar, parity)) return true;
-    if ((it & 63) == 63) {
-      if (abort_flag && *abort_flag) return false;
-      if (clock64() - t0 > WAIT_CYCLES) return false;
-    }
+    if ((it & 63) == 63 && abort_flag && *abort_flag) return false;
   }
+  return false;
 }
 
 __device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
@@ -578,6 +580,24 @@ __device__ __forceinline__ int step_barrier_or(int flag, int nthreads) {
   return res;
 }
 
+__device__ __forceinline__ void cp_async16(void *dst, const void *src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+// wait until at most n of this thread's most recent cp.async groups are pending (n small, runtime)
+__device__ __forceinline__ void cp_async_wait_pending(int n) {
+  switch (n) {
+    case 0: asm volatile("cp.async.wait_group 0;" ::: "memory"); break;
+    case 1: asm volatile("cp.async.wait_group 1;" ::: "memory"); break;
+    case 2: asm volatile("cp.async.wait_group 2;" ::: "memory"); break;
+    case 3: asm volatile("cp.async.wait_group 3;" ::: "memory"); break;
+    case 4: asm volatile("cp.async.wait_group 4;" ::: "memory"); break;
+    case 5: asm volatile("cp.async.wait_group 5;" ::: "memory"); break;
+    case 6: asm volatile("cp.async.wait_group 6;" ::: "memory"); break;
+    default: asm volatile("cp.async.wait_group 7;" ::: "memory"); break;
+  }
+}
+
 // 16-byte group loads of a factor row
 template <typename T> struct Vec16;
 template <> struct Vec16<float> {
@@ -595,10 +615,10 @@ template <> struct Vec16<double> {
 
 // geometry of panel p: rows of the panel inside the matrix, and its far rows [2 NB, rend)
 struct PanelGeo {
-  int N, NB, RP;
+  int N, NB, RP, FR;  // FR = rows per far chunk
   __device__ int rend(int p) const { return min(N - p * NB, RP); }
   __device__ int nfar(int p) const { return max(0, rend(p) - 2 * NB); }
-  __device__ int nchunks(int p) const { return (nfar(p) + WS_FAR_ROWS - 1) / WS_FAR_ROWS; }
+  __device__ int nchunks(int p) const { return (nfar(p) + FR - 1) / FR; }
   __device__ int c0rows() const { return min(2 * NB, RP); }
 };
 
@@ -611,9 +631,10 @@ __global__ void __launch_bounds__(WS_THREADS) k_band_solve_ws(int count, const i
   static_assert(NB * sizeof(T) == 128, "factor rows are 128 bytes");
   constexpr int E = 16 / sizeof(T);  // elements per 16-byte group
   constexpr int NT_STEP = (1 + WS_BULK_WARPS) * 32;
+  constexpr int RPT = far_rpt<T>();
+  constexpr int WS_FAR_ROWS = WS_BULK_WARPS * 32 * RPT;
   extern __shared__ __align__(128) unsigned char smdyn[];
   __shared__ __align__(8) uint64_t full_far[WS_MAX_FAR_STAGES], empty_far[WS_MAX_FAR_STAGES];
-  __shared__ __align__(8) uint64_t full_c0[WS_MAX_C0_STAGES], empty_c0[WS_MAX_C0_STAGES];
   __shared__ T red[2][WS_BULK_WARPS][NB];
   __shared__ T stage[WS_BULK_WARPS][8][NB];
   __shared__ volatile int s_abort;
@@ -626,7 +647,7 @@ __global__ void __launch_bounds__(WS_THREADS) k_band_solve_ws(int count, const i
   const int RP = NB + bw;
   const int np = (N + NB - 1) / NB;
   const int VN = np * NB + NB;  // padded local vector
-  const PanelGeo geo{N, NB, RP};
+  const PanelGeo geo{N, NB, RP, WS_FAR_ROWS};
   const T *B = band + band_off[k];
   const int *ln = lnodes + node_off[k];
   T *far_ring = reinterpret_cast<T *>(smdyn);
@@ -638,10 +659,6 @@ __global__ void __launch_bounds__(WS_THREADS) k_band_solve_ws(int count, const i
     for (int i = 0; i < far_stages; ++i) {
       mbar_init(&full_far[i], 1);
       mbar_init(&empty_far[i], WS_BULK_WARPS);
-    }
-    for (int i = 0; i < c0_stages; ++i) {
-      mbar_init(&full_c0[i], 1);
-      mbar_init(&empty_c0[i], 1);
     }
     s_abort = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -660,21 +677,10 @@ __global__ void __launch_bounds__(WS_THREADS) k_band_solve_ws(int count, const i
   if (wid == 1) {
     // ------------------------------------------------------------ producer
     if (lane == 0) {
-      int c0_n = 0, far_n = 0;
+      int far_n = 0;
       bool ok = true;
       for (int s = 0; s < nsteps && ok; ++s) {
         const int p = (s < np) ? s : (2 * np - 1 - s);
-        {
-          const int slot = c0_n % c0_stages, use = c0_n / c0_stages;
-          if (use > 0 && !mbar_wait_bounded(&empty_c0[slot], (uint32_t)((use - 1) & 1), &s_abort)) {
-            ok = false;
-            break;
-          }
-          const uint32_t bytes = (uint32_t)c0rows * 128u;
-          mbar_expect_tx(&full_c0[slot], bytes);
-          bulk_g2s(c0_ring + (size_t)slot * 2 * NB * NB, B + (long long)p * RP * NB, bytes, &full_c0[slot]);
-          ++c0_n;
-        }
         const int q = p - 1;
         if (q >= 0) {
           const int nf = geo.nfar(q), nc = geo.nchunks(q);
@@ -698,29 +704,36 @@ __global__ void __launch_bounds__(WS_THREADS) k_band_solve_ws(int count, const i
         atomicCAS(status, 0, (int)HPLMM_ERR_TIMEOUT);
       }
       // let every copy issued into a stage land before shared memory is released (no-op when all were consumed)
-      for (int i = 0; i < c0_stages && i < c0_n; ++i) {
-        int last = i + ((c0_n - 1 - i) / c0_stages) * c0_stages;
-        mbar_wait_bounded(&full_c0[i], (uint32_t)((last / c0_stages) & 1), nullptr);
-      }
       for (int i = 0; i < far_stages && i < far_n; ++i) {
         int last = i + ((far_n - 1 - i) / far_stages) * far_stages;
         mbar_wait_bounded(&full_far[i], (uint32_t)((last / far_stages) & 1), nullptr);
       }
     }
-    __syncwarp();
   } else if (wid == 0) {
     // ------------------------------------------------------------ leader: diagonal and near blocks
-    int c0_n = 0;
+    // the chunk of step s lives in slot s % c0_stages; lane l copies the 16-byte pieces l, l+32, ...
+    auto issue_c0 = [&](int s) {
+      if (s < nsteps) {
+        const int p = (s < np) ? s : (2 * np - 1 - s);
+        const unsigned char *src = reinterpret_cast<const unsigned char *>(B + (long long)p * RP * NB);
+        unsigned char *dst = reinterpret_cast<unsigned char *>(c0_ring + (size_t)(s % c0_stages) * 2 * NB * NB);
+        for (int piece = lane; piece < c0rows * 8; piece += 32) cp_async16(dst + piece * 16, src + piece * 16);
+      }
+      cp_async_commit();
+    };
+    for (int s = 0; s < c0_stages - 1; ++s) issue_c0(s);
     T near = 0;
     for (int s = 0; s < nsteps; ++s) {
       const bool fwd = s < np;
       const int p = fwd ? s : (2 * np - 1 - s);
       const int k0 = p * NB, nb = min(NB, N - k0);
-      const int slot = c0_n % c0_stages;
+      // refill the slot read during step s-1 (every lane finished it before the last step barrier)
+      issue_c0(s + c0_stages - 1);
+      cp_async_wait_pending(c0_stages - 1);
+      __syncwarp();
       int fail = 0;
-      if (!mbar_wait_bounded(&full_c0[slot], (uint32_t)((c0_n / c0_stages) & 1), &s_abort)) fail = 1;
-      if (!fail) {
-        const T *c0 = c0_ring + (size_t)slot * 2 * NB * NB;
+      {
+        const T *c0 = c0_ring + (size_t)(s % c0_stages) * 2 * NB * NB;
         const int i = lane % NB;
         if (fwd) {
           T x = (lane < nb) ? v[k0 + lane] - near : (T)0;
@@ -732,14 +745,16 @@ __global__ void __launch_bounds__(WS_THREADS) k_band_solve_ws(int count, const i
           }
           if (lane < nb) v[k0 + lane] = y;
           // near product for the next block (rows NB .. c0rows of the chunk)
-          // (rows at or past c0rows were not copied: their coefficients are taken as zero)
-          const bool nvalid = NB + i < c0rows;
           T nr = 0;
+          if (NB + i < c0rows) {
 #pragma unroll
-          for (int j = 0; j < NB; ++j) {
-            const int jj = (j + i) % NB;
-            const T coef = nvalid ? c0[(NB + i) * NB + jj] : (T)0;
-            nr += coef * __shfl_sync(0xffffffffu, y, jj);
+            for (int j = 0; j < NB; ++j) {
+              const int jj = (j + i) % NB;
+              nr += c0[(NB + i) * NB + jj] * __shfl_sync(0xffffffffu, y, jj);
+            }
+          } else {
+#pragma unroll
+            for (int j = 0; j < NB; ++j) (void)__shfl_sync(0xffffffffu, y, j);
           }
           near = nr;
         } else {
@@ -759,10 +774,7 @@ __global__ void __launch_bounds__(WS_THREADS) k_band_solve_ws(int count, const i
           for (int cc = 0; cc < NB; ++cc) x += c0[cc * NB + i] * __shfl_sync(0xffffffffu, t, cc);
           if (lane < nb) v[k0 + lane] = x;
         }
-        __syncwarp();
-        if (lane == 0) mbar_arrive(&empty_c0[slot]);
       }
-      ++c0_n;
       if (fail) s_abort = 1;
       if (step_barrier_or(fail, NT_STEP)) break;
     }
@@ -794,9 +806,11 @@ __global__ void __launch_bounds__(WS_THREADS) k_band_solve_ws(int count, const i
           const int slot = far_n % far_stages;
           if (!fail && !mbar_wait_bounded(&full_far[slot], (uint32_t)((far_n / far_stages) & 1), &s_abort)) fail = 1;
           if (!fail) {
-            const int rr = cix * WS_FAR_ROWS + tb;  // far row index
+#pragma unroll
+           for (int h = 0; h < RPT; ++h) {
+            const int rr = cix * WS_FAR_ROWS + h * (WS_BULK_WARPS * 32) + tb;  // far row index (same offset mod 8)
             if (rr < nf) {
-              const T *row = far_ring + (size_t)slot * WS_FAR_ROWS * NB + (size_t)tb * NB;
+              const T *row = far_ring + (size_t)slot * WS_FAR_ROWS * NB + (size_t)(h * WS_BULK_WARPS * 32 + tb) * NB;
               const int vrow = kq + 2 * NB + rr;
               if (fwd) {
                 T s0 = 0, s1 = 0;
@@ -823,6 +837,7 @@ __global__ void __launch_bounds__(WS_THREADS) k_band_solve_ws(int count, const i
                 }
               }
             }
+           }
             __syncwarp();
             if (lane == 0) mbar_arrive(&empty_far[slot]);
           }
@@ -855,6 +870,7 @@ __global__ void __launch_bounds__(WS_THREADS) k_band_solve_ws(int count, const i
       if (step_barrier_or(fail, NT_STEP)) break;
     }
   }
+  cp_async_wait_pending(0);
   __syncthreads();
   if (s_abort) return;
   for (int l = threadIdx.x; l < N; l += WS_THREADS) {
@@ -1111,9 +1127,10 @@ void smoother_apply(hplmm_ctx *c, LocalSet &S, const double *r_pad, double *z_pa
   for (int k = 0; k < S.count; ++k)
     if (S.h_n[k] > 0) vmax = std::max(vmax, ((S.h_n[k] + NBv - 1) / NBv) * NBv + NBv);
   const size_t vbytes = ((esz * (size_t)std::max(vmax, 1) + 127) / 128) * 128;
-  const size_t far_stage = (size_t)WS_FAR_ROWS * 128, c0_stage = (size_t)2 * NBv * 128;
+  const size_t far_stage = (size_t)WS_BULK_WARPS * 32 * (f64 ? far_rpt<double>() : far_rpt<float>()) * 128;
+  const size_t c0_stage = (size_t)2 * NBv * 128;
   const size_t budget = 216 * 1024;
-  int c0s = 3;
+  int c0s = 4;
   HP_REQUIRE(vbytes + c0s * c0_stage + 2 * far_stage <= budget, HPLMM_ERR_INVALID,
              "local problem too large for the smoother (" + std::to_string(vmax) + " local DOFs)");
   int fs = (int)std::min<size_t>(WS_MAX_FAR_STAGES, (budget - vbytes - c0s * c0_stage) / far_stage);
