@@ -245,22 +245,58 @@ __global__ void k_scatter_free(const int *dof_slot, const double *dof, double *p
   if (i < n_dof) pad[dof_slot[i]] = dof[i];
 }
 
-// y = A x (or y = sub - A x when sub != nullptr); one thread per node row, 3x3 blocks
+// ---------------------------------------------------------------- sliced-ELL copy of A_hat for the SpMV
+// Rows are grouped in slices of 32 consecutive nodes (one warp); a slice is padded to its longest row, and
+// stored slot-major with the 9 block entries of a slot element-major, so that every load of the SpMV is one
+// contiguous 128-byte (FP32) or 256-byte (FP64) access across the warp.  Padding slots point at the row's
+// own node with zero values.
+__global__ void k_sell_width(const int *row_ptr, int n_nodes, int n_slices, int *width) {
+  int sl = blockIdx.x * blockDim.x + threadIdx.x;
+  if (sl >= n_slices) return;
+  int w = 0;
+  for (int r = sl * 32; r < min(n_nodes, sl * 32 + 32); ++r) w = max(w, row_ptr[r + 1] - row_ptr[r]);
+  width[sl] = 32 * w;  // entries of the slice
+}
+
+__global__ void k_sell_fill(const int *row_ptr, const int *col, const double *val, int n_nodes,
+                            const int *slice_off, int *scol, double *sval64, float *sval32) {
+  int n = blockIdx.x * blockDim.x + threadIdx.x;
+  int sl = n >> 5, lane = n & 31;
+  if (sl * 32 >= n_nodes) return;
+  long long base = slice_off[sl];
+  int w = (slice_off[sl + 1] - slice_off[sl]) / 32;
+  int b = (n < n_nodes) ? row_ptr[n] : 0, len = (n < n_nodes) ? row_ptr[n + 1] - b : 0;
+  for (int j = 0; j < w; ++j) {
+    long long ent = base + (long long)j * 32 + lane;
+    scol[ent] = (j < len) ? col[b + j] : (n < n_nodes ? n : 0);
+    for (int e = 0; e < 9; ++e) {
+      double v = (j < len) ? val[(long long)(b + j) * 9 + e] : 0.0;
+      long long at = (base + (long long)j * 32) * 9 + (long long)e * 32 + lane;
+      sval64[at] = v;
+      sval32[at] = (float)v;
+    }
+  }
+}
+
+// y = A x (or y = sub - A x when sub != nullptr) on the sliced-ELL copy; one thread per node row
 template <typename T>
-__global__ void k_spmv(const int *row_ptr, const int *col, const T *val, const double *x, double *y,
-                       const double *sub, int n_nodes) {
+__global__ void k_spmv_sell(const int *slice_off, const int *scol, const T *sval, const double *x, double *y,
+                            const double *sub, int n_nodes) {
   int n = blockIdx.x * blockDim.x + threadIdx.x;
   if (n >= n_nodes) return;
   using A = typename std::conditional<std::is_same<T, double>::value, double, float>::type;
+  const int sl = n >> 5, lane = n & 31;
+  const long long base = slice_off[sl];
+  const int w = (slice_off[sl + 1] - slice_off[sl]) >> 5;
   A s0 = 0, s1 = 0, s2 = 0;
-  int e = row_ptr[n + 1];
-  for (int p = row_ptr[n]; p < e; ++p) {
-    int m = col[p];
-    const T *v = val + (long long)p * 9;
+  for (int j = 0; j < w; ++j) {
+    const long long slot = base + (long long)j * 32;
+    const int m = scol[slot + lane];
+    const T *v = sval + slot * 9 + lane;
     A x0 = (A)x[3 * m], x1 = (A)x[3 * m + 1], x2 = (A)x[3 * m + 2];
-    s0 += (A)v[0] * x0 + (A)v[1] * x1 + (A)v[2] * x2;
-    s1 += (A)v[3] * x0 + (A)v[4] * x1 + (A)v[5] * x2;
-    s2 += (A)v[6] * x0 + (A)v[7] * x1 + (A)v[8] * x2;
+    s0 += (A)v[0] * x0 + (A)v[32] * x1 + (A)v[64] * x2;
+    s1 += (A)v[96] * x0 + (A)v[128] * x1 + (A)v[160] * x2;
+    s2 += (A)v[192] * x0 + (A)v[224] * x1 + (A)v[256] * x2;
   }
   if (sub) {
     y[3 * n] = sub[3 * n] - (double)s0;
@@ -360,6 +396,24 @@ void assemble(hplmm_ctx *c, const uint8_t *mask, int nx, int ny, int nz, const f
   c->dof_slot.alloc(c->n_dof);
   k_free_finalize<<<grid_for(nslot, 256), 256, 0, s>>>(c->fixed.p, c->free_index.p, c->dof_slot.p, nslot);
   HP_CHECK_LAUNCH();
+  // sliced-ELL copies (FP64 and the FP32 shadow) for the SpMV; the CSR FP32 values are then dropped
+  {
+    int nsl = (int)((nn + 31) / 32);
+    c->sell_off.alloc(nsl + 1);
+    k_sell_width<<<grid_for(nsl, 256), 256, 0, s>>>(c->row_ptr.p, c->n_nodes, nsl, c->sell_off.p);
+    HP_CHECK_LAUNCH();
+    HP_CUDA(cudaMemsetAsync(c->sell_off.p + nsl, 0, sizeof(int), s));
+    long long nent = exclusive_scan_i32(c->sell_off.p, c->sell_off.p, nsl + 1, s);
+    HP_REQUIRE(nent < (1LL << 31), HPLMM_ERR_INVALID, "assemble: too many blocks for 32-bit SpMV offsets");
+    c->sell_col.alloc(nent);
+    c->sell_val64.alloc(nent * 9);
+    c->sell_val32.alloc(nent * 9);
+    k_sell_fill<<<grid_for((long long)nsl * 32, 128), 128, 0, s>>>(c->row_ptr.p, c->col.p, c->val64.p, c->n_nodes,
+                                                                   c->sell_off.p, c->sell_col.p, c->sell_val64.p,
+                                                                   c->sell_val32.p);
+    HP_CHECK_LAUNCH();
+    c->val32.release();
+  }
   if (b_out) gather_free(c, c->b_pad.p, b_out);
   HP_CUDA(cudaStreamSynchronize(s));
   c->assembled = true;
@@ -379,11 +433,13 @@ void scatter_free(hplmm_ctx *c, const double *dof, double *pad) {
 void spmv(hplmm_ctx *c, const double *x_pad, double *y_pad, hplmm_prec prec, const double *sub) {
   ProfScope ps(c, HPLMM_PH_SPMV);
   if (prec == HPLMM_FP64) {
-    k_spmv<double><<<grid_for(c->n_nodes, 128), 128, 0, c->stream>>>(c->row_ptr.p, c->col.p, c->val64.p, x_pad,
-                                                                      y_pad, sub, c->n_nodes);
+    k_spmv_sell<double><<<grid_for(c->n_nodes, 128), 128, 0, c->stream>>>(c->sell_off.p, c->sell_col.p,
+                                                                           c->sell_val64.p, x_pad, y_pad, sub,
+                                                                           c->n_nodes);
   } else {
-    k_spmv<float><<<grid_for(c->n_nodes, 128), 128, 0, c->stream>>>(c->row_ptr.p, c->col.p, c->val32.p, x_pad,
-                                                                     y_pad, sub, c->n_nodes);
+    k_spmv_sell<float><<<grid_for(c->n_nodes, 128), 128, 0, c->stream>>>(c->sell_off.p, c->sell_col.p,
+                                                                          c->sell_val32.p, x_pad, y_pad, sub,
+                                                                          c->n_nodes);
   }
   HP_CHECK_LAUNCH();
 }

@@ -158,7 +158,11 @@ struct hplmm_ctx {
   hp::Buf<int> row_ptr, col;       // BSR over nodes, 3x3 blocks
   long long nnzb = 0;
   hp::Buf<double> val64;           // nnzb*9, fixed rows/cols zeroed
-  hp::Buf<float> val32;            // FP32 shadow
+  hp::Buf<float> val32;            // FP32 shadow (assembly only; released once the sliced copy exists)
+  hp::Buf<int> sell_off;           // sliced ELL (32-node slices): entry offset of each slice, n_slices+1
+  hp::Buf<int> sell_col;           // block column per entry (slot-major within a slice)
+  hp::Buf<double> sell_val64;      // 9 values per entry, element-major within a slot
+  hp::Buf<float> sell_val32;
   hp::Buf<double> b_pad;           // n_nodes*3 right-hand side, 0 on fixed slots
   hp::Buf<double> b_corr;          // right-hand side defining the correction columns (padded)
 

@@ -26,6 +26,30 @@ namespace {
 
 constexpr int FACT_THREADS = 256;
 
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+// 16-byte asynchronous global->shared copies (cp.async), tracked per thread in commit groups
+__device__ __forceinline__ void cp_async16(void *dst, const void *src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+// wait until at most n of this thread's most recent cp.async groups are pending (n small, runtime)
+__device__ __forceinline__ void cp_async_wait_pending(int n) {
+  switch (n) {
+    case 0: asm volatile("cp.async.wait_group 0;" ::: "memory"); break;
+    case 1: asm volatile("cp.async.wait_group 1;" ::: "memory"); break;
+    case 2: asm volatile("cp.async.wait_group 2;" ::: "memory"); break;
+    case 3: asm volatile("cp.async.wait_group 3;" ::: "memory"); break;
+    case 4: asm volatile("cp.async.wait_group 4;" ::: "memory"); break;
+    case 5: asm volatile("cp.async.wait_group 5;" ::: "memory"); break;
+    case 6: asm volatile("cp.async.wait_group 6;" ::: "memory"); break;
+    default: asm volatile("cp.async.wait_group 7;" ::: "memory"); break;
+  }
+}
+
+
 __device__ __forceinline__ long long panel_addr(int i, int j, int NB, int bw) {
   int p = j / NB, c = j - p * NB, r = i - p * NB;
   return (long long)p * (NB + bw) * NB + (long long)r * NB + c;
@@ -379,6 +403,207 @@ __global__ void __launch_bounds__(FACT_THREADS) k_band_chol(const int *order, in
   }
 }
 
+// FP32 banded Cholesky, one CTA per problem (persistent, problems taken from a cost-ordered queue).
+// Per panel of NB = 32 columns:
+//   1. the panel's rows [0, R) are loaded into shared memory (row stride 36 floats: rows start in
+//      different 16-byte bank groups, so per-thread 16-byte row reads are conflict-free);
+//   2. warp 0 factorises the 32x32 diagonal block with the rows held in registers (lane r = row r,
+//      columns broadcast by shuffles) and forms inv(L_kk) column by column (lane j = column j);
+//   3. every thread turns its rows of the sub-diagonal block into L rows: L_r = A_r inv(L_kk)^T;
+//   4. the panel (inv(L_kk) in its first 32 rows, then the L rows) is written back;
+//   5. the trailing update A_ij -= L_i . L_j of the (R-32)^2 lower window is done in 32x32 warp tiles:
+//      lane = column j (its L row in 32 registers), 32 row accumulators, the A row operand broadcast by
+//      16-byte shared-memory loads, and the tile's old values loaded from the band before the arithmetic
+//      so that their latency is hidden behind the 1024 multiply-adds.
+constexpr int CHOL32_THREADS = 256;
+constexpr int CHOL32_LD = 36;
+
+__global__ void __launch_bounds__(CHOL32_THREADS, 1) k_band_chol32(const int *order, int count, int *queue,
+                                                                const int *nloc, const int *bwv,
+                                                                const long long *band_off, float *band, int *status,
+                                                                int where, int bwv_max) {
+  constexpr int NB = 32, LD = CHOL32_LD;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  float *P = reinterpret_cast<float *>(smraw);
+  __shared__ __align__(16) float Lk[NB][LD];
+  __shared__ __align__(16) float Dv[NB][LD];
+  __shared__ int s_job;
+  float *Cst = P + (size_t)(NB + bwv_max) * LD;  // per-warp 32x32 staging of the trailing tiles
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = CHOL32_THREADS / 32;
+  for (;;) {
+    if (threadIdx.x == 0) s_job = atomicAdd(queue, 1);
+    __syncthreads();
+    const int job = s_job;
+    __syncthreads();
+    if (job >= count) return;
+    const int k = order[job];
+    const int N = nloc[k], bw = bwv[k];
+    if (N == 0) continue;
+    float *B = band + band_off[k];
+    const int RP = NB + bw;
+    for (int k0 = 0, p = 0; k0 < N; k0 += NB, ++p) {
+      const int nb = min(NB, N - k0);
+      const int R = min(N - k0, RP);
+      float *Bp = B + (long long)p * RP * NB;
+      // 1. load rows [0, R): 8 float4 per row
+      {
+        const float4 *src = reinterpret_cast<const float4 *>(Bp);
+        const int n4 = R * 8;
+        int e = threadIdx.x;
+        for (; e + 3 * CHOL32_THREADS < n4; e += 4 * CHOL32_THREADS) {
+          float4 v0 = src[e], v1 = src[e + CHOL32_THREADS], v2 = src[e + 2 * CHOL32_THREADS],
+                 v3 = src[e + 3 * CHOL32_THREADS];
+          *reinterpret_cast<float4 *>(P + (e >> 3) * LD + (e & 7) * 4) = v0;
+          int e1 = e + CHOL32_THREADS, e2 = e + 2 * CHOL32_THREADS, e3 = e + 3 * CHOL32_THREADS;
+          *reinterpret_cast<float4 *>(P + (e1 >> 3) * LD + (e1 & 7) * 4) = v1;
+          *reinterpret_cast<float4 *>(P + (e2 >> 3) * LD + (e2 & 7) * 4) = v2;
+          *reinterpret_cast<float4 *>(P + (e3 >> 3) * LD + (e3 & 7) * 4) = v3;
+        }
+        for (; e < n4; e += CHOL32_THREADS) *reinterpret_cast<float4 *>(P + (e >> 3) * LD + (e & 7) * 4) = src[e];
+      }
+      __syncthreads();
+      // 2. diagonal block (warp 0)
+      if (wid == 0) {
+        const int r = lane;
+        float a[NB];
+#pragma unroll
+        for (int c = 0; c < NB; ++c) a[c] = (r < nb && c < nb && c <= r) ? P[r * LD + c] : 0.f;
+#pragma unroll
+        for (int cc = 0; cc < NB; ++cc) {
+          if (cc < nb) {
+            float d = __shfl_sync(0xffffffffu, a[cc], cc);
+            if (!(d > 0.f)) {
+              if (lane == 0 && atomicCAS(status, 0, (int)HPLMM_ERR_SINGULAR) == 0) {
+                status[1] = where;
+                status[2] = k;
+                status[3] = k0 + cc;
+              }
+              d = 1.f;
+            }
+            const float sd = sqrtf(d);
+            const float l = (r > cc) ? a[cc] / sd : (r == cc ? sd : 0.f);
+            a[cc] = l;
+#pragma unroll
+            for (int c2 = cc + 1; c2 < NB; ++c2) {
+              const float l2 = __shfl_sync(0xffffffffu, l, c2);
+              if (c2 <= r) a[c2] -= l * l2;
+            }
+          }
+        }
+        // L_kk rows to shared memory (identity on the padding rows, so the inverse stays defined)
+#pragma unroll
+        for (int c = 0; c < NB; ++c) Lk[r][c] = (r < nb) ? ((c <= r) ? a[c] : 0.f) : (c == r ? 1.f : 0.f);
+        __syncwarp();
+        // column j = lane of inv(L_kk): y_i = (delta_ij - sum_{q<i} L_iq y_q) / L_ii
+        const int j = lane;
+        float y[NB];
+#pragma unroll
+        for (int i = 0; i < NB; ++i) {
+          float s = (i == j) ? 1.f : 0.f;
+#pragma unroll
+          for (int q = 0; q < i; ++q) s -= Lk[i][q] * y[q];
+          y[i] = s / Lk[i][i];
+        }
+#pragma unroll
+        for (int i = 0; i < NB; ++i) Dv[i][j] = (i < nb && j < nb) ? y[i] : 0.f;
+      }
+      __syncthreads();
+      // 3. L rows of the sub-diagonal block: L_r[cc] = sum_{q <= cc} A_r[q] inv[cc][q] (row r is read into
+      //    registers first, so each thread overwrites only its own row)
+      for (int r = nb + threadIdx.x; r < R; r += CHOL32_THREADS) {
+        float ar[NB];
+#pragma unroll
+        for (int g = 0; g < 8; ++g) {
+          float4 t = *reinterpret_cast<const float4 *>(P + r * LD + 4 * g);
+          ar[4 * g] = t.x; ar[4 * g + 1] = t.y; ar[4 * g + 2] = t.z; ar[4 * g + 3] = t.w;
+        }
+#pragma unroll 1
+        for (int cc = 0; cc < NB; ++cc) {
+          float s0 = 0.f, s1 = 0.f;
+#pragma unroll
+          for (int g = 0; g < 8; ++g) {
+            if (4 * g <= cc) {
+              float4 d = *reinterpret_cast<const float4 *>(&Dv[cc][4 * g]);
+              s0 = fmaf(ar[4 * g], d.x, s0);
+              s1 = fmaf(ar[4 * g + 1], d.y, s1);
+              s0 = fmaf(ar[4 * g + 2], d.z, s0);
+              s1 = fmaf(ar[4 * g + 3], d.w, s1);
+            }
+          }
+          P[r * LD + cc] = s0 + s1;
+        }
+      }
+      __syncthreads();
+      // 4. write the panel back: inv(L_kk) in the first NB rows, then the L rows
+      {
+        float4 *dst = reinterpret_cast<float4 *>(Bp);
+        for (int e = threadIdx.x; e < R * 8; e += CHOL32_THREADS) {
+          const int rr = e >> 3, g = e & 7;
+          dst[e] = (rr < NB) ? *reinterpret_cast<const float4 *>(&Dv[rr][4 * g])
+                             : *reinterpret_cast<const float4 *>(P + rr * LD + 4 * g);
+        }
+      }
+      // 5. trailing update in 32x32 warp tiles over the lower window (column-major order of tiles); the
+      //    tile's old values are fetched into the warp's staging area by cp.async before the arithmetic
+      const int Wn = R - nb;
+      const int nt = (Wn + 31) / 32;
+      const int ntiles = nt * (nt + 1) / 2;
+      float *cst = Cst + (size_t)wid * 32 * 32;
+      for (int t = wid; t < ntiles; t += nw) {
+        int tj = 0, rem = t;
+        while (rem >= nt - tj) {
+          rem -= nt - tj;
+          ++tj;
+        }
+        const int ti = tj + rem;
+        // window rows nb + ti*32 + q live in panel p+1+tj at row (ti - tj)*32 + q (here nb = NB)
+        float *tile = B + (long long)(p + 1 + tj) * RP * NB + (long long)(ti - tj) * 32 * NB;
+        const int rows_valid = min(32, R - (nb + ti * 32));
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          const int piece = u * 32 + lane;  // row piece >> 3, 16-byte group piece & 7
+          if ((piece >> 3) < rows_valid) cp_async16(cst + piece * 4, tile + piece * 4);
+        }
+        cp_async_commit();
+        const int jl = nb + tj * 32 + lane;  // this lane's window column (= row of P)
+        const bool jok = jl < R;
+        float pj[NB];
+#pragma unroll
+        for (int g = 0; g < 8; ++g) {
+          float4 t4 = jok ? *reinterpret_cast<const float4 *>(P + jl * LD + 4 * g) : make_float4(0.f, 0.f, 0.f, 0.f);
+          pj[4 * g] = t4.x; pj[4 * g + 1] = t4.y; pj[4 * g + 2] = t4.z; pj[4 * g + 3] = t4.w;
+        }
+        float acc[32];
+#pragma unroll
+        for (int q = 0; q < 32; ++q) {
+          const int il = min(nb + ti * 32 + q, R - 1);  // rows past the window read a valid row (discarded)
+          const float *ar = P + il * LD;
+          // four independent multiply-add chains (written as fmaf so that each product is one instruction)
+          float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
+#pragma unroll
+          for (int g = 0; g < 8; ++g) {
+            float4 a4 = *reinterpret_cast<const float4 *>(ar + 4 * g);
+            s0 = fmaf(a4.x, pj[4 * g], s0);
+            s1 = fmaf(a4.y, pj[4 * g + 1], s1);
+            s2 = fmaf(a4.z, pj[4 * g + 2], s2);
+            s3 = fmaf(a4.w, pj[4 * g + 3], s3);
+          }
+          acc[q] = (s0 + s1) + (s2 + s3);
+        }
+        cp_async_wait_pending(0);
+        __syncwarp();
+#pragma unroll
+        for (int q = 0; q < 32; ++q) {
+          const int il = nb + ti * 32 + q;
+          if (q < rows_valid && jok && jl <= il) tile[q * NB + lane] = cst[q * 32 + lane] - acc[q];
+        }
+        __syncwarp();
+      }
+      __syncthreads();
+    }
+  }
+}
+
 // ---------------------------------------------------------------- multi-RHS solves
 // One CTA per (problem, block of RB right-hand sides).  X holds the right-hand
 // sides row-major (local DOF rows, ld columns) and is overwritten by the solution.
@@ -487,6 +712,196 @@ __global__ void __launch_bounds__(256) k_band_solve_multi(const int *items, int 
   }
 }
 
+// FP32 multi-right-hand-side band solve, one CTA per (problem, block of 32 right-hand sides).
+// The 32 right-hand-side columns of the rows inside the current band window live in a shared-memory ring
+// (row i in slot i mod XR, XR >= RP + NB), so every row of X is read once and written once per sweep; the
+// factor panels are streamed through a second ring in chunks of SM32_CH rows by cp.async (all threads,
+// coalesced, two chunks ahead).  Per panel p (forward): Y = inv(L_pp) X_p, then X_r -= L_r Y for the window
+// rows r (lane = right-hand side, its Y column in registers, the L row broadcast from shared memory).
+// Backward: the window rows' column sums L_r^T X_r are accumulated per warp, reduced, and
+// X_p = inv(L_pp)^T (Y_p - sum).  Rows leave the ring (written to global memory) when the window passes them.
+constexpr int SM32_THREADS = 256;
+constexpr int SM32_CH = 128;  // factor rows per streamed chunk (16 KiB)
+constexpr int SM32_STAGES = 3;
+
+__global__ void __launch_bounds__(SM32_THREADS, 1) k_band_solve_multi32(const int *items, int n_items,
+                                                                        const int *nloc, const int *bwv,
+                                                                        const long long *band_off,
+                                                                        const float *band, float *Xbase,
+                                                                        const long long *x_off, const int *x_ld,
+                                                                        int XR) {
+  constexpr int NB = 32;
+  constexpr int NW = SM32_THREADS / 32;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  float *Lring = reinterpret_cast<float *>(smraw);            // [SM32_STAGES][SM32_CH][32]
+  float *Xw = Lring + (size_t)SM32_STAGES * SM32_CH * NB;      // [XR][32]
+  __shared__ float red[NW][NB][NB + 1];
+  __shared__ float Yb[NB][NB + 1];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int it = blockIdx.x;
+  if (it >= n_items) return;
+  const int k = items[2 * it], r0 = items[2 * it + 1];
+  const int N = nloc[k], bw = bwv[k];
+  if (N == 0) return;
+  const int ld = x_ld[k];
+  const int ncol = min(32, ld - r0);
+  const bool colok = lane < ncol;
+  const float *Bk = band + band_off[k];
+  float *X = Xbase + x_off[k] + r0;
+  const int RP = NB + bw;
+  const int np = (N + NB - 1) / NB;
+
+  // row i of X <-> ring slot i % XR
+  auto load_rows = [&](int a, int b) {  // rows [a, b) from global into the ring (warp per row, lane = column)
+    for (int i = a + wid; i < b; i += NW) Xw[(size_t)(i % XR) * NB + lane] = colok ? X[(long long)i * ld + lane] : 0.f;
+  };
+  auto store_rows = [&](int a, int b) {
+    for (int i = a + wid; i < b; i += NW)
+      if (colok) X[(long long)i * ld + lane] = Xw[(size_t)(i % XR) * NB + lane];
+  };
+  // chunk stream of one sweep: panel p (in sweep order), chunk c covers panel rows [c CH, min(R_p, (c+1) CH))
+  auto panel_rows = [&](int p) { return max(min(N - p * NB, RP), NB); };
+  auto issue_chunk = [&](int p, int c, int slot) {
+    if (p >= 0 && p < np) {
+      const int rows = min(SM32_CH, panel_rows(p) - c * SM32_CH);
+      const float *src = Bk + ((long long)p * RP + (long long)c * SM32_CH) * NB;
+      float *dst = Lring + (size_t)slot * SM32_CH * NB;
+      for (int piece = threadIdx.x; piece < rows * 8; piece += SM32_THREADS) cp_async16(dst + piece * 4, src + piece * 4);
+    }
+    cp_async_commit();
+  };
+
+  for (int dir = 0; dir < 2; ++dir) {
+    // sequence of (panel, chunk) in this sweep; forward panels ascending, backward descending with the
+    // chunk holding inv(L_pp) (chunk 0) last
+    auto nch = [&](int p) { return (panel_rows(p) + SM32_CH - 1) / SM32_CH; };
+    // iterator state for the prefetch (ip, ic) and the consumption (p, c)
+    int ip = dir == 0 ? 0 : np - 1, ic = 0;
+    auto chunk_index = [&](int p, int c) {  // backward: 1, 2, ..., n-1, then 0
+      return dir == 0 ? c : ((c + 1) % nch(p));
+    };
+    auto advance = [&](int &pp, int &cc) {
+      if (++cc >= nch(pp)) {
+        cc = 0;
+        pp += dir == 0 ? 1 : -1;
+      }
+    };
+    int slot_issue = 0;
+    for (int s = 0; s < SM32_STAGES - 1; ++s) {
+      issue_chunk((ip >= 0 && ip < np) ? ip : -1, (ip >= 0 && ip < np) ? chunk_index(ip, ic) : 0, slot_issue);
+      slot_issue = (slot_issue + 1) % SM32_STAGES;
+      if (ip >= 0 && ip < np) advance(ip, ic);
+    }
+    // initial ring contents
+    if (dir == 0) {
+      load_rows(0, min(N, RP));
+    } else {
+      load_rows(max(0, (np - 1) * NB), N);
+    }
+    int slot_use = 0;
+    for (int p = dir == 0 ? 0 : np - 1; dir == 0 ? p < np : p >= 0; p += dir == 0 ? 1 : -1) {
+      const int k0 = p * NB, nb = min(NB, N - k0);
+      const int R = min(N - k0, RP);
+      const int nc = nch(p);
+      float acc[NB];
+#pragma unroll
+      for (int e = 0; e < NB; ++e) acc[e] = 0.f;
+      float ycol[NB];
+      for (int cseq = 0; cseq < nc; ++cseq) {
+        cp_async_wait_pending(SM32_STAGES - 2);
+        __syncthreads();  // chunk cseq landed for every thread; previous chunk fully consumed
+        issue_chunk((ip >= 0 && ip < np) ? ip : -1, (ip >= 0 && ip < np) ? chunk_index(ip, ic) : 0, slot_issue);
+        slot_issue = (slot_issue + 1) % SM32_STAGES;
+        if (ip >= 0 && ip < np) advance(ip, ic);
+        const int c = dir == 0 ? cseq : ((cseq + 1) % nc);
+        const float *Lc = Lring + (size_t)slot_use * SM32_CH * NB;
+        slot_use = (slot_use + 1) % SM32_STAGES;
+        const int row0 = c * SM32_CH;
+        const int rows = min(SM32_CH, panel_rows(p) - row0);
+        if (dir == 0) {
+          if (c == 0) {
+            // Y = inv(L_pp) X_p  (rows q of the block, lane = column); Yb then holds Y
+            for (int q = wid; q < NB; q += NW) {
+              float y = 0.f;
+#pragma unroll
+              for (int cc = 0; cc < NB; ++cc) y = fmaf(Lc[q * NB + cc], Xw[(size_t)((k0 + cc) % XR) * NB + lane], y);
+              Yb[q][lane] = (q < nb) ? y : 0.f;
+            }
+            __syncthreads();
+            for (int q = wid; q < nb; q += NW) Xw[(size_t)((k0 + q) % XR) * NB + lane] = Yb[q][lane];
+#pragma unroll
+            for (int cc = 0; cc < NB; ++cc) ycol[cc] = Yb[cc][lane];
+          }
+          // window rows of this chunk: X_r -= L_r . Y
+          const int lo = max(row0, nb), hi = min(row0 + rows, R);
+          for (int r = lo + wid; r < hi; r += NW) {
+            const float *lr = Lc + (size_t)(r - row0) * NB;
+            float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
+#pragma unroll
+            for (int g = 0; g < 8; ++g) {
+              float4 l4 = *reinterpret_cast<const float4 *>(lr + 4 * g);
+              s0 = fmaf(l4.x, ycol[4 * g], s0);
+              s1 = fmaf(l4.y, ycol[4 * g + 1], s1);
+              s2 = fmaf(l4.z, ycol[4 * g + 2], s2);
+              s3 = fmaf(l4.w, ycol[4 * g + 3], s3);
+            }
+            Xw[(size_t)((k0 + r) % XR) * NB + lane] -= (s0 + s1) + (s2 + s3);
+          }
+        } else {
+          // accumulate L_r^T X_r over the window rows of this chunk
+          const int lo = max(row0, nb), hi = min(row0 + rows, R);
+          for (int r = lo + wid; r < hi; r += NW) {
+            const float *lr = Lc + (size_t)(r - row0) * NB;
+            const float xr = Xw[(size_t)((k0 + r) % XR) * NB + lane];
+#pragma unroll
+            for (int g = 0; g < 8; ++g) {
+              float4 l4 = *reinterpret_cast<const float4 *>(lr + 4 * g);
+              acc[4 * g] = fmaf(l4.x, xr, acc[4 * g]);
+              acc[4 * g + 1] = fmaf(l4.y, xr, acc[4 * g + 1]);
+              acc[4 * g + 2] = fmaf(l4.z, xr, acc[4 * g + 2]);
+              acc[4 * g + 3] = fmaf(l4.w, xr, acc[4 * g + 3]);
+            }
+          }
+          if (c == 0) {
+            // finish the panel: t = Y_p - sum over warps, X_p = inv(L_pp)^T t
+#pragma unroll
+            for (int e = 0; e < NB; ++e) red[wid][e][lane] = acc[e];
+            __syncthreads();
+            for (int q = wid; q < NB; q += NW) {
+              float sum = 0.f;
+#pragma unroll
+              for (int w = 0; w < NW; ++w) sum += red[w][q][lane];
+              Yb[q][lane] = (q < nb) ? Xw[(size_t)((k0 + q) % XR) * NB + lane] - sum : 0.f;
+            }
+            __syncthreads();
+            for (int q = wid; q < nb; q += NW) {
+              float xq = 0.f;
+#pragma unroll
+              for (int cc = 0; cc < NB; ++cc) xq = fmaf(Lc[cc * NB + q], Yb[cc][lane], xq);
+              Xw[(size_t)((k0 + q) % XR) * NB + lane] = xq;
+            }
+          }
+        }
+      }
+      __syncthreads();
+      // ring maintenance
+      if (dir == 0) {
+        // block p is final for the forward sweep; rows entering the next window come in
+        store_rows(k0, k0 + nb);
+        if (p + 1 < np) load_rows(min(N, k0 + RP), min(N, k0 + NB + RP));
+      } else {
+        // block p is final; the next (lower) block comes in with its forward values
+        store_rows(k0, k0 + nb);
+        if (p > 0) load_rows(k0 - NB, k0);
+      }
+      __syncthreads();
+    }
+    // forward: rows still in the ring are already stored (each block is stored when final)
+    cp_async_wait_pending(0);
+    __syncthreads();
+  }
+}
+
 // ---------------------------------------------------------------- single-RHS smoother solves
 // One CTA per problem solves L L^T x = r for the gathered local right-hand side (kept in shared memory as
 // the vector v) and adds (contact grids, which overlap) or stores (grain grids) x into z.
@@ -524,9 +939,6 @@ constexpr int WS_MAX_FAR_STAGES = 8;
 constexpr int WS_MAX_C0_STAGES = 8;
 constexpr long long WAIT_LIMIT = 1LL << 26;
 
-__device__ __forceinline__ uint32_t smem_u32(const void *p) {
-  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
-}
 
 __device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
   asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
@@ -578,24 +990,6 @@ __device__ __forceinline__ int step_barrier_or(int flag, int nthreads) {
       : "r"(flag), "r"(nthreads)
       : "memory");
   return res;
-}
-
-__device__ __forceinline__ void cp_async16(void *dst, const void *src) {
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-// wait until at most n of this thread's most recent cp.async groups are pending (n small, runtime)
-__device__ __forceinline__ void cp_async_wait_pending(int n) {
-  switch (n) {
-    case 0: asm volatile("cp.async.wait_group 0;" ::: "memory"); break;
-    case 1: asm volatile("cp.async.wait_group 1;" ::: "memory"); break;
-    case 2: asm volatile("cp.async.wait_group 2;" ::: "memory"); break;
-    case 3: asm volatile("cp.async.wait_group 3;" ::: "memory"); break;
-    case 4: asm volatile("cp.async.wait_group 4;" ::: "memory"); break;
-    case 5: asm volatile("cp.async.wait_group 5;" ::: "memory"); break;
-    case 6: asm volatile("cp.async.wait_group 6;" ::: "memory"); break;
-    default: asm volatile("cp.async.wait_group 7;" ::: "memory"); break;
-  }
 }
 
 // 16-byte group loads of a factor row
@@ -938,11 +1332,21 @@ void layout_and_factor(hplmm_ctx *c, LocalSet &S, int where) {
   Buf<int> queue;
   queue.alloc(1);
   queue.zero(s);
-  auto kern = k_band_chol<T, NB>;
-  HP_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   int grid = std::min(K, 2 * num_sms());
-  kern<<<grid, FACT_THREADS, smem, s>>>(S.order.p, K, queue.p, S.n.p, S.bw.p, S.band_off.p, band, c->status.p,
-                                        where);
+  if constexpr (sizeof(T) == 4) {
+    const size_t smem32 =
+        ((size_t)(NB + bwmax) * CHOL32_LD + (size_t)(CHOL32_THREADS / 32) * 32 * 32) * sizeof(float);
+    HP_REQUIRE(smem32 <= 216 * 1024, HPLMM_ERR_INVALID,
+               "local problem half bandwidth " + std::to_string(bwmax) + " is too large; use smaller grain grids");
+    HP_CUDA(cudaFuncSetAttribute(k_band_chol32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem32));
+    k_band_chol32<<<grid, CHOL32_THREADS, smem32, s>>>(S.order.p, K, queue.p, S.n.p, S.bw.p, S.band_off.p, band,
+                                                       c->status.p, where, bwmax);
+  } else {
+    auto kern = k_band_chol<T, NB>;
+    HP_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    kern<<<grid, FACT_THREADS, smem, s>>>(S.order.p, K, queue.p, S.n.p, S.bw.p, S.band_off.p, band, c->status.p,
+                                          where);
+  }
   HP_CHECK_LAUNCH();
   HP_CUDA(cudaStreamSynchronize(s));
 }
@@ -1100,8 +1504,21 @@ static void solve_multi_t(hplmm_ctx *c, LocalSet &S, T *X, const Buf<long long> 
   ProfScope ps(c, HPLMM_PH_BASIS_SOLVE);
   Buf<int> it;
   it.upload(items, s);
-  k_band_solve_multi<T, NB><<<n_items, 256, 0, s>>>(it.p, n_items, S.n.p, S.bw.p, S.band_off.p, band_ptr<T>(S), X,
-                                                    x_off.p, x_ld.p);
+  if constexpr (sizeof(T) == 4) {
+    int rpmax = NB;
+    for (int k = 0; k < S.count; ++k)
+      if (S.h_n[k] > 0) rpmax = std::max(rpmax, NB + S.h_bw[k]);
+    const int XR = ((rpmax + NB + NB - 1) / NB) * NB;  // ring rows >= RP + NB
+    const size_t smem = ((size_t)SM32_STAGES * SM32_CH * NB + (size_t)XR * NB) * sizeof(float);
+    HP_REQUIRE(smem <= 180 * 1024, HPLMM_ERR_INVALID,
+               "local problem half bandwidth " + std::to_string(rpmax - NB) + " is too large for the basis solves");
+    HP_CUDA(cudaFuncSetAttribute(k_band_solve_multi32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    k_band_solve_multi32<<<n_items, SM32_THREADS, smem, s>>>(it.p, n_items, S.n.p, S.bw.p, S.band_off.p,
+                                                             band_ptr<T>(S), X, x_off.p, x_ld.p, XR);
+  } else {
+    k_band_solve_multi<T, NB><<<n_items, 256, 0, s>>>(it.p, n_items, S.n.p, S.bw.p, S.band_off.p, band_ptr<T>(S),
+                                                      X, x_off.p, x_ld.p);
+  }
   HP_CHECK_LAUNCH();
   HP_CUDA(cudaStreamSynchronize(s));
 }
