@@ -243,6 +243,7 @@ constexpr int TB = 64;
 __global__ void k_potrf_tile(double *A, long long N, int kt, double *Dinv, int *status) {
   __shared__ double L[TB][TB + 1];
   __shared__ double W[TB][TB + 1];
+  __shared__ double rdiag[TB];  // reciprocals of the factor's diagonal (one division per column)
   int k0 = kt * TB;
   int nb = (int)min((long long)TB, N - k0);
   for (int e = threadIdx.x; e < TB * TB; e += blockDim.x) {
@@ -261,10 +262,12 @@ __global__ void k_potrf_tile(double *A, long long N, int kt, double *Dinv, int *
         }
         d = 1.0;
       }
-      L[c][c] = sqrt(d);
+      const double sd = sqrt(d);
+      L[c][c] = sd;
+      rdiag[c] = 1.0 / sd;
     }
     __syncthreads();
-    for (int r = c + 1 + threadIdx.x; r < nb; r += blockDim.x) L[r][c] /= L[c][c];
+    for (int r = c + 1 + threadIdx.x; r < nb; r += blockDim.x) L[r][c] *= rdiag[c];
     __syncthreads();
     for (int e = threadIdx.x; e < TB * TB; e += blockDim.x) {
       int r = e / TB, c2 = e % TB;
@@ -272,6 +275,8 @@ __global__ void k_potrf_tile(double *A, long long N, int kt, double *Dinv, int *
     }
     __syncthreads();
   }
+  for (int i = nb + threadIdx.x; i < TB; i += blockDim.x) rdiag[i] = 1.0;  // identity padding rows
+  __syncthreads();
   // inverse of the lower factor block, column j by thread j
   if (threadIdx.x < TB) {
     int j = threadIdx.x;
@@ -282,7 +287,7 @@ __global__ void k_potrf_tile(double *A, long long N, int kt, double *Dinv, int *
       } else {
         double s = (i == j) ? 1.0 : 0.0;
         for (int q = j; q < i; ++q) s -= L[i][q] * W[q][j];
-        v = s / L[i][i];
+        v = s * rdiag[i];
       }
       W[i][j] = v;
     }
@@ -712,11 +717,13 @@ void build_coarse(hplmm_ctx *c, const double *b_corr) {
   long long No = c->n_coarse;
   c->Ao.alloc(std::max<long long>(No * No, 1));
   c->Ao.zero(s);
-  ProfScope ps_gal(c, HPLMM_PH_GALERKIN);
-  if (f64)
-    galerkin<double>(c, gbox, hgal, gal_off, c->gcol_off, c->gcol, maxvol);
-  else
-    galerkin<float>(c, gbox, hgal, gal_off, c->gcol_off, c->gcol, maxvol);
+  {
+    ProfScope ps_gal(c, HPLMM_PH_GALERKIN);
+    if (f64)
+      galerkin<double>(c, gbox, hgal, gal_off, c->gcol_off, c->gcol, maxvol);
+    else
+      galerkin<float>(c, gbox, hgal, gal_off, c->gcol_off, c->gcol, maxvol);
+  }
   if (No > 0) {
     ProfScope ps_chol(c, HPLMM_PH_COARSE_CHOL);
     k_symmetrize<<<grid_for(No * No, 256), 256, 0, s>>>(c->Ao.p, No, nullptr);

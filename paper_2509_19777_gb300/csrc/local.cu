@@ -721,8 +721,185 @@ __global__ void __launch_bounds__(256) k_band_solve_multi(const int *items, int 
 // Backward: the window rows' column sums L_r^T X_r are accumulated per warp, reduced, and
 // X_p = inv(L_pp)^T (Y_p - sum).  Rows leave the ring (written to global memory) when the window passes them.
 constexpr int SM32_THREADS = 256;
+constexpr int SM32_NW = SM32_THREADS / 32;
 constexpr int SM32_CH = 128;  // factor rows per streamed chunk (16 KiB)
 constexpr int SM32_STAGES = 3;
+
+struct Multi32Ctx {
+  const float *Bk;  // factor of the problem
+  float *X;         // first right-hand-side column of the block, row stride ld
+  float *Lring, *Xw;
+  float (*red)[32][32];
+  float (*Yb)[33];
+  int N, RP, np, ld, XR;
+  bool colok;
+  int lane, wid;
+  // chunk stream state
+  int slot_issue, slot_use, ip, ic;
+};
+
+__device__ __forceinline__ int ring_slot(int i, int XR) { return i % XR; }
+
+__device__ __forceinline__ int m32_panel_rows(const Multi32Ctx &m, int p) {
+  return max(min(m.N - p * 32, m.RP), 32);
+}
+__device__ __forceinline__ int m32_nch(const Multi32Ctx &m, int p) {
+  return (m32_panel_rows(m, p) + SM32_CH - 1) / SM32_CH;
+}
+
+template <int DIR>
+__device__ __forceinline__ void m32_issue(Multi32Ctx &m) {
+  if (m.ip >= 0 && m.ip < m.np) {
+    const int p = m.ip;
+    const int nc = m32_nch(m, p);
+    const int c = DIR == 0 ? m.ic : ((m.ic + 1) % nc);  // backward: chunk 0 (inv(L_pp)) last
+    const int rows = min(SM32_CH, m32_panel_rows(m, p) - c * SM32_CH);
+    const float *src = m.Bk + ((long long)p * m.RP + (long long)c * SM32_CH) * 32;
+    float *dst = m.Lring + (size_t)m.slot_issue * SM32_CH * 32;
+    for (int piece = threadIdx.x; piece < rows * 8; piece += SM32_THREADS) cp_async16(dst + piece * 4, src + piece * 4);
+    if (++m.ic >= nc) {
+      m.ic = 0;
+      m.ip += DIR == 0 ? 1 : -1;
+    }
+  }
+  cp_async_commit();
+  m.slot_issue = (m.slot_issue + 1) % SM32_STAGES;
+}
+
+__device__ __forceinline__ void m32_load_rows(const Multi32Ctx &m, int a, int b) {
+  for (int i = a + m.wid; i < b; i += SM32_NW)
+    m.Xw[(size_t)ring_slot(i, m.XR) * 32 + m.lane] = m.colok ? m.X[(long long)i * m.ld + m.lane] : 0.f;
+}
+__device__ __forceinline__ void m32_store_rows(const Multi32Ctx &m, int a, int b) {
+  for (int i = a + m.wid; i < b; i += SM32_NW)
+    if (m.colok) m.X[(long long)i * m.ld + m.lane] = m.Xw[(size_t)ring_slot(i, m.XR) * 32 + m.lane];
+}
+
+template <int DIR>
+__device__ void m32_sweep(Multi32Ctx &m) {
+  constexpr int NB = 32;
+  const int lane = m.lane, wid = m.wid;
+  m.slot_issue = 0;
+  m.slot_use = 0;
+  m.ip = DIR == 0 ? 0 : m.np - 1;
+  m.ic = 0;
+  for (int s = 0; s < SM32_STAGES - 1; ++s) m32_issue<DIR>(m);
+  if (DIR == 0)
+    m32_load_rows(m, 0, min(m.N, m.RP));
+  else
+    m32_load_rows(m, max(0, (m.np - 1) * NB), m.N);
+  for (int p = DIR == 0 ? 0 : m.np - 1; DIR == 0 ? p < m.np : p >= 0; p += DIR == 0 ? 1 : -1) {
+    const int k0 = p * NB, nb = min(NB, m.N - k0);
+    const int R = min(m.N - k0, m.RP);
+    const int nc = m32_nch(m, p);
+    float vec[NB];  // forward: this lane's column of Y; backward: column sums of the window rows
+#pragma unroll
+    for (int e = 0; e < NB; ++e) vec[e] = 0.f;
+    for (int cseq = 0; cseq < nc; ++cseq) {
+      cp_async_wait_pending(SM32_STAGES - 2);
+      __syncthreads();  // this chunk landed for every thread; the previous one is fully consumed
+      m32_issue<DIR>(m);
+      const int c = DIR == 0 ? cseq : ((cseq + 1) % nc);
+      const float *Lc = m.Lring + (size_t)m.slot_use * SM32_CH * NB;
+      m.slot_use = (m.slot_use + 1) % SM32_STAGES;
+      const int row0 = c * SM32_CH;
+      const int rows = min(SM32_CH, m32_panel_rows(m, p) - row0);
+      if (DIR == 0 && c == 0) {
+        // Y = inv(L_pp) X_p (row q of the block, lane = column)
+        for (int q = wid; q < NB; q += SM32_NW) {
+          float y = 0.f;
+#pragma unroll
+          for (int cc = 0; cc < NB; ++cc)
+            y = fmaf(Lc[q * NB + cc], m.Xw[(size_t)ring_slot(k0 + cc, m.XR) * NB + lane], y);
+          m.Yb[q][lane] = (q < nb) ? y : 0.f;
+        }
+        __syncthreads();
+        for (int q = wid; q < nb; q += SM32_NW) m.Xw[(size_t)ring_slot(k0 + q, m.XR) * NB + lane] = m.Yb[q][lane];
+#pragma unroll
+        for (int cc = 0; cc < NB; ++cc) vec[cc] = m.Yb[cc][lane];
+      }
+      // window rows of this chunk, two per warp iteration (the second clamped to a valid row and masked)
+      const int lo = max(row0, nb), hi = min(row0 + rows, R);
+      int r = lo + wid;
+      int slot = ring_slot(k0 + r, m.XR);  // advanced incrementally below
+      for (; r < hi; r += 2 * SM32_NW) {
+        const bool okb = r + SM32_NW < hi;
+        const int rb = okb ? r + SM32_NW : r;
+        int slotb = slot + SM32_NW;
+        if (slotb >= m.XR) slotb -= m.XR;
+        if (!okb) slotb = slot;
+        const float *la = Lc + (size_t)(r - row0) * NB;
+        const float *lb = Lc + (size_t)(rb - row0) * NB;
+        float *xa = m.Xw + (size_t)slot * NB + lane;
+        float *xb = m.Xw + (size_t)slotb * NB + lane;
+        if (DIR == 0) {
+          // X_r -= L_r . Y
+          float a0 = 0.f, a1 = 0.f, b0 = 0.f, b1 = 0.f;
+#pragma unroll
+          for (int g = 0; g < 8; ++g) {
+            float4 l4 = *reinterpret_cast<const float4 *>(la + 4 * g);
+            float4 m4 = *reinterpret_cast<const float4 *>(lb + 4 * g);
+            a0 = fmaf(l4.x, vec[4 * g], a0);
+            a1 = fmaf(l4.y, vec[4 * g + 1], a1);
+            a0 = fmaf(l4.z, vec[4 * g + 2], a0);
+            a1 = fmaf(l4.w, vec[4 * g + 3], a1);
+            b0 = fmaf(m4.x, vec[4 * g], b0);
+            b1 = fmaf(m4.y, vec[4 * g + 1], b1);
+            b0 = fmaf(m4.z, vec[4 * g + 2], b0);
+            b1 = fmaf(m4.w, vec[4 * g + 3], b1);
+          }
+          const float xav = *xa, xbv = *xb;
+          *xa = xav - (a0 + a1);
+          if (okb) *xb = xbv - (b0 + b1);
+        } else {
+          // column sums L_r^T X_r
+          const float xr = *xa, xs = okb ? *xb : 0.f;
+#pragma unroll
+          for (int g = 0; g < 8; ++g) {
+            float4 l4 = *reinterpret_cast<const float4 *>(la + 4 * g);
+            float4 m4 = *reinterpret_cast<const float4 *>(lb + 4 * g);
+            vec[4 * g] = fmaf(m4.x, xs, fmaf(l4.x, xr, vec[4 * g]));
+            vec[4 * g + 1] = fmaf(m4.y, xs, fmaf(l4.y, xr, vec[4 * g + 1]));
+            vec[4 * g + 2] = fmaf(m4.z, xs, fmaf(l4.z, xr, vec[4 * g + 2]));
+            vec[4 * g + 3] = fmaf(m4.w, xs, fmaf(l4.w, xr, vec[4 * g + 3]));
+          }
+        }
+        slot += 2 * SM32_NW;
+        while (slot >= m.XR) slot -= m.XR;
+      }
+      if (DIR == 1 && c == 0) {
+        // finish the panel: t = Y_p - (sum over warps), X_p = inv(L_pp)^T t
+#pragma unroll
+        for (int e = 0; e < NB; ++e) m.red[wid][e][lane] = vec[e];
+        __syncthreads();
+        for (int q = wid; q < NB; q += SM32_NW) {
+          float sum = 0.f;
+#pragma unroll
+          for (int w = 0; w < SM32_NW; ++w) sum += m.red[w][q][lane];
+          m.Yb[q][lane] = (q < nb) ? m.Xw[(size_t)ring_slot(k0 + q, m.XR) * NB + lane] - sum : 0.f;
+        }
+        __syncthreads();
+        for (int q = wid; q < nb; q += SM32_NW) {
+          float xq = 0.f;
+#pragma unroll
+          for (int cc = 0; cc < NB; ++cc) xq = fmaf(Lc[cc * NB + q], m.Yb[cc][lane], xq);
+          m.Xw[(size_t)ring_slot(k0 + q, m.XR) * NB + lane] = xq;
+        }
+      }
+    }
+    __syncthreads();
+    // block p is final for this sweep; the next window's new rows come in
+    m32_store_rows(m, k0, k0 + nb);
+    if (DIR == 0) {
+      if (p + 1 < m.np) m32_load_rows(m, min(m.N, k0 + m.RP), min(m.N, k0 + NB + m.RP));
+    } else {
+      if (p > 0) m32_load_rows(m, k0 - NB, k0);
+    }
+    __syncthreads();
+  }
+  cp_async_wait_pending(0);
+  __syncthreads();
+}
 
 __global__ void __launch_bounds__(SM32_THREADS, 1) k_band_solve_multi32(const int *items, int n_items,
                                                                         const int *nloc, const int *bwv,
@@ -730,176 +907,31 @@ __global__ void __launch_bounds__(SM32_THREADS, 1) k_band_solve_multi32(const in
                                                                         const float *band, float *Xbase,
                                                                         const long long *x_off, const int *x_ld,
                                                                         int XR) {
-  constexpr int NB = 32;
-  constexpr int NW = SM32_THREADS / 32;
   extern __shared__ __align__(16) unsigned char smraw[];
-  float *Lring = reinterpret_cast<float *>(smraw);            // [SM32_STAGES][SM32_CH][32]
-  float *Xw = Lring + (size_t)SM32_STAGES * SM32_CH * NB;      // [XR][32]
-  __shared__ float red[NW][NB][NB + 1];
-  __shared__ float Yb[NB][NB + 1];
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  __shared__ float red[SM32_NW][32][32];
+  __shared__ float Yb[32][33];
   const int it = blockIdx.x;
   if (it >= n_items) return;
   const int k = items[2 * it], r0 = items[2 * it + 1];
-  const int N = nloc[k], bw = bwv[k];
+  const int N = nloc[k];
   if (N == 0) return;
-  const int ld = x_ld[k];
-  const int ncol = min(32, ld - r0);
-  const bool colok = lane < ncol;
-  const float *Bk = band + band_off[k];
-  float *X = Xbase + x_off[k] + r0;
-  const int RP = NB + bw;
-  const int np = (N + NB - 1) / NB;
-
-  // row i of X <-> ring slot i % XR
-  auto load_rows = [&](int a, int b) {  // rows [a, b) from global into the ring (warp per row, lane = column)
-    for (int i = a + wid; i < b; i += NW) Xw[(size_t)(i % XR) * NB + lane] = colok ? X[(long long)i * ld + lane] : 0.f;
-  };
-  auto store_rows = [&](int a, int b) {
-    for (int i = a + wid; i < b; i += NW)
-      if (colok) X[(long long)i * ld + lane] = Xw[(size_t)(i % XR) * NB + lane];
-  };
-  // chunk stream of one sweep: panel p (in sweep order), chunk c covers panel rows [c CH, min(R_p, (c+1) CH))
-  auto panel_rows = [&](int p) { return max(min(N - p * NB, RP), NB); };
-  auto issue_chunk = [&](int p, int c, int slot) {
-    if (p >= 0 && p < np) {
-      const int rows = min(SM32_CH, panel_rows(p) - c * SM32_CH);
-      const float *src = Bk + ((long long)p * RP + (long long)c * SM32_CH) * NB;
-      float *dst = Lring + (size_t)slot * SM32_CH * NB;
-      for (int piece = threadIdx.x; piece < rows * 8; piece += SM32_THREADS) cp_async16(dst + piece * 4, src + piece * 4);
-    }
-    cp_async_commit();
-  };
-
-  for (int dir = 0; dir < 2; ++dir) {
-    // sequence of (panel, chunk) in this sweep; forward panels ascending, backward descending with the
-    // chunk holding inv(L_pp) (chunk 0) last
-    auto nch = [&](int p) { return (panel_rows(p) + SM32_CH - 1) / SM32_CH; };
-    // iterator state for the prefetch (ip, ic) and the consumption (p, c)
-    int ip = dir == 0 ? 0 : np - 1, ic = 0;
-    auto chunk_index = [&](int p, int c) {  // backward: 1, 2, ..., n-1, then 0
-      return dir == 0 ? c : ((c + 1) % nch(p));
-    };
-    auto advance = [&](int &pp, int &cc) {
-      if (++cc >= nch(pp)) {
-        cc = 0;
-        pp += dir == 0 ? 1 : -1;
-      }
-    };
-    int slot_issue = 0;
-    for (int s = 0; s < SM32_STAGES - 1; ++s) {
-      issue_chunk((ip >= 0 && ip < np) ? ip : -1, (ip >= 0 && ip < np) ? chunk_index(ip, ic) : 0, slot_issue);
-      slot_issue = (slot_issue + 1) % SM32_STAGES;
-      if (ip >= 0 && ip < np) advance(ip, ic);
-    }
-    // initial ring contents
-    if (dir == 0) {
-      load_rows(0, min(N, RP));
-    } else {
-      load_rows(max(0, (np - 1) * NB), N);
-    }
-    int slot_use = 0;
-    for (int p = dir == 0 ? 0 : np - 1; dir == 0 ? p < np : p >= 0; p += dir == 0 ? 1 : -1) {
-      const int k0 = p * NB, nb = min(NB, N - k0);
-      const int R = min(N - k0, RP);
-      const int nc = nch(p);
-      float acc[NB];
-#pragma unroll
-      for (int e = 0; e < NB; ++e) acc[e] = 0.f;
-      float ycol[NB];
-      for (int cseq = 0; cseq < nc; ++cseq) {
-        cp_async_wait_pending(SM32_STAGES - 2);
-        __syncthreads();  // chunk cseq landed for every thread; previous chunk fully consumed
-        issue_chunk((ip >= 0 && ip < np) ? ip : -1, (ip >= 0 && ip < np) ? chunk_index(ip, ic) : 0, slot_issue);
-        slot_issue = (slot_issue + 1) % SM32_STAGES;
-        if (ip >= 0 && ip < np) advance(ip, ic);
-        const int c = dir == 0 ? cseq : ((cseq + 1) % nc);
-        const float *Lc = Lring + (size_t)slot_use * SM32_CH * NB;
-        slot_use = (slot_use + 1) % SM32_STAGES;
-        const int row0 = c * SM32_CH;
-        const int rows = min(SM32_CH, panel_rows(p) - row0);
-        if (dir == 0) {
-          if (c == 0) {
-            // Y = inv(L_pp) X_p  (rows q of the block, lane = column); Yb then holds Y
-            for (int q = wid; q < NB; q += NW) {
-              float y = 0.f;
-#pragma unroll
-              for (int cc = 0; cc < NB; ++cc) y = fmaf(Lc[q * NB + cc], Xw[(size_t)((k0 + cc) % XR) * NB + lane], y);
-              Yb[q][lane] = (q < nb) ? y : 0.f;
-            }
-            __syncthreads();
-            for (int q = wid; q < nb; q += NW) Xw[(size_t)((k0 + q) % XR) * NB + lane] = Yb[q][lane];
-#pragma unroll
-            for (int cc = 0; cc < NB; ++cc) ycol[cc] = Yb[cc][lane];
-          }
-          // window rows of this chunk: X_r -= L_r . Y
-          const int lo = max(row0, nb), hi = min(row0 + rows, R);
-          for (int r = lo + wid; r < hi; r += NW) {
-            const float *lr = Lc + (size_t)(r - row0) * NB;
-            float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
-#pragma unroll
-            for (int g = 0; g < 8; ++g) {
-              float4 l4 = *reinterpret_cast<const float4 *>(lr + 4 * g);
-              s0 = fmaf(l4.x, ycol[4 * g], s0);
-              s1 = fmaf(l4.y, ycol[4 * g + 1], s1);
-              s2 = fmaf(l4.z, ycol[4 * g + 2], s2);
-              s3 = fmaf(l4.w, ycol[4 * g + 3], s3);
-            }
-            Xw[(size_t)((k0 + r) % XR) * NB + lane] -= (s0 + s1) + (s2 + s3);
-          }
-        } else {
-          // accumulate L_r^T X_r over the window rows of this chunk
-          const int lo = max(row0, nb), hi = min(row0 + rows, R);
-          for (int r = lo + wid; r < hi; r += NW) {
-            const float *lr = Lc + (size_t)(r - row0) * NB;
-            const float xr = Xw[(size_t)((k0 + r) % XR) * NB + lane];
-#pragma unroll
-            for (int g = 0; g < 8; ++g) {
-              float4 l4 = *reinterpret_cast<const float4 *>(lr + 4 * g);
-              acc[4 * g] = fmaf(l4.x, xr, acc[4 * g]);
-              acc[4 * g + 1] = fmaf(l4.y, xr, acc[4 * g + 1]);
-              acc[4 * g + 2] = fmaf(l4.z, xr, acc[4 * g + 2]);
-              acc[4 * g + 3] = fmaf(l4.w, xr, acc[4 * g + 3]);
-            }
-          }
-          if (c == 0) {
-            // finish the panel: t = Y_p - sum over warps, X_p = inv(L_pp)^T t
-#pragma unroll
-            for (int e = 0; e < NB; ++e) red[wid][e][lane] = acc[e];
-            __syncthreads();
-            for (int q = wid; q < NB; q += NW) {
-              float sum = 0.f;
-#pragma unroll
-              for (int w = 0; w < NW; ++w) sum += red[w][q][lane];
-              Yb[q][lane] = (q < nb) ? Xw[(size_t)((k0 + q) % XR) * NB + lane] - sum : 0.f;
-            }
-            __syncthreads();
-            for (int q = wid; q < nb; q += NW) {
-              float xq = 0.f;
-#pragma unroll
-              for (int cc = 0; cc < NB; ++cc) xq = fmaf(Lc[cc * NB + q], Yb[cc][lane], xq);
-              Xw[(size_t)((k0 + q) % XR) * NB + lane] = xq;
-            }
-          }
-        }
-      }
-      __syncthreads();
-      // ring maintenance
-      if (dir == 0) {
-        // block p is final for the forward sweep; rows entering the next window come in
-        store_rows(k0, k0 + nb);
-        if (p + 1 < np) load_rows(min(N, k0 + RP), min(N, k0 + NB + RP));
-      } else {
-        // block p is final; the next (lower) block comes in with its forward values
-        store_rows(k0, k0 + nb);
-        if (p > 0) load_rows(k0 - NB, k0);
-      }
-      __syncthreads();
-    }
-    // forward: rows still in the ring are already stored (each block is stored when final)
-    cp_async_wait_pending(0);
-    __syncthreads();
-  }
+  Multi32Ctx m;
+  m.lane = threadIdx.x & 31;
+  m.wid = threadIdx.x >> 5;
+  m.N = N;
+  m.RP = 32 + bwv[k];
+  m.np = (N + 31) / 32;
+  m.ld = x_ld[k];
+  m.XR = XR;
+  m.colok = m.lane < min(32, m.ld - r0);
+  m.Bk = band + band_off[k];
+  m.X = Xbase + x_off[k] + r0;
+  m.Lring = reinterpret_cast<float *>(smraw);
+  m.Xw = m.Lring + (size_t)SM32_STAGES * SM32_CH * 32;
+  m.red = red;
+  m.Yb = Yb;
+  m32_sweep<0>(m);
+  m32_sweep<1>(m);
 }
 
 // ---------------------------------------------------------------- single-RHS smoother solves
