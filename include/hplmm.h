@@ -61,9 +61,13 @@ typedef struct {
   int max_iters;         /* cap on total GMRES iterations (paper: 300) */
   int strict_two_grain;  /* 1: shape vectors only on the two grains of each interface (the paper's
                             literal Eq. col_pk); 0 (default): on every grain whose voxels touch it */
-  int use_graph;         /* 1: replay the preconditioner apply as a captured CUDA graph */
+  int use_graph;         /* 1: capture one preconditioner apply as a CUDA graph at its first use after
+                            set-up and replay it for every apply (phase timings then report the replays as
+                            HPLMM_PH_APPLY_GRAPH) */
   int verbose;           /* 1: print phase timings to stderr */
   int profile;           /* 1: time every phase with CUDA events on the context's stream (hplmm_get_profile) */
+  int autotune;          /* 1: at set-up, time the smoother solve's pipeline depths on this problem's local
+                            problems and keep the fastest (cached per problem-size bucket for the process) */
 } hplmm_options;
 
 /* Boundary conditions on the six faces of the image box, in the order
@@ -212,6 +216,7 @@ typedef enum {
   HPLMM_PH_APPLY_GRAINS,      /* M_g^{-1}: grain-grid solves */
   HPLMM_PH_SPMV,              /* every A_hat x product */
   HPLMM_PH_KRYLOV,            /* FGMRES vector work (CGS2 products, updates) */
+  HPLMM_PH_APPLY_GRAPH,       /* whole preconditioner applies replayed from a captured CUDA graph (use_graph) */
   HPLMM_PH_COUNT
 } hplmm_phase;
 

@@ -40,14 +40,15 @@ EXPORTED = [
     "hplmm_reset_profile", "hplmm_kernel_launches", "hplmm_get_costs", "hplmm_last_error", "hplmm_destroy",
 ]
 PHASES = ["maps", "factor_grains", "factor_contacts", "basis_rhs", "basis_solve", "galerkin", "coarse_chol",
-          "apply_coarse", "apply_contacts", "apply_grains", "spmv", "krylov"]
+          "apply_coarse", "apply_contacts", "apply_grains", "spmv", "krylov", "apply_graph"]
 
 
 class hplmm_options(ctypes.Structure):
     _fields_ = [("n_mortar", ctypes.c_int), ("beta", ctypes.c_double), ("contact_halfwidth", ctypes.c_int),
                 ("n_st", ctypes.c_int), ("local_prec", ctypes.c_int), ("apply_prec", ctypes.c_int),
                 ("restart", ctypes.c_int), ("max_iters", ctypes.c_int), ("strict_two_grain", ctypes.c_int),
-                ("use_graph", ctypes.c_int), ("verbose", ctypes.c_int), ("profile", ctypes.c_int)]
+                ("use_graph", ctypes.c_int), ("verbose", ctypes.c_int), ("profile", ctypes.c_int),
+                ("autotune", ctypes.c_int)]
 
 
 class hplmm_bcs(ctypes.Structure):
@@ -306,13 +307,14 @@ class Solver:
 
     def __init__(self, n_mortar=4, beta=4.0, contact_halfwidth=2, n_st=1, local_prec="fp64", apply_prec="fp64",
                  restart=30, max_iters=300, strict_two_grain=False, use_graph=False, verbose=False, profile=False,
-                 stream=None):
+                 autotune=False, stream=None):
         o = hplmm_default_options()
         o.n_mortar, o.beta, o.contact_halfwidth, o.n_st = n_mortar, beta, contact_halfwidth, n_st
         o.local_prec, o.apply_prec = PREC[local_prec], PREC[apply_prec]
         o.restart, o.max_iters = restart, max_iters
         o.strict_two_grain, o.use_graph, o.verbose = int(strict_two_grain), int(use_graph), int(verbose)
         o.profile = int(profile)
+        o.autotune = int(autotune)
         self.options = o
         self.ctx = hplmm_create(o, stream)
         self.n_dof = 0

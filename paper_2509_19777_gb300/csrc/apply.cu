@@ -155,6 +155,67 @@ void precond_apply(hplmm_ctx *c, const double *r_pad, double *z_pad) {
   }
 }
 
+void drop_apply_graph(hplmm_ctx *c) {
+  if (c->apply_graph) {
+    cudaStreamSynchronize(c->stream);
+    cudaGraphExecDestroy(c->apply_graph);
+    c->apply_graph = nullptr;
+  }
+  c->graph_kernels = 0;
+}
+
+// One apply replayed from a CUDA graph: the launches of precond_apply are captured once (on a private
+// stream, reading the fixed work vector w_gin and writing w_gout) and the executable graph is launched on
+// the context's stream for every apply, with the input and output copied in and out.
+static void build_apply_graph(hplmm_ctx *c) {
+  const long long L = 3LL * c->n_nodes;
+  if (!c->cap_stream) HP_CUDA(cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking));
+  c->w_gin.alloc(L);
+  c->w_gout.alloc(L);
+  HP_CUDA(cudaStreamSynchronize(c->stream));
+  cudaStream_t user = c->stream;
+  const long long l0 = launch_count();
+  cudaGraph_t g = nullptr;
+  c->stream = c->cap_stream;
+  c->capturing = true;
+  cudaError_t e = cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal);
+  if (e == cudaSuccess) {
+    try {
+      precond_apply(c, c->w_gin.p, c->w_gout.p);
+    } catch (...) {
+      cudaStreamEndCapture(c->cap_stream, &g);
+      if (g) cudaGraphDestroy(g);
+      c->stream = user;
+      c->capturing = false;
+      throw;
+    }
+    e = cudaStreamEndCapture(c->cap_stream, &g);
+  }
+  c->stream = user;
+  c->capturing = false;
+  HP_CUDA(e);
+  const long long captured = launch_count() - l0;
+  add_launches(-captured);  // recorded, not launched
+  cudaError_t e2 = cudaGraphInstantiate(&c->apply_graph, g, 0);
+  cudaGraphDestroy(g);
+  HP_CUDA(e2);
+  c->graph_kernels = captured;
+}
+
+void precond_apply_any(hplmm_ctx *c, const double *r_pad, double *z_pad) {
+  if (!c->opt.use_graph) {
+    precond_apply(c, r_pad, z_pad);
+    return;
+  }
+  if (!c->apply_graph) build_apply_graph(c);
+  const long long L = 3LL * c->n_nodes;
+  ProfScope ps(c, HPLMM_PH_APPLY_GRAPH);
+  HP_CUDA(cudaMemcpyAsync(c->w_gin.p, r_pad, sizeof(double) * L, cudaMemcpyDeviceToDevice, c->stream));
+  HP_CUDA(cudaGraphLaunch(c->apply_graph, c->stream));
+  add_launches(c->graph_kernels);
+  HP_CUDA(cudaMemcpyAsync(z_pad, c->w_gout.p, sizeof(double) * L, cudaMemcpyDeviceToDevice, c->stream));
+}
+
 int fgmres(hplmm_ctx *c, const double *b_pad, double *x_pad, double tol, hplmm_stats *st) {
   cudaStream_t s = c->stream;
   long long L = 3LL * c->n_nodes;
@@ -198,7 +259,7 @@ int fgmres(hplmm_ctx *c, const double *b_pad, double *x_pad, double tol, hplmm_s
     for (int j = 0; j < m; ++j) {
       double *vj = V + (long long)j * L;
       double *zj = Z + (long long)j * L;
-      precond_apply(c, vj, zj);
+      precond_apply_any(c, vj, zj);
       spmv(c, zj, w, HPLMM_FP64);
       ++its;
       // CGS2

@@ -321,6 +321,7 @@ void assemble(hplmm_ctx *c, const uint8_t *mask, int nx, int ny, int nz, const f
   cudaStream_t s = c->stream;
   c->assembled = false;
   c->setup_done = false;
+  drop_apply_graph(c);
   c->nx = nx;
   c->ny = ny;
   c->nz = nz;

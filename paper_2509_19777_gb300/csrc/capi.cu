@@ -13,6 +13,7 @@ namespace hp {
 static std::atomic<long long> g_launches{0};
 long long note_launch() { return ++g_launches; }
 long long launch_count() { return g_launches.load(); }
+void add_launches(long long n) { g_launches += n; }
 
 cudaEvent_t prof_event(hplmm_ctx *c) {
   if (!c->ev_pool.empty()) {
@@ -73,6 +74,8 @@ void validate_options(const hplmm_options &o) {
              "apply_prec must be FP64 or FP32");
   HP_REQUIRE(o.restart >= 1 && o.restart <= 60, HPLMM_ERR_INVALID, "restart must lie in [1, 60]");
   HP_REQUIRE(o.max_iters >= 1, HPLMM_ERR_INVALID, "max_iters must be positive");
+  HP_REQUIRE(o.use_graph == 0 || o.use_graph == 1, HPLMM_ERR_INVALID, "use_graph must be 0 or 1");
+  HP_REQUIRE(o.autotune == 0 || o.autotune == 1, HPLMM_ERR_INVALID, "autotune must be 0 or 1");
 }
 
 void require_setup(hplmm_ctx *c) {
@@ -113,6 +116,7 @@ void hplmm_default_options(hplmm_options *o) {
   o->use_graph = 0;
   o->verbose = 0;
   o->profile = 0;
+  o->autotune = 0;
 }
 
 hplmm_status hplmm_create(hplmm_ctx **ctx, const hplmm_options *opt, void *cuda_stream) {
@@ -163,6 +167,7 @@ hplmm_status hplmm_setup(hplmm_ctx *c, const int32_t *partition, int n_grains, i
       c->n_grains = px * py * pz;
     }
     c->setup_done = false;
+    hp::drop_apply_graph(c);
     cudaStream_t s = c->stream;
     long long L = 3LL * c->n_nodes;
     c->b_corr.alloc(L);
@@ -189,6 +194,11 @@ hplmm_status hplmm_setup(hplmm_ctx *c, const int32_t *partition, int n_grains, i
     alloc_work(c);
     hp::check_status(c);
     double t3 = now_s();
+    // pipeline depths of the smoother solves (part of the smoother build)
+    hp::tune_local(c);
+    double t4 = now_s();
+    t2 += t4 - t3;
+    t3 = t4;
     c->t_ml = t2 - t1;
     c->t_mg = (t1 - t0) + (t3 - t2);
     if (c->opt.verbose)
@@ -204,7 +214,7 @@ hplmm_status hplmm_apply(hplmm_ctx *c, const double *r, double *z) {
     require_setup(c);
     HP_REQUIRE(r && z && r != z, HPLMM_ERR_INVALID, "apply: r and z must be distinct device vectors");
     hp::scatter_free(c, r, c->w_in.p);
-    hp::precond_apply(c, c->w_in.p, c->w_out.p);
+    hp::precond_apply_any(c, c->w_in.p, c->w_out.p);
     hp::gather_free(c, c->w_out.p, z);
   });
 }
@@ -386,8 +396,9 @@ const char *hplmm_last_error(const hplmm_ctx *c) {
 
 void hplmm_destroy(hplmm_ctx *c) {
   if (!c) return;
-  if (c->apply_graph) cudaGraphExecDestroy(c->apply_graph);
   cudaStreamSynchronize(c->stream);
+  if (c->apply_graph) cudaGraphExecDestroy(c->apply_graph);
+  if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
   for (auto &r : c->prof_pending) {
     cudaEventDestroy(r.e0);
     cudaEventDestroy(r.e1);

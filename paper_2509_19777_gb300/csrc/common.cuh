@@ -226,10 +226,12 @@ struct hplmm_ctx {
   int gmres_cap = 0;
   hp::Buf<double> w_partial;
 
-  // graph of the apply
+  // graph of the apply (options.use_graph): captured on a private stream from fixed work vectors
   cudaGraphExec_t apply_graph = nullptr;
-  const double *graph_r = nullptr;
-  double *graph_z = nullptr;
+  cudaStream_t cap_stream = nullptr;
+  bool capturing = false;
+  long long graph_kernels = 0;     // kernels in the captured apply
+  hp::Buf<double> w_gin, w_gout;
 
   double t_ml = 0, t_mg = 0;
 
@@ -247,6 +249,7 @@ struct hplmm_ctx {
 
 namespace hp {
 long long launch_count();
+void add_launches(long long n);  // launches issued by a graph replay (negative: undo counts of a capture)
 cudaEvent_t prof_event(hplmm_ctx *c);
 void prof_harvest(hplmm_ctx *c);
 
@@ -257,7 +260,7 @@ struct ProfScope {
   cudaEvent_t e0 = nullptr;
   long long l0 = 0;
   ProfScope(hplmm_ctx *ctx, int phase) : c(ctx), ph(phase) {
-    if (!c->opt.profile) return;
+    if (!c->opt.profile || c->capturing) return;
     e0 = prof_event(c);
     cudaEventRecord(e0, c->stream);
     l0 = launch_count();
@@ -295,6 +298,9 @@ void coarse_apply(hplmm_ctx *c, const double *r_pad, double *z_pad);
 void prolong_column(hplmm_ctx *c, long long col, double *out_pad);
 // apply.cu
 void precond_apply(hplmm_ctx *c, const double *r_pad, double *z_pad);
+void precond_apply_any(hplmm_ctx *c, const double *r_pad, double *z_pad);  // graph replay when use_graph
+void drop_apply_graph(hplmm_ctx *c);
+void tune_local(hplmm_ctx *c);
 void smoother_stage(hplmm_ctx *c, const double *r_pad, double *z_pad);
 int fgmres(hplmm_ctx *c, const double *b_pad, double *x_pad, double tol, hplmm_stats *st);
 void check_status(hplmm_ctx *c);

@@ -14,7 +14,10 @@
 #include "common.cuh"
 
 #include <algorithm>
+#include <map>
+#include <mutex>
 #include <numeric>
+#include <tuple>
 
 namespace hp {
 
@@ -1579,12 +1582,13 @@ void smoother_apply(hplmm_ctx *c, LocalSet &S, const double *r_pad, double *z_pa
   const size_t far_stage = (size_t)WS_BULK_WARPS * 32 * (f64 ? far_rpt<double>() : far_rpt<float>()) * 128;
   const size_t c0_stage = (size_t)2 * NBv * 128;
   const size_t budget = 216 * 1024;
-  int c0s = 4;
-  HP_REQUIRE(vbytes + c0s * c0_stage + 2 * far_stage <= budget, HPLMM_ERR_INVALID,
+  HP_REQUIRE(vbytes + 2 * c0_stage + 2 * far_stage <= budget, HPLMM_ERR_INVALID,
              "local problem too large for the smoother (" + std::to_string(vmax) + " local DOFs)");
+  // depths: the tuner's choice when there is one, else 4 diagonal stages and as many far stages as fit
+  int c0s = S.tuned_c0_stages > 0 ? S.tuned_c0_stages : 4;
+  if (vbytes + c0s * c0_stage + 2 * far_stage > budget) c0s = 2;
   int fs = (int)std::min<size_t>(WS_MAX_FAR_STAGES, (budget - vbytes - c0s * c0_stage) / far_stage);
   if (S.tuned_far_stages > 0) fs = std::min(fs, S.tuned_far_stages);
-  if (S.tuned_c0_stages > 0) c0s = S.tuned_c0_stages;
   const size_t smem = (size_t)fs * far_stage + (size_t)c0s * c0_stage + vbytes;
   if (f64) {
     auto kern = k_band_solve_ws<double, 16>;
@@ -1598,6 +1602,96 @@ void smoother_apply(hplmm_ctx *c, LocalSet &S, const double *r_pad, double *z_pa
                                            S.band32.p, r_pad, z_pad, atomic ? 1 : 0, fs, c0s, c->status.p);
   }
   HP_CHECK_LAUNCH();
+}
+
+// ---------------------------------------------------------------- tuner of the smoother solve pipeline
+// For each set of local problems, time the smoother solve under every pipeline depth that fits in shared
+// memory (far-row stages x diagonal-chunk stages) on the set's own factors, and keep the fastest.  Results
+// are cached for the process, keyed by (count, largest local size, largest half bandwidth, precision), so a
+// repeated set-up of the same size pays nothing.
+namespace {
+struct TuneKey {
+  int count, nmax, bwmax, prec;
+  bool operator<(const TuneKey &o) const {
+    return std::tie(count, nmax, bwmax, prec) < std::tie(o.count, o.nmax, o.bwmax, o.prec);
+  }
+};
+std::mutex g_tune_mu;
+std::map<TuneKey, std::pair<int, int>> g_tune_cache;
+}  // namespace
+
+static void tune_set(hplmm_ctx *c, LocalSet &S, bool atomic) {
+  S.tuned_far_stages = S.tuned_c0_stages = 0;
+  if (S.count == 0) return;
+  TuneKey key{S.count, 0, 0, (int)S.prec};
+  for (int k = 0; k < S.count; ++k) {
+    key.nmax = std::max(key.nmax, S.h_n[k]);
+    key.bwmax = std::max(key.bwmax, S.h_bw[k]);
+  }
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    auto it = g_tune_cache.find(key);
+    if (it != g_tune_cache.end()) {
+      S.tuned_far_stages = it->second.first;
+      S.tuned_c0_stages = it->second.second;
+      return;
+    }
+  }
+  const bool f64 = S.prec == HPLMM_FP64;
+  const int NBv = f64 ? 16 : 32;
+  const size_t esz = f64 ? 8 : 4;
+  const int vmax = ((key.nmax + NBv - 1) / NBv) * NBv + NBv;
+  const size_t vbytes = ((esz * (size_t)vmax + 127) / 128) * 128;
+  const size_t far_slot = (size_t)WS_BULK_WARPS * 32 * (f64 ? far_rpt<double>() : far_rpt<float>()) * 128;
+  const size_t c0_slot = (size_t)2 * NBv * 128, budget = 216 * 1024;
+  cudaStream_t s = c->stream;
+  cudaEvent_t e0, e1;
+  HP_CUDA(cudaEventCreate(&e0));
+  HP_CUDA(cudaEventCreate(&e1));
+  const bool prof = c->opt.profile;
+  c->opt.profile = 0;  // tuning launches are not part of any phase
+  float best = 1e30f;
+  int bf = 0, bc = 0;
+  for (int c0d = 2; c0d <= 4; ++c0d)
+    for (int fd = 2; fd <= 8; ++fd) {
+      if (vbytes + c0d * c0_slot + fd * far_slot > budget) break;
+      S.tuned_far_stages = fd;
+      S.tuned_c0_stages = c0d;
+      smoother_apply(c, S, c->b_pad.p, c->w_zz.p, atomic);  // warm-up
+      HP_CUDA(cudaEventRecord(e0, s));
+      for (int rep = 0; rep < 3; ++rep) smoother_apply(c, S, c->b_pad.p, c->w_zz.p, atomic);
+      HP_CUDA(cudaEventRecord(e1, s));
+      HP_CUDA(cudaEventSynchronize(e1));
+      float ms = 0.f;
+      HP_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+      if (ms < best) {
+        best = ms;
+        bf = fd;
+        bc = c0d;
+      }
+    }
+  c->opt.profile = prof;
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  S.tuned_far_stages = bf;
+  S.tuned_c0_stages = bc;
+  if (c->opt.verbose)
+    fprintf(stderr, "[hplmm] tuner: %d problems (n<=%d, bw<=%d): far stages %d, diagonal stages %d, %.3f ms\n",
+            S.count, key.nmax, key.bwmax, bf, bc, best / 3);
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  g_tune_cache[key] = {bf, bc};
+}
+
+void tune_local(hplmm_ctx *c) {
+  if (!c->opt.autotune) {
+    c->grains.tuned_far_stages = c->grains.tuned_c0_stages = 0;
+    c->contacts.tuned_far_stages = c->contacts.tuned_c0_stages = 0;
+    return;
+  }
+  tune_set(c, c->contacts, true);
+  tune_set(c, c->grains, false);
+  HP_CUDA(cudaMemsetAsync(c->w_zz.p, 0, sizeof(double) * 3 * (size_t)c->n_nodes, c->stream));
+  HP_CUDA(cudaStreamSynchronize(c->stream));
 }
 
 }  // namespace hp
