@@ -38,6 +38,8 @@ CHOSEN = dict(local_prec="fp32", apply_prec="fp32", use_graph=True, autotune=Tru
 # the phase-profiled repetition launches the apply kernel by kernel (a graph replay is one opaque phase)
 CHOSEN_PROFILED = dict(CHOSEN, use_graph=False)
 PLAIN = dict(local_prec="fp64", apply_prec="fp64")
+BF16 = dict(CHOSEN, apply_prec="bf16")
+FORMS = {"chosen": CHOSEN, "bf16": BF16, "plain": PLAIN}
 METHOD = dict(n_mortar=4, contact_halfwidth=2, n_st=1, restart=30, max_iters=300)
 
 
@@ -53,6 +55,7 @@ def parse():
     ap.add_argument("--quick", action="store_true",
                     help="profiling mode: time only the chosen form (no plain, e2e or CPU legs); prints a short line")
     ap.add_argument("--workload", default=WORKLOAD, help="synthetic workload for --quick runs (e.g. porous32)")
+    ap.add_argument("--form", default="chosen", choices=sorted(FORMS), help="form timed by --quick runs")
     return ap.parse_args()
 
 
@@ -378,11 +381,13 @@ def main():
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")   # 256 MiB > 129 MB L2
     if args.quick:
         problem = synth.make_workload(args.workload, args.seed + rank)
-        st_, _, tt, stt, _, _, _, launches = run_form(hp, problem, CHOSEN, args.steps, args.warmup, flush, stream)
+        form = FORMS[args.form]
+        st_, _, tt, stt, _, _, _, launches = run_form(hp, problem, form, args.steps, args.warmup, flush, stream)
         st_.close()
-        sq, _, tq, stq, prof, costs, sizes, _ = run_form(hp, problem, CHOSEN_PROFILED, args.steps, args.warmup,
-                                                         flush, stream, profile=True)
-        print(json.dumps({"workload": args.workload, "ms_per_step": statistics.mean(tt), "iters": stt.iters,
+        sq, _, tq, stq, prof, costs, sizes, _ = run_form(hp, problem, dict(form, use_graph=False), args.steps,
+                                                         args.warmup, flush, stream, profile=True)
+        print(json.dumps({"workload": args.workload, "form": args.form, "ms_per_step": statistics.mean(tt),
+                          "iters": stt.iters,
                           "launches_per_step": launches / args.steps,
                           "profiled_ms_per_step": statistics.mean(tq),
                           "profile_ms_per_step": {k: v[0] / args.steps for k, v in prof.items()}}), flush=True)

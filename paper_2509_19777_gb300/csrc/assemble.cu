@@ -414,6 +414,12 @@ void assemble(hplmm_ctx *c, const uint8_t *mask, int nx, int ny, int nz, const f
                                                                    c->sell_val32.p);
     HP_CHECK_LAUNCH();
     c->val32.release();
+    if (c->opt.apply_prec == HPLMM_BF16) {
+      c->sell_val16.alloc(nent * 9);
+      to_bf16(c->sell_val32.p, c->sell_val16.p, nent * 9, s);
+    } else {
+      c->sell_val16.release();
+    }
   }
   if (b_out) gather_free(c, c->b_pad.p, b_out);
   HP_CUDA(cudaStreamSynchronize(s));
@@ -433,7 +439,11 @@ void scatter_free(hplmm_ctx *c, const double *dof, double *pad) {
 
 void spmv(hplmm_ctx *c, const double *x_pad, double *y_pad, hplmm_prec prec, const double *sub) {
   ProfScope ps(c, HPLMM_PH_SPMV);
-  if (prec == HPLMM_FP64) {
+  if (prec == HPLMM_BF16) {
+    k_spmv_sell<__nv_bfloat16><<<grid_for(c->n_nodes, 128), 128, 0, c->stream>>>(c->sell_off.p, c->sell_col.p,
+                                                                                  c->sell_val16.p, x_pad, y_pad,
+                                                                                  sub, c->n_nodes);
+  } else if (prec == HPLMM_FP64) {
     k_spmv_sell<double><<<grid_for(c->n_nodes, 128), 128, 0, c->stream>>>(c->sell_off.p, c->sell_col.p,
                                                                            c->sell_val64.p, x_pad, y_pad, sub,
                                                                            c->n_nodes);

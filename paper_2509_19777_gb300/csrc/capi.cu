@@ -70,8 +70,10 @@ void validate_options(const hplmm_options &o) {
   HP_REQUIRE(o.n_st >= 1 && o.n_st <= 16, HPLMM_ERR_INVALID, "n_st must lie in [1, 16]");
   HP_REQUIRE(o.local_prec == HPLMM_FP64 || o.local_prec == HPLMM_FP32, HPLMM_ERR_INVALID,
              "local_prec must be FP64 or FP32");
-  HP_REQUIRE(o.apply_prec == HPLMM_FP64 || o.apply_prec == HPLMM_FP32, HPLMM_ERR_INVALID,
-             "apply_prec must be FP64 or FP32");
+  HP_REQUIRE(o.apply_prec == HPLMM_FP64 || o.apply_prec == HPLMM_FP32 || o.apply_prec == HPLMM_BF16,
+             HPLMM_ERR_INVALID, "apply_prec must be FP64, FP32 or BF16");
+  HP_REQUIRE(o.apply_prec != HPLMM_BF16 || o.local_prec == HPLMM_FP32, HPLMM_ERR_INVALID,
+             "the BF16 apply stores BF16 copies of FP32 local factors and panels: it needs local_prec = FP32");
   HP_REQUIRE(o.restart >= 1 && o.restart <= 60, HPLMM_ERR_INVALID, "restart must lie in [1, 60]");
   HP_REQUIRE(o.max_iters >= 1, HPLMM_ERR_INVALID, "max_iters must be positive");
   HP_REQUIRE(o.use_graph == 0 || o.use_graph == 1, HPLMM_ERR_INVALID, "use_graph must be 0 or 1");

@@ -664,6 +664,12 @@ void build_coarse(hplmm_ctx *c, const double *b_corr) {
     solve_local_multi_f64(c, c->grains, c->X64.p, c->panel_off, c->kg, c->h_kg);
   else
     solve_local_multi_f32(c, c->grains, c->X32.p, c->panel_off, c->kg, c->h_kg);
+  if (!f64 && c->opt.apply_prec == HPLMM_BF16) {
+    c->X16.alloc(std::max<long long>(poff[G], 1));
+    to_bf16(c->X32.p, c->X16.p, poff[G], s);
+  } else {
+    c->X16.release();
+  }
 
   // global column of every local panel column
   std::vector<int> hgoff(G + 1, 0), hgcol;
@@ -781,10 +787,15 @@ void coarse_apply(hplmm_ctx *c, const double *r_pad, double *z_pad) {
   int nmax = 1;
   for (int g = 0; g < G; ++g) nmax = std::max(nmax, c->grains.h_n[g]);
   dim3 gr((nmax + RCHUNK - 1) / RCHUNK, G);
+  const bool b16 = !f64 && c->opt.apply_prec == HPLMM_BF16;
   if (f64)
     k_restrict_grain<double, double><<<gr, 256, 0, s>>>(c->grains.node_off.p, c->grains.n.p, c->grains.lnodes.p,
                                                         c->kg.p, c->panel_off.p, c->X64.p, c->gcol_off.p, c->gcol.p,
                                                         r_pad, t);
+  else if (b16)
+    k_restrict_grain<__nv_bfloat16, float><<<gr, 256, 0, s>>>(c->grains.node_off.p, c->grains.n.p,
+                                                              c->grains.lnodes.p, c->kg.p, c->panel_off.p, c->X16.p,
+                                                              c->gcol_off.p, c->gcol.p, r_pad, t);
   else
     k_restrict_grain<float, float><<<gr, 256, 0, s>>>(c->grains.node_off.p, c->grains.n.p, c->grains.lnodes.p,
                                                       c->kg.p, c->panel_off.p, c->X32.p, c->gcol_off.p, c->gcol.p,
@@ -803,6 +814,10 @@ void coarse_apply(hplmm_ctx *c, const double *r_pad, double *z_pad) {
     k_prolong_grain<double, double><<<gp, 256, 0, s>>>(c->grains.node_off.p, c->grains.n.p, c->grains.lnodes.p,
                                                        c->kg.p, c->panel_off.p, c->X64.p, c->gcol_off.p, c->gcol.p, t,
                                                        z_pad);
+  else if (b16)
+    k_prolong_grain<__nv_bfloat16, float><<<gp, 256, 0, s>>>(c->grains.node_off.p, c->grains.n.p,
+                                                             c->grains.lnodes.p, c->kg.p, c->panel_off.p, c->X16.p,
+                                                             c->gcol_off.p, c->gcol.p, t, z_pad);
   else
     k_prolong_grain<float, float><<<gp, 256, 0, s>>>(c->grains.node_off.p, c->grains.n.p, c->grains.lnodes.p,
                                                      c->kg.p, c->panel_off.p, c->X32.p, c->gcol_off.p, c->gcol.p, t,

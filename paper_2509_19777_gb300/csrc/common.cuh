@@ -1,6 +1,7 @@
 // Internal definitions shared by the hPLMM CUDA translation units.
 #pragma once
 
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -125,6 +126,8 @@ struct LocalSet {
   Buf<int> lmap;      // box cell (permuted lexicographic) -> ordinal or -1 (node_off based)
   Buf<double> band64;   // FP64 factors (panel width 16; diagonal rows hold inv(L_kk))
   Buf<float> band32;    // FP32 factors (panel width 32)
+  Buf<__nv_bfloat16> band16;  // BF16 copy of the FP32 factors, used by the apply in the BF16 form
+  bool apply_bf16 = false;
   Buf<int> order;     // problems sorted by decreasing factorisation cost
   int tuned_far_stages = 0;  // smoother solve pipeline depths picked by the tuner (0 = largest that fits)
   int tuned_c0_stages = 0;
@@ -163,6 +166,7 @@ struct hplmm_ctx {
   hp::Buf<int> sell_col;           // block column per entry (slot-major within a slice)
   hp::Buf<double> sell_val64;      // 9 values per entry, element-major within a slot
   hp::Buf<float> sell_val32;
+  hp::Buf<__nv_bfloat16> sell_val16;  // BF16 copy (only for the BF16 apply form)
   hp::Buf<double> b_pad;           // n_nodes*3 right-hand side, 0 on fixed slots
   hp::Buf<double> b_corr;          // right-hand side defining the correction columns (padded)
 
@@ -207,6 +211,7 @@ struct hplmm_ctx {
   // ---- coarse space (Section 4.2)
   hp::Buf<double> X64;             // basis panels X_g (local DOF rows x k_g), FP64
   hp::Buf<float> X32;              // FP32 copy/compute
+  hp::Buf<__nv_bfloat16> X16;      // BF16 copy of X32 for the restriction/prolongation of the BF16 form
   hp::Buf<double> Ao;              // N^o x N^o
   hp::Buf<double> gal64;           // Galerkin work: P and Y on the grains' node boxes (FP64 form)
   hp::Buf<float> gal32;            // (FP32 form)
@@ -286,6 +291,8 @@ void compute_W(hplmm_ctx *c, int64_t *W);
 // local.cu
 void build_local_sets(hplmm_ctx *c);
 void factor_local(hplmm_ctx *c, LocalSet &S, hplmm_prec prec);
+// elementwise FP32 -> BF16 copy (round to nearest even)
+void to_bf16(const float *src, __nv_bfloat16 *dst, long long n, cudaStream_t s);
 void solve_local_multi_f64(hplmm_ctx *c, LocalSet &S, double *X, const Buf<long long> &x_off, const Buf<int> &x_ld,
                            const std::vector<int> &h_ld);
 void solve_local_multi_f32(hplmm_ctx *c, LocalSet &S, float *X, const Buf<long long> &x_off, const Buf<int> &x_ld,

@@ -13,6 +13,8 @@
 // triangular solves into small dense products.
 #include "common.cuh"
 
+#include <cuda_bf16.h>
+
 #include <algorithm>
 #include <map>
 #include <mutex>
@@ -967,12 +969,15 @@ __global__ void __launch_bounds__(SM32_THREADS, 1) k_band_solve_multi32(const in
 // shared-memory phase therefore touch 8 different bank groups.
 constexpr int WS_BULK_WARPS = 8;
 constexpr int WS_THREADS = (2 + WS_BULK_WARPS) * 32;
-// far rows per bulk thread per chunk: 2 for FP32 factors (64 KiB chunks), 1 for FP64 (32 KiB chunks, since
-// the FP64 local vector already takes half of the shared memory)
-template <typename T> constexpr int far_rpt() { return sizeof(T) == 4 ? 2 : 1; }
+// Factors are stored in S (float, double or bf16) and the arithmetic runs in T (double for FP64 factors,
+// float otherwise); a stored row is NB elements of S, 128 bytes (FP32, FP64) or 64 bytes (BF16).
+template <typename S> struct ComputeOf { using type = float; };
+template <> struct ComputeOf<double> { using type = double; };
+// far rows per bulk thread per chunk: 64 KiB chunks for FP32 and BF16 factors, 32 KiB for FP64 (the FP64
+// local vector already takes half of the shared memory)
+template <typename S> constexpr int far_rpt() { return sizeof(S) == 8 ? 1 : (sizeof(S) == 4 ? 2 : 4); }
 constexpr int WS_MAX_FAR_STAGES = 8;
-constexpr int WS_MAX_C0_STAGES = 8;
-constexpr long long WAIT_LIMIT = 1LL << 26;
+constexpr long long WAIT_CYCLES = 4000000000LL;  // about two seconds of SM clock
 
 
 __device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
@@ -999,13 +1004,16 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
   return done != 0;
 }
 
-// bounded wait; gives up early when another warp has raised the abort flag
+// bounded wait (about two seconds); gives up early when another warp has raised the abort flag
 __device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity, const volatile int *abort_flag) {
-  for (long long it = 0; it < WAIT_LIMIT; ++it) {
+  const long long t0 = clock64();
+  for (long long it = 0;; ++it) {
     if (mbar_try_wait(bar, parity)) return true;
-    if ((it & 63) == 63 && abort_flag && *abort_flag) return false;
+    if ((it & 63) == 63) {
+      if (abort_flag && *abort_flag) return false;
+      if (clock64() - t0 > WAIT_CYCLES) return false;
+    }
   }
-  return false;
 }
 
 __device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
@@ -1027,8 +1035,8 @@ __device__ __forceinline__ int step_barrier_or(int flag, int nthreads) {
   return res;
 }
 
-// 16-byte group loads of a factor row
-template <typename T> struct Vec16;
+// 16-byte group loads of a stored factor row, converted to the compute type
+template <typename S> struct Vec16;
 template <> struct Vec16<float> {
   static __device__ __forceinline__ void load(const float *p, float *o) {
     float4 v = *reinterpret_cast<const float4 *>(p);
@@ -1041,6 +1049,23 @@ template <> struct Vec16<double> {
     o[0] = v.x; o[1] = v.y;
   }
 };
+template <> struct Vec16<__nv_bfloat16> {
+  static __device__ __forceinline__ void load(const __nv_bfloat16 *p, float *o) {
+    uint4 u = *reinterpret_cast<const uint4 *>(p);
+    const uint32_t w[4] = {u.x, u.y, u.z, u.w};
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      o[2 * i] = __uint_as_float(w[i] << 16);             // element 2i (low half)
+      o[2 * i + 1] = __uint_as_float(w[i] & 0xffff0000u);  // element 2i+1 (high half)
+    }
+  }
+};
+template <typename S> __device__ __forceinline__ typename ComputeOf<S>::type ld_elem(const S *p) {
+  return (typename ComputeOf<S>::type)(*p);
+}
+template <> __device__ __forceinline__ float ld_elem<__nv_bfloat16>(const __nv_bfloat16 *p) {
+  return __bfloat162float(*p);
+}
 
 // geometry of panel p: rows of the panel inside the matrix, and its far rows [2 NB, rend)
 struct PanelGeo {
@@ -1051,16 +1076,19 @@ struct PanelGeo {
   __device__ int c0rows() const { return min(2 * NB, RP); }
 };
 
-template <typename T, int NB>
+template <typename S, int NB>
 __global__ void __launch_bounds__(WS_THREADS) k_band_solve_ws(int count, const int *nloc, const int *bwv,
                                                               const long long *band_off, const long long *node_off,
-                                                              const int *lnodes, const T *band, const double *r,
+                                                              const int *lnodes, const S *band, const double *r,
                                                               double *z, int atomic, int far_stages, int c0_stages,
                                                               int *status) {
-  static_assert(NB * sizeof(T) == 128, "factor rows are 128 bytes");
-  constexpr int E = 16 / sizeof(T);  // elements per 16-byte group
+  using T = typename ComputeOf<S>::type;
+  constexpr int ROWB = NB * (int)sizeof(S);  // bytes per stored row
+  static_assert(ROWB == 128 || ROWB == 64, "factor rows are 128 or 64 bytes");
+  constexpr int G = ROWB / 16;               // 16-byte groups per row
+  constexpr int E = 16 / sizeof(S);          // elements per 16-byte group
   constexpr int NT_STEP = (1 + WS_BULK_WARPS) * 32;
-  constexpr int RPT = far_rpt<T>();
+  constexpr int RPT = far_rpt<S>();
   constexpr int WS_FAR_ROWS = WS_BULK_WARPS * 32 * RPT;
   extern __shared__ __align__(128) unsigned char smdyn[];
   __shared__ __align__(8) uint64_t full_far[WS_MAX_FAR_STAGES], empty_far[WS_MAX_FAR_STAGES];
@@ -1077,11 +1105,11 @@ __global__ void __launch_bounds__(WS_THREADS) k_band_solve_ws(int count, const i
   const int np = (N + NB - 1) / NB;
   const int VN = np * NB + NB;  // padded local vector
   const PanelGeo geo{N, NB, RP, WS_FAR_ROWS};
-  const T *B = band + band_off[k];
+  const S *B = band + band_off[k];
   const int *ln = lnodes + node_off[k];
-  T *far_ring = reinterpret_cast<T *>(smdyn);
-  T *c0_ring = far_ring + (size_t)far_stages * WS_FAR_ROWS * NB;
-  T *v = c0_ring + (size_t)c0_stages * 2 * NB * NB;
+  S *far_ring = reinterpret_cast<S *>(smdyn);
+  S *c0_ring = far_ring + (size_t)far_stages * WS_FAR_ROWS * NB;
+  T *v = reinterpret_cast<T *>(c0_ring + (size_t)c0_stages * 2 * NB * NB);
   const int c0rows = geo.c0rows();
 
   if (threadIdx.x == 0) {
@@ -1120,7 +1148,7 @@ __global__ void __launch_bounds__(WS_THREADS) k_band_solve_ws(int count, const i
               break;
             }
             const int rows = min(WS_FAR_ROWS, nf - cix * WS_FAR_ROWS);
-            const uint32_t bytes = (uint32_t)rows * 128u;
+            const uint32_t bytes = (uint32_t)rows * (uint32_t)ROWB;
             mbar_expect_tx(&full_far[slot], bytes);
             bulk_g2s(far_ring + (size_t)slot * WS_FAR_ROWS * NB,
                      B + ((long long)q * RP + 2 * NB + (long long)cix * WS_FAR_ROWS) * NB, bytes, &full_far[slot]);
@@ -1146,7 +1174,7 @@ __global__ void __launch_bounds__(WS_THREADS) k_band_solve_ws(int count, const i
         const int p = (s < np) ? s : (2 * np - 1 - s);
         const unsigned char *src = reinterpret_cast<const unsigned char *>(B + (long long)p * RP * NB);
         unsigned char *dst = reinterpret_cast<unsigned char *>(c0_ring + (size_t)(s % c0_stages) * 2 * NB * NB);
-        for (int piece = lane; piece < c0rows * 8; piece += 32) cp_async16(dst + piece * 16, src + piece * 16);
+        for (int piece = lane; piece < c0rows * G; piece += 32) cp_async16(dst + piece * 16, src + piece * 16);
       }
       cp_async_commit();
     };
@@ -1162,7 +1190,7 @@ __global__ void __launch_bounds__(WS_THREADS) k_band_solve_ws(int count, const i
       __syncwarp();
       int fail = 0;
       {
-        const T *c0 = c0_ring + (size_t)(s % c0_stages) * 2 * NB * NB;
+        const S *c0 = c0_ring + (size_t)(s % c0_stages) * 2 * NB * NB;
         const int i = lane % NB;
         if (fwd) {
           T x = (lane < nb) ? v[k0 + lane] - near : (T)0;
@@ -1170,20 +1198,18 @@ __global__ void __launch_bounds__(WS_THREADS) k_band_solve_ws(int count, const i
 #pragma unroll
           for (int j = 0; j < NB; ++j) {
             const int jj = (j + i) % NB;
-            y += c0[i * NB + jj] * __shfl_sync(0xffffffffu, x, jj);
+            y += ld_elem(c0 + i * NB + jj) * __shfl_sync(0xffffffffu, x, jj);
           }
           if (lane < nb) v[k0 + lane] = y;
-          // near product for the next block (rows NB .. c0rows of the chunk)
+          // near product for the next block (rows NB .. c0rows of the chunk; the rest were not copied, their
+          // coefficients are taken as zero)
+          const bool nvalid = NB + i < c0rows;
           T nr = 0;
-          if (NB + i < c0rows) {
 #pragma unroll
-            for (int j = 0; j < NB; ++j) {
-              const int jj = (j + i) % NB;
-              nr += c0[(NB + i) * NB + jj] * __shfl_sync(0xffffffffu, y, jj);
-            }
-          } else {
-#pragma unroll
-            for (int j = 0; j < NB; ++j) (void)__shfl_sync(0xffffffffu, y, j);
+          for (int j = 0; j < NB; ++j) {
+            const int jj = (j + i) % NB;
+            const T coef = nvalid ? ld_elem(c0 + (NB + i) * NB + jj) : (T)0;
+            nr += coef * __shfl_sync(0xffffffffu, y, jj);
           }
           near = nr;
         } else {
@@ -1196,11 +1222,11 @@ __global__ void __launch_bounds__(WS_THREADS) k_band_solve_ws(int count, const i
           // near: L_{p+1,p}^T x_{p+1}; rows past the matrix hold zeros in v
           T nt = 0;
           const int nrows = c0rows - NB;
-          for (int rr = 0; rr < nrows; ++rr) nt += c0[(NB + rr) * NB + i] * v[k0 + NB + rr];
+          for (int rr = 0; rr < nrows; ++rr) nt += ld_elem(c0 + (NB + rr) * NB + i) * v[k0 + NB + rr];
           T t = (lane < nb) ? v[k0 + lane] - far - nt : (T)0;
           T x = 0;
 #pragma unroll
-          for (int cc = 0; cc < NB; ++cc) x += c0[cc * NB + i] * __shfl_sync(0xffffffffu, t, cc);
+          for (int cc = 0; cc < NB; ++cc) x += ld_elem(c0 + cc * NB + i) * __shfl_sync(0xffffffffu, t, cc);
           if (lane < nb) v[k0 + lane] = x;
         }
       }
@@ -1211,7 +1237,9 @@ __global__ void __launch_bounds__(WS_THREADS) k_band_solve_ws(int count, const i
     // ------------------------------------------------------------ bulk: far rows of panel p-1
     const int bw_id = wid - 2;
     const int tb = threadIdx.x - 64;
-    const int off = tb & 7;  // this thread's rows are congruent to off modulo 8
+    // rotation of this thread's group order: rows of 8 groups use (row mod 8); rows of 4 groups use
+    // ((row / 2) mod 4), which again spreads 8 consecutive rows over 8 distinct 16-byte bank groups
+    const int off = (G == 8) ? (tb & 7) : ((tb >> 1) & 3);
     int far_n = 0;
     for (int s = 0; s < nsteps; ++s) {
       const bool fwd = s < np;
@@ -1226,7 +1254,9 @@ __global__ void __launch_bounds__(WS_THREADS) k_band_solve_ws(int count, const i
         if (fwd) {
           // y_{q} in rotated group order
 #pragma unroll
-          for (int g = 0; g < 8; ++g) Vec16<T>::load(v + kq + ((g + off) & 7) * E, &yr[g * E]);
+          for (int g = 0; g < G; ++g)
+#pragma unroll
+            for (int e = 0; e < E; ++e) yr[g * E + e] = v[kq + ((g + off) % G) * E + e];
         } else {
 #pragma unroll
           for (int e = 0; e < NB; ++e) acc[e] = 0;
@@ -1239,15 +1269,15 @@ __global__ void __launch_bounds__(WS_THREADS) k_band_solve_ws(int count, const i
            for (int h = 0; h < RPT; ++h) {
             const int rr = cix * WS_FAR_ROWS + h * (WS_BULK_WARPS * 32) + tb;  // far row index (same offset mod 8)
             if (rr < nf) {
-              const T *row = far_ring + (size_t)slot * WS_FAR_ROWS * NB + (size_t)(h * WS_BULK_WARPS * 32 + tb) * NB;
+              const S *row = far_ring + (size_t)slot * WS_FAR_ROWS * NB + (size_t)(h * WS_BULK_WARPS * 32 + tb) * NB;
               const int vrow = kq + 2 * NB + rr;
               if (fwd) {
                 T s0 = 0, s1 = 0;
 #pragma unroll
-                for (int g = 0; g < 8; g += 2) {
+                for (int g = 0; g < G; g += 2) {
                   T ra[E], rb[E];
-                  Vec16<T>::load(row + ((g + off) & 7) * E, ra);
-                  Vec16<T>::load(row + ((g + 1 + off) & 7) * E, rb);
+                  Vec16<S>::load(row + ((g + off) % G) * E, ra);
+                  Vec16<S>::load(row + ((g + 1 + off) % G) * E, rb);
 #pragma unroll
                   for (int e = 0; e < E; ++e) {
                     s0 += ra[e] * yr[g * E + e];
@@ -1258,9 +1288,9 @@ __global__ void __launch_bounds__(WS_THREADS) k_band_solve_ws(int count, const i
               } else {
                 const T xv = v[vrow];
 #pragma unroll
-                for (int g = 0; g < 8; ++g) {
+                for (int g = 0; g < G; ++g) {
                   T ra[E];
-                  Vec16<T>::load(row + ((g + off) & 7) * E, ra);
+                  Vec16<S>::load(row + ((g + off) % G) * E, ra);
 #pragma unroll
                   for (int e = 0; e < E; ++e) acc[g * E + e] += ra[e] * xv;
                 }
@@ -1273,23 +1303,28 @@ __global__ void __launch_bounds__(WS_THREADS) k_band_solve_ws(int count, const i
           ++far_n;
         }
         if (!fwd) {
-          // reduce the column sums: lanes with equal (lane & 7) share the rotation
+          // reduce the column sums over the lanes that share a rotation (8 groups: equal lane & 7, i.e. lane
+          // bits 3 and 4 vary; 4 groups: equal (lane >> 1) & 3, i.e. bits 0, 3 and 4 vary), then undo the
+          // rotation of one representative lane per rotation class
 #pragma unroll
           for (int e = 0; e < NB; ++e) {
+            if (G == 4) acc[e] += __shfl_xor_sync(0xffffffffu, acc[e], 1);
             acc[e] += __shfl_xor_sync(0xffffffffu, acc[e], 8);
             acc[e] += __shfl_xor_sync(0xffffffffu, acc[e], 16);
           }
-          if (lane < 8) {
+          const bool rep_lane = (G == 8) ? (lane < 8) : ((lane & 0x19) == 0);
+          if (rep_lane) {
+            const int cls = (G == 8) ? lane : ((lane >> 1) & 3);
 #pragma unroll
-            for (int g = 0; g < 8; ++g)
+            for (int g = 0; g < G; ++g)
 #pragma unroll
-              for (int e = 0; e < E; ++e) stage[bw_id][lane][((g + lane) & 7) * E + e] = acc[g * E + e];
+              for (int e = 0; e < E; ++e) stage[bw_id][cls][((g + cls) % G) * E + e] = acc[g * E + e];
           }
           __syncwarp();
           if (lane < NB) {
             T sum = 0;
 #pragma unroll
-            for (int c = 0; c < 8; ++c) sum += stage[bw_id][c][lane];
+            for (int c = 0; c < G; ++c) sum += stage[bw_id][c][lane];
             red[q & 1][bw_id][lane] = sum;
           }
           __syncwarp();
@@ -1508,6 +1543,17 @@ void build_local_sets(hplmm_ctx *c) {
   }
 }
 
+__global__ void k_to_bf16(const float *src, __nv_bfloat16 *dst, long long n) {
+  long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) dst[i] = __float2bfloat16_rn(src[i]);
+}
+
+void to_bf16(const float *src, __nv_bfloat16 *dst, long long n, cudaStream_t s) {
+  if (n <= 0) return;
+  k_to_bf16<<<grid_for(n, 256), 256, 0, s>>>(src, dst, n);
+  HP_CHECK_LAUNCH();
+}
+
 void factor_local(hplmm_ctx *c, LocalSet &S, hplmm_prec prec) {
   if (S.count == 0) return;
   int where = (&S == &c->grains) ? 1 : 2;
@@ -1517,6 +1563,15 @@ void factor_local(hplmm_ctx *c, LocalSet &S, hplmm_prec prec) {
   else
     layout_and_factor<float>(c, S, where);
   S.prec = prec;
+  // BF16 form: the apply streams a BF16 copy of the FP32 factors (FP32 arithmetic)
+  S.apply_bf16 = prec == HPLMM_FP32 && c->opt.apply_prec == HPLMM_BF16;
+  if (S.apply_bf16) {
+    long long n = S.h_band_off.empty() ? 0 : S.h_band_off.back();
+    S.band16.alloc(std::max<long long>(n, 1));
+    to_bf16(S.band32.p, S.band16.p, n, c->stream);
+  } else {
+    S.band16.release();
+  }
 }
 
 template <typename T>
@@ -1567,34 +1622,52 @@ void solve_local_multi_f32(hplmm_ctx *c, LocalSet &S, float *X, const Buf<long l
   solve_multi_t<float>(c, S, X, x_off, x_ld, h_ld);
 }
 
+// shared-memory plan of the smoother solve for a set: bytes of one far stage, one diagonal stage and the
+// padded local vector (stored-row width 128 bytes for FP32/FP64 factors, 64 bytes for BF16)
+struct SolvePlan {
+  size_t far_slot, c0_slot, vbytes;
+};
+
+static SolvePlan solve_plan(const LocalSet &S) {
+  const bool f64 = S.prec == HPLMM_FP64;
+  const int NBv = f64 ? 16 : 32;
+  const size_t esz = f64 ? 8 : 4;  // local vector element
+  const size_t rowb = S.apply_bf16 ? 64 : 128;
+  const int rpt = f64 ? far_rpt<double>() : (S.apply_bf16 ? far_rpt<__nv_bfloat16>() : far_rpt<float>());
+  int vmax = 0;
+  for (int k = 0; k < S.count; ++k)
+    if (S.h_n[k] > 0) vmax = std::max(vmax, ((S.h_n[k] + NBv - 1) / NBv) * NBv + NBv);
+  SolvePlan pl;
+  pl.vbytes = ((esz * (size_t)std::max(vmax, 1) + 127) / 128) * 128;
+  pl.far_slot = (size_t)WS_BULK_WARPS * 32 * rpt * rowb;
+  pl.c0_slot = (size_t)2 * NBv * rowb;
+  return pl;
+}
+
 void smoother_apply(hplmm_ctx *c, LocalSet &S, const double *r_pad, double *z_pad, bool atomic) {
   if (S.count == 0) return;
   ProfScope ps(c, (&S == &c->grains) ? HPLMM_PH_APPLY_GRAINS : HPLMM_PH_APPLY_CONTACTS);
   cudaStream_t s = c->stream;
-  const bool f64 = S.prec == HPLMM_FP64;
-  const int NBv = f64 ? 16 : 32;
-  const size_t esz = f64 ? 8 : 4;
-  // shared memory: far ring (32 KiB stages), diagonal+near ring (2 NB rows of 128 bytes), padded local vector
-  int vmax = 0;
-  for (int k = 0; k < S.count; ++k)
-    if (S.h_n[k] > 0) vmax = std::max(vmax, ((S.h_n[k] + NBv - 1) / NBv) * NBv + NBv);
-  const size_t vbytes = ((esz * (size_t)std::max(vmax, 1) + 127) / 128) * 128;
-  const size_t far_stage = (size_t)WS_BULK_WARPS * 32 * (f64 ? far_rpt<double>() : far_rpt<float>()) * 128;
-  const size_t c0_stage = (size_t)2 * NBv * 128;
+  const SolvePlan pl = solve_plan(S);
   const size_t budget = 216 * 1024;
-  HP_REQUIRE(vbytes + 2 * c0_stage + 2 * far_stage <= budget, HPLMM_ERR_INVALID,
-             "local problem too large for the smoother (" + std::to_string(vmax) + " local DOFs)");
+  HP_REQUIRE(pl.vbytes + 2 * pl.c0_slot + 2 * pl.far_slot <= budget, HPLMM_ERR_INVALID,
+             "local problem too large for the smoother (" + std::to_string(pl.vbytes) + " bytes of local vector)");
   // depths: the tuner's choice when there is one, else 4 diagonal stages and as many far stages as fit
   int c0s = S.tuned_c0_stages > 0 ? S.tuned_c0_stages : 4;
-  if (vbytes + c0s * c0_stage + 2 * far_stage > budget) c0s = 2;
-  int fs = (int)std::min<size_t>(WS_MAX_FAR_STAGES, (budget - vbytes - c0s * c0_stage) / far_stage);
+  if (pl.vbytes + c0s * pl.c0_slot + 2 * pl.far_slot > budget) c0s = 2;
+  int fs = (int)std::min<size_t>(WS_MAX_FAR_STAGES, (budget - pl.vbytes - c0s * pl.c0_slot) / pl.far_slot);
   if (S.tuned_far_stages > 0) fs = std::min(fs, S.tuned_far_stages);
-  const size_t smem = (size_t)fs * far_stage + (size_t)c0s * c0_stage + vbytes;
-  if (f64) {
+  const size_t smem = (size_t)fs * pl.far_slot + (size_t)c0s * pl.c0_slot + pl.vbytes;
+  if (S.prec == HPLMM_FP64) {
     auto kern = k_band_solve_ws<double, 16>;
     HP_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     kern<<<S.count, WS_THREADS, smem, s>>>(S.count, S.n.p, S.bw.p, S.band_off.p, S.node_off.p, S.lnodes.p,
                                            S.band64.p, r_pad, z_pad, atomic ? 1 : 0, fs, c0s, c->status.p);
+  } else if (S.apply_bf16) {
+    auto kern = k_band_solve_ws<__nv_bfloat16, 32>;
+    HP_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    kern<<<S.count, WS_THREADS, smem, s>>>(S.count, S.n.p, S.bw.p, S.band_off.p, S.node_off.p, S.lnodes.p,
+                                           S.band16.p, r_pad, z_pad, atomic ? 1 : 0, fs, c0s, c->status.p);
   } else {
     auto kern = k_band_solve_ws<float, 32>;
     HP_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
@@ -1623,7 +1696,7 @@ std::map<TuneKey, std::pair<int, int>> g_tune_cache;
 static void tune_set(hplmm_ctx *c, LocalSet &S, bool atomic) {
   S.tuned_far_stages = S.tuned_c0_stages = 0;
   if (S.count == 0) return;
-  TuneKey key{S.count, 0, 0, (int)S.prec};
+  TuneKey key{S.count, 0, 0, (int)S.prec + (S.apply_bf16 ? 8 : 0)};
   for (int k = 0; k < S.count; ++k) {
     key.nmax = std::max(key.nmax, S.h_n[k]);
     key.bwmax = std::max(key.bwmax, S.h_bw[k]);
@@ -1637,13 +1710,8 @@ static void tune_set(hplmm_ctx *c, LocalSet &S, bool atomic) {
       return;
     }
   }
-  const bool f64 = S.prec == HPLMM_FP64;
-  const int NBv = f64 ? 16 : 32;
-  const size_t esz = f64 ? 8 : 4;
-  const int vmax = ((key.nmax + NBv - 1) / NBv) * NBv + NBv;
-  const size_t vbytes = ((esz * (size_t)vmax + 127) / 128) * 128;
-  const size_t far_slot = (size_t)WS_BULK_WARPS * 32 * (f64 ? far_rpt<double>() : far_rpt<float>()) * 128;
-  const size_t c0_slot = (size_t)2 * NBv * 128, budget = 216 * 1024;
+  const SolvePlan pl = solve_plan(S);
+  const size_t vbytes = pl.vbytes, far_slot = pl.far_slot, c0_slot = pl.c0_slot, budget = 216 * 1024;
   cudaStream_t s = c->stream;
   cudaEvent_t e0, e1;
   HP_CUDA(cudaEventCreate(&e0));

@@ -131,6 +131,36 @@ def test_mixed_precision_forms(name, local, applyp):
     s.close()
 
 
+@pytest.mark.parametrize("name", ["cube16_n4", "porous32_n4"])
+def test_bf16_apply_form(name):
+    # BF16 copies of the FP32 local factors, basis panels and A_hat inside the apply (FP32 arithmetic, FP64
+    # coarse solve): the apply differs from the FP64 oracle by BF16 rounding (8-bit significand, unit roundoff
+    # 2^-9 ~ 2e-3) amplified by the local problems' conditioning; the outer FP64 FGMRES still reaches the FP64
+    # residual, and the solution matches the oracle's to the tolerance's accuracy
+    p, opt, sysm, M = oracle_case(name)
+    s = gpu_solver(name, local_prec="fp32", apply_prec="bf16")
+    rng = np.random.default_rng(2)
+    r = rng.standard_normal(sysm.n_dof)
+    e_apply = rel(_n(s.apply(_t(r))), M.apply(r))
+    print(f"{name}: BF16 apply relative error vs FP64 oracle {e_apply:.3e}")
+    assert 1e-5 < e_apply < 0.2, e_apply  # BF16 rounding is visible, but the operator is the same
+    x, rc, st = s.solve(tol=1e-8)
+    xn = _n(x)
+    assert rc == 0
+    assert np.linalg.norm(sysm.b - sysm.A @ xn) / np.linalg.norm(sysm.b) <= 1e-8
+    x_ref, st_ref = oracle_solution(name)
+    assert rel(xn, x_ref) < 1e-6
+    print(f"{name}: BF16 form {st.iters} iterations (FP64 oracle {st_ref['iters']})")
+    s.close()
+
+
+def test_bf16_needs_fp32_locals():
+    import paper_2509_19777_gb300 as hp
+    with pytest.raises(hp.HplmmError) as ei:
+        hp.Solver(local_prec="fp64", apply_prec="bf16")
+    assert ei.value.code == hp.HPLMM_ERR_INVALID
+
+
 def test_state_errors_and_arguments():
     import paper_2509_19777_gb300 as hp
     s = hp.Solver()
