@@ -16,6 +16,9 @@ Modules, in the paper's order:
   precond       Section 4.1, Eqs. multi_precond and local_smoother: the multiplicative two-level M
   gmres         Section 5: right-preconditioned restarted GMRES
   accuracy      Eq. err_metric: first-pass L2 errors of displacement and maximum shear stress
+  warmstart     learned warm start of the local basis solves (3-D convolutional network, Adam) and the
+                block-Jacobi preconditioned CG basis solver it feeds (an optional iterative path beside the
+                paper's exact local solves of Eqs. col_pk and col_cg)
 
 Parity status: every function is pinned by tests/test_oracle_*.py against
 closed forms, invariants or brute force; see the pin list in each module.

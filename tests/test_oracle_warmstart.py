@@ -1,0 +1,124 @@
+"""Pins for oracle/warmstart.py: the learned warm start of the local basis
+solves and the preconditioned CG basis solver (no counterpart in the paper's
+own runs, which solve the local problems exactly; Eqs. col_pk, col_cg)."""
+import numpy as np
+import scipy.sparse as sp
+import scipy.sparse.linalg as spla
+
+import synth
+from oracle import precond, warmstart as ws
+from oracle.decomposition import cartesian_partition
+
+
+def _toy(seed, B=2, D=4, channels=(2, 3, 3, 2)):
+    rng = np.random.default_rng(seed)
+    x = rng.standard_normal((B, channels[0], D, D, D))
+    t = rng.standard_normal((B, channels[-1], D, D, D))
+    valid = (rng.uniform(size=t.shape) < 0.7).astype(np.float64)
+    theta = rng.standard_normal(ws.n_params(channels)) * 0.3
+    return x, t, valid, theta
+
+
+def test_gradient_matches_central_differences():
+    channels = (2, 3, 3, 2)
+    x, t, valid, theta = _toy(0, channels=channels)
+    loss, g = ws.loss_and_grad(theta, x, t, valid, channels)
+    rng = np.random.default_rng(1)
+    idx = rng.choice(theta.size, size=40, replace=False)
+    h = 1e-6
+    for i in idx:
+        tp, tm = theta.copy(), theta.copy()
+        tp[i] += h
+        tm[i] -= h
+        fd = (ws.loss_and_grad(tp, x, t, valid, channels)[0] - ws.loss_and_grad(tm, x, t, valid, channels)[0]) / (2 * h)
+        assert abs(fd - g[i]) <= 1e-6 * max(1.0, abs(fd)), (i, fd, g[i])
+
+
+def test_delta_kernel_shifts_the_input():
+    # a single tap (tz, ty, tx) = (2, 1, 0) with weight 1 gives y[z][y][x] = x[z+1][y][x-1] (zeros outside)
+    rng = np.random.default_rng(2)
+    x = rng.standard_normal((1, 1, 5, 5, 5))
+    W = np.zeros((1, 1, 3, 3, 3))
+    W[0, 0, 2, 1, 0] = 1.0
+    y = ws.conv3d(x, W, np.zeros(1))
+    ref = np.zeros_like(x)
+    ref[0, 0, :4, :, 1:] = x[0, 0, 1:, :, :4]
+    assert np.array_equal(y, ref)
+
+
+def test_conv_is_linear_and_bias_is_constant():
+    rng = np.random.default_rng(3)
+    x1, x2 = rng.standard_normal((2, 1, 2, 4, 4, 4))
+    W = rng.standard_normal((3, 2, 3, 3, 3))
+    b = rng.standard_normal(3)
+    y = ws.conv3d(x1 + 2 * x2, W, b)
+    y1 = ws.conv3d(x1, W, np.zeros(3))
+    y2 = ws.conv3d(x2, W, np.zeros(3))
+    assert np.allclose(y, y1 + 2 * y2 + b[None, :, None, None, None], atol=1e-12)
+
+
+def test_adam_first_step_and_convergence():
+    # the bias-corrected first step moves every coordinate by lr * g / (|g| + eps) ~ lr * sign(g)
+    th = np.array([1.0, -2.0])
+    g = np.array([0.5, -4.0])
+    t1, m, v = ws.adam_step(th, g, np.zeros(2), np.zeros(2), 1, 0.1)
+    assert np.allclose(t1, th - 0.1 * g / (np.abs(g) + 1e-8), atol=1e-15)
+    # and it minimises (w - 3)^2
+    w, m, v = np.array([0.0]), np.zeros(1), np.zeros(1)
+    for k in range(1, 3001):
+        w, m, v = ws.adam_step(w, 2 * (w - 3.0), m, v, k, 0.05)
+    assert abs(w[0] - 3.0) < 1e-3
+
+
+def test_param_count_and_packing():
+    assert ws.n_params() == 32 * 5 * 27 + 32 + 2 * (32 * 32 * 27 + 32) + 3 * 32 * 27 + 3
+    th = ws.init_params(4)
+    assert th.dtype == np.float32 and th.size == ws.n_params()
+    assert np.array_equal(ws.pack(ws.unpack(th)), th)
+
+
+def test_sample_reproduces_the_basis_column():
+    # the target channels of a grain's sample, mapped back to DOFs, are its exact basis column; the rhs
+    # channels times s are the right-hand side, and every free DOF of the grain is a valid entry
+    p = synth.make_workload("cube16", 0)
+    sysm, M = precond.build(p, precond.Options(n_mortar=2, contact_halfwidth=1))
+    part = cartesian_partition(p.mask.shape, p.grains)
+    A = sysm.A.tocsr()
+    g = 3
+    I = M.dec.grain_dofs[g]
+    o = ws.grain_box_origin(sysm, part, g)
+    fields, ebar = ws.grain_fields(sysm, part, g, o)
+    pos = ws.dof_positions(sysm, I, o)
+    assert np.all((np.stack(pos[1:]) >= 0) & (np.stack(pos[1:]) < ws.GRID))
+    rng = np.random.default_rng(5)
+    rhs = rng.standard_normal(I.size)
+    x = spla.spsolve(A[I][:, I].tocsc(), rhs)
+    inp, tgt, valid, s = ws.make_sample(fields, ebar, pos, rhs, x)
+    assert valid.sum() == I.size
+    assert np.allclose(inp[2:][pos] * s, rhs, rtol=0, atol=1e-12)
+    assert np.allclose(ws.guess_from_prediction(tgt, ebar, s, pos), x, rtol=1e-12, atol=0)
+    assert inp[0].sum() == 16 * 16 * 16 / 8  # a solid 8^3 grain of cube16 (2x2x2 grains)
+
+
+def test_pcg_matches_direct_solve_and_warm_start_helps():
+    p = synth.make_workload("tiny10", 5)
+    sysm, M = precond.build(p, precond.Options(n_mortar=2, contact_halfwidth=1))
+    A = sysm.A.tocsr()
+    I = M.dec.grain_dofs[0]
+    Agg = A[I][:, I]
+    node = sysm.free[I] // 3
+    Dinv = ws.block_jacobi_inverse(Agg, node)
+    rng = np.random.default_rng(6)
+    b = rng.standard_normal(I.size)
+    x_ref = spla.spsolve(Agg.tocsc(), b)
+    x, its, rel0 = ws.pcg(Agg, b, Dinv, tol=1e-10)
+    assert np.linalg.norm(x - x_ref) <= 1e-8 * np.linalg.norm(x_ref)
+    assert rel0 == 1.0 and its > 0
+    # a guess within 0.1% of the solution starts from a smaller residual and needs fewer iterations
+    x0 = x_ref + 1e-3 * np.linalg.norm(x_ref) / np.sqrt(I.size) * rng.standard_normal(I.size)
+    xw, its_w, rel0_w = ws.pcg(Agg, b, Dinv, x0=x0, tol=1e-10)
+    assert rel0_w < rel0 and its_w < its
+    assert np.linalg.norm(xw - x_ref) <= 1e-8 * np.linalg.norm(x_ref)
+    # the block-Jacobi operator is the inverse of the node-diagonal part
+    Bd = Agg.toarray() * (node[:, None] == node[None, :])
+    assert np.allclose(Dinv.toarray() @ Bd, np.eye(I.size), atol=1e-10)
