@@ -56,6 +56,7 @@ def parse():
                     help="profiling mode: time only the chosen form (no plain, e2e or CPU legs); prints a short line")
     ap.add_argument("--workload", default=WORKLOAD, help="synthetic workload for --quick runs (e.g. porous32)")
     ap.add_argument("--form", default="chosen", choices=sorted(FORMS), help="form timed by --quick runs")
+    ap.add_argument("--no-tune", action="store_true", help="--quick runs without the set-up tuner (profiling)")
     return ap.parse_args()
 
 
@@ -381,7 +382,7 @@ def main():
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")   # 256 MiB > 129 MB L2
     if args.quick:
         problem = synth.make_workload(args.workload, args.seed + rank)
-        form = FORMS[args.form]
+        form = dict(FORMS[args.form], autotune=False) if args.no_tune else FORMS[args.form]
         st_, _, tt, stt, _, _, _, launches = run_form(hp, problem, form, args.steps, args.warmup, flush, stream)
         st_.close()
         sq, _, tq, stq, prof, costs, sizes, _ = run_form(hp, problem, dict(form, use_graph=False), args.steps,
