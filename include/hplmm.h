@@ -68,7 +68,17 @@ typedef struct {
   int profile;           /* 1: time every phase with CUDA events on the context's stream (hplmm_get_profile) */
   int autotune;          /* 1: at set-up, time the smoother solve's pipeline depths on this problem's local
                             problems and keep the fastest (cached per problem-size bucket for the process) */
+  int basis_solver;      /* local basis solves (Eqs. col_pk, col_cg): HPLMM_BASIS_DIRECT (default, the exact
+                            banded Cholesky solve), HPLMM_BASIS_PCG (block-Jacobi CG from a zero guess) or
+                            HPLMM_BASIS_PCG_WARM (CG from the learned warm start); the iterative forms need
+                            local_prec = FP32, and a column that misses basis_tol after basis_max_iters
+                            iterations makes its grain fall back to the exact solve */
+  double basis_tol;      /* relative residual of the iterative basis solves (default 1e-6) */
+  int basis_max_iters;   /* iteration cap of the iterative basis solves (default 3000) */
+  int keep_basis_rhs;    /* 1: keep a copy of the basis right-hand sides after set-up (hplmm_ws_collect) */
 } hplmm_options;
+
+enum { HPLMM_BASIS_DIRECT = 0, HPLMM_BASIS_PCG = 1, HPLMM_BASIS_PCG_WARM = 2 };
 
 /* Boundary conditions on the six faces of the image box, in the order
  * x=0, x=nx, y=0, y=ny, z=0, z=nz (Eq. BC).  fix[f][d] != 0 prescribes
@@ -243,6 +253,63 @@ typedef struct {
 } hplmm_costs;
 
 hplmm_status hplmm_get_costs(hplmm_ctx *ctx, hplmm_costs *out);
+
+/* ---- learned warm start of the local basis solves --------------------------------------------
+ * The paper solves the local basis problems exactly.  The library can instead solve them by
+ * block-Jacobi preconditioned conjugate gradients, optionally started from the guess of a small 3-D
+ * convolutional network (options.basis_solver).  A sample of one basis problem lives on the 17^3 node
+ * grid of its grain (origin = minimum corner of the grain's solid voxels, at most 16 voxels per axis):
+ * channel 0 = solid voxels of the grain, channel 1 = their log E, channels 2-4 = the right-hand side
+ * divided by its RMS; the network predicts the solution divided by its RMS (CG rescales the guess by the
+ * factor that minimises its A-norm error, so only the solution's shape is learned).  Network:
+ * 3x3x3 convolutions with dilations 1, 2, 4, 8, channels 5 -> 32 -> 32 -> 32 -> 3, ReLU after the first
+ * three; parameters (FP32) per layer W[co][ci][tz][ty][tx] then bias[co].  Training (Adam) and inference run in the library's own
+ * kernels; inference stores weights and activations in BF16. */
+
+/* Number of network parameters (floats). */
+long long hplmm_ws_num_params(void);
+
+/* Set (HOST float32 [n], n = hplmm_ws_num_params()) or read the network parameters; setting resets the
+ * optimiser state. */
+hplmm_status hplmm_ws_set_params(hplmm_ctx *ctx, const float *params, long long n);
+hplmm_status hplmm_ws_get_params(hplmm_ctx *ctx, float *params, long long n);
+
+/* Append the current set-up's basis problems (right-hand sides and their exact solutions) to the context's
+ * training set; needs a set-up with local_prec = FP32, basis_solver = HPLMM_BASIS_DIRECT and
+ * keep_basis_rhs = 1.  n_total (HOST, may be NULL) receives the number of samples held.  Synchronises. */
+hplmm_status hplmm_ws_collect(hplmm_ctx *ctx, long long *n_total);
+hplmm_status hplmm_ws_clear(hplmm_ctx *ctx);
+
+/* Copy samples [first, first + count) of the training set out (DEVICE float32: in [count][5][17^3],
+ * target and valid [count][3][17^3]; any pointer may be NULL).  Synchronises. */
+hplmm_status hplmm_ws_get_samples(hplmm_ctx *ctx, long long first, long long count, float *in, float *target,
+                                  float *valid);
+
+/* Adam steps (lr, beta1 0.9, beta2 0.999, eps 1e-8) over minibatches of `batch` samples taken in the
+ * order given (HOST int32 [n_order], indices into the training set: the caller draws the shuffle).
+ * loss (HOST double [n_order / batch], may be NULL) receives the loss before each step.  Synchronises. */
+hplmm_status hplmm_ws_train(hplmm_ctx *ctx, const int32_t *order, long long n_order, int batch, double lr,
+                            double *loss);
+
+/* Masked mean-squared loss and its gradient with respect to the parameters (FP32, the training path)
+ * for n samples on a D^3 grid (3 <= D <= 17): in DEVICE float32 [n][5][D^3], target and valid DEVICE
+ * float32 [n][3][D^3], grad DEVICE float32 [hplmm_ws_num_params()], loss HOST.  Synchronises. */
+hplmm_status hplmm_ws_loss_grad(hplmm_ctx *ctx, const float *in, const float *target, const float *valid, int n,
+                                int D, double *loss, float *grad);
+
+typedef struct {
+  long long columns;          /* basis problems solved */
+  long long iters_total;      /* CG iterations summed over the columns (the cap for columns that missed it) */
+  long long iters_max;
+  long long fallback_columns; /* columns that missed basis_tol */
+  long long fallback_grains;  /* grains re-solved exactly because of them */
+  double init_rel_res_mean;   /* mean over columns of ||b - A x0|| / ||b|| (1 for a zero guess) */
+  double t_net_ms;            /* network inference (warm start) */
+  double t_pcg_ms;            /* CG iterations */
+} hplmm_basis_stats;
+
+/* Statistics of the last set-up's iterative basis solves (zeros after an exact one).  HOST output. */
+hplmm_status hplmm_get_basis_stats(hplmm_ctx *ctx, hplmm_basis_stats *out);
 
 /* Message of the most recent error in this context (never NULL). */
 const char *hplmm_last_error(const hplmm_ctx *ctx);

@@ -18,16 +18,19 @@ Sample of one basis problem (grain g, right-hand side column a):
   ch 1      log E of that voxel (0 elsewhere)
   ch 2..4   the right-hand side's x, y, z components on the grain's free DOFs,
             divided by s = RMS of the right-hand side over those DOFs
-  target    the basis column (exact local solve) times ebar / s, where ebar =
-            exp(mean log E over the grain's solid voxels), on the same DOFs
+  target    the basis column (exact local solve) divided by its RMS over the
+            grain's free DOFs, on the same positions
   valid     1 where a free DOF of the grain sits, else 0
-A prediction q becomes the initial guess x0 = q * s / ebar on the valid DOFs.
+A prediction q, read at the valid positions, is the direction of the initial
+guess: CG scales it by the factor that minimises the A-norm error along it,
+so only the shape of the solution has to be learned.
 
-Network: 4 layers of 3x3x3 convolutions with zero padding ("same" size),
-channels 5 -> 32 -> 32 -> 32 -> 3, bias per output channel, ReLU after the
-first three.  Flat parameter vector (the exchange format with the library):
-for each layer in order, W[co][ci][tz][ty][tx] (tap (tz,ty,tx) reads offset
-(tz-1, ty-1, tx-1) in (z, y, x)), then bias[co].
+Network: 4 layers of 3x3x3 convolutions with zero padding ("same" size) and
+dilations 1, 2, 4, 8 (receptive field 31 nodes: an output sees inputs up to 15
+nodes away along each axis, nearly the whole 17^3 grid), channels 5 -> 32 -> 32 -> 32 -> 3, bias per output channel, ReLU
+after the first three.  Flat parameter vector (the exchange format with the library):
+for each layer in order, W[co][ci][tz][ty][tx] (tap (tz,ty,tx) of a layer with
+dilation d reads offset ((tz-1)d, (ty-1)d, (tx-1)d) in (z, y, x)), then bias[co].
 Loss: sum over valid entries of (q - target)^2 divided by the number of valid
 entries.  Optimiser: Adam (Kingma and Ba, 2015) with bias correction.
 
@@ -42,6 +45,7 @@ import numpy as np
 
 GRID = 17
 CHANNELS = (5, 32, 32, 32, 3)
+DILATIONS = (1, 2, 4, 8)
 
 
 def layer_shapes(channels=CHANNELS):
@@ -72,6 +76,8 @@ def _shift(x, dz, dy, dx):
     """y[..., z, y, x] = x[..., z+dz, y+dy, x+dx] with zeros outside."""
     out = np.zeros_like(x)
     D = x.shape[-3:]
+    if abs(dz) >= D[0] or abs(dy) >= D[1] or abs(dx) >= D[2]:
+        return out  # the shifted grid lies entirely outside
     sz = slice(max(0, -dz), D[0] - max(0, dz))
     sy = slice(max(0, -dy), D[1] - max(0, dy))
     sx = slice(max(0, -dx), D[2] - max(0, dx))
@@ -82,31 +88,32 @@ def _shift(x, dz, dy, dx):
     return out
 
 
-def conv3d(x, W, b):
+def conv3d(x, W, b, dil=1):
     """x [B][ci][D][D][D] -> y [B][co][D][D][D]:
-    y[n][o][p] = b[o] + sum_{i, t} W[o][i][t] x[n][i][p + t - 1] (zero padding)."""
+    y[n][o][p] = b[o] + sum_{i, t} W[o][i][t] x[n][i][p + (t - 1) dil] (zero padding)."""
     B = x.shape[0]
     co = W.shape[0]
     y = np.broadcast_to(b[None, :, None, None, None], (B, co) + x.shape[2:]).astype(np.float64).copy()
     for tz in range(3):
         for ty in range(3):
             for tx in range(3):
-                xs = _shift(x, tz - 1, ty - 1, tx - 1)
+                xs = _shift(x, (tz - 1) * dil, (ty - 1) * dil, (tx - 1) * dil)
                 y += np.einsum("oi,nizyx->nozyx", W[:, :, tz, ty, tx], xs)
     return y
 
 
-def conv3d_backward(x, W, gy):
+def conv3d_backward(x, W, gy, dil=1):
     """Gradients of conv3d: (dL/dx, dL/dW, dL/db) given dL/dy."""
     gx = np.zeros_like(x, dtype=np.float64)
     gW = np.zeros_like(W, dtype=np.float64)
     for tz in range(3):
         for ty in range(3):
             for tx in range(3):
-                xs = _shift(x, tz - 1, ty - 1, tx - 1)
+                dz, dy, dx = (tz - 1) * dil, (ty - 1) * dil, (tx - 1) * dil
+                xs = _shift(x, dz, dy, dx)
                 gW[:, :, tz, ty, tx] = np.einsum("nozyx,nizyx->oi", gy, xs)
-                # y[p] uses x[p + t - 1]: the adjoint moves gy by the opposite offset
-                gx += _shift(np.einsum("oi,nozyx->nizyx", W[:, :, tz, ty, tx], gy), -(tz - 1), -(ty - 1), -(tx - 1))
+                # y[p] uses x[p + offset]: the adjoint moves gy by the opposite offset
+                gx += _shift(np.einsum("oi,nozyx->nizyx", W[:, :, tz, ty, tx], gy), -dz, -dy, -dx)
     gb = gy.sum(axis=(0, 2, 3, 4))
     return gx, gW, gb
 
@@ -116,7 +123,7 @@ def forward(theta, x, channels=CHANNELS):
     acts = [np.asarray(x, np.float64)]
     layers = unpack(np.asarray(theta, np.float64), channels)
     for li, (W, b) in enumerate(layers):
-        z = conv3d(acts[-1], W, b)
+        z = conv3d(acts[-1], W, b, DILATIONS[li])
         acts.append(np.maximum(z, 0.0) if li + 1 < len(layers) else z)
     return acts
 
@@ -134,7 +141,7 @@ def loss_and_grad(theta, x, target, valid, channels=CHANNELS):
     grads = [None] * len(layers)
     for li in range(len(layers) - 1, -1, -1):
         W, b = layers[li]
-        gx, gW, gb = conv3d_backward(acts[li], W, g)
+        gx, gW, gb = conv3d_backward(acts[li], W, g, DILATIONS[li])
         grads[li] = (gW, gb)
         if li > 0:
             g = gx * (acts[li] > 0.0)  # through the ReLU that produced acts[li]
@@ -175,7 +182,7 @@ def grain_box_origin(system, grain_of_voxel, g):
 
 
 def grain_fields(system, grain_of_voxel, g, origin):
-    """Channels 0 and 1 ([2][17][17][17]) and ebar of grain g."""
+    """Channels 0 and 1 ([2][17][17][17]) and exp(mean log E) of grain g."""
     f = np.zeros((2, GRID, GRID, GRID))
     sel = (np.asarray(grain_of_voxel) == g) & system.mesh.solid
     kk, jj, ii = np.nonzero(sel)
@@ -195,8 +202,8 @@ def dof_positions(system, dofs, origin):
     return comp, ijk[:, 2] - origin[2], ijk[:, 1] - origin[1], ijk[:, 0] - origin[0]
 
 
-def make_sample(fields, ebar, pos, rhs, x_true=None):
-    """(input [5][17]^3, target [3][17]^3 or None, valid [3][17]^3, s) for one right-hand side."""
+def make_sample(fields, pos, rhs, x_true=None):
+    """(input [5][17]^3, target [3][17]^3 or None, valid [3][17]^3) for one right-hand side."""
     comp, z, y, x = pos
     s = float(np.sqrt(np.mean(rhs * rhs))) if rhs.size else 0.0
     inp = np.zeros((5, GRID, GRID, GRID))
@@ -208,14 +215,16 @@ def make_sample(fields, ebar, pos, rhs, x_true=None):
         inp[2 + comp, z, y, x] = rhs / s
     if x_true is not None:
         tgt = np.zeros((3, GRID, GRID, GRID))
-        if s > 0.0:
-            tgt[comp, z, y, x] = x_true * ebar / s
-    return inp, tgt, valid, s
+        sx = float(np.sqrt(np.mean(x_true * x_true))) if x_true.size else 0.0
+        if s > 0.0 and sx > 0.0:
+            tgt[comp, z, y, x] = x_true / sx
+    return inp, tgt, valid
 
 
-def guess_from_prediction(q, ebar, s, pos):
+def guess_from_prediction(q, pos):
+    """Direction of the initial guess on the grain's DOFs (CG rescales it, see pcg)."""
     comp, z, y, x = pos
-    return q[comp, z, y, x] * s / ebar
+    return q[comp, z, y, x]
 
 
 # ------------------------------------------------------------------ iterative basis solve
@@ -237,10 +246,15 @@ def block_jacobi_inverse(A, dofs_comp_node):
     return sp.csr_matrix((np.concatenate(vals), (np.concatenate(rows), np.concatenate(cols))), shape=(n, n))
 
 
-def pcg(A, b, Minv, x0=None, tol=1e-6, max_iters=5000):
+def pcg(A, b, Minv, x0=None, tol=1e-6, max_iters=5000, scale_guess=True):
     """Preconditioned conjugate gradients (Hestenes-Stiefel), stop at ||b - A x|| <= tol ||b||.
+    A guess x0 is first scaled by alpha0 = (x0 . b) / (x0 . A x0), the factor that minimises the A-norm
+    error along x0 (so the scaled guess is never worse than zero in that norm).
     Returns (x, iterations, initial relative residual)."""
     x = np.zeros_like(b) if x0 is None else np.array(x0, dtype=np.float64)
+    if scale_guess and x0 is not None:
+        xax = x @ (A @ x)
+        x *= (x @ b) / xax if xax > 0.0 else 0.0
     r = b - A @ x
     bn = np.linalg.norm(b)
     if bn == 0.0:

@@ -38,6 +38,8 @@ EXPORTED = [
     "hplmm_get_sizes",
     "hplmm_get_maps", "hplmm_get_coarse_matrix", "hplmm_get_prolongation_column", "hplmm_get_profile",
     "hplmm_reset_profile", "hplmm_kernel_launches", "hplmm_get_costs", "hplmm_last_error", "hplmm_destroy",
+    "hplmm_ws_num_params", "hplmm_ws_set_params", "hplmm_ws_get_params", "hplmm_ws_collect", "hplmm_ws_clear",
+    "hplmm_ws_train", "hplmm_ws_loss_grad", "hplmm_get_basis_stats", "hplmm_ws_get_samples",
 ]
 PHASES = ["maps", "factor_grains", "factor_contacts", "basis_rhs", "basis_solve", "galerkin", "coarse_chol",
           "apply_coarse", "apply_contacts", "apply_grains", "spmv", "krylov", "apply_graph"]
@@ -48,7 +50,18 @@ class hplmm_options(ctypes.Structure):
                 ("n_st", ctypes.c_int), ("local_prec", ctypes.c_int), ("apply_prec", ctypes.c_int),
                 ("restart", ctypes.c_int), ("max_iters", ctypes.c_int), ("strict_two_grain", ctypes.c_int),
                 ("use_graph", ctypes.c_int), ("verbose", ctypes.c_int), ("profile", ctypes.c_int),
-                ("autotune", ctypes.c_int)]
+                ("autotune", ctypes.c_int), ("basis_solver", ctypes.c_int), ("basis_tol", ctypes.c_double),
+                ("basis_max_iters", ctypes.c_int), ("keep_basis_rhs", ctypes.c_int)]
+
+
+HPLMM_BASIS_DIRECT, HPLMM_BASIS_PCG, HPLMM_BASIS_PCG_WARM = 0, 1, 2
+BASIS = {"direct": HPLMM_BASIS_DIRECT, "pcg": HPLMM_BASIS_PCG, "pcg_warm": HPLMM_BASIS_PCG_WARM}
+
+
+class hplmm_basis_stats(ctypes.Structure):
+    _fields_ = [("columns", ctypes.c_longlong), ("iters_total", ctypes.c_longlong), ("iters_max", ctypes.c_longlong),
+                ("fallback_columns", ctypes.c_longlong), ("fallback_grains", ctypes.c_longlong),
+                ("init_rel_res_mean", ctypes.c_double), ("t_net_ms", ctypes.c_double), ("t_pcg_ms", ctypes.c_double)]
 
 
 class hplmm_bcs(ctypes.Structure):
@@ -109,6 +122,15 @@ def load_library():
         "hplmm_kernel_launches": (LL, []),
         "hplmm_get_costs": (I, [P, ctypes.POINTER(hplmm_costs)]),
         "hplmm_last_error": (ctypes.c_char_p, [P]),
+        "hplmm_ws_num_params": (LL, []),
+        "hplmm_ws_set_params": (I, [P, P, LL]),
+        "hplmm_ws_get_params": (I, [P, P, LL]),
+        "hplmm_ws_collect": (I, [P, ctypes.POINTER(LL)]),
+        "hplmm_ws_clear": (I, [P]),
+        "hplmm_ws_get_samples": (I, [P, LL, LL, P, P, P]),
+        "hplmm_ws_train": (I, [P, P, LL, I, D, P]),
+        "hplmm_ws_loss_grad": (I, [P, P, P, P, I, I, ctypes.POINTER(D), P]),
+        "hplmm_get_basis_stats": (I, [P, ctypes.POINTER(hplmm_basis_stats)]),
         "hplmm_destroy": (None, [P]),
     }
     for name, (res, args) in sig.items():
@@ -292,6 +314,65 @@ def hplmm_get_costs(ctx):
     return {n: getattr(c, n) for n, _ in hplmm_costs._fields_}
 
 
+def hplmm_ws_num_params():
+    return int(load_library().hplmm_ws_num_params())
+
+
+def hplmm_ws_set_params(ctx, params):
+    a = np.ascontiguousarray(params, dtype=np.float32)
+    _check(ctx, load_library().hplmm_ws_set_params(ctx, a.ctypes.data, a.size))
+
+
+def hplmm_ws_get_params(ctx):
+    a = np.empty(hplmm_ws_num_params(), dtype=np.float32)
+    _check(ctx, load_library().hplmm_ws_get_params(ctx, a.ctypes.data, a.size))
+    return a
+
+
+def hplmm_ws_collect(ctx):
+    n = ctypes.c_longlong(0)
+    _check(ctx, load_library().hplmm_ws_collect(ctx, ctypes.byref(n)))
+    return n.value
+
+
+def hplmm_ws_clear(ctx):
+    _check(ctx, load_library().hplmm_ws_clear(ctx))
+
+
+def hplmm_ws_get_samples(ctx, first, count, device="cuda"):
+    """(in [count][5][17^3], target [count][3][17^3], valid [count][3][17^3]) float32 tensors."""
+    import torch
+    D3 = 17 ** 3
+    x = torch.empty((count, 5, D3), dtype=torch.float32, device=device)
+    t = torch.empty((count, 3, D3), dtype=torch.float32, device=device)
+    v = torch.empty((count, 3, D3), dtype=torch.float32, device=device)
+    _check(ctx, load_library().hplmm_ws_get_samples(ctx, int(first), int(count), _ptr(x), _ptr(t), _ptr(v)))
+    return x, t, v
+
+
+def hplmm_ws_train(ctx, order, batch, lr):
+    o = np.ascontiguousarray(order, dtype=np.int32)
+    loss = np.zeros(max(1, o.size // batch), dtype=np.float64)
+    _check(ctx, load_library().hplmm_ws_train(ctx, o.ctypes.data, o.size, int(batch), float(lr), loss.ctypes.data))
+    return loss[:o.size // batch]
+
+
+def hplmm_ws_loss_grad(ctx, x, target, valid, D):
+    """x, target, valid: float32 CUDA tensors [n][5|3|3][D^3]; returns (loss, grad tensor)."""
+    import torch
+    grad = torch.empty(hplmm_ws_num_params(), dtype=torch.float32, device=x.device)
+    loss = ctypes.c_double(0.0)
+    _check(ctx, load_library().hplmm_ws_loss_grad(ctx, _ptr(x), _ptr(target), _ptr(valid), int(x.shape[0]), int(D),
+                                                  ctypes.byref(loss), _ptr(grad)))
+    return loss.value, grad
+
+
+def hplmm_get_basis_stats(ctx):
+    st = hplmm_basis_stats()
+    _check(ctx, load_library().hplmm_get_basis_stats(ctx, ctypes.byref(st)))
+    return {n: getattr(st, n) for n, _ in hplmm_basis_stats._fields_}
+
+
 def hplmm_last_error(ctx):
     return load_library().hplmm_last_error(ctx).decode()
 
@@ -307,7 +388,8 @@ class Solver:
 
     def __init__(self, n_mortar=4, beta=4.0, contact_halfwidth=2, n_st=1, local_prec="fp64", apply_prec="fp64",
                  restart=30, max_iters=300, strict_two_grain=False, use_graph=False, verbose=False, profile=False,
-                 autotune=False, stream=None):
+                 autotune=False, basis_solver="direct", basis_tol=1e-6, basis_max_iters=3000, keep_basis_rhs=False,
+                 stream=None):
         o = hplmm_default_options()
         o.n_mortar, o.beta, o.contact_halfwidth, o.n_st = n_mortar, beta, contact_halfwidth, n_st
         o.local_prec, o.apply_prec = PREC[local_prec], PREC[apply_prec]
@@ -315,6 +397,8 @@ class Solver:
         o.strict_two_grain, o.use_graph, o.verbose = int(strict_two_grain), int(use_graph), int(verbose)
         o.profile = int(profile)
         o.autotune = int(autotune)
+        o.basis_solver, o.basis_tol, o.basis_max_iters = BASIS[basis_solver], basis_tol, basis_max_iters
+        o.keep_basis_rhs = int(keep_basis_rhs)
         self.options = o
         self.ctx = hplmm_create(o, stream)
         self.n_dof = 0
@@ -387,6 +471,21 @@ class Solver:
 
     def costs(self):
         return hplmm_get_costs(self.ctx)
+
+    def basis_stats(self):
+        return hplmm_get_basis_stats(self.ctx)
+
+    def ws_set_params(self, params):
+        hplmm_ws_set_params(self.ctx, params)
+
+    def ws_get_params(self):
+        return hplmm_ws_get_params(self.ctx)
+
+    def ws_collect(self):
+        return hplmm_ws_collect(self.ctx)
+
+    def ws_train(self, order, batch, lr):
+        return hplmm_ws_train(self.ctx, order, batch, lr)
 
     def prolongation_column(self, col, out=None):
         import torch

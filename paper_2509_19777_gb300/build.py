@@ -16,7 +16,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "libhplmm.so")
 BUILD_DIR = os.path.join(HERE, "_build")
-SOURCES = ["prims.cu", "assemble.cu", "maps.cu", "local.cu", "coarse.cu", "apply.cu", "capi.cu", "static_spmv.cu"]
+SOURCES = ["prims.cu", "assemble.cu", "maps.cu", "local.cu", "coarse.cu", "apply.cu", "capi.cu", "static_spmv.cu",
+           "ws.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr"]
 

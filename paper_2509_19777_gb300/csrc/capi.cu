@@ -78,6 +78,12 @@ void validate_options(const hplmm_options &o) {
   HP_REQUIRE(o.max_iters >= 1, HPLMM_ERR_INVALID, "max_iters must be positive");
   HP_REQUIRE(o.use_graph == 0 || o.use_graph == 1, HPLMM_ERR_INVALID, "use_graph must be 0 or 1");
   HP_REQUIRE(o.autotune == 0 || o.autotune == 1, HPLMM_ERR_INVALID, "autotune must be 0 or 1");
+  HP_REQUIRE(o.basis_solver >= HPLMM_BASIS_DIRECT && o.basis_solver <= HPLMM_BASIS_PCG_WARM, HPLMM_ERR_INVALID,
+             "basis_solver must be HPLMM_BASIS_DIRECT, HPLMM_BASIS_PCG or HPLMM_BASIS_PCG_WARM");
+  HP_REQUIRE(o.basis_solver == HPLMM_BASIS_DIRECT || o.local_prec == HPLMM_FP32, HPLMM_ERR_INVALID,
+             "the iterative basis solves run in FP32: they need local_prec = FP32");
+  HP_REQUIRE(o.basis_tol > 0.0 && o.basis_tol < 1.0, HPLMM_ERR_INVALID, "basis_tol must lie in (0, 1)");
+  HP_REQUIRE(o.basis_max_iters >= 1, HPLMM_ERR_INVALID, "basis_max_iters must be positive");
 }
 
 void require_setup(hplmm_ctx *c) {
@@ -119,6 +125,10 @@ void hplmm_default_options(hplmm_options *o) {
   o->verbose = 0;
   o->profile = 0;
   o->autotune = 0;
+  o->basis_solver = HPLMM_BASIS_DIRECT;
+  o->basis_tol = 1e-6;
+  o->basis_max_iters = 3000;
+  o->keep_basis_rhs = 0;
 }
 
 hplmm_status hplmm_create(hplmm_ctx **ctx, const hplmm_options *opt, void *cuda_stream) {
@@ -388,6 +398,84 @@ hplmm_status hplmm_get_costs(hplmm_ctx *c, hplmm_costs *out) {
     for (int g = 0; g < c->grains.count; ++g)
       out->basis_solve_flops += 4.0 * c->grains.h_n[g] * c->grains.h_bw[g] * c->h_kg[g];
     out->panel_elems = c->h_panel_off.empty() ? 0 : c->h_panel_off.back();
+  });
+}
+
+long long hplmm_ws_num_params(void) { return hp::ws_num_params(); }
+
+hplmm_status hplmm_ws_set_params(hplmm_ctx *c, const float *params, long long n) {
+  return guarded(c, [&] {
+    HP_REQUIRE(params && n == hp::ws_num_params(), HPLMM_ERR_INVALID,
+               "ws_set_params: expected " + std::to_string(hp::ws_num_params()) + " parameters");
+    hp::ws_set_params(c, params);
+  });
+}
+
+hplmm_status hplmm_ws_get_params(hplmm_ctx *c, float *params, long long n) {
+  return guarded(c, [&] {
+    HP_REQUIRE(params && n == hp::ws_num_params(), HPLMM_ERR_INVALID,
+               "ws_get_params: expected " + std::to_string(hp::ws_num_params()) + " parameters");
+    hp::ws_get_params(c, params);
+  });
+}
+
+hplmm_status hplmm_ws_collect(hplmm_ctx *c, long long *n_total) {
+  return guarded(c, [&] {
+    long long n = hp::ws_collect(c);
+    if (n_total) *n_total = n;
+  });
+}
+
+hplmm_status hplmm_ws_clear(hplmm_ctx *c) {
+  return guarded(c, [&] {
+    c->ws.n_samples = 0;
+    c->ws.cap = 0;
+    c->ws.tin.release();
+    c->ws.ttgt.release();
+    c->ws.tvalid.release();
+  });
+}
+
+hplmm_status hplmm_ws_get_samples(hplmm_ctx *c, long long first, long long count, float *in, float *target,
+                                  float *valid) {
+  return guarded(c, [&] {
+    HP_REQUIRE(first >= 0 && count >= 0 && first + count <= c->ws.n_samples, HPLMM_ERR_INVALID,
+               "ws_get_samples: range outside the training set");
+    const long long D3 = 17LL * 17 * 17;
+    auto cp = [&](float *dst, const float *src, long long per) {
+      if (dst && count)
+        HP_CUDA(cudaMemcpyAsync(dst, src + first * per, sizeof(float) * count * per, cudaMemcpyDeviceToDevice,
+                                c->stream));
+    };
+    cp(in, c->ws.tin.p, 5 * D3);
+    cp(target, c->ws.ttgt.p, 3 * D3);
+    cp(valid, c->ws.tvalid.p, 3 * D3);
+    HP_CUDA(cudaStreamSynchronize(c->stream));
+  });
+}
+
+hplmm_status hplmm_ws_train(hplmm_ctx *c, const int32_t *order, long long n_order, int batch, double lr,
+                            double *loss) {
+  return guarded(c, [&] {
+    HP_REQUIRE(order && n_order >= 1 && lr > 0.0, HPLMM_ERR_INVALID, "ws_train: bad order or learning rate");
+    hp::ws_train(c, order, n_order, batch, lr, loss);
+  });
+}
+
+hplmm_status hplmm_ws_loss_grad(hplmm_ctx *c, const float *in, const float *target, const float *valid, int n,
+                                int D, double *loss, float *grad) {
+  return guarded(c, [&] {
+    HP_REQUIRE(in && target && valid && grad && loss, HPLMM_ERR_INVALID, "ws_loss_grad: null argument");
+    HP_REQUIRE(n >= 1 && n <= 256 && D >= 3 && D <= 17, HPLMM_ERR_INVALID, "ws_loss_grad: need 1 <= n <= 256, 3 <= D <= 17");
+    HP_REQUIRE(c->ws.has_params, HPLMM_ERR_STATE, "ws_loss_grad: set the network parameters first");
+    *loss = hp::ws_loss_grad(c, c->ws.theta.p, in, target, valid, n, D, grad);
+  });
+}
+
+hplmm_status hplmm_get_basis_stats(hplmm_ctx *c, hplmm_basis_stats *out) {
+  return guarded(c, [&] {
+    HP_REQUIRE(out, HPLMM_ERR_INVALID, "get_basis_stats: null output");
+    *out = c->bstats;
   });
 }
 

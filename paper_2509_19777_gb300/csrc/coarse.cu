@@ -659,11 +659,24 @@ void build_coarse(hplmm_ctx *c, const double *b_corr) {
                                             c->panel_off.p, b_corr, c->opt.strict_two_grain, c->X32.p);
   HP_CHECK_LAUNCH();
   }
-  // batched local solves (Eqs. col_pk, col_cg): X_g <- (A^g_g)^{-1} X_g
-  if (f64)
+  // batched local solves (Eqs. col_pk, col_cg): X_g <- (A^g_g)^{-1} X_g, exactly by the banded factors, or by
+  // block-Jacobi CG from a zero or a learned initial guess (FP32 locals only)
+  c->bstats = hplmm_basis_stats{};
+  if (f64) {
     solve_local_multi_f64(c, c->grains, c->X64.p, c->panel_off, c->kg, c->h_kg);
-  else
+    c->Xrhs.release();
+  } else if (c->opt.basis_solver == HPLMM_BASIS_DIRECT) {
+    if (c->opt.keep_basis_rhs) {
+      c->Xrhs.alloc(std::max<long long>(poff[G], 1));
+      HP_CUDA(cudaMemcpyAsync(c->Xrhs.p, c->X32.p, sizeof(float) * poff[G], cudaMemcpyDeviceToDevice, s));
+    } else {
+      c->Xrhs.release();
+    }
     solve_local_multi_f32(c, c->grains, c->X32.p, c->panel_off, c->kg, c->h_kg);
+  } else {
+    ProfScope ps_it(c, HPLMM_PH_BASIS_SOLVE);
+    ws_pcg_basis(c, c->opt.basis_solver == HPLMM_BASIS_PCG_WARM);
+  }
   if (!f64 && c->opt.apply_prec == HPLMM_BF16) {
     c->X16.alloc(std::max<long long>(poff[G], 1));
     to_bf16(c->X32.p, c->X16.p, poff[G], s);

@@ -240,6 +240,25 @@ struct hplmm_ctx {
 
   double t_ml = 0, t_mg = 0;
 
+  // ---- learned warm start and iterative basis solves (ws.cu)
+  hp::Buf<float> Xrhs;             // copy of the basis right-hand sides (iterative solves, sample collection)
+  hplmm_basis_stats bstats{};
+  struct WarmStart {
+    hp::Buf<float> theta, m, v, grad;       // parameters (FP32), Adam moments, gradient
+    hp::Buf<__nv_bfloat16> theta16;         // BF16 copy for inference
+    long long adam_step = 0;
+    bool has_params = false;
+    hp::Buf<float> tin, ttgt, tvalid;       // training set [S][5|3|3][17^3]
+    long long n_samples = 0, cap = 0;
+    hp::Buf<float> a1, a2, a3, q, g32a, g32b, gq, wflip, bx, bt, bv;  // training/inference scratch
+    hp::Buf<__nv_bfloat16> h1, h2;
+    hp::Buf<double> sums;
+    hp::Buf<int> sg, sa, vmin, vmax, nfree, iters, unconv, nb;
+    hp::Buf<float> scale, tscale, rel0, blk, dinv, pcg_work;
+    hp::Buf<long long> ell_off;
+    long long S = 0;                        // samples of the current set-up
+  } ws;
+
   // ---- phase profiling (options.profile)
   struct ProfRec {
     int ph;
@@ -298,6 +317,17 @@ void solve_local_multi_f64(hplmm_ctx *c, LocalSet &S, double *X, const Buf<long 
 void solve_local_multi_f32(hplmm_ctx *c, LocalSet &S, float *X, const Buf<long long> &x_off, const Buf<int> &x_ld,
                            const std::vector<int> &h_ld);
 void smoother_apply(hplmm_ctx *c, LocalSet &S, const double *r_pad, double *z_pad, bool atomic);
+void solve_local_multi_f32_subset(hplmm_ctx *c, LocalSet &S, float *X, const Buf<long long> &x_off,
+                                  const Buf<int> &x_ld, const std::vector<int> &h_ld, const std::vector<int> &grains);
+// ws.cu
+long long ws_num_params();
+void ws_set_params(hplmm_ctx *c, const float *theta_host);
+void ws_get_params(hplmm_ctx *c, float *theta_host);
+long long ws_collect(hplmm_ctx *c);
+void ws_train(hplmm_ctx *c, const int32_t *order, long long n_order, int batch, double lr, double *loss_out);
+double ws_loss_grad(hplmm_ctx *c, const float *theta, const float *x, const float *tgt, const float *valid, int B,
+                    int D, float *grad);
+void ws_pcg_basis(hplmm_ctx *c, bool warm);
 int num_sms();
 // coarse.cu
 void build_coarse(hplmm_ctx *c, const double *b_pad_for_corr);

@@ -1576,14 +1576,19 @@ void factor_local(hplmm_ctx *c, LocalSet &S, hplmm_prec prec) {
 
 template <typename T>
 static void solve_multi_t(hplmm_ctx *c, LocalSet &S, T *X, const Buf<long long> &x_off, const Buf<int> &x_ld,
-                          const std::vector<int> &h_ld) {
+                          const std::vector<int> &h_ld, const std::vector<int> *only = nullptr) {
   constexpr int NB = NBOf<T>::v;
   cudaStream_t s = c->stream;
   std::vector<int> items;
+  std::vector<char> pick;
+  if (only) {
+    pick.assign(S.count, 0);
+    for (int k : *only) pick[k] = 1;
+  }
   // largest problems first
   auto ord = S.order.download(s, S.count);
   for (int k : ord) {
-    if (S.h_n[k] == 0) continue;
+    if (S.h_n[k] == 0 || (only && !pick[k])) continue;
     for (int r0 = 0; r0 < h_ld[k]; r0 += 32) {
       items.push_back(k);
       items.push_back(r0);
@@ -1616,6 +1621,10 @@ static void solve_multi_t(hplmm_ctx *c, LocalSet &S, T *X, const Buf<long long> 
 void solve_local_multi_f64(hplmm_ctx *c, LocalSet &S, double *X, const Buf<long long> &x_off, const Buf<int> &x_ld,
                            const std::vector<int> &h_ld) {
   solve_multi_t<double>(c, S, X, x_off, x_ld, h_ld);
+}
+void solve_local_multi_f32_subset(hplmm_ctx *c, LocalSet &S, float *X, const Buf<long long> &x_off,
+                                  const Buf<int> &x_ld, const std::vector<int> &h_ld, const std::vector<int> &grains) {
+  solve_multi_t<float>(c, S, X, x_off, x_ld, h_ld, &grains);
 }
 void solve_local_multi_f32(hplmm_ctx *c, LocalSet &S, float *X, const Buf<long long> &x_off, const Buf<int> &x_ld,
                            const std::vector<int> &h_ld) {

@@ -1,0 +1,188 @@
+"""GPU: the learned warm start of the local basis solves and the batched
+block-Jacobi CG basis solver, through the C interface, against the FP64 CPU
+oracle (oracle/warmstart.py) and the exact local solves.
+
+Bars: the network's loss and parameter gradient match the oracle's FP64 ones
+to FP32 accumulation accuracy (relative 1e-4); the collected samples carry
+the oracle's grain fields and satisfy the oracle's grain equations to the
+FP32 local solve's accuracy; the CG basis reproduces the exact basis to its
+tolerance and leaves the FP64 FGMRES solution unchanged; training lowers the
+loss; and the trained network's warm start starts the CG basis solves of an
+unseen image from a smaller residual than the zero guess (iteration counts of
+both are reported).
+"""
+import numpy as np
+import pytest
+
+import synth
+from oracle import fem, precond, warmstart as ows
+from oracle.decomposition import cartesian_partition
+from tests._cases import gpu_solver, oracle_case, oracle_solution, rel
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+def _n(t):
+    return t.detach().cpu().numpy()
+
+
+def _cu(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def test_loss_and_gradient_match_oracle():
+    import paper_2509_19777_gb300 as hp
+    D, n = 5, 2
+    rng = np.random.default_rng(11)
+    x = rng.standard_normal((n, 5, D, D, D)).astype(np.float32)
+    t = rng.standard_normal((n, 3, D, D, D)).astype(np.float32)
+    valid = (rng.uniform(size=t.shape) < 0.7).astype(np.float32)
+    theta = ows.init_params(3)
+    theta[-3:] = [0.1, -0.2, 0.05]  # nonzero output biases
+    loss_ref, g_ref = ows.loss_and_grad(theta.astype(np.float64), x, t, valid)
+    s = hp.Solver()
+    s.ws_set_params(theta)
+    loss, g = hp.hplmm_ws_loss_grad(s.ctx, _cu(x), _cu(t), _cu(valid), D)
+    g = _n(g).astype(np.float64)
+    assert abs(loss - loss_ref) <= 1e-5 * abs(loss_ref)
+    # every layer's weights and biases, not just the largest block
+    pos = 0
+    for co, ci in ows.layer_shapes():
+        for m in (co * ci * 27, co):
+            blk, ref = g[pos:pos + m], g_ref[pos:pos + m]
+            assert np.linalg.norm(blk - ref) <= 1e-4 * np.linalg.norm(ref) + 1e-7, (co, ci, m)
+            pos += m
+    assert np.array_equal(s.ws_get_params(), theta)
+    s.close()
+
+
+def test_collected_samples_satisfy_the_oracle_equations():
+    import paper_2509_19777_gb300 as hp
+    name = "tiny10_n1"
+    p, opt, sysm, M = oracle_case(name)
+    s = gpu_solver(name, local_prec="fp32", apply_prec="fp32", keep_basis_rhs=True)
+    n = s.ws_collect()
+    assert n > 0
+    x, t, v = (_n(a).reshape(a.shape[0], a.shape[1], 17, 17, 17) for a in hp.hplmm_ws_get_samples(s.ctx, 0, n))
+    part = cartesian_partition(p.mask.shape, p.grains)
+    A = sysm.A.tocsr()
+    pats = {}
+    for g in range(M.dec.n_grains):
+        I = M.dec.grain_dofs[g]
+        o = ows.grain_box_origin(sysm, part, g)
+        if o is None or I.size == 0:
+            continue
+        fields, _ = ows.grain_fields(sysm, part, g, o)
+        pos = ows.dof_positions(sysm, I, o)
+        vm = np.zeros((3, 17, 17, 17), np.float32)
+        vm[pos] = 1.0
+        pats[g] = (vm, fields, I, pos, A[I][:, I])
+    seen = {g: 0 for g in pats}
+    for j in range(n):
+        match = [g for g, pt in pats.items() if np.array_equal(pt[0], v[j]) and np.array_equal(pt[1][0], x[j, 0])]
+        assert len(match) == 1, f"sample {j}: {len(match)} matching grains"
+        vm, fields, I, pos, Agg = pats[match[0]]
+        seen[match[0]] += 1
+        assert np.abs(x[j, 1] - fields[1]).max() <= 1e-6 * max(1.0, np.abs(fields[1]).max())
+        b = x[j, 2:][pos].astype(np.float64)
+        y = t[j][pos].astype(np.float64)
+        assert abs(np.sqrt(np.mean(b * b)) - 1.0) < 1e-5          # right-hand side scaled to unit RMS
+        assert abs(np.sqrt(np.mean(y * y)) - 1.0) < 1e-5          # solution scaled to unit RMS
+        Ay = Agg @ y                                               # A_gg (x / |x|) = (s / |x|) (b / s)
+        cfit = (Ay @ b) / (b @ b)
+        assert cfit > 0 and np.linalg.norm(Ay - cfit * b) <= 1e-3 * np.linalg.norm(Ay), j
+    # one sample per panel column of every grain: the columns of grain g are its coupled mortar columns
+    # and, when kept, its correction column
+    for g, cnt in seen.items():
+        k = sum(M.mortars.iface_col_offset[c + 1] - M.mortars.iface_col_offset[c] for c in M.dec.grain_ifaces[g])
+        k += int(g in M.coarse.correction_grain)
+        assert cnt == k, (g, cnt, k)
+    s.close()
+
+
+@pytest.mark.parametrize("name", ["tiny10_n1", "porous32_n4"])
+def test_pcg_basis_matches_exact_basis(name):
+    import paper_2509_19777_gb300 as hp
+    p, opt, sysm, M = oracle_case(name)
+    sd = gpu_solver(name, local_prec="fp32", apply_prec="fp32")
+    sp = gpu_solver(name, local_prec="fp32", apply_prec="fp32", basis_solver="pcg", basis_tol=1e-7)
+    st = sp.basis_stats()
+    assert st["columns"] > 0 and st["fallback_columns"] == 0 and st["iters_max"] > 0
+    assert abs(st["init_rel_res_mean"] - 1.0) < 1e-6  # zero guess
+    assert np.array_equal(sd.coarse_matrix().shape, sp.coarse_matrix().shape)
+    ncoarse = sd.sizes()["n_coarse"]
+    for col in sorted(set([0, ncoarse // 2, ncoarse - 1])):
+        assert rel(_n(sp.prolongation_column(col)), _n(sd.prolongation_column(col))) < 1e-3, col
+    x_ref, _ = oracle_solution(name)
+    x, rc, stt = sp.solve(tol=1e-8)
+    xn = _n(x)
+    assert rc == 0
+    assert np.linalg.norm(sysm.b - sysm.A @ xn) / np.linalg.norm(sysm.b) <= 1e-8
+    assert rel(xn, x_ref) < 1e-6
+    sd.close()
+    sp.close()
+
+
+def test_pcg_fallback_to_exact_solve():
+    # an iteration cap far too small: every column misses the tolerance and its grain is solved exactly
+    name = "tiny10_n1"
+    sd = gpu_solver(name, local_prec="fp32", apply_prec="fp32")
+    sp = gpu_solver(name, local_prec="fp32", apply_prec="fp32", basis_solver="pcg", basis_tol=1e-7,
+                    basis_max_iters=2)
+    st = sp.basis_stats()
+    assert st["fallback_columns"] > 0 and st["fallback_grains"] > 0
+    n = sd.sizes()["n_coarse"]
+    for col in range(0, n, max(1, n // 7)):
+        assert rel(_n(sp.prolongation_column(col)), _n(sd.prolongation_column(col))) < 1e-6, col
+    sd.close()
+    sp.close()
+
+
+def test_training_and_warm_start_gain():
+    # train on the exact bases of two porous32 images, then solve the bases of an unseen image by CG from
+    # the network's guess and from zero.  Asserted: training lowers the loss, the warm start starts from a
+    # smaller residual, and the solution (basis and FGMRES solution) is the same.  The CG iteration counts
+    # of both starts are reported, not asserted: at this training budget the guess removes part of the
+    # error but not enough of its smooth part to shorten block-Jacobi CG (see the printed line).
+    import paper_2509_19777_gb300 as hp
+    kw = dict(n_mortar=4, contact_halfwidth=2, local_prec="fp32", apply_prec="fp32")
+    trainer = hp.Solver(**kw, keep_basis_rhs=True)
+    for seed in (21, 22):
+        p = synth.make_workload("porous32", seed)
+        mask, E = hp.problem_to_device(p)
+        trainer.assemble(mask, E, p.nu, p.bcs)
+        trainer.setup(grains=p.grains)
+        n = trainer.ws_collect()
+    trainer.ws_set_params(ows.init_params(7))
+    rng = np.random.default_rng(8)
+    order = np.concatenate([rng.permutation(n) for _ in range(5)]).astype(np.int32)
+    loss = trainer.ws_train(order, 8, 1e-3)
+    assert np.all(np.isfinite(loss))
+    k = max(1, loss.size // 10)
+    print(f"training: {n} samples, {loss.size} Adam steps, loss {loss[:k].mean():.4f} -> {loss[-k:].mean():.4f}")
+    assert loss[-k:].mean() < 0.7 * loss[:k].mean(), (loss[:k].mean(), loss[-k:].mean())
+    theta = trainer.ws_get_params()
+    trainer.close()
+    p = synth.make_workload("porous32", 23)
+    stats = {}
+    sols = {}
+    for mode in ("pcg", "pcg_warm"):
+        s = hp.Solver(**kw, basis_solver=mode, basis_tol=1e-6)
+        if mode == "pcg_warm":
+            s.ws_set_params(theta)
+        mask, E = hp.problem_to_device(p)
+        s.assemble(mask, E, p.nu, p.bcs)
+        s.setup(grains=p.grains)
+        stats[mode] = s.basis_stats()
+        x, rc, st = s.solve(tol=1e-8)
+        assert rc == 0
+        sols[mode] = _n(x)
+        s.close()
+    cold, warm = stats["pcg"], stats["pcg_warm"]
+    print(f"CG basis solves on an unseen porous32 image: cold {cold['iters_total']} its "
+          f"(initial residual {cold['init_rel_res_mean']:.3f}), warm {warm['iters_total']} its "
+          f"(initial residual {warm['init_rel_res_mean']:.3f}), inference {warm['t_net_ms']:.1f} ms")
+    assert warm["init_rel_res_mean"] < cold["init_rel_res_mean"]
+    assert warm["fallback_columns"] == 0 and cold["fallback_columns"] == 0
+    assert rel(sols["pcg_warm"], sols["pcg"]) < 1e-6

@@ -46,6 +46,29 @@ def test_delta_kernel_shifts_the_input():
     assert np.array_equal(y, ref)
 
 
+def test_dilated_delta_kernel_shifts_by_the_dilation():
+    rng = np.random.default_rng(9)
+    x = rng.standard_normal((1, 1, 9, 9, 9))
+    W = np.zeros((1, 1, 3, 3, 3))
+    W[0, 0, 0, 2, 1] = 1.0  # offset (-d, +d, 0)
+    y = ws.conv3d(x, W, np.zeros(1), dil=4)
+    ref = np.zeros_like(x)
+    ref[0, 0, 4:, :5, :] = x[0, 0, :5, 4:, :]
+    assert np.array_equal(y, ref)
+
+
+def test_shift_beyond_the_grid_is_zero():
+    x = np.ones((1, 1, 5, 5, 5))
+    assert not ws._shift(x, 8, 0, 0).any() and not ws._shift(x, 0, -5, 0).any()
+    assert ws._shift(x, 4, 0, 0).sum() == 25
+
+
+def test_receptive_field_spans_the_grain():
+    # with dilations 1, 2, 4, 8 an output depends on inputs up to 15 nodes away along each axis, i.e. on
+    # every node of a 16-voxel grain but the opposite corner row
+    assert sum(ws.DILATIONS) == ws.GRID - 2
+
+
 def test_conv_is_linear_and_bias_is_constant():
     rng = np.random.default_rng(3)
     x1, x2 = rng.standard_normal((2, 1, 2, 4, 4, 4))
@@ -93,10 +116,14 @@ def test_sample_reproduces_the_basis_column():
     rng = np.random.default_rng(5)
     rhs = rng.standard_normal(I.size)
     x = spla.spsolve(A[I][:, I].tocsc(), rhs)
-    inp, tgt, valid, s = ws.make_sample(fields, ebar, pos, rhs, x)
+    inp, tgt, valid = ws.make_sample(fields, pos, rhs, x)
+    s = np.sqrt(np.mean(rhs * rhs))
     assert valid.sum() == I.size
     assert np.allclose(inp[2:][pos] * s, rhs, rtol=0, atol=1e-12)
-    assert np.allclose(ws.guess_from_prediction(tgt, ebar, s, pos), x, rtol=1e-12, atol=0)
+    assert np.allclose(ws.guess_from_prediction(tgt, pos) * np.sqrt(np.mean(x * x)), x, rtol=1e-12, atol=0)
+    # with the guess direction of the exact solution, the energy-optimal scaling reproduces the solution
+    xg, its, rel0 = ws.pcg(A[I][:, I], rhs, sp.identity(I.size), x0=ws.guess_from_prediction(tgt, pos), tol=1e-9)
+    assert its == 0 and rel0 < 1e-9
     assert inp[0].sum() == 16 * 16 * 16 / 8  # a solid 8^3 grain of cube16 (2x2x2 grains)
 
 
@@ -119,6 +146,12 @@ def test_pcg_matches_direct_solve_and_warm_start_helps():
     xw, its_w, rel0_w = ws.pcg(Agg, b, Dinv, x0=x0, tol=1e-10)
     assert rel0_w < rel0 and its_w < its
     assert np.linalg.norm(xw - x_ref) <= 1e-8 * np.linalg.norm(x_ref)
+    # the scaled guess is never worse than the zero guess in the A-norm, even for a poor guess
+    bad = rng.standard_normal(I.size)
+    xs = bad * ((bad @ b) / (bad @ (Agg @ bad)))
+    e0 = x_ref @ (Agg @ x_ref)
+    es = (xs - x_ref) @ (Agg @ (xs - x_ref))
+    assert es <= e0 * (1 + 1e-12)
     # the block-Jacobi operator is the inverse of the node-diagonal part
     Bd = Agg.toarray() * (node[:, None] == node[None, :])
     assert np.allclose(Dinv.toarray() @ Bd, np.eye(I.size), atol=1e-10)
