@@ -59,12 +59,15 @@ __global__ void __launch_bounds__(256) k_mdot(const double *V, long long ldv, in
   }
 }
 
+// out[j] = sum over blocks of partial[b][j]: one warp per j, lanes over the blocks, fixed reduction order
 __global__ void k_mdot_final(const double *partial, int nblocks, int nv, double *out) {
-  int j = threadIdx.x;
+  int j = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  int lane = threadIdx.x & 31;
   if (j >= nv) return;
   double s = 0.0;
-  for (int b = 0; b < nblocks; ++b) s += partial[(long long)b * MAXV + j];
-  out[j] = s;
+  for (int b = lane; b < nblocks; b += 32) s += partial[(long long)b * MAXV + j];
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+  if (lane == 0) out[j] = s;
 }
 
 // w -= sum_j V_j h[j]
@@ -95,7 +98,7 @@ void mdot(hplmm_ctx *c, const double *V, long long ldv, int nv, const double *w,
   ProfScope ps(c, HPLMM_PH_KRYLOV);
   k_mdot<<<MDOT_BLOCKS, 256, 0, c->stream>>>(V, ldv, nv, w, n, c->w_partial.p);
   HP_CHECK_LAUNCH();
-  k_mdot_final<<<1, MAXV, 0, c->stream>>>(c->w_partial.p, MDOT_BLOCKS, nv, out);
+  k_mdot_final<<<(nv + 7) / 8, 256, 0, c->stream>>>(c->w_partial.p, MDOT_BLOCKS, nv, out);
   HP_CHECK_LAUNCH();
 }
 

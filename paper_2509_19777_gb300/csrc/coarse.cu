@@ -460,7 +460,7 @@ __global__ void k_trmv_lower_t(const double *Y, long long N, const double *u, do
 // t[gcol] += sum over grain rows of X_g[row][a] r_loc[row]; CTA = (grain, chunk of RCHUNK rows):
 // the chunk's residual entries are gathered once into shared memory, then each thread owns columns and
 // reads the panel rows coalesced.
-constexpr int RCHUNK = 512;
+constexpr int RCHUNK = 128;
 
 template <typename T, typename A>
 __global__ void __launch_bounds__(256) k_restrict_grain(const long long *node_off, const int *nloc, const int *lnodes,
@@ -519,6 +519,8 @@ template <typename T, typename A>
 __global__ void k_prolong_grain(const long long *node_off, const int *nloc, const int *lnodes, const int *kg,
                                 const long long *panel_off, const T *X, const int *gcol_off, const int *gcol,
                                 const double *u, double *z) {
+  // z rows of grain g = X_g u_g: one warp per row pair (lanes over the k_g columns, coalesced), the two
+  // rows' loads issued together
   __shared__ A ul[512];
   int g = blockIdx.y;
   int k = kg[g];
@@ -529,14 +531,27 @@ __global__ void k_prolong_grain(const long long *node_off, const int *nloc, cons
   const T *Xg = X + panel_off[g];
   const int *ln = lnodes + node_off[g];
   int nw = blockDim.x >> 5;
-  for (int row = blockIdx.x * nw + wid; row < N; row += gridDim.x * nw) {
+  for (int row = 2 * (blockIdx.x * nw + wid); row < N; row += 2 * gridDim.x * nw) {
+    const bool two = row + 1 < N;
     const T *xr = Xg + (long long)row * k;
-    A s = 0;
-    for (int a = lane; a < k; a += 32) s += (A)xr[a] * ul[a];
-    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    const T *xs = two ? xr + k : xr;
+    A s = 0, s2 = 0;
+    for (int a = lane; a < k; a += 32) {
+      A ua = ul[a];
+      s += (A)xr[a] * ua;
+      s2 += (A)xs[a] * ua;
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      s += __shfl_down_sync(0xffffffffu, s, o);
+      s2 += __shfl_down_sync(0xffffffffu, s2, o);
+    }
     if (lane == 0) {
       int o = row / 3, d = row - 3 * o;
       z[3LL * ln[o] + d] = (double)s;
+      if (two) {
+        int o2 = (row + 1) / 3, d2 = row + 1 - 3 * o2;
+        z[3LL * ln[o2] + d2] = (double)s2;
+      }
     }
   }
 }
@@ -822,7 +837,7 @@ void coarse_apply(hplmm_ctx *c, const double *r_pad, double *z_pad) {
   dim3 gt(grid_for(std::min<long long>(No, 1024), 256), (unsigned)((No + 31) / 32));
   k_trmv_lower_t<<<gt, 256, 0, s>>>(c->Linv.p, No, u, t);
   HP_CHECK_LAUNCH();
-  dim3 gp(16, G);
+  dim3 gp(64, G);
   if (f64)
     k_prolong_grain<double, double><<<gp, 256, 0, s>>>(c->grains.node_off.p, c->grains.n.p, c->grains.lnodes.p,
                                                        c->kg.p, c->panel_off.p, c->X64.p, c->gcol_off.p, c->gcol.p, t,
@@ -854,7 +869,7 @@ void prolong_column(hplmm_ctx *c, long long col, double *out_pad) {
   HP_CUDA(cudaMemsetAsync(u, 0, sizeof(double) * No, s));
   double one = 1.0;
   HP_CUDA(cudaMemcpyAsync(u + col, &one, sizeof(double), cudaMemcpyHostToDevice, s));
-  dim3 gp(16, G);
+  dim3 gp(64, G);
   if (f64)
     k_prolong_grain<double, double><<<gp, 256, 0, s>>>(c->grains.node_off.p, c->grains.n.p, c->grains.lnodes.p,
                                                        c->kg.p, c->panel_off.p, c->X64.p, c->gcol_off.p, c->gcol.p, u,

@@ -131,6 +131,7 @@ struct LocalSet {
   Buf<int> order;     // problems sorted by decreasing factorisation cost
   int tuned_far_stages = 0;  // smoother solve pipeline depths picked by the tuner (0 = largest that fits)
   int tuned_c0_stages = 0;
+  int tuned_rpt = 0;         // far rows per bulk thread per copy chosen by the tuner (0 = default)
   hplmm_prec prec = HPLMM_FP64;
 };
 

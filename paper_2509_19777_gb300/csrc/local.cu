@@ -1076,7 +1076,7 @@ struct PanelGeo {
   __device__ int c0rows() const { return min(2 * NB, RP); }
 };
 
-template <typename S, int NB>
+template <typename S, int NB, int RPT>
 __global__ void __launch_bounds__(WS_THREADS) k_band_solve_ws(int count, const int *nloc, const int *bwv,
                                                               const long long *band_off, const long long *node_off,
                                                               const int *lnodes, const S *band, const double *r,
@@ -1088,7 +1088,6 @@ __global__ void __launch_bounds__(WS_THREADS) k_band_solve_ws(int count, const i
   constexpr int G = ROWB / 16;               // 16-byte groups per row
   constexpr int E = 16 / sizeof(S);          // elements per 16-byte group
   constexpr int NT_STEP = (1 + WS_BULK_WARPS) * 32;
-  constexpr int RPT = far_rpt<S>();
   constexpr int WS_FAR_ROWS = WS_BULK_WARPS * 32 * RPT;
   extern __shared__ __align__(128) unsigned char smdyn[];
   __shared__ __align__(8) uint64_t full_far[WS_MAX_FAR_STAGES], empty_far[WS_MAX_FAR_STAGES];
@@ -1637,12 +1636,20 @@ struct SolvePlan {
   size_t far_slot, c0_slot, vbytes;
 };
 
-static SolvePlan solve_plan(const LocalSet &S) {
+// far rows per bulk thread of the instantiated kernels: FP64 1; FP32 1 or 2; BF16 2 or 4
+static int default_rpt(const LocalSet &S) {
+  return S.prec == HPLMM_FP64 ? far_rpt<double>() : (S.apply_bf16 ? far_rpt<__nv_bfloat16>() : far_rpt<float>());
+}
+static std::vector<int> rpt_choices(const LocalSet &S) {
+  if (S.prec == HPLMM_FP64) return {1};
+  return S.apply_bf16 ? std::vector<int>{2, 4} : std::vector<int>{1, 2};
+}
+
+static SolvePlan solve_plan(const LocalSet &S, int rpt) {
   const bool f64 = S.prec == HPLMM_FP64;
   const int NBv = f64 ? 16 : 32;
   const size_t esz = f64 ? 8 : 4;  // local vector element
   const size_t rowb = S.apply_bf16 ? 64 : 128;
-  const int rpt = f64 ? far_rpt<double>() : (S.apply_bf16 ? far_rpt<__nv_bfloat16>() : far_rpt<float>());
   int vmax = 0;
   for (int k = 0; k < S.count; ++k)
     if (S.h_n[k] > 0) vmax = std::max(vmax, ((S.h_n[k] + NBv - 1) / NBv) * NBv + NBv);
@@ -1657,7 +1664,8 @@ void smoother_apply(hplmm_ctx *c, LocalSet &S, const double *r_pad, double *z_pa
   if (S.count == 0) return;
   ProfScope ps(c, (&S == &c->grains) ? HPLMM_PH_APPLY_GRAINS : HPLMM_PH_APPLY_CONTACTS);
   cudaStream_t s = c->stream;
-  const SolvePlan pl = solve_plan(S);
+  const int rpt = S.tuned_rpt > 0 ? S.tuned_rpt : default_rpt(S);
+  const SolvePlan pl = solve_plan(S, rpt);
   const size_t budget = 216 * 1024;
   HP_REQUIRE(pl.vbytes + 2 * pl.c0_slot + 2 * pl.far_slot <= budget, HPLMM_ERR_INVALID,
              "local problem too large for the smoother (" + std::to_string(pl.vbytes) + " bytes of local vector)");
@@ -1667,28 +1675,24 @@ void smoother_apply(hplmm_ctx *c, LocalSet &S, const double *r_pad, double *z_pa
   int fs = (int)std::min<size_t>(WS_MAX_FAR_STAGES, (budget - pl.vbytes - c0s * pl.c0_slot) / pl.far_slot);
   if (S.tuned_far_stages > 0) fs = std::min(fs, S.tuned_far_stages);
   const size_t smem = (size_t)fs * pl.far_slot + (size_t)c0s * pl.c0_slot + pl.vbytes;
-  if (S.prec == HPLMM_FP64) {
-    auto kern = k_band_solve_ws<double, 16>;
+  auto go = [&](auto kern, const auto *band) {
     HP_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    kern<<<S.count, WS_THREADS, smem, s>>>(S.count, S.n.p, S.bw.p, S.band_off.p, S.node_off.p, S.lnodes.p,
-                                           S.band64.p, r_pad, z_pad, atomic ? 1 : 0, fs, c0s, c->status.p);
-  } else if (S.apply_bf16) {
-    auto kern = k_band_solve_ws<__nv_bfloat16, 32>;
-    HP_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    kern<<<S.count, WS_THREADS, smem, s>>>(S.count, S.n.p, S.bw.p, S.band_off.p, S.node_off.p, S.lnodes.p,
-                                           S.band16.p, r_pad, z_pad, atomic ? 1 : 0, fs, c0s, c->status.p);
-  } else {
-    auto kern = k_band_solve_ws<float, 32>;
-    HP_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    kern<<<S.count, WS_THREADS, smem, s>>>(S.count, S.n.p, S.bw.p, S.band_off.p, S.node_off.p, S.lnodes.p,
-                                           S.band32.p, r_pad, z_pad, atomic ? 1 : 0, fs, c0s, c->status.p);
-  }
+    kern<<<S.count, WS_THREADS, smem, s>>>(S.count, S.n.p, S.bw.p, S.band_off.p, S.node_off.p, S.lnodes.p, band,
+                                           r_pad, z_pad, atomic ? 1 : 0, fs, c0s, c->status.p);
+  };
+  if (S.prec == HPLMM_FP64)
+    go(k_band_solve_ws<double, 16, 1>, S.band64.p);
+  else if (S.apply_bf16)
+    rpt == 2 ? go(k_band_solve_ws<__nv_bfloat16, 32, 2>, S.band16.p) : go(k_band_solve_ws<__nv_bfloat16, 32, 4>, S.band16.p);
+  else
+    rpt == 1 ? go(k_band_solve_ws<float, 32, 1>, S.band32.p) : go(k_band_solve_ws<float, 32, 2>, S.band32.p);
   HP_CHECK_LAUNCH();
 }
 
 // ---------------------------------------------------------------- tuner of the smoother solve pipeline
-// For each set of local problems, time the smoother solve under every pipeline depth that fits in shared
-// memory (far-row stages x diagonal-chunk stages) on the set's own factors, and keep the fastest.  Results
+// For each set of local problems, time the smoother solve under every plan that fits in shared memory (far
+// rows per bulk thread x far-row stages x diagonal-chunk stages) on the set's own factors, and keep the
+// fastest.  Results
 // are cached for the process, keyed by (count, largest local size, largest half bandwidth, precision), so a
 // repeated set-up of the same size pays nothing.
 namespace {
@@ -1699,11 +1703,14 @@ struct TuneKey {
   }
 };
 std::mutex g_tune_mu;
-std::map<TuneKey, std::pair<int, int>> g_tune_cache;
+struct TuneChoice {
+  int rpt, far_stages, c0_stages;
+};
+std::map<TuneKey, TuneChoice> g_tune_cache;
 }  // namespace
 
 static void tune_set(hplmm_ctx *c, LocalSet &S, bool atomic) {
-  S.tuned_far_stages = S.tuned_c0_stages = 0;
+  S.tuned_far_stages = S.tuned_c0_stages = S.tuned_rpt = 0;
   if (S.count == 0) return;
   TuneKey key{S.count, 0, 0, (int)S.prec + (S.apply_bf16 ? 8 : 0)};
   for (int k = 0; k < S.count; ++k) {
@@ -1714,13 +1721,13 @@ static void tune_set(hplmm_ctx *c, LocalSet &S, bool atomic) {
     std::lock_guard<std::mutex> lk(g_tune_mu);
     auto it = g_tune_cache.find(key);
     if (it != g_tune_cache.end()) {
-      S.tuned_far_stages = it->second.first;
-      S.tuned_c0_stages = it->second.second;
+      S.tuned_rpt = it->second.rpt;
+      S.tuned_far_stages = it->second.far_stages;
+      S.tuned_c0_stages = it->second.c0_stages;
       return;
     }
   }
-  const SolvePlan pl = solve_plan(S);
-  const size_t vbytes = pl.vbytes, far_slot = pl.far_slot, c0_slot = pl.c0_slot, budget = 216 * 1024;
+  const size_t budget = 216 * 1024;
   cudaStream_t s = c->stream;
   cudaEvent_t e0, e1;
   HP_CUDA(cudaEventCreate(&e0));
@@ -1728,10 +1735,14 @@ static void tune_set(hplmm_ctx *c, LocalSet &S, bool atomic) {
   const bool prof = c->opt.profile;
   c->opt.profile = 0;  // tuning launches are not part of any phase
   float best = 1e30f;
-  int bf = 0, bc = 0;
-  for (int c0d = 2; c0d <= 4; ++c0d)
+  int bf = 0, bc = 0, br = 0;
+  // candidates include small-footprint plans that let two CTAs share an SM (<= ~110 KiB each)
+  for (int rpt : rpt_choices(S))
+   for (int c0d = 2; c0d <= 4; ++c0d)
     for (int fd = 2; fd <= 8; ++fd) {
-      if (vbytes + c0d * c0_slot + fd * far_slot > budget) break;
+      const SolvePlan pl = solve_plan(S, rpt);
+      if (pl.vbytes + c0d * pl.c0_slot + fd * pl.far_slot > budget) break;
+      S.tuned_rpt = rpt;
       S.tuned_far_stages = fd;
       S.tuned_c0_stages = c0d;
       smoother_apply(c, S, c->b_pad.p, c->w_zz.p, atomic);  // warm-up
@@ -1745,24 +1756,28 @@ static void tune_set(hplmm_ctx *c, LocalSet &S, bool atomic) {
         best = ms;
         bf = fd;
         bc = c0d;
+        br = rpt;
       }
     }
   c->opt.profile = prof;
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
+  S.tuned_rpt = br;
   S.tuned_far_stages = bf;
   S.tuned_c0_stages = bc;
   if (c->opt.verbose)
-    fprintf(stderr, "[hplmm] tuner: %d problems (n<=%d, bw<=%d): far stages %d, diagonal stages %d, %.3f ms\n",
-            S.count, key.nmax, key.bwmax, bf, bc, best / 3);
+    fprintf(stderr,
+            "[hplmm] tuner: %d problems (n<=%d, bw<=%d): %d far rows per thread, far stages %d, diagonal stages %d, "
+            "%.3f ms\n",
+            S.count, key.nmax, key.bwmax, br, bf, bc, best / 3);
   std::lock_guard<std::mutex> lk(g_tune_mu);
-  g_tune_cache[key] = {bf, bc};
+  g_tune_cache[key] = {br, bf, bc};
 }
 
 void tune_local(hplmm_ctx *c) {
   if (!c->opt.autotune) {
-    c->grains.tuned_far_stages = c->grains.tuned_c0_stages = 0;
-    c->contacts.tuned_far_stages = c->contacts.tuned_c0_stages = 0;
+    c->grains.tuned_far_stages = c->grains.tuned_c0_stages = c->grains.tuned_rpt = 0;
+    c->contacts.tuned_far_stages = c->contacts.tuned_c0_stages = c->contacts.tuned_rpt = 0;
     return;
   }
   tune_set(c, c->contacts, true);
