@@ -215,8 +215,9 @@ hplmm_status hplmm_get_prolongation_column(hplmm_ctx *ctx, long long col, double
 /* Phases timed when options.profile = 1 (CUDA events around each phase's launches). */
 typedef enum {
   HPLMM_PH_MAPS = 0,          /* grain/interface maps and mortars (Sections 3.1-3.3) */
-  HPLMM_PH_FACTOR_GRAINS,     /* banded Cholesky of the grain blocks A^g_g */
-  HPLMM_PH_FACTOR_CONTACTS,   /* banded Cholesky of the contact-grid blocks */
+  HPLMM_PH_FACTOR_GRAINS,     /* banded Cholesky of the grain blocks A^g_g, together with the contact-grid
+                                 blocks factored concurrently on a second stream */
+  HPLMM_PH_FACTOR_CONTACTS,   /* (kept for compatibility: zero, the contact grids are timed above) */
   HPLMM_PH_BASIS_RHS,         /* right-hand sides of Eqs. col_pk and col_cg */
   HPLMM_PH_BASIS_SOLVE,       /* batched multi-RHS local solves building P */
   HPLMM_PH_GALERKIN,          /* A^o = P_hat^T A_hat P_hat */

@@ -197,8 +197,7 @@ hplmm_status hplmm_setup(hplmm_ctx *c, const int32_t *partition, int n_grains, i
     }
     double t1 = now_s();
     // smoother build (T_ML): exact local factorisations of grains and contact grids
-    hp::factor_local(c, c->grains, c->opt.local_prec);
-    hp::factor_local(c, c->contacts, c->opt.local_prec);
+    hp::factor_local_both(c, c->opt.local_prec);
     hp::check_status(c);
     double t2 = now_s();
     // coarse build (T_MG): basis solves, Galerkin product, coarse Cholesky
@@ -489,6 +488,9 @@ void hplmm_destroy(hplmm_ctx *c) {
   cudaStreamSynchronize(c->stream);
   if (c->apply_graph) cudaGraphExecDestroy(c->apply_graph);
   if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
+  if (c->aux_stream) cudaStreamDestroy(c->aux_stream);
+  if (c->ev_fork) cudaEventDestroy(c->ev_fork);
+  if (c->ev_join) cudaEventDestroy(c->ev_join);
   for (auto &r : c->prof_pending) {
     cudaEventDestroy(r.e0);
     cudaEventDestroy(r.e1);

@@ -129,6 +129,7 @@ struct LocalSet {
   Buf<__nv_bfloat16> band16;  // BF16 copy of the FP32 factors, used by the apply in the BF16 form
   bool apply_bf16 = false;
   Buf<int> order;     // problems sorted by decreasing factorisation cost
+  Buf<int> queue;     // work counter of the persistent factorisation
   int tuned_far_stages = 0;  // smoother solve pipeline depths picked by the tuner (0 = largest that fits)
   int tuned_c0_stages = 0;
   int tuned_rpt = 0;         // far rows per bulk thread per copy chosen by the tuner (0 = default)
@@ -235,6 +236,8 @@ struct hplmm_ctx {
   // graph of the apply (options.use_graph): captured on a private stream from fixed work vectors
   cudaGraphExec_t apply_graph = nullptr;
   cudaStream_t cap_stream = nullptr;
+  cudaStream_t aux_stream = nullptr;   // second stream of the concurrent local factorisations
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   bool capturing = false;
   long long graph_kernels = 0;     // kernels in the captured apply
   hp::Buf<double> w_gin, w_gout;
@@ -311,6 +314,7 @@ void compute_W(hplmm_ctx *c, int64_t *W);
 // local.cu
 void build_local_sets(hplmm_ctx *c);
 void factor_local(hplmm_ctx *c, LocalSet &S, hplmm_prec prec);
+void factor_local_both(hplmm_ctx *c, hplmm_prec prec);  // grains and contact grids concurrently
 // elementwise FP32 -> BF16 copy (round to nearest even)
 void to_bf16(const float *src, __nv_bfloat16 *dst, long long n, cudaStream_t s);
 void solve_local_multi_f64(hplmm_ctx *c, LocalSet &S, double *X, const Buf<long long> &x_off, const Buf<int> &x_ld,

@@ -1369,9 +1369,8 @@ int num_sms() {
 namespace {
 
 template <typename T>
-void layout_and_factor(hplmm_ctx *c, LocalSet &S, int where) {
+void layout_and_factor(hplmm_ctx *c, LocalSet &S, int where, cudaStream_t s, bool sync) {
   constexpr int NB = NBOf<T>::v;
-  cudaStream_t s = c->stream;
   int K = S.count;
   // band and inverse-block offsets for this precision
   std::vector<long long> boff(K + 1, 0);
@@ -1398,9 +1397,9 @@ void layout_and_factor(hplmm_ctx *c, LocalSet &S, int where) {
   k_local_extract<T><<<K, 128, 0, s>>>(S.box.p, S.node_off.p, S.n.p, S.bw.p, S.band_off.p, S.lmap.p, S.lnodes.p,
                                        c->node_ijk.p, c->row_ptr.p, c->col.p, c->val64.p, c->fixed.p, band, NB);
   HP_CHECK_LAUNCH();
-  Buf<int> queue;
-  queue.alloc(1);
-  queue.zero(s);
+  S.queue.alloc(1);
+  S.queue.zero(s);
+  int *queue = S.queue.p;
   int grid = std::min(K, 2 * num_sms());
   if constexpr (sizeof(T) == 4) {
     const size_t smem32 =
@@ -1408,16 +1407,16 @@ void layout_and_factor(hplmm_ctx *c, LocalSet &S, int where) {
     HP_REQUIRE(smem32 <= 216 * 1024, HPLMM_ERR_INVALID,
                "local problem half bandwidth " + std::to_string(bwmax) + " is too large; use smaller grain grids");
     HP_CUDA(cudaFuncSetAttribute(k_band_chol32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem32));
-    k_band_chol32<<<grid, CHOL32_THREADS, smem32, s>>>(S.order.p, K, queue.p, S.n.p, S.bw.p, S.band_off.p, band,
+    k_band_chol32<<<grid, CHOL32_THREADS, smem32, s>>>(S.order.p, K, queue, S.n.p, S.bw.p, S.band_off.p, band,
                                                        c->status.p, where, bwmax);
   } else {
     auto kern = k_band_chol<T, NB>;
     HP_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    kern<<<grid, FACT_THREADS, smem, s>>>(S.order.p, K, queue.p, S.n.p, S.bw.p, S.band_off.p, band, c->status.p,
+    kern<<<grid, FACT_THREADS, smem, s>>>(S.order.p, K, queue, S.n.p, S.bw.p, S.band_off.p, band, c->status.p,
                                           where);
   }
   HP_CHECK_LAUNCH();
-  HP_CUDA(cudaStreamSynchronize(s));
+  if (sync) HP_CUDA(cudaStreamSynchronize(s));
 }
 
 }  // namespace
@@ -1553,14 +1552,47 @@ void to_bf16(const float *src, __nv_bfloat16 *dst, long long n, cudaStream_t s) 
   HP_CHECK_LAUNCH();
 }
 
+static void bf16_copy(hplmm_ctx *c, LocalSet &S, hplmm_prec prec);
+
 void factor_local(hplmm_ctx *c, LocalSet &S, hplmm_prec prec) {
   if (S.count == 0) return;
   int where = (&S == &c->grains) ? 1 : 2;
   ProfScope ps(c, where == 1 ? HPLMM_PH_FACTOR_GRAINS : HPLMM_PH_FACTOR_CONTACTS);
   if (prec == HPLMM_FP64)
-    layout_and_factor<double>(c, S, where);
+    layout_and_factor<double>(c, S, where, c->stream, true);
   else
-    layout_and_factor<float>(c, S, where);
+    layout_and_factor<float>(c, S, where, c->stream, true);
+  bf16_copy(c, S, prec);
+}
+
+// Both sets at once: the grain factorisation (few large problems, one SM each) on the context's stream and
+// the contact grids' on a second stream, so the contact grids fill the SMs the grains leave idle.  The phase
+// timer HPLMM_PH_FACTOR_GRAINS covers both.
+void factor_local_both(hplmm_ctx *c, hplmm_prec prec) {
+  ProfScope ps(c, HPLMM_PH_FACTOR_GRAINS);
+  if (!c->aux_stream) HP_CUDA(cudaStreamCreateWithFlags(&c->aux_stream, cudaStreamNonBlocking));
+  if (!c->ev_fork) HP_CUDA(cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming));
+  if (!c->ev_join) HP_CUDA(cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming));
+  HP_CUDA(cudaEventRecord(c->ev_fork, c->stream));
+  HP_CUDA(cudaStreamWaitEvent(c->aux_stream, c->ev_fork, 0));
+  auto run = [&](LocalSet &S, int where, cudaStream_t st) {
+    if (S.count == 0) return;
+    if (prec == HPLMM_FP64)
+      layout_and_factor<double>(c, S, where, st, false);
+    else
+      layout_and_factor<float>(c, S, where, st, false);
+  };
+  run(c->grains, 1, c->stream);
+  run(c->contacts, 2, c->aux_stream);
+  HP_CUDA(cudaEventRecord(c->ev_join, c->aux_stream));
+  HP_CUDA(cudaStreamWaitEvent(c->stream, c->ev_join, 0));
+  HP_CUDA(cudaStreamSynchronize(c->stream));
+  bf16_copy(c, c->grains, prec);
+  bf16_copy(c, c->contacts, prec);
+}
+
+static void bf16_copy(hplmm_ctx *c, LocalSet &S, hplmm_prec prec) {
+  if (S.count == 0) return;
   S.prec = prec;
   // BF16 form: the apply streams a BF16 copy of the FP32 factors (FP32 arithmetic)
   S.apply_bf16 = prec == HPLMM_FP32 && c->opt.apply_prec == HPLMM_BF16;
@@ -1752,6 +1784,9 @@ static void tune_set(hplmm_ctx *c, LocalSet &S, bool atomic) {
       HP_CUDA(cudaEventSynchronize(e1));
       float ms = 0.f;
       HP_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+      if (c->opt.verbose)
+        fprintf(stderr, "[hplmm] tuner trial: %d problems, %d far rows per thread, far %d, diagonal %d: %.3f ms\n",
+                S.count, rpt, fd, c0d, ms / 3);
       if (ms < best) {
         best = ms;
         bf = fd;
