@@ -408,6 +408,24 @@ __global__ void __launch_bounds__(FACT_THREADS) k_band_chol(const int *order, in
   }
 }
 
+// TF32 tensor-core helpers: round to TF32 (the value keeps the FP32 format with 13 low mantissa bits cleared),
+// split x = hi + lo into two TF32 parts, and one m16n8k8 MMA with FP32 accumulation (d += a b)
+__device__ __forceinline__ uint32_t tf32_rna(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return r;
+}
+__device__ __forceinline__ void split_tf32(float x, uint32_t &hi, uint32_t &lo) {
+  hi = tf32_rna(x);
+  lo = tf32_rna(x - __uint_as_float(hi));
+}
+__device__ __forceinline__ void mma_tf32(float (&d)[4], const uint32_t (&a)[4], const uint32_t (&b)[2]) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, {%0,%1,%2,%3};"
+      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+}
+
 // FP32 banded Cholesky, one CTA per problem (persistent, problems taken from a cost-ordered queue).
 // Per panel of NB = 32 columns:
 //   1. the panel's rows [0, R) are loaded into shared memory (row stride 36 floats: rows start in
@@ -416,10 +434,9 @@ __global__ void __launch_bounds__(FACT_THREADS) k_band_chol(const int *order, in
 //      columns broadcast by shuffles) and forms inv(L_kk) column by column (lane j = column j);
 //   3. every thread turns its rows of the sub-diagonal block into L rows: L_r = A_r inv(L_kk)^T;
 //   4. the panel (inv(L_kk) in its first 32 rows, then the L rows) is written back;
-//   5. the trailing update A_ij -= L_i . L_j of the (R-32)^2 lower window is done in 32x32 warp tiles:
-//      lane = column j (its L row in 32 registers), 32 row accumulators, the A row operand broadcast by
-//      16-byte shared-memory loads, and the tile's old values loaded from the band before the arithmetic
-//      so that their latency is hidden behind the 1024 multiply-adds.
+//   5. the trailing update A_ij -= L_i . L_j of the (R-32)^2 lower window is done in 32x32 warp tiles on
+//      the tensor cores (split-TF32 MMAs, FP32 accuracy), the tile's old values fetched into the warp's
+//      staging area by cp.async before the arithmetic.
 constexpr int CHOL32_THREADS = 256;
 constexpr int CHOL32_LD = 36;
 
@@ -570,38 +587,59 @@ __global__ void __launch_bounds__(CHOL32_THREADS, 1) k_band_chol32(const int *or
           if ((piece >> 3) < rows_valid) cp_async16(cst + piece * 4, tile + piece * 4);
         }
         cp_async_commit();
-        const int jl = nb + tj * 32 + lane;  // this lane's window column (= row of P)
-        const bool jok = jl < R;
-        float pj[NB];
+        // A_ij -= sum_k L_ik L_jk on the tensor cores: m16n8k8 TF32 products with each operand split into a
+        // TF32 high part and a TF32 remainder (a b ~ a_lo b_hi + a_hi b_lo + a_hi b_hi), which keeps FP32
+        // accuracy; FP32 accumulation.  Warp tile 32x32 = 2 (rows) x 4 (columns) MMA tiles, K = 32 in 4 steps.
+        const int g8 = lane >> 2, tq = lane & 3;
+        const int rbase = nb + ti * 32, cbase = nb + tj * 32;
+        float acc[2][4][4];
 #pragma unroll
-        for (int g = 0; g < 8; ++g) {
-          float4 t4 = jok ? *reinterpret_cast<const float4 *>(P + jl * LD + 4 * g) : make_float4(0.f, 0.f, 0.f, 0.f);
-          pj[4 * g] = t4.x; pj[4 * g + 1] = t4.y; pj[4 * g + 2] = t4.z; pj[4 * g + 3] = t4.w;
-        }
-        float acc[32];
+        for (int mi = 0; mi < 2; ++mi)
 #pragma unroll
-        for (int q = 0; q < 32; ++q) {
-          const int il = min(nb + ti * 32 + q, R - 1);  // rows past the window read a valid row (discarded)
-          const float *ar = P + il * LD;
-          // four independent multiply-add chains (written as fmaf so that each product is one instruction)
-          float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
+          for (int ni = 0; ni < 4; ++ni)
 #pragma unroll
-          for (int g = 0; g < 8; ++g) {
-            float4 a4 = *reinterpret_cast<const float4 *>(ar + 4 * g);
-            s0 = fmaf(a4.x, pj[4 * g], s0);
-            s1 = fmaf(a4.y, pj[4 * g + 1], s1);
-            s2 = fmaf(a4.z, pj[4 * g + 2], s2);
-            s3 = fmaf(a4.w, pj[4 * g + 3], s3);
+            for (int e = 0; e < 4; ++e) acc[mi][ni][e] = 0.f;
+#pragma unroll
+        for (int k0 = 0; k0 < NB; k0 += 8) {
+          uint32_t ahi[2][4], alo[2][4];
+#pragma unroll
+          for (int mi = 0; mi < 2; ++mi) {
+            const int r0 = min(rbase + 16 * mi + g8, R - 1), r1 = min(rbase + 16 * mi + g8 + 8, R - 1);
+            split_tf32(P[r0 * LD + k0 + tq], ahi[mi][0], alo[mi][0]);
+            split_tf32(P[r1 * LD + k0 + tq], ahi[mi][1], alo[mi][1]);
+            split_tf32(P[r0 * LD + k0 + tq + 4], ahi[mi][2], alo[mi][2]);
+            split_tf32(P[r1 * LD + k0 + tq + 4], ahi[mi][3], alo[mi][3]);
           }
-          acc[q] = (s0 + s1) + (s2 + s3);
+#pragma unroll
+          for (int ni = 0; ni < 4; ++ni) {
+            const int n = cbase + 8 * ni + g8;
+            const bool nok = n < R;
+            uint32_t bhi[2], blo[2];
+            split_tf32(nok ? P[n * LD + k0 + tq] : 0.f, bhi[0], blo[0]);
+            split_tf32(nok ? P[n * LD + k0 + tq + 4] : 0.f, bhi[1], blo[1]);
+#pragma unroll
+            for (int mi = 0; mi < 2; ++mi) {
+              mma_tf32(acc[mi][ni], alo[mi], bhi);
+              mma_tf32(acc[mi][ni], ahi[mi], blo);
+              mma_tf32(acc[mi][ni], ahi[mi], bhi);
+            }
+          }
         }
         cp_async_wait_pending(0);
         __syncwarp();
+        // accumulator element (mi, ni, 2h + e) is row 16 mi + g8 + 8 h, column 8 ni + 2 tq + e of the tile
 #pragma unroll
-        for (int q = 0; q < 32; ++q) {
-          const int il = nb + ti * 32 + q;
-          if (q < rows_valid && jok && jl <= il) tile[q * NB + lane] = cst[q * 32 + lane] - acc[q];
-        }
+        for (int mi = 0; mi < 2; ++mi)
+#pragma unroll
+          for (int ni = 0; ni < 4; ++ni)
+#pragma unroll
+            for (int h = 0; h < 2; ++h)
+#pragma unroll
+              for (int e = 0; e < 2; ++e) {
+                const int q = 16 * mi + g8 + 8 * h, col = 8 * ni + 2 * tq + e;
+                const int il = rbase + q, jl = cbase + col;
+                if (q < rows_valid && jl < R && jl <= il) tile[q * NB + col] = cst[q * 32 + col] - acc[mi][ni][2 * h + e];
+              }
         __syncwarp();
       }
       __syncthreads();
