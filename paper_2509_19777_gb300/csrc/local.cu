@@ -437,7 +437,7 @@ __device__ __forceinline__ void mma_tf32(float (&d)[4], const uint32_t (&a)[4], 
 //   5. the trailing update A_ij -= L_i . L_j of the (R-32)^2 lower window is done in 32x32 warp tiles on
 //      the tensor cores (split-TF32 MMAs, FP32 accuracy), the tile's old values fetched into the warp's
 //      staging area by cp.async before the arithmetic.
-constexpr int CHOL32_THREADS = 256;
+constexpr int CHOL32_THREADS = 512;
 constexpr int CHOL32_LD = 36;
 
 __global__ void __launch_bounds__(CHOL32_THREADS, 1) k_band_chol32(const int *order, int count, int *queue,
