@@ -390,7 +390,7 @@ def main():
         print(json.dumps({"workload": args.workload, "form": args.form, "ms_per_step": statistics.mean(tt),
                           "iters": stt.iters,
                           "launches_per_step": launches / args.steps,
-                          "profiled_ms_per_step": statistics.mean(tq),
+                          "profiled_ms_per_step": statistics.mean(tq), "costs": costs,
                           "profile_ms_per_step": {k: v[0] / args.steps for k, v in prof.items()}}), flush=True)
         sq.close()
         return
