@@ -52,6 +52,8 @@ def parse():
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--no-plain", action="store_true", help="skip the plain FP64 comparison run")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--no-ws", action="store_true", help="skip the learned warm-start evaluation")
+    ap.add_argument("--no-forms", action="store_true", help="skip the BF16 form line")
     ap.add_argument("--quick", action="store_true",
                     help="profiling mode: time only the chosen form (no plain, e2e or CPU legs); prints a short line")
     ap.add_argument("--workload", default=WORKLOAD, help="synthetic workload for --quick runs (e.g. porous32)")
@@ -179,6 +181,63 @@ def run_form(hp, problem, form, steps, warmup, flush, stream, profile=False):
     costs = s.costs()
     sizes = s.sizes()
     return s, x, times, st, prof, costs, sizes, launches
+
+
+def warm_start_eval(hp, stream, seed=0):
+    """Learned warm start of the basis solves: train the network on the exact bases of two porous32 images
+    (seeded initial weights and minibatch order drawn here and passed to the library), then solve the bases
+    of an unseen porous32 image by block-Jacobi CG from the network's guess and from zero; report the CG
+    iterations, the starting residuals and the times, next to the exact banded solve of the chosen form."""
+    import numpy as np
+    import torch
+    import synth
+    from synth.netinit import init_params
+    kw = dict(METHOD, local_prec="fp32", apply_prec="fp32")
+    tr = hp.Solver(**kw, keep_basis_rhs=True, stream=stream)
+    n = 0
+    for s in (21, 22):
+        p = synth.make_workload("porous32", s)
+        mask, E = hp.problem_to_device(p)
+        tr.assemble(mask, E, p.nu, p.bcs)
+        tr.setup(grains=p.grains)
+        n = tr.ws_collect()
+    tr.ws_set_params(init_params(7 + seed))
+    rng = np.random.default_rng(8 + seed)
+    epochs = 6
+    order = np.concatenate([rng.permutation(n) for _ in range(epochs)]).astype(np.int32)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    loss = tr.ws_train(order, 8, 1e-3)
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t0
+    theta = tr.ws_get_params()
+    tr.close()
+    p = synth.make_workload("porous32", 23)
+    out = {"train": {"samples": int(n), "epochs": epochs, "steps": int(loss.size), "batch": 8, "lr": 1e-3,
+                     "loss_first_10pct": float(loss[:max(1, loss.size // 10)].mean()),
+                     "loss_last_10pct": float(loss[-max(1, loss.size // 10):].mean()), "seconds": t_train},
+           "eval_image": "porous32 seed 23 (unseen)", "basis_tol": 1e-6}
+    for mode in ("direct", "pcg", "pcg_warm"):
+        s = hp.Solver(**kw, basis_solver=mode, basis_tol=1e-6, profile=True, stream=stream)
+        if mode == "pcg_warm":
+            s.ws_set_params(theta)
+        mask, E = hp.problem_to_device(p)
+        s.assemble(mask, E, p.nu, p.bcs)
+        s.setup(grains=p.grains)
+        s.reset_profile()
+        s.setup(grains=p.grains)
+        x, rc, st = s.solve(tol=TOL)
+        bs = s.basis_stats()
+        prof = s.profile()
+        out[mode] = {"basis_ms": prof["basis_solve"][0], "cg_iters_total": bs["iters_total"],
+                     "cg_iters_max": bs["iters_max"], "init_rel_res_mean": bs["init_rel_res_mean"],
+                     "fallback_columns": bs["fallback_columns"], "net_ms": bs["t_net_ms"],
+                     "fgmres_iters": st.iters, "rel_res_true": st.rel_res_true}
+        s.close()
+    c, w = out["pcg"]["cg_iters_total"], out["pcg_warm"]["cg_iters_total"]
+    out["cg_iterations_saved"] = int(c - w)
+    out["cg_iterations_saved_frac"] = (c - w) / c if c else None
+    return out
 
 
 def run_e2e(hp, problem, form, steps, warmup, flush, stream):
@@ -460,6 +519,20 @@ def main():
         "gpu_launches_per_step": launches / max(1, args.steps),
         "clocks": clocks,
     }
+    if rank == 0 and not args.no_forms:
+        # the BF16 form (BF16 storage of the local factors, panels and A_hat in the apply) on the same image
+        sb, xb, tb, stb, _, _, _, _ = run_form(hp, problem, BF16, max(1, min(args.steps, 3)), max(1, args.warmup),
+                                               flush, stream)
+        line["forms"] = {"bf16": {"value": statistics.mean(tb) / 1e3, "iters": stb.iters,
+                                  "rel_res_true": stb.rel_res_true,
+                                  "rel_diff_vs_plain_fp64": (float(np.linalg.norm(xb.cpu().numpy() - xp_h) /
+                                                                   np.linalg.norm(xp_h)) if plain else None)}}
+        sb.close()
+    if rank == 0 and not args.no_ws:
+        try:
+            line["warm_start"] = warm_start_eval(hp, stream)
+        except Exception as e:  # reported, never required for the headline
+            line["warm_start"] = {"error": str(e)[-300:]}
     if rank == 0 and world == 1 and not args.no_cpu:
         try:
             sample = _oracle_subprocess(args.seed)

@@ -158,13 +158,9 @@ def adam_step(theta, grad, m, v, step, lr, b1=0.9, b2=0.999, eps=1e-8):
 
 
 def init_params(seed, channels=CHANNELS):
-    """He-uniform weights (bound sqrt(6 / fan_in)), zero biases; the library receives these as input."""
-    rng = np.random.default_rng(seed)
-    layers = []
-    for co, ci in layer_shapes(channels):
-        bound = np.sqrt(6.0 / (ci * 27))
-        layers.append((rng.uniform(-bound, bound, size=(co, ci, 3, 3, 3)), np.zeros(co)))
-    return pack(layers).astype(np.float32)
+    """Seeded initial parameters: the shared input generator synth.netinit (the library receives them)."""
+    from synth.netinit import init_params as draw
+    return draw(seed, channels)
 
 
 # ------------------------------------------------------------------ samples of one grain
