@@ -130,9 +130,12 @@ struct LocalSet {
   bool apply_bf16 = false;
   Buf<int> order;     // problems sorted by decreasing factorisation cost
   Buf<int> queue;     // work counter of the persistent factorisation
-  int tuned_far_stages = 0;  // smoother solve pipeline depths picked by the tuner (0 = largest that fits)
+  Buf<int> gidx;      // global vector index of every local DOF (vec_off based)
+  Buf<double> yscr;   // smoother scratch: forward-sweep result per local DOF (vec_off based; FP32 sets use
+                      // it as a float array)
+  int tuned_chunk_rows = 0;  // smoother solve plan picked by the tuner (0 = default): far chunk rows,
+  int tuned_ring_rows = 0;   // far ring rows (0 = largest that fits) and diagonal-chunk stages
   int tuned_c0_stages = 0;
-  int tuned_rpt = 0;         // far rows per bulk thread per copy chosen by the tuner (0 = default)
   hplmm_prec prec = HPLMM_FP64;
 };
 

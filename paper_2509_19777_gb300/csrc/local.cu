@@ -223,6 +223,19 @@ __global__ void k_local_bw(const int *box, const long long *node_off, const int 
 }
 
 // scatter the lower band of the principal submatrix into panel-blocked storage
+// global vector index of every local DOF: 3 * (global node of ordinal l / 3) + l mod 3
+__global__ void k_local_gidx(const int *nloc, const long long *node_off, const long long *vec_off, const int *lnodes,
+                             int *gidx) {
+  const int k = blockIdx.x;
+  const int n = nloc[k];
+  const int *ln = lnodes + node_off[k];
+  int *gk = gidx + vec_off[k];
+  for (int l = threadIdx.x; l < n; l += blockDim.x) {
+    const int o = l / 3;
+    gk[l] = 3 * ln[o] + (l - 3 * o);
+  }
+}
+
 template <typename T>
 __global__ void k_local_extract(const int *box, const long long *node_off, const int *nloc, const int *bwv,
                                 const long long *band_off, const int *lmap, const int *lnodes, const int *node_ijk,
@@ -978,43 +991,57 @@ __global__ void __launch_bounds__(SM32_THREADS, 1) k_band_solve_multi32(const in
 }
 
 // ---------------------------------------------------------------- single-RHS smoother solves
-// One CTA per problem solves L L^T x = r for the gathered local right-hand side (kept in shared memory as
-// the vector v) and adds (contact grids, which overlap) or stores (grain grids) x into z.
+// One CTA per problem solves L L^T x = r for the gathered local right-hand side and adds (contact grids,
+// which overlap) or stores (grain grids) x into z.
 //
 // Both sweeps run in steps, one per panel (forward: p = 0 .. np-1, backward: p = np-1 .. 0).  The work of a
 // step is split between warps so that the short sequential chain of the triangular solve overlaps the
 // bandwidth-heavy part:
 //   - the leader warp handles the diagonal block of panel p and its "near" block (the next NB rows):
 //       forward  y_p = inv(L_pp) (v_p - L_{p,p-1} y_{p-1}),   near product L_{p+1,p} y_p kept in registers;
-//       backward x_p = inv(L_pp)^T (v_p - L_{p+1,p}^T x_{p+1} - far_p);
+//       backward x_p = inv(L_pp)^T (y_p - L_{p+1,p}^T x_{p+1} - far_p);
 //   - the bulk warps handle the "far" rows (beyond the near block) of panel p-1, one row per thread:
 //       forward  v[rows] -= L_far(p-1) y_{p-1};
-//       backward far_{p-1} = L_far(p-1)^T v[rows] (column sums reduced per warp);
-//   - a producer warp streams the far rows with bulk asynchronous copies (cp.async.bulk) into a ring of
-//     shared-memory stages guarded by full/empty mbarriers, running ahead of the consumers.  On this GPU a
-//     bulk copy costs about half a microsecond of serialised copy-engine time per SM almost regardless of
-//     its size up to 64 KiB, so the chunks are large (FAR_ROWS_PER_THREAD rows per bulk thread, 64 KiB);
-//   - the leader warp fetches its own small diagonal+near chunks with coalesced 16-byte cp.async copies a
-//     few steps ahead (a bulk copy of 8 KiB would cost as much engine time as one of 64 KiB).
-// The leader and bulk warps meet once per step on a named barrier that also ORs their error flags.  Every
-// wait is bounded; on expiry the kernel records HPLMM_ERR_TIMEOUT, lets every copy in flight land and
-// returns without writing z.
+//       backward far_{p-1} = L_far(p-1)^T x[rows] (column sums reduced per warp);
+//   - a producer warp streams the far rows of successive panels with bulk asynchronous copies
+//     (cp.async.bulk) into a ring of shared-memory rows.  Chunks of up to `chunk_rows` rows are packed back
+//     to back (a chunk that reaches the end of the ring is split into two copies), each guarded by a
+//     full/empty mbarrier pair; a chunk is issued as soon as the rows it lands on have been released, so
+//     the copies of the next one or two panels are in flight while a panel is consumed.  The step time is
+//     otherwise bounded by the latency of a copy issued one panel ahead.
+//   - the producer also copies the leader's diagonal+near chunk of each step (2 NB rows) into a small ring
+//     of its own, ahead of the far rows of the same step; the leader never issues or waits on a load on its
+//     chain: right-hand-side values, scratch values and output indices are fetched one or two steps ahead.
+// There is no per-step barrier: each role waits only for what it reads, through mbarriers.  Bulk step s
+// needs leader step s-1 (y_{p-1}, or the x values above panel p-1).  In the forward sweep the rows of panel
+// p are final once the first NB far rows of bulk step s-1 (warp 0 signals them as soon as its part of the
+// first chunk is done) and all of bulk step s-2 are done, so the leader runs up to one step ahead of the
+// bulk warps, and consecutive bulk steps may overlap (their updates of v are shared-memory atomics).  In
+// the backward sweep the far sums of panel p come from bulk step s-1.  Every wait is bounded; on expiry
+// the kernel records HPLMM_ERR_TIMEOUT, lets every copy in flight land and returns (z is then incomplete;
+// the status tells the caller).
 //
-// Shared-memory bank conflicts: a factor row is 128 bytes (8 groups of 16 bytes).  A bulk thread always
-// works on rows with the same index modulo 8 (rows of a chunk start at a multiple of 8 and the bulk thread
-// count is a multiple of 8), and visits the row's 16-byte groups starting at that offset, with its copy of
-// y (or its column accumulators) kept in the same rotated order in registers.  The 8 threads of one
-// shared-memory phase therefore touch 8 different bank groups.
+// Local vector window: only rows [p NB - 2 NB, p NB + RP + NB) of the local vector are live at step p, so
+// shared memory holds a window of W >= RP + 3 NB rows (a power of two; row l lives in slot l mod W).  In the
+// forward sweep the leader refills the slots of panel p-3 (last read by bulk step p-2) with the
+// right-hand-side rows W further on (index and value fetched two and one steps ahead) and saves y_p to a
+// global scratch
+// vector; the backward sweep reads y_p back from there, keeps x in the window for the far products, and
+// writes each x_p to z as soon as it is known.
+//
+// Shared-memory bank conflicts: a factor row is 128 bytes (8 groups of 16 bytes).  A bulk thread visits its
+// row's 16-byte groups starting at (thread mod 8), with its copy of y (or its column accumulators) kept in
+// the same rotated order in registers; the 8 threads of one shared-memory phase therefore touch 8 different
+// bank groups wherever the rows sit in the ring.
 constexpr int WS_BULK_WARPS = 8;
-constexpr int WS_THREADS = (2 + WS_BULK_WARPS) * 32;
+constexpr int WS_THREADS = (3 + WS_BULK_WARPS) * 32;  // leader, far producer, diagonal-chunk producer, bulk
+constexpr int WS_BULK_THREADS = WS_BULK_WARPS * 32;
 // Factors are stored in S (float, double or bf16) and the arithmetic runs in T (double for FP64 factors,
 // float otherwise); a stored row is NB elements of S, 128 bytes (FP32, FP64) or 64 bytes (BF16).
 template <typename S> struct ComputeOf { using type = float; };
 template <> struct ComputeOf<double> { using type = double; };
-// far rows per bulk thread per chunk: 64 KiB chunks for FP32 and BF16 factors, 32 KiB for FP64 (the FP64
-// local vector already takes half of the shared memory)
-template <typename S> constexpr int far_rpt() { return sizeof(S) == 8 ? 1 : (sizeof(S) == 4 ? 2 : 4); }
-constexpr int WS_MAX_FAR_STAGES = 8;
+constexpr int WS_NSTG = 16;  // full/empty barrier pairs: far chunks in flight or buffered at once
+constexpr int WS_MAX_C0 = 4;  // diagonal+near chunk stages (2 .. 4)
 constexpr long long WAIT_CYCLES = 4000000000LL;  // about two seconds of SM clock
 
 
@@ -1062,17 +1089,6 @@ __device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t by
       : "memory");
 }
 
-// named barrier 1 over the leader and bulk warps; returns the OR of `flag` over its threads
-__device__ __forceinline__ int step_barrier_or(int flag, int nthreads) {
-  int res;
-  asm volatile(
-      "{\n .reg .pred p, q;\n setp.ne.s32 p, %1, 0;\n bar.red.or.pred q, 1, %2, p;\n selp.s32 %0, 1, 0, q;\n}\n"
-      : "=r"(res)
-      : "r"(flag), "r"(nthreads)
-      : "memory");
-  return res;
-}
-
 // 16-byte group loads of a stored factor row, converted to the compute type
 template <typename S> struct Vec16;
 template <> struct Vec16<float> {
@@ -1107,30 +1123,48 @@ template <> __device__ __forceinline__ float ld_elem<__nv_bfloat16>(const __nv_b
 
 // geometry of panel p: rows of the panel inside the matrix, and its far rows [2 NB, rend)
 struct PanelGeo {
-  int N, NB, RP, FR;  // FR = rows per far chunk
+  int N, NB, RP;
   __device__ int rend(int p) const { return min(N - p * NB, RP); }
   __device__ int nfar(int p) const { return max(0, rend(p) - 2 * NB); }
-  __device__ int nchunks(int p) const { return (nfar(p) + FR - 1) / FR; }
   __device__ int c0rows() const { return min(2 * NB, RP); }
 };
 
-template <typename S, int NB, int RPT>
-__global__ void __launch_bounds__(WS_THREADS) k_band_solve_ws(int count, const int *nloc, const int *bwv,
-                                                              const long long *band_off, const long long *node_off,
-                                                              const int *lnodes, const S *band, const double *r,
-                                                              double *z, int atomic, int far_stages, int c0_stages,
-                                                              int *status) {
+// n consecutive compute-type values from shared memory with 16-byte loads (p 16-byte aligned)
+template <typename T, int n> __device__ __forceinline__ void ld_vec(const T *p, T *o) {
+  static_assert((n * sizeof(T)) % 16 == 0, "whole 16-byte groups");
+  if constexpr (sizeof(T) == 4) {
+#pragma unroll
+    for (int u = 0; u < n / 4; ++u) {
+      const float4 w = reinterpret_cast<const float4 *>(p)[u];
+      o[4 * u] = w.x; o[4 * u + 1] = w.y; o[4 * u + 2] = w.z; o[4 * u + 3] = w.w;
+    }
+  } else {
+#pragma unroll
+    for (int u = 0; u < n / 2; ++u) {
+      const double2 w = reinterpret_cast<const double2 *>(p)[u];
+      o[2 * u] = w.x; o[2 * u + 1] = w.y;
+    }
+  }
+}
+
+template <typename S, int NB>
+__global__ void __launch_bounds__(WS_THREADS) k_band_solve_ws(
+    int count, const int *nloc, const int *bwv, const long long *band_off, const long long *vec_off,
+    const int *gidx, const S *band, const double *r, double *z, typename ComputeOf<S>::type *yscr, int atomic,
+    int ring_rows, int chunk_rows, int c0_stages, int wmask, int *status) {
   using T = typename ComputeOf<S>::type;
   constexpr int ROWB = NB * (int)sizeof(S);  // bytes per stored row
   static_assert(ROWB == 128 || ROWB == 64, "factor rows are 128 or 64 bytes");
-  constexpr int G = ROWB / 16;               // 16-byte groups per row
+  constexpr int G = ROWB / 16;               // 16-byte groups per stored row
   constexpr int E = 16 / sizeof(S);          // elements per 16-byte group
-  constexpr int NT_STEP = (1 + WS_BULK_WARPS) * 32;
-  constexpr int WS_FAR_ROWS = WS_BULK_WARPS * 32 * RPT;
   extern __shared__ __align__(128) unsigned char smdyn[];
-  __shared__ __align__(8) uint64_t full_far[WS_MAX_FAR_STAGES], empty_far[WS_MAX_FAR_STAGES];
+  __shared__ __align__(8) uint64_t full_far[WS_NSTG], empty_far[WS_NSTG];
+  __shared__ __align__(8) uint64_t full_c0[WS_MAX_C0], empty_c0[WS_MAX_C0];
+  // step dependencies (rings of 4, event j on barrier j & 3): leader step done, first NB far rows of a bulk
+  // step done (warp 0), bulk step done (every bulk warp)
+  __shared__ __align__(8) uint64_t ydone[4], urg[4], bdone[4];
   __shared__ T red[2][WS_BULK_WARPS][NB];
-  __shared__ T stage[WS_BULK_WARPS][8][NB];
+  __shared__ __align__(16) T lbuf[NB];  // leader: the panel's right-hand side, broadcast to its lanes
   __shared__ volatile int s_abort;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const int k = blockIdx.x;
@@ -1140,248 +1174,413 @@ __global__ void __launch_bounds__(WS_THREADS) k_band_solve_ws(int count, const i
   const int bw = bwv[k];
   const int RP = NB + bw;
   const int np = (N + NB - 1) / NB;
-  const int VN = np * NB + NB;  // padded local vector
-  const PanelGeo geo{N, NB, RP, WS_FAR_ROWS};
+  const int W = wmask + 1;
+  const PanelGeo geo{N, NB, RP};
   const S *B = band + band_off[k];
-  const int *ln = lnodes + node_off[k];
-  S *far_ring = reinterpret_cast<S *>(smdyn);
-  S *c0_ring = far_ring + (size_t)far_stages * WS_FAR_ROWS * NB;
+  // far chunks: when a whole step's far rows (at most nf_int) fit twice in the ring, every step is one copy
+  // into a slot of nf_int rows (ring_eff a multiple of nf_int: no copy is split); otherwise chunks of
+  // chunk_rows rows packed back to back, a chunk that reaches the end of the ring split into two copies
+  const int nf_int = max(0, RP - 2 * NB);
+  const bool whole = chunk_rows >= nf_int && nf_int > 0 && ring_rows >= 2 * nf_int;
+  const int ring_eff = whole ? (ring_rows / nf_int) * nf_int : ring_rows;
+  const int cr = whole ? nf_int : chunk_rows;
+  const int *gi = gidx + vec_off[k];
+  T *ys = yscr + vec_off[k];
+  S *ring = reinterpret_cast<S *>(smdyn);
+  S *c0_ring = ring + (size_t)ring_rows * NB;
   T *v = reinterpret_cast<T *>(c0_ring + (size_t)c0_stages * 2 * NB * NB);
   const int c0rows = geo.c0rows();
 
   if (threadIdx.x == 0) {
-    for (int i = 0; i < far_stages; ++i) {
+    for (int i = 0; i < WS_NSTG; ++i) {
       mbar_init(&full_far[i], 1);
       mbar_init(&empty_far[i], WS_BULK_WARPS);
+    }
+    for (int i = 0; i < c0_stages; ++i) {
+      mbar_init(&full_c0[i], 32);
+      mbar_init(&empty_c0[i], 1);
+    }
+    for (int i = 0; i < 4; ++i) {
+      mbar_init(&ydone[i], 1);
+      mbar_init(&urg[i], 1);
+      mbar_init(&bdone[i], WS_BULK_WARPS);
     }
     s_abort = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
-  for (int l = threadIdx.x; l < VN; l += WS_THREADS) {
-    T val = 0;
-    if (l < N) {
-      int o = l / 3, d = l - 3 * o;
-      val = (T)r[3LL * ln[o] + d];
-    }
-    v[l] = val;
-  }
+  // initial window: rows 0 .. min(W, N) - 1 of the right-hand side (slots of rows >= N are never read)
+  for (int l = threadIdx.x; l < min(W, N); l += WS_THREADS) v[l] = (T)r[gi[l]];
   __syncthreads();
 
   const int nsteps = 2 * np;
   if (wid == 1) {
     // ------------------------------------------------------------ producer
+    // per step: the far rows of the bulk warps' panel
     if (lane == 0) {
-      int far_n = 0;
+      int start_tab[WS_NSTG];  // absolute ring row of each far chunk not yet known to be released
+      int n = 0, rel = 0, abs_pos = 0;
       bool ok = true;
       for (int s = 0; s < nsteps && ok; ++s) {
         const int p = (s < np) ? s : (2 * np - 1 - s);
         const int q = p - 1;
-        if (q >= 0) {
-          const int nf = geo.nfar(q), nc = geo.nchunks(q);
-          for (int cix = 0; cix < nc; ++cix) {
-            const int slot = far_n % far_stages, use = far_n / far_stages;
-            if (use > 0 && !mbar_wait_bounded(&empty_far[slot], (uint32_t)((use - 1) & 1), &s_abort)) {
+        if (q < 0) continue;
+        const int nf = geo.nfar(q);
+        for (int r0 = 0; r0 < nf; r0 += cr) {
+          const int rows = min(cr, nf - r0);
+          const int alloc = whole ? nf_int : rows;
+          // release (in order) every chunk whose barrier pair or ring rows this chunk reuses
+          while (rel < n && (rel <= n - WS_NSTG || start_tab[rel % WS_NSTG] < abs_pos + alloc - ring_eff)) {
+            if (!mbar_wait_bounded(&empty_far[rel % WS_NSTG], (uint32_t)((rel / WS_NSTG) & 1), &s_abort)) {
               ok = false;
               break;
             }
-            const int rows = min(WS_FAR_ROWS, nf - cix * WS_FAR_ROWS);
-            const uint32_t bytes = (uint32_t)rows * (uint32_t)ROWB;
-            mbar_expect_tx(&full_far[slot], bytes);
-            bulk_g2s(far_ring + (size_t)slot * WS_FAR_ROWS * NB,
-                     B + ((long long)q * RP + 2 * NB + (long long)cix * WS_FAR_ROWS) * NB, bytes, &full_far[slot]);
-            ++far_n;
+            ++rel;
           }
+          if (!ok) break;
+          const int slot = n % WS_NSTG;
+          start_tab[slot] = abs_pos;
+          const int pos = abs_pos % ring_eff;
+          const S *src = B + ((long long)q * RP + 2 * NB + r0) * NB;
+          const int first = min(rows, ring_eff - pos);
+          mbar_expect_tx(&full_far[slot], (uint32_t)rows * (uint32_t)ROWB);
+          bulk_g2s(ring + (size_t)pos * NB, src, (uint32_t)first * ROWB, &full_far[slot]);
+          if (first < rows) bulk_g2s(ring, src + (size_t)first * NB, (uint32_t)(rows - first) * ROWB, &full_far[slot]);
+          abs_pos += alloc;
+          ++n;
         }
       }
       if (!ok) {
         s_abort = 1;
         atomicCAS(status, 0, (int)HPLMM_ERR_TIMEOUT);
       }
-      // let every copy issued into a stage land before shared memory is released (no-op when all were consumed)
-      for (int i = 0; i < far_stages && i < far_n; ++i) {
-        int last = i + ((far_n - 1 - i) / far_stages) * far_stages;
-        mbar_wait_bounded(&full_far[i], (uint32_t)((last / far_stages) & 1), nullptr);
-      }
+      // let every copy still in flight land before shared memory is released (no-op when all were consumed)
+      for (int m = max(rel, n - WS_NSTG); m < n; ++m)
+        mbar_wait_bounded(&full_far[m % WS_NSTG], (uint32_t)((m / WS_NSTG) & 1), nullptr);
     }
+  } else if (wid == 2) {
+    // ------------------------------------------------------------ diagonal-chunk producer
+    // per-thread 16-byte cp.async copies (the load/store path, leaving the bulk-copy engine to the far rows);
+    // each lane's copies of a stage complete into the stage's full barrier (32 arrivals)
+    for (int s = 0; s < nsteps; ++s) {
+      const int p = (s < np) ? s : (2 * np - 1 - s);
+      const int slot = s % c0_stages;
+      if (s >= c0_stages && !mbar_wait_bounded(&empty_c0[slot], (uint32_t)((s / c0_stages - 1) & 1), &s_abort)) {
+        s_abort = 1;
+        if (lane == 0) atomicCAS(status, 0, (int)HPLMM_ERR_TIMEOUT);
+        break;
+      }
+      const unsigned char *src = reinterpret_cast<const unsigned char *>(B + (long long)p * RP * NB);
+      unsigned char *dst = reinterpret_cast<unsigned char *>(c0_ring + (size_t)slot * 2 * NB * NB);
+      for (int piece = lane; piece < c0rows * G; piece += 32) cp_async16(dst + piece * 16, src + piece * 16);
+      asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(smem_u32(&full_c0[slot])) : "memory");
+    }
+    cp_async_wait_pending(0);
   } else if (wid == 0) {
     // ------------------------------------------------------------ leader: diagonal and near blocks
-    // the chunk of step s lives in slot s % c0_stages; lane l copies the 16-byte pieces l, l+32, ...
-    auto issue_c0 = [&](int s) {
-      if (s < nsteps) {
-        const int p = (s < np) ? s : (2 * np - 1 - s);
-        const unsigned char *src = reinterpret_cast<const unsigned char *>(B + (long long)p * RP * NB);
-        unsigned char *dst = reinterpret_cast<unsigned char *>(c0_ring + (size_t)(s % c0_stages) * 2 * NB * NB);
-        for (int piece = lane; piece < c0rows * G; piece += 32) cp_async16(dst + piece * 16, src + piece * 16);
-      }
-      cp_async_commit();
-    };
-    for (int s = 0; s < c0_stages - 1; ++s) issue_c0(s);
+    const int i = lane % NB;
+    const bool own = lane < NB;  // lanes that own row i of the panel (all lanes for NB = 32)
+    // rotation of the 16-byte groups of row i (distinct bank groups within each 8-lane phase)
+    const int off = (G == 8) ? (i & 7) : ((i >> 1) & 3);
+    // window refill of the forward sweep: at step p the slot of row (p - 3) NB + i (its last reader, bulk
+    // step p - 2, has finished) takes row refill_row(p) = (p - 3) NB + W + i; its index is loaded two steps
+    // and its value one step ahead
+    auto refill_row = [&](int pp) { return (pp - 3) * NB + W + i; };
+    int rg = -1;       // global index of refill_row(p + 1)
+    double rv = 0.0;   // right-hand side of refill_row(p)
+    if (own && refill_row(1) < N) rg = gi[refill_row(1)];
     T near = 0;
+    T y_next = 0;      // backward: y of the panel of the next step
+    int zg_next = -1;  // backward: global index of row i of the panel of the next step
+    int fail = 0;
     for (int s = 0; s < nsteps; ++s) {
       const bool fwd = s < np;
       const int p = fwd ? s : (2 * np - 1 - s);
       const int k0 = p * NB, nb = min(NB, N - k0);
-      // refill the slot read during step s-1 (every lane finished it before the last step barrier)
-      issue_c0(s + c0_stages - 1);
-      cp_async_wait_pending(c0_stages - 1);
-      __syncwarp();
-      int fail = 0;
-      {
-        const S *c0 = c0_ring + (size_t)(s % c0_stages) * 2 * NB * NB;
-        const int i = lane % NB;
+      // forward: the rows of panel p are final once the first NB far rows of bulk step s-1 and all of bulk
+      // step s-2 are done; backward: the far sums of panel p come from bulk step s-1
+      if (fwd) {
+        if (s >= 1 && !mbar_wait_bounded(&urg[(s - 1) & 3], (uint32_t)(((s - 1) >> 2) & 1), &s_abort)) fail = 1;
+        if (s >= 2 && !fail && !mbar_wait_bounded(&bdone[(s - 2) & 3], (uint32_t)(((s - 2) >> 2) & 1), &s_abort))
+          fail = 1;
+      } else {
+        if (!mbar_wait_bounded(&bdone[(s - 1) & 3], (uint32_t)(((s - 1) >> 2) & 1), &s_abort)) fail = 1;
+      }
+      if (fwd && !fail) {
+        if (p >= 3 && own && refill_row(p) < N) v[refill_row(p) & wmask] = (T)rv;
+        rv = (rg >= 0) ? r[rg] : 0.0;
+        rg = -1;
+        if (own && refill_row(p + 2) < N) rg = gi[refill_row(p + 2)];
+      }
+      const int slot = s % c0_stages;
+      if (!fail && !mbar_wait_bounded(&full_c0[slot], (uint32_t)((s / c0_stages) & 1), &s_abort)) fail = 1;
+      if (!fail) {
+        const S *c0 = c0_ring + (size_t)slot * 2 * NB * NB;
         if (fwd) {
-          T x = (lane < nb) ? v[k0 + lane] - near : (T)0;
-          T y = 0;
+          // y_p = inv(L_pp) x with x = v_p - near (row i of inv(L_pp) against x broadcast from shared memory)
+          const T x = (lane < nb) ? v[(k0 + lane) & wmask] - near : (T)0;
+          if (own) lbuf[i] = x;
+          __syncwarp();
+          T a0 = 0, a1 = 0;
 #pragma unroll
-          for (int j = 0; j < NB; ++j) {
-            const int jj = (j + i) % NB;
-            y += ld_elem(c0 + i * NB + jj) * __shfl_sync(0xffffffffu, x, jj);
+          for (int g = 0; g < G; ++g) {
+            const int gg = (g + off) % G;
+            T cf[E], xv[E];
+            Vec16<S>::load(c0 + i * NB + gg * E, cf);
+            ld_vec<T, E>(lbuf + gg * E, xv);
+#pragma unroll
+            for (int e = 0; e < E; ++e) (g & 1 ? a1 : a0) += cf[e] * xv[e];
           }
-          if (lane < nb) v[k0 + lane] = y;
+          T y = (lane < nb) ? a0 + a1 : (T)0;
+          if (own) {
+            v[(k0 + i) & wmask] = y;  // read by the bulk warps at the next step and by the near product
+            if (lane < nb) ys[k0 + i] = y;
+          }
+          __syncwarp();
           // near product for the next block (rows NB .. c0rows of the chunk; the rest were not copied, their
           // coefficients are taken as zero)
           const bool nvalid = NB + i < c0rows;
-          T nr = 0;
+          T b0 = 0, b1 = 0;
 #pragma unroll
-          for (int j = 0; j < NB; ++j) {
-            const int jj = (j + i) % NB;
-            const T coef = nvalid ? ld_elem(c0 + (NB + i) * NB + jj) : (T)0;
-            nr += coef * __shfl_sync(0xffffffffu, y, jj);
+          for (int g = 0; g < G; ++g) {
+            const int gg = (g + off) % G;
+            T cf[E], yv[E];
+            Vec16<S>::load(c0 + (NB + i) * NB + gg * E, cf);
+            ld_vec<T, E>(v + ((k0 + gg * E) & wmask), yv);
+#pragma unroll
+            for (int e = 0; e < E; ++e) (g & 1 ? b1 : b0) += cf[e] * yv[e];
           }
-          near = nr;
+          near = nvalid ? b0 + b1 : (T)0;
+          if (p == np - 1) {
+            // the backward sweep starts with this panel
+            y_next = y;
+            zg_next = -1;
+            if (lane < nb) zg_next = gi[k0 + i];
+          }
         } else {
+          const T yv = y_next;
+          const int zg = zg_next;
+          if (p > 0) {
+            y_next = own ? ys[k0 - NB + i] : (T)0;
+            zg_next = -1;
+            if (own) zg_next = gi[k0 - NB + i];
+          }
           // far partial sums of panel p (bulk warps computed them in the previous step)
           T far = 0;
           if (p + 1 < np) {
 #pragma unroll
             for (int w = 0; w < WS_BULK_WARPS; ++w) far += red[p & 1][w][i];
           }
-          // near: L_{p+1,p}^T x_{p+1}; rows past the matrix hold zeros in v
-          T nt = 0;
-          const int nrows = c0rows - NB;
-          for (int rr = 0; rr < nrows; ++rr) nt += ld_elem(c0 + (NB + rr) * NB + i) * v[k0 + NB + rr];
-          T t = (lane < nb) ? v[k0 + lane] - far - nt : (T)0;
-          T x = 0;
+          // near: L_{p+1,p}^T x_{p+1} (column i of the near block; rows past the matrix contribute nothing)
+          const int nrows = min(c0rows - NB, N - k0 - NB);
+          T n0 = 0, n1 = 0;
+          if (nrows > 0) {
+            const T *xn = v + ((k0 + NB) & wmask);
 #pragma unroll
-          for (int cc = 0; cc < NB; ++cc) x += ld_elem(c0 + cc * NB + i) * __shfl_sync(0xffffffffu, t, cc);
-          if (lane < nb) v[k0 + lane] = x;
+            for (int g = 0; g < NB / (16 / (int)sizeof(T)); ++g) {
+              constexpr int ET = 16 / sizeof(T);
+              T xv[ET];
+              ld_vec<T, ET>(xn + g * ET, xv);
+#pragma unroll
+              for (int e = 0; e < ET; ++e) {
+                const int rr = g * ET + e;
+                const T c = ld_elem(c0 + (NB + rr) * NB + i);
+                if (rr < nrows) (e & 1 ? n1 : n0) += c * xv[e];
+              }
+            }
+          }
+          const T t = (lane < nb) ? yv - far - (n0 + n1) : (T)0;
+          if (own) lbuf[i] = t;
+          __syncwarp();
+          // x_p = inv(L_pp)^T t (column i of inv(L_pp) against t broadcast from shared memory)
+          T a0 = 0, a1 = 0;
+#pragma unroll
+          for (int g = 0; g < NB / (16 / (int)sizeof(T)); ++g) {
+            constexpr int ET = 16 / sizeof(T);
+            T tv[ET];
+            ld_vec<T, ET>(lbuf + g * ET, tv);
+#pragma unroll
+            for (int e = 0; e < ET; ++e) (e & 1 ? a1 : a0) += ld_elem(c0 + (g * ET + e) * NB + i) * tv[e];
+          }
+          const T x = a0 + a1;
+          if (lane < nb) {
+            v[(k0 + i) & wmask] = x;
+            if (atomic)
+              atomicAdd(&z[zg], (double)x);
+            else
+              z[zg] = (double)x;
+          }
+        }
+        __syncwarp();
+        if (lane == 0) {
+          mbar_arrive(&empty_c0[slot]);
+          mbar_arrive(&ydone[s & 3]);
         }
       }
-      if (fail) s_abort = 1;
-      if (step_barrier_or(fail, NT_STEP)) break;
+      if (fail) {
+        s_abort = 1;
+        if (lane == 0) atomicCAS(status, 0, (int)HPLMM_ERR_TIMEOUT);
+        break;
+      }
     }
   } else {
     // ------------------------------------------------------------ bulk: far rows of panel p-1
-    const int bw_id = wid - 2;
-    const int tb = threadIdx.x - 64;
-    // rotation of this thread's group order: rows of 8 groups use (row mod 8); rows of 4 groups use
-    // ((row / 2) mod 4), which again spreads 8 consecutive rows over 8 distinct 16-byte bank groups
+    const int bw_id = wid - 3;
+    const int tb = threadIdx.x - 96;
+    // rotation of this thread's group order: rows of 8 groups use (thread mod 8); rows of 4 groups use
+    // ((thread / 2) mod 4), which again spreads 8 consecutive rows over 8 distinct 16-byte bank groups
     const int off = (G == 8) ? (tb & 7) : ((tb >> 1) & 3);
-    int far_n = 0;
-    for (int s = 0; s < nsteps; ++s) {
+    int n = 0, pos = 0;  // chunk sequence number and ring row of the next chunk
+    int fail = 0;
+    for (int s = 0; s < nsteps && !fail; ++s) {
       const bool fwd = s < np;
       const int p = fwd ? s : (2 * np - 1 - s);
       const int q = p - 1;
-      int fail = 0;
-      if (q >= 0) {
+      bool urgent_pending = (bw_id == 0);  // warp 0 owns far rows 0 .. 31, the next panel's rows
+      // y_{p-1} (forward) or x of the panels above (backward) come from leader step s-1
+      if (s >= 1 && !mbar_wait_bounded(&ydone[(s - 1) & 3], (uint32_t)(((s - 1) >> 2) & 1), &s_abort)) fail = 1;
+      if (q >= 0 && !fail) {
         const int kq = q * NB;
-        const int nf = geo.nfar(q), nc = geo.nchunks(q);
+        const int nf = geo.nfar(q);
         T acc[NB];
         T yr[NB];
         if (fwd) {
           // y_{q} in rotated group order
 #pragma unroll
-          for (int g = 0; g < G; ++g)
-#pragma unroll
-            for (int e = 0; e < E; ++e) yr[g * E + e] = v[kq + ((g + off) % G) * E + e];
+          for (int g = 0; g < G; ++g) ld_vec<T, E>(v + ((kq + ((g + off) % G) * E) & wmask), yr + g * E);
         } else {
 #pragma unroll
           for (int e = 0; e < NB; ++e) acc[e] = 0;
         }
-        for (int cix = 0; cix < nc; ++cix) {
-          const int slot = far_n % far_stages;
-          if (!fail && !mbar_wait_bounded(&full_far[slot], (uint32_t)((far_n / far_stages) & 1), &s_abort)) fail = 1;
+        for (int r0 = 0; r0 < nf; r0 += cr) {
+          const int rows = min(cr, nf - r0);
+          const int slot = n % WS_NSTG;
+          if (!fail && !mbar_wait_bounded(&full_far[slot], (uint32_t)((n / WS_NSTG) & 1), &s_abort)) fail = 1;
           if (!fail) {
-#pragma unroll
-           for (int h = 0; h < RPT; ++h) {
-            const int rr = cix * WS_FAR_ROWS + h * (WS_BULK_WARPS * 32) + tb;  // far row index (same offset mod 8)
-            if (rr < nf) {
-              const S *row = far_ring + (size_t)slot * WS_FAR_ROWS * NB + (size_t)(h * WS_BULK_WARPS * 32 + tb) * NB;
-              const int vrow = kq + 2 * NB + rr;
+            // two rows per thread per pass (t and t + WS_BULK_THREADS)
+            for (int t = tb; t < rows; t += 2 * WS_BULK_THREADS) {
+              const int t2 = t + WS_BULK_THREADS;
+              const bool two = t2 < rows;
+              int rs = pos + t, rs2 = pos + t2;
+              if (rs >= ring_eff) rs -= ring_eff;
+              if (rs2 >= ring_eff) rs2 -= ring_eff;
+              if (two && rs2 >= ring_rows) rs2 -= ring_rows;
+              const S *row = ring + (size_t)rs * NB;
+              const S *row2 = ring + (size_t)(two ? rs2 : rs) * NB;
+              const int vrow = (kq + 2 * NB + r0 + t) & wmask;
+              const int vrow2 = (kq + 2 * NB + r0 + t2) & wmask;
+              // forward updates use shared-memory atomics: consecutive bulk steps may overlap on a row
               if (fwd) {
-                T s0 = 0, s1 = 0;
+                if (two) {
+                  T s0 = 0, s1 = 0, s2 = 0, s3 = 0;
 #pragma unroll
-                for (int g = 0; g < G; g += 2) {
-                  T ra[E], rb[E];
-                  Vec16<S>::load(row + ((g + off) % G) * E, ra);
-                  Vec16<S>::load(row + ((g + 1 + off) % G) * E, rb);
+                  for (int g = 0; g < G; g += 2) {
+                    T ra[E], rb[E], rc[E], rd[E];
+                    Vec16<S>::load(row + ((g + off) % G) * E, ra);
+                    Vec16<S>::load(row + ((g + 1 + off) % G) * E, rb);
+                    Vec16<S>::load(row2 + ((g + off) % G) * E, rc);
+                    Vec16<S>::load(row2 + ((g + 1 + off) % G) * E, rd);
 #pragma unroll
-                  for (int e = 0; e < E; ++e) {
-                    s0 += ra[e] * yr[g * E + e];
-                    s1 += rb[e] * yr[(g + 1) * E + e];
+                    for (int e = 0; e < E; ++e) {
+                      s0 += ra[e] * yr[g * E + e];
+                      s1 += rb[e] * yr[(g + 1) * E + e];
+                      s2 += rc[e] * yr[g * E + e];
+                      s3 += rd[e] * yr[(g + 1) * E + e];
+                    }
                   }
+                  atomicAdd(&v[vrow], -(s0 + s1));
+                  atomicAdd(&v[vrow2], -(s2 + s3));
+                } else {
+                  T s0 = 0, s1 = 0;
+#pragma unroll
+                  for (int g = 0; g < G; g += 2) {
+                    T ra[E], rb[E];
+                    Vec16<S>::load(row + ((g + off) % G) * E, ra);
+                    Vec16<S>::load(row + ((g + 1 + off) % G) * E, rb);
+#pragma unroll
+                    for (int e = 0; e < E; ++e) {
+                      s0 += ra[e] * yr[g * E + e];
+                      s1 += rb[e] * yr[(g + 1) * E + e];
+                    }
+                  }
+                  atomicAdd(&v[vrow], -(s0 + s1));
                 }
-                v[vrow] -= s0 + s1;
               } else {
                 const T xv = v[vrow];
+                if (two) {
+                  const T xv2 = v[vrow2];
 #pragma unroll
-                for (int g = 0; g < G; ++g) {
-                  T ra[E];
-                  Vec16<S>::load(row + ((g + off) % G) * E, ra);
+                  for (int g = 0; g < G; ++g) {
+                    T ra[E], rc[E];
+                    Vec16<S>::load(row + ((g + off) % G) * E, ra);
+                    Vec16<S>::load(row2 + ((g + off) % G) * E, rc);
 #pragma unroll
-                  for (int e = 0; e < E; ++e) acc[g * E + e] += ra[e] * xv;
+                    for (int e = 0; e < E; ++e) acc[g * E + e] += ra[e] * xv + rc[e] * xv2;
+                  }
+                } else {
+#pragma unroll
+                  for (int g = 0; g < G; ++g) {
+                    T ra[E];
+                    Vec16<S>::load(row + ((g + off) % G) * E, ra);
+#pragma unroll
+                    for (int e = 0; e < E; ++e) acc[g * E + e] += ra[e] * xv;
+                  }
                 }
               }
             }
-           }
             __syncwarp();
             if (lane == 0) mbar_arrive(&empty_far[slot]);
+            if (fwd && urgent_pending) {
+              // warp 0's part of the first chunk covered far rows 0 .. 31: the leader may start the next panel
+              if (lane == 0) mbar_arrive(&urg[s & 3]);
+              urgent_pending = false;
+            }
           }
-          ++far_n;
+          pos += whole ? nf_int : rows;
+          if (pos >= ring_eff) pos -= ring_eff;
+          ++n;
         }
         if (!fwd) {
           // reduce the column sums over the lanes that share a rotation (8 groups: equal lane & 7, i.e. lane
-          // bits 3 and 4 vary; 4 groups: equal (lane >> 1) & 3, i.e. bits 0, 3 and 4 vary), then undo the
-          // rotation of one representative lane per rotation class
+          // bits 3 and 4 vary; 4 groups: equal (lane >> 1) & 3, i.e. bits 0, 3 and 4 vary) ...
 #pragma unroll
           for (int e = 0; e < NB; ++e) {
             if (G == 4) acc[e] += __shfl_xor_sync(0xffffffffu, acc[e], 1);
             acc[e] += __shfl_xor_sync(0xffffffffu, acc[e], 8);
             acc[e] += __shfl_xor_sync(0xffffffffu, acc[e], 16);
           }
+          // ... then across the rotation classes: the representative of class c collects column group c.  In
+          // round d it takes, from the representative of class c - d, that lane's rotated group d, which holds
+          // column group (d + c - d) = c
+          const int cls = (G == 8) ? (lane & 7) : ((lane >> 1) & 3);
+          T tot[E];
+#pragma unroll
+          for (int e = 0; e < E; ++e) tot[e] = 0;
+#pragma unroll
+          for (int d = 0; d < G; ++d) {
+            const int src = (G == 8) ? ((cls - d) & 7) : (((cls - d) & 3) << 1);
+#pragma unroll
+            for (int e = 0; e < E; ++e) tot[e] += __shfl_sync(0xffffffffu, acc[d * E + e], src);
+          }
           const bool rep_lane = (G == 8) ? (lane < 8) : ((lane & 0x19) == 0);
           if (rep_lane) {
-            const int cls = (G == 8) ? lane : ((lane >> 1) & 3);
 #pragma unroll
-            for (int g = 0; g < G; ++g)
-#pragma unroll
-              for (int e = 0; e < E; ++e) stage[bw_id][cls][((g + cls) % G) * E + e] = acc[g * E + e];
+            for (int e = 0; e < E; ++e) red[q & 1][bw_id][cls * E + e] = tot[e];
           }
-          __syncwarp();
-          if (lane < NB) {
-            T sum = 0;
-#pragma unroll
-            for (int c = 0; c < G; ++c) sum += stage[bw_id][c][lane];
-            red[q & 1][bw_id][lane] = sum;
-          }
-          __syncwarp();
         }
       }
-      if (fail) s_abort = 1;
-      if (step_barrier_or(fail, NT_STEP)) break;
+      if (fail) {
+        s_abort = 1;
+        if (lane == 0) atomicCAS(status, 0, (int)HPLMM_ERR_TIMEOUT);
+        break;
+      }
+      __syncwarp();
+      if (lane == 0) {
+        if (urgent_pending) mbar_arrive(&urg[s & 3]);  // no far rows in this step's first pass
+        mbar_arrive(&bdone[s & 3]);
+      }
     }
   }
-  cp_async_wait_pending(0);
   __syncthreads();
-  if (s_abort) return;
-  for (int l = threadIdx.x; l < N; l += WS_THREADS) {
-    int o = l / 3, d = l - 3 * o;
-    long long slot = 3LL * ln[o] + d;
-    if (atomic)
-      atomicAdd(&z[slot], (double)v[l]);
-    else
-      z[slot] = (double)v[l];
-  }
 }
 
 template <typename T>
@@ -1497,6 +1696,10 @@ static void enumerate_set(hplmm_ctx *c, LocalSet &S, int kind) {
   S.h_vec_off = voff;
   S.vec_total = voff[K];
   S.vec_off.upload(voff, s);
+  S.yscr.alloc(std::max<long long>(S.vec_total, 1));
+  S.gidx.alloc(std::max<long long>(S.vec_total, 1));
+  k_local_gidx<<<K, 256, 0, s>>>(S.n.p, S.node_off.p, S.vec_off.p, S.lnodes.p, S.gidx.p);
+  HP_CHECK_LAUNCH();
   std::vector<int> ord(K);
   std::iota(ord.begin(), ord.end(), 0);
   std::stable_sort(ord.begin(), ord.end(), [&](int a, int b) {
@@ -1700,71 +1903,75 @@ void solve_local_multi_f32(hplmm_ctx *c, LocalSet &S, float *X, const Buf<long l
   solve_multi_t<float>(c, S, X, x_off, x_ld, h_ld);
 }
 
-// shared-memory plan of the smoother solve for a set: bytes of one far stage, one diagonal stage and the
-// padded local vector (stored-row width 128 bytes for FP32/FP64 factors, 64 bytes for BF16)
+// shared-memory plan of the smoother solve for a set: stored-row width (128 bytes for FP32/FP64 factors, 64
+// bytes for BF16), one diagonal+near chunk, and the local vector window (a power of two >= RP + 3 NB rows)
 struct SolvePlan {
-  size_t far_slot, c0_slot, vbytes;
+  int rowb, W;
+  size_t c0_slot, vbytes;
 };
+constexpr size_t WS_SMEM_BUDGET = 224 * 1024;  // dynamic shared memory of one CTA per SM
+constexpr size_t WS_SMEM_PAIR = 108 * 1024;    // dynamic shared memory that lets two CTAs share an SM
 
-// far rows per bulk thread of the instantiated kernels: FP64 1; FP32 1 or 2; BF16 2 or 4
-static int default_rpt(const LocalSet &S) {
-  return S.prec == HPLMM_FP64 ? far_rpt<double>() : (S.apply_bf16 ? far_rpt<__nv_bfloat16>() : far_rpt<float>());
-}
-static std::vector<int> rpt_choices(const LocalSet &S) {
-  if (S.prec == HPLMM_FP64) return {1};
-  return S.apply_bf16 ? std::vector<int>{2, 4} : std::vector<int>{1, 2};
-}
-
-static SolvePlan solve_plan(const LocalSet &S, int rpt) {
+static SolvePlan solve_plan(const LocalSet &S) {
   const bool f64 = S.prec == HPLMM_FP64;
   const int NBv = f64 ? 16 : 32;
-  const size_t esz = f64 ? 8 : 4;  // local vector element
-  const size_t rowb = S.apply_bf16 ? 64 : 128;
-  int vmax = 0;
-  for (int k = 0; k < S.count; ++k)
-    if (S.h_n[k] > 0) vmax = std::max(vmax, ((S.h_n[k] + NBv - 1) / NBv) * NBv + NBv);
+  const size_t esz = f64 ? 8 : 4;  // compute type of the local vector
   SolvePlan pl;
-  pl.vbytes = ((esz * (size_t)std::max(vmax, 1) + 127) / 128) * 128;
-  pl.far_slot = (size_t)WS_BULK_WARPS * 32 * rpt * rowb;
-  pl.c0_slot = (size_t)2 * NBv * rowb;
+  pl.rowb = S.apply_bf16 ? 64 : 128;
+  pl.c0_slot = (size_t)2 * NBv * pl.rowb;
+  int need = 4 * NBv;  // RP + 3 NB rows
+  for (int k = 0; k < S.count; ++k)
+    if (S.h_n[k] > 0) need = std::max(need, S.h_bw[k] + 4 * NBv);
+  pl.W = 1;
+  while (pl.W < need) pl.W <<= 1;
+  pl.vbytes = ((esz * (size_t)pl.W + 127) / 128) * 128;
   return pl;
+}
+
+// far chunk sizes (rows) the tuner tries: 64 KiB, and a whole step's far rows per copy
+static std::vector<int> chunk_choices(const LocalSet &S) {
+  return S.apply_bf16 ? std::vector<int>{1024, 4096} : std::vector<int>{512, 2048};
+}
+
+// ring rows that fit in `budget` bytes next to c0s diagonal stages and the window (a multiple of 8)
+static int ring_rows_for(const SolvePlan &pl, int c0s, size_t budget) {
+  const long long avail = (long long)budget - (long long)c0s * (long long)pl.c0_slot - (long long)pl.vbytes;
+  return avail > 0 ? (int)((avail / pl.rowb) & ~7LL) : 0;
 }
 
 void smoother_apply(hplmm_ctx *c, LocalSet &S, const double *r_pad, double *z_pad, bool atomic) {
   if (S.count == 0) return;
   ProfScope ps(c, (&S == &c->grains) ? HPLMM_PH_APPLY_GRAINS : HPLMM_PH_APPLY_CONTACTS);
   cudaStream_t s = c->stream;
-  const int rpt = S.tuned_rpt > 0 ? S.tuned_rpt : default_rpt(S);
-  const SolvePlan pl = solve_plan(S, rpt);
-  const size_t budget = 216 * 1024;
-  HP_REQUIRE(pl.vbytes + 2 * pl.c0_slot + 2 * pl.far_slot <= budget, HPLMM_ERR_INVALID,
-             "local problem too large for the smoother (" + std::to_string(pl.vbytes) + " bytes of local vector)");
-  // depths: the tuner's choice when there is one, else 4 diagonal stages and as many far stages as fit
-  int c0s = S.tuned_c0_stages > 0 ? S.tuned_c0_stages : 4;
-  if (pl.vbytes + c0s * pl.c0_slot + 2 * pl.far_slot > budget) c0s = 2;
-  int fs = (int)std::min<size_t>(WS_MAX_FAR_STAGES, (budget - pl.vbytes - c0s * pl.c0_slot) / pl.far_slot);
-  if (S.tuned_far_stages > 0) fs = std::min(fs, S.tuned_far_stages);
-  const size_t smem = (size_t)fs * pl.far_slot + (size_t)c0s * pl.c0_slot + pl.vbytes;
-  auto go = [&](auto kern, const auto *band) {
+  const SolvePlan pl = solve_plan(S);
+  // depths: the tuner's choice when there is one, else 3 diagonal stages, 64 KiB chunks and the largest ring
+  const int c0s = S.tuned_c0_stages > 0 ? S.tuned_c0_stages : 3;
+  int ring = ring_rows_for(pl, c0s, WS_SMEM_BUDGET);
+  if (S.tuned_ring_rows > 0) ring = std::min(ring, S.tuned_ring_rows);
+  HP_REQUIRE(ring >= 64, HPLMM_ERR_INVALID,
+             "local problem too large for the smoother (window of " + std::to_string(pl.W) + " rows)");
+  const int chunk = std::min(ring, S.tuned_chunk_rows > 0 ? S.tuned_chunk_rows : chunk_choices(S).back());
+  const size_t smem = (size_t)ring * pl.rowb + (size_t)c0s * pl.c0_slot + pl.vbytes;
+  auto go = [&](auto kern, const auto *band, auto *ys) {
     HP_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    kern<<<S.count, WS_THREADS, smem, s>>>(S.count, S.n.p, S.bw.p, S.band_off.p, S.node_off.p, S.lnodes.p, band,
-                                           r_pad, z_pad, atomic ? 1 : 0, fs, c0s, c->status.p);
+    kern<<<S.count, WS_THREADS, smem, s>>>(S.count, S.n.p, S.bw.p, S.band_off.p, S.vec_off.p, S.gidx.p, band,
+                                           r_pad, z_pad, ys, atomic ? 1 : 0, ring, chunk, c0s, pl.W - 1,
+                                           c->status.p);
   };
   if (S.prec == HPLMM_FP64)
-    go(k_band_solve_ws<double, 16, 1>, S.band64.p);
+    go(k_band_solve_ws<double, 16>, S.band64.p, S.yscr.p);
   else if (S.apply_bf16)
-    rpt == 2 ? go(k_band_solve_ws<__nv_bfloat16, 32, 2>, S.band16.p) : go(k_band_solve_ws<__nv_bfloat16, 32, 4>, S.band16.p);
+    go(k_band_solve_ws<__nv_bfloat16, 32>, S.band16.p, reinterpret_cast<float *>(S.yscr.p));
   else
-    rpt == 1 ? go(k_band_solve_ws<float, 32, 1>, S.band32.p) : go(k_band_solve_ws<float, 32, 2>, S.band32.p);
+    go(k_band_solve_ws<float, 32>, S.band32.p, reinterpret_cast<float *>(S.yscr.p));
   HP_CHECK_LAUNCH();
 }
 
 // ---------------------------------------------------------------- tuner of the smoother solve pipeline
-// For each set of local problems, time the smoother solve under every plan that fits in shared memory (far
-// rows per bulk thread x far-row stages x diagonal-chunk stages) on the set's own factors, and keep the
-// fastest.  Results
-// are cached for the process, keyed by (count, largest local size, largest half bandwidth, precision), so a
-// repeated set-up of the same size pays nothing.
+// For each set of local problems, time the smoother solve under every plan (far chunk size x diagonal-chunk
+// stages x ring size: the largest, or one small enough for two CTAs per SM) on the set's own factors, and
+// keep the fastest.  Results are cached for the process, keyed by (count, largest local size, largest half
+// bandwidth, precision), so a repeated set-up of the same size pays nothing.
 namespace {
 struct TuneKey {
   int count, nmax, bwmax, prec;
@@ -1774,13 +1981,13 @@ struct TuneKey {
 };
 std::mutex g_tune_mu;
 struct TuneChoice {
-  int rpt, far_stages, c0_stages;
+  int chunk_rows, ring_rows, c0_stages;
 };
 std::map<TuneKey, TuneChoice> g_tune_cache;
 }  // namespace
 
 static void tune_set(hplmm_ctx *c, LocalSet &S, bool atomic) {
-  S.tuned_far_stages = S.tuned_c0_stages = S.tuned_rpt = 0;
+  S.tuned_chunk_rows = S.tuned_ring_rows = S.tuned_c0_stages = 0;
   if (S.count == 0) return;
   TuneKey key{S.count, 0, 0, (int)S.prec + (S.apply_bf16 ? 8 : 0)};
   for (int k = 0; k < S.count; ++k) {
@@ -1791,13 +1998,13 @@ static void tune_set(hplmm_ctx *c, LocalSet &S, bool atomic) {
     std::lock_guard<std::mutex> lk(g_tune_mu);
     auto it = g_tune_cache.find(key);
     if (it != g_tune_cache.end()) {
-      S.tuned_rpt = it->second.rpt;
-      S.tuned_far_stages = it->second.far_stages;
+      S.tuned_chunk_rows = it->second.chunk_rows;
+      S.tuned_ring_rows = it->second.ring_rows;
       S.tuned_c0_stages = it->second.c0_stages;
       return;
     }
   }
-  const size_t budget = 216 * 1024;
+  const SolvePlan pl = solve_plan(S);
   cudaStream_t s = c->stream;
   cudaEvent_t e0, e1;
   HP_CUDA(cudaEventCreate(&e0));
@@ -1805,52 +2012,49 @@ static void tune_set(hplmm_ctx *c, LocalSet &S, bool atomic) {
   const bool prof = c->opt.profile;
   c->opt.profile = 0;  // tuning launches are not part of any phase
   float best = 1e30f;
-  int bf = 0, bc = 0, br = 0;
-  // candidates include small-footprint plans that let two CTAs share an SM (<= ~110 KiB each)
-  for (int rpt : rpt_choices(S))
-   for (int c0d = 2; c0d <= 4; ++c0d)
-    for (int fd = 2; fd <= 8; ++fd) {
-      const SolvePlan pl = solve_plan(S, rpt);
-      if (pl.vbytes + c0d * pl.c0_slot + fd * pl.far_slot > budget) break;
-      S.tuned_rpt = rpt;
-      S.tuned_far_stages = fd;
-      S.tuned_c0_stages = c0d;
-      smoother_apply(c, S, c->b_pad.p, c->w_zz.p, atomic);  // warm-up
-      HP_CUDA(cudaEventRecord(e0, s));
-      for (int rep = 0; rep < 3; ++rep) smoother_apply(c, S, c->b_pad.p, c->w_zz.p, atomic);
-      HP_CUDA(cudaEventRecord(e1, s));
-      HP_CUDA(cudaEventSynchronize(e1));
-      float ms = 0.f;
-      HP_CUDA(cudaEventElapsedTime(&ms, e0, e1));
-      if (c->opt.verbose)
-        fprintf(stderr, "[hplmm] tuner trial: %d problems, %d far rows per thread, far %d, diagonal %d: %.3f ms\n",
-                S.count, rpt, fd, c0d, ms / 3);
-      if (ms < best) {
-        best = ms;
-        bf = fd;
-        bc = c0d;
-        br = rpt;
+  TuneChoice bc{0, 0, 0};
+  for (int chunk : chunk_choices(S))
+    for (int c0d = 2; c0d <= 4; ++c0d)
+      for (size_t budget : {WS_SMEM_BUDGET, WS_SMEM_PAIR}) {
+        const int ring = ring_rows_for(pl, c0d, budget);
+        const int cr = std::min(chunk, ring);
+        if (cr < 64) continue;
+        S.tuned_chunk_rows = cr;
+        S.tuned_ring_rows = ring;
+        S.tuned_c0_stages = c0d;
+        smoother_apply(c, S, c->b_pad.p, c->w_zz.p, atomic);  // warm-up
+        HP_CUDA(cudaEventRecord(e0, s));
+        for (int rep = 0; rep < 3; ++rep) smoother_apply(c, S, c->b_pad.p, c->w_zz.p, atomic);
+        HP_CUDA(cudaEventRecord(e1, s));
+        HP_CUDA(cudaEventSynchronize(e1));
+        float ms = 0.f;
+        HP_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+        if (c->opt.verbose)
+          fprintf(stderr, "[hplmm] tuner trial: %d problems, chunk %d rows, ring %d rows, diagonal %d: %.3f ms\n",
+                  S.count, cr, ring, c0d, ms / 3);
+        if (ms < best) {
+          best = ms;
+          bc = {cr, ring, c0d};
+        }
       }
-    }
   c->opt.profile = prof;
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
-  S.tuned_rpt = br;
-  S.tuned_far_stages = bf;
-  S.tuned_c0_stages = bc;
+  S.tuned_chunk_rows = bc.chunk_rows;
+  S.tuned_ring_rows = bc.ring_rows;
+  S.tuned_c0_stages = bc.c0_stages;
   if (c->opt.verbose)
     fprintf(stderr,
-            "[hplmm] tuner: %d problems (n<=%d, bw<=%d): %d far rows per thread, far stages %d, diagonal stages %d, "
-            "%.3f ms\n",
-            S.count, key.nmax, key.bwmax, br, bf, bc, best / 3);
+            "[hplmm] tuner: %d problems (n<=%d, bw<=%d): chunk %d rows, ring %d rows, diagonal stages %d, %.3f ms\n",
+            S.count, key.nmax, key.bwmax, bc.chunk_rows, bc.ring_rows, bc.c0_stages, best / 3);
   std::lock_guard<std::mutex> lk(g_tune_mu);
-  g_tune_cache[key] = {br, bf, bc};
+  g_tune_cache[key] = bc;
 }
 
 void tune_local(hplmm_ctx *c) {
   if (!c->opt.autotune) {
-    c->grains.tuned_far_stages = c->grains.tuned_c0_stages = c->grains.tuned_rpt = 0;
-    c->contacts.tuned_far_stages = c->contacts.tuned_c0_stages = c->contacts.tuned_rpt = 0;
+    c->grains.tuned_chunk_rows = c->grains.tuned_ring_rows = c->grains.tuned_c0_stages = 0;
+    c->contacts.tuned_chunk_rows = c->contacts.tuned_ring_rows = c->contacts.tuned_c0_stages = 0;
     return;
   }
   tune_set(c, c->contacts, true);
