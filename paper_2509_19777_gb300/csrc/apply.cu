@@ -35,21 +35,21 @@ __global__ void k_scale_copy(double *y, const double *x, double a, long long n) 
 constexpr int MDOT_BLOCKS = 304;
 constexpr int MAXV = 64;
 
-// partial[b][j] = sum over block b's slice of V_j . w  (j < nv); nv <= MAXV
-__global__ void __launch_bounds__(256) k_mdot(const double *V, long long ldv, int nv, const double *w, long long n,
-                                              double *partial) {
-  __shared__ double red[8][MAXV];
-  int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  double acc[MAXV];
-  for (int j = 0; j < nv; ++j) acc[j] = 0.0;
-  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-    double wi = w[i];
-    for (int j = 0; j < nv; ++j) acc[j] += V[j * ldv + i] * wi;
-  }
-  for (int j = 0; j < nv; ++j) {
-    double s = acc[j];
-    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
-    if (lane == 0) red[wid][j] = s;
+// Block reduction of acc[0..nv) into partial[block][.], then the last block to finish (a ticket on
+// *counter) sums the partials of all blocks into out[0..nv) in a fixed order (deterministic) and resets the
+// ticket: thread (group g, lane j) sums blocks g, g+8, ... of output j, then the 8 groups are added in order.
+template <int CAP>
+__device__ void reduce_blocks(double (&acc)[CAP], int nv, double *partial, double *out, unsigned *counter) {
+  __shared__ double red[8][CAP > 32 ? CAP : 32];
+  __shared__ bool last;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+  for (int j = 0; j < CAP; ++j) {
+    if (j < nv) {
+      double s = acc[j];
+      for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+      if (lane == 0) red[wid][j] = s;
+    }
   }
   __syncthreads();
   for (int j = threadIdx.x; j < nv; j += blockDim.x) {
@@ -57,20 +57,103 @@ __global__ void __launch_bounds__(256) k_mdot(const double *V, long long ldv, in
     for (int w2 = 0; w2 < 8; ++w2) s += red[w2][j];
     partial[(long long)blockIdx.x * MAXV + j] = s;
   }
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) last = atomicAdd(counter, 1u) == gridDim.x - 1;
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  for (int j0 = 0; j0 < nv; j0 += 32) {
+    const int j = j0 + lane;
+    double s = 0.0;
+    if (j < nv) {
+#pragma unroll 8
+      for (int b = wid; b < (int)gridDim.x; b += 8) s += __ldcg(&partial[(long long)b * MAXV + j]);
+    }
+    red[wid][lane] = s;
+    __syncthreads();
+    if (threadIdx.x < 32 && j < nv) {
+      double t = 0.0;
+      for (int g = 0; g < 8; ++g) t += red[g][threadIdx.x];
+      out[j] = t;
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *counter = 0u;
 }
 
-// out[j] = sum over blocks of partial[b][j]: one warp per j, lanes over the blocks, fixed reduction order
-__global__ void k_mdot_final(const double *partial, int nblocks, int nv, double *out) {
-  int j = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-  int lane = threadIdx.x & 31;
-  if (j >= nv) return;
-  double s = 0.0;
-  for (int b = lane; b < nblocks; b += 32) s += partial[(long long)b * MAXV + j];
-  for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
-  if (lane == 0) out[j] = s;
+// out[j] = V_j . w for j < nv <= CAP (accumulators in registers), U elements per thread per pass so that
+// about CAP x U loads are in flight per thread.  The loads are branch-free: slots j >= nv read vector nv-1
+// again (the same addresses, served by L1) and their sums are discarded; elements past n are clamped to
+// n-1 with a zero weight.
+template <int CAP, int U>
+__global__ void __launch_bounds__(256) k_cgs_dot(const double *V, long long ldv, int nv, const double *w, long long n,
+                                                 double *partial, double *out, unsigned *counter) {
+  double acc[CAP];
+#pragma unroll
+  for (int j = 0; j < CAP; ++j) acc[j] = 0.0;
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long i0 = (long long)blockIdx.x * blockDim.x + threadIdx.x; i0 < n; i0 += U * stride) {
+    double wv[U];
+    long long ii[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const long long i = i0 + u * stride;
+      ii[u] = i < n ? i : n - 1;
+      wv[u] = i < n ? w[ii[u]] : 0.0;
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u)
+#pragma unroll
+      for (int j = 0; j < CAP; ++j) acc[j] += V[(long long)min(j, nv - 1) * ldv + ii[u]] * wv[u];
+  }
+  reduce_blocks<CAP>(acc, nv, partial, out, counter);
 }
 
-// w -= sum_j V_j h[j]
+// w <- w - V h over j < nv <= CAP, and in the same pass either out[j] = V_j . w_new (mode 0, the next CGS
+// pass) or out[0] = w_new . w_new (mode 1)
+template <int CAP, int U>
+__global__ void __launch_bounds__(256) k_cgs_update(const double *V, long long ldv, int nv, const double *h, double *w,
+                                                    long long n, int mode, double *partial, double *out,
+                                                    unsigned *counter) {
+  __shared__ double hs[CAP];
+  for (int j = threadIdx.x; j < CAP; j += blockDim.x) hs[j] = j < nv ? h[j] : 0.0;
+  __syncthreads();
+  double acc[CAP];
+#pragma unroll
+  for (int j = 0; j < CAP; ++j) acc[j] = 0.0;
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long i0 = (long long)blockIdx.x * blockDim.x + threadIdx.x; i0 < n; i0 += U * stride) {
+    double v[U][CAP];  // slots j >= nv repeat vector nv-1 (finite) and meet hs[j] = 0
+    double wv[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const long long i = min(i0 + u * stride, n - 1);
+      wv[u] = w[i];
+#pragma unroll
+      for (int j = 0; j < CAP; ++j) v[u][j] = V[(long long)min(j, nv - 1) * ldv + i];
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const long long i = i0 + u * stride;
+      double s = wv[u];
+#pragma unroll
+      for (int j = 0; j < CAP; ++j) s -= v[u][j] * hs[j];
+      if (i < n) {
+        w[i] = s;
+        if (mode == 0) {
+#pragma unroll
+          for (int j = 0; j < CAP; ++j) acc[j] += v[u][j] * s;
+        } else {
+          acc[0] += s * s;
+        }
+      }
+    }
+  }
+  reduce_blocks<CAP>(acc, mode == 0 ? nv : 1, partial, out, counter);
+}
+
+// w -= sum_j V_j h[j] (any nv <= MAXV; the fused kernels cover nv <= 32)
 __global__ void k_mupdate(double *w, const double *V, long long ldv, int nv, const double *h, long long n) {
   __shared__ double hs[MAXV];
   for (int j = threadIdx.x; j < nv; j += blockDim.x) hs[j] = h[j];
@@ -94,11 +177,65 @@ __global__ void k_mcombine(double *x, const double *Z, long long ldz, int nv, co
   }
 }
 
+// out[j] = V_j . w, j < nv (one launch)
 void mdot(hplmm_ctx *c, const double *V, long long ldv, int nv, const double *w, long long n, double *out) {
   ProfScope ps(c, HPLMM_PH_KRYLOV);
-  k_mdot<<<MDOT_BLOCKS, 256, 0, c->stream>>>(V, ldv, nv, w, n, c->w_partial.p);
+  double *pp = c->w_partial.p;
+  unsigned *ct = c->w_ticket.p;
+  auto go = [&](auto kern) { kern<<<MDOT_BLOCKS, 256, 0, c->stream>>>(V, ldv, nv, w, n, pp, out, ct); };
+  if (nv <= 1)
+    go(k_cgs_dot<1, 8>);
+  else if (nv <= 2)
+    go(k_cgs_dot<2, 8>);
+  else if (nv <= 4)
+    go(k_cgs_dot<4, 8>);
+  else if (nv <= 8)
+    go(k_cgs_dot<8, 4>);
+  else if (nv <= 12)
+    go(k_cgs_dot<12, 2>);
+  else if (nv <= 16)
+    go(k_cgs_dot<16, 2>);
+  else if (nv <= 24)
+    go(k_cgs_dot<24, 1>);
+  else if (nv <= 32)
+    go(k_cgs_dot<32, 1>);
+  else
+    go(k_cgs_dot<64, 1>);
   HP_CHECK_LAUNCH();
-  k_mdot_final<<<(nv + 7) / 8, 256, 0, c->stream>>>(c->w_partial.p, MDOT_BLOCKS, nv, out);
+}
+
+// w -= V h; then out = V^T w (mode 0) or out[0] = w . w (mode 1)
+void cgs_update(hplmm_ctx *c, const double *V, long long ldv, int nv, const double *h, double *w, long long n, int mode,
+                double *out) {
+  ProfScope ps(c, HPLMM_PH_KRYLOV);
+  double *pp = c->w_partial.p;
+  unsigned *ct = c->w_ticket.p;
+  auto go = [&](auto kern) { kern<<<MDOT_BLOCKS, 256, 0, c->stream>>>(V, ldv, nv, h, w, n, mode, pp, out, ct); };
+  if (nv <= 1)
+    go(k_cgs_update<1, 8>);
+  else if (nv <= 2)
+    go(k_cgs_update<2, 8>);
+  else if (nv <= 4)
+    go(k_cgs_update<4, 8>);
+  else if (nv <= 8)
+    go(k_cgs_update<8, 4>);
+  else if (nv <= 12)
+    go(k_cgs_update<12, 2>);
+  else if (nv <= 16)
+    go(k_cgs_update<16, 2>);
+  else if (nv <= 24)
+    go(k_cgs_update<24, 1>);
+  else if (nv <= 32)
+    go(k_cgs_update<32, 1>);
+  else {
+    k_mupdate<<<MDOT_BLOCKS, 256, 0, c->stream>>>(w, V, ldv, nv, h, n);
+    HP_CHECK_LAUNCH();
+    if (mode == 0)
+      mdot(c, V, ldv, nv, w, n, out);
+    else
+      mdot(c, w, 0, 1, w, n, out);
+    return;
+  }
   HP_CHECK_LAUNCH();
 }
 
@@ -265,20 +402,10 @@ int fgmres(hplmm_ctx *c, const double *b_pad, double *x_pad, double tol, hplmm_s
       precond_apply_any(c, vj, zj);
       spmv(c, zj, w, HPLMM_FP64);
       ++its;
-      // CGS2
+      // CGS2 in three passes over the basis: h1 = V^T w; w -= V h1 with h2 = V^T w; w -= V h2 with |w|^2
       mdot(c, V, L, j + 1, w, L, dev_h);
-      {
-        ProfScope ps(c, HPLMM_PH_KRYLOV);
-        k_mupdate<<<MDOT_BLOCKS, 256, 0, s>>>(w, V, L, j + 1, dev_h, L);
-        HP_CHECK_LAUNCH();
-      }
-      mdot(c, V, L, j + 1, w, L, dev_h + MAXV);
-      {
-        ProfScope ps(c, HPLMM_PH_KRYLOV);
-        k_mupdate<<<MDOT_BLOCKS, 256, 0, s>>>(w, V, L, j + 1, dev_h + MAXV, L);
-        HP_CHECK_LAUNCH();
-      }
-      mdot(c, w, 0, 1, w, L, dev_h + 2 * MAXV);
+      cgs_update(c, V, L, j + 1, dev_h, w, L, 0, dev_h + MAXV);
+      cgs_update(c, V, L, j + 1, dev_h + MAXV, w, L, 1, dev_h + 2 * MAXV);
       HP_CUDA(cudaMemcpyAsync(hh.data(), dev_h, sizeof(double) * (2 * MAXV + 1), cudaMemcpyDeviceToHost, s));
       HP_CUDA(cudaStreamSynchronize(s));
       for (int i = 0; i <= j; ++i) H[(size_t)i * m + j] = hh[i] + hh[MAXV + i];

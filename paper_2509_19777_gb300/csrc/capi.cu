@@ -103,6 +103,10 @@ void alloc_work(hplmm_ctx *c) {
   c->Z.alloc((size_t)m * L);
   c->w_h.alloc(2 * 64 + 8);
   c->w_partial.alloc(304 * 64);
+  if (c->w_ticket.n == 0) {
+    c->w_ticket.alloc(1);
+    c->w_ticket.zero(c->stream);
+  }
 }
 
 }  // namespace

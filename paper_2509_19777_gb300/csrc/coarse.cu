@@ -433,25 +433,46 @@ __global__ void k_trinv_update(double *Y, const double *L, long long N, int kt, 
     }
 }
 
-// u = Y t over the lower triangle: warp per row
+// u = Y t over the lower triangle: warp per row, 8 loads per lane in flight
 __global__ void k_trmv_lower(const double *Y, long long N, const double *t, double *u) {
-  int lane = threadIdx.x & 31;
-  long long row = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  const long long row = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   if (row >= N) return;
   const double *yr = Y + row * N;
-  double s = 0.0;
-  for (long long j = lane; j <= row; j += 32) s += yr[j] * t[j];
+  double s0 = 0.0, s1 = 0.0;
+  for (long long jb = 0; jb <= row; jb += 256) {
+    double yv[8], tv[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const long long j = jb + q * 32 + lane;
+      const bool in = j <= row;
+      yv[q] = in ? yr[j] : 0.0;
+      tv[q] = in ? t[j] : 0.0;
+    }
+#pragma unroll
+    for (int q = 0; q < 8; ++q) (q & 1 ? s1 : s0) += yv[q] * tv[q];
+  }
+  double s = s0 + s1;
   for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
   if (lane == 0) u[row] = s;
 }
 
-// z = Y^T u over the lower triangle: CTA per 32-row slab, threads over columns, atomic accumulation
+// z = Y^T u over the lower triangle: CTA per 32-row slab, threads over columns (the slab's 32 loads per
+// column issued together), atomic accumulation
 __global__ void k_trmv_lower_t(const double *Y, long long N, const double *u, double *z) {
-  long long r0 = (long long)blockIdx.y * 32;
-  long long r1 = min(N, r0 + 32);
+  __shared__ double us[32];
+  const long long r0 = (long long)blockIdx.y * 32;
+  const long long r1 = min(N, r0 + 32);
+  if (threadIdx.x < 32) us[threadIdx.x] = (r0 + threadIdx.x < r1) ? u[r0 + threadIdx.x] : 0.0;
+  __syncthreads();
   for (long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x; j < r1; j += (long long)gridDim.x * blockDim.x) {
-    double s = 0.0;
-    for (long long i = max(r0, j); i < r1; ++i) s += Y[i * N + j] * u[i];
+    double s0 = 0.0, s1 = 0.0;
+#pragma unroll
+    for (int q = 0; q < 32; ++q) {
+      const long long i = r0 + q;
+      if (i >= j && i < r1) (q & 1 ? s1 : s0) += Y[i * N + j] * us[q];
+    }
+    const double s = s0 + s1;
     if (s != 0.0) atomicAdd(&z[j], s);
   }
 }
@@ -514,44 +535,63 @@ __global__ void k_restrict_iface(const int *iface_nodes, const int *iface_of_nod
   }
 }
 
-// z on grain rows = X_g u[K_g]; warp per row
+// z on grain rows = X_g u[K_g]: one warp per 8 consecutive rows (lanes over the k_g columns, coalesced;
+// the 8 rows' loads issued together), the 8 partial sums reduced by a butterfly that halves the values per
+// lane at each of the first three levels (9 shuffles for 8 rows)
 template <typename T, typename A>
-__global__ void k_prolong_grain(const long long *node_off, const int *nloc, const int *lnodes, const int *kg,
-                                const long long *panel_off, const T *X, const int *gcol_off, const int *gcol,
-                                const double *u, double *z) {
-  // z rows of grain g = X_g u_g: one warp per row pair (lanes over the k_g columns, coalesced), the two
-  // rows' loads issued together
+__global__ void __launch_bounds__(256) k_prolong_grain(const long long *node_off, const int *nloc, const int *lnodes,
+                                                       const int *kg, const long long *panel_off, const T *X,
+                                                       const int *gcol_off, const int *gcol, const double *u,
+                                                       double *z) {
+  constexpr int R = 8;
   __shared__ A ul[512];
-  int g = blockIdx.y;
-  int k = kg[g];
+  const int g = blockIdx.y;
+  const int k = kg[g];
   for (int a = threadIdx.x; a < k; a += blockDim.x) ul[a] = (A)u[gcol[gcol_off[g] + a]];
   __syncthreads();
-  int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  int N = nloc[g];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int N = nloc[g];
   const T *Xg = X + panel_off[g];
   const int *ln = lnodes + node_off[g];
-  int nw = blockDim.x >> 5;
-  for (int row = 2 * (blockIdx.x * nw + wid); row < N; row += 2 * gridDim.x * nw) {
-    const bool two = row + 1 < N;
-    const T *xr = Xg + (long long)row * k;
-    const T *xs = two ? xr + k : xr;
-    A s = 0, s2 = 0;
+  const int nw = blockDim.x >> 5;
+  for (int row0 = R * (blockIdx.x * nw + wid); row0 < N; row0 += R * gridDim.x * nw) {
+    A acc[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) acc[r] = 0;
     for (int a = lane; a < k; a += 32) {
-      A ua = ul[a];
-      s += (A)xr[a] * ua;
-      s2 += (A)xs[a] * ua;
+      const A ua = ul[a];
+#pragma unroll
+      for (int r = 0; r < R; ++r)
+        if (row0 + r < N) acc[r] += (A)Xg[(long long)(row0 + r) * k + a] * ua;
     }
-    for (int o = 16; o > 0; o >>= 1) {
-      s += __shfl_down_sync(0xffffffffu, s, o);
-      s2 += __shfl_down_sync(0xffffffffu, s2, o);
+    // level xor 16: rows 0-3 stay on lanes with bit 4 clear, rows 4-7 on the others; then xor 8, xor 4
+#pragma unroll
+    for (int h = 0; h < 4; ++h) {
+      const bool up = lane & 16;
+      const A send = up ? acc[h] : acc[h + 4];
+      const A keep = up ? acc[h + 4] : acc[h];
+      acc[h] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
     }
-    if (lane == 0) {
-      int o = row / 3, d = row - 3 * o;
-      z[3LL * ln[o] + d] = (double)s;
-      if (two) {
-        int o2 = (row + 1) / 3, d2 = row + 1 - 3 * o2;
-        z[3LL * ln[o2] + d2] = (double)s2;
-      }
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const bool up = lane & 8;
+      const A send = up ? acc[h] : acc[h + 2];
+      const A keep = up ? acc[h + 2] : acc[h];
+      acc[h] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
+    }
+    {
+      const bool up = lane & 4;
+      const A send = up ? acc[0] : acc[1];
+      const A keep = up ? acc[1] : acc[0];
+      acc[0] = keep + __shfl_xor_sync(0xffffffffu, send, 4);
+    }
+    acc[0] += __shfl_xor_sync(0xffffffffu, acc[0], 2);
+    acc[0] += __shfl_xor_sync(0xffffffffu, acc[0], 1);
+    // lane l holds row 4 (bit 4) + 2 (bit 3) + (bit 2)
+    const int row = row0 + ((lane >> 4) & 1) * 4 + ((lane >> 3) & 1) * 2 + ((lane >> 2) & 1);
+    if ((lane & 3) == 0 && row < N) {
+      const int o = row / 3, d = row - 3 * o;
+      z[3LL * ln[o] + d] = (double)acc[0];
     }
   }
 }

@@ -235,6 +235,7 @@ struct hplmm_ctx {
   hp::Buf<double> V, Z, w_dots, w_h;
   int gmres_cap = 0;
   hp::Buf<double> w_partial;
+  hp::Buf<unsigned> w_ticket;      // last-block ticket of the Krylov reductions (zero between launches)
 
   // graph of the apply (options.use_graph): captured on a private stream from fixed work vectors
   cudaGraphExec_t apply_graph = nullptr;
