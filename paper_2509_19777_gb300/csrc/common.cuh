@@ -136,6 +136,7 @@ struct LocalSet {
   int tuned_chunk_rows = 0;  // smoother solve plan picked by the tuner (0 = default): far chunk rows,
   int tuned_ring_rows = 0;   // far ring rows (0 = largest that fits) and diagonal-chunk stages
   int tuned_c0_stages = 0;
+  int tuned_cluster = 0;     // CTAs per problem of the smoother solve (0 = default: 2 when the set is small)
   hplmm_prec prec = HPLMM_FP64;
 };
 

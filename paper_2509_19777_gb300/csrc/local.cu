@@ -1069,11 +1069,24 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
   return done != 0;
 }
 
+// the same with acquire semantics at cluster scope (phases completed by arrivals from the other CTA)
+__device__ __forceinline__ bool mbar_try_wait_cluster(uint64_t *bar, uint32_t parity) {
+  uint32_t done;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n"
+      " selp.b32 %0, 1, 0, p;\n}\n"
+      : "=r"(done)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return done != 0;
+}
+
 // bounded wait (about two seconds); gives up early when another warp has raised the abort flag
+template <bool CLUSTER = false>
 __device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity, const volatile int *abort_flag) {
   const long long t0 = clock64();
   for (long long it = 0;; ++it) {
-    if (mbar_try_wait(bar, parity)) return true;
+    if (CLUSTER ? mbar_try_wait_cluster(bar, parity) : mbar_try_wait(bar, parity)) return true;
     if ((it & 63) == 63) {
       if (abort_flag && *abort_flag) return false;
       if (clock64() - t0 > WAIT_CYCLES) return false;
@@ -1087,6 +1100,57 @@ __device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t by
           smem_u32(dst)),
       "l"(src), "r"(bytes), "r"(smem_u32(bar))
       : "memory");
+}
+
+// ---- two-CTA clusters: rank, shared-memory addresses in the other CTA, remote stores and arrivals
+__device__ __forceinline__ uint32_t cluster_rank() {
+  uint32_t r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+  return r;
+}
+__device__ __forceinline__ uint32_t peer_addr(const void *p, uint32_t rank) {
+  uint32_t a;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(a) : "r"(smem_u32(p)), "r"(rank));
+  return a;
+}
+__device__ __forceinline__ void st_peer(uint32_t addr, float v) {
+  asm volatile("st.shared::cluster.f32 [%0], %1;" ::"r"(addr), "f"(v) : "memory");
+}
+__device__ __forceinline__ void st_peer(uint32_t addr, double v) {
+  asm volatile("st.shared::cluster.f64 [%0], %1;" ::"r"(addr), "d"(v) : "memory");
+}
+__device__ __forceinline__ void st_peer_u32(uint32_t addr, uint32_t v) {
+  asm volatile("st.shared::cluster.u32 [%0], %1;" ::"r"(addr), "r"(v) : "memory");
+}
+// arrival on an mbarrier of the other CTA, releasing this thread's prior writes at cluster scope
+__device__ __forceinline__ void mbar_arrive_peer(uint32_t addr) {
+  asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(addr) : "memory");
+}
+// asynchronous store into the other CTA's shared memory that completes its bytes on an mbarrier there (the
+// sender does not wait; the receiver sees the value once the barrier phase completes)
+__device__ __forceinline__ void st_async_peer(uint32_t addr, float v, uint32_t bar) {
+  asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.f32 [%0], %1, [%2];" ::"r"(addr), "f"(v),
+               "r"(bar)
+               : "memory");
+}
+__device__ __forceinline__ void st_async_peer(uint32_t addr, double v, uint32_t bar) {
+  asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.f64 [%0], %1, [%2];" ::"r"(addr), "d"(v),
+               "r"(bar)
+               : "memory");
+}
+// every thread of both CTAs (not warp-aligned: the producer lanes may be diverged)
+__device__ __forceinline__ void cluster_sync_all() {
+  asm volatile("barrier.cluster.arrive.release;\n\tbarrier.cluster.wait.acquire;" ::: "memory");
+}
+// named barrier `id` over `nthreads` threads; returns the OR of `flag` over them
+__device__ __forceinline__ int bar_red_or(int id, int nthreads, int flag) {
+  int res;
+  asm volatile(
+      "{\n .reg .pred p, q;\n setp.ne.s32 p, %1, 0;\n bar.red.or.pred q, %2, %3, p;\n selp.s32 %0, 1, 0, q;\n}\n"
+      : "=r"(res)
+      : "r"(flag), "r"(id), "r"(nthreads)
+      : "memory");
+  return res;
 }
 
 // 16-byte group loads of a stored factor row, converted to the compute type
@@ -1147,7 +1211,7 @@ template <typename T, int n> __device__ __forceinline__ void ld_vec(const T *p, 
   }
 }
 
-template <typename S, int NB>
+template <typename S, int NB, int CL>
 __global__ void __launch_bounds__(WS_THREADS) k_band_solve_ws(
     int count, const int *nloc, const int *bwv, const long long *band_off, const long long *vec_off,
     const int *gidx, const S *band, const double *r, double *z, typename ComputeOf<S>::type *yscr, int atomic,
@@ -1163,12 +1227,21 @@ __global__ void __launch_bounds__(WS_THREADS) k_band_solve_ws(
   // step dependencies (rings of 4, event j on barrier j & 3): leader step done, first NB far rows of a bulk
   // step done (warp 0), bulk step done (every bulk warp)
   __shared__ __align__(8) uint64_t ydone[4], urg[4], bdone[4];
+  // two-CTA form: rank 1's finished partial sums pushed to rank 0 (forward: the rows of panel t+3 after its
+  // step t; backward: the far sums of the panel it processed), and rank 1's step-done barriers on rank 0
+  __shared__ __align__(8) uint64_t pdone[4];
+  __shared__ __align__(16) T v1push[5][NB];  // row 4: sink of steps with nothing to push
+  __shared__ T red1[4][NB];
+  // rank 1: bulk step done (every bulk warp) for its pusher warp, and its per-warp far sums (4 panels deep)
+  __shared__ __align__(8) uint64_t r1done[4];
+  __shared__ T red_r1[4][WS_BULK_WARPS][NB];
   __shared__ T red[2][WS_BULK_WARPS][NB];
   __shared__ __align__(16) T lbuf[NB];  // leader: the panel's right-hand side, broadcast to its lanes
   __shared__ volatile int s_abort;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  const int k = blockIdx.x;
-  if (k >= count) return;
+  const int rank = (CL == 2) ? (int)cluster_rank() : 0;
+  const int k = (CL == 2) ? (int)(blockIdx.x >> 1) : (int)blockIdx.x;
+  if (k >= count) return;  // the same for both CTAs of a cluster
   const int N = nloc[k];
   if (N == 0) return;
   const int bw = bwv[k];
@@ -1177,13 +1250,32 @@ __global__ void __launch_bounds__(WS_THREADS) k_band_solve_ws(
   const int W = wmask + 1;
   const PanelGeo geo{N, NB, RP};
   const S *B = band + band_off[k];
-  // far chunks: when a whole step's far rows (at most nf_int) fit twice in the ring, every step is one copy
-  // into a slot of nf_int rows (ring_eff a multiple of nf_int: no copy is split); otherwise chunks of
-  // chunk_rows rows packed back to back, a chunk that reaches the end of the ring split into two copies
+  // far rows of panel q: rank 0 takes [0, hsplit(q)), rank 1 [hsplit(q), nfar(q)).  Rank 1 gets rows only
+  // when the panel has at least 4 NB far rows, and never fewer than 2 NB go to rank 0, so that rank 1's
+  // updates reach rows at least 4 NB below their panel
+  auto hsplit = [&](int q) {
+    const int nf = geo.nfar(q);
+    return (CL == 1 || nf < 4 * NB) ? nf : max(2 * NB, (nf / 2) & ~7);
+  };
+  auto my_lo = [&](int q) { return rank == 0 ? 0 : hsplit(q); };
+  auto my_cnt = [&](int q) { return rank == 0 ? hsplit(q) : geo.nfar(q) - hsplit(q); };
+  // panel whose far rows this CTA's bulk warps process at step s: p-1, and p-2 for rank 1 in the backward
+  // sweep (its rows need only x values of panels p+2 and above, so it runs one panel ahead)
+  auto bulk_q = [&](int s) {
+    const bool fw = s < np;
+    const int pp = fw ? s : (2 * np - 1 - s);
+    return (rank == 1 && !fw) ? pp - 2 : pp - 1;
+  };
+  // far chunks: when a whole step's far rows of this CTA (at most slot_rows) fit twice in the ring, every step
+  // is one copy into a slot of slot_rows rows (ring_eff a multiple of slot_rows: no copy is split);
+  // otherwise chunks of chunk_rows rows packed back to back, a chunk that reaches the end of the ring split
+  // into two copies
   const int nf_int = max(0, RP - 2 * NB);
-  const bool whole = chunk_rows >= nf_int && nf_int > 0 && ring_rows >= 2 * nf_int;
-  const int ring_eff = whole ? (ring_rows / nf_int) * nf_int : ring_rows;
-  const int cr = whole ? nf_int : chunk_rows;
+  const int h_int = (CL == 1 || nf_int < 4 * NB) ? nf_int : max(2 * NB, (nf_int / 2) & ~7);
+  const int slot_rows = rank == 0 ? max(h_int, min(nf_int, 4 * NB - 1)) : min(nf_int, nf_int - h_int + 8);
+  const bool whole = chunk_rows >= slot_rows && slot_rows > 0 && ring_rows >= 2 * slot_rows;
+  const int ring_eff = whole ? (ring_rows / slot_rows) * slot_rows : ring_rows;
+  const int cr = whole ? slot_rows : chunk_rows;
   const int *gi = gidx + vec_off[k];
   T *ys = yscr + vec_off[k];
   S *ring = reinterpret_cast<S *>(smdyn);
@@ -1201,19 +1293,55 @@ __global__ void __launch_bounds__(WS_THREADS) k_band_solve_ws(
       mbar_init(&empty_c0[i], 1);
     }
     for (int i = 0; i < 4; ++i) {
+      // rank 0: the leader's local arrival; rank 1: its armer's arrival plus the leader's st.async bytes
       mbar_init(&ydone[i], 1);
       mbar_init(&urg[i], 1);
       mbar_init(&bdone[i], WS_BULK_WARPS);
+      mbar_init(&pdone[i], 1);                   // rank 0: its armer's arrival plus the pusher's st.async bytes
+      mbar_init(&r1done[i], WS_BULK_WARPS);
     }
     s_abort = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
-  // initial window: rows 0 .. min(W, N) - 1 of the right-hand side (slots of rows >= N are never read)
-  for (int l = threadIdx.x; l < min(W, N); l += WS_THREADS) v[l] = (T)r[gi[l]];
-  __syncthreads();
+  if (rank == 0) {
+    // initial window: rows 0 .. min(W, N) - 1 of the right-hand side (slots of rows >= N are never read)
+    for (int l = threadIdx.x; l < min(W, N); l += WS_THREADS) v[l] = (T)r[gi[l]];
+  } else {
+    for (int l = threadIdx.x; l < W; l += WS_THREADS) v[l] = (T)0;  // rank 1 accumulates its own updates
+  }
+  if constexpr (CL == 2)
+    cluster_sync_all();  // barriers initialised and windows set in both CTAs before any remote access
+  else
+    __syncthreads();
+  const uint32_t peer = (uint32_t)(rank ^ 1);
+  auto raise_abort = [&]() {
+    s_abort = 1;
+    if constexpr (CL == 2) st_peer_u32(peer_addr((const void *)&s_abort, peer), 1u);
+  };
 
   const int nsteps = 2 * np;
-  if (wid == 1) {
+  // two-CTA form: each step's exchange is NB values of T sent with st.async; the receiving CTA's armer
+  // arms the step's barrier with those bytes once the barrier's previous phase (4 steps earlier) completed,
+  // and finally waits for the last phases, so that no CTA exits with stores still arriving
+  constexpr uint32_t XBYTES = NB * sizeof(T);
+  auto armer = [&](uint64_t *bars) {
+    bool ok = true;
+    for (int j = 0; j < nsteps && ok; ++j) {
+      if (j >= 4 && !mbar_wait_bounded<true>(&bars[j & 3], (uint32_t)(((j - 4) >> 2) & 1), &s_abort)) ok = false;
+      if (ok) mbar_expect_tx(&bars[j & 3], XBYTES);
+    }
+    if (!ok) {
+      raise_abort();
+      atomicCAS(status, 0, (int)HPLMM_ERR_TIMEOUT);
+    }
+    for (int j = max(0, nsteps - 4); j < nsteps; ++j)
+      mbar_wait_bounded<true>(&bars[j & 3], (uint32_t)((j >> 2) & 1), nullptr);
+  };
+  if (CL == 2 && wid == 1 && lane == 1 && rank == 0) {
+    armer(pdone);
+  } else if (CL == 2 && wid == 2 && lane == 0 && rank == 1) {
+    armer(ydone);
+  } else if (wid == 1) {
     // ------------------------------------------------------------ producer
     // per step: the far rows of the bulk warps' panel
     if (lane == 0) {
@@ -1221,13 +1349,12 @@ __global__ void __launch_bounds__(WS_THREADS) k_band_solve_ws(
       int n = 0, rel = 0, abs_pos = 0;
       bool ok = true;
       for (int s = 0; s < nsteps && ok; ++s) {
-        const int p = (s < np) ? s : (2 * np - 1 - s);
-        const int q = p - 1;
+        const int q = bulk_q(s);
         if (q < 0) continue;
-        const int nf = geo.nfar(q);
+        const int nf = my_cnt(q), lo = my_lo(q);
         for (int r0 = 0; r0 < nf; r0 += cr) {
           const int rows = min(cr, nf - r0);
-          const int alloc = whole ? nf_int : rows;
+          const int alloc = whole ? slot_rows : rows;
           // release (in order) every chunk whose barrier pair or ring rows this chunk reuses
           while (rel < n && (rel <= n - WS_NSTG || start_tab[rel % WS_NSTG] < abs_pos + alloc - ring_eff)) {
             if (!mbar_wait_bounded(&empty_far[rel % WS_NSTG], (uint32_t)((rel / WS_NSTG) & 1), &s_abort)) {
@@ -1240,7 +1367,7 @@ __global__ void __launch_bounds__(WS_THREADS) k_band_solve_ws(
           const int slot = n % WS_NSTG;
           start_tab[slot] = abs_pos;
           const int pos = abs_pos % ring_eff;
-          const S *src = B + ((long long)q * RP + 2 * NB + r0) * NB;
+          const S *src = B + ((long long)q * RP + 2 * NB + lo + r0) * NB;
           const int first = min(rows, ring_eff - pos);
           mbar_expect_tx(&full_far[slot], (uint32_t)rows * (uint32_t)ROWB);
           bulk_g2s(ring + (size_t)pos * NB, src, (uint32_t)first * ROWB, &full_far[slot]);
@@ -1250,14 +1377,14 @@ __global__ void __launch_bounds__(WS_THREADS) k_band_solve_ws(
         }
       }
       if (!ok) {
-        s_abort = 1;
+        raise_abort();
         atomicCAS(status, 0, (int)HPLMM_ERR_TIMEOUT);
       }
       // let every copy still in flight land before shared memory is released (no-op when all were consumed)
       for (int m = max(rel, n - WS_NSTG); m < n; ++m)
         mbar_wait_bounded(&full_far[m % WS_NSTG], (uint32_t)((m / WS_NSTG) & 1), nullptr);
     }
-  } else if (wid == 2) {
+  } else if (wid == 2 && rank == 0) {
     // ------------------------------------------------------------ diagonal-chunk producer
     // per-thread 16-byte cp.async copies (the load/store path, leaving the bulk-copy engine to the far rows);
     // each lane's copies of a stage complete into the stage's full barrier (32 arrivals)
@@ -1265,7 +1392,7 @@ __global__ void __launch_bounds__(WS_THREADS) k_band_solve_ws(
       const int p = (s < np) ? s : (2 * np - 1 - s);
       const int slot = s % c0_stages;
       if (s >= c0_stages && !mbar_wait_bounded(&empty_c0[slot], (uint32_t)((s / c0_stages - 1) & 1), &s_abort)) {
-        s_abort = 1;
+        raise_abort();
         if (lane == 0) atomicCAS(status, 0, (int)HPLMM_ERR_TIMEOUT);
         break;
       }
@@ -1275,7 +1402,7 @@ __global__ void __launch_bounds__(WS_THREADS) k_band_solve_ws(
       asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(smem_u32(&full_c0[slot])) : "memory");
     }
     cp_async_wait_pending(0);
-  } else if (wid == 0) {
+  } else if (wid == 0 && rank == 0) {
     // ------------------------------------------------------------ leader: diagonal and near blocks
     const int i = lane % NB;
     const bool own = lane < NB;  // lanes that own row i of the panel (all lanes for NB = 32)
@@ -1298,12 +1425,21 @@ __global__ void __launch_bounds__(WS_THREADS) k_band_solve_ws(
       const int k0 = p * NB, nb = min(NB, N - k0);
       // forward: the rows of panel p are final once the first NB far rows of bulk step s-1 and all of bulk
       // step s-2 are done; backward: the far sums of panel p come from bulk step s-1
+      // two-CTA form: rank 1's part of panel p's rows (forward, pushed after its step s-3) or of panel p's far
+      // sums (backward, pushed after its step s-2)
       if (fwd) {
         if (s >= 1 && !mbar_wait_bounded(&urg[(s - 1) & 3], (uint32_t)(((s - 1) >> 2) & 1), &s_abort)) fail = 1;
         if (s >= 2 && !fail && !mbar_wait_bounded(&bdone[(s - 2) & 3], (uint32_t)(((s - 2) >> 2) & 1), &s_abort))
           fail = 1;
+        if (CL == 2 && p >= 3 && !fail &&
+            !mbar_wait_bounded<true>(&pdone[(s - 3) & 3], (uint32_t)(((s - 3) >> 2) & 1), &s_abort))
+          fail = 1;
       } else {
         if (!mbar_wait_bounded(&bdone[(s - 1) & 3], (uint32_t)(((s - 1) >> 2) & 1), &s_abort)) fail = 1;
+        // (waited at every backward step: each completed phase frees its barrier for the bytes 4 steps later)
+        if (CL == 2 && s >= 2 && !fail &&
+            !mbar_wait_bounded<true>(&pdone[(s - 2) & 3], (uint32_t)(((s - 2) >> 2) & 1), &s_abort))
+          fail = 1;
       }
       if (fwd && !fail) {
         if (p >= 3 && own && refill_row(p) < N) v[refill_row(p) & wmask] = (T)rv;
@@ -1317,7 +1453,9 @@ __global__ void __launch_bounds__(WS_THREADS) k_band_solve_ws(
         const S *c0 = c0_ring + (size_t)slot * 2 * NB * NB;
         if (fwd) {
           // y_p = inv(L_pp) x with x = v_p - near (row i of inv(L_pp) against x broadcast from shared memory)
-          const T x = (lane < nb) ? v[(k0 + lane) & wmask] - near : (T)0;
+          T vin = (lane < nb) ? v[(k0 + lane) & wmask] : (T)0;
+          if (CL == 2 && p >= 3 && lane < nb) vin += v1push[p & 3][i];
+          const T x = (lane < nb) ? vin - near : (T)0;
           if (own) lbuf[i] = x;
           __syncwarp();
           T a0 = 0, a1 = 0;
@@ -1333,6 +1471,7 @@ __global__ void __launch_bounds__(WS_THREADS) k_band_solve_ws(
           T y = (lane < nb) ? a0 + a1 : (T)0;
           if (own) {
             v[(k0 + i) & wmask] = y;  // read by the bulk warps at the next step and by the near product
+            if constexpr (CL == 2) st_async_peer(peer_addr(&v[(k0 + i) & wmask], 1), y, peer_addr(&ydone[s & 3], 1));
             if (lane < nb) ys[k0 + i] = y;
           }
           __syncwarp();
@@ -1370,6 +1509,7 @@ __global__ void __launch_bounds__(WS_THREADS) k_band_solve_ws(
 #pragma unroll
             for (int w = 0; w < WS_BULK_WARPS; ++w) far += red[p & 1][w][i];
           }
+          if (CL == 2 && p <= np - 3) far += red1[p & 3][i];
           // near: L_{p+1,p}^T x_{p+1} (column i of the near block; rows past the matrix contribute nothing)
           const int nrows = min(c0rows - NB, N - k0 - NB);
           T n0 = 0, n1 = 0;
@@ -1402,6 +1542,9 @@ __global__ void __launch_bounds__(WS_THREADS) k_band_solve_ws(
             for (int e = 0; e < ET; ++e) (e & 1 ? a1 : a0) += ld_elem(c0 + (g * ET + e) * NB + i) * tv[e];
           }
           const T x = a0 + a1;
+          // rank 1 receives a full panel every step (zeros past the matrix, in slots it never reads)
+          if (CL == 2 && own)
+            st_async_peer(peer_addr(&v[(k0 + i) & wmask], 1), lane < nb ? x : (T)0, peer_addr(&ydone[s & 3], 1));
           if (lane < nb) {
             v[(k0 + i) & wmask] = x;
             if (atomic)
@@ -1417,13 +1560,43 @@ __global__ void __launch_bounds__(WS_THREADS) k_band_solve_ws(
         }
       }
       if (fail) {
-        s_abort = 1;
+        raise_abort();
         if (lane == 0) atomicCAS(status, 0, (int)HPLMM_ERR_TIMEOUT);
         break;
       }
     }
-  } else {
-    // ------------------------------------------------------------ bulk: far rows of panel p-1
+  } else if (CL == 2 && wid == 0 && rank == 1) {
+    // ------------------------------------------------------------ rank 1: pusher
+    // after rank 1's bulk warps finished step s it pushes to rank 0 (forward: the rows of panel s+3, final
+    // now; backward: the far sums of panel q), clears the window slots of panel q (read as y_q for the last
+    // time) and releases the step, one arrival per lane; the bulk warps meanwhile go on with later steps
+    for (int s = 0; s < nsteps; ++s) {
+      if (!mbar_wait_bounded(&r1done[s & 3], (uint32_t)((s >> 2) & 1), &s_abort)) {
+        raise_abort();
+        if (lane == 0) atomicCAS(status, 0, (int)HPLMM_ERR_TIMEOUT);
+        break;
+      }
+      const int q = bulk_q(s);
+      // NB values every step (to the sink row when there is nothing to push)
+      const T *dst = &v1push[4][0];
+      T val = 0;
+      if (s < np) {
+        if (s + 3 < np) {
+          dst = &v1push[(s + 3) & 3][0];
+          val = lane < NB ? v[((s + 3) * NB + lane) & wmask] : (T)0;
+        }
+        if (q >= 0 && lane < NB) v[(q * NB + lane) & wmask] = (T)0;
+      } else if (q >= 0) {
+        dst = &red1[q & 3][0];
+        if (lane < NB) {
+#pragma unroll
+          for (int w = 0; w < WS_BULK_WARPS; ++w) val += red_r1[q & 3][w][lane];
+        }
+      }
+      if (lane < NB) st_async_peer(peer_addr(dst + lane, 0), val, peer_addr(&pdone[s & 3], 0));
+    }
+  } else if (wid >= 3) {
+    // ------------------------------------------------------------ bulk: far rows of panel bulk_q(s)
     const int bw_id = wid - 3;
     const int tb = threadIdx.x - 96;
     // rotation of this thread's group order: rows of 8 groups use (thread mod 8); rows of 4 groups use
@@ -1433,14 +1606,22 @@ __global__ void __launch_bounds__(WS_THREADS) k_band_solve_ws(
     int fail = 0;
     for (int s = 0; s < nsteps && !fail; ++s) {
       const bool fwd = s < np;
-      const int p = fwd ? s : (2 * np - 1 - s);
-      const int q = p - 1;
-      bool urgent_pending = (bw_id == 0);  // warp 0 owns far rows 0 .. 31, the next panel's rows
-      // y_{p-1} (forward) or x of the panels above (backward) come from leader step s-1
-      if (s >= 1 && !mbar_wait_bounded(&ydone[(s - 1) & 3], (uint32_t)(((s - 1) >> 2) & 1), &s_abort)) fail = 1;
+      const int q = bulk_q(s);
+      bool urgent_pending = (bw_id == 0 && rank == 0);  // rank 0's warp 0 owns far rows 0 .. 31
+      // y_q (forward) or the x values above panel q (backward) come from leader step s-1; rank 1 in the
+      // backward sweep needs only leader step s-2
+      {
+        const int dep = (rank == 1 && !fwd) ? s - 2 : s - 1;
+        if (dep >= 0) {
+          const bool okw = rank == 0
+                               ? mbar_wait_bounded(&ydone[dep & 3], (uint32_t)((dep >> 2) & 1), &s_abort)
+                               : mbar_wait_bounded<true>(&ydone[dep & 3], (uint32_t)((dep >> 2) & 1), &s_abort);
+          if (!okw) fail = 1;
+        }
+      }
       if (q >= 0 && !fail) {
         const int kq = q * NB;
-        const int nf = geo.nfar(q);
+        const int nf = my_cnt(q), lo = my_lo(q);
         T acc[NB];
         T yr[NB];
         if (fwd) {
@@ -1463,11 +1644,10 @@ __global__ void __launch_bounds__(WS_THREADS) k_band_solve_ws(
               int rs = pos + t, rs2 = pos + t2;
               if (rs >= ring_eff) rs -= ring_eff;
               if (rs2 >= ring_eff) rs2 -= ring_eff;
-              if (two && rs2 >= ring_rows) rs2 -= ring_rows;
               const S *row = ring + (size_t)rs * NB;
               const S *row2 = ring + (size_t)(two ? rs2 : rs) * NB;
-              const int vrow = (kq + 2 * NB + r0 + t) & wmask;
-              const int vrow2 = (kq + 2 * NB + r0 + t2) & wmask;
+              const int vrow = (kq + 2 * NB + lo + r0 + t) & wmask;
+              const int vrow2 = (kq + 2 * NB + lo + r0 + t2) & wmask;
               // forward updates use shared-memory atomics: consecutive bulk steps may overlap on a row
               if (fwd) {
                 if (two) {
@@ -1535,7 +1715,7 @@ __global__ void __launch_bounds__(WS_THREADS) k_band_solve_ws(
               urgent_pending = false;
             }
           }
-          pos += whole ? nf_int : rows;
+          pos += whole ? slot_rows : rows;
           if (pos >= ring_eff) pos -= ring_eff;
           ++n;
         }
@@ -1564,23 +1744,35 @@ __global__ void __launch_bounds__(WS_THREADS) k_band_solve_ws(
           const bool rep_lane = (G == 8) ? (lane < 8) : ((lane & 0x19) == 0);
           if (rep_lane) {
 #pragma unroll
-            for (int e = 0; e < E; ++e) red[q & 1][bw_id][cls * E + e] = tot[e];
+            for (int e = 0; e < E; ++e) {
+              if (rank == 0)
+                red[q & 1][bw_id][cls * E + e] = tot[e];
+              else
+                red_r1[q & 3][bw_id][cls * E + e] = tot[e];
+            }
           }
         }
       }
       if (fail) {
-        s_abort = 1;
+        raise_abort();
         if (lane == 0) atomicCAS(status, 0, (int)HPLMM_ERR_TIMEOUT);
         break;
       }
       __syncwarp();
       if (lane == 0) {
-        if (urgent_pending) mbar_arrive(&urg[s & 3]);  // no far rows in this step's first pass
-        mbar_arrive(&bdone[s & 3]);
+        if (rank == 0) {
+          if (urgent_pending) mbar_arrive(&urg[s & 3]);  // no far rows in this step's first pass
+          mbar_arrive(&bdone[s & 3]);
+        } else {
+          mbar_arrive(&r1done[s & 3]);
+        }
       }
     }
   }
-  __syncthreads();
+  if constexpr (CL == 2)
+    cluster_sync_all();  // no CTA leaves while its peer may still access its shared memory
+  else
+    __syncthreads();
 }
 
 template <typename T>
@@ -1909,8 +2101,30 @@ struct SolvePlan {
   int rowb, W;
   size_t c0_slot, vbytes;
 };
-constexpr size_t WS_SMEM_BUDGET = 224 * 1024;  // dynamic shared memory of one CTA per SM
-constexpr size_t WS_SMEM_PAIR = 108 * 1024;    // dynamic shared memory that lets two CTAs share an SM
+// dynamic shared-memory budgets of a smoother kernel: one CTA per SM (the opt-in maximum per block less the
+// kernel's static shared memory), or two CTAs per SM (half of the SM's shared memory, less the static part
+// and the per-block reservation)
+struct SmemBudget {
+  size_t one, pair;
+};
+template <typename K> static SmemBudget smem_budget(K kern) {
+  static std::mutex mu;
+  static std::map<const void *, SmemBudget> cache;
+  std::lock_guard<std::mutex> lk(mu);
+  auto it = cache.find((const void *)kern);
+  if (it != cache.end()) return it->second;
+  cudaFuncAttributes fa{};
+  HP_CUDA(cudaFuncGetAttributes(&fa, kern));
+  int dev = 0, optin = 0, per_sm = 0;
+  HP_CUDA(cudaGetDevice(&dev));
+  HP_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+  HP_CUDA(cudaDeviceGetAttribute(&per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev));
+  SmemBudget b;
+  b.one = (size_t)optin - fa.sharedSizeBytes - 256;
+  b.pair = (size_t)per_sm / 2 - fa.sharedSizeBytes - 1024 - 256;
+  cache[(const void *)kern] = b;
+  return b;
+}
 
 static SolvePlan solve_plan(const LocalSet &S) {
   const bool f64 = S.prec == HPLMM_FP64;
@@ -1939,31 +2153,63 @@ static int ring_rows_for(const SolvePlan &pl, int c0s, size_t budget) {
   return avail > 0 ? (int)((avail / pl.rowb) & ~7LL) : 0;
 }
 
+// CTAs per local problem: two (a cluster sharing each panel's far rows) when the set leaves at least half
+// of the SMs idle with one CTA per problem, else one; the tuner may override
+static int default_cluster(const LocalSet &S) { return 2 * S.count <= num_sms() ? 2 : 1; }
+
 void smoother_apply(hplmm_ctx *c, LocalSet &S, const double *r_pad, double *z_pad, bool atomic) {
   if (S.count == 0) return;
   ProfScope ps(c, (&S == &c->grains) ? HPLMM_PH_APPLY_GRAINS : HPLMM_PH_APPLY_CONTACTS);
   cudaStream_t s = c->stream;
   const SolvePlan pl = solve_plan(S);
-  // depths: the tuner's choice when there is one, else 3 diagonal stages, 64 KiB chunks and the largest ring
+  const int cl = S.tuned_cluster > 0 ? S.tuned_cluster : default_cluster(S);
+  // depths: the tuner's choice when there is one, else 3 diagonal stages, whole-step chunks and the largest
+  // ring
   const int c0s = S.tuned_c0_stages > 0 ? S.tuned_c0_stages : 3;
-  int ring = ring_rows_for(pl, c0s, WS_SMEM_BUDGET);
-  if (S.tuned_ring_rows > 0) ring = std::min(ring, S.tuned_ring_rows);
-  HP_REQUIRE(ring >= 64, HPLMM_ERR_INVALID,
-             "local problem too large for the smoother (window of " + std::to_string(pl.W) + " rows)");
-  const int chunk = std::min(ring, S.tuned_chunk_rows > 0 ? S.tuned_chunk_rows : chunk_choices(S).back());
-  const size_t smem = (size_t)ring * pl.rowb + (size_t)c0s * pl.c0_slot + pl.vbytes;
   auto go = [&](auto kern, const auto *band, auto *ys) {
+    const SmemBudget bud = smem_budget(kern);
+    int ring = ring_rows_for(pl, c0s, bud.one);
+    if (S.tuned_ring_rows > 0) ring = std::min(ring, S.tuned_ring_rows);
+    HP_REQUIRE(ring >= 64, HPLMM_ERR_INVALID,
+               "local problem too large for the smoother (window of " + std::to_string(pl.W) + " rows)");
+    const int chunk = std::min(ring, S.tuned_chunk_rows > 0 ? S.tuned_chunk_rows : chunk_choices(S).back());
+    const size_t smem = (size_t)ring * pl.rowb + (size_t)c0s * pl.c0_slot + pl.vbytes;
     HP_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    kern<<<S.count, WS_THREADS, smem, s>>>(S.count, S.n.p, S.bw.p, S.band_off.p, S.vec_off.p, S.gidx.p, band,
-                                           r_pad, z_pad, ys, atomic ? 1 : 0, ring, chunk, c0s, pl.W - 1,
-                                           c->status.p);
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)(S.count * cl));
+    cfg.blockDim = dim3(WS_THREADS);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = (unsigned)cl;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    HP_CUDA(cudaLaunchKernelEx(&cfg, kern, S.count, (const int *)S.n.p, (const int *)S.bw.p,
+                               (const long long *)S.band_off.p, (const long long *)S.vec_off.p,
+                               (const int *)S.gidx.p, band, (const double *)r_pad, z_pad, ys, atomic ? 1 : 0, ring,
+                               chunk, c0s, pl.W - 1, c->status.p));
   };
-  if (S.prec == HPLMM_FP64)
-    go(k_band_solve_ws<double, 16>, S.band64.p, S.yscr.p);
-  else if (S.apply_bf16)
-    go(k_band_solve_ws<__nv_bfloat16, 32>, S.band16.p, reinterpret_cast<float *>(S.yscr.p));
-  else
-    go(k_band_solve_ws<float, 32>, S.band32.p, reinterpret_cast<float *>(S.yscr.p));
+  if (S.prec == HPLMM_FP64) {
+    if (cl == 2)
+      go(k_band_solve_ws<double, 16, 2>, (const double *)S.band64.p, S.yscr.p);
+    else
+      go(k_band_solve_ws<double, 16, 1>, (const double *)S.band64.p, S.yscr.p);
+  } else if (S.apply_bf16) {
+    float *ys = reinterpret_cast<float *>(S.yscr.p);
+    if (cl == 2)
+      go(k_band_solve_ws<__nv_bfloat16, 32, 2>, (const __nv_bfloat16 *)S.band16.p, ys);
+    else
+      go(k_band_solve_ws<__nv_bfloat16, 32, 1>, (const __nv_bfloat16 *)S.band16.p, ys);
+  } else {
+    float *ys = reinterpret_cast<float *>(S.yscr.p);
+    if (cl == 2)
+      go(k_band_solve_ws<float, 32, 2>, (const float *)S.band32.p, ys);
+    else
+      go(k_band_solve_ws<float, 32, 1>, (const float *)S.band32.p, ys);
+  }
   HP_CHECK_LAUNCH();
 }
 
@@ -1981,13 +2227,13 @@ struct TuneKey {
 };
 std::mutex g_tune_mu;
 struct TuneChoice {
-  int chunk_rows, ring_rows, c0_stages;
+  int chunk_rows, ring_rows, c0_stages, cluster;
 };
 std::map<TuneKey, TuneChoice> g_tune_cache;
 }  // namespace
 
 static void tune_set(hplmm_ctx *c, LocalSet &S, bool atomic) {
-  S.tuned_chunk_rows = S.tuned_ring_rows = S.tuned_c0_stages = 0;
+  S.tuned_chunk_rows = S.tuned_ring_rows = S.tuned_c0_stages = S.tuned_cluster = 0;
   if (S.count == 0) return;
   TuneKey key{S.count, 0, 0, (int)S.prec + (S.apply_bf16 ? 8 : 0)};
   for (int k = 0; k < S.count; ++k) {
@@ -2001,6 +2247,7 @@ static void tune_set(hplmm_ctx *c, LocalSet &S, bool atomic) {
       S.tuned_chunk_rows = it->second.chunk_rows;
       S.tuned_ring_rows = it->second.ring_rows;
       S.tuned_c0_stages = it->second.c0_stages;
+      S.tuned_cluster = it->second.cluster;
       return;
     }
   }
@@ -2012,16 +2259,22 @@ static void tune_set(hplmm_ctx *c, LocalSet &S, bool atomic) {
   const bool prof = c->opt.profile;
   c->opt.profile = 0;  // tuning launches are not part of any phase
   float best = 1e30f;
-  TuneChoice bc{0, 0, 0};
-  for (int chunk : chunk_choices(S))
+  TuneChoice bc{0, 0, 0, 0};
+  // budgets of the FP32 one-CTA kernel (the static shared memory of every instantiation is about the same;
+  // smoother_apply clamps the ring to the launched kernel's own budget)
+  const SmemBudget bud = S.prec == HPLMM_FP64 ? smem_budget(k_band_solve_ws<double, 16, 1>)
+                                              : smem_budget(k_band_solve_ws<float, 32, 1>);
+  for (int cl : {1, 2})
+   for (int chunk : chunk_choices(S))
     for (int c0d = 2; c0d <= 4; ++c0d)
-      for (size_t budget : {WS_SMEM_BUDGET, WS_SMEM_PAIR}) {
+      for (size_t budget : {bud.one, bud.pair}) {
         const int ring = ring_rows_for(pl, c0d, budget);
         const int cr = std::min(chunk, ring);
         if (cr < 64) continue;
         S.tuned_chunk_rows = cr;
         S.tuned_ring_rows = ring;
         S.tuned_c0_stages = c0d;
+        S.tuned_cluster = cl;
         smoother_apply(c, S, c->b_pad.p, c->w_zz.p, atomic);  // warm-up
         HP_CUDA(cudaEventRecord(e0, s));
         for (int rep = 0; rep < 3; ++rep) smoother_apply(c, S, c->b_pad.p, c->w_zz.p, atomic);
@@ -2030,11 +2283,13 @@ static void tune_set(hplmm_ctx *c, LocalSet &S, bool atomic) {
         float ms = 0.f;
         HP_CUDA(cudaEventElapsedTime(&ms, e0, e1));
         if (c->opt.verbose)
-          fprintf(stderr, "[hplmm] tuner trial: %d problems, chunk %d rows, ring %d rows, diagonal %d: %.3f ms\n",
-                  S.count, cr, ring, c0d, ms / 3);
+          fprintf(stderr,
+                  "[hplmm] tuner trial: %d problems, %d CTA(s) each, chunk %d rows, ring %d rows, diagonal %d: "
+                  "%.3f ms\n",
+                  S.count, cl, cr, ring, c0d, ms / 3);
         if (ms < best) {
           best = ms;
-          bc = {cr, ring, c0d};
+          bc = {cr, ring, c0d, cl};
         }
       }
   c->opt.profile = prof;
@@ -2043,18 +2298,21 @@ static void tune_set(hplmm_ctx *c, LocalSet &S, bool atomic) {
   S.tuned_chunk_rows = bc.chunk_rows;
   S.tuned_ring_rows = bc.ring_rows;
   S.tuned_c0_stages = bc.c0_stages;
+  S.tuned_cluster = bc.cluster;
   if (c->opt.verbose)
     fprintf(stderr,
-            "[hplmm] tuner: %d problems (n<=%d, bw<=%d): chunk %d rows, ring %d rows, diagonal stages %d, %.3f ms\n",
-            S.count, key.nmax, key.bwmax, bc.chunk_rows, bc.ring_rows, bc.c0_stages, best / 3);
+            "[hplmm] tuner: %d problems (n<=%d, bw<=%d): %d CTA(s) each, chunk %d rows, ring %d rows, diagonal "
+            "stages %d, %.3f ms\n",
+            S.count, key.nmax, key.bwmax, bc.cluster, bc.chunk_rows, bc.ring_rows, bc.c0_stages, best / 3);
   std::lock_guard<std::mutex> lk(g_tune_mu);
   g_tune_cache[key] = bc;
 }
 
 void tune_local(hplmm_ctx *c) {
   if (!c->opt.autotune) {
-    c->grains.tuned_chunk_rows = c->grains.tuned_ring_rows = c->grains.tuned_c0_stages = 0;
+    c->grains.tuned_chunk_rows = c->grains.tuned_ring_rows = c->grains.tuned_c0_stages = c->grains.tuned_cluster = 0;
     c->contacts.tuned_chunk_rows = c->contacts.tuned_ring_rows = c->contacts.tuned_c0_stages = 0;
+    c->contacts.tuned_cluster = 0;
     return;
   }
   tune_set(c, c->contacts, true);
