@@ -1058,13 +1058,16 @@ __device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
 
-// potentially suspending probe of a phase (returns after the phase completed or a hardware time limit)
+// potentially suspending probe of a phase: the thread sleeps until the phase completes or about
+// MBAR_SUSPEND_NS nanoseconds pass, so that waiting warps leave their scheduler's issue slots to the warps
+// that compute
+constexpr uint32_t MBAR_SUSPEND_NS = 20000;
 __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
   uint32_t done;
   asm volatile(
-      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.b32 %0, 1, 0, p;\n}\n"
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n selp.b32 %0, 1, 0, p;\n}\n"
       : "=r"(done)
-      : "r"(smem_u32(bar)), "r"(parity)
+      : "r"(smem_u32(bar)), "r"(parity), "r"(MBAR_SUSPEND_NS)
       : "memory");
   return done != 0;
 }
@@ -1073,10 +1076,10 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
 __device__ __forceinline__ bool mbar_try_wait_cluster(uint64_t *bar, uint32_t parity) {
   uint32_t done;
   asm volatile(
-      "{\n .reg .pred p;\n mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n"
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2, %3;\n"
       " selp.b32 %0, 1, 0, p;\n}\n"
       : "=r"(done)
-      : "r"(smem_u32(bar)), "r"(parity)
+      : "r"(smem_u32(bar)), "r"(parity), "r"(MBAR_SUSPEND_NS)
       : "memory");
   return done != 0;
 }
@@ -1087,7 +1090,7 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity
   const long long t0 = clock64();
   for (long long it = 0;; ++it) {
     if (CLUSTER ? mbar_try_wait_cluster(bar, parity) : mbar_try_wait(bar, parity)) return true;
-    if ((it & 63) == 63) {
+    if ((it & 3) == 3) {
       if (abort_flag && *abort_flag) return false;
       if (clock64() - t0 > WAIT_CYCLES) return false;
     }
@@ -1637,10 +1640,13 @@ __global__ void __launch_bounds__(WS_THREADS) k_band_solve_ws(
           const int slot = n % WS_NSTG;
           if (!fail && !mbar_wait_bounded(&full_far[slot], (uint32_t)((n / WS_NSTG) & 1), &s_abort)) fail = 1;
           if (!fail) {
-            // two rows per thread per pass (t and t + WS_BULK_THREADS)
+            // two rows per thread per pass (t and t + WS_BULK_THREADS); the choice between the one- and the
+            // two-row code is made per warp (a lane without a second row re-reads its first row, with no
+            // update or a zero weight), so that no warp runs both
             for (int t = tb; t < rows; t += 2 * WS_BULK_THREADS) {
               const int t2 = t + WS_BULK_THREADS;
               const bool two = t2 < rows;
+              const bool warp_two = __any_sync(__activemask(), two);
               int rs = pos + t, rs2 = pos + t2;
               if (rs >= ring_eff) rs -= ring_eff;
               if (rs2 >= ring_eff) rs2 -= ring_eff;
@@ -1650,7 +1656,7 @@ __global__ void __launch_bounds__(WS_THREADS) k_band_solve_ws(
               const int vrow2 = (kq + 2 * NB + lo + r0 + t2) & wmask;
               // forward updates use shared-memory atomics: consecutive bulk steps may overlap on a row
               if (fwd) {
-                if (two) {
+                if (warp_two) {
                   T s0 = 0, s1 = 0, s2 = 0, s3 = 0;
 #pragma unroll
                   for (int g = 0; g < G; g += 2) {
@@ -1668,7 +1674,7 @@ __global__ void __launch_bounds__(WS_THREADS) k_band_solve_ws(
                     }
                   }
                   atomicAdd(&v[vrow], -(s0 + s1));
-                  atomicAdd(&v[vrow2], -(s2 + s3));
+                  if (two) atomicAdd(&v[vrow2], -(s2 + s3));
                 } else {
                   T s0 = 0, s1 = 0;
 #pragma unroll
@@ -1686,8 +1692,8 @@ __global__ void __launch_bounds__(WS_THREADS) k_band_solve_ws(
                 }
               } else {
                 const T xv = v[vrow];
-                if (two) {
-                  const T xv2 = v[vrow2];
+                if (warp_two) {
+                  const T xv2 = two ? v[vrow2] : (T)0;
 #pragma unroll
                   for (int g = 0; g < G; ++g) {
                     T ra[E], rc[E];
