@@ -76,6 +76,9 @@ typedef struct {
   double basis_tol;      /* relative residual of the iterative basis solves (default 1e-6) */
   int basis_max_iters;   /* iteration cap of the iterative basis solves (default 3000) */
   int keep_basis_rhs;    /* 1: keep a copy of the basis right-hand sides after set-up (hplmm_ws_collect) */
+  int smoother_ctas;     /* CTAs per local problem in the smoother solves: 0 (default) the tuner's choice, or
+                            two for a set with at most half as many problems as the GPU has SMs, else one;
+                            1 or 2 force it (two: a cluster that splits each panel's far rows) */
 } hplmm_options;
 
 enum { HPLMM_BASIS_DIRECT = 0, HPLMM_BASIS_PCG = 1, HPLMM_BASIS_PCG_WARM = 2 };

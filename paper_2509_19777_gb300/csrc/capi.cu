@@ -84,6 +84,7 @@ void validate_options(const hplmm_options &o) {
              "the iterative basis solves run in FP32: they need local_prec = FP32");
   HP_REQUIRE(o.basis_tol > 0.0 && o.basis_tol < 1.0, HPLMM_ERR_INVALID, "basis_tol must lie in (0, 1)");
   HP_REQUIRE(o.basis_max_iters >= 1, HPLMM_ERR_INVALID, "basis_max_iters must be positive");
+  HP_REQUIRE(o.smoother_ctas >= 0 && o.smoother_ctas <= 2, HPLMM_ERR_INVALID, "smoother_ctas must be 0, 1 or 2");
 }
 
 void require_setup(hplmm_ctx *c) {
@@ -133,6 +134,7 @@ void hplmm_default_options(hplmm_options *o) {
   o->basis_tol = 1e-6;
   o->basis_max_iters = 3000;
   o->keep_basis_rhs = 0;
+  o->smoother_ctas = 0;
 }
 
 hplmm_status hplmm_create(hplmm_ctx **ctx, const hplmm_options *opt, void *cuda_stream) {

@@ -2168,7 +2168,8 @@ void smoother_apply(hplmm_ctx *c, LocalSet &S, const double *r_pad, double *z_pa
   ProfScope ps(c, (&S == &c->grains) ? HPLMM_PH_APPLY_GRAINS : HPLMM_PH_APPLY_CONTACTS);
   cudaStream_t s = c->stream;
   const SolvePlan pl = solve_plan(S);
-  const int cl = S.tuned_cluster > 0 ? S.tuned_cluster : default_cluster(S);
+  const int cl = c->opt.smoother_ctas > 0 ? c->opt.smoother_ctas
+                 : (S.tuned_cluster > 0 ? S.tuned_cluster : default_cluster(S));
   // depths: the tuner's choice when there is one, else 3 diagonal stages, whole-step chunks and the largest
   // ring
   const int c0s = S.tuned_c0_stages > 0 ? S.tuned_c0_stages : 3;
@@ -2241,7 +2242,7 @@ std::map<TuneKey, TuneChoice> g_tune_cache;
 static void tune_set(hplmm_ctx *c, LocalSet &S, bool atomic) {
   S.tuned_chunk_rows = S.tuned_ring_rows = S.tuned_c0_stages = S.tuned_cluster = 0;
   if (S.count == 0) return;
-  TuneKey key{S.count, 0, 0, (int)S.prec + (S.apply_bf16 ? 8 : 0)};
+  TuneKey key{S.count, 0, 0, (int)S.prec + (S.apply_bf16 ? 8 : 0) + 16 * c->opt.smoother_ctas};
   for (int k = 0; k < S.count; ++k) {
     key.nmax = std::max(key.nmax, S.h_n[k]);
     key.bwmax = std::max(key.bwmax, S.h_bw[k]);
@@ -2272,6 +2273,7 @@ static void tune_set(hplmm_ctx *c, LocalSet &S, bool atomic) {
                                               : smem_budget(k_band_solve_ws<float, 32, 1>);
   for (int cl : {1, 2})
    for (int chunk : chunk_choices(S))
+    if (c->opt.smoother_ctas == 0 || c->opt.smoother_ctas == cl)
     for (int c0d = 2; c0d <= 4; ++c0d)
       for (size_t budget : {bud.one, bud.pair}) {
         const int ring = ring_rows_for(pl, c0d, budget);

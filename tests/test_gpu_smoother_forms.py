@@ -1,0 +1,87 @@
+"""GPU: the two forms of the smoother solve (one CTA per local problem, or a two-CTA
+cluster that splits each panel's far rows) and the Krylov kernels over the whole range of
+basis sizes, through the C interface, against each other and the FP64 CPU oracle.
+
+Bars: M_CG^{-1} r of the two forms agrees to the rounding of the form's precision (FP64:
+1e-12 relative, only the order of additions differs; FP32: 1e-5; BF16 storage: 1e-3) and
+matches the oracle's (FP64 form: 1e-10; FP32: 5e-3, the FP32 unit roundoff 6e-8 amplified by
+local condition numbers of a few 1e4 on the heterogeneous porous grains, measured 1.3e-3;
+BF16: 0.2 as for the whole apply); FGMRES with restart lengths that
+take the basis past 32 vectors (the largest register block and the generic update) reaches
+the FP64 true residual and the oracle's solution.
+"""
+import numpy as np
+import pytest
+
+from tests._cases import gpu_solver, oracle_case, oracle_solution, rel
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+def _t(x):
+    return torch.from_numpy(np.ascontiguousarray(x, dtype=np.float64)).cuda()
+
+
+def _n(t):
+    return t.detach().cpu().numpy()
+
+
+FORMS = [
+    (dict(local_prec="fp64", apply_prec="fp64"), 1e-12, 1e-10),
+    (dict(local_prec="fp32", apply_prec="fp32"), 1e-5, 5e-3),
+    (dict(local_prec="fp32", apply_prec="bf16"), 1e-3, 0.2),
+]
+
+
+@pytest.mark.parametrize("name", ["cube16_n4", "porous32_n4", "tiny10_strict"])
+@pytest.mark.parametrize("form,tol_forms,tol_oracle", FORMS)
+def test_one_and_two_cta_smoothers_agree(name, form, tol_forms, tol_oracle):
+    p, opt, sysm, M = oracle_case(name)
+    rng = np.random.default_rng(17)
+    r = rng.standard_normal(sysm.n_dof)
+    z_ref = M.smoother.apply(r)
+    out = {}
+    for ctas in (1, 2):
+        s = gpu_solver(name, smoother_ctas=ctas, **form)
+        out[ctas] = _n(s.apply_smoother(_t(r)))
+        s.close()
+    assert rel(out[2], out[1]) < tol_forms
+    for ctas in (1, 2):
+        assert rel(out[ctas], z_ref) < tol_oracle, ctas
+
+
+@pytest.mark.parametrize("ctas", [1, 2])
+def test_two_cta_solve_matches_oracle(ctas):
+    name = "porous32_n4"
+    x_ref, _ = oracle_solution(name)
+    p, opt, sysm, M = oracle_case(name)
+    s = gpu_solver(name, smoother_ctas=ctas, local_prec="fp32", apply_prec="fp32", use_graph=True)
+    x, rc, st = s.solve(tol=1e-8)
+    xn = _n(x)
+    assert rc == 0
+    assert np.linalg.norm(sysm.b - sysm.A @ xn) / np.linalg.norm(sysm.b) <= 1e-8
+    assert rel(xn, x_ref) < 1e-6
+    s.close()
+
+
+@pytest.mark.parametrize("restart", [3, 12, 45])
+def test_krylov_basis_sizes(restart):
+    # restart 45 builds bases of up to 46 vectors: every register block of the CGS2 kernels (1 .. 32) and,
+    # past 32, the generic update followed by the 64-wide dot product
+    name = "cube16_n4"
+    x_ref, _ = oracle_solution(name)
+    p, opt, sysm, M = oracle_case(name)
+    s = gpu_solver(name, restart=restart)
+    x, rc, st = s.solve(tol=1e-11)
+    xn = _n(x)
+    assert rc == 0
+    assert np.linalg.norm(sysm.b - sysm.A @ xn) / np.linalg.norm(sysm.b) <= 1e-11
+    assert rel(xn, x_ref) < 1e-8
+    s.close()
+
+
+def test_smoother_ctas_validated():
+    import paper_2509_19777_gb300 as hp
+    with pytest.raises(hp.HplmmError):
+        hp.Solver(smoother_ctas=3)
