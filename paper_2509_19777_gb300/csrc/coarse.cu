@@ -240,84 +240,137 @@ __global__ void k_symmetrize(double *A, long long N, double *asym) {
 // ---------------------------------------------------------------- dense FP64 Cholesky (64x64 tiles)
 constexpr int TB = 64;
 
-__global__ void k_potrf_tile(double *A, long long N, int kt, double *Dinv, int *status) {
-  __shared__ double L[TB][TB + 1];
-  __shared__ double W[TB][TB + 1];
-  __shared__ double rdiag[TB];  // reciprocals of the factor's diagonal (one division per column)
-  int k0 = kt * TB;
-  int nb = (int)min((long long)TB, N - k0);
-  for (int e = threadIdx.x; e < TB * TB; e += blockDim.x) {
-    int r = e / TB, c = e % TB;
-    L[r][c] = (r < nb && c < nb && c <= r) ? A[(long long)(k0 + r) * N + k0 + c] : (r == c ? 1.0 : 0.0);
+// Diagonal tile: Cholesky factor L_kk and its inverse, one CTA of 256 threads.  Thread t keeps the 16
+// elements (r, c) with c = t mod 64, r = t / 64 + 4 u (u = 0 .. 15) in registers through both phases:
+//   factor (right-looking, one column per step): the owner of (cc, cc) takes the square root, the owners of
+//   column cc scale it and publish it, every thread updates its elements right of cc;
+//   inverse W = L^{-1} (row by row): the owners of row q scale it by 1/L_qq and publish it, every thread
+//   subtracts L_rq W_q from its rows r > q.
+// The tile's padding rows and columns (past N) are the identity, so the steps stay well defined.
+__global__ void __launch_bounds__(256) k_potrf_tile(double *A, long long N, int kt, double *Dinv, int *status) {
+  __shared__ double colv[TB];
+  __shared__ double rdiag[TB];
+  __shared__ double Ls[TB][TB + 1];
+  __shared__ double wrow[2][TB];
+  const int t = threadIdx.x;
+  const int c = t & (TB - 1), r0 = t >> 6;
+  const int k0 = kt * TB;
+  const int nb = (int)min((long long)TB, N - k0);
+  double a[16];
+#pragma unroll
+  for (int u = 0; u < 16; ++u) {
+    const int r = r0 + 4 * u;
+    a[u] = (r < nb && c < nb && c <= r) ? A[(long long)(k0 + r) * N + k0 + c] : (r == c ? 1.0 : 0.0);
   }
-  __syncthreads();
-  for (int c = 0; c < nb; ++c) {
-    if (threadIdx.x == 0) {
-      double d = L[c][c];
+  for (int cc = 0; cc < TB; ++cc) {
+    if (c == cc && (cc & 3) == r0) {
+      const int uc = cc >> 2;
+      double d = 0.0;
+#pragma unroll
+      for (int u = 0; u < 16; ++u) d = (u == uc) ? a[u] : d;
       if (!(d > 0.0)) {
         if (atomicCAS(status, 0, (int)HPLMM_ERR_SINGULAR) == 0) {
           status[1] = 3;
           status[2] = 0;
-          status[3] = k0 + c;
+          status[3] = k0 + cc;
         }
         d = 1.0;
       }
       const double sd = sqrt(d);
-      L[c][c] = sd;
-      rdiag[c] = 1.0 / sd;
+#pragma unroll
+      for (int u = 0; u < 16; ++u) a[u] = (u == uc) ? sd : a[u];
+      rdiag[cc] = 1.0 / sd;
     }
     __syncthreads();
-    for (int r = c + 1 + threadIdx.x; r < nb; r += blockDim.x) L[r][c] *= rdiag[c];
-    __syncthreads();
-    for (int e = threadIdx.x; e < TB * TB; e += blockDim.x) {
-      int r = e / TB, c2 = e % TB;
-      if (r > c && c2 > c && c2 <= r && r < nb) L[r][c2] -= L[r][c] * L[c2][c];
-    }
-    __syncthreads();
-  }
-  for (int i = nb + threadIdx.x; i < TB; i += blockDim.x) rdiag[i] = 1.0;  // identity padding rows
-  __syncthreads();
-  // inverse of the lower factor block, column j by thread j
-  if (threadIdx.x < TB) {
-    int j = threadIdx.x;
-    for (int i = 0; i < TB; ++i) {
-      double v;
-      if (i < j) {
-        v = 0.0;
-      } else {
-        double s = (i == j) ? 1.0 : 0.0;
-        for (int q = j; q < i; ++q) s -= L[i][q] * W[q][j];
-        v = s * rdiag[i];
+    if (c == cc) {
+      const double rd = rdiag[cc];
+#pragma unroll
+      for (int u = 0; u < 16; ++u) {
+        const int r = r0 + 4 * u;
+        if (r > cc) {
+          a[u] *= rd;
+          colv[r] = a[u];
+        }
       }
-      W[i][j] = v;
+    }
+    __syncthreads();
+    if (c > cc) {
+      const double vc = colv[c];
+#pragma unroll
+      for (int u = 0; u < 16; ++u) {
+        const int r = r0 + 4 * u;
+        if (r >= c) a[u] -= colv[r] * vc;
+      }
     }
   }
+  // factor to the matrix and to shared memory (the inverse reads its columns)
+#pragma unroll
+  for (int u = 0; u < 16; ++u) {
+    const int r = r0 + 4 * u;
+    Ls[r][c] = (c <= r) ? a[u] : 0.0;
+    if (r < nb && c < nb) A[(long long)(k0 + r) * N + k0 + c] = (c <= r) ? a[u] : 0.0;
+  }
   __syncthreads();
-  for (int e = threadIdx.x; e < TB * TB; e += blockDim.x) {
-    int r = e / TB, c = e % TB;
-    if (r < nb && c < nb) A[(long long)(k0 + r) * N + k0 + c] = (c <= r) ? L[r][c] : 0.0;
-    Dinv[(long long)kt * TB * TB + e] = (r < nb && c < nb) ? W[r][c] : 0.0;
+  double w[16];
+#pragma unroll
+  for (int u = 0; u < 16; ++u) w[u] = (r0 + 4 * u == c) ? 1.0 : 0.0;
+  for (int q = 0; q < TB; ++q) {
+    if ((q & 3) == r0) {
+      const double rd = rdiag[q];
+      const int uq = q >> 2;
+      double wv = 0.0;
+#pragma unroll
+      for (int u = 0; u < 16; ++u) {
+        w[u] = (u == uq) ? w[u] * rd : w[u];
+        wv = (u == uq) ? w[u] : wv;
+      }
+      wrow[q & 1][c] = wv;
+    }
+    __syncthreads();
+    if (c <= q) {
+      const double wq = wrow[q & 1][c];
+#pragma unroll
+      for (int u = 0; u < 16; ++u) {
+        const int r = r0 + 4 * u;
+        if (r > q) w[u] -= Ls[r][q] * wq;
+      }
+    }
+  }
+  // padding rows of the factor are identity rows, so rdiag is 1 there and W stays the identity
+#pragma unroll
+  for (int u = 0; u < 16; ++u) {
+    const int r = r0 + 4 * u;
+    Dinv[(long long)kt * TB * TB + r * TB + c] = (r < nb && c < nb) ? w[u] : 0.0;
   }
 }
 
-// A[it][kt] <- A[it][kt] * inv(L_kk)^T for it > kt
-__global__ void k_trsm_tiles(double *A, long long N, int kt, const double *Dinv) {
+// A[it][kt] <- A[it][kt] * inv(L_kk)^T for it > kt; CTA (tile, slice of 16 rows): the tiles of a step are
+// few, so each is split over 4 CTAs (the FP64 pipe of one SM is the limit)
+__global__ void __launch_bounds__(256) k_trsm_tiles(double *A, long long N, int kt, const double *Dinv) {
   __shared__ double Di[TB][TB + 1];
-  __shared__ double Bt[TB][TB + 1];
-  int it = kt + 1 + blockIdx.x;
-  int k0 = kt * TB, i0 = it * TB;
-  int nbk = (int)min((long long)TB, N - k0), nbi = (int)min((long long)TB, N - i0);
+  __shared__ double Bt[16][TB + 1];
+  const int it = kt + 1 + blockIdx.x, rs = 16 * blockIdx.y;
+  const int k0 = kt * TB, i0 = it * TB;
+  const int nbk = (int)min((long long)TB, N - k0), nbi = (int)min((long long)TB, N - i0);
   for (int e = threadIdx.x; e < TB * TB; e += blockDim.x) {
-    int r = e / TB, c = e % TB;
+    const int r = e / TB, c = e % TB;
     Di[r][c] = Dinv[(long long)kt * TB * TB + e];
-    Bt[r][c] = (r < nbi && c < nbk) ? A[(long long)(i0 + r) * N + k0 + c] : 0.0;
+  }
+  for (int e = threadIdx.x; e < 16 * TB; e += blockDim.x) {
+    const int r = e / TB, c = e % TB;
+    Bt[r][c] = (rs + r < nbi && c < nbk) ? A[(long long)(i0 + rs + r) * N + k0 + c] : 0.0;
   }
   __syncthreads();
-  for (int e = threadIdx.x; e < TB * TB; e += blockDim.x) {
-    int r = e / TB, c = e % TB;
-    double s = 0.0;
-    for (int q = 0; q <= c; ++q) s += Bt[r][q] * Di[c][q];
-    if (r < nbi && c < nbk) A[(long long)(i0 + r) * N + k0 + c] = s;
+  for (int e = threadIdx.x; e < 16 * TB; e += blockDim.x) {
+    const int r = e / TB, c = e % TB;
+    double s0 = 0.0, s1 = 0.0;
+    int q = 0;
+    for (; q + 1 <= c; q += 2) {
+      s0 += Bt[r][q] * Di[c][q];
+      s1 += Bt[r][q + 1] * Di[c][q + 1];
+    }
+    if (q <= c) s0 += Bt[r][q] * Di[c][q];
+    if (rs + r < nbi && c < nbk) A[(long long)(i0 + rs + r) * N + k0 + c] = s0 + s1;
   }
 }
 
@@ -369,34 +422,34 @@ __global__ void k_eye(double *Y, long long N) {
   if (i < N) Y[i * N + i] = 1.0;
 }
 
-__global__ void k_trinv_scale(double *Y, long long N, int kt, const double *Dinv) {
-  __shared__ double D[TB][TB + 1];
+// Y[kt][jt] <- inv(L_kk) Y[kt][jt] for jt <= kt; CTA (column tile, slice of 16 rows), thread = 1 x 4 outputs
+__global__ void __launch_bounds__(256) k_trinv_scale(double *Y, long long N, int kt, const double *Dinv) {
+  __shared__ double D[16][TB + 1];
   __shared__ double Bt[TB][TB + 1];
-  int jt = blockIdx.x;  // 0..kt
-  int k0 = kt * TB, j0 = jt * TB;
-  int nbk = (int)min((long long)TB, N - k0), nbj = (int)min((long long)TB, N - j0);
+  const int jt = blockIdx.x, rs = 16 * blockIdx.y;
+  const int k0 = kt * TB, j0 = jt * TB;
+  const int nbk = (int)min((long long)TB, N - k0), nbj = (int)min((long long)TB, N - j0);
+  for (int e = threadIdx.x; e < 16 * TB; e += blockDim.x) {
+    const int r = e / TB, c = e % TB;
+    D[r][c] = Dinv[(long long)kt * TB * TB + (long long)(rs + r) * TB + c];
+  }
   for (int e = threadIdx.x; e < TB * TB; e += blockDim.x) {
-    int r = e / TB, c = e % TB;
-    D[r][c] = Dinv[(long long)kt * TB * TB + e];
+    const int r = e / TB, c = e % TB;
     Bt[r][c] = (r < nbk && c < nbj) ? Y[(long long)(k0 + r) * N + j0 + c] : 0.0;
   }
   __syncthreads();
-  int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
-  double acc[4][4] = {};
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  double acc[4] = {0.0, 0.0, 0.0, 0.0};
   for (int q = 0; q < TB; ++q) {
-    double a[4], b[4];
-    for (int u = 0; u < 4; ++u) {
-      a[u] = D[ty + 16 * u][q];
-      b[u] = Bt[q][tx + 16 * u];
-    }
-    for (int u = 0; u < 4; ++u)
-      for (int v = 0; v < 4; ++v) acc[u][v] += a[u] * b[v];
+    const double a = D[ty][q];
+#pragma unroll
+    for (int v = 0; v < 4; ++v) acc[v] += a * Bt[q][tx + 16 * v];
   }
-  for (int u = 0; u < 4; ++u)
-    for (int v = 0; v < 4; ++v) {
-      int r = ty + 16 * u, c = tx + 16 * v;
-      if (r < nbk && c < nbj) Y[(long long)(k0 + r) * N + j0 + c] = acc[u][v];
-    }
+#pragma unroll
+  for (int v = 0; v < 4; ++v) {
+    const int r = rs + ty, c = tx + 16 * v;
+    if (r < nbk && c < nbj) Y[(long long)(k0 + r) * N + j0 + c] = acc[v];
+  }
 }
 
 // Y[it][jt] -= L[it][kt] Y[kt][jt] for it > kt, jt <= kt
@@ -807,31 +860,39 @@ void build_coarse(hplmm_ctx *c, const double *b_corr) {
     HP_CUDA(cudaMemcpyAsync(c->Lo.p, c->Ao.p, sizeof(double) * No * No, cudaMemcpyDeviceToDevice, s));
     int T = (int)((No + TB - 1) / TB);
     c->Lo_dinv.alloc((size_t)T * TB * TB);
+    // explicit inverse factor Y = L^{-1} (FP64), so that each apply is two parallel triangular products.  Its
+    // step kt needs only the factor's block column kt, so it runs on the second stream behind the Cholesky:
+    // after the column is final (diagonal tile and the tiles below) the Cholesky's trailing update and the
+    // inverse's step share the GPU.  One event, recorded once per step, orders the two streams.
+    c->Linv.alloc(No * No);
+    c->Linv.zero(s);
+    k_eye<<<grid_for(No, 256), 256, 0, s>>>(c->Linv.p, No);
+    HP_CHECK_LAUNCH();
+    if (!c->aux_stream) HP_CUDA(cudaStreamCreateWithFlags(&c->aux_stream, cudaStreamNonBlocking));
+    if (!c->ev_fork) HP_CUDA(cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming));
+    if (!c->ev_join) HP_CUDA(cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming));
+    cudaStream_t s2 = c->aux_stream;
     for (int kt = 0; kt < T; ++kt) {
       k_potrf_tile<<<1, 256, 0, s>>>(c->Lo.p, No, kt, c->Lo_dinv.p, c->status.p);
       HP_CHECK_LAUNCH();
       int m = T - kt - 1;
       if (m > 0) {
-        k_trsm_tiles<<<m, 256, 0, s>>>(c->Lo.p, No, kt, c->Lo_dinv.p);
+        k_trsm_tiles<<<dim3(m, 4), 256, 0, s>>>(c->Lo.p, No, kt, c->Lo_dinv.p);
+        HP_CHECK_LAUNCH();
+      }
+      HP_CUDA(cudaEventRecord(c->ev_fork, s));
+      HP_CUDA(cudaStreamWaitEvent(s2, c->ev_fork, 0));
+      k_trinv_scale<<<dim3(kt + 1, 4), 256, 0, s2>>>(c->Linv.p, No, kt, c->Lo_dinv.p);
+      HP_CHECK_LAUNCH();
+      if (m > 0) {
+        k_trinv_update<<<m * (kt + 1), 256, 0, s2>>>(c->Linv.p, c->Lo.p, No, kt, T);
         HP_CHECK_LAUNCH();
         k_syrk_tiles<<<m * (m + 1) / 2, 256, 0, s>>>(c->Lo.p, No, kt, T);
         HP_CHECK_LAUNCH();
       }
     }
-    // explicit inverse factor Y = L^{-1} (FP64), so that each apply is two parallel triangular products
-    c->Linv.alloc(No * No);
-    c->Linv.zero(s);
-    k_eye<<<grid_for(No, 256), 256, 0, s>>>(c->Linv.p, No);
-    HP_CHECK_LAUNCH();
-    for (int kt = 0; kt < T; ++kt) {
-      k_trinv_scale<<<kt + 1, 256, 0, s>>>(c->Linv.p, No, kt, c->Lo_dinv.p);
-      HP_CHECK_LAUNCH();
-      int m = T - kt - 1;
-      if (m > 0) {
-        k_trinv_update<<<m * (kt + 1), 256, 0, s>>>(c->Linv.p, c->Lo.p, No, kt, T);
-        HP_CHECK_LAUNCH();
-      }
-    }
+    HP_CUDA(cudaEventRecord(c->ev_join, s2));
+    HP_CUDA(cudaStreamWaitEvent(s, c->ev_join, 0));
   }
   HP_CUDA(cudaStreamSynchronize(s));
 }
