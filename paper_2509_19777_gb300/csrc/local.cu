@@ -1007,11 +1007,11 @@ __global__ void __launch_bounds__(SM32_THREADS, 1) k_band_solve_multi32(const in
 //     (cp.async.bulk) into a ring of shared-memory rows.  Chunks of up to `chunk_rows` rows are packed back
 //     to back (a chunk that reaches the end of the ring is split into two copies), each guarded by a
 //     full/empty mbarrier pair; a chunk is issued as soon as the rows it lands on have been released, so
-//     the copies of the next one or two panels are in flight while a panel is consumed.  The step time is
-//     otherwise bounded by the latency of a copy issued one panel ahead.
-//   - the producer also copies the leader's diagonal+near chunk of each step (2 NB rows) into a small ring
-//     of its own, ahead of the far rows of the same step; the leader never issues or waits on a load on its
-//     chain: right-hand-side values, scratch values and output indices are fetched one or two steps ahead.
+//     the copies of the next one or two panels are in flight while a panel is consumed.
+//   - a diagonal-chunk warp copies the leader's diagonal+near chunk of each step (2 NB rows) into a small
+//     ring of its own with 16-byte cp.async (the load/store path), a few steps ahead; the leader never issues
+//     or waits on a load on its chain: right-hand-side values, scratch values and output indices are fetched
+//     one or two steps ahead.
 // There is no per-step barrier: each role waits only for what it reads, through mbarriers.  Bulk step s
 // needs leader step s-1 (y_{p-1}, or the x values above panel p-1).  In the forward sweep the rows of panel
 // p are final once the first NB far rows of bulk step s-1 (warp 0 signals them as soon as its part of the
