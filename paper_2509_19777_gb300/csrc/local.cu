@@ -452,6 +452,10 @@ __device__ __forceinline__ void mma_tf32(float (&d)[4], const uint32_t (&a)[4], 
 //      staging area by cp.async before the arithmetic.
 constexpr int CHOL32_THREADS = 512;
 constexpr int CHOL32_LD = 36;
+// row stride of a warp's staged 32x32 trailing tile: with 40 floats, the 8-byte pairs each lane reads in
+// the MMA accumulator layout (row g8 (+8, +16), columns 2 tq, 2 tq + 1) fall on 32 distinct banks per
+// half-warp, where a stride of 32 put 8 lanes on every bank
+constexpr int CHOL32_CST_LD = 40;
 
 __global__ void __launch_bounds__(CHOL32_THREADS, 1) k_band_chol32(const int *order, int count, int *queue,
                                                                 const int *nloc, const int *bwv,
@@ -463,7 +467,7 @@ __global__ void __launch_bounds__(CHOL32_THREADS, 1) k_band_chol32(const int *or
   __shared__ __align__(16) float Lk[NB][LD];
   __shared__ __align__(16) float Dv[NB][LD];
   __shared__ int s_job;
-  float *Cst = P + (size_t)(NB + bwv_max) * LD;  // per-warp 32x32 staging of the trailing tiles
+  float *Cst = P + (size_t)(NB + bwv_max) * LD;  // per-warp 32x32 staging of the trailing tiles (row stride 40)
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = CHOL32_THREADS / 32;
   for (;;) {
     if (threadIdx.x == 0) s_job = atomicAdd(queue, 1);
@@ -552,20 +556,28 @@ __global__ void __launch_bounds__(CHOL32_THREADS, 1) k_band_chol32(const int *or
           float4 t = *reinterpret_cast<const float4 *>(P + r * LD + 4 * g);
           ar[4 * g] = t.x; ar[4 * g + 1] = t.y; ar[4 * g + 2] = t.z; ar[4 * g + 3] = t.w;
         }
+        // four columns per pass, stored as one 16-byte group (rows 144 bytes apart: 8 consecutive rows hit 8
+        // distinct bank groups); the row's original values stay in registers
 #pragma unroll 1
-        for (int cc = 0; cc < NB; ++cc) {
-          float s0 = 0.f, s1 = 0.f;
+        for (int cg = 0; cg < NB / 4; ++cg) {
+          float o[4];
 #pragma unroll
-          for (int g = 0; g < 8; ++g) {
-            if (4 * g <= cc) {
-              float4 d = *reinterpret_cast<const float4 *>(&Dv[cc][4 * g]);
-              s0 = fmaf(ar[4 * g], d.x, s0);
-              s1 = fmaf(ar[4 * g + 1], d.y, s1);
-              s0 = fmaf(ar[4 * g + 2], d.z, s0);
-              s1 = fmaf(ar[4 * g + 3], d.w, s1);
+          for (int j = 0; j < 4; ++j) {
+            const int cc = 4 * cg + j;
+            float s0 = 0.f, s1 = 0.f;
+#pragma unroll
+            for (int g = 0; g < 8; ++g) {
+              if (4 * g <= cc) {
+                float4 d = *reinterpret_cast<const float4 *>(&Dv[cc][4 * g]);
+                s0 = fmaf(ar[4 * g], d.x, s0);
+                s1 = fmaf(ar[4 * g + 1], d.y, s1);
+                s0 = fmaf(ar[4 * g + 2], d.z, s0);
+                s1 = fmaf(ar[4 * g + 3], d.w, s1);
+              }
             }
+            o[j] = s0 + s1;
           }
-          P[r * LD + cc] = s0 + s1;
+          *reinterpret_cast<float4 *>(P + r * LD + 4 * cg) = make_float4(o[0], o[1], o[2], o[3]);
         }
       }
       __syncthreads();
@@ -583,7 +595,7 @@ __global__ void __launch_bounds__(CHOL32_THREADS, 1) k_band_chol32(const int *or
       const int Wn = R - nb;
       const int nt = (Wn + 31) / 32;
       const int ntiles = nt * (nt + 1) / 2;
-      float *cst = Cst + (size_t)wid * 32 * 32;
+      float *cst = Cst + (size_t)wid * 32 * CHOL32_CST_LD;
       for (int t = wid; t < ntiles; t += nw) {
         int tj = 0, rem = t;
         while (rem >= nt - tj) {
@@ -597,7 +609,7 @@ __global__ void __launch_bounds__(CHOL32_THREADS, 1) k_band_chol32(const int *or
 #pragma unroll
         for (int u = 0; u < 8; ++u) {
           const int piece = u * 32 + lane;  // row piece >> 3, 16-byte group piece & 7
-          if ((piece >> 3) < rows_valid) cp_async16(cst + piece * 4, tile + piece * 4);
+          if ((piece >> 3) < rows_valid) cp_async16(cst + (piece >> 3) * CHOL32_CST_LD + (piece & 7) * 4, tile + piece * 4);
         }
         cp_async_commit();
         // A_ij -= sum_k L_ik L_jk on the tensor cores: m16n8k8 TF32 products with each operand split into a
@@ -646,13 +658,16 @@ __global__ void __launch_bounds__(CHOL32_THREADS, 1) k_band_chol32(const int *or
 #pragma unroll
           for (int ni = 0; ni < 4; ++ni)
 #pragma unroll
-            for (int h = 0; h < 2; ++h)
+            for (int h = 0; h < 2; ++h) {
+              const int q = 16 * mi + g8 + 8 * h, col0 = 8 * ni + 2 * tq;
+              const float2 old = *reinterpret_cast<const float2 *>(cst + q * CHOL32_CST_LD + col0);
 #pragma unroll
               for (int e = 0; e < 2; ++e) {
-                const int q = 16 * mi + g8 + 8 * h, col = 8 * ni + 2 * tq + e;
+                const int col = col0 + e;
                 const int il = rbase + q, jl = cbase + col;
-                if (q < rows_valid && jl < R && jl <= il) tile[q * NB + col] = cst[q * 32 + col] - acc[mi][ni][2 * h + e];
+                if (q < rows_valid && jl < R && jl <= il) tile[q * NB + col] = (e ? old.y : old.x) - acc[mi][ni][2 * h + e];
               }
+            }
         __syncwarp();
       }
       __syncthreads();
@@ -1838,7 +1853,7 @@ void layout_and_factor(hplmm_ctx *c, LocalSet &S, int where, cudaStream_t s, boo
   int grid = std::min(K, 2 * num_sms());
   if constexpr (sizeof(T) == 4) {
     const size_t smem32 =
-        ((size_t)(NB + bwmax) * CHOL32_LD + (size_t)(CHOL32_THREADS / 32) * 32 * 32) * sizeof(float);
+        ((size_t)(NB + bwmax) * CHOL32_LD + (size_t)(CHOL32_THREADS / 32) * 32 * CHOL32_CST_LD) * sizeof(float);
     HP_REQUIRE(smem32 <= 216 * 1024, HPLMM_ERR_INVALID,
                "local problem half bandwidth " + std::to_string(bwmax) + " is too large; use smaller grain grids");
     HP_CUDA(cudaFuncSetAttribute(k_band_chol32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem32));
