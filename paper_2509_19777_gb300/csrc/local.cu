@@ -1131,18 +1131,8 @@ __device__ __forceinline__ uint32_t peer_addr(const void *p, uint32_t rank) {
   asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(a) : "r"(smem_u32(p)), "r"(rank));
   return a;
 }
-__device__ __forceinline__ void st_peer(uint32_t addr, float v) {
-  asm volatile("st.shared::cluster.f32 [%0], %1;" ::"r"(addr), "f"(v) : "memory");
-}
-__device__ __forceinline__ void st_peer(uint32_t addr, double v) {
-  asm volatile("st.shared::cluster.f64 [%0], %1;" ::"r"(addr), "d"(v) : "memory");
-}
 __device__ __forceinline__ void st_peer_u32(uint32_t addr, uint32_t v) {
   asm volatile("st.shared::cluster.u32 [%0], %1;" ::"r"(addr), "r"(v) : "memory");
-}
-// arrival on an mbarrier of the other CTA, releasing this thread's prior writes at cluster scope
-__device__ __forceinline__ void mbar_arrive_peer(uint32_t addr) {
-  asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(addr) : "memory");
 }
 // asynchronous store into the other CTA's shared memory that completes its bytes on an mbarrier there (the
 // sender does not wait; the receiver sees the value once the barrier phase completes)
@@ -1160,17 +1150,6 @@ __device__ __forceinline__ void st_async_peer(uint32_t addr, double v, uint32_t 
 __device__ __forceinline__ void cluster_sync_all() {
   asm volatile("barrier.cluster.arrive.release;\n\tbarrier.cluster.wait.acquire;" ::: "memory");
 }
-// named barrier `id` over `nthreads` threads; returns the OR of `flag` over them
-__device__ __forceinline__ int bar_red_or(int id, int nthreads, int flag) {
-  int res;
-  asm volatile(
-      "{\n .reg .pred p, q;\n setp.ne.s32 p, %1, 0;\n bar.red.or.pred q, %2, %3, p;\n selp.s32 %0, 1, 0, q;\n}\n"
-      : "=r"(res)
-      : "r"(flag), "r"(id), "r"(nthreads)
-      : "memory");
-  return res;
-}
-
 // 16-byte group loads of a stored factor row, converted to the compute type
 template <typename S> struct Vec16;
 template <> struct Vec16<float> {
@@ -1332,6 +1311,13 @@ __global__ void __launch_bounds__(WS_THREADS) k_band_solve_ws(
   else
     __syncthreads();
   const uint32_t peer = (uint32_t)(rank ^ 1);
+  // the other CTA's window and step barriers, mapped once (shared::cluster addresses are linear in each CTA's
+  // window, so a slot's address is the base plus its byte offset)
+  const uint32_t peer_v = (CL == 2) ? peer_addr(v, peer) : 0u;
+  const uint32_t peer_ydone = (CL == 2) ? peer_addr(&ydone[0], peer) : 0u;
+  const uint32_t peer_pdone = (CL == 2) ? peer_addr(&pdone[0], peer) : 0u;
+  const uint32_t peer_v1push = (CL == 2) ? peer_addr(&v1push[0][0], peer) : 0u;
+  const uint32_t peer_red1 = (CL == 2) ? peer_addr(&red1[0][0], peer) : 0u;
   auto raise_abort = [&]() {
     s_abort = 1;
     if constexpr (CL == 2) st_peer_u32(peer_addr((const void *)&s_abort, peer), 1u);
@@ -1489,7 +1475,8 @@ __global__ void __launch_bounds__(WS_THREADS) k_band_solve_ws(
           T y = (lane < nb) ? a0 + a1 : (T)0;
           if (own) {
             v[(k0 + i) & wmask] = y;  // read by the bulk warps at the next step and by the near product
-            if constexpr (CL == 2) st_async_peer(peer_addr(&v[(k0 + i) & wmask], 1), y, peer_addr(&ydone[s & 3], 1));
+            if constexpr (CL == 2)
+              st_async_peer(peer_v + (uint32_t)(((k0 + i) & wmask) * sizeof(T)), y, peer_ydone + 8u * (s & 3));
             if (lane < nb) ys[k0 + i] = y;
           }
           __syncwarp();
@@ -1562,7 +1549,8 @@ __global__ void __launch_bounds__(WS_THREADS) k_band_solve_ws(
           const T x = a0 + a1;
           // rank 1 receives a full panel every step (zeros past the matrix, in slots it never reads)
           if (CL == 2 && own)
-            st_async_peer(peer_addr(&v[(k0 + i) & wmask], 1), lane < nb ? x : (T)0, peer_addr(&ydone[s & 3], 1));
+            st_async_peer(peer_v + (uint32_t)(((k0 + i) & wmask) * sizeof(T)), lane < nb ? x : (T)0,
+                          peer_ydone + 8u * (s & 3));
           if (lane < nb) {
             v[(k0 + i) & wmask] = x;
             if (atomic)
@@ -1596,22 +1584,22 @@ __global__ void __launch_bounds__(WS_THREADS) k_band_solve_ws(
       }
       const int q = bulk_q(s);
       // NB values every step (to the sink row when there is nothing to push)
-      const T *dst = &v1push[4][0];
+      uint32_t dst = peer_v1push + 4u * NB * sizeof(T);
       T val = 0;
       if (s < np) {
         if (s + 3 < np) {
-          dst = &v1push[(s + 3) & 3][0];
+          dst = peer_v1push + (uint32_t)(((s + 3) & 3) * NB * sizeof(T));
           val = lane < NB ? v[((s + 3) * NB + lane) & wmask] : (T)0;
         }
         if (q >= 0 && lane < NB) v[(q * NB + lane) & wmask] = (T)0;
       } else if (q >= 0) {
-        dst = &red1[q & 3][0];
+        dst = peer_red1 + (uint32_t)((q & 3) * NB * sizeof(T));
         if (lane < NB) {
 #pragma unroll
           for (int w = 0; w < WS_BULK_WARPS; ++w) val += red_r1[q & 3][w][lane];
         }
       }
-      if (lane < NB) st_async_peer(peer_addr(dst + lane, 0), val, peer_addr(&pdone[s & 3], 0));
+      if (lane < NB) st_async_peer(dst + (uint32_t)(lane * sizeof(T)), val, peer_pdone + 8u * (s & 3));
     }
   } else if (wid >= 3) {
     // ------------------------------------------------------------ bulk: far rows of panel bulk_q(s)
