@@ -8,7 +8,9 @@
 // Section 5: right-preconditioned GMRES.  Because the mixed-precision apply is
 // not exactly linear, the flexible variant (FGMRES, storing Z_j = M^{-1} v_j) is
 // used; classical Gram-Schmidt with one re-orthogonalisation (CGS2) keeps the
-// Arnoldi basis orthogonal in FP64 with two block reductions per step.
+// Arnoldi basis orthogonal in FP64 with three passes over the basis per step
+// (h1 = V^T w; w -= V h1 fused with h2 = V^T w; w -= V h2 fused with |w|^2),
+// each reduced to its result inside the same launch.
 #include "common.cuh"
 
 #include <chrono>

@@ -1006,8 +1006,8 @@ __global__ void __launch_bounds__(SM32_THREADS, 1) k_band_solve_multi32(const in
 }
 
 // ---------------------------------------------------------------- single-RHS smoother solves
-// One CTA per problem solves L L^T x = r for the gathered local right-hand side and adds (contact grids,
-// which overlap) or stores (grain grids) x into z.
+// One CTA, or a two-CTA cluster (below), per problem solves L L^T x = r for the gathered local right-hand
+// side and adds (contact grids, which overlap) or stores (grain grids) x into z.
 //
 // Both sweeps run in steps, one per panel (forward: p = 0 .. np-1, backward: p = np-1 .. 0).  The work of a
 // step is split between warps so that the short sequential chain of the triangular solve overlaps the
@@ -1015,7 +1015,8 @@ __global__ void __launch_bounds__(SM32_THREADS, 1) k_band_solve_multi32(const in
 //   - the leader warp handles the diagonal block of panel p and its "near" block (the next NB rows):
 //       forward  y_p = inv(L_pp) (v_p - L_{p,p-1} y_{p-1}),   near product L_{p+1,p} y_p kept in registers;
 //       backward x_p = inv(L_pp)^T (y_p - L_{p+1,p}^T x_{p+1} - far_p);
-//   - the bulk warps handle the "far" rows (beyond the near block) of panel p-1, one row per thread:
+//   - the bulk warps handle the "far" rows (beyond the near block) of panel p-1, up to two rows per thread
+//     per pass:
 //       forward  v[rows] -= L_far(p-1) y_{p-1};
 //       backward far_{p-1} = L_far(p-1)^T x[rows] (column sums reduced per warp);
 //   - a producer warp streams the far rows of successive panels with bulk asynchronous copies
@@ -1043,6 +1044,16 @@ __global__ void __launch_bounds__(SM32_THREADS, 1) k_band_solve_multi32(const in
 // global scratch
 // vector; the backward sweep reads y_p back from there, keeps x in the window for the far products, and
 // writes each x_p to z as soon as it is known.
+//
+// Two-CTA form (CL = 2, for sets with at most half as many problems as SMs): the cluster splits each
+// panel's far rows, rank 0 (with the leader) the first part, at least 2 NB rows, rank 1 the rest.  Rank
+// 1's rows then only update rows at least 4 NB below their panel, so it accumulates them in its own window
+// and its pusher warp sends rank 0 the finished values of panel s+3 after its step s (forward), or, running
+// one panel ahead in the backward sweep, the far sums of the panel it processed.  The leader sends y_p /
+// x_p into rank 1's window.  Every exchange is NB values sent with st.async, completing its bytes on an
+// mbarrier of the receiving CTA that an idle lane there arms (expected bytes) once the barrier's previous
+// phase has completed; each side's waits on the other are therefore phase-exact, and a release-ordered
+// remote arrive (which would keep its thread until the stores land) is never needed.
 //
 // Shared-memory bank conflicts: a factor row is 128 bytes (8 groups of 16 bytes).  A bulk thread visits its
 // row's 16-byte groups starting at (thread mod 8), with its copy of y (or its column accumulators) kept in
