@@ -281,12 +281,16 @@ def run_e2e(hp, problem, form, steps, warmup, flush, stream):
     return times, h2d, d2h
 
 
+# the sources the smoother solve's translation unit is compiled from: its recorded DRAM traffic stays valid
+# while these are unchanged
+SMOOTHER_SOURCES = ("paper_2509_19777_gb300/csrc/local.cu", "paper_2509_19777_gb300/csrc/common.cuh",
+                    "include/hplmm.h")
+
+
 def kernel_source_hash():
     h = hashlib.sha256()
-    csrc = os.path.join(ROOT, "paper_2509_19777_gb300", "csrc")
-    for f in sorted(os.listdir(csrc)):
-        if f.endswith((".cu", ".cuh")):
-            h.update(open(os.path.join(csrc, f), "rb").read())
+    for f in SMOOTHER_SOURCES:
+        h.update(open(os.path.join(ROOT, f), "rb").read())
     return h.hexdigest()[:16]
 
 
