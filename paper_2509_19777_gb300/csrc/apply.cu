@@ -179,29 +179,40 @@ __global__ void k_mcombine(double *x, const double *Z, long long ldz, int nv, co
   }
 }
 
+// Register-block shapes of the fused Gram-Schmidt kernels: capacity CAP (the smallest listed one >= nv is
+// taken; the CAP - nv padded slots still cost an FP64 multiply-add per element, and the FP64 pipe is what
+// bounds these kernels, so the capacities step by 2) and U elements per thread per pass, so that about
+// CAP x U loads are in flight.
+template <int C, int U>
+struct CgsShape {
+  static constexpr int cap = C, u = U;
+};
+template <typename F, typename S0, typename... Ss>
+bool pick_cgs_shape(int nv, F &&f) {
+  if (nv <= S0::cap) {
+    f(S0{});
+    return true;
+  }
+  if constexpr (sizeof...(Ss) > 0)
+    return pick_cgs_shape<F, Ss...>(nv, static_cast<F &&>(f));
+  else
+    return false;
+}
+template <typename F>
+bool for_cgs_shape(int nv, F &&f) {
+  return pick_cgs_shape<F, CgsShape<1, 8>, CgsShape<2, 8>, CgsShape<3, 8>, CgsShape<4, 8>, CgsShape<6, 4>,
+                        CgsShape<8, 4>, CgsShape<10, 2>, CgsShape<12, 2>, CgsShape<14, 2>, CgsShape<16, 2>,
+                        CgsShape<18, 1>, CgsShape<20, 1>, CgsShape<22, 1>, CgsShape<24, 1>, CgsShape<26, 1>,
+                        CgsShape<28, 1>, CgsShape<30, 1>, CgsShape<32, 1>>(nv, static_cast<F &&>(f));
+}
+
 // out[j] = V_j . w, j < nv (one launch)
 void mdot(hplmm_ctx *c, const double *V, long long ldv, int nv, const double *w, long long n, double *out) {
   ProfScope ps(c, HPLMM_PH_KRYLOV);
   double *pp = c->w_partial.p;
   unsigned *ct = c->w_ticket.p;
   auto go = [&](auto kern) { kern<<<MDOT_BLOCKS, 256, 0, c->stream>>>(V, ldv, nv, w, n, pp, out, ct); };
-  if (nv <= 1)
-    go(k_cgs_dot<1, 8>);
-  else if (nv <= 2)
-    go(k_cgs_dot<2, 8>);
-  else if (nv <= 4)
-    go(k_cgs_dot<4, 8>);
-  else if (nv <= 8)
-    go(k_cgs_dot<8, 4>);
-  else if (nv <= 12)
-    go(k_cgs_dot<12, 2>);
-  else if (nv <= 16)
-    go(k_cgs_dot<16, 2>);
-  else if (nv <= 24)
-    go(k_cgs_dot<24, 1>);
-  else if (nv <= 32)
-    go(k_cgs_dot<32, 1>);
-  else
+  if (!for_cgs_shape(nv, [&](auto sh) { go(k_cgs_dot<decltype(sh)::cap, decltype(sh)::u>); }))
     go(k_cgs_dot<64, 1>);
   HP_CHECK_LAUNCH();
 }
@@ -213,32 +224,16 @@ void cgs_update(hplmm_ctx *c, const double *V, long long ldv, int nv, const doub
   double *pp = c->w_partial.p;
   unsigned *ct = c->w_ticket.p;
   auto go = [&](auto kern) { kern<<<MDOT_BLOCKS, 256, 0, c->stream>>>(V, ldv, nv, h, w, n, mode, pp, out, ct); };
-  if (nv <= 1)
-    go(k_cgs_update<1, 8>);
-  else if (nv <= 2)
-    go(k_cgs_update<2, 8>);
-  else if (nv <= 4)
-    go(k_cgs_update<4, 8>);
-  else if (nv <= 8)
-    go(k_cgs_update<8, 4>);
-  else if (nv <= 12)
-    go(k_cgs_update<12, 2>);
-  else if (nv <= 16)
-    go(k_cgs_update<16, 2>);
-  else if (nv <= 24)
-    go(k_cgs_update<24, 1>);
-  else if (nv <= 32)
-    go(k_cgs_update<32, 1>);
-  else {
-    k_mupdate<<<MDOT_BLOCKS, 256, 0, c->stream>>>(w, V, ldv, nv, h, n);
+  if (for_cgs_shape(nv, [&](auto sh) { go(k_cgs_update<decltype(sh)::cap, decltype(sh)::u>); })) {
     HP_CHECK_LAUNCH();
-    if (mode == 0)
-      mdot(c, V, ldv, nv, w, n, out);
-    else
-      mdot(c, w, 0, 1, w, n, out);
     return;
   }
+  k_mupdate<<<MDOT_BLOCKS, 256, 0, c->stream>>>(w, V, ldv, nv, h, n);
   HP_CHECK_LAUNCH();
+  if (mode == 0)
+    mdot(c, V, ldv, nv, w, n, out);
+  else
+    mdot(c, w, 0, 1, w, n, out);
 }
 
 }  // namespace

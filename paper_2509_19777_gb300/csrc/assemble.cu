@@ -294,9 +294,17 @@ __global__ void k_spmv_sell(const int *slice_off, const int *scol, const T *sval
     const int m = scol[slot + lane];
     const T *v = sval + slot * 9 + lane;
     A x0 = (A)x[3 * m], x1 = (A)x[3 * m + 1], x2 = (A)x[3 * m + 2];
-    s0 += (A)v[0] * x0 + (A)v[32] * x1 + (A)v[64] * x2;
-    s1 += (A)v[96] * x0 + (A)v[128] * x1 + (A)v[160] * x2;
-    s2 += (A)v[192] * x0 + (A)v[224] * x1 + (A)v[256] * x2;
+    // one multiply-add per entry into the running sums (a product summed into a partial first would cost
+    // an extra multiply and add, and the FP64 form is bound by the FP64 pipe)
+    s0 += (A)v[0] * x0;
+    s0 += (A)v[32] * x1;
+    s0 += (A)v[64] * x2;
+    s1 += (A)v[96] * x0;
+    s1 += (A)v[128] * x1;
+    s1 += (A)v[160] * x2;
+    s2 += (A)v[192] * x0;
+    s2 += (A)v[224] * x1;
+    s2 += (A)v[256] * x2;
   }
   if (sub) {
     y[3 * n] = sub[3 * n] - (double)s0;

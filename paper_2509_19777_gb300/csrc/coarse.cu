@@ -240,34 +240,60 @@ __global__ void k_symmetrize(double *A, long long N, double *asym) {
 // ---------------------------------------------------------------- dense FP64 Cholesky (64x64 tiles)
 constexpr int TB = 64;
 
-// Diagonal tile: Cholesky factor L_kk and its inverse, one CTA of 256 threads.  Thread t keeps the 16
-// elements (r, c) with c = t mod 64, r = t / 64 + 4 u (u = 0 .. 15) in registers through both phases:
-//   factor (right-looking, one column per step): the owner of (cc, cc) takes the square root, the owners of
-//   column cc scale it and publish it, every thread updates its elements right of cc;
-//   inverse W = L^{-1} (row by row): the owners of row q scale it by 1/L_qq and publish it, every thread
-//   subtracts L_rq W_q from its rows r > q.
+// Diagonal tile: Cholesky factor L_kk and its inverse W = L_kk^{-1}, one CTA of 256 threads.  One SM's
+// FP64 pipe is the limit (this kernel is on the critical path of the factorisation), so each step issues
+// only the elements it changes:
+//   factor, right-looking, one column per step.  The tile's lower triangle is numbered "column 63 first,
+//   rows ascending within a column" and element e lives in register slot e / 256 of thread e mod 256.  The
+//   trailing triangle of step cc (columns > cc) is then the prefix e < M(cc) = m(m+1)/2, m = 63 - cc, and
+//   column cc the 64 - cc elements after it, so a warp's slot is wholly busy, wholly idle or on the
+//   boundary.  Step cc: the owner of (cc, cc) takes its square root (right after its own update of step
+//   cc - 1), the owners of column cc scale it and publish it in row cc of the shared tile, the owners of the
+//   prefix subtract the rank-1 product;
+//   inverse, right-looking, one step behind the factor in the same phases: step q subtracts L_rq W_qj from
+//   rows r > q, columns j <= q (addressed compactly), and finishes row q + 1 with 1 / L_{q+1,q+1} as it makes
+//   the last update there.  W's strict lower part and the published factor columns (upper part, transposed)
+//   share one shared tile; W's diagonal is rdiag.
 // The tile's padding rows and columns (past N) are the identity, so the steps stay well defined.
+constexpr int PT_NE = TB * (TB + 1) / 2;
+constexpr int PT_SLOTS = (PT_NE + 255) / 256;
+
 __global__ void __launch_bounds__(256) k_potrf_tile(double *A, long long N, int kt, double *Dinv, int *status) {
-  __shared__ double colv[TB];
-  __shared__ double rdiag[TB];
-  __shared__ double Ls[TB][TB + 1];
-  __shared__ double wrow[2][TB];
-  const int t = threadIdx.x;
-  const int c = t & (TB - 1), r0 = t >> 6;
+  __shared__ double S[TB][TB + 1];  // S[q][r] = L_rq (r > q); S[r][j] = W_rj (r > j)
+  __shared__ double rdiag[TB], ldiag[TB];
+  const int t = threadIdx.x, lane = t & 31, wbase = t & ~31;
   const int k0 = kt * TB;
   const int nb = (int)min((long long)TB, N - k0);
-  double a[16];
-#pragma unroll
-  for (int u = 0; u < 16; ++u) {
-    const int r = r0 + 4 * u;
-    a[u] = (r < nb && c < nb && c <= r) ? A[(long long)(k0 + r) * N + k0 + c] : (r == c ? 1.0 : 0.0);
+  for (int e = t; e < TB * TB; e += 256) {
+    const int r = e / TB, c = e % TB;
+    if (c <= r) S[r][c] = (r < nb && c < nb) ? A[(long long)(k0 + r) * N + k0 + c] : (r == c ? 1.0 : 0.0);
   }
-  for (int cc = 0; cc < TB; ++cc) {
-    if (c == cc && (cc & 3) == r0) {
-      const int uc = cc >> 2;
+  __syncthreads();
+  double a[PT_SLOTS];
+  int rs[PT_SLOTS], cs[PT_SLOTS];
+#pragma unroll
+  for (int k = 0; k < PT_SLOTS; ++k) {
+    const int e = 256 * k + t;
+    // column j = 63 - c (counted from the right) holds j + 1 elements and starts at j (j + 1) / 2
+    int j = (int)((sqrtf(8.0f * (float)e + 1.0f) - 1.0f) * 0.5f);
+    while (j * (j + 1) / 2 > e) --j;
+    while ((j + 1) * (j + 2) / 2 <= e) ++j;
+    cs[k] = TB - 1 - j;
+    rs[k] = cs[k] + e - j * (j + 1) / 2;
+    a[k] = e < PT_NE ? S[rs[k]][cs[k]] : 0.0;
+  }
+  __syncthreads();
+  for (int e = t; e < TB * TB; e += 256) {
+    const int r = e / TB, c = e % TB;
+    if (c < r) S[r][c] = 0.0;
+  }
+  auto diag = [&](int cc) {
+    const int e = (TB - 1 - cc) * (TB - cc) / 2;
+    if ((e & 255) == t) {
+      const int kd = e >> 8;
       double d = 0.0;
 #pragma unroll
-      for (int u = 0; u < 16; ++u) d = (u == uc) ? a[u] : d;
+      for (int k = 0; k < PT_SLOTS; ++k) d = (k == kd) ? a[k] : d;
       if (!(d > 0.0)) {
         if (atomicCAS(status, 0, (int)HPLMM_ERR_SINGULAR) == 0) {
           status[1] = 3;
@@ -278,69 +304,58 @@ __global__ void __launch_bounds__(256) k_potrf_tile(double *A, long long N, int 
       }
       const double sd = sqrt(d);
 #pragma unroll
-      for (int u = 0; u < 16; ++u) a[u] = (u == uc) ? sd : a[u];
+      for (int k = 0; k < PT_SLOTS; ++k) a[k] = (k == kd) ? sd : a[k];
+      ldiag[cc] = sd;
       rdiag[cc] = 1.0 / sd;
     }
-    __syncthreads();
-    if (c == cc) {
-      const double rd = rdiag[cc];
+  };
+  diag(0);
+  __syncthreads();
+  for (int cc = 0; cc < TB; ++cc) {
+    const int M = (TB - 1 - cc) * (TB - cc) / 2;
+    // column cc below the diagonal: scale and publish
+    const int lo = M + 1, hi = M + TB - 1 - cc;
+    const double rd = rdiag[cc];
 #pragma unroll
-      for (int u = 0; u < 16; ++u) {
-        const int r = r0 + 4 * u;
-        if (r > cc) {
-          a[u] *= rd;
-          colv[r] = a[u];
+    for (int k = 0; k < PT_SLOTS; ++k) {
+      const int eb = 256 * k + wbase;
+      if (eb <= hi && eb + 31 >= lo) {
+        const int e = eb + lane;
+        if (e >= lo && e <= hi) {
+          a[k] *= rd;
+          S[cc][rs[k]] = a[k];
         }
       }
     }
     __syncthreads();
-    if (c > cc) {
-      const double vc = colv[c];
+    // trailing triangle of the factor
 #pragma unroll
-      for (int u = 0; u < 16; ++u) {
-        const int r = r0 + 4 * u;
-        if (r >= c) a[u] -= colv[r] * vc;
+    for (int k = 0; k < PT_SLOTS; ++k) {
+      const int eb = 256 * k + wbase;
+      if (eb < M && eb + lane < M) a[k] -= S[cc][rs[k]] * S[cc][cs[k]];
+    }
+    // inverse step q = cc - 1
+    if (cc >= 1) {
+      const int q = cc - 1, ncol = q + 1, cnt = (TB - 1 - q) * ncol;
+      const double rq = rdiag[q], rn = rdiag[q + 1];
+      for (int e = t; e < cnt; e += 256) {
+        const int ro = e / ncol, j = e - ro * ncol, r = q + 1 + ro;
+        const double wq = (j == q) ? rq : S[q][j];
+        double v = S[r][j] - S[q][r] * wq;
+        if (ro == 0) v *= rn;
+        S[r][j] = v;
       }
     }
-  }
-  // factor to the matrix and to shared memory (the inverse reads its columns)
-#pragma unroll
-  for (int u = 0; u < 16; ++u) {
-    const int r = r0 + 4 * u;
-    Ls[r][c] = (c <= r) ? a[u] : 0.0;
-    if (r < nb && c < nb) A[(long long)(k0 + r) * N + k0 + c] = (c <= r) ? a[u] : 0.0;
-  }
-  __syncthreads();
-  double w[16];
-#pragma unroll
-  for (int u = 0; u < 16; ++u) w[u] = (r0 + 4 * u == c) ? 1.0 : 0.0;
-  for (int q = 0; q < TB; ++q) {
-    if ((q & 3) == r0) {
-      const double rd = rdiag[q];
-      const int uq = q >> 2;
-      double wv = 0.0;
-#pragma unroll
-      for (int u = 0; u < 16; ++u) {
-        w[u] = (u == uq) ? w[u] * rd : w[u];
-        wv = (u == uq) ? w[u] : wv;
-      }
-      wrow[q & 1][c] = wv;
-    }
+    if (cc + 1 < TB) diag(cc + 1);
     __syncthreads();
-    if (c <= q) {
-      const double wq = wrow[q & 1][c];
-#pragma unroll
-      for (int u = 0; u < 16; ++u) {
-        const int r = r0 + 4 * u;
-        if (r > q) w[u] -= Ls[r][q] * wq;
-      }
-    }
   }
-  // padding rows of the factor are identity rows, so rdiag is 1 there and W stays the identity
-#pragma unroll
-  for (int u = 0; u < 16; ++u) {
-    const int r = r0 + 4 * u;
-    Dinv[(long long)kt * TB * TB + r * TB + c] = (r < nb && c < nb) ? w[u] : 0.0;
+  // the factor and the inverse out, row-major; padding rows of the factor are identity rows, so rdiag is 1
+  // there and W stays the identity
+  for (int e = t; e < TB * TB; e += 256) {
+    const int r = e / TB, c = e % TB;
+    const bool in = r < nb && c < nb;
+    if (in) A[(long long)(k0 + r) * N + k0 + c] = c < r ? S[c][r] : (c == r ? ldiag[r] : 0.0);
+    Dinv[(long long)kt * TB * TB + e] = in ? (c < r ? S[r][c] : (c == r ? rdiag[r] : 0.0)) : 0.0;
   }
 }
 
@@ -486,11 +501,15 @@ __global__ void k_trinv_update(double *Y, const double *L, long long N, int kt, 
     }
 }
 
-// u = Y t over the lower triangle: warp per row, 8 loads per lane in flight
-__global__ void k_trmv_lower(const double *Y, long long N, const double *t, double *u) {
-  const int lane = threadIdx.x & 31;
-  const long long row = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  if (row >= N) return;
+// u = Y t over the lower triangle: warp per row, 8 loads per lane in flight.  Row lengths grow with the row
+// index, so a CTA takes the rows of four pairs (p, N-1-p), each pair N+1 elements long: every CTA carries
+// the same work (with consecutive rows per CTA the long rows, all at the end of the grid, fell to a few SMs)
+__global__ void __launch_bounds__(256) k_trmv_lower(const double *Y, long long N, const double *t, double *u) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const long long p = 4LL * blockIdx.x + (wid & 3);
+  if (p >= (N + 1) / 2) return;
+  const long long row = wid < 4 ? p : N - 1 - p;
+  if (wid >= 4 && row == p) return;  // the middle row of an odd N
   const double *yr = Y + row * N;
   double s0 = 0.0, s1 = 0.0;
   for (long long jb = 0; jb <= row; jb += 256) {
@@ -510,24 +529,43 @@ __global__ void k_trmv_lower(const double *Y, long long N, const double *t, doub
   if (lane == 0) u[row] = s;
 }
 
-// z = Y^T u over the lower triangle: CTA per 32-row slab, threads over columns (the slab's 32 loads per
-// column issued together), atomic accumulation
-__global__ void k_trmv_lower_t(const double *Y, long long N, const double *u, double *z) {
-  __shared__ double us[32];
-  const long long r0 = (long long)blockIdx.y * 32;
-  const long long r1 = min(N, r0 + 32);
-  if (threadIdx.x < 32) us[threadIdx.x] = (r0 + threadIdx.x < r1) ? u[r0 + threadIdx.x] : 0.0;
+// z = Y^T u over the lower triangle, in 64 x 64 tiles (row slab, column chunk) of the lower triangle, one CTA
+// of 64 threads per tile so that the CTAs carry equal work: thread per column with the slab's 64 loads issued
+// together, atomic accumulation into z
+constexpr int TRMV_SLAB = 64;
+__global__ void __launch_bounds__(64, 8) k_trmv_lower_t(const double *Y, long long N, const double *u, double *z) {
+  __shared__ double us[TRMV_SLAB];
+  const int tix = blockIdx.x;
+  int ti = (int)((sqrtf(8.0f * (float)tix + 1.0f) - 1.0f) * 0.5f);
+  while ((ti + 1) * (ti + 2) / 2 <= tix) ++ti;
+  while (ti * (ti + 1) / 2 > tix) --ti;
+  const int tj = tix - ti * (ti + 1) / 2;
+  const long long r0 = (long long)ti * TRMV_SLAB, r1 = min(N, r0 + TRMV_SLAB);
+  for (int q = threadIdx.x; q < TRMV_SLAB; q += blockDim.x) us[q] = r0 + q < N ? u[r0 + q] : 0.0;
   __syncthreads();
-  for (long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x; j < r1; j += (long long)gridDim.x * blockDim.x) {
-    double s0 = 0.0, s1 = 0.0;
+  const long long j = (long long)tj * TRMV_SLAB + threadIdx.x;
+  if (j >= r1) return;
+  double s0 = 0.0, s1 = 0.0;
+  if (tj < ti && r1 - r0 == TRMV_SLAB) {
+    // a full tile below the diagonal: no bounds, 32 loads per thread in flight
+    const double *yp = Y + r0 * N + j;
 #pragma unroll
-    for (int q = 0; q < 32; ++q) {
+    for (int h = 0; h < TRMV_SLAB; h += 32) {
+      double y[32];
+#pragma unroll
+      for (int q = 0; q < 32; ++q) y[q] = yp[(long long)(h + q) * N];
+#pragma unroll
+      for (int q = 0; q < 32; ++q) (q & 1 ? s1 : s0) += y[q] * us[h + q];
+    }
+  } else {
+#pragma unroll
+    for (int q = 0; q < TRMV_SLAB; ++q) {
       const long long i = r0 + q;
       if (i >= j && i < r1) (q & 1 ? s1 : s0) += Y[i * N + j] * us[q];
     }
-    const double s = s0 + s1;
-    if (s != 0.0) atomicAdd(&z[j], s);
   }
+  const double s = s0 + s1;
+  if (s != 0.0) atomicAdd(&z[j], s);
 }
 
 // ---------------------------------------------------------------- restriction / prolongation
@@ -932,11 +970,11 @@ void coarse_apply(hplmm_ctx *c, const double *r_pad, double *z_pad) {
   HP_CHECK_LAUNCH();
   // u = Y t, then t <- Y^T u  (A^o)^{-1} = Y^T Y
   double *u = c->w_coarse_u.p;
-  k_trmv_lower<<<grid_for(No * 32, 256), 256, 0, s>>>(c->Linv.p, No, t, u);
+  k_trmv_lower<<<grid_for((No + 1) / 2, 4), 256, 0, s>>>(c->Linv.p, No, t, u);
   HP_CHECK_LAUNCH();
   HP_CUDA(cudaMemsetAsync(t, 0, sizeof(double) * No, s));
-  dim3 gt(grid_for(std::min<long long>(No, 1024), 256), (unsigned)((No + 31) / 32));
-  k_trmv_lower_t<<<gt, 256, 0, s>>>(c->Linv.p, No, u, t);
+  const long long nslab = (No + TRMV_SLAB - 1) / TRMV_SLAB;
+  k_trmv_lower_t<<<(unsigned)(nslab * (nslab + 1) / 2), 64, 0, s>>>(c->Linv.p, No, u, t);
   HP_CHECK_LAUNCH();
   dim3 gp(64, G);
   if (f64)

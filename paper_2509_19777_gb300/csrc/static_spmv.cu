@@ -60,9 +60,15 @@ __global__ void k_na_spmv(const int *row_ptr, const int *col, const double *val,
     int m = col[p];
     const double *v = val + (long long)p * 9;
     double x0 = x[3 * m], x1 = x[3 * m + 1], x2 = x[3 * m + 2];
-    s0 += v[0] * x0 + v[1] * x1 + v[2] * x2;
-    s1 += v[3] * x0 + v[4] * x1 + v[5] * x2;
-    s2 += v[6] * x0 + v[7] * x1 + v[8] * x2;
+    s0 += v[0] * x0;
+    s0 += v[1] * x1;
+    s0 += v[2] * x2;
+    s1 += v[3] * x0;
+    s1 += v[4] * x1;
+    s1 += v[5] * x2;
+    s2 += v[6] * x0;
+    s2 += v[7] * x1;
+    s2 += v[8] * x2;
   }
   y[3 * n] = s0;
   y[3 * n + 1] = s1;
