@@ -246,29 +246,76 @@ __global__ void k_scatter_free(const int *dof_slot, const double *dof, double *p
 }
 
 // ---------------------------------------------------------------- sliced-ELL copy of A_hat for the SpMV
-// Rows are grouped in slices of 32 consecutive nodes (one warp); a slice is padded to its longest row, and
-// stored slot-major with the 9 block entries of a slot element-major, so that every load of the SpMV is one
-// contiguous 128-byte (FP32) or 256-byte (FP64) access across the warp.  Padding slots point at the row's
-// own node with zero values.
-__global__ void k_sell_width(const int *row_ptr, int n_nodes, int n_slices, int *width) {
+// Rows are grouped in slices of 32 (one warp); a slice is padded to its longest row, and stored slot-major
+// with the 9 block entries of a slot element-major, so that every load of the SpMV is one contiguous
+// 128-byte (FP32) or 256-byte (FP64) access across the warp.  Padding slots point at the row's own node with
+// zero values.  The rows are taken longest first within windows of SELL_SIGMA consecutive nodes (sliced ELL
+// with local sorting), so that a slice's rows have nearly equal lengths: on a porous image the node degrees
+// vary, and slices of 32 consecutive nodes padded about 13% of the slots, each an idle FP64 multiply-add.
+constexpr int SELL_SIGMA = 1024;
+
+// perm[window start + position] = node: a stable counting sort of each window's rows by length (longest
+// first), one CTA of SELL_SIGMA threads per window; lengths above 30 share the first bucket
+__global__ void __launch_bounds__(SELL_SIGMA) k_sell_sort(const int *row_ptr, int n_nodes, int *perm) {
+  __shared__ int cnt[32][32];  // [key][warp]: rows of the warp with the key, then the exclusive offsets
+  __shared__ int ksum[32];
+  const int t = threadIdx.x, lane = t & 31, w = t >> 5;
+  const long long n = (long long)blockIdx.x * SELL_SIGMA + t;
+  const int len = n < n_nodes ? row_ptr[n + 1] - row_ptr[n] : -1;
+  const int key = len < 0 ? 31 : 30 - min(len, 30);  // rows past the end sort last and are not written
+  cnt[w][lane] = 0;
+  __syncthreads();
+  const unsigned same = __match_any_sync(0xffffffffu, key);
+  const int rank = __popc(same & ((1u << lane) - 1u));
+  if (rank == 0) cnt[key][w] = __popc(same);
+  __syncthreads();
+  // exclusive scan over the entries in (key, warp) order: thread t holds entry (t / 32, t % 32)
+  const int v = cnt[w][lane];
+  int inc = v;
+  for (int o = 1; o < 32; o <<= 1) {
+    const int y = __shfl_up_sync(0xffffffffu, inc, o);
+    if (lane >= o) inc += y;
+  }
+  if (lane == 31) ksum[w] = inc;
+  __syncthreads();
+  if (w == 0) {
+    const int s0 = ksum[lane];
+    int si = s0;
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(0xffffffffu, si, o);
+      if (lane >= o) si += y;
+    }
+    ksum[lane] = si - s0;
+  }
+  __syncthreads();
+  cnt[w][lane] = inc - v + ksum[w];
+  __syncthreads();
+  if (len >= 0) perm[(long long)blockIdx.x * SELL_SIGMA + cnt[key][w] + rank] = (int)n;
+}
+
+__global__ void k_sell_width(const int *row_ptr, const int *perm, int n_nodes, int n_slices, int *width) {
   int sl = blockIdx.x * blockDim.x + threadIdx.x;
   if (sl >= n_slices) return;
   int w = 0;
-  for (int r = sl * 32; r < min(n_nodes, sl * 32 + 32); ++r) w = max(w, row_ptr[r + 1] - row_ptr[r]);
+  for (int i = sl * 32; i < min(n_nodes, sl * 32 + 32); ++i) {
+    const int r = perm[i];
+    w = max(w, row_ptr[r + 1] - row_ptr[r]);
+  }
   width[sl] = 32 * w;  // entries of the slice
 }
 
-__global__ void k_sell_fill(const int *row_ptr, const int *col, const double *val, int n_nodes,
+__global__ void k_sell_fill(const int *row_ptr, const int *col, const double *val, const int *perm, int n_nodes,
                             const int *slice_off, int *scol, double *sval64, float *sval32) {
   int n = blockIdx.x * blockDim.x + threadIdx.x;
   int sl = n >> 5, lane = n & 31;
   if (sl * 32 >= n_nodes) return;
   long long base = slice_off[sl];
   int w = (slice_off[sl + 1] - slice_off[sl]) / 32;
-  int b = (n < n_nodes) ? row_ptr[n] : 0, len = (n < n_nodes) ? row_ptr[n + 1] - b : 0;
+  const int node = n < n_nodes ? perm[n] : 0;
+  int b = (n < n_nodes) ? row_ptr[node] : 0, len = (n < n_nodes) ? row_ptr[node + 1] - b : 0;
   for (int j = 0; j < w; ++j) {
     long long ent = base + (long long)j * 32 + lane;
-    scol[ent] = (j < len) ? col[b + j] : (n < n_nodes ? n : 0);
+    scol[ent] = (j < len) ? col[b + j] : node;
     for (int e = 0; e < 9; ++e) {
       double v = (j < len) ? val[(long long)(b + j) * 9 + e] : 0.0;
       long long at = (base + (long long)j * 32) * 9 + (long long)e * 32 + lane;
@@ -278,12 +325,15 @@ __global__ void k_sell_fill(const int *row_ptr, const int *col, const double *va
   }
 }
 
-// y = A x (or y = sub - A x when sub != nullptr) on the sliced-ELL copy; one thread per node row
+// y = A x (or y = sub - A x when sub != nullptr) on the sliced-ELL copy; one thread per row position n (node
+// perm[n]).  The FP64 form is bound by the FP64 pipe; 64-thread blocks (about 23 per SM, all resident) keep the
+// SMs' shares of the uneven slices close to one another.
 template <typename T>
-__global__ void k_spmv_sell(const int *slice_off, const int *scol, const T *sval, const double *x, double *y,
-                            const double *sub, int n_nodes) {
+__global__ void k_spmv_sell(const int *slice_off, const int *scol, const T *sval, const int *perm, const double *x,
+                            double *y, const double *sub, int n_nodes) {
   int n = blockIdx.x * blockDim.x + threadIdx.x;
   if (n >= n_nodes) return;
+  const int node = perm[n];
   using A = typename std::conditional<std::is_same<T, double>::value, double, float>::type;
   const int sl = n >> 5, lane = n & 31;
   const long long base = slice_off[sl];
@@ -307,13 +357,13 @@ __global__ void k_spmv_sell(const int *slice_off, const int *scol, const T *sval
     s2 += (A)v[256] * x2;
   }
   if (sub) {
-    y[3 * n] = sub[3 * n] - (double)s0;
-    y[3 * n + 1] = sub[3 * n + 1] - (double)s1;
-    y[3 * n + 2] = sub[3 * n + 2] - (double)s2;
+    y[3 * node] = sub[3 * node] - (double)s0;
+    y[3 * node + 1] = sub[3 * node + 1] - (double)s1;
+    y[3 * node + 2] = sub[3 * node + 2] - (double)s2;
   } else {
-    y[3 * n] = (double)s0;
-    y[3 * n + 1] = (double)s1;
-    y[3 * n + 2] = (double)s2;
+    y[3 * node] = (double)s0;
+    y[3 * node + 1] = (double)s1;
+    y[3 * node + 2] = (double)s2;
   }
 }
 
@@ -408,8 +458,11 @@ void assemble(hplmm_ctx *c, const uint8_t *mask, int nx, int ny, int nz, const f
   // sliced-ELL copies (FP64 and the FP32 shadow) for the SpMV; the CSR FP32 values are then dropped
   {
     int nsl = (int)((nn + 31) / 32);
+    c->sell_perm.alloc(nn);
+    k_sell_sort<<<grid_for(nn, SELL_SIGMA), SELL_SIGMA, 0, s>>>(c->row_ptr.p, c->n_nodes, c->sell_perm.p);
+    HP_CHECK_LAUNCH();
     c->sell_off.alloc(nsl + 1);
-    k_sell_width<<<grid_for(nsl, 256), 256, 0, s>>>(c->row_ptr.p, c->n_nodes, nsl, c->sell_off.p);
+    k_sell_width<<<grid_for(nsl, 256), 256, 0, s>>>(c->row_ptr.p, c->sell_perm.p, c->n_nodes, nsl, c->sell_off.p);
     HP_CHECK_LAUNCH();
     HP_CUDA(cudaMemsetAsync(c->sell_off.p + nsl, 0, sizeof(int), s));
     long long nent = exclusive_scan_i32(c->sell_off.p, c->sell_off.p, nsl + 1, s);
@@ -417,9 +470,9 @@ void assemble(hplmm_ctx *c, const uint8_t *mask, int nx, int ny, int nz, const f
     c->sell_col.alloc(nent);
     c->sell_val64.alloc(nent * 9);
     c->sell_val32.alloc(nent * 9);
-    k_sell_fill<<<grid_for((long long)nsl * 32, 128), 128, 0, s>>>(c->row_ptr.p, c->col.p, c->val64.p, c->n_nodes,
-                                                                   c->sell_off.p, c->sell_col.p, c->sell_val64.p,
-                                                                   c->sell_val32.p);
+    k_sell_fill<<<grid_for((long long)nsl * 32, 128), 128, 0, s>>>(c->row_ptr.p, c->col.p, c->val64.p,
+                                                                   c->sell_perm.p, c->n_nodes, c->sell_off.p,
+                                                                   c->sell_col.p, c->sell_val64.p, c->sell_val32.p);
     HP_CHECK_LAUNCH();
     c->val32.release();
     if (c->opt.apply_prec == HPLMM_BF16) {
@@ -447,19 +500,15 @@ void scatter_free(hplmm_ctx *c, const double *dof, double *pad) {
 
 void spmv(hplmm_ctx *c, const double *x_pad, double *y_pad, hplmm_prec prec, const double *sub) {
   ProfScope ps(c, HPLMM_PH_SPMV);
-  if (prec == HPLMM_BF16) {
-    k_spmv_sell<__nv_bfloat16><<<grid_for(c->n_nodes, 128), 128, 0, c->stream>>>(c->sell_off.p, c->sell_col.p,
-                                                                                  c->sell_val16.p, x_pad, y_pad,
-                                                                                  sub, c->n_nodes);
-  } else if (prec == HPLMM_FP64) {
-    k_spmv_sell<double><<<grid_for(c->n_nodes, 128), 128, 0, c->stream>>>(c->sell_off.p, c->sell_col.p,
-                                                                           c->sell_val64.p, x_pad, y_pad, sub,
-                                                                           c->n_nodes);
-  } else {
-    k_spmv_sell<float><<<grid_for(c->n_nodes, 128), 128, 0, c->stream>>>(c->sell_off.p, c->sell_col.p,
-                                                                          c->sell_val32.p, x_pad, y_pad, sub,
-                                                                          c->n_nodes);
-  }
+  const unsigned grid = grid_for(c->n_nodes, 64);
+  const int *off = c->sell_off.p, *col = c->sell_col.p, *perm = c->sell_perm.p;
+  if (prec == HPLMM_BF16)
+    k_spmv_sell<__nv_bfloat16><<<grid, 64, 0, c->stream>>>(off, col, c->sell_val16.p, perm, x_pad, y_pad, sub,
+                                                            c->n_nodes);
+  else if (prec == HPLMM_FP64)
+    k_spmv_sell<double><<<grid, 64, 0, c->stream>>>(off, col, c->sell_val64.p, perm, x_pad, y_pad, sub, c->n_nodes);
+  else
+    k_spmv_sell<float><<<grid, 64, 0, c->stream>>>(off, col, c->sell_val32.p, perm, x_pad, y_pad, sub, c->n_nodes);
   HP_CHECK_LAUNCH();
 }
 

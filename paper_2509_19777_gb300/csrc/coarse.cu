@@ -240,105 +240,135 @@ __global__ void k_symmetrize(double *A, long long N, double *asym) {
 // ---------------------------------------------------------------- dense FP64 Cholesky (64x64 tiles)
 constexpr int TB = 64;
 
-// Diagonal tile: Cholesky factor L_kk and its inverse W = L_kk^{-1}, one CTA of 256 threads.  One SM's
-// FP64 pipe is the limit (this kernel is on the critical path of the factorisation), so each step issues
-// only the elements it changes:
-//   factor, right-looking, one column per step.  The tile's lower triangle is numbered "column 63 first,
-//   rows ascending within a column" and element e lives in register slot e / 256 of thread e mod 256.  The
-//   trailing triangle of step cc (columns > cc) is then the prefix e < M(cc) = m(m+1)/2, m = 63 - cc, and
-//   column cc the 64 - cc elements after it, so a warp's slot is wholly busy, wholly idle or on the
-//   boundary.  Step cc: the owner of (cc, cc) takes its square root (right after its own update of step
-//   cc - 1), the owners of column cc scale it and publish it in row cc of the shared tile, the owners of the
-//   prefix subtract the rank-1 product;
-//   inverse, right-looking, one step behind the factor in the same phases: step q subtracts L_rq W_qj from
-//   rows r > q, columns j <= q (addressed compactly), and finishes row q + 1 with 1 / L_{q+1,q+1} as it makes
-//   the last update there.  W's strict lower part and the published factor columns (upper part, transposed)
-//   share one shared tile; W's diagonal is rdiag.
-// The tile's padding rows and columns (past N) are the identity, so the steps stay well defined.
-constexpr int PT_NE = TB * (TB + 1) / 2;
-constexpr int PT_SLOTS = (PT_NE + 255) / 256;
+// Diagonal tile: Cholesky factor L_kk and its inverse W = L_kk^{-1}, one CTA of 512 threads.  The kernel is
+// on the critical path of the factorisation and its steps are short, so it is laid out for latency: one
+// block barrier per step, and the pivot's square root off the path of the updates.
+//   factor, right-looking on unscaled columns (a_rc -= a_rq a_cq / d_q): warp 0 holds the diagonal (lane l:
+//   rows l and l + 32); the other 15 warps hold the strictly lower triangle, numbered "column 62 first, rows
+//   ascending within a column", element e in slot e / 480 of owner e mod 480.  The trailing triangle of step q
+//   is then the prefix e < M(q) and column q the 63 - q elements after it, so a warp's slot is wholly busy,
+//   wholly idle or on the boundary.  Phase q: the owners update the prefix with column q (published raw in
+//   row q of the shared tile) and publish column q + 1, which that update completed; warp 0 updates the
+//   diagonal and the lane of row q + 1 takes its pivot (1/sqrt(d) by rsqrt, d / sqrt(d), 1/d) while the
+//   others work;
+//   inverse, right-looking, two phases behind: step q subtracts L_rq W_qj from rows r > q (columns j <= q,
+//   addressed compactly) and finishes row q + 1 with 1/L_{q+1,q+1} as it makes the last update there; it
+//   reads column q scaled, written over the raw one in the phase after the factor used it.
+// The shared tile holds the factor's columns transposed in its upper part (raw, then scaled) and W's strict
+// lower part below; W's diagonal and L's are the pivot arrays.  The tile's padding rows and columns (past
+// N) are the identity, so the steps stay well defined.
+constexpr int PT_THREADS = 512;
+constexpr int PT_OFF = TB * (TB - 1) / 2;                     // strictly lower elements
+constexpr int PT_OWNERS = PT_THREADS - 32;                    // threads of warps 1 ..
+constexpr int PT_SLOTS = (PT_OFF + PT_OWNERS - 1) / PT_OWNERS;  // register slots per owner
 
-__global__ void __launch_bounds__(256) k_potrf_tile(double *A, long long N, int kt, double *Dinv, int *status) {
-  __shared__ double S[TB][TB + 1];  // S[q][r] = L_rq (r > q); S[r][j] = W_rj (r > j)
-  __shared__ double rdiag[TB], ldiag[TB];
-  const int t = threadIdx.x, lane = t & 31, wbase = t & ~31;
+// elements of the columns right of q in the owners' numbering
+__device__ __forceinline__ int pt_prefix(int q) { return q >= TB - 1 ? 0 : (TB - 2 - q) * (TB - 1 - q) / 2; }
+
+__global__ void __launch_bounds__(PT_THREADS) k_potrf_tile(double *A, long long N, int kt, double *Dinv,
+                                                           int *status) {
+  __shared__ double S[TB][TB + 1];  // S[q][r] = column q of the factor at row r > q; S[r][j] = W_rj, r > j
+  __shared__ double prd[TB], piv[TB], pl[TB];  // 1/L_qq, 1/d_q, L_qq
+  const int t = threadIdx.x, lane = t & 31, wid = t >> 5;
+  const int u = t - 32, ub = (wid - 1) * 32;
   const int k0 = kt * TB;
   const int nb = (int)min((long long)TB, N - k0);
-  for (int e = t; e < TB * TB; e += 256) {
+  for (int e = t; e < TB * TB; e += PT_THREADS) {
     const int r = e / TB, c = e % TB;
     if (c <= r) S[r][c] = (r < nb && c < nb) ? A[(long long)(k0 + r) * N + k0 + c] : (r == c ? 1.0 : 0.0);
   }
   __syncthreads();
+  double dg[2] = {0.0, 0.0};
   double a[PT_SLOTS];
   int rs[PT_SLOTS], cs[PT_SLOTS];
 #pragma unroll
   for (int k = 0; k < PT_SLOTS; ++k) {
-    const int e = 256 * k + t;
-    // column j = 63 - c (counted from the right) holds j + 1 elements and starts at j (j + 1) / 2
+    // column j = 62 - c (from the right) holds j + 1 elements, rows c + 1 .. 63, from offset j (j + 1) / 2
+    const int e = wid > 0 ? PT_OWNERS * k + u : 0;
     int j = (int)((sqrtf(8.0f * (float)e + 1.0f) - 1.0f) * 0.5f);
-    while (j * (j + 1) / 2 > e) --j;
+    while (j > 0 && j * (j + 1) / 2 > e) --j;
     while ((j + 1) * (j + 2) / 2 <= e) ++j;
-    cs[k] = TB - 1 - j;
-    rs[k] = cs[k] + e - j * (j + 1) / 2;
-    a[k] = e < PT_NE ? S[rs[k]][cs[k]] : 0.0;
+    cs[k] = TB - 2 - j;
+    rs[k] = cs[k] + 1 + e - j * (j + 1) / 2;
+    a[k] = (wid > 0 && e < PT_OFF) ? S[rs[k]][cs[k]] : 0.0;
+  }
+  if (wid == 0) {
+    dg[0] = S[lane][lane];
+    dg[1] = S[lane + 32][lane + 32];
   }
   __syncthreads();
-  for (int e = t; e < TB * TB; e += 256) {
+  for (int e = t; e < TB * TB; e += PT_THREADS) {
     const int r = e / TB, c = e % TB;
     if (c < r) S[r][c] = 0.0;
   }
-  auto diag = [&](int cc) {
-    const int e = (TB - 1 - cc) * (TB - cc) / 2;
-    if ((e & 255) == t) {
-      const int kd = e >> 8;
-      double d = 0.0;
-#pragma unroll
-      for (int k = 0; k < PT_SLOTS; ++k) d = (k == kd) ? a[k] : d;
-      if (!(d > 0.0)) {
-        if (atomicCAS(status, 0, (int)HPLMM_ERR_SINGULAR) == 0) {
-          status[1] = 3;
-          status[2] = 0;
-          status[3] = k0 + cc;
-        }
-        d = 1.0;
+  auto pivot = [&](int q, double d) {
+    if (!(d > 0.0)) {
+      if (atomicCAS(status, 0, (int)HPLMM_ERR_SINGULAR) == 0) {
+        status[1] = 3;
+        status[2] = 0;
+        status[3] = k0 + q;
       }
-      const double sd = sqrt(d);
-#pragma unroll
-      for (int k = 0; k < PT_SLOTS; ++k) a[k] = (k == kd) ? sd : a[k];
-      ldiag[cc] = sd;
-      rdiag[cc] = 1.0 / sd;
+      d = 1.0;
     }
+    const double r = rsqrt(d);
+    prd[q] = r;
+    piv[q] = r * r;
+    pl[q] = d * r;
   };
-  diag(0);
-  __syncthreads();
-  for (int cc = 0; cc < TB; ++cc) {
-    const int M = (TB - 1 - cc) * (TB - cc) / 2;
-    // column cc below the diagonal: scale and publish
-    const int lo = M + 1, hi = M + TB - 1 - cc;
-    const double rd = rdiag[cc];
+  // column 0 raw and its pivot
+  if (wid > 0) {
+    const int lo = pt_prefix(0);
 #pragma unroll
     for (int k = 0; k < PT_SLOTS; ++k) {
-      const int eb = 256 * k + wbase;
-      if (eb <= hi && eb + 31 >= lo) {
-        const int e = eb + lane;
-        if (e >= lo && e <= hi) {
-          a[k] *= rd;
-          S[cc][rs[k]] = a[k];
+      const int e = PT_OWNERS * k + u;
+      if (e >= lo && e < lo + TB - 1) S[0][rs[k]] = a[k];
+    }
+  } else if (lane == 0) {
+    pivot(0, dg[0]);
+  }
+  __syncthreads();
+  for (int cc = 0; cc <= TB; ++cc) {
+    if (cc < TB) {
+      const double iv = piv[cc];
+      if (wid == 0) {
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          const int r = lane + 32 * h;
+          if (r > cc) {
+            const double v = S[cc][r];
+            dg[h] -= (v * iv) * v;
+          }
+        }
+        if (cc + 1 < TB && lane == ((cc + 1) & 31)) pivot(cc + 1, cc + 1 < 32 ? dg[0] : dg[1]);
+      } else {
+        const int M = pt_prefix(cc), Mn = pt_prefix(cc + 1);
+        const double rd = prd[cc];
+#pragma unroll
+        for (int k = 0; k < PT_SLOTS; ++k) {
+          const int eb = PT_OWNERS * k + ub, e = eb + lane;
+          if (eb < M && e < M) {
+            const double p = S[cc][rs[k]] * iv;
+            a[k] -= p * S[cc][cs[k]];
+            if (e >= Mn) S[cc + 1][rs[k]] = a[k];  // column cc + 1 is complete: publish it raw
+          }
+          if (eb + 31 >= M && eb < M + TB - 1 - cc && e >= M && e < M + TB - 1 - cc) a[k] *= rd;  // column cc
         }
       }
     }
-    __syncthreads();
-    // trailing triangle of the factor
+    if (wid > 0 && cc >= 1) {
+      // column cc - 1 scaled, over its raw copy (read by the factor in the previous phase)
+      const int q = cc - 1, lo = pt_prefix(q), hi = lo + TB - 1 - q;
 #pragma unroll
-    for (int k = 0; k < PT_SLOTS; ++k) {
-      const int eb = 256 * k + wbase;
-      if (eb < M && eb + lane < M) a[k] -= S[cc][rs[k]] * S[cc][cs[k]];
+      for (int k = 0; k < PT_SLOTS; ++k) {
+        const int eb = PT_OWNERS * k + ub, e = eb + lane;
+        if (eb + 31 >= lo && eb < hi && e >= lo && e < hi) S[q][rs[k]] = a[k];
+      }
     }
-    // inverse step q = cc - 1
-    if (cc >= 1) {
-      const int q = cc - 1, ncol = q + 1, cnt = (TB - 1 - q) * ncol;
-      const double rq = rdiag[q], rn = rdiag[q + 1];
-      for (int e = t; e < cnt; e += 256) {
+    if (wid > 0 && cc >= 2) {
+      // inverse step q = cc - 2
+      const int q = cc - 2, ncol = q + 1, cnt = (TB - 1 - q) * ncol;
+      const double rq = prd[q], rn = prd[q + 1];
+      for (int e = u; e < cnt; e += PT_OWNERS) {
         const int ro = e / ncol, j = e - ro * ncol, r = q + 1 + ro;
         const double wq = (j == q) ? rq : S[q][j];
         double v = S[r][j] - S[q][r] * wq;
@@ -346,16 +376,15 @@ __global__ void __launch_bounds__(256) k_potrf_tile(double *A, long long N, int 
         S[r][j] = v;
       }
     }
-    if (cc + 1 < TB) diag(cc + 1);
     __syncthreads();
   }
-  // the factor and the inverse out, row-major; padding rows of the factor are identity rows, so rdiag is 1
-  // there and W stays the identity
-  for (int e = t; e < TB * TB; e += 256) {
+  // the factor and the inverse out, row-major; padding rows of the factor are identity rows, so their
+  // pivots are 1 and W stays the identity there
+  for (int e = t; e < TB * TB; e += PT_THREADS) {
     const int r = e / TB, c = e % TB;
     const bool in = r < nb && c < nb;
-    if (in) A[(long long)(k0 + r) * N + k0 + c] = c < r ? S[c][r] : (c == r ? ldiag[r] : 0.0);
-    Dinv[(long long)kt * TB * TB + e] = in ? (c < r ? S[r][c] : (c == r ? rdiag[r] : 0.0)) : 0.0;
+    if (in) A[(long long)(k0 + r) * N + k0 + c] = c < r ? S[c][r] : (c == r ? pl[r] : 0.0);
+    Dinv[(long long)kt * TB * TB + e] = in ? (c < r ? S[r][c] : (c == r ? prd[r] : 0.0)) : 0.0;
   }
 }
 
@@ -911,7 +940,7 @@ void build_coarse(hplmm_ctx *c, const double *b_corr) {
     if (!c->ev_join) HP_CUDA(cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming));
     cudaStream_t s2 = c->aux_stream;
     for (int kt = 0; kt < T; ++kt) {
-      k_potrf_tile<<<1, 256, 0, s>>>(c->Lo.p, No, kt, c->Lo_dinv.p, c->status.p);
+      k_potrf_tile<<<1, PT_THREADS, 0, s>>>(c->Lo.p, No, kt, c->Lo_dinv.p, c->status.p);
       HP_CHECK_LAUNCH();
       int m = T - kt - 1;
       if (m > 0) {

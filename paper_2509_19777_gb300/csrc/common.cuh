@@ -168,7 +168,8 @@ struct hplmm_ctx {
   long long nnzb = 0;
   hp::Buf<double> val64;           // nnzb*9, fixed rows/cols zeroed
   hp::Buf<float> val32;            // FP32 shadow (assembly only; released once the sliced copy exists)
-  hp::Buf<int> sell_off;           // sliced ELL (32-node slices): entry offset of each slice, n_slices+1
+  hp::Buf<int> sell_perm;          // sliced ELL: node of each row position (longest rows first per window)
+  hp::Buf<int> sell_off;           // sliced ELL (32-row slices): entry offset of each slice, n_slices+1
   hp::Buf<int> sell_col;           // block column per entry (slot-major within a slice)
   hp::Buf<double> sell_val64;      // 9 values per entry, element-major within a slot
   hp::Buf<float> sell_val32;
