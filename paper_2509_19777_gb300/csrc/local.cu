@@ -889,53 +889,63 @@ __device__ void m32_sweep(Multi32Ctx &m) {
 #pragma unroll
         for (int cc = 0; cc < NB; ++cc) vec[cc] = m.Yb[cc][lane];
       }
-      // window rows of this chunk, two per warp iteration (the second clamped to a valid row and masked)
+      // window rows of this chunk, four per warp iteration (rows r + 8i; past the end clamped to row r and
+      // masked), so that each warp has four independent rows of work in flight
       const int lo = max(row0, nb), hi = min(row0 + rows, R);
       int r = lo + wid;
       int slot = ring_slot(k0 + r, m.XR);  // advanced incrementally below
-      for (; r < hi; r += 2 * SM32_NW) {
-        const bool okb = r + SM32_NW < hi;
-        const int rb = okb ? r + SM32_NW : r;
-        int slotb = slot + SM32_NW;
-        if (slotb >= m.XR) slotb -= m.XR;
-        if (!okb) slotb = slot;
-        const float *la = Lc + (size_t)(r - row0) * NB;
-        const float *lb = Lc + (size_t)(rb - row0) * NB;
-        float *xa = m.Xw + (size_t)slot * NB + lane;
-        float *xb = m.Xw + (size_t)slotb * NB + lane;
+      for (; r < hi; r += 4 * SM32_NW) {
+        const float *lr[4];
+        float *xr[4];
+        bool ok[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          ok[i] = r + i * SM32_NW < hi;
+          int si = slot + i * SM32_NW;
+          if (si >= m.XR) si -= m.XR;
+          if (!ok[i]) si = slot;
+          lr[i] = Lc + (size_t)((ok[i] ? r + i * SM32_NW : r) - row0) * NB;
+          xr[i] = m.Xw + (size_t)si * NB + lane;
+        }
         if (DIR == 0) {
           // X_r -= L_r . Y
-          float a0 = 0.f, a1 = 0.f, b0 = 0.f, b1 = 0.f;
+          float acc[4][2];
+#pragma unroll
+          for (int i = 0; i < 4; ++i) acc[i][0] = acc[i][1] = 0.f;
 #pragma unroll
           for (int g = 0; g < 8; ++g) {
-            float4 l4 = *reinterpret_cast<const float4 *>(la + 4 * g);
-            float4 m4 = *reinterpret_cast<const float4 *>(lb + 4 * g);
-            a0 = fmaf(l4.x, vec[4 * g], a0);
-            a1 = fmaf(l4.y, vec[4 * g + 1], a1);
-            a0 = fmaf(l4.z, vec[4 * g + 2], a0);
-            a1 = fmaf(l4.w, vec[4 * g + 3], a1);
-            b0 = fmaf(m4.x, vec[4 * g], b0);
-            b1 = fmaf(m4.y, vec[4 * g + 1], b1);
-            b0 = fmaf(m4.z, vec[4 * g + 2], b0);
-            b1 = fmaf(m4.w, vec[4 * g + 3], b1);
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+              const float4 l4 = *reinterpret_cast<const float4 *>(lr[i] + 4 * g);
+              acc[i][0] = fmaf(l4.x, vec[4 * g], acc[i][0]);
+              acc[i][1] = fmaf(l4.y, vec[4 * g + 1], acc[i][1]);
+              acc[i][0] = fmaf(l4.z, vec[4 * g + 2], acc[i][0]);
+              acc[i][1] = fmaf(l4.w, vec[4 * g + 3], acc[i][1]);
+            }
           }
-          const float xav = *xa, xbv = *xb;
-          *xa = xav - (a0 + a1);
-          if (okb) *xb = xbv - (b0 + b1);
+#pragma unroll
+          for (int i = 0; i < 4; ++i) {
+            const float xv = *xr[i];
+            if (ok[i]) *xr[i] = xv - (acc[i][0] + acc[i][1]);
+          }
         } else {
-          // column sums L_r^T X_r
-          const float xr = *xa, xs = okb ? *xb : 0.f;
+          // column sums L_r^T X_r, rows in ascending order
+          float xv[4];
+#pragma unroll
+          for (int i = 0; i < 4; ++i) xv[i] = ok[i] ? *xr[i] : 0.f;
 #pragma unroll
           for (int g = 0; g < 8; ++g) {
-            float4 l4 = *reinterpret_cast<const float4 *>(la + 4 * g);
-            float4 m4 = *reinterpret_cast<const float4 *>(lb + 4 * g);
-            vec[4 * g] = fmaf(m4.x, xs, fmaf(l4.x, xr, vec[4 * g]));
-            vec[4 * g + 1] = fmaf(m4.y, xs, fmaf(l4.y, xr, vec[4 * g + 1]));
-            vec[4 * g + 2] = fmaf(m4.z, xs, fmaf(l4.z, xr, vec[4 * g + 2]));
-            vec[4 * g + 3] = fmaf(m4.w, xs, fmaf(l4.w, xr, vec[4 * g + 3]));
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+              const float4 l4 = *reinterpret_cast<const float4 *>(lr[i] + 4 * g);
+              vec[4 * g] = fmaf(l4.x, xv[i], vec[4 * g]);
+              vec[4 * g + 1] = fmaf(l4.y, xv[i], vec[4 * g + 1]);
+              vec[4 * g + 2] = fmaf(l4.z, xv[i], vec[4 * g + 2]);
+              vec[4 * g + 3] = fmaf(l4.w, xv[i], vec[4 * g + 3]);
+            }
           }
         }
-        slot += 2 * SM32_NW;
+        slot += 4 * SM32_NW;
         while (slot >= m.XR) slot -= m.XR;
       }
       if (DIR == 1 && c == 0) {
