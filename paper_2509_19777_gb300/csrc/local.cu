@@ -40,6 +40,19 @@ __device__ __forceinline__ void cp_async16(void *dst, const void *src) {
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+// rank of this CTA in its cluster, and a barrier over every thread of the cluster with release/acquire
+// ordering of the memory operations before and after it (not warp-aligned: lanes may be diverged)
+__device__ __forceinline__ uint32_t cluster_rank() {
+  uint32_t r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+  return r;
+}
+__device__ __forceinline__ void cluster_sync_all() {
+  asm volatile("barrier.cluster.arrive.release;\n\tbarrier.cluster.wait.acquire;" ::: "memory");
+}
+// the two halves of that barrier, for work in between
+__device__ __forceinline__ void cluster_arrive() { asm volatile("barrier.cluster.arrive.release;" ::: "memory"); }
+__device__ __forceinline__ void cluster_wait() { asm volatile("barrier.cluster.wait.acquire;" ::: "memory"); }
 // wait until at most n of this thread's most recent cp.async groups are pending (n small, runtime)
 __device__ __forceinline__ void cp_async_wait_pending(int n) {
   switch (n) {
@@ -450,6 +463,11 @@ __device__ __forceinline__ void mma_tf32(float (&d)[4], const uint32_t (&a)[4], 
 //   5. the trailing update A_ij -= L_i . L_j of the (R-32)^2 lower window is done in 32x32 warp tiles on
 //      the tensor cores (split-TF32 MMAs, FP32 accuracy), the tile's old values fetched into the warp's
 //      staging area by cp.async before the arithmetic.
+// CL = 2 (sets with at most half as many problems as SMs, where one SM per problem would leave most SMs
+// idle): a cluster of two CTAs per problem.  Both CTAs load the panel and compute steps 2-3 (the same
+// arithmetic on the same data, so the same values); rank 0 writes the panel back; the trailing tiles
+// alternate between the two; a cluster barrier (release / acquire) ends each panel, so the next panel's
+// loads, which read L2 only, see both CTAs' tile updates.  The factor is bit-identical to CL = 1.
 constexpr int CHOL32_THREADS = 512;
 constexpr int CHOL32_LD = 36;
 // row stride of a warp's staged 32x32 trailing tile: with 40 floats, the 8-byte pairs each lane reads in
@@ -457,6 +475,7 @@ constexpr int CHOL32_LD = 36;
 // half-warp, where a stride of 32 put 8 lanes on every bank
 constexpr int CHOL32_CST_LD = 40;
 
+template <int CL>
 __global__ void __launch_bounds__(CHOL32_THREADS, 1) k_band_chol32(const int *order, int count, int *queue,
                                                                 const int *nloc, const int *bwv,
                                                                 const long long *band_off, float *band, int *status,
@@ -469,11 +488,18 @@ __global__ void __launch_bounds__(CHOL32_THREADS, 1) k_band_chol32(const int *or
   __shared__ int s_job;
   float *Cst = P + (size_t)(NB + bwv_max) * LD;  // per-warp 32x32 staging of the trailing tiles (row stride 40)
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = CHOL32_THREADS / 32;
-  for (;;) {
-    if (threadIdx.x == 0) s_job = atomicAdd(queue, 1);
-    __syncthreads();
-    const int job = s_job;
-    __syncthreads();
+  const int rank = CL == 2 ? (int)cluster_rank() : 0;
+  for (int round = 0;; ++round) {
+    int job;
+    if constexpr (CL == 1) {
+      if (threadIdx.x == 0) s_job = atomicAdd(queue, 1);
+      __syncthreads();
+      job = s_job;
+      __syncthreads();
+    } else {
+      if (round > 0) return;
+      job = blockIdx.x / CL;  // both CTAs of a cluster: the same problem, the same control flow
+    }
     if (job >= count) return;
     const int k = order[job];
     const int N = nloc[k], bw = bwv[k];
@@ -488,18 +514,22 @@ __global__ void __launch_bounds__(CHOL32_THREADS, 1) k_band_chol32(const int *or
       {
         const float4 *src = reinterpret_cast<const float4 *>(Bp);
         const int n4 = R * 8;
+        // the other CTA of a cluster updated some of these rows: read them from L2
+        auto ld4 = [&](int i) { return CL == 2 ? __ldcg(src + i) : src[i]; };
         int e = threadIdx.x;
         for (; e + 3 * CHOL32_THREADS < n4; e += 4 * CHOL32_THREADS) {
-          float4 v0 = src[e], v1 = src[e + CHOL32_THREADS], v2 = src[e + 2 * CHOL32_THREADS],
-                 v3 = src[e + 3 * CHOL32_THREADS];
+          float4 v0 = ld4(e), v1 = ld4(e + CHOL32_THREADS), v2 = ld4(e + 2 * CHOL32_THREADS),
+                 v3 = ld4(e + 3 * CHOL32_THREADS);
           *reinterpret_cast<float4 *>(P + (e >> 3) * LD + (e & 7) * 4) = v0;
           int e1 = e + CHOL32_THREADS, e2 = e + 2 * CHOL32_THREADS, e3 = e + 3 * CHOL32_THREADS;
           *reinterpret_cast<float4 *>(P + (e1 >> 3) * LD + (e1 & 7) * 4) = v1;
           *reinterpret_cast<float4 *>(P + (e2 >> 3) * LD + (e2 & 7) * 4) = v2;
           *reinterpret_cast<float4 *>(P + (e3 >> 3) * LD + (e3 & 7) * 4) = v3;
         }
-        for (; e < n4; e += CHOL32_THREADS) *reinterpret_cast<float4 *>(P + (e >> 3) * LD + (e & 7) * 4) = src[e];
+        for (; e < n4; e += CHOL32_THREADS) *reinterpret_cast<float4 *>(P + (e >> 3) * LD + (e & 7) * 4) = ld4(e);
       }
+      // this CTA has read the panel, which rank 0 overwrites in step 4 (the wait comes after steps 2-3)
+      if constexpr (CL == 2) cluster_arrive();
       __syncthreads();
       // 2. diagonal block (warp 0)
       if (wid == 0) {
@@ -582,7 +612,8 @@ __global__ void __launch_bounds__(CHOL32_THREADS, 1) k_band_chol32(const int *or
       }
       __syncthreads();
       // 4. write the panel back: inv(L_kk) in the first NB rows, then the L rows
-      {
+      if constexpr (CL == 2) cluster_wait();
+      if (rank == 0) {
         float4 *dst = reinterpret_cast<float4 *>(Bp);
         for (int e = threadIdx.x; e < R * 8; e += CHOL32_THREADS) {
           const int rr = e >> 3, g = e & 7;
@@ -596,7 +627,7 @@ __global__ void __launch_bounds__(CHOL32_THREADS, 1) k_band_chol32(const int *or
       const int nt = (Wn + 31) / 32;
       const int ntiles = nt * (nt + 1) / 2;
       float *cst = Cst + (size_t)wid * 32 * CHOL32_CST_LD;
-      for (int t = wid; t < ntiles; t += nw) {
+      for (int t = wid * CL + rank; t < ntiles; t += nw * CL) {
         int tj = 0, rem = t;
         while (rem >= nt - tj) {
           rem -= nt - tj;
@@ -670,7 +701,10 @@ __global__ void __launch_bounds__(CHOL32_THREADS, 1) k_band_chol32(const int *or
             }
         __syncwarp();
       }
-      __syncthreads();
+      if constexpr (CL == 2)
+        cluster_sync_all();
+      else
+        __syncthreads();
     }
   }
 }
@@ -1141,12 +1175,7 @@ __device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t by
       : "memory");
 }
 
-// ---- two-CTA clusters: rank, shared-memory addresses in the other CTA, remote stores and arrivals
-__device__ __forceinline__ uint32_t cluster_rank() {
-  uint32_t r;
-  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
-  return r;
-}
+// ---- two-CTA clusters: shared-memory addresses in the other CTA, remote stores and arrivals
 __device__ __forceinline__ uint32_t peer_addr(const void *p, uint32_t rank) {
   uint32_t a;
   asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(a) : "r"(smem_u32(p)), "r"(rank));
@@ -1166,10 +1195,6 @@ __device__ __forceinline__ void st_async_peer(uint32_t addr, double v, uint32_t 
   asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.f64 [%0], %1, [%2];" ::"r"(addr), "d"(v),
                "r"(bar)
                : "memory");
-}
-// every thread of both CTAs (not warp-aligned: the producer lanes may be diverged)
-__device__ __forceinline__ void cluster_sync_all() {
-  asm volatile("barrier.cluster.arrive.release;\n\tbarrier.cluster.wait.acquire;" ::: "memory");
 }
 // 16-byte group loads of a stored factor row, converted to the compute type
 template <typename S> struct Vec16;
@@ -1865,9 +1890,29 @@ void layout_and_factor(hplmm_ctx *c, LocalSet &S, int where, cudaStream_t s, boo
         ((size_t)(NB + bwmax) * CHOL32_LD + (size_t)(CHOL32_THREADS / 32) * 32 * CHOL32_CST_LD) * sizeof(float);
     HP_REQUIRE(smem32 <= 216 * 1024, HPLMM_ERR_INVALID,
                "local problem half bandwidth " + std::to_string(bwmax) + " is too large; use smaller grain grids");
-    HP_CUDA(cudaFuncSetAttribute(k_band_chol32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem32));
-    k_band_chol32<<<grid, CHOL32_THREADS, smem32, s>>>(S.order.p, K, queue, S.n.p, S.bw.p, S.band_off.p, band,
-                                                       c->status.p, where, bwmax);
+    if (2 * K <= num_sms()) {
+      // few problems: a two-CTA cluster each, in cost order
+      HP_CUDA(cudaFuncSetAttribute(k_band_chol32<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem32));
+      cudaLaunchConfig_t cfg = {};
+      cfg.gridDim = dim3((unsigned)(2 * K));
+      cfg.blockDim = dim3(CHOL32_THREADS);
+      cfg.dynamicSmemBytes = smem32;
+      cfg.stream = s;
+      cudaLaunchAttribute at[1];
+      at[0].id = cudaLaunchAttributeClusterDimension;
+      at[0].val.clusterDim.x = 2;
+      at[0].val.clusterDim.y = 1;
+      at[0].val.clusterDim.z = 1;
+      cfg.attrs = at;
+      cfg.numAttrs = 1;
+      HP_CUDA(cudaLaunchKernelEx(&cfg, k_band_chol32<2>, (const int *)S.order.p, K, queue, (const int *)S.n.p,
+                                 (const int *)S.bw.p, (const long long *)S.band_off.p, band, c->status.p, where,
+                                 bwmax));
+    } else {
+      HP_CUDA(cudaFuncSetAttribute(k_band_chol32<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem32));
+      k_band_chol32<1><<<grid, CHOL32_THREADS, smem32, s>>>(S.order.p, K, queue, S.n.p, S.bw.p, S.band_off.p,
+                                                            band, c->status.p, where, bwmax);
+    }
   } else {
     auto kern = k_band_chol<T, NB>;
     HP_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
