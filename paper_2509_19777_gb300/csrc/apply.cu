@@ -84,10 +84,11 @@ __device__ void reduce_blocks(double (&acc)[CAP], int nv, double *partial, doubl
   if (threadIdx.x == 0) *counter = 0u;
 }
 
-// out[j] = V_j . w for j < nv <= CAP (accumulators in registers), U elements per thread per pass so that
-// about CAP x U loads are in flight per thread.  The loads are branch-free: slots j >= nv read vector nv-1
-// again (the same addresses, served by L1) and their sums are discarded; elements past n are clamped to
-// n-1 with a zero weight.
+// out[j] = V_j . w for j < nv <= CAP (accumulators in registers), U elements per thread per pass.  The
+// grid-stride loop is software-pipelined: the next pass's CAP x U loads are issued before this pass's
+// multiply-adds, which do not depend on them, so a thread always has a full pass of loads in flight.  The
+// loads are branch-free: slots j >= nv read vector nv-1 again (the same addresses, served by L1) and their
+// sums are discarded; elements past n are clamped to n-1 with a zero weight.
 template <int CAP, int U>
 __global__ void __launch_bounds__(256) k_cgs_dot(const double *V, long long ldv, int nv, const double *w, long long n,
                                                  double *partial, double *out, unsigned *counter) {
@@ -95,19 +96,32 @@ __global__ void __launch_bounds__(256) k_cgs_dot(const double *V, long long ldv,
 #pragma unroll
   for (int j = 0; j < CAP; ++j) acc[j] = 0.0;
   const long long stride = (long long)gridDim.x * blockDim.x;
-  for (long long i0 = (long long)blockIdx.x * blockDim.x + threadIdx.x; i0 < n; i0 += U * stride) {
-    double wv[U];
-    long long ii[U];
+  auto load = [&](long long i0, double (&v)[U][CAP], double (&wv)[U]) {
 #pragma unroll
     for (int u = 0; u < U; ++u) {
       const long long i = i0 + u * stride;
-      ii[u] = i < n ? i : n - 1;
-      wv[u] = i < n ? w[ii[u]] : 0.0;
+      const long long ii = i < n ? i : n - 1;
+      wv[u] = i < n ? w[ii] : 0.0;
+#pragma unroll
+      for (int j = 0; j < CAP; ++j) v[u][j] = V[(long long)min(j, nv - 1) * ldv + ii];
     }
+  };
+  long long i0 = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  double v[U][CAP], wv[U];
+  load(i0, v, wv);
+  for (; i0 < n; i0 += U * stride) {
+    double vn[U][CAP], wn[U];
+    load(i0 + U * stride, vn, wn);
 #pragma unroll
     for (int u = 0; u < U; ++u)
 #pragma unroll
-      for (int j = 0; j < CAP; ++j) acc[j] += V[(long long)min(j, nv - 1) * ldv + ii[u]] * wv[u];
+      for (int j = 0; j < CAP; ++j) acc[j] += v[u][j] * wv[u];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      wv[u] = wn[u];
+#pragma unroll
+      for (int j = 0; j < CAP; ++j) v[u][j] = vn[u][j];
+    }
   }
   reduce_blocks<CAP>(acc, nv, partial, out, counter);
 }
