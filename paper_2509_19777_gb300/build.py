@@ -7,7 +7,9 @@ static CUDA runtime into one C-ABI shared object beside this file.
 from __future__ import annotations
 
 import concurrent.futures as cf
+import hashlib
 import os
+import platform
 import shutil
 import subprocess
 import sys
@@ -15,8 +17,9 @@ import sys
 HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "libhplmm.so")
+STAMP = OUT + ".sha256"
 BUILD_DIR = os.path.join(HERE, "_build")
-SOURCES = ["prims.cu", "assemble.cu", "maps.cu", "local.cu", "coarse.cu", "apply.cu", "capi.cu", "static_spmv.cu",
+SOURCES = ["prims.cu", "assemble.cu", "maps.cu", "local.cu", "coarse.cu", "cfactor.cu", "apply.cu", "capi.cu", "static_spmv.cu",
            "ws.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr"]
@@ -42,15 +45,30 @@ def _compile(src, extra):
     return obj, r.stderr
 
 
+def source_hash():
+    """SHA-256 over the sources, headers, compiler flags and this machine's architecture: the identity of a
+    build.  A library copied from another machine or built from other sources never matches it."""
+    h = hashlib.sha256()
+    files = [os.path.join(CSRC, s) for s in SOURCES]
+    files += sorted(os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".cuh", ".h")))
+    files.append(os.path.join(os.path.dirname(HERE), "include", "hplmm.h"))
+    for p in files:
+        h.update(os.path.basename(p).encode())
+        with open(p, "rb") as f:
+            h.update(f.read())
+    h.update(" ".join(ARCH + FLAGS).encode())
+    h.update(platform.machine().encode())
+    return h.hexdigest()
+
+
 def build_library(verbose=False, ptxas_info=False, force=False):
-    """Build libhplmm.so if any source is newer than it (or force)."""
-    srcs = [os.path.join(CSRC, s) for s in SOURCES]
-    hdrs = [os.path.join(CSRC, h) for h in os.listdir(CSRC) if h.endswith((".cuh", ".h"))]
-    hdrs.append(os.path.join(os.path.dirname(HERE), "include", "hplmm.h"))
-    if not force and os.path.exists(OUT):
-        newest = max(os.path.getmtime(p) for p in srcs + hdrs)
-        if os.path.getmtime(OUT) >= newest:
-            return OUT
+    """Build libhplmm.so unless the library beside this file was built from exactly these sources on this
+    kind of machine (a hash of them is recorded next to it), or always when force is set."""
+    want = source_hash()
+    if not force and os.path.exists(OUT) and os.path.exists(STAMP):
+        with open(STAMP) as f:
+            if f.read().strip() == want:
+                return OUT
     os.makedirs(BUILD_DIR, exist_ok=True)
     extra = ["-Xptxas", "-v"] if ptxas_info else []
     with cf.ThreadPoolExecutor(max_workers=min(len(SOURCES), os.cpu_count() or 4)) as ex:
@@ -65,6 +83,8 @@ def build_library(verbose=False, ptxas_info=False, force=False):
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
     os.replace(tmp, OUT)
+    with open(STAMP, "w") as f:
+        f.write(want + "\n")
     return OUT
 
 

@@ -266,6 +266,9 @@ void check_status(hplmm_ctx *c) {
                             std::to_string(w[3]) + "): the matrix is singular or not positive definite");
     }
     if (code == HPLMM_ERR_TIMEOUT) throw Error(code, "a device-side wait ran out of its budget");
+    if (code == HPLMM_ERR_INVALID && w[1] == 4)
+      throw Error(code, "coarse factor: coarse column " + std::to_string(w[3]) + " is missing from front " +
+                            std::to_string(w[2]) + " (inconsistent symbolic analysis)");
     throw Error(HPLMM_ERR_CUDA, "device error word " + std::to_string(st));
   }
 }

@@ -99,6 +99,7 @@ void alloc_work(hplmm_ctx *c) {
   long long No = std::max<long long>(c->n_coarse, 1);
   c->w_coarse_t.alloc(No);
   c->w_coarse_u.alloc(No);
+  c->w_coarse_y.alloc(No);
   int m = c->opt.restart;
   c->V.alloc((size_t)(m + 1) * L);
   c->Z.alloc((size_t)m * L);
@@ -345,6 +346,9 @@ hplmm_status hplmm_get_coarse_matrix(hplmm_ctx *c, double *A_o) {
   return guarded(c, [&] {
     require_setup(c);
     HP_REQUIRE(A_o, HPLMM_ERR_INVALID, "get_coarse_matrix: null output");
+    HP_REQUIRE(c->dense_ao || c->n_coarse == 0, HPLMM_ERR_INVALID,
+               "get_coarse_matrix: the dense A^o is kept only for N^o <= 12288 (this set-up has " +
+                   std::to_string(c->n_coarse) + ")");
     size_t bytes = sizeof(double) * (size_t)c->n_coarse * (size_t)c->n_coarse;
     if (bytes) HP_CUDA(cudaMemcpyAsync(A_o, c->Ao.p, bytes, cudaMemcpyDeviceToDevice, c->stream));
     HP_CUDA(cudaStreamSynchronize(c->stream));

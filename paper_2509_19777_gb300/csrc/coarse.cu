@@ -188,7 +188,7 @@ __global__ void k_gal_Y(const int *gbox, const long long *gal_off, const int *kg
 template <typename T>
 __global__ void __launch_bounds__(256) k_gal_gemm(const int *tiles, const int *gbox, const long long *gal_off,
                                                   const int *kg, const int *gcol_off, const int *gcol, const T *P,
-                                                  const T *Y, double *Ao, long long No) {
+                                                  const T *Y, CFView cf, double *Ao, long long No) {
   __shared__ T Ps[32][33];
   __shared__ T Ys[32][33];
   int g = tiles[3 * blockIdx.x], a0 = tiles[3 * blockIdx.x + 1], b0 = tiles[3 * blockIdx.x + 2];
@@ -222,7 +222,10 @@ __global__ void __launch_bounds__(256) k_gal_gemm(const int *tiles, const int *g
   for (int i = 0; i < 2; ++i)
     for (int j = 0; j < 2; ++j) {
       int a = a0 + ty + 16 * i, bb = b0 + tx + 16 * j;
-      if (a < k && bb < k) atomicAdd(&Ao[(long long)gc[a] * No + gc[bb]], (double)acc[i][j]);
+      if (a < k && bb < k) {
+        cf_add(cf, gc[a], gc[bb], (double)acc[i][j]);
+        if (Ao) atomicAdd(&Ao[(long long)gc[a] * No + gc[bb]], (double)acc[i][j]);
+      }
     }
 }
 
@@ -237,371 +240,13 @@ __global__ void k_symmetrize(double *A, long long N, double *asym) {
   A[j * N + i] = m;
 }
 
-// ---------------------------------------------------------------- dense FP64 Cholesky (64x64 tiles)
-constexpr int TB = 64;
-
-// Diagonal tile: Cholesky factor L_kk and its inverse W = L_kk^{-1}, one CTA of 512 threads.  The kernel is
-// on the critical path of the factorisation and its steps are short, so it is laid out for latency: one
-// block barrier per step, and the pivot's square root off the path of the updates.
-//   factor, right-looking on unscaled columns (a_rc -= a_rq a_cq / d_q): warp 0 holds the diagonal (lane l:
-//   rows l and l + 32); the other 15 warps hold the strictly lower triangle, numbered "column 62 first, rows
-//   ascending within a column", element e in slot e / 480 of owner e mod 480.  The trailing triangle of step q
-//   is then the prefix e < M(q) and column q the 63 - q elements after it, so a warp's slot is wholly busy,
-//   wholly idle or on the boundary.  Phase q: the owners update the prefix with column q (published raw in
-//   row q of the shared tile) and publish column q + 1, which that update completed; warp 0 updates the
-//   diagonal and the lane of row q + 1 takes its pivot (1/sqrt(d) by rsqrt, d / sqrt(d), 1/d) while the
-//   others work;
-//   inverse, right-looking, two phases behind: step q subtracts L_rq W_qj from rows r > q (columns j <= q,
-//   addressed compactly) and finishes row q + 1 with 1/L_{q+1,q+1} as it makes the last update there; it
-//   reads column q scaled, written over the raw one in the phase after the factor used it.
-// The shared tile holds the factor's columns transposed in its upper part (raw, then scaled) and W's strict
-// lower part below; W's diagonal and L's are the pivot arrays.  The tile's padding rows and columns (past
-// N) are the identity, so the steps stay well defined.
-constexpr int PT_THREADS = 512;
-constexpr int PT_OFF = TB * (TB - 1) / 2;                     // strictly lower elements
-constexpr int PT_OWNERS = PT_THREADS - 32;                    // threads of warps 1 ..
-constexpr int PT_SLOTS = (PT_OFF + PT_OWNERS - 1) / PT_OWNERS;  // register slots per owner
-
-// elements of the columns right of q in the owners' numbering
-__device__ __forceinline__ int pt_prefix(int q) { return q >= TB - 1 ? 0 : (TB - 2 - q) * (TB - 1 - q) / 2; }
-
-__global__ void __launch_bounds__(PT_THREADS) k_potrf_tile(double *A, long long N, int kt, double *Dinv,
-                                                           int *status) {
-  __shared__ double S[TB][TB + 1];  // S[q][r] = column q of the factor at row r > q; S[r][j] = W_rj, r > j
-  __shared__ double prd[TB], piv[TB], pl[TB];  // 1/L_qq, 1/d_q, L_qq
-  const int t = threadIdx.x, lane = t & 31, wid = t >> 5;
-  const int u = t - 32, ub = (wid - 1) * 32;
-  const int k0 = kt * TB;
-  const int nb = (int)min((long long)TB, N - k0);
-  for (int e = t; e < TB * TB; e += PT_THREADS) {
-    const int r = e / TB, c = e % TB;
-    if (c <= r) S[r][c] = (r < nb && c < nb) ? A[(long long)(k0 + r) * N + k0 + c] : (r == c ? 1.0 : 0.0);
-  }
-  __syncthreads();
-  double dg[2] = {0.0, 0.0};
-  double a[PT_SLOTS];
-  int rs[PT_SLOTS], cs[PT_SLOTS];
-#pragma unroll
-  for (int k = 0; k < PT_SLOTS; ++k) {
-    // column j = 62 - c (from the right) holds j + 1 elements, rows c + 1 .. 63, from offset j (j + 1) / 2
-    const int e = wid > 0 ? PT_OWNERS * k + u : 0;
-    int j = (int)((sqrtf(8.0f * (float)e + 1.0f) - 1.0f) * 0.5f);
-    while (j > 0 && j * (j + 1) / 2 > e) --j;
-    while ((j + 1) * (j + 2) / 2 <= e) ++j;
-    cs[k] = TB - 2 - j;
-    rs[k] = cs[k] + 1 + e - j * (j + 1) / 2;
-    a[k] = (wid > 0 && e < PT_OFF) ? S[rs[k]][cs[k]] : 0.0;
-  }
-  if (wid == 0) {
-    dg[0] = S[lane][lane];
-    dg[1] = S[lane + 32][lane + 32];
-  }
-  __syncthreads();
-  for (int e = t; e < TB * TB; e += PT_THREADS) {
-    const int r = e / TB, c = e % TB;
-    if (c < r) S[r][c] = 0.0;
-  }
-  auto pivot = [&](int q, double d) {
-    if (!(d > 0.0)) {
-      if (atomicCAS(status, 0, (int)HPLMM_ERR_SINGULAR) == 0) {
-        status[1] = 3;
-        status[2] = 0;
-        status[3] = k0 + q;
-      }
-      d = 1.0;
-    }
-    const double r = rsqrt(d);
-    prd[q] = r;
-    piv[q] = r * r;
-    pl[q] = d * r;
-  };
-  // column 0 raw and its pivot
-  if (wid > 0) {
-    const int lo = pt_prefix(0);
-#pragma unroll
-    for (int k = 0; k < PT_SLOTS; ++k) {
-      const int e = PT_OWNERS * k + u;
-      if (e >= lo && e < lo + TB - 1) S[0][rs[k]] = a[k];
-    }
-  } else if (lane == 0) {
-    pivot(0, dg[0]);
-  }
-  __syncthreads();
-  for (int cc = 0; cc <= TB; ++cc) {
-    if (cc < TB) {
-      const double iv = piv[cc];
-      if (wid == 0) {
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-          const int r = lane + 32 * h;
-          if (r > cc) {
-            const double v = S[cc][r];
-            dg[h] -= (v * iv) * v;
-          }
-        }
-        if (cc + 1 < TB && lane == ((cc + 1) & 31)) pivot(cc + 1, cc + 1 < 32 ? dg[0] : dg[1]);
-      } else {
-        const int M = pt_prefix(cc), Mn = pt_prefix(cc + 1);
-        const double rd = prd[cc];
-#pragma unroll
-        for (int k = 0; k < PT_SLOTS; ++k) {
-          const int eb = PT_OWNERS * k + ub, e = eb + lane;
-          if (eb < M && e < M) {
-            const double p = S[cc][rs[k]] * iv;
-            a[k] -= p * S[cc][cs[k]];
-            if (e >= Mn) S[cc + 1][rs[k]] = a[k];  // column cc + 1 is complete: publish it raw
-          }
-          if (eb + 31 >= M && eb < M + TB - 1 - cc && e >= M && e < M + TB - 1 - cc) a[k] *= rd;  // column cc
-        }
-      }
-    }
-    if (wid > 0 && cc >= 1) {
-      // column cc - 1 scaled, over its raw copy (read by the factor in the previous phase)
-      const int q = cc - 1, lo = pt_prefix(q), hi = lo + TB - 1 - q;
-#pragma unroll
-      for (int k = 0; k < PT_SLOTS; ++k) {
-        const int eb = PT_OWNERS * k + ub, e = eb + lane;
-        if (eb + 31 >= lo && eb < hi && e >= lo && e < hi) S[q][rs[k]] = a[k];
-      }
-    }
-    if (wid > 0 && cc >= 2) {
-      // inverse step q = cc - 2
-      const int q = cc - 2, ncol = q + 1, cnt = (TB - 1 - q) * ncol;
-      const double rq = prd[q], rn = prd[q + 1];
-      for (int e = u; e < cnt; e += PT_OWNERS) {
-        const int ro = e / ncol, j = e - ro * ncol, r = q + 1 + ro;
-        const double wq = (j == q) ? rq : S[q][j];
-        double v = S[r][j] - S[q][r] * wq;
-        if (ro == 0) v *= rn;
-        S[r][j] = v;
-      }
-    }
-    __syncthreads();
-  }
-  // the factor and the inverse out, row-major; padding rows of the factor are identity rows, so their
-  // pivots are 1 and W stays the identity there
-  for (int e = t; e < TB * TB; e += PT_THREADS) {
-    const int r = e / TB, c = e % TB;
-    const bool in = r < nb && c < nb;
-    if (in) A[(long long)(k0 + r) * N + k0 + c] = c < r ? S[c][r] : (c == r ? pl[r] : 0.0);
-    Dinv[(long long)kt * TB * TB + e] = in ? (c < r ? S[r][c] : (c == r ? prd[r] : 0.0)) : 0.0;
-  }
-}
-
-// A[it][kt] <- A[it][kt] * inv(L_kk)^T for it > kt; CTA (tile, slice of 16 rows): the tiles of a step are
-// few, so each is split over 4 CTAs (the FP64 pipe of one SM is the limit)
-__global__ void __launch_bounds__(256) k_trsm_tiles(double *A, long long N, int kt, const double *Dinv) {
-  __shared__ double Di[TB][TB + 1];
-  __shared__ double Bt[16][TB + 1];
-  const int it = kt + 1 + blockIdx.x, rs = 16 * blockIdx.y;
-  const int k0 = kt * TB, i0 = it * TB;
-  const int nbk = (int)min((long long)TB, N - k0), nbi = (int)min((long long)TB, N - i0);
-  for (int e = threadIdx.x; e < TB * TB; e += blockDim.x) {
-    const int r = e / TB, c = e % TB;
-    Di[r][c] = Dinv[(long long)kt * TB * TB + e];
-  }
-  for (int e = threadIdx.x; e < 16 * TB; e += blockDim.x) {
-    const int r = e / TB, c = e % TB;
-    Bt[r][c] = (rs + r < nbi && c < nbk) ? A[(long long)(i0 + rs + r) * N + k0 + c] : 0.0;
-  }
-  __syncthreads();
-  for (int e = threadIdx.x; e < 16 * TB; e += blockDim.x) {
-    const int r = e / TB, c = e % TB;
-    double s0 = 0.0, s1 = 0.0;
-    int q = 0;
-    for (; q + 1 <= c; q += 2) {
-      s0 += Bt[r][q] * Di[c][q];
-      s1 += Bt[r][q + 1] * Di[c][q + 1];
-    }
-    if (q <= c) s0 += Bt[r][q] * Di[c][q];
-    if (rs + r < nbi && c < nbk) A[(long long)(i0 + rs + r) * N + k0 + c] = s0 + s1;
-  }
-}
-
-// A[it][jt] -= A[it][kt] A[jt][kt]^T for it >= jt > kt (lower tiles only)
-__global__ void k_syrk_tiles(double *A, long long N, int kt, int T) {
-  __shared__ double Ai[TB][TB + 1];
-  __shared__ double Aj[TB][TB + 1];
-  int m = T - kt - 1;
-  int t = blockIdx.x;
-  int ti = (int)((sqrt(8.0 * t + 1.0) - 1.0) * 0.5);
-  while ((ti + 1) * (ti + 2) / 2 <= t) ++ti;
-  while (ti * (ti + 1) / 2 > t) --ti;
-  int tj = t - ti * (ti + 1) / 2;
-  if (ti >= m) return;
-  int it = kt + 1 + ti, jt = kt + 1 + tj;
-  int k0 = kt * TB, i0 = it * TB, j0 = jt * TB;
-  int nbk = (int)min((long long)TB, N - k0);
-  int nbi = (int)min((long long)TB, N - i0), nbj = (int)min((long long)TB, N - j0);
-  for (int e = threadIdx.x; e < TB * TB; e += blockDim.x) {
-    int r = e / TB, c = e % TB;
-    Ai[r][c] = (r < nbi && c < nbk) ? A[(long long)(i0 + r) * N + k0 + c] : 0.0;
-    Aj[r][c] = (r < nbj && c < nbk) ? A[(long long)(j0 + r) * N + k0 + c] : 0.0;
-  }
-  __syncthreads();
-  // 256 threads, 4x4 outputs each
-  int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
-  double acc[4][4] = {};
-  for (int q = 0; q < TB; ++q) {
-    double a[4], b[4];
-    for (int u = 0; u < 4; ++u) {
-      a[u] = Ai[ty + 16 * u][q];
-      b[u] = Aj[tx + 16 * u][q];
-    }
-    for (int u = 0; u < 4; ++u)
-      for (int v = 0; v < 4; ++v) acc[u][v] += a[u] * b[v];
-  }
-  for (int u = 0; u < 4; ++u)
-    for (int v = 0; v < 4; ++v) {
-      int r = ty + 16 * u, c = tx + 16 * v;
-      if (r < nbi && c < nbj && (it != jt || c <= r)) A[(long long)(i0 + r) * N + j0 + c] -= acc[u][v];
-    }
-}
-
-// ---------------------------------------------------------------- explicit inverse factor Y = L^{-1}
-// Right-looking block substitution of L Y = I: for block row k, Y_kj = inv(L_kk) B_kj (j <= k), then
-// B_ij -= L_ik Y_kj for i > k.  Y starts as the identity (B) and is overwritten in place.
-__global__ void k_eye(double *Y, long long N) {
-  long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < N) Y[i * N + i] = 1.0;
-}
-
-// Y[kt][jt] <- inv(L_kk) Y[kt][jt] for jt <= kt; CTA (column tile, slice of 16 rows), thread = 1 x 4 outputs
-__global__ void __launch_bounds__(256) k_trinv_scale(double *Y, long long N, int kt, const double *Dinv) {
-  __shared__ double D[16][TB + 1];
-  __shared__ double Bt[TB][TB + 1];
-  const int jt = blockIdx.x, rs = 16 * blockIdx.y;
-  const int k0 = kt * TB, j0 = jt * TB;
-  const int nbk = (int)min((long long)TB, N - k0), nbj = (int)min((long long)TB, N - j0);
-  for (int e = threadIdx.x; e < 16 * TB; e += blockDim.x) {
-    const int r = e / TB, c = e % TB;
-    D[r][c] = Dinv[(long long)kt * TB * TB + (long long)(rs + r) * TB + c];
-  }
-  for (int e = threadIdx.x; e < TB * TB; e += blockDim.x) {
-    const int r = e / TB, c = e % TB;
-    Bt[r][c] = (r < nbk && c < nbj) ? Y[(long long)(k0 + r) * N + j0 + c] : 0.0;
-  }
-  __syncthreads();
-  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
-  double acc[4] = {0.0, 0.0, 0.0, 0.0};
-  for (int q = 0; q < TB; ++q) {
-    const double a = D[ty][q];
-#pragma unroll
-    for (int v = 0; v < 4; ++v) acc[v] += a * Bt[q][tx + 16 * v];
-  }
-#pragma unroll
-  for (int v = 0; v < 4; ++v) {
-    const int r = rs + ty, c = tx + 16 * v;
-    if (r < nbk && c < nbj) Y[(long long)(k0 + r) * N + j0 + c] = acc[v];
-  }
-}
-
-// Y[it][jt] -= L[it][kt] Y[kt][jt] for it > kt, jt <= kt
-__global__ void k_trinv_update(double *Y, const double *L, long long N, int kt, int T) {
-  __shared__ double Lt[TB][TB + 1];
-  __shared__ double Yt[TB][TB + 1];
-  int ncol = kt + 1;
-  int it = kt + 1 + blockIdx.x / ncol, jt = blockIdx.x % ncol;
-  if (it >= T) return;
-  int i0 = it * TB, k0 = kt * TB, j0 = jt * TB;
-  int nbi = (int)min((long long)TB, N - i0), nbk = (int)min((long long)TB, N - k0),
-      nbj = (int)min((long long)TB, N - j0);
-  for (int e = threadIdx.x; e < TB * TB; e += blockDim.x) {
-    int r = e / TB, c = e % TB;
-    Lt[r][c] = (r < nbi && c < nbk) ? L[(long long)(i0 + r) * N + k0 + c] : 0.0;
-    Yt[r][c] = (r < nbk && c < nbj) ? Y[(long long)(k0 + r) * N + j0 + c] : 0.0;
-  }
-  __syncthreads();
-  int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
-  double acc[4][4] = {};
-  for (int q = 0; q < TB; ++q) {
-    double a[4], b[4];
-    for (int u = 0; u < 4; ++u) {
-      a[u] = Lt[ty + 16 * u][q];
-      b[u] = Yt[q][tx + 16 * u];
-    }
-    for (int u = 0; u < 4; ++u)
-      for (int v = 0; v < 4; ++v) acc[u][v] += a[u] * b[v];
-  }
-  for (int u = 0; u < 4; ++u)
-    for (int v = 0; v < 4; ++v) {
-      int r = ty + 16 * u, c = tx + 16 * v;
-      if (r < nbi && c < nbj) Y[(long long)(i0 + r) * N + j0 + c] -= acc[u][v];
-    }
-}
-
-// u = Y t over the lower triangle: warp per row, 8 loads per lane in flight.  Row lengths grow with the row
-// index, so a CTA takes the rows of four pairs (p, N-1-p), each pair N+1 elements long: every CTA carries
-// the same work (with consecutive rows per CTA the long rows, all at the end of the grid, fell to a few SMs)
-__global__ void __launch_bounds__(256) k_trmv_lower(const double *Y, long long N, const double *t, double *u) {
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  const long long p = 4LL * blockIdx.x + (wid & 3);
-  if (p >= (N + 1) / 2) return;
-  const long long row = wid < 4 ? p : N - 1 - p;
-  if (wid >= 4 && row == p) return;  // the middle row of an odd N
-  const double *yr = Y + row * N;
-  double s0 = 0.0, s1 = 0.0;
-  for (long long jb = 0; jb <= row; jb += 256) {
-    double yv[8], tv[8];
-#pragma unroll
-    for (int q = 0; q < 8; ++q) {
-      const long long j = jb + q * 32 + lane;
-      const bool in = j <= row;
-      yv[q] = in ? yr[j] : 0.0;
-      tv[q] = in ? t[j] : 0.0;
-    }
-#pragma unroll
-    for (int q = 0; q < 8; ++q) (q & 1 ? s1 : s0) += yv[q] * tv[q];
-  }
-  double s = s0 + s1;
-  for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
-  if (lane == 0) u[row] = s;
-}
-
-// z = Y^T u over the lower triangle, in 64 x 64 tiles (row slab, column chunk) of the lower triangle, one CTA
-// of 64 threads per tile so that the CTAs carry equal work: thread per column with the slab's 64 loads issued
-// together, atomic accumulation into z
-constexpr int TRMV_SLAB = 64;
-__global__ void __launch_bounds__(64, 8) k_trmv_lower_t(const double *Y, long long N, const double *u, double *z) {
-  __shared__ double us[TRMV_SLAB];
-  const int tix = blockIdx.x;
-  int ti = (int)((sqrtf(8.0f * (float)tix + 1.0f) - 1.0f) * 0.5f);
-  while ((ti + 1) * (ti + 2) / 2 <= tix) ++ti;
-  while (ti * (ti + 1) / 2 > tix) --ti;
-  const int tj = tix - ti * (ti + 1) / 2;
-  const long long r0 = (long long)ti * TRMV_SLAB, r1 = min(N, r0 + TRMV_SLAB);
-  for (int q = threadIdx.x; q < TRMV_SLAB; q += blockDim.x) us[q] = r0 + q < N ? u[r0 + q] : 0.0;
-  __syncthreads();
-  const long long j = (long long)tj * TRMV_SLAB + threadIdx.x;
-  if (j >= r1) return;
-  double s0 = 0.0, s1 = 0.0;
-  if (tj < ti && r1 - r0 == TRMV_SLAB) {
-    // a full tile below the diagonal: no bounds, 32 loads per thread in flight
-    const double *yp = Y + r0 * N + j;
-#pragma unroll
-    for (int h = 0; h < TRMV_SLAB; h += 32) {
-      double y[32];
-#pragma unroll
-      for (int q = 0; q < 32; ++q) y[q] = yp[(long long)(h + q) * N];
-#pragma unroll
-      for (int q = 0; q < 32; ++q) (q & 1 ? s1 : s0) += y[q] * us[h + q];
-    }
-  } else {
-#pragma unroll
-    for (int q = 0; q < TRMV_SLAB; ++q) {
-      const long long i = r0 + q;
-      if (i >= j && i < r1) (q & 1 ? s1 : s0) += Y[i * N + j] * us[q];
-    }
-  }
-  const double s = s0 + s1;
-  if (s != 0.0) atomicAdd(&z[j], s);
-}
-
 // ---------------------------------------------------------------- restriction / prolongation
 // t[gcol] += sum over grain rows of X_g[row][a] r_loc[row]; CTA = (grain, chunk of RCHUNK rows):
 // the chunk's residual entries are gathered once into shared memory, then each thread owns columns and
 // reads the panel rows coalesced.
 constexpr int RCHUNK = 128;
+// largest coarse dimension for which the dense A^o is also kept (for inspection only)
+constexpr long long DENSE_COARSE_MAX = 12288;
 
 template <typename T, typename A>
 __global__ void __launch_bounds__(256) k_restrict_grain(const long long *node_off, const int *nloc, const int *lnodes,
@@ -785,8 +430,11 @@ void galerkin(hplmm_ctx *c, const Buf<int> &gbox, const std::vector<long long> &
   if (!tiles.empty()) {
     Buf<int> tl;
     tl.upload(tiles, s);
+    const CoarseFactor &F = c->cf;
+    CFView cv{F.erank.p, F.owner.p, F.fpos.p, F.m.p, F.P.p, F.rank.p, F.foff.p, F.ioff.p, F.F.p, c->status.p};
     k_gal_gemm<T><<<(unsigned)(tiles.size() / 3), 256, 0, s>>>(tl.p, gbox.p, gal_off.p, c->kg.p, gcol_off.p, gcol.p,
-                                                               P.p, Y.p, c->Ao.p, c->n_coarse);
+                                                               P.p, Y.p, cv, c->dense_ao ? c->Ao.p : nullptr,
+                                                               c->n_coarse);
     HP_CHECK_LAUNCH();
   }
   HP_CUDA(cudaStreamSynchronize(s));
@@ -909,8 +557,19 @@ void build_coarse(hplmm_ctx *c, const double *b_corr) {
   Buf<long long> gal_off;
   gal_off.upload(hgal, s);
   long long No = c->n_coarse;
-  c->Ao.alloc(std::max<long long>(No * No, 1));
-  c->Ao.zero(s);
+  // the dense A^o is kept only for inspection (hplmm_get_coarse_matrix) of small coarse spaces; the solver
+  // uses the sparse factor
+  c->dense_ao = No > 0 && No <= DENSE_COARSE_MAX;
+  if (c->dense_ao) {
+    c->Ao.alloc(No * No);
+    c->Ao.zero(s);
+  } else {
+    c->Ao.release();
+  }
+  {
+    ProfScope ps_sym(c, HPLMM_PH_COARSE_CHOL);
+    cf_analyse(c, hbox);
+  }
   {
     ProfScope ps_gal(c, HPLMM_PH_GALERKIN);
     if (f64)
@@ -920,46 +579,11 @@ void build_coarse(hplmm_ctx *c, const double *b_corr) {
   }
   if (No > 0) {
     ProfScope ps_chol(c, HPLMM_PH_COARSE_CHOL);
-    k_symmetrize<<<grid_for(No * No, 256), 256, 0, s>>>(c->Ao.p, No, nullptr);
-    HP_CHECK_LAUNCH();
-    // Cholesky factor (FP64) in a copy
-    c->Lo.alloc(No * No);
-    HP_CUDA(cudaMemcpyAsync(c->Lo.p, c->Ao.p, sizeof(double) * No * No, cudaMemcpyDeviceToDevice, s));
-    int T = (int)((No + TB - 1) / TB);
-    c->Lo_dinv.alloc((size_t)T * TB * TB);
-    // explicit inverse factor Y = L^{-1} (FP64), so that each apply is two parallel triangular products.  Its
-    // step kt needs only the factor's block column kt, so it runs on the second stream behind the Cholesky:
-    // after the column is final (diagonal tile and the tiles below) the Cholesky's trailing update and the
-    // inverse's step share the GPU.  One event, recorded once per step, orders the two streams.
-    c->Linv.alloc(No * No);
-    c->Linv.zero(s);
-    k_eye<<<grid_for(No, 256), 256, 0, s>>>(c->Linv.p, No);
-    HP_CHECK_LAUNCH();
-    if (!c->aux_stream) HP_CUDA(cudaStreamCreateWithFlags(&c->aux_stream, cudaStreamNonBlocking));
-    if (!c->ev_fork) HP_CUDA(cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming));
-    if (!c->ev_join) HP_CUDA(cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming));
-    cudaStream_t s2 = c->aux_stream;
-    for (int kt = 0; kt < T; ++kt) {
-      k_potrf_tile<<<1, PT_THREADS, 0, s>>>(c->Lo.p, No, kt, c->Lo_dinv.p, c->status.p);
+    if (c->dense_ao) {
+      k_symmetrize<<<grid_for(No * No, 256), 256, 0, s>>>(c->Ao.p, No, nullptr);
       HP_CHECK_LAUNCH();
-      int m = T - kt - 1;
-      if (m > 0) {
-        k_trsm_tiles<<<dim3(m, 4), 256, 0, s>>>(c->Lo.p, No, kt, c->Lo_dinv.p);
-        HP_CHECK_LAUNCH();
-      }
-      HP_CUDA(cudaEventRecord(c->ev_fork, s));
-      HP_CUDA(cudaStreamWaitEvent(s2, c->ev_fork, 0));
-      k_trinv_scale<<<dim3(kt + 1, 4), 256, 0, s2>>>(c->Linv.p, No, kt, c->Lo_dinv.p);
-      HP_CHECK_LAUNCH();
-      if (m > 0) {
-        k_trinv_update<<<m * (kt + 1), 256, 0, s2>>>(c->Linv.p, c->Lo.p, No, kt, T);
-        HP_CHECK_LAUNCH();
-        k_syrk_tiles<<<m * (m + 1) / 2, 256, 0, s>>>(c->Lo.p, No, kt, T);
-        HP_CHECK_LAUNCH();
-      }
     }
-    HP_CUDA(cudaEventRecord(c->ev_join, s2));
-    HP_CUDA(cudaStreamWaitEvent(s, c->ev_join, 0));
+    cf_factor(c);
   }
   HP_CUDA(cudaStreamSynchronize(s));
 }
@@ -997,14 +621,10 @@ void coarse_apply(hplmm_ctx *c, const double *r_pad, double *z_pad) {
                                                       c->kg.p, c->panel_off.p, c->X32.p, c->gcol_off.p, c->gcol.p,
                                                       r_pad, t);
   HP_CHECK_LAUNCH();
-  // u = Y t, then t <- Y^T u  (A^o)^{-1} = Y^T Y
+  // u = (A^o)^{-1} t by the sparse factor; the prolongation reads u
   double *u = c->w_coarse_u.p;
-  k_trmv_lower<<<grid_for((No + 1) / 2, 4), 256, 0, s>>>(c->Linv.p, No, t, u);
-  HP_CHECK_LAUNCH();
-  HP_CUDA(cudaMemsetAsync(t, 0, sizeof(double) * No, s));
-  const long long nslab = (No + TRMV_SLAB - 1) / TRMV_SLAB;
-  k_trmv_lower_t<<<(unsigned)(nslab * (nslab + 1) / 2), 64, 0, s>>>(c->Linv.p, No, u, t);
-  HP_CHECK_LAUNCH();
+  cf_solve(c, t, c->w_coarse_y.p, u);
+  t = u;
   dim3 gp(64, G);
   if (f64)
     k_prolong_grain<double, double><<<gp, 256, 0, s>>>(c->grains.node_off.p, c->grains.n.p, c->grains.lnodes.p,

@@ -140,6 +140,87 @@ struct LocalSet {
   hplmm_prec prec = HPLMM_FP64;
 };
 
+// ---------------------------------------------------------------- sparse coarse factor (cfactor.cu)
+// Multifrontal FP64 Cholesky of A^o.  A^o = sum over grains of a dense block on the grain's coupled
+// columns, so the grains play the part of finite elements: a recursive bisection of the grain centres
+// gives a nested-dissection tree, every coarse column group (an interface's mortar columns, or a grain's
+// correction column) is eliminated at the lowest tree node whose subtree holds every grain coupled to it,
+// and nodes with few columns are merged into their parents.  Front f (dense, row-major m x m) holds its
+// p pivot columns, padded with identity columns to P (a multiple of 64), then its b boundary columns,
+// which belong to ancestors; its boundary block receives the Schur update and is added into the parent.
+struct FTask {
+  int f, a, b, c;  // front and up to three tile or block indices
+};
+struct FLaunch {
+  int kind;        // kernel (see cfactor.cu)
+  int kt;          // tile step of the factorisation
+  long long off;   // first task
+  int count;       // tasks
+};
+struct CoarseFactor {
+  int nf = 0, nlev = 0;
+  long long F_total = 0, Y_total = 0, D_total = 0, idx_total = 0;
+  std::vector<int> h_m, h_P, h_p, h_b, h_parent, h_level;
+  std::vector<long long> h_foff, h_yoff, h_doff, h_ioff;
+  Buf<int> m, P, p, b, parent;
+  Buf<long long> foff, yoff, doff, ioff, roff;
+  const int *bdev() const { return b.p; }
+  Buf<int> idx;     // coarse column of every front row (-1 on padding rows)
+  Buf<int> rank;    // elimination rank of every front row (-1 on padding rows)
+  Buf<int> rel;     // per front: row of each of its boundary rows in the parent's front
+  Buf<int> erank, owner, fpos;  // per coarse column: elimination rank, front, row in that front
+  Buf<double> F;    // fronts; after the factorisation their first P columns hold [L_pp; L_bp]
+  Buf<double> Y;    // per front: inv(L_pp), P x P row-major
+  Buf<double> D;    // per front: inverses of the 64 x 64 diagonal tiles of L_pp
+  Buf<FTask> tasks;
+  std::vector<FLaunch> fact;            // factorisation launches, in order
+  std::vector<std::vector<FLaunch>> fwd, bwd;  // solve launches per level (forward ascending, backward
+                                               // descending levels)
+  double flops = 0;                     // factorisation flops (pivot block, panel and Schur update)
+  long long solve_bytes = 0;            // bytes of L and inv(L_pp) read by one coarse solve
+};
+
+// device view of the front layout, for adding A^o entries into the fronts
+struct CFView {
+  const int *erank, *owner, *fpos, *m, *P, *rank;
+  const long long *foff, *ioff;
+  double *F;
+  int *status;
+};
+
+// position of coarse column `col` among the rows of front f: a pivot row, or a boundary row found by
+// binary search of its elimination rank among the front's boundary rows (sorted by rank)
+__device__ __forceinline__ int cf_row(const CFView &v, int f, int col) {
+  if (v.owner[col] == f) return v.fpos[col];
+  const int r = v.erank[col];
+  const int *rk = v.rank + v.ioff[f];
+  int a = v.P[f], b = v.m[f];
+  const int end = b;
+  while (a < b) {
+    const int mid = (a + b) >> 1;
+    if (rk[mid] < r) a = mid + 1;
+    else b = mid;
+  }
+  return (a < end && rk[a] == r) ? a : -1;
+}
+
+// A^o[ca][cb] += val, into the front of whichever of the two columns is eliminated first
+__device__ __forceinline__ void cf_add(const CFView &v, int ca, int cb, double val) {
+  const int x = v.erank[ca] <= v.erank[cb] ? ca : cb;
+  const int f = v.owner[x];
+  const long long m = v.m[f];
+  const int ra = cf_row(v, f, ca), rb = cf_row(v, f, cb);
+  if (ra < 0 || rb < 0) {  // not in the front: the symbolic analysis is inconsistent
+    if (atomicCAS(v.status, 0, (int)HPLMM_ERR_INVALID) == 0) {
+      v.status[1] = 4;
+      v.status[2] = f;
+      v.status[3] = ra < 0 ? ca : cb;
+    }
+    return;
+  }
+  atomicAdd(v.F + v.foff[f] + (long long)ra * m + rb, val);
+}
+
 }  // namespace hp
 
 // ---------------------------------------------------------------- the context
@@ -219,18 +300,17 @@ struct hplmm_ctx {
   hp::Buf<double> X64;             // basis panels X_g (local DOF rows x k_g), FP64
   hp::Buf<float> X32;              // FP32 copy/compute
   hp::Buf<__nv_bfloat16> X16;      // BF16 copy of X32 for the restriction/prolongation of the BF16 form
-  hp::Buf<double> Ao;              // N^o x N^o
+  hp::Buf<double> Ao;              // N^o x N^o dense copy, kept only when N^o <= dense_coarse_max
+  bool dense_ao = false;
   hp::Buf<double> gal64;           // Galerkin work: P and Y on the grains' node boxes (FP64 form)
   hp::Buf<float> gal32;            // (FP32 form)
-  hp::Buf<double> Lo;              // Cholesky factor (lower, row-major full storage)
-  hp::Buf<double> Lo_dinv;         // inverses of its 64x64 diagonal tiles
-  hp::Buf<double> Linv;            // Y = L^{-1} (lower), so that (A^o)^{-1} = Y^T Y
+  hp::CoarseFactor cf;             // sparse (multifrontal) Cholesky factor of A^o
   hp::Buf<int> gcol_off, gcol;     // global coarse column of each panel column
   hp::Buf<int> status;             // device error word
 
   // ---- apply / GMRES work vectors (padded n_nodes*3)
   hp::Buf<double> w_r1, w_r2, w_z1, w_zz, w_zg, w_t, w_w;
-  hp::Buf<double> w_coarse_t, w_coarse_u;
+  hp::Buf<double> w_coarse_t, w_coarse_u, w_coarse_y;
   hp::Buf<double> w_loc64;         // local vectors for smoother
   hp::Buf<float> w_loc32;
   hp::Buf<double> w_in, w_out;     // padded copies of API vectors
@@ -342,6 +422,12 @@ void ws_pcg_basis(hplmm_ctx *c, bool warm);
 int num_sms();
 // coarse.cu
 void build_coarse(hplmm_ctx *c, const double *b_pad_for_corr);
+// cfactor.cu: symbolic analysis from the grains' voxel boxes (lo[3], ext[3] per grain), numeric
+// factorisation of the fronts the Galerkin product filled, and x = (A^o)^{-1} t (t is overwritten, y is
+// work; all three of length N^o)
+void cf_analyse(hplmm_ctx *c, const std::vector<int> &gbox);
+void cf_factor(hplmm_ctx *c);
+void cf_solve(hplmm_ctx *c, double *t, double *y, double *x);
 void coarse_apply(hplmm_ctx *c, const double *r_pad, double *z_pad);
 void prolong_column(hplmm_ctx *c, long long col, double *out_pad);
 // apply.cu

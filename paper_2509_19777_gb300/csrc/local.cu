@@ -910,12 +910,14 @@ __device__ void m32_sweep(Multi32Ctx &m) {
       const int row0 = c * SM32_CH;
       const int rows = min(SM32_CH, m32_panel_rows(m, p) - row0);
       if (DIR == 0 && c == 0) {
-        // Y = inv(L_pp) X_p (row q of the block, lane = column)
+        // Y = inv(L_pp) X_p (row q of the block, lane = column); the ring slots of rows past the end of a
+        // short last panel were never written (shared memory starts undefined), so they are masked rather
+        // than multiplied by the zero columns of inv(L_pp)
         for (int q = wid; q < NB; q += SM32_NW) {
           float y = 0.f;
 #pragma unroll
           for (int cc = 0; cc < NB; ++cc)
-            y = fmaf(Lc[q * NB + cc], m.Xw[(size_t)ring_slot(k0 + cc, m.XR) * NB + lane], y);
+            if (cc < nb) y = fmaf(Lc[q * NB + cc], m.Xw[(size_t)ring_slot(k0 + cc, m.XR) * NB + lane], y);
           m.Yb[q][lane] = (q < nb) ? y : 0.f;
         }
         __syncthreads();
