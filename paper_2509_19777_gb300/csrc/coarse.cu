@@ -100,8 +100,8 @@ __global__ void k_gal_fill(const int *gbox, const long long *gal_off, const int 
                            const uint8_t *fixed, const int *gbox_grain, const long long *node_off_g,
                            const int *lmap_g, const long long *panel_off, const T *X, const int *mortar_off,
                            const long long *eta_off, const double *eta, const int *comp_mask, const int *gi_off,
-                           const int *gi_iface, const int *gi_colbase, T *P) {
-  int g = blockIdx.y;
+                           const int *gi_iface, const int *gi_colbase, int g0, long long gbase, T *P) {
+  int g = g0 + blockIdx.y;
   const int *bx = gbox + 6 * g;
   int ex = bx[3], ey = bx[4], ez = bx[5];
   int vol = ex * ey * ez;
@@ -112,7 +112,7 @@ __global__ void k_gal_fill(const int *gbox, const long long *gal_off, const int 
   long long NX = nx + 1, NY = ny + 1;
   int n = grid_to_node[((long long)z * NY + y) * NX + x];
   if (n < 0) return;
-  T *Pr = P + gal_off[g] + (long long)3 * cell * k;
+  T *Pr = P + (gal_off[g] - gbase) + (long long)3 * cell * k;
   if (node_cls[n] == g) {
     // ordinal of n in the grain problem: box of the grain set (lo, ext, perm)
     const int *b = gbox_grain + 9 * g;
@@ -142,9 +142,9 @@ __global__ void k_gal_fill(const int *gbox, const long long *gal_off, const int 
 template <typename T>
 __global__ void k_gal_Y(const int *gbox, const long long *gal_off, const int *kg, const int *vg, const uint8_t *mask,
                         const float *E, int nx, int ny, int nz, const double *Kref, const uint8_t *fixed,
-                        const int *grid_to_node, const T *P, T *Y) {
+                        const int *grid_to_node, int g0, long long gbase, const T *P, T *Y) {
   __shared__ T K[576];
-  int g = blockIdx.y;
+  int g = g0 + blockIdx.y;
   for (int e = threadIdx.x; e < 576; e += blockDim.x) K[e] = (T)Kref[e];
   __syncthreads();
   const int *bx = gbox + 6 * g;
@@ -154,8 +154,8 @@ __global__ void k_gal_Y(const int *gbox, const long long *gal_off, const int *kg
   if (cell >= vol) return;
   int k = kg[g];
   int x = bx[0] + cell % ex, y = bx[1] + (cell / ex) % ey, z = bx[2] + cell / (ex * ey);
-  const T *Pg = P + gal_off[g];
-  T *Yr = Y + gal_off[g] + (long long)3 * cell * k;
+  const T *Pg = P + (gal_off[g] - gbase);
+  T *Yr = Y + (gal_off[g] - gbase) + (long long)3 * cell * k;
   for (int a = threadIdx.x; a < k; a += blockDim.x) {
     T acc[3] = {0, 0, 0};
     for (int dz = -1; dz <= 0; ++dz)
@@ -188,15 +188,16 @@ __global__ void k_gal_Y(const int *gbox, const long long *gal_off, const int *kg
 template <typename T>
 __global__ void __launch_bounds__(256) k_gal_gemm(const int *tiles, const int *gbox, const long long *gal_off,
                                                   const int *kg, const int *gcol_off, const int *gcol, const T *P,
-                                                  const T *Y, CFView cf, double *Ao, long long No) {
+                                                  const T *Y, long long gbase, CFView cf, double *Ao,
+                                                  long long No) {
   __shared__ T Ps[32][33];
   __shared__ T Ys[32][33];
   int g = tiles[3 * blockIdx.x], a0 = tiles[3 * blockIdx.x + 1], b0 = tiles[3 * blockIdx.x + 2];
   const int *bx = gbox + 6 * g;
   long long M = 3LL * bx[3] * bx[4] * bx[5];
   int k = kg[g];
-  const T *Pg = P + gal_off[g];
-  const T *Yg = Y + gal_off[g];
+  const T *Pg = P + (gal_off[g] - gbase);
+  const T *Yg = Y + (gal_off[g] - gbase);
   int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;  // 16 x 16 threads, 2x2 outputs each
   T acc[2][2] = {{0, 0}, {0, 0}};
   for (long long r0 = 0; r0 < M; r0 += 32) {
@@ -247,6 +248,8 @@ __global__ void k_symmetrize(double *A, long long N, double *asym) {
 constexpr int RCHUNK = 128;
 // largest coarse dimension for which the dense A^o is also kept (for inspection only)
 constexpr long long DENSE_COARSE_MAX = 12288;
+// elements of each of the Galerkin work arrays (P and Y on the grains' node boxes) per batch of grains
+constexpr long long GAL_WORK_ELEMS = 1LL << 28;
 
 template <typename T, typename A>
 __global__ void __launch_bounds__(256) k_restrict_grain(const long long *node_off, const int *nloc, const int *lnodes,
@@ -400,42 +403,50 @@ void galerkin(hplmm_ctx *c, const Buf<int> &gbox, const std::vector<long long> &
   cudaStream_t s = c->stream;
   int G = c->n_grains;
   Buf<T> &work = gal_buf<T>(c);
-  long long tot = std::max<long long>(hgal[G], 1);
-  work.alloc(2 * tot);
-  HP_CUDA(cudaMemsetAsync(work.p, 0, sizeof(T) * tot, s));
-  struct {
-    T *p;
-  } P{work.p}, Y{work.p + tot};
-  dim3 gf(grid_for(maxvol, 128), G);
-  k_gal_fill<T><<<gf, 128, 0, s>>>(gbox.p, gal_off.p, c->kg.p, c->grid_to_node.p, c->nx, c->ny, c->node_cls.p,
-                                   c->iface_of_node.p, c->iface_slot.p, c->fixed.p, c->grains.box.p,
-                                   c->grains.node_off.p, c->grains.lmap.p, c->panel_off.p, panel_ptr<T>(c),
-                                   c->mortar_off.p, c->eta_off.p, c->eta.p, c->comp_mask.p, c->gi_off.p,
-                                   c->gi_iface.p, c->gi_colbase.p, P.p);
-  HP_CHECK_LAUNCH();
-  dim3 gy(maxvol, G);
-  k_gal_Y<T><<<gy, 128, 0, s>>>(gbox.p, gal_off.p, c->kg.p, c->vgrain.p, c->mask.p, c->E.p, c->nx, c->ny, c->nz,
-                                c->Kref.p, c->fixed.p, c->grid_to_node.p, P.p, Y.p);
-  HP_CHECK_LAUNCH();
-  std::vector<int> tiles;
-  for (int g = 0; g < G; ++g) {
-    int k = c->h_kg[g];
-    for (int a0 = 0; a0 < k; a0 += 32)
-      for (int b0 = 0; b0 < k; b0 += 32) {
-        tiles.push_back(g);
-        tiles.push_back(a0);
-        tiles.push_back(b0);
-      }
-  }
-  if (!tiles.empty()) {
-    Buf<int> tl;
-    tl.upload(tiles, s);
-    const CoarseFactor &F = c->cf;
-    CFView cv{F.erank.p, F.owner.p, F.fpos.p, F.m.p, F.P.p, F.rank.p, F.foff.p, F.ioff.p, F.F.p, c->status.p};
-    k_gal_gemm<T><<<(unsigned)(tiles.size() / 3), 256, 0, s>>>(tl.p, gbox.p, gal_off.p, c->kg.p, gcol_off.p, gcol.p,
-                                                               P.p, Y.p, cv, c->dense_ao ? c->Ao.p : nullptr,
-                                                               c->n_coarse);
+  // grains in batches whose P and Y on the node boxes fit the work budget (at least one grain per batch)
+  long long most = 1;
+  for (int g = 0; g < G; ++g) most = std::max(most, hgal[g + 1] - hgal[g]);
+  const long long cap = std::max(most, std::min<long long>(hgal[G], GAL_WORK_ELEMS));
+  work.alloc(2 * cap);
+  const CoarseFactor &F = c->cf;
+  CFView cv{F.erank.p, F.owner.p, F.fpos.p, F.m.p, F.P.p, F.rank.p, F.foff.p, F.ioff.p, F.F.p, c->status.p};
+  Buf<int> tl;
+  for (int g0 = 0; g0 < G;) {
+    int g1 = g0 + 1;
+    while (g1 < G && hgal[g1 + 1] - hgal[g0] <= cap) ++g1;
+    const long long base = hgal[g0], tot = std::max<long long>(hgal[g1] - hgal[g0], 1);
+    T *P = work.p, *Y = work.p + cap;
+    HP_CUDA(cudaMemsetAsync(P, 0, sizeof(T) * tot, s));
+    dim3 gf(grid_for(maxvol, 128), g1 - g0);
+    k_gal_fill<T><<<gf, 128, 0, s>>>(gbox.p, gal_off.p, c->kg.p, c->grid_to_node.p, c->nx, c->ny, c->node_cls.p,
+                                     c->iface_of_node.p, c->iface_slot.p, c->fixed.p, c->grains.box.p,
+                                     c->grains.node_off.p, c->grains.lmap.p, c->panel_off.p, panel_ptr<T>(c),
+                                     c->mortar_off.p, c->eta_off.p, c->eta.p, c->comp_mask.p, c->gi_off.p,
+                                     c->gi_iface.p, c->gi_colbase.p, g0, base, P);
     HP_CHECK_LAUNCH();
+    dim3 gy(maxvol, g1 - g0);
+    k_gal_Y<T><<<gy, 128, 0, s>>>(gbox.p, gal_off.p, c->kg.p, c->vgrain.p, c->mask.p, c->E.p, c->nx, c->ny, c->nz,
+                                  c->Kref.p, c->fixed.p, c->grid_to_node.p, g0, base, P, Y);
+    HP_CHECK_LAUNCH();
+    std::vector<int> tiles;
+    for (int g = g0; g < g1; ++g) {
+      int k = c->h_kg[g];
+      for (int a0 = 0; a0 < k; a0 += 32)
+        for (int b0 = 0; b0 < k; b0 += 32) {
+          tiles.push_back(g);
+          tiles.push_back(a0);
+          tiles.push_back(b0);
+        }
+    }
+    if (!tiles.empty()) {
+      HP_CUDA(cudaStreamSynchronize(s));  // the previous batch's tile list is still read until here
+      tl.upload(tiles, s);
+      k_gal_gemm<T><<<(unsigned)(tiles.size() / 3), 256, 0, s>>>(tl.p, gbox.p, gal_off.p, c->kg.p, gcol_off.p,
+                                                                 gcol.p, P, Y, base, cv,
+                                                                 c->dense_ao ? c->Ao.p : nullptr, c->n_coarse);
+      HP_CHECK_LAUNCH();
+    }
+    g0 = g1;
   }
   HP_CUDA(cudaStreamSynchronize(s));
 }

@@ -253,13 +253,13 @@ template <typename T>
 __global__ void k_local_extract(const int *box, const long long *node_off, const int *nloc, const int *bwv,
                                 const long long *band_off, const int *lmap, const int *lnodes, const int *node_ijk,
                                 const int *row_ptr, const int *col, const double *val, const uint8_t *fixed, T *band,
-                                int NB) {
-  int k = blockIdx.x;
+                                int NB, const int *plist, long long bbase) {
+  int k = plist ? plist[blockIdx.x] : (int)blockIdx.x;
   Box b = load_box(box, k);
   long long off = node_off[k];
   int cnt = nloc[k] / 3;
   int bw = bwv[k];
-  T *B = band + band_off[k];
+  T *B = band + (band_off[k] - bbase);
   for (int o = threadIdx.x; o < cnt; o += blockDim.x) {
     int n = lnodes[off + o];
     for (int p = row_ptr[n]; p < row_ptr[n + 1]; ++p) {
@@ -479,7 +479,7 @@ template <int CL>
 __global__ void __launch_bounds__(CHOL32_THREADS, 1) k_band_chol32(const int *order, int count, int *queue,
                                                                 const int *nloc, const int *bwv,
                                                                 const long long *band_off, float *band, int *status,
-                                                                int where, int bwv_max) {
+                                                                int where, int bwv_max, long long bbase) {
   constexpr int NB = 32, LD = CHOL32_LD;
   extern __shared__ __align__(16) unsigned char smraw[];
   float *P = reinterpret_cast<float *>(smraw);
@@ -504,7 +504,7 @@ __global__ void __launch_bounds__(CHOL32_THREADS, 1) k_band_chol32(const int *or
     const int k = order[job];
     const int N = nloc[k], bw = bwv[k];
     if (N == 0) continue;
-    float *B = band + band_off[k];
+    float *B = band + (band_off[k] - bbase);
     const int RP = NB + bw;
     for (int k0 = 0, p = 0; k0 < N; k0 += NB, ++p) {
       const int nb = min(NB, N - k0);
@@ -1023,7 +1023,7 @@ __global__ void __launch_bounds__(SM32_THREADS, 1) k_band_solve_multi32(const in
                                                                         const long long *band_off,
                                                                         const float *band, float *Xbase,
                                                                         const long long *x_off, const int *x_ld,
-                                                                        int XR) {
+                                                                        int XR, long long bbase) {
   extern __shared__ __align__(16) unsigned char smraw[];
   __shared__ float red[SM32_NW][32][32];
   __shared__ float Yb[32][33];
@@ -1041,7 +1041,7 @@ __global__ void __launch_bounds__(SM32_THREADS, 1) k_band_solve_multi32(const in
   m.ld = x_ld[k];
   m.XR = XR;
   m.colok = m.lane < min(32, m.ld - r0);
-  m.Bk = band + band_off[k];
+  m.Bk = band + (band_off[k] - bbase);
   m.X = Xbase + x_off[k] + r0;
   m.Lring = reinterpret_cast<float *>(smraw);
   m.Xw = m.Lring + (size_t)SM32_STAGES * SM32_CH * 32;
@@ -1854,74 +1854,96 @@ int num_sms() {
 
 namespace {
 
+// band offsets of a set in the panel layout of precision T; returns the largest half bandwidth
 template <typename T>
-void layout_and_factor(hplmm_ctx *c, LocalSet &S, int where, cudaStream_t s, bool sync) {
+int layout_set(LocalSet &S, cudaStream_t s) {
   constexpr int NB = NBOf<T>::v;
-  int K = S.count;
-  // band and inverse-block offsets for this precision
+  const int K = S.count;
   std::vector<long long> boff(K + 1, 0);
   int bwmax = 0;
   for (int k = 0; k < K; ++k) {
-    int N = S.h_n[k], bw = S.h_bw[k];
-    long long np = (N + NB - 1) / NB;
+    const int N = S.h_n[k], bw = S.h_bw[k];
+    const long long np = (N + NB - 1) / NB;
     boff[k + 1] = boff[k] + np * (NB + bw) * NB;
     if (N > 0) bwmax = std::max(bwmax, bw);
   }
-  size_t smem = (size_t)(NB + bwmax) * (NB + 16 / sizeof(T)) * sizeof(T);
+  const size_t smem = (size_t)(NB + bwmax) * (NB + 16 / sizeof(T)) * sizeof(T);
   HP_REQUIRE(smem <= 200 * 1024, HPLMM_ERR_INVALID,
              "local problem half bandwidth " + std::to_string(bwmax) + " is too large; use smaller grain grids");
   S.h_band_off = boff;
   S.band_off.upload(boff, s);
+  return bwmax;
+}
+
+// FP32 banded Cholesky of `count` problems listed in `order` (their bands at band + band_off[k] - bbase):
+// a two-CTA cluster per problem when the problems leave at least half of the SMs idle, else one CTA per
+// problem taking problems from the queue
+void launch_chol32(hplmm_ctx *c, LocalSet &S, int where, cudaStream_t s, const int *order, int count, float *band,
+                   long long bbase, int bwmax) {
+  constexpr int NB = 32;
+  const size_t smem32 =
+      ((size_t)(NB + bwmax) * CHOL32_LD + (size_t)(CHOL32_THREADS / 32) * 32 * CHOL32_CST_LD) * sizeof(float);
+  HP_REQUIRE(smem32 <= 216 * 1024, HPLMM_ERR_INVALID,
+             "local problem half bandwidth " + std::to_string(bwmax) + " is too large; use smaller grain grids");
+  S.queue.alloc(1);
+  HP_CUDA(cudaMemsetAsync(S.queue.p, 0, sizeof(int), s));
+  if (2 * count <= num_sms()) {
+    HP_CUDA(cudaFuncSetAttribute(k_band_chol32<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem32));
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)(2 * count));
+    cfg.blockDim = dim3(CHOL32_THREADS);
+    cfg.dynamicSmemBytes = smem32;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = 2;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    HP_CUDA(cudaLaunchKernelEx(&cfg, k_band_chol32<2>, order, count, S.queue.p, (const int *)S.n.p,
+                               (const int *)S.bw.p, (const long long *)S.band_off.p, band, c->status.p, where,
+                               bwmax, bbase));
+  } else {
+    const int grid = std::min(count, 2 * num_sms());
+    HP_CUDA(cudaFuncSetAttribute(k_band_chol32<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem32));
+    k_band_chol32<1><<<grid, CHOL32_THREADS, smem32, s>>>(order, count, S.queue.p, S.n.p, S.bw.p, S.band_off.p,
+                                                          band, c->status.p, where, bwmax, bbase);
+  }
+  HP_CHECK_LAUNCH();
+}
+
+template <typename T>
+void layout_and_factor(hplmm_ctx *c, LocalSet &S, int where, cudaStream_t s, bool sync) {
+  constexpr int NB = NBOf<T>::v;
+  const int K = S.count;
+  const int bwmax = layout_set<T>(S, s);
+  const long long total = S.h_band_off[K];
   if (sizeof(T) == 8) {
-    S.band64.alloc(std::max<long long>(boff[K], 1));
+    S.band64.alloc(std::max<long long>(total, 1));
     S.band64.zero(s);
   } else {
-    S.band32.alloc(std::max<long long>(boff[K], 1));
+    S.band32.alloc(std::max<long long>(total, 1));
     S.band32.zero(s);
   }
   T *band = band_ptr<T>(S);
   k_local_extract<T><<<K, 128, 0, s>>>(S.box.p, S.node_off.p, S.n.p, S.bw.p, S.band_off.p, S.lmap.p, S.lnodes.p,
-                                       c->node_ijk.p, c->row_ptr.p, c->col.p, c->val64.p, c->fixed.p, band, NB);
+                                       c->node_ijk.p, c->row_ptr.p, c->col.p, c->val64.p, c->fixed.p, band, NB,
+                                       nullptr, 0LL);
   HP_CHECK_LAUNCH();
-  S.queue.alloc(1);
-  S.queue.zero(s);
-  int *queue = S.queue.p;
-  int grid = std::min(K, 2 * num_sms());
   if constexpr (sizeof(T) == 4) {
-    const size_t smem32 =
-        ((size_t)(NB + bwmax) * CHOL32_LD + (size_t)(CHOL32_THREADS / 32) * 32 * CHOL32_CST_LD) * sizeof(float);
-    HP_REQUIRE(smem32 <= 216 * 1024, HPLMM_ERR_INVALID,
-               "local problem half bandwidth " + std::to_string(bwmax) + " is too large; use smaller grain grids");
-    if (2 * K <= num_sms()) {
-      // few problems: a two-CTA cluster each, in cost order
-      HP_CUDA(cudaFuncSetAttribute(k_band_chol32<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem32));
-      cudaLaunchConfig_t cfg = {};
-      cfg.gridDim = dim3((unsigned)(2 * K));
-      cfg.blockDim = dim3(CHOL32_THREADS);
-      cfg.dynamicSmemBytes = smem32;
-      cfg.stream = s;
-      cudaLaunchAttribute at[1];
-      at[0].id = cudaLaunchAttributeClusterDimension;
-      at[0].val.clusterDim.x = 2;
-      at[0].val.clusterDim.y = 1;
-      at[0].val.clusterDim.z = 1;
-      cfg.attrs = at;
-      cfg.numAttrs = 1;
-      HP_CUDA(cudaLaunchKernelEx(&cfg, k_band_chol32<2>, (const int *)S.order.p, K, queue, (const int *)S.n.p,
-                                 (const int *)S.bw.p, (const long long *)S.band_off.p, band, c->status.p, where,
-                                 bwmax));
-    } else {
-      HP_CUDA(cudaFuncSetAttribute(k_band_chol32<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem32));
-      k_band_chol32<1><<<grid, CHOL32_THREADS, smem32, s>>>(S.order.p, K, queue, S.n.p, S.bw.p, S.band_off.p,
-                                                            band, c->status.p, where, bwmax);
-    }
+    launch_chol32(c, S, where, s, S.order.p, K, band, 0LL, bwmax);
   } else {
+    const size_t smem = (size_t)(NB + bwmax) * (NB + 16 / sizeof(T)) * sizeof(T);
+    S.queue.alloc(1);
+    S.queue.zero(s);
+    const int grid = std::min(K, 2 * num_sms());
     auto kern = k_band_chol<T, NB>;
     HP_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    kern<<<grid, FACT_THREADS, smem, s>>>(S.order.p, K, queue, S.n.p, S.bw.p, S.band_off.p, band, c->status.p,
+    kern<<<grid, FACT_THREADS, smem, s>>>(S.order.p, K, S.queue.p, S.n.p, S.bw.p, S.band_off.p, band, c->status.p,
                                           where);
+    HP_CHECK_LAUNCH();
   }
-  HP_CHECK_LAUNCH();
   if (sync) HP_CUDA(cudaStreamSynchronize(s));
 }
 
@@ -2150,7 +2172,7 @@ static void solve_multi_t(hplmm_ctx *c, LocalSet &S, T *X, const Buf<long long> 
                "local problem half bandwidth " + std::to_string(rpmax - NB) + " is too large for the basis solves");
     HP_CUDA(cudaFuncSetAttribute(k_band_solve_multi32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     k_band_solve_multi32<<<n_items, SM32_THREADS, smem, s>>>(it.p, n_items, S.n.p, S.bw.p, S.band_off.p,
-                                                             band_ptr<T>(S), X, x_off.p, x_ld.p, XR);
+                                                             band_ptr<T>(S), X, x_off.p, x_ld.p, XR, 0LL);
   } else {
     k_band_solve_multi<T, NB><<<n_items, 256, 0, s>>>(it.p, n_items, S.n.p, S.bw.p, S.band_off.p, band_ptr<T>(S),
                                                       X, x_off.p, x_ld.p);

@@ -16,12 +16,20 @@ CASES = {
     "tiny10_n1": ("tiny10", 5, dict(n_mortar=1, contact_halfwidth=1)),
     "tiny10_strict": ("tiny10", 6, dict(n_mortar=3, contact_halfwidth=1, strict_two_grain=True)),
     "porous32_n4": ("porous32", 1, dict(n_mortar=4, contact_halfwidth=2)),
+    # large local sets: 216 grains of 4^3 voxels (more grains than half the SMs: one CTA per problem in the
+    # factorisation) and 512 grains (more problems than two per SM: the persistent queue hands CTAs several
+    # problems), both with more than 500 contact grids and a deep coarse elimination tree
+    "porous24_g216": ("porous24", 1, dict(n_mortar=1, contact_halfwidth=1, grains=(6, 6, 6))),
+    "porous32_g512": ("porous32", 1, dict(n_mortar=1, contact_halfwidth=1, grains=(8, 8, 8))),
 }
 
 
 def problem(name):
     wl, seed, opt = CASES[name]
-    return synth.make_workload(wl, seed), opt
+    p = synth.make_workload(wl, seed)
+    if "grains" in opt:
+        p.grains = tuple(opt["grains"])
+    return p, opt
 
 
 @functools.lru_cache(maxsize=None)
@@ -39,6 +47,16 @@ def oracle_solution(name, tol=1e-11):
     p, opt, sysm, M = oracle_case(name)
     x, st = gmres.gmres(sysm.A, sysm.b, M.apply, tol=tol)
     return x, st
+
+
+def maxrel(a, b):
+    """Element-wise error: max |a - b| over the largest |b| (a wrong value on a few entries of a long vector
+    shows here even when the norm-wise error stays small)."""
+    a = np.asarray(a, dtype=np.float64)
+    b = np.asarray(b, dtype=np.float64)
+    m = np.abs(b).max() if b.size else 0.0
+    d = np.abs(a - b).max() if b.size else 0.0
+    return d / m if m > 0 else d
 
 
 def rel(a, b):
