@@ -79,6 +79,10 @@ typedef struct {
   int smoother_ctas;     /* CTAs per local problem in the smoother solves: 0 (default) the tuner's choice, or
                             two for a set with at most half as many problems as the GPU has SMs, else one;
                             1 or 2 force it (two: a cluster that splits each panel's far rows) */
+  int stage_mb;          /* BF16 apply form (local_prec FP32, apply_prec BF16, exact basis solves): the local
+                            factors are computed in FP32 in chunks of at most this many MiB, each chunk of grains
+                            used for its basis solves, then kept only as BF16 (0 = default, 6144); the result does
+                            not depend on it */
 } hplmm_options;
 
 enum { HPLMM_BASIS_DIRECT = 0, HPLMM_BASIS_PCG = 1, HPLMM_BASIS_PCG_WARM = 2 };
@@ -253,7 +257,14 @@ typedef struct {
   long long grain_dofs;           /* sum of local DOFs of the grain blocks */
   long long contact_dofs;         /* sum of local DOFs of the contact-grid blocks */
   long long panel_elems;          /* stored basis-panel elements sum N_g k_g */
-  int local_elem_bytes;           /* bytes per stored local factor / panel element */
+  int local_elem_bytes;           /* bytes per local factor element read by the apply (8 FP64, 4 FP32, 2 in the
+                                     BF16 form) */
+  long long n_nodes;              /* existing fine nodes (vectors inside the library are 3 n_nodes long) */
+  long long sell_blocks;          /* stored 3x3 blocks of the sliced-ELL copy of A_hat (padding included) */
+  long long coarse_solve_bytes;   /* bytes of the coarse factor read by one coarse solve (L and inv(L_pp)) */
+  double coarse_factor_flops;     /* flops of the multifrontal coarse Cholesky (pivot blocks, panels, updates) */
+  long long coarse_fronts;        /* fronts of the coarse factor */
+  long long coarse_front_bytes;   /* device bytes of the fronts (dense, m x m each) */
 } hplmm_costs;
 
 hplmm_status hplmm_get_costs(hplmm_ctx *ctx, hplmm_costs *out);

@@ -85,6 +85,7 @@ void validate_options(const hplmm_options &o) {
   HP_REQUIRE(o.basis_tol > 0.0 && o.basis_tol < 1.0, HPLMM_ERR_INVALID, "basis_tol must lie in (0, 1)");
   HP_REQUIRE(o.basis_max_iters >= 1, HPLMM_ERR_INVALID, "basis_max_iters must be positive");
   HP_REQUIRE(o.smoother_ctas >= 0 && o.smoother_ctas <= 2, HPLMM_ERR_INVALID, "smoother_ctas must be 0, 1 or 2");
+  HP_REQUIRE(o.stage_mb >= 0, HPLMM_ERR_INVALID, "stage_mb must be non-negative");
 }
 
 void require_setup(hplmm_ctx *c) {
@@ -202,16 +203,28 @@ hplmm_status hplmm_setup(hplmm_ctx *c, const int32_t *partition, int n_grains, i
       hp::build_mortars(c);
       hp::build_local_sets(c);
     }
-    double t1 = now_s();
-    // smoother build (T_ML): exact local factorisations of grains and contact grids
-    hp::factor_local_both(c, c->opt.local_prec);
-    hp::check_status(c);
-    double t2 = now_s();
-    // coarse build (T_MG): basis solves, Galerkin product, coarse Cholesky
-    hp::build_coarse(c, c->b_corr.p);
+    double t1 = now_s(), t2, t3;
+    const bool staged = c->opt.local_prec == HPLMM_FP32 && c->opt.apply_prec == HPLMM_BF16 &&
+                        c->opt.basis_solver == HPLMM_BASIS_DIRECT;
+    if (staged) {
+      // BF16 form: FP32 factors in chunks, each chunk of grains used for its basis solves, then kept as
+      // BF16 (the local factorisations and basis solves are timed together as the smoother build)
+      hp::coarse_rhs(c, c->b_corr.p);
+      hp::factor_staged(c, c->X32.p, c->panel_off, c->kg, c->h_kg);
+      hp::check_status(c);
+      t2 = now_s();
+      hp::coarse_finish(c);
+    } else {
+      // smoother build (T_ML): exact local factorisations of grains and contact grids
+      hp::factor_local_both(c, c->opt.local_prec);
+      hp::check_status(c);
+      t2 = now_s();
+      // coarse build (T_MG): basis solves, Galerkin product, coarse Cholesky
+      hp::build_coarse(c, c->b_corr.p);
+    }
     alloc_work(c);
     hp::check_status(c);
-    double t3 = now_s();
+    t3 = now_s();
     // pipeline depths of the smoother solves (part of the smoother build)
     hp::tune_local(c);
     double t4 = now_s();
@@ -394,7 +407,7 @@ hplmm_status hplmm_get_costs(hplmm_ctx *c, hplmm_costs *out) {
     HP_REQUIRE(out, HPLMM_ERR_INVALID, "get_costs: null output");
     std::memset(out, 0, sizeof(*out));
     out->nnzb = c->nnzb;
-    out->local_elem_bytes = c->opt.local_prec == HPLMM_FP64 ? 8 : 4;
+    out->local_elem_bytes = c->opt.local_prec == HPLMM_FP64 ? 8 : (c->opt.apply_prec == HPLMM_BF16 ? 2 : 4);
     auto acc = [&](const hp::LocalSet &S, long long &elems, double &flops, long long &dofs) {
       elems = S.h_band_off.empty() ? 0 : S.h_band_off.back();
       for (int k = 0; k < S.count; ++k) {
@@ -407,6 +420,12 @@ hplmm_status hplmm_get_costs(hplmm_ctx *c, hplmm_costs *out) {
     for (int g = 0; g < c->grains.count; ++g)
       out->basis_solve_flops += 4.0 * c->grains.h_n[g] * c->grains.h_bw[g] * c->h_kg[g];
     out->panel_elems = c->h_panel_off.empty() ? 0 : c->h_panel_off.back();
+    out->n_nodes = c->n_nodes;
+    out->sell_blocks = (long long)c->sell_col.n;
+    out->coarse_solve_bytes = c->cf.solve_bytes;
+    out->coarse_factor_flops = c->cf.flops;
+    out->coarse_fronts = c->cf.nf;
+    out->coarse_front_bytes = 8LL * c->cf.F_total;
   });
 }
 

@@ -453,7 +453,7 @@ void galerkin(hplmm_ctx *c, const Buf<int> &gbox, const std::vector<long long> &
 
 }  // namespace
 
-void build_coarse(hplmm_ctx *c, const double *b_corr) {
+void coarse_rhs(hplmm_ctx *c, const double *b_corr) {
   cudaStream_t s = c->stream;
   int G = c->n_grains;
   bool f64 = c->opt.local_prec == HPLMM_FP64;
@@ -493,24 +493,33 @@ void build_coarse(hplmm_ctx *c, const double *b_corr) {
                                             c->panel_off.p, b_corr, c->opt.strict_two_grain, c->X32.p);
   HP_CHECK_LAUNCH();
   }
+  if (!f64 && c->opt.basis_solver == HPLMM_BASIS_DIRECT && c->opt.keep_basis_rhs) {
+    c->Xrhs.alloc(std::max<long long>(poff[G], 1));
+    HP_CUDA(cudaMemcpyAsync(c->Xrhs.p, c->X32.p, sizeof(float) * poff[G], cudaMemcpyDeviceToDevice, s));
+  } else if (f64 || c->opt.basis_solver == HPLMM_BASIS_DIRECT) {
+    c->Xrhs.release();
+  }
+}
+
+void coarse_basis_solve(hplmm_ctx *c) {
   // batched local solves (Eqs. col_pk, col_cg): X_g <- (A^g_g)^{-1} X_g, exactly by the banded factors, or by
   // block-Jacobi CG from a zero or a learned initial guess (FP32 locals only)
   c->bstats = hplmm_basis_stats{};
-  if (f64) {
+  if (c->opt.local_prec == HPLMM_FP64) {
     solve_local_multi_f64(c, c->grains, c->X64.p, c->panel_off, c->kg, c->h_kg);
-    c->Xrhs.release();
   } else if (c->opt.basis_solver == HPLMM_BASIS_DIRECT) {
-    if (c->opt.keep_basis_rhs) {
-      c->Xrhs.alloc(std::max<long long>(poff[G], 1));
-      HP_CUDA(cudaMemcpyAsync(c->Xrhs.p, c->X32.p, sizeof(float) * poff[G], cudaMemcpyDeviceToDevice, s));
-    } else {
-      c->Xrhs.release();
-    }
     solve_local_multi_f32(c, c->grains, c->X32.p, c->panel_off, c->kg, c->h_kg);
   } else {
     ProfScope ps_it(c, HPLMM_PH_BASIS_SOLVE);
     ws_pcg_basis(c, c->opt.basis_solver == HPLMM_BASIS_PCG_WARM);
   }
+}
+
+void coarse_finish(hplmm_ctx *c) {
+  cudaStream_t s = c->stream;
+  int G = c->n_grains;
+  bool f64 = c->opt.local_prec == HPLMM_FP64;
+  const std::vector<long long> &poff = c->h_panel_off;
   if (!f64 && c->opt.apply_prec == HPLMM_BF16) {
     c->X16.alloc(std::max<long long>(poff[G], 1));
     to_bf16(c->X32.p, c->X16.p, poff[G], s);
@@ -597,6 +606,12 @@ void build_coarse(hplmm_ctx *c, const double *b_corr) {
     cf_factor(c);
   }
   HP_CUDA(cudaStreamSynchronize(s));
+}
+
+void build_coarse(hplmm_ctx *c, const double *b_corr) {
+  coarse_rhs(c, b_corr);
+  coarse_basis_solve(c);
+  coarse_finish(c);
 }
 
 void coarse_apply(hplmm_ctx *c, const double *r_pad, double *z_pad) {

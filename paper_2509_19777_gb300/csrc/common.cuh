@@ -295,6 +295,7 @@ struct hplmm_ctx {
 
   // ---- local problems
   hp::LocalSet grains, contacts;
+  hp::Buf<float> stage32;          // FP32 chunk of the staged BF16 set-up
 
   // ---- coarse space (Section 4.2)
   hp::Buf<double> X64;             // basis panels X_g (local DOF rows x k_g), FP64
@@ -408,6 +409,8 @@ void solve_local_multi_f64(hplmm_ctx *c, LocalSet &S, double *X, const Buf<long 
 void solve_local_multi_f32(hplmm_ctx *c, LocalSet &S, float *X, const Buf<long long> &x_off, const Buf<int> &x_ld,
                            const std::vector<int> &h_ld);
 void smoother_apply(hplmm_ctx *c, LocalSet &S, const double *r_pad, double *z_pad, bool atomic);
+void factor_staged(hplmm_ctx *c, float *X, const Buf<long long> &x_off, const Buf<int> &x_ld,
+                   const std::vector<int> &h_ld);  // BF16 form: chunked FP32 factors + basis solves -> BF16
 void solve_local_multi_f32_subset(hplmm_ctx *c, LocalSet &S, float *X, const Buf<long long> &x_off,
                                   const Buf<int> &x_ld, const std::vector<int> &h_ld, const std::vector<int> &grains);
 // ws.cu
@@ -421,7 +424,10 @@ double ws_loss_grad(hplmm_ctx *c, const float *theta, const float *x, const floa
 void ws_pcg_basis(hplmm_ctx *c, bool warm);
 int num_sms();
 // coarse.cu
-void build_coarse(hplmm_ctx *c, const double *b_pad_for_corr);
+void build_coarse(hplmm_ctx *c, const double *b_pad_for_corr);  // = the three steps below
+void coarse_rhs(hplmm_ctx *c, const double *b_pad_for_corr);     // panels X_g = right-hand sides
+void coarse_basis_solve(hplmm_ctx *c);                             // X_g <- (A^g_g)^{-1} X_g
+void coarse_finish(hplmm_ctx *c);                                  // Galerkin product, coarse factor
 // cfactor.cu: symbolic analysis from the grains' voxel boxes (lo[3], ext[3] per grain), numeric
 // factorisation of the fronts the Galerkin product filled, and x = (A^o)^{-1} t (t is overwritten, y is
 // work; all three of length N^o)

@@ -469,6 +469,8 @@ __device__ __forceinline__ void mma_tf32(float (&d)[4], const uint32_t (&a)[4], 
 // alternate between the two; a cluster barrier (release / acquire) ends each panel, so the next panel's
 // loads, which read L2 only, see both CTAs' tile updates.  The factor is bit-identical to CL = 1.
 constexpr int CHOL32_THREADS = 512;
+// FP32 scratch of the staged BF16 set-up (floats): one chunk of local factors at a time
+constexpr long long STAGE_ELEMS = 3LL << 29;
 constexpr int CHOL32_LD = 36;
 // row stride of a warp's staged 32x32 trailing tile: with 40 floats, the 8-byte pairs each lane reads in
 // the MMA accumulator layout (row g8 (+8, +16), columns 2 tq, 2 tq + 1) fall on 32 distinct banks per
@@ -2139,7 +2141,9 @@ static void bf16_copy(hplmm_ctx *c, LocalSet &S, hplmm_prec prec) {
 
 template <typename T>
 static void solve_multi_t(hplmm_ctx *c, LocalSet &S, T *X, const Buf<long long> &x_off, const Buf<int> &x_ld,
-                          const std::vector<int> &h_ld, const std::vector<int> *only = nullptr) {
+                          const std::vector<int> &h_ld, const std::vector<int> *only = nullptr,
+                          const T *band = nullptr, long long bbase = 0) {
+  if (!band) band = band_ptr<T>(S);
   constexpr int NB = NBOf<T>::v;
   cudaStream_t s = c->stream;
   std::vector<int> items;
@@ -2172,9 +2176,9 @@ static void solve_multi_t(hplmm_ctx *c, LocalSet &S, T *X, const Buf<long long> 
                "local problem half bandwidth " + std::to_string(rpmax - NB) + " is too large for the basis solves");
     HP_CUDA(cudaFuncSetAttribute(k_band_solve_multi32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     k_band_solve_multi32<<<n_items, SM32_THREADS, smem, s>>>(it.p, n_items, S.n.p, S.bw.p, S.band_off.p,
-                                                             band_ptr<T>(S), X, x_off.p, x_ld.p, XR, 0LL);
+                                                             band, X, x_off.p, x_ld.p, XR, bbase);
   } else {
-    k_band_solve_multi<T, NB><<<n_items, 256, 0, s>>>(it.p, n_items, S.n.p, S.bw.p, S.band_off.p, band_ptr<T>(S),
+    k_band_solve_multi<T, NB><<<n_items, 256, 0, s>>>(it.p, n_items, S.n.p, S.bw.p, S.band_off.p, band,
                                                       X, x_off.p, x_ld.p);
   }
   HP_CHECK_LAUNCH();
@@ -2192,6 +2196,60 @@ void solve_local_multi_f32_subset(hplmm_ctx *c, LocalSet &S, float *X, const Buf
 void solve_local_multi_f32(hplmm_ctx *c, LocalSet &S, float *X, const Buf<long long> &x_off, const Buf<int> &x_ld,
                            const std::vector<int> &h_ld) {
   solve_multi_t<float>(c, S, X, x_off, x_ld, h_ld);
+}
+
+// Staged set-up of the BF16 form: the apply streams BF16 copies of the FP32 local factors, so the FP32
+// factors need not outlive the set-up.  Each set is factored in chunks of consecutive problems whose FP32
+// bands fit a scratch buffer (options.stage_mb, default STAGE_ELEMS floats); a chunk of grains serves its grains' basis solves (Eqs.
+// col_pk, col_cg) while it is FP32, then every chunk is rounded to BF16 into the set's BF16 band.  The
+// result equals the unstaged form's (the same FP32 factors and solves); the device then holds the BF16
+// bands, one FP32 chunk and the FP32 panels, instead of every FP32 band and its BF16 copy.
+void factor_staged(hplmm_ctx *c, float *X, const Buf<long long> &x_off, const Buf<int> &x_ld,
+                   const std::vector<int> &h_ld) {
+  cudaStream_t s = c->stream;
+  c->bstats = hplmm_basis_stats{};
+  for (int which = 0; which < 2; ++which) {
+    LocalSet &S = which == 0 ? c->grains : c->contacts;
+    const int where = which == 0 ? 1 : 2;
+    S.prec = HPLMM_FP32;
+    S.apply_bf16 = true;
+    S.band32.release();
+    const int K = S.count;
+    if (K == 0) continue;
+    const int bwmax = layout_set<float>(S, s);
+    const std::vector<long long> &boff = S.h_band_off;
+    S.band16.alloc(std::max<long long>(boff[K], 1));
+    long long most = 1;
+    for (int k = 0; k < K; ++k) most = std::max(most, boff[k + 1] - boff[k]);
+    const long long budget = c->opt.stage_mb > 0 ? ((long long)c->opt.stage_mb << 20) / 4 : STAGE_ELEMS;
+    const long long cap = std::max(most, std::min<long long>(boff[K], budget));
+    c->stage32.alloc(cap);
+    const std::vector<int> ord = S.order.download(s, K);
+    Buf<int> plist;
+    for (int k0 = 0; k0 < K;) {
+      int k1 = k0 + 1;
+      while (k1 < K && boff[k1 + 1] - boff[k0] <= cap) ++k1;
+      const long long base = boff[k0], elems = boff[k1] - boff[k0];
+      std::vector<int> pl;  // the chunk's problems, most expensive first
+      for (int k : ord)
+        if (k >= k0 && k < k1) pl.push_back(k);
+      HP_CUDA(cudaStreamSynchronize(s));  // the previous chunk's list is read until here
+      plist.upload(pl, s);
+      {
+        ProfScope ps(c, HPLMM_PH_FACTOR_GRAINS);
+        HP_CUDA(cudaMemsetAsync(c->stage32.p, 0, sizeof(float) * elems, s));
+        k_local_extract<float><<<(unsigned)pl.size(), 128, 0, s>>>(
+            S.box.p, S.node_off.p, S.n.p, S.bw.p, S.band_off.p, S.lmap.p, S.lnodes.p, c->node_ijk.p, c->row_ptr.p,
+            c->col.p, c->val64.p, c->fixed.p, c->stage32.p, 32, plist.p, base);
+        HP_CHECK_LAUNCH();
+        launch_chol32(c, S, where, s, plist.p, (int)pl.size(), c->stage32.p, base, bwmax);
+      }
+      if (which == 0) solve_multi_t<float>(c, S, X, x_off, x_ld, h_ld, &pl, c->stage32.p, base);
+      to_bf16(c->stage32.p, S.band16.p + base, elems, s);
+      k0 = k1;
+    }
+    HP_CUDA(cudaStreamSynchronize(s));
+  }
 }
 
 // shared-memory plan of the smoother solve for a set: stored-row width (128 bytes for FP32/FP64 factors, 64

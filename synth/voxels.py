@@ -101,27 +101,34 @@ def lognormal_modulus(shape, sigma_corr, rng, mu=0.0, sigma=1.0):
 
 
 def _slits_and_voronoi(shape, rng, n_slits=20, radius=32.0, n_seeds=64, contrast=1e-4, phases=(1.0, 10.0)):
+    from scipy.spatial import cKDTree
     nz, ny, nx = shape
-    zz, yy, xx = np.meshgrid(np.arange(nz) + 0.5, np.arange(ny) + 0.5, np.arange(nx) + 0.5, indexing="ij")
-    pts = np.stack([xx.ravel(), yy.ravel(), zz.ravel()], axis=1)
     seeds = rng.uniform(0.0, 1.0, size=(n_seeds, 3)) * np.array([nx, ny, nz])
     phase = rng.integers(0, 2, size=n_seeds)
-    E = np.empty(pts.shape[0], np.float64)
-    chunk = 1 << 20
-    for s in range(0, pts.shape[0], chunk):
-        p = pts[s:s + chunk]
-        d2 = ((p[:, None, :] - seeds[None, :, :]) ** 2).sum(axis=2)
-        E[s:s + chunk] = np.where(phase[np.argmin(d2, axis=1)] == 0, phases[0], phases[1])
+    tree = cKDTree(seeds)
+    E = np.empty(nz * ny * nx, np.float64)
+    xs, ys = np.arange(nx) + 0.5, np.arange(ny) + 0.5
+    yy, xx = np.meshgrid(ys, xs, indexing="ij")
+    for k in range(nz):  # one z-layer of voxel centres at a time
+        pts = np.stack([xx.ravel(), yy.ravel(), np.full(xx.size, k + 0.5)], axis=1)
+        _, near = tree.query(pts)
+        E[k * ny * nx:(k + 1) * ny * nx] = np.where(phase[near] == 0, phases[0], phases[1])
+    E = E.reshape(shape)
     for _ in range(n_slits):
         c = rng.uniform(0.0, 1.0, size=3) * np.array([nx, ny, nz])
         nrm = rng.standard_normal(3)
         nrm /= np.linalg.norm(nrm)
-        rel = pts - c
+        # only voxel centres within radius + 1 of the centre can lie on the disk: test that box
+        lo = np.maximum(np.floor(c - radius - 1).astype(int), 0)
+        hi = np.minimum(np.ceil(c + radius + 1).astype(int), [nx, ny, nz])
+        zz, yy2, xx2 = np.meshgrid(np.arange(lo[2], hi[2]) + 0.5, np.arange(lo[1], hi[1]) + 0.5,
+                                   np.arange(lo[0], hi[0]) + 0.5, indexing="ij")
+        rel = np.stack([xx2 - c[0], yy2 - c[1], zz - c[2]], axis=-1)
         dn = rel @ nrm
-        dt2 = (rel * rel).sum(axis=1) - dn * dn
+        dt2 = (rel * rel).sum(axis=-1) - dn * dn
         hit = (np.abs(dn) <= 0.5) & (dt2 <= radius * radius)
-        E[hit] *= contrast
-    return E.reshape(shape).astype(np.float32)
+        E[lo[2]:hi[2], lo[1]:hi[1], lo[0]:hi[0]][hit] *= contrast
+    return E.astype(np.float32)
 
 
 def make_workload(name, seed=0):
@@ -144,11 +151,16 @@ def make_workload(name, seed=0):
         mask = porous_mask(shape, 0.4, 3.0, rng)
         E = lognormal_modulus(shape, 3.0, rng)
         return Problem(name, mask, E, 0.3, (8, 8, 8), bcs_clamped_traction(), 4, seed)
-    if name == "fractured256":
-        shape = (256, 256, 256)
+    if name.startswith("fractured"):
+        # fractured<n>: the 256^3 recipe at edge n (16^3-voxel grains); smaller edges keep the slit radius and
+        # scale the slit and Voronoi seed counts with the volume (at least 3 slits and 8 seeds)
+        n = int(name[len("fractured"):])
+        shape = (n, n, n)
+        frac = (n / 256.0) ** 3
         mask = porous_mask(shape, 0.25, 2.0, rng)
-        E = _slits_and_voronoi(shape, rng)
-        return Problem(name, mask, E, 0.25, (16, 16, 16), bcs_clamped_traction(), 2, seed)
+        E = _slits_and_voronoi(shape, rng, n_slits=max(3, int(round(20 * frac))),
+                               n_seeds=max(8, int(round(64 * frac))))
+        return Problem(name, mask, E, 0.25, (n // 16,) * 3, bcs_clamped_traction(), 2, seed)
     if name.startswith("tiny"):
         # tiny<n>: porous n^3 block with 2x2x2 subdomains, small enough for dense checks
         n = int(name[4:])

@@ -16,6 +16,9 @@ CASES = {
     "tiny10_n1": ("tiny10", 5, dict(n_mortar=1, contact_halfwidth=1)),
     "tiny10_strict": ("tiny10", 6, dict(n_mortar=3, contact_halfwidth=1, strict_two_grain=True)),
     "porous32_n4": ("porous32", 1, dict(n_mortar=4, contact_halfwidth=2)),
+    # the fractured recipe at 32^3 (2x2x2 grains): Voronoi two-phase E in {1, 10} and three one-voxel slits
+    # with E x 1e-4 crossing the grains and their interfaces
+    "fractured32_n2": ("fractured32", 0, dict(n_mortar=2, contact_halfwidth=2)),
     # large local sets: 216 grains of 4^3 voxels (more grains than half the SMs: one CTA per problem in the
     # factorisation) and 512 grains (more problems than two per SM: the persistent queue hands CTAs several
     # problems), both with more than 500 contact grids and a deep coarse elimination tree

@@ -25,7 +25,7 @@ def _n(t):
     return t.detach().cpu().numpy()
 
 
-@pytest.fixture(scope="module", params=SMALL + ["porous32_n4"])
+@pytest.fixture(scope="module", params=SMALL + ["porous32_n4", "fractured32_n2"])
 def case(request):
     name = request.param
     p, opt, sysm, M = oracle_case(name)
@@ -111,7 +111,7 @@ def test_solve_fp64(case):
     assert abs(st.iters - st_ref["iters"]) <= 2
 
 
-@pytest.mark.parametrize("name", ["cube16_n4", "porous32_n4"])
+@pytest.mark.parametrize("name", ["cube16_n4", "porous32_n4", "fractured32_n2"])
 @pytest.mark.parametrize("local,applyp", [("fp32", "fp32"), ("fp32", "fp64"), ("fp64", "fp32")])
 def test_mixed_precision_forms(name, local, applyp):
     # FP32 local factors / basis / smoother and FP32 SpMV inside the apply: the outer FP64 FGMRES still
