@@ -55,8 +55,10 @@ typedef struct {
   int contact_halfwidth; /* w: contact grid = nodes within L-inf distance w of an interface (Section 3.1) */
   int n_st;              /* smoother stages, Eq. local_smoother (paper: 1 with M_CG) */
   hplmm_prec local_prec; /* precision of local factorisations and basis solves: FP64 or FP32 */
-  hplmm_prec apply_prec; /* precision of the preconditioner apply (SpMV, smoother, restriction and
-                            prolongation): FP64, FP32 or BF16 storage, FP32 accumulation for the latter two */
+  hplmm_prec apply_prec; /* precision of the preconditioner apply: FP64 (everything), FP32 (local factors,
+                            basis panels and the A_hat of its residual updates stored in FP32, FP32
+                            arithmetic) or BF16 (local factors and basis panels stored in BF16, the residual
+                            updates' A_hat in FP32, FP32 arithmetic); the coarse solve is FP64 in every form */
   int restart;           /* GMRES restart length (default 30) */
   int max_iters;         /* cap on total GMRES iterations (paper: 300) */
   int strict_two_grain;  /* 1: shape vectors only on the two grains of each interface (the paper's

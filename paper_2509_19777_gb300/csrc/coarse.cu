@@ -449,6 +449,7 @@ void galerkin(hplmm_ctx *c, const Buf<int> &gbox, const std::vector<long long> &
     g0 = g1;
   }
   HP_CUDA(cudaStreamSynchronize(s));
+  work.release();
 }
 
 }  // namespace

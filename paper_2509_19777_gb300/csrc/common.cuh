@@ -254,7 +254,6 @@ struct hplmm_ctx {
   hp::Buf<int> sell_col;           // block column per entry (slot-major within a slice)
   hp::Buf<double> sell_val64;      // 9 values per entry, element-major within a slot
   hp::Buf<float> sell_val32;
-  hp::Buf<__nv_bfloat16> sell_val16;  // BF16 copy (only for the BF16 apply form)
   hp::Buf<double> b_pad;           // n_nodes*3 right-hand side, 0 on fixed slots
   hp::Buf<double> b_corr;          // right-hand side defining the correction columns (padded)
 

@@ -2250,6 +2250,7 @@ void factor_staged(hplmm_ctx *c, float *X, const Buf<long long> &x_off, const Bu
     }
     HP_CUDA(cudaStreamSynchronize(s));
   }
+  c->stage32.release();  // the rest of the set-up and the solve need the memory more than the next set-up
 }
 
 // shared-memory plan of the smoother solve for a set: stored-row width (128 bytes for FP32/FP64 factors, 64
