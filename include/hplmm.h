@@ -85,6 +85,10 @@ typedef struct {
                             factors are computed in FP32 in chunks of at most this many MiB, each chunk of grains
                             used for its basis solves, then kept only as BF16 (0 = default, 6144); the result does
                             not depend on it */
+  int wait_budget_us;    /* budget of each bounded device-side wait in the smoother's pipelined solves, in
+                            microseconds at the nominal 2,070 MHz SM clock (0 = default, about 2 s); a wait that
+                            runs out makes the launch stop and the next synchronising call return
+                            HPLMM_ERR_TIMEOUT (a small value is how the tests exercise that path) */
 } hplmm_options;
 
 enum { HPLMM_BASIS_DIRECT = 0, HPLMM_BASIS_PCG = 1, HPLMM_BASIS_PCG_WARM = 2 };
@@ -173,8 +177,10 @@ hplmm_status hplmm_spmv(hplmm_ctx *ctx, const double *x, double *y);
  * up the array's device address once (make that first call before any stream
  * capture).  All calls share the array and it keeps the previous call's
  * contents (the padded input is cleared each call); calls that overlap on the
- * GPU race.  x, y: DEVICE float64 [n_dof].  Asynchronous on the context's
- * stream. */
+ * GPU race.  The context's device must be the current device
+ * (HPLMM_ERR_INVALID otherwise), and the cached address assumes the device's
+ * primary context is not reset while the library is loaded.  x, y: DEVICE
+ * float64 [n_dof].  Asynchronous on the context's stream. */
 hplmm_status hplmm_spmv_noalloc(hplmm_ctx *ctx, const double *x, double *y);
 
 /* Right-preconditioned FGMRES(restart) with CGS2 Arnoldi in FP64 (Section 5),
@@ -247,6 +253,12 @@ hplmm_status hplmm_reset_profile(hplmm_ctx *ctx);
 
 /* Process-wide number of CUDA kernels this library has launched. */
 long long hplmm_kernel_launches(void);
+
+/* Testing aid (the paper has no counterpart): after `after` more device allocations by the library, the next
+ * one fails as if the device were out of memory, and the call that made it returns HPLMM_ERR_OOM; later
+ * allocations succeed again.  A negative value cancels a pending failure.  Process-wide; it lets a caller
+ * exercise its out-of-memory handling without exhausting the device. */
+void hplmm_inject_alloc_failure(long long after);
 
 /* Algorithmic sizes of the current set-up, for roofline accounting (HOST output). */
 typedef struct {

@@ -385,6 +385,7 @@ int fgmres(hplmm_ctx *c, const double *b_pad, double *x_pad, double tol, hplmm_s
   HP_CUDA(cudaMemcpyAsync(hh.data(), dev_h, sizeof(double), cudaMemcpyDeviceToHost, s));
   HP_CUDA(cudaStreamSynchronize(s));
   double bnorm = std::sqrt(hh[0]);
+  HP_REQUIRE(std::isfinite(bnorm), HPLMM_ERR_INVALID, "solve: the right-hand side has non-finite entries");
   int its = 0, restarts = 0;
   double rel = 0.0;
   if (bnorm == 0.0) {

@@ -369,6 +369,14 @@ __global__ void k_spmv_sell(const int *slice_off, const int *scol, const T *sval
 
 }  // namespace
 
+// first solid voxel whose modulus is not a positive finite number (atomic minimum of its index)
+__global__ void k_bad_modulus(const uint8_t *mask, const float *E, long long nvox, long long *first) {
+  long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (v >= nvox || !mask[v]) return;
+  const float e = E[v];
+  if (!(e > 0.f) || !isfinite(e)) atomicMin((unsigned long long *)first, (unsigned long long)v);
+}
+
 void assemble(hplmm_ctx *c, const uint8_t *mask, int nx, int ny, int nz, const float *E, double E0, double nu,
               const hplmm_bcs *bcs, double *b_out) {
   HP_REQUIRE(mask != nullptr && bcs != nullptr, HPLMM_ERR_INVALID, "assemble: mask and bcs are required");
@@ -395,6 +403,18 @@ void assemble(hplmm_ctx *c, const uint8_t *mask, int nx, int ny, int nz, const f
     std::vector<float> h(nvox, (float)E0);
     HP_CUDA(cudaMemcpyAsync(c->E.p, h.data(), nvox * sizeof(float), cudaMemcpyHostToDevice, s));
     HP_CUDA(cudaStreamSynchronize(s));
+  }
+  {
+    // a solid voxel with E <= 0, NaN or infinite would make A_hat indefinite or undefined
+    Buf<long long> first;
+    first.alloc(1);
+    first.fill_bytes(0x7f, s);
+    k_bad_modulus<<<grid_for(nvox, 256), 256, 0, s>>>(c->mask.p, c->E.p, nvox, first.p);
+    HP_CHECK_LAUNCH();
+    const long long v = first.download(s, 1)[0];
+    HP_REQUIRE(v >= nvox, HPLMM_ERR_INVALID,
+               "assemble: solid voxel (" + std::to_string(v % nx) + ", " + std::to_string((v / nx) % ny) + ", " +
+                   std::to_string(v / ((long long)nx * ny)) + ") has a modulus that is not a positive finite number");
   }
   c->n_grid = (long long)(nx + 1) * (ny + 1) * (nz + 1);
   Buf<int> flag;
@@ -476,6 +496,8 @@ void assemble(hplmm_ctx *c, const uint8_t *mask, int nx, int ny, int nz, const f
     HP_CHECK_LAUNCH();
     c->val32.release();
   }
+  // every connected solid part needs a prescribed displacement, else A_hat is singular (rigid motions)
+  check_anchored(c);
   if (b_out) gather_free(c, c->b_pad.p, b_out);
   HP_CUDA(cudaStreamSynchronize(s));
   c->assembled = true;

@@ -11,6 +11,14 @@ using hp::Error;
 
 namespace hp {
 static std::atomic<long long> g_launches{0};
+static std::atomic<long long> g_fail_after{-1};  // allocations left before the injected failure; -1: none
+bool alloc_should_fail() {
+  long long v = g_fail_after.load();
+  while (v >= 0) {
+    if (g_fail_after.compare_exchange_weak(v, v - 1)) return v == 0;
+  }
+  return false;
+}
 long long note_launch() { return ++g_launches; }
 long long launch_count() { return g_launches.load(); }
 void add_launches(long long n) { g_launches += n; }
@@ -86,6 +94,7 @@ void validate_options(const hplmm_options &o) {
   HP_REQUIRE(o.basis_max_iters >= 1, HPLMM_ERR_INVALID, "basis_max_iters must be positive");
   HP_REQUIRE(o.smoother_ctas >= 0 && o.smoother_ctas <= 2, HPLMM_ERR_INVALID, "smoother_ctas must be 0, 1 or 2");
   HP_REQUIRE(o.stage_mb >= 0, HPLMM_ERR_INVALID, "stage_mb must be non-negative");
+  HP_REQUIRE(o.wait_budget_us >= 0, HPLMM_ERR_INVALID, "wait_budget_us must be non-negative");
 }
 
 void require_setup(hplmm_ctx *c) {
@@ -400,6 +409,8 @@ hplmm_status hplmm_reset_profile(hplmm_ctx *c) {
 }
 
 long long hplmm_kernel_launches(void) { return hp::launch_count(); }
+
+void hplmm_inject_alloc_failure(long long after) { hp::g_fail_after.store(after < 0 ? -1 : after); }
 
 hplmm_status hplmm_get_costs(hplmm_ctx *c, hplmm_costs *out) {
   return guarded(c, [&] {

@@ -44,6 +44,9 @@ long long note_launch();
     if (!(cond)) throw ::hp::Error(code, msg); \
   } while (0)
 
+// test hook (hplmm_inject_alloc_failure): true when this device allocation is to fail as if out of memory
+bool alloc_should_fail();
+
 // ---------------------------------------------------------------- device buffer
 template <typename T>
 struct Buf {
@@ -66,6 +69,9 @@ struct Buf {
       return;
     }
     release();
+    if (alloc_should_fail())
+      throw Error(HPLMM_ERR_OOM, "cudaMalloc of " + std::to_string(count * sizeof(T)) +
+                                     " bytes failed: injected failure (hplmm_inject_alloc_failure)");
     cudaError_t e = cudaMalloc(&p, count * sizeof(T));
     if (e != cudaSuccess) {
       p = nullptr;
@@ -394,6 +400,7 @@ void spmv(hplmm_ctx *c, const double *x_pad, double *y_pad, hplmm_prec prec, con
 void gather_free(hplmm_ctx *c, const double *pad, double *dof);
 void scatter_free(hplmm_ctx *c, const double *dof, double *pad);
 // maps.cu
+void check_anchored(hplmm_ctx *c);  // throws HPLMM_ERR_SINGULAR when a solid part has no prescribed displacement
 void build_maps(hplmm_ctx *c, const int32_t *partition);
 void build_mortars(hplmm_ctx *c);
 void compute_W(hplmm_ctx *c, int64_t *W);

@@ -1158,15 +1158,19 @@ __device__ __forceinline__ bool mbar_try_wait_cluster(uint64_t *bar, uint32_t pa
   return done != 0;
 }
 
-// bounded wait (about two seconds); gives up early when another warp has raised the abort flag
+// bounded wait: gives up after `budget` SM cycles, or early when another warp has raised the abort flag.  The
+// pipeline's waits take the caller's budget (options.wait_budget_us; about two seconds by default); the
+// drains at the end (copies and remote stores still landing in this CTA's shared memory) always take
+// WAIT_CYCLES, so that a CTA that gave up never leaves with data in flight towards it
 template <bool CLUSTER = false>
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity, const volatile int *abort_flag) {
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity, const volatile int *abort_flag,
+                                                  long long budget = WAIT_CYCLES) {
   const long long t0 = clock64();
   for (long long it = 0;; ++it) {
     if (CLUSTER ? mbar_try_wait_cluster(bar, parity) : mbar_try_wait(bar, parity)) return true;
     if ((it & 3) == 3) {
       if (abort_flag && *abort_flag) return false;
-      if (clock64() - t0 > WAIT_CYCLES) return false;
+      if (clock64() - t0 > budget) return false;
     }
   }
 }
@@ -1262,7 +1266,7 @@ template <typename S, int NB, int CL>
 __global__ void __launch_bounds__(WS_THREADS) k_band_solve_ws(
     int count, const int *nloc, const int *bwv, const long long *band_off, const long long *vec_off,
     const int *gidx, const S *band, const double *r, double *z, typename ComputeOf<S>::type *yscr, int atomic,
-    int ring_rows, int chunk_rows, int c0_stages, int wmask, int *status) {
+    int ring_rows, int chunk_rows, int c0_stages, int wmask, int *status, long long wait_cycles) {
   using T = typename ComputeOf<S>::type;
   constexpr int ROWB = NB * (int)sizeof(S);  // bytes per stored row
   static_assert(ROWB == 128 || ROWB == 64, "factor rows are 128 or 64 bytes");
@@ -1381,7 +1385,7 @@ __global__ void __launch_bounds__(WS_THREADS) k_band_solve_ws(
   auto armer = [&](uint64_t *bars) {
     bool ok = true;
     for (int j = 0; j < nsteps && ok; ++j) {
-      if (j >= 4 && !mbar_wait_bounded<true>(&bars[j & 3], (uint32_t)(((j - 4) >> 2) & 1), &s_abort)) ok = false;
+      if (j >= 4 && !mbar_wait_bounded<true>(&bars[j & 3], (uint32_t)(((j - 4) >> 2) & 1), &s_abort, wait_cycles)) ok = false;
       if (ok) mbar_expect_tx(&bars[j & 3], XBYTES);
     }
     if (!ok) {
@@ -1411,7 +1415,7 @@ __global__ void __launch_bounds__(WS_THREADS) k_band_solve_ws(
           const int alloc = whole ? slot_rows : rows;
           // release (in order) every chunk whose barrier pair or ring rows this chunk reuses
           while (rel < n && (rel <= n - WS_NSTG || start_tab[rel % WS_NSTG] < abs_pos + alloc - ring_eff)) {
-            if (!mbar_wait_bounded(&empty_far[rel % WS_NSTG], (uint32_t)((rel / WS_NSTG) & 1), &s_abort)) {
+            if (!mbar_wait_bounded(&empty_far[rel % WS_NSTG], (uint32_t)((rel / WS_NSTG) & 1), &s_abort, wait_cycles)) {
               ok = false;
               break;
             }
@@ -1445,7 +1449,7 @@ __global__ void __launch_bounds__(WS_THREADS) k_band_solve_ws(
     for (int s = 0; s < nsteps; ++s) {
       const int p = (s < np) ? s : (2 * np - 1 - s);
       const int slot = s % c0_stages;
-      if (s >= c0_stages && !mbar_wait_bounded(&empty_c0[slot], (uint32_t)((s / c0_stages - 1) & 1), &s_abort)) {
+      if (s >= c0_stages && !mbar_wait_bounded(&empty_c0[slot], (uint32_t)((s / c0_stages - 1) & 1), &s_abort, wait_cycles)) {
         raise_abort();
         if (lane == 0) atomicCAS(status, 0, (int)HPLMM_ERR_TIMEOUT);
         break;
@@ -1482,17 +1486,17 @@ __global__ void __launch_bounds__(WS_THREADS) k_band_solve_ws(
       // two-CTA form: rank 1's part of panel p's rows (forward, pushed after its step s-3) or of panel p's far
       // sums (backward, pushed after its step s-2)
       if (fwd) {
-        if (s >= 1 && !mbar_wait_bounded(&urg[(s - 1) & 3], (uint32_t)(((s - 1) >> 2) & 1), &s_abort)) fail = 1;
-        if (s >= 2 && !fail && !mbar_wait_bounded(&bdone[(s - 2) & 3], (uint32_t)(((s - 2) >> 2) & 1), &s_abort))
+        if (s >= 1 && !mbar_wait_bounded(&urg[(s - 1) & 3], (uint32_t)(((s - 1) >> 2) & 1), &s_abort, wait_cycles)) fail = 1;
+        if (s >= 2 && !fail && !mbar_wait_bounded(&bdone[(s - 2) & 3], (uint32_t)(((s - 2) >> 2) & 1), &s_abort, wait_cycles))
           fail = 1;
         if (CL == 2 && p >= 3 && !fail &&
-            !mbar_wait_bounded<true>(&pdone[(s - 3) & 3], (uint32_t)(((s - 3) >> 2) & 1), &s_abort))
+            !mbar_wait_bounded<true>(&pdone[(s - 3) & 3], (uint32_t)(((s - 3) >> 2) & 1), &s_abort, wait_cycles))
           fail = 1;
       } else {
-        if (!mbar_wait_bounded(&bdone[(s - 1) & 3], (uint32_t)(((s - 1) >> 2) & 1), &s_abort)) fail = 1;
+        if (!mbar_wait_bounded(&bdone[(s - 1) & 3], (uint32_t)(((s - 1) >> 2) & 1), &s_abort, wait_cycles)) fail = 1;
         // (waited at every backward step: each completed phase frees its barrier for the bytes 4 steps later)
         if (CL == 2 && s >= 2 && !fail &&
-            !mbar_wait_bounded<true>(&pdone[(s - 2) & 3], (uint32_t)(((s - 2) >> 2) & 1), &s_abort))
+            !mbar_wait_bounded<true>(&pdone[(s - 2) & 3], (uint32_t)(((s - 2) >> 2) & 1), &s_abort, wait_cycles))
           fail = 1;
       }
       if (fwd && !fail) {
@@ -1502,7 +1506,7 @@ __global__ void __launch_bounds__(WS_THREADS) k_band_solve_ws(
         if (own && refill_row(p + 2) < N) rg = gi[refill_row(p + 2)];
       }
       const int slot = s % c0_stages;
-      if (!fail && !mbar_wait_bounded(&full_c0[slot], (uint32_t)((s / c0_stages) & 1), &s_abort)) fail = 1;
+      if (!fail && !mbar_wait_bounded(&full_c0[slot], (uint32_t)((s / c0_stages) & 1), &s_abort, wait_cycles)) fail = 1;
       if (!fail) {
         const S *c0 = c0_ring + (size_t)slot * 2 * NB * NB;
         if (fwd) {
@@ -1627,7 +1631,7 @@ __global__ void __launch_bounds__(WS_THREADS) k_band_solve_ws(
     // now; backward: the far sums of panel q), clears the window slots of panel q (read as y_q for the last
     // time) and releases the step, one arrival per lane; the bulk warps meanwhile go on with later steps
     for (int s = 0; s < nsteps; ++s) {
-      if (!mbar_wait_bounded(&r1done[s & 3], (uint32_t)((s >> 2) & 1), &s_abort)) {
+      if (!mbar_wait_bounded(&r1done[s & 3], (uint32_t)((s >> 2) & 1), &s_abort, wait_cycles)) {
         raise_abort();
         if (lane == 0) atomicCAS(status, 0, (int)HPLMM_ERR_TIMEOUT);
         break;
@@ -1670,8 +1674,8 @@ __global__ void __launch_bounds__(WS_THREADS) k_band_solve_ws(
         const int dep = (rank == 1 && !fwd) ? s - 2 : s - 1;
         if (dep >= 0) {
           const bool okw = rank == 0
-                               ? mbar_wait_bounded(&ydone[dep & 3], (uint32_t)((dep >> 2) & 1), &s_abort)
-                               : mbar_wait_bounded<true>(&ydone[dep & 3], (uint32_t)((dep >> 2) & 1), &s_abort);
+                               ? mbar_wait_bounded(&ydone[dep & 3], (uint32_t)((dep >> 2) & 1), &s_abort, wait_cycles)
+                               : mbar_wait_bounded<true>(&ydone[dep & 3], (uint32_t)((dep >> 2) & 1), &s_abort, wait_cycles);
           if (!okw) fail = 1;
         }
       }
@@ -1691,7 +1695,7 @@ __global__ void __launch_bounds__(WS_THREADS) k_band_solve_ws(
         for (int r0 = 0; r0 < nf; r0 += cr) {
           const int rows = min(cr, nf - r0);
           const int slot = n % WS_NSTG;
-          if (!fail && !mbar_wait_bounded(&full_far[slot], (uint32_t)((n / WS_NSTG) & 1), &s_abort)) fail = 1;
+          if (!fail && !mbar_wait_bounded(&full_far[slot], (uint32_t)((n / WS_NSTG) & 1), &s_abort, wait_cycles)) fail = 1;
           if (!fail) {
             // two rows per thread per pass (t and t + WS_BULK_THREADS); the choice between the one- and the
             // two-row code is made per warp (a lane without a second row re-reads its first row, with no
@@ -2349,7 +2353,8 @@ void smoother_apply(hplmm_ctx *c, LocalSet &S, const double *r_pad, double *z_pa
     HP_CUDA(cudaLaunchKernelEx(&cfg, kern, S.count, (const int *)S.n.p, (const int *)S.bw.p,
                                (const long long *)S.band_off.p, (const long long *)S.vec_off.p,
                                (const int *)S.gidx.p, band, (const double *)r_pad, z_pad, ys, atomic ? 1 : 0, ring,
-                               chunk, c0s, pl.W - 1, c->status.p));
+                               chunk, c0s, pl.W - 1, c->status.p,
+                               c->opt.wait_budget_us > 0 ? (long long)c->opt.wait_budget_us * 2070LL : WAIT_CYCLES));
   };
   if (S.prec == HPLMM_FP64) {
     if (cl == 2)

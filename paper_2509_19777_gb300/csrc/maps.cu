@@ -130,6 +130,24 @@ __global__ void k_cc_jump(const long long *pairkey, int *label, int n_nodes) {
   label[n] = l;
 }
 
+__global__ void k_cc_init(int *label, long long *key, int n_nodes) {
+  int n = blockIdx.x * blockDim.x + threadIdx.x;
+  if (n >= n_nodes) return;
+  label[n] = n;
+  key[n] = 0;
+}
+
+// a component is anchored when one of its nodes has a prescribed displacement component
+__global__ void k_anchor_mark(const uint8_t *fixed, const int *label, int n_nodes, int *anchored) {
+  int n = blockIdx.x * blockDim.x + threadIdx.x;
+  if (n < n_nodes && (fixed[3 * n] | fixed[3 * n + 1] | fixed[3 * n + 2])) anchored[label[n]] = 1;
+}
+
+__global__ void k_floating_first(const int *label, const int *anchored, int n_nodes, int *first) {
+  int n = blockIdx.x * blockDim.x + threadIdx.x;
+  if (n < n_nodes && !anchored[label[n]]) atomicMin(first, n);
+}
+
 __global__ void k_root_flags(const long long *pairkey, const int *label, int n_nodes, int *flag) {
   int n = blockIdx.x * blockDim.x + threadIdx.x;
   if (n < n_nodes) flag[n] = (pairkey[n] >= 0 && label[n] == n) ? 1 : 0;
@@ -420,6 +438,45 @@ __global__ void k_w_out(const uint64_t *keys, long long n_dof, int64_t *W) {
 }
 
 }  // namespace
+
+// Connected parts of the solid (nodes joined by a shared solid voxel, i.e. by a block of A_hat): a part with
+// no prescribed displacement component can move rigidly, so A_hat is singular; report a node of it.
+void check_anchored(hplmm_ctx *c) {
+  cudaStream_t s = c->stream;
+  const int nn = c->n_nodes;
+  Buf<int> label, anchored, changed, first;
+  Buf<long long> key;
+  label.alloc(nn);
+  key.alloc(nn);
+  anchored.alloc(nn);
+  anchored.zero(s);
+  changed.alloc(1);
+  first.alloc(1);
+  first.fill_bytes(0x7f, s);
+  k_cc_init<<<grid_for(nn, 256), 256, 0, s>>>(label.p, key.p, nn);
+  HP_CHECK_LAUNCH();
+  for (int it = 0; it < 100000; ++it) {
+    changed.zero(s);
+    k_cc_step<<<grid_for(nn, 256), 256, 0, s>>>(c->row_ptr.p, c->col.p, key.p, label.p, nn, changed.p);
+    HP_CHECK_LAUNCH();
+    k_cc_jump<<<grid_for(nn, 256), 256, 0, s>>>(key.p, label.p, nn);
+    HP_CHECK_LAUNCH();
+    if (changed.download(s, 1)[0] == 0) break;
+  }
+  k_anchor_mark<<<grid_for(nn, 256), 256, 0, s>>>(c->fixed.p, label.p, nn, anchored.p);
+  HP_CHECK_LAUNCH();
+  k_floating_first<<<grid_for(nn, 256), 256, 0, s>>>(label.p, anchored.p, nn, first.p);
+  HP_CHECK_LAUNCH();
+  const int n = first.download(s, 1)[0];
+  if (n < nn) {
+    int ijk[3];
+    HP_CUDA(cudaMemcpyAsync(ijk, c->node_ijk.p + 3LL * n, sizeof(ijk), cudaMemcpyDeviceToHost, s));
+    HP_CUDA(cudaStreamSynchronize(s));
+    throw Error(HPLMM_ERR_SINGULAR, "assemble: the solid part holding node (" + std::to_string(ijk[0]) + ", " +
+                                        std::to_string(ijk[1]) + ", " + std::to_string(ijk[2]) +
+                                        ") has no prescribed displacement: it can move rigidly (A_hat is singular)");
+  }
+}
 
 void build_maps(hplmm_ctx *c, const int32_t *partition) {
   cudaStream_t s = c->stream;

@@ -26,7 +26,8 @@ static __device__ __align__(256) double g_noalloc_scratch[2 * NOALLOC_MAX_SLOTS]
 std::mutex g_mu;
 double *g_scratch_ptr[MAX_DEVICES] = {};
 
-// the array's device address on the current device (looked up once per device)
+// the array's device address on the current device (looked up once per device and cached for the process:
+// the cache assumes the device's primary context is never reset while the library is loaded)
 double *scratch_for_device(int dev) {
   std::lock_guard<std::mutex> lock(g_mu);
   if (dev < 0 || dev >= MAX_DEVICES) throw hp::Error(HPLMM_ERR_INVALID, "device index out of range");
@@ -88,6 +89,11 @@ extern "C" hplmm_status hplmm_spmv_noalloc(hplmm_ctx *c, const double *x, double
                    std::to_string(NOALLOC_MAX_SLOTS) + " slots (262,144 nodes); use hplmm_spmv");
     int dev = 0;
     HP_CUDA(cudaGetDevice(&dev));
+    // the array's address is per device: the one looked up must be that of the device the context's
+    // stream and buffers belong to
+    HP_REQUIRE(dev == c->device, HPLMM_ERR_INVALID,
+               "spmv_noalloc: the context belongs to device " + std::to_string(c->device) +
+                   " but device " + std::to_string(dev) + " is current; make the context's device current");
     double *xp = scratch_for_device(dev);
     double *yp = xp + NOALLOC_MAX_SLOTS;
     cudaStream_t s = c->stream;

@@ -138,12 +138,18 @@ def test_bf16_apply_form(name):
     # 2^-9 ~ 2e-3) amplified by the local problems' conditioning; the outer FP64 FGMRES still reaches the FP64
     # residual, and the solution matches the oracle's to the tolerance's accuracy
     p, opt, sysm, M = oracle_case(name)
-    s = gpu_solver(name, local_prec="fp32", apply_prec="bf16")
     rng = np.random.default_rng(2)
     r = rng.standard_normal(sysm.n_dof)
+    s32 = gpu_solver(name, local_prec="fp32", apply_prec="fp32")
+    e32 = rel(_n(s32.apply(_t(r))), M.apply(r))
+    s32.close()
+    s = gpu_solver(name, local_prec="fp32", apply_prec="bf16")
     e_apply = rel(_n(s.apply(_t(r))), M.apply(r))
-    print(f"{name}: BF16 apply relative error vs FP64 oracle {e_apply:.3e}")
-    assert 1e-5 < e_apply < 0.2, e_apply  # BF16 rounding is visible, but the operator is the same
+    print(f"{name}: BF16 apply relative error vs FP64 oracle {e_apply:.3e} (FP32 form {e32:.3e})")
+    # the BF16 form is the FP32 form with its stored local factors and basis panels rounded to BF16: to first
+    # order the error grows with the unit roundoff at the amplification the FP32 form shows (see
+    # test_gpu_smoother_forms.test_bf16_error_follows_roundoff), and the rounding is visible
+    assert e32 < e_apply <= (1.0 + 2.0 ** 15) * e32, (e_apply, e32)
     x, rc, st = s.solve(tol=1e-8)
     xn = _n(x)
     assert rc == 0

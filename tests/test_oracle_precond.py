@@ -62,6 +62,32 @@ def test_schwarz_local_exactness(tiny):
             assert np.allclose(z[I], v[I], atol=1e-10 * np.abs(v).max())
 
 
+def test_contact_grid_local_exactness():
+    # M_zeta with exact local solves on principal submatrices of A_hat (Eq. local_smoother_CG): on a bar cut
+    # into three grains along x, the two contact grids (w = 1) are disjoint, so for v supported on one grid,
+    # (M_zeta A v) restricted to that grid is v itself; a dropped grid gives 0 there, a wrong submatrix
+    # (not principal, or a missing coupling) gives something else
+    shape = (4, 4, 12)                                            # [z][y][x]
+    bcs = synth.bcs_clamped_traction(traction=(0.0, 0.0, 1.0))
+    p = synth.Problem("bar", np.ones(shape, np.uint8), np.linspace(0.5, 2.0, 192).reshape(shape).astype(np.float32),
+                      0.3, (3, 1, 1), bcs, 2, 0)
+    sysm, M = precond.build(p, precond.Options(n_mortar=2, contact_halfwidth=1))
+    S = M.smoother
+    assert len(S.contact_sets) == 2
+    a, b = (set(np.asarray(c).tolist()) for c in S.contact_sets)
+    assert not (a & b)
+    rng = np.random.default_rng(1)
+    for I in S.contact_sets:
+        I = np.asarray(I)
+        v = np.zeros(sysm.n_dof)
+        v[I] = rng.standard_normal(I.size)
+        z = S.M_zeta(sysm.A @ v)
+        assert np.allclose(z[I], v[I], atol=1e-10 * np.abs(v).max())
+        # and the grid is the L-inf dilation (w = 1) of its interface plane: three node layers in x
+        xs = sysm.mesh.node_ijk[sysm.free[I] // 3, 0]
+        assert xs.max() - xs.min() == 2 and xs.min() in (3, 7)
+
+
 def test_contact_grid_is_linf_dilation():
     mask = np.ones((5, 5, 5), np.uint8)
     m = fem.Mesh(mask)
