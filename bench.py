@@ -537,6 +537,51 @@ def compare_forms(hp, np, torch, synth, spec_name, flush, stream, seed):
     return out
 
 
+def multi_load_eval(hp, torch, synth, spec_name, flush, stream, seed, k=4):
+    """Load-step reuse: one set-up, then k load cases (top-face tractions in z, x, y and a combination) solved
+    one at a time and all together in lockstep (hplmm_solve_multi), against k separate set-up + solve steps."""
+    spec = WORKLOADS[spec_name]
+    form = spec["chosen"]
+    p = synth.make_workload(spec_name, seed)
+    trs = [(0.0, 0.0, 1.0), (1.0, 0.0, 0.0), (0.0, 0.7, 0.0), (0.3, -0.4, 0.5)][:k]
+    mask, E = hp.problem_to_device(p)
+    B = []
+    for t in trs:   # the right-hand sides of the load cases, assembled by the library itself
+        sb = make_solver(hp, spec, form, stream)
+        sb.assemble(mask, E, p.nu, synth.bcs_clamped_traction(traction=t))
+        B.append(sb.b.clone())
+        sb.close()
+    B = torch.stack(B)
+    s = make_solver(hp, spec, form, stream)
+    s.assemble(mask, E, p.nu, p.bcs)
+
+    def timed(fn):
+        flush.zero_()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        out = fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / 1e3, out
+
+    s.setup(grains=p.grains)  # warm-up
+    s.solve(B[0], None, TOL)
+    t_setup, _ = timed(lambda: s.setup(grains=p.grains))
+    singles = [timed(lambda q=q: s.solve(B[q], None, TOL)) for q in range(k)]
+    s.solve_multi(B, None, TOL)  # warm-up of the multi-vector buffers
+    t_multi, (_, rc, st) = timed(lambda: s.solve_multi(B, None, TOL))
+    s.close()
+    t_single = sum(t for t, _ in singles)
+    return {"workload": spec_name, "loads": k, "form": form, "t_setup_s": t_setup,
+            "t_solve_each_s": [t for t, _ in singles], "iters_each": [o[2].iters for _, o in singles],
+            "t_solve_multi_s": t_multi, "iters_multi": [x.iters for x in st], "rc_multi": rc,
+            "per_extra_load_s_one_at_a_time": t_single / k,
+            "per_load_s_in_lockstep": t_multi / k,
+            "k_separate_setup_and_solve_s": k * t_setup + t_single,
+            "one_setup_and_lockstep_s": t_setup + t_multi}
+
+
 def main():
     args = parse()
     rank, world, local = dist_init()
@@ -646,6 +691,11 @@ def main():
                                              ["speedup_chosen_vs_plain_fp64"])
         except Exception as e:  # reported, never required for the headline
             line["plain_fp64"] = {"error": str(e)[-300:]}
+    if rank == 0 and not args.no_plain:
+        try:
+            line["multi_load"] = multi_load_eval(hp, torch, synth, PLAIN_WORKLOAD, flush, stream, args.seed)
+        except Exception as e:
+            line["multi_load"] = {"error": str(e)[-300:]}
     if rank == 0 and not args.no_ws:
         try:
             line["warm_start"] = warm_start_eval(hp, stream)

@@ -190,6 +190,20 @@ hplmm_status hplmm_spmv_noalloc(hplmm_ctx *ctx, const double *x, double *y);
  * may be NULL.  Returns HPLMM_OK or HPLMM_NOT_CONVERGED.  Synchronises. */
 hplmm_status hplmm_solve(hplmm_ctx *ctx, const double *b, double *x, double tol, hplmm_stats *st);
 
+/* Several loads on one set-up (the reuse the paper builds the preconditioner for: Section 1, Section 6.3
+ * on front-loading the set-up cost, Section 7.4).  hplmm_apply_multi: Z_q = M^{-1} R_q for q < k, the k
+ * vectors applied together: the coarse restriction and prolongation read each basis panel once per eight
+ * vectors, the SpMVs read A_hat once per four, and the smoother's local solves read each factor once per 32
+ * (the FP64 and FP32 forms; the BF16 form keeps only BF16 factors and solves vector by vector).
+ * hplmm_solve_multi: k right-preconditioned FGMRES solves in lockstep, each Arnoldi step applying M^{-1} to
+ * all unfinished solves' vectors at once; every solve keeps its own basis, restarts and stopping test
+ * (||b_q - A x_q|| / ||b_q|| <= tol); st (HOST, may be NULL) receives k entries.  R, Z, B, X: DEVICE
+ * float64 [k][n_dof] (vector q at offset q n_dof); 1 <= k <= 64; Z (X) may not alias R (B).  apply_multi is
+ * asynchronous, solve_multi synchronises.  The correction columns of the coarse space stay those of the
+ * set-up's right-hand side. */
+hplmm_status hplmm_apply_multi(hplmm_ctx *ctx, const double *R, double *Z, int k);
+hplmm_status hplmm_solve_multi(hplmm_ctx *ctx, const double *B, double *X, int k, double tol, hplmm_stats *st);
+
 /* Sizes of the index maps, for hplmm_get_maps.  HOST outputs. */
 typedef struct {
   long long n_nodes;        /* existing fine nodes */

@@ -40,7 +40,7 @@ EXPORTED = [
     "hplmm_reset_profile", "hplmm_kernel_launches", "hplmm_get_costs", "hplmm_last_error", "hplmm_destroy",
     "hplmm_ws_num_params", "hplmm_ws_set_params", "hplmm_ws_get_params", "hplmm_ws_collect", "hplmm_ws_clear",
     "hplmm_ws_train", "hplmm_ws_loss_grad", "hplmm_get_basis_stats", "hplmm_ws_get_samples",
-    "hplmm_inject_alloc_failure",
+    "hplmm_inject_alloc_failure", "hplmm_apply_multi", "hplmm_solve_multi",
 ]
 PHASES = ["maps", "factor_grains", "factor_contacts", "basis_rhs", "basis_solve", "galerkin", "coarse_chol",
           "apply_coarse", "apply_contacts", "apply_grains", "spmv", "krylov", "apply_graph"]
@@ -126,6 +126,8 @@ def load_library():
         "hplmm_reset_profile": (I, [P]),
         "hplmm_kernel_launches": (LL, []),
         "hplmm_inject_alloc_failure": (None, [LL]),
+        "hplmm_apply_multi": (I, [P, P, P, I]),
+        "hplmm_solve_multi": (I, [P, P, P, I, D, ctypes.POINTER(hplmm_stats)]),
         "hplmm_get_costs": (I, [P, ctypes.POINTER(hplmm_costs)]),
         "hplmm_last_error": (ctypes.c_char_p, [P]),
         "hplmm_ws_num_params": (LL, []),
@@ -318,6 +320,21 @@ def hplmm_inject_alloc_failure(after):
     load_library().hplmm_inject_alloc_failure(int(after))
 
 
+def hplmm_apply_multi(ctx, R, Z):
+    """Z[q] = M^{-1} R[q] for the rows q of the [k, n_dof] float64 CUDA tensors R and Z."""
+    _check(ctx, load_library().hplmm_apply_multi(ctx, _ptr(R), _ptr(Z), int(R.shape[0])))
+    return Z
+
+
+def hplmm_solve_multi(ctx, B, X, tol=1e-8):
+    """Solve A X[q] = B[q] for the rows q of [k, n_dof] float64 CUDA tensors; returns (X, rc, stats list)."""
+    k = int(B.shape[0])
+    st = (hplmm_stats * k)()
+    rc = load_library().hplmm_solve_multi(ctx, _ptr(B), _ptr(X), k, float(tol), st)
+    _check(ctx, rc, allow=(HPLMM_OK, HPLMM_NOT_CONVERGED))
+    return X, rc, list(st)
+
+
 def hplmm_get_costs(ctx):
     c = hplmm_costs()
     _check(ctx, load_library().hplmm_get_costs(ctx, ctypes.byref(c)))
@@ -466,6 +483,18 @@ class Solver:
         x = torch.empty(self.n_dof, dtype=torch.float64, device="cuda") if x is None else x
         rc, st = hplmm_solve(self.ctx, b, x, tol)
         return x, rc, st
+
+    def apply_multi(self, R, Z=None):
+        import torch
+        if Z is None:
+            Z = torch.empty_like(R)
+        return hplmm_apply_multi(self.ctx, R, Z)
+
+    def solve_multi(self, B, X=None, tol=1e-8):
+        import torch
+        if X is None:
+            X = torch.empty_like(B)
+        return hplmm_solve_multi(self.ctx, B, X, tol)
 
     def sizes(self):
         return hplmm_get_sizes(self.ctx)

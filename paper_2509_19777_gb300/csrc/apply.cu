@@ -309,6 +309,33 @@ void precond_apply(hplmm_ctx *c, const double *r_pad, double *z_pad) {
   }
 }
 
+// M^{-1} for k vectors at stride L (Eq. multi_precond with n_st stages of M_CG): the multi-right-hand-side
+// forms of the coarse correction, the SpMVs and the smoother solves read each matrix, panel and factor once
+// per group of vectors instead of once per vector
+void precond_apply_multi(hplmm_ctx *c, const double *R, double *Z, int k) {
+  cudaStream_t s = c->stream;
+  const long long L = 3LL * c->n_nodes, LK = L * k;
+  for (auto *b : {&c->mw_r1, &c->mw_r2, &c->mw_z1, &c->mw_zz, &c->mw_zg, &c->mw_t}) b->alloc(LK);
+  coarse_apply_multi(c, R, c->mw_z1.p, k);
+  spmv_multi(c, c->mw_z1.p, c->mw_r1.p, k, c->opt.apply_prec, R);
+  HP_CUDA(cudaMemcpyAsync(Z, c->mw_z1.p, sizeof(double) * LK, cudaMemcpyDeviceToDevice, s));
+  for (int st = 0; st < c->opt.n_st; ++st) {
+    HP_CUDA(cudaMemsetAsync(c->mw_zz.p, 0, sizeof(double) * LK, s));
+    smoother_apply_multi(c, c->contacts, c->mw_r1.p, c->mw_zz.p, k, true);
+    spmv_multi(c, c->mw_zz.p, c->mw_r2.p, k, c->opt.apply_prec, c->mw_r1.p);
+    HP_CUDA(cudaMemsetAsync(c->mw_zg.p, 0, sizeof(double) * LK, s));
+    smoother_apply_multi(c, c->grains, c->mw_r2.p, c->mw_zg.p, k, false);
+    k_add2<<<grid_for(LK, 256), 256, 0, s>>>(c->mw_t.p, c->mw_zz.p, c->mw_zg.p, LK);
+    HP_CHECK_LAUNCH();
+    k_axpby<<<grid_for(LK, 256), 256, 0, s>>>(Z, c->mw_t.p, 1.0, 1.0, LK);
+    HP_CHECK_LAUNCH();
+    if (st + 1 < c->opt.n_st) {
+      spmv_multi(c, c->mw_t.p, c->mw_r2.p, k, c->opt.apply_prec, c->mw_r1.p);
+      HP_CUDA(cudaMemcpyAsync(c->mw_r1.p, c->mw_r2.p, sizeof(double) * LK, cudaMemcpyDeviceToDevice, s));
+    }
+  }
+}
+
 void drop_apply_graph(hplmm_ctx *c) {
   if (c->apply_graph) {
     cudaStreamSynchronize(c->stream);
@@ -465,6 +492,153 @@ int fgmres(hplmm_ctx *c, const double *b_pad, double *x_pad, double tol, hplmm_s
     st->rel_res_true = rel;
   }
   return rel <= tol ? HPLMM_OK : HPLMM_NOT_CONVERGED;
+}
+
+}  // namespace hp
+
+namespace hp {
+
+// k right-preconditioned FGMRES(m) solves with one preconditioner, run in lockstep so that every Arnoldi
+// step applies M^{-1} to the current basis vectors of all unfinished solves at once (precond_apply_multi) and
+// multiplies them by A_hat together; each solve keeps its own basis, Hessenberg matrix, Givens rotations
+// and restarts.  B and X hold k padded vectors at stride 3 n_nodes; st (host, may be NULL) k entries.
+int fgmres_multi(hplmm_ctx *c, const double *B, double *X, int k, double tol, hplmm_stats *st) {
+  cudaStream_t s = c->stream;
+  const long long L = 3LL * c->n_nodes;
+  const int m = c->opt.restart, maxit = c->opt.max_iters;
+  const size_t per = (size_t)(2 * m + 1) * L;  // V (m + 1 vectors) and Z (m vectors) of one solve
+  c->mV.alloc(per * k);
+  c->mw_in.alloc(L * k);
+  c->mw_out.alloc(L * k);
+  c->mw_w.alloc(L * k);
+  c->mh.alloc((size_t)(2 * MAXV + 8) * k);
+  struct Rhs {
+    double bnorm = 0, rel = 0;
+    int its = 0, restarts = 0, kk = 0;
+    bool done = false, cyc = false;
+    std::vector<double> H, cs, sn, g, y;
+  };
+  std::vector<Rhs> R(k);
+  std::vector<double> hh(2 * MAXV + 1, 0.0);
+  auto V = [&](int i) { return c->mV.p + per * i; };
+  auto Zb = [&](int i) { return c->mV.p + per * i + (size_t)(m + 1) * L; };
+  auto dh = [&](int i) { return c->mh.p + (size_t)(2 * MAXV + 8) * i; };
+  HP_CUDA(cudaMemsetAsync(X, 0, sizeof(double) * L * k, s));
+  for (int i = 0; i < k; ++i) {
+    R[i].H.assign((size_t)(m + 1) * m, 0.0);
+    R[i].cs.assign(m, 0.0);
+    R[i].sn.assign(m, 0.0);
+    R[i].g.assign(m + 1, 0.0);
+    R[i].y.assign(m, 0.0);
+    mdot(c, B + i * L, 0, 1, B + i * L, L, dh(i));
+    HP_CUDA(cudaMemcpyAsync(hh.data(), dh(i), sizeof(double), cudaMemcpyDeviceToHost, s));
+    HP_CUDA(cudaStreamSynchronize(s));
+    R[i].bnorm = std::sqrt(hh[0]);
+    HP_REQUIRE(std::isfinite(R[i].bnorm), HPLMM_ERR_INVALID,
+               "solve: right-hand side " + std::to_string(i) + " has non-finite entries");
+    if (R[i].bnorm == 0.0) R[i].done = true;
+  }
+  for (;;) {
+    // true residuals and the start of a cycle for every unfinished solve
+    bool any = false;
+    for (int i = 0; i < k; ++i) {
+      Rhs &r = R[i];
+      if (r.done) continue;
+      spmv(c, X + i * L, V(i), HPLMM_FP64, B + i * L);
+      mdot(c, V(i), 0, 1, V(i), L, dh(i));
+      HP_CUDA(cudaMemcpyAsync(hh.data(), dh(i), sizeof(double), cudaMemcpyDeviceToHost, s));
+      HP_CUDA(cudaStreamSynchronize(s));
+      const double beta = std::sqrt(hh[0]);
+      r.rel = beta / r.bnorm;
+      if (r.rel <= tol || r.its >= maxit) {
+        r.done = true;
+        continue;
+      }
+      any = true;
+      k_scale_copy<<<grid_for(L, 256), 256, 0, s>>>(V(i), V(i), 1.0 / beta, L);
+      HP_CHECK_LAUNCH();
+      std::fill(r.g.begin(), r.g.end(), 0.0);
+      r.g[0] = beta;
+      r.kk = 0;
+      r.cyc = true;
+    }
+    if (!any) break;
+    for (int j = 0; j < m; ++j) {
+      std::vector<int> act;
+      for (int i = 0; i < k; ++i)
+        if (!R[i].done && R[i].cyc) act.push_back(i);
+      if (act.empty()) break;
+      const int na = (int)act.size();
+      for (int q = 0; q < na; ++q)
+        HP_CUDA(cudaMemcpyAsync(c->mw_in.p + q * L, V(act[q]) + (size_t)j * L, sizeof(double) * L,
+                                cudaMemcpyDeviceToDevice, s));
+      precond_apply_multi(c, c->mw_in.p, c->mw_out.p, na);
+      spmv_multi(c, c->mw_out.p, c->mw_w.p, na, HPLMM_FP64);
+      for (int q = 0; q < na; ++q) {
+        const int i = act[q];
+        Rhs &r = R[i];
+        double *w = c->mw_w.p + q * L;
+        HP_CUDA(cudaMemcpyAsync(Zb(i) + (size_t)j * L, c->mw_out.p + q * L, sizeof(double) * L,
+                                cudaMemcpyDeviceToDevice, s));
+        ++r.its;
+        mdot(c, V(i), L, j + 1, w, L, dh(i));
+        cgs_update(c, V(i), L, j + 1, dh(i), w, L, 0, dh(i) + MAXV);
+        cgs_update(c, V(i), L, j + 1, dh(i) + MAXV, w, L, 1, dh(i) + 2 * MAXV);
+        HP_CUDA(cudaMemcpyAsync(hh.data(), dh(i), sizeof(double) * (2 * MAXV + 1), cudaMemcpyDeviceToHost, s));
+        HP_CUDA(cudaStreamSynchronize(s));
+        for (int a = 0; a <= j; ++a) r.H[(size_t)a * m + j] = hh[a] + hh[MAXV + a];
+        const double hn = std::sqrt(std::max(hh[2 * MAXV], 0.0));
+        r.H[(size_t)(j + 1) * m + j] = hn;
+        for (int a = 0; a < j; ++a) {
+          const double u = r.H[(size_t)a * m + j], v = r.H[(size_t)(a + 1) * m + j];
+          r.H[(size_t)a * m + j] = r.cs[a] * u + r.sn[a] * v;
+          r.H[(size_t)(a + 1) * m + j] = -r.sn[a] * u + r.cs[a] * v;
+        }
+        const double u = r.H[(size_t)j * m + j], v = r.H[(size_t)(j + 1) * m + j];
+        const double den = std::hypot(u, v);
+        r.cs[j] = u / den;
+        r.sn[j] = v / den;
+        r.H[(size_t)j * m + j] = den;
+        r.H[(size_t)(j + 1) * m + j] = 0.0;
+        r.g[j + 1] = -r.sn[j] * r.g[j];
+        r.g[j] = r.cs[j] * r.g[j];
+        r.kk = j + 1;
+        const double est = std::fabs(r.g[j + 1]) / r.bnorm;
+        if (hn > 0.0) {
+          k_scale_copy<<<grid_for(L, 256), 256, 0, s>>>(V(i) + (size_t)(j + 1) * L, w, 1.0 / hn, L);
+          HP_CHECK_LAUNCH();
+        }
+        if (est <= tol || hn == 0.0 || r.its >= maxit) r.cyc = false;
+      }
+    }
+    // x += Z y for every solve that ran this cycle
+    for (int i = 0; i < k; ++i) {
+      Rhs &r = R[i];
+      if (r.done || r.kk == 0) continue;
+      for (int a = r.kk - 1; a >= 0; --a) {
+        double t = r.g[a];
+        for (int q = a + 1; q < r.kk; ++q) t -= r.H[(size_t)a * m + q] * r.y[q];
+        r.y[a] = t / r.H[(size_t)a * m + a];
+      }
+      HP_CUDA(cudaMemcpyAsync(dh(i), r.y.data(), sizeof(double) * r.kk, cudaMemcpyHostToDevice, s));
+      k_mcombine<<<MDOT_BLOCKS, 256, 0, s>>>(X + i * L, Zb(i), L, r.kk, dh(i), L);
+      HP_CHECK_LAUNCH();
+      HP_CUDA(cudaStreamSynchronize(s));
+      ++r.restarts;
+      r.kk = 0;
+    }
+  }
+  check_status(c);
+  bool all = true;
+  for (int i = 0; i < k; ++i) {
+    if (st) {
+      st[i].iters = R[i].its;
+      st[i].restarts = R[i].restarts;
+      st[i].rel_res_true = R[i].rel;
+    }
+    if (!(R[i].rel <= tol)) all = false;
+  }
+  return all ? HPLMM_OK : HPLMM_NOT_CONVERGED;
 }
 
 }  // namespace hp

@@ -6,6 +6,8 @@
 // vectors are [n_nodes][3] with zeros on fixed slots.
 #include "common.cuh"
 
+#include <algorithm>
+
 namespace hp {
 namespace {
 
@@ -367,6 +369,54 @@ __global__ void k_spmv_sell(const int *slice_off, const int *scol, const T *sval
   }
 }
 
+// Y_q = A X_q (or SUB_q - A X_q) for up to four vectors q < kc, at stride L: the matrix is read once for the
+// group (the multi-right-hand-side solve shares one preconditioner over several load cases)
+template <typename T>
+__global__ void k_spmv_sell4(const int *slice_off, const int *scol, const T *sval, const int *perm, const double *x,
+                             double *y, const double *sub, int n_nodes, long long L, int kc) {
+  int n = blockIdx.x * blockDim.x + threadIdx.x;
+  if (n >= n_nodes) return;
+  const int node = perm[n];
+  using A = typename std::conditional<std::is_same<T, double>::value, double, float>::type;
+  const int sl = n >> 5, lane = n & 31;
+  const long long base = slice_off[sl];
+  const int w = (slice_off[sl + 1] - slice_off[sl]) >> 5;
+  A s[4][3] = {};
+  for (int j = 0; j < w; ++j) {
+    const long long slot = base + (long long)j * 32;
+    const int m = scol[slot + lane];
+    const T *v = sval + slot * 9 + lane;
+    A a[9];
+#pragma unroll
+    for (int e = 0; e < 9; ++e) a[e] = (A)v[32 * e];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      if (q < kc) {
+        const double *xq = x + q * L + 3LL * m;
+        const A x0 = (A)xq[0], x1 = (A)xq[1], x2 = (A)xq[2];
+        s[q][0] += a[0] * x0 + a[1] * x1 + a[2] * x2;
+        s[q][1] += a[3] * x0 + a[4] * x1 + a[5] * x2;
+        s[q][2] += a[6] * x0 + a[7] * x1 + a[8] * x2;
+      }
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    if (q >= kc) continue;
+    double *yq = y + q * L + 3LL * node;
+    if (sub) {
+      const double *sq = sub + q * L + 3LL * node;
+      yq[0] = sq[0] - (double)s[q][0];
+      yq[1] = sq[1] - (double)s[q][1];
+      yq[2] = sq[2] - (double)s[q][2];
+    } else {
+      yq[0] = (double)s[q][0];
+      yq[1] = (double)s[q][1];
+      yq[2] = (double)s[q][2];
+    }
+  }
+}
+
 }  // namespace
 
 // first solid voxel whose modulus is not a positive finite number (atomic minimum of its index)
@@ -526,6 +576,24 @@ void spmv(hplmm_ctx *c, const double *x_pad, double *y_pad, hplmm_prec prec, con
   else
     k_spmv_sell<float><<<grid, 64, 0, c->stream>>>(off, col, c->sell_val32.p, perm, x_pad, y_pad, sub, c->n_nodes);
   HP_CHECK_LAUNCH();
+}
+
+void spmv_multi(hplmm_ctx *c, const double *X, double *Y, int k, hplmm_prec prec, const double *SUB) {
+  ProfScope ps(c, HPLMM_PH_SPMV);
+  const unsigned grid = grid_for(c->n_nodes, 64);
+  const long long L = 3LL * c->n_nodes;
+  const int *off = c->sell_off.p, *col = c->sell_col.p, *perm = c->sell_perm.p;
+  for (int q0 = 0; q0 < k; q0 += 4) {
+    const int kc = std::min(4, k - q0);
+    const double *sub = SUB ? SUB + q0 * L : nullptr;
+    if (prec == HPLMM_FP64)
+      k_spmv_sell4<double><<<grid, 64, 0, c->stream>>>(off, col, c->sell_val64.p, perm, X + q0 * L, Y + q0 * L, sub,
+                                                       c->n_nodes, L, kc);
+    else
+      k_spmv_sell4<float><<<grid, 64, 0, c->stream>>>(off, col, c->sell_val32.p, perm, X + q0 * L, Y + q0 * L, sub,
+                                                      c->n_nodes, L, kc);
+    HP_CHECK_LAUNCH();
+  }
 }
 
 }  // namespace hp

@@ -322,6 +322,53 @@ hplmm_status hplmm_solve(hplmm_ctx *c, const double *b, double *x, double tol, h
   return g != HPLMM_OK ? g : rc;
 }
 
+hplmm_status hplmm_apply_multi(hplmm_ctx *c, const double *R, double *Z, int k) {
+  return guarded(c, [&] {
+    require_setup(c);
+    HP_REQUIRE(R && Z && R != Z, HPLMM_ERR_INVALID, "apply_multi: R and Z must be distinct device arrays");
+    HP_REQUIRE(k >= 1 && k <= 64, HPLMM_ERR_INVALID, "apply_multi: k must lie in [1, 64]");
+    const long long L = 3LL * c->n_nodes;
+    c->mw_pin.alloc(L * k);
+    c->mw_pout.alloc(L * k);
+    for (int q = 0; q < k; ++q) hp::scatter_free(c, R + q * c->n_dof, c->mw_pin.p + q * L);
+    hp::precond_apply_multi(c, c->mw_pin.p, c->mw_pout.p, k);
+    for (int q = 0; q < k; ++q) hp::gather_free(c, c->mw_pout.p + q * L, Z + q * c->n_dof);
+  });
+}
+
+hplmm_status hplmm_solve_multi(hplmm_ctx *c, const double *B, double *X, int k, double tol, hplmm_stats *st) {
+  hplmm_status rc = HPLMM_OK;
+  hplmm_status g = guarded(c, [&] {
+    require_setup(c);
+    HP_REQUIRE(B && X && B != X, HPLMM_ERR_INVALID, "solve_multi: B and X must be distinct device arrays");
+    HP_REQUIRE(k >= 1 && k <= 64, HPLMM_ERR_INVALID, "solve_multi: k must lie in [1, 64]");
+    HP_REQUIRE(tol > 0.0, HPLMM_ERR_INVALID, "solve_multi: tol must be positive");
+    const long long L = 3LL * c->n_nodes;
+    c->mw_pin.alloc(L * k);
+    c->mw_pout.alloc(L * k);
+    for (int q = 0; q < k; ++q) hp::scatter_free(c, B + q * c->n_dof, c->mw_pin.p + q * L);
+    double t0 = now_s();
+    std::vector<hplmm_stats> sv(k);
+    rc = (hplmm_status)hp::fgmres_multi(c, c->mw_pin.p, c->mw_pout.p, k, tol, sv.data());
+    for (int q = 0; q < k; ++q) hp::gather_free(c, c->mw_pout.p + q * L, X + q * c->n_dof);
+    HP_CUDA(cudaStreamSynchronize(c->stream));
+    hp::prof_harvest(c);
+    double t1 = now_s();
+    if (st)
+      for (int q = 0; q < k; ++q) {
+        st[q] = sv[q];
+        st[q].t_setup_ml = c->t_ml;
+        st[q].t_setup_mg = c->t_mg;
+        st[q].t_solve = t1 - t0;
+        st[q].n_dof = c->n_dof;
+        st[q].n_coarse = c->n_coarse;
+        st[q].n_interfaces = c->n_ifaces;
+        st[q].n_grains = c->n_grains;
+      }
+  });
+  return g != HPLMM_OK ? g : rc;
+}
+
 hplmm_status hplmm_get_sizes(hplmm_ctx *c, hplmm_sizes *out) {
   return guarded(c, [&] {
     HP_REQUIRE(out, HPLMM_ERR_INVALID, "get_sizes: null output");

@@ -383,6 +383,86 @@ __global__ void k_prolong_iface(const int *iface_nodes, const int *iface_of_node
   }
 }
 
+// multi-right-hand-side restriction: t_q[gcol] += sum over grain rows of X_g[row][a] r_q[row] for q < kc
+// (kc <= 8 vectors at stride L, their coarse vectors at stride No): each panel element read once per group
+template <typename T, typename A>
+__global__ void __launch_bounds__(256) k_restrict_grain8(const long long *node_off, const int *nloc,
+                                                         const int *lnodes, const int *kg, const long long *panel_off,
+                                                         const T *X, const int *gcol_off, const int *gcol,
+                                                         const double *r, long long L, double *t, long long No,
+                                                         int kc) {
+  __shared__ A rl[8][RCHUNK];
+  const int g = blockIdx.y;
+  const int N = nloc[g];
+  const int row0 = blockIdx.x * RCHUNK;
+  if (row0 >= N) return;
+  const int cnt = min(RCHUNK, N - row0);
+  const int k = kg[g];
+  const int *ln = lnodes + node_off[g];
+  for (int e = threadIdx.x; e < 8 * RCHUNK; e += blockDim.x) {
+    const int q = e / RCHUNK, rr = e % RCHUNK;
+    A v = 0;
+    if (q < kc && rr < cnt) {
+      const int row = row0 + rr, o = row / 3, d = row - 3 * o;
+      v = (A)r[q * L + 3LL * ln[o] + d];
+    }
+    rl[q][rr] = v;
+  }
+  __syncthreads();
+  const T *Xg = X + panel_off[g] + (long long)row0 * k;
+  for (int a = threadIdx.x; a < k; a += blockDim.x) {
+    A acc[8] = {};
+    for (int rr = 0; rr < cnt; ++rr) {
+      const A x = (A)Xg[(long long)rr * k + a];
+#pragma unroll
+      for (int q = 0; q < 8; ++q) acc[q] += x * rl[q][rr];
+    }
+    const int col = gcol[gcol_off[g] + a];
+#pragma unroll
+    for (int q = 0; q < 8; ++q)
+      if (q < kc) atomicAdd(&t[q * No + col], (double)acc[q]);
+  }
+}
+
+// multi-right-hand-side prolongation on grain rows: z_q[row] = X_g[row][.] u_q[K_g]; warp per row
+template <typename T, typename A>
+__global__ void __launch_bounds__(256) k_prolong_grain8(const long long *node_off, const int *nloc, const int *lnodes,
+                                                        const int *kg, const long long *panel_off, const T *X,
+                                                        const int *gcol_off, const int *gcol, const double *u,
+                                                        long long No, double *z, long long L, int kc) {
+  __shared__ A ul[8][512];
+  const int g = blockIdx.y;
+  const int k = kg[g];
+  for (int e = threadIdx.x; e < 8 * k; e += blockDim.x) {
+    const int q = e / k, a = e % k;
+    ul[q][a] = q < kc ? (A)u[q * No + gcol[gcol_off[g] + a]] : (A)0;
+  }
+  __syncthreads();
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int N = nloc[g];
+  const T *Xg = X + panel_off[g];
+  const int *ln = lnodes + node_off[g];
+  for (int row = blockIdx.x * nw + wid; row < N; row += gridDim.x * nw) {
+    A acc[8] = {};
+    for (int a = lane; a < k; a += 32) {
+      const A x = (A)Xg[(long long)row * k + a];
+#pragma unroll
+      for (int q = 0; q < 8; ++q) acc[q] += x * ul[q][a];
+    }
+#pragma unroll
+    for (int q = 0; q < 8; ++q)
+      for (int o = 16; o > 0; o >>= 1) acc[q] += __shfl_xor_sync(0xffffffffu, acc[q], o);
+    if (lane < kc) {
+      A v = acc[0];
+#pragma unroll
+      for (int q = 1; q < 8; ++q)
+        if (lane == q) v = acc[q];
+      const int o = row / 3, d = row - 3 * o;
+      z[lane * L + 3LL * ln[o] + d] = (double)v;
+    }
+  }
+}
+
 template <typename T>
 Buf<T> &gal_buf(hplmm_ctx *c);
 template <>
@@ -672,6 +752,77 @@ void coarse_apply(hplmm_ctx *c, const double *r_pad, double *z_pad) {
         c->eta.p, c->comp_mask.p, c->col_off.p, c->fixed.p, t, z_pad);
     HP_CHECK_LAUNCH();
   }
+}
+
+// M_G^{-1} for k vectors at stride L (Z_q = P_hat (A^o)^{-1} P_hat^T R_q): the basis panels are read once per
+// group of eight vectors in the restriction and in the prolongation; the coarse solves run per vector
+void coarse_apply_multi(hplmm_ctx *c, const double *R, double *Z, int k) {
+  ProfScope ps(c, HPLMM_PH_APPLY_COARSE);
+  cudaStream_t s = c->stream;
+  const long long No = c->n_coarse, L = 3LL * c->n_nodes;
+  const int G = c->n_grains;
+  const bool f64 = c->opt.local_prec == HPLMM_FP64;
+  const bool b16 = !f64 && c->opt.apply_prec == HPLMM_BF16;
+  HP_CUDA(cudaMemsetAsync(Z, 0, sizeof(double) * L * k, s));
+  if (No == 0) return;
+  c->mw_ct.alloc((size_t)No * k);
+  c->mw_cu.alloc((size_t)No * k);
+  double *t = c->mw_ct.p, *u = c->mw_cu.p;
+  HP_CUDA(cudaMemsetAsync(t, 0, sizeof(double) * No * k, s));
+  int nmax = 1;
+  for (int g = 0; g < G; ++g) nmax = std::max(nmax, c->grains.h_n[g]);
+  for (int q0 = 0; q0 < k; q0 += 8) {
+    const int kc = std::min(8, k - q0);
+    dim3 gr((nmax + RCHUNK - 1) / RCHUNK, G);
+    if (f64)
+      k_restrict_grain8<double, double><<<gr, 256, 0, s>>>(c->grains.node_off.p, c->grains.n.p, c->grains.lnodes.p,
+                                                           c->kg.p, c->panel_off.p, c->X64.p, c->gcol_off.p,
+                                                           c->gcol.p, R + q0 * L, L, t + q0 * No, No, kc);
+    else if (b16)
+      k_restrict_grain8<__nv_bfloat16, float><<<gr, 256, 0, s>>>(c->grains.node_off.p, c->grains.n.p,
+                                                                 c->grains.lnodes.p, c->kg.p, c->panel_off.p,
+                                                                 c->X16.p, c->gcol_off.p, c->gcol.p, R + q0 * L, L,
+                                                                 t + q0 * No, No, kc);
+    else
+      k_restrict_grain8<float, float><<<gr, 256, 0, s>>>(c->grains.node_off.p, c->grains.n.p, c->grains.lnodes.p,
+                                                         c->kg.p, c->panel_off.p, c->X32.p, c->gcol_off.p, c->gcol.p,
+                                                         R + q0 * L, L, t + q0 * No, No, kc);
+    HP_CHECK_LAUNCH();
+  }
+  for (int q = 0; q < k; ++q) {
+    if (c->n_iface_nodes > 0) {
+      k_restrict_iface<<<grid_for(c->n_iface_nodes, 128), 128, 0, s>>>(
+          c->iface_nodes.p, c->iface_of_node.p, c->n_iface_nodes, c->iface_slot.p, c->mortar_off.p, c->eta_off.p,
+          c->eta.p, c->comp_mask.p, c->col_off.p, c->fixed.p, R + q * L, t + q * No);
+      HP_CHECK_LAUNCH();
+    }
+    cf_solve(c, t + q * No, c->w_coarse_y.p, u + q * No);
+  }
+  for (int q0 = 0; q0 < k; q0 += 8) {
+    const int kc = std::min(8, k - q0);
+    dim3 gp(64, G);
+    if (f64)
+      k_prolong_grain8<double, double><<<gp, 256, 0, s>>>(c->grains.node_off.p, c->grains.n.p, c->grains.lnodes.p,
+                                                          c->kg.p, c->panel_off.p, c->X64.p, c->gcol_off.p, c->gcol.p,
+                                                          u + q0 * No, No, Z + q0 * L, L, kc);
+    else if (b16)
+      k_prolong_grain8<__nv_bfloat16, float><<<gp, 256, 0, s>>>(c->grains.node_off.p, c->grains.n.p,
+                                                                c->grains.lnodes.p, c->kg.p, c->panel_off.p, c->X16.p,
+                                                                c->gcol_off.p, c->gcol.p, u + q0 * No, No, Z + q0 * L,
+                                                                L, kc);
+    else
+      k_prolong_grain8<float, float><<<gp, 256, 0, s>>>(c->grains.node_off.p, c->grains.n.p, c->grains.lnodes.p,
+                                                        c->kg.p, c->panel_off.p, c->X32.p, c->gcol_off.p, c->gcol.p,
+                                                        u + q0 * No, No, Z + q0 * L, L, kc);
+    HP_CHECK_LAUNCH();
+  }
+  if (c->n_iface_nodes > 0)
+    for (int q = 0; q < k; ++q) {
+      k_prolong_iface<<<grid_for(c->n_iface_nodes, 128), 128, 0, s>>>(
+          c->iface_nodes.p, c->iface_of_node.p, c->n_iface_nodes, c->iface_slot.p, c->mortar_off.p, c->eta_off.p,
+          c->eta.p, c->comp_mask.p, c->col_off.p, c->fixed.p, u + q * No, Z + q * L);
+      HP_CHECK_LAUNCH();
+    }
 }
 
 void prolong_column(hplmm_ctx *c, long long col, double *out_pad) {

@@ -317,6 +317,10 @@ struct hplmm_ctx {
   // ---- apply / GMRES work vectors (padded n_nodes*3)
   hp::Buf<double> w_r1, w_r2, w_z1, w_zz, w_zg, w_t, w_w;
   hp::Buf<double> w_coarse_t, w_coarse_u, w_coarse_y;
+  // multi-right-hand-side work (k vectors each): coarse vectors, padded fine vectors, local panels
+  hp::Buf<double> mw_ct, mw_cu, mw_r1, mw_r2, mw_z1, mw_zz, mw_zg, mw_t, mw_in, mw_out;
+  hp::Buf<double> mloc64, mV, mw_w, mh, mw_pin, mw_pout;
+  hp::Buf<float> mloc32;
   hp::Buf<double> w_loc64;         // local vectors for smoother
   hp::Buf<float> w_loc32;
   hp::Buf<double> w_in, w_out;     // padded copies of API vectors
@@ -397,6 +401,8 @@ struct ProfScope {
 void assemble(hplmm_ctx *c, const uint8_t *mask, int nx, int ny, int nz, const float *E, double E0, double nu,
               const hplmm_bcs *bcs, double *b_out);
 void spmv(hplmm_ctx *c, const double *x_pad, double *y_pad, hplmm_prec prec, const double *sub = nullptr);
+// k vectors at stride 3 n_nodes (the matrix read once per group of four)
+void spmv_multi(hplmm_ctx *c, const double *X, double *Y, int k, hplmm_prec prec, const double *SUB = nullptr);
 void gather_free(hplmm_ctx *c, const double *pad, double *dof);
 void scatter_free(hplmm_ctx *c, const double *dof, double *pad);
 // maps.cu
@@ -415,6 +421,7 @@ void solve_local_multi_f64(hplmm_ctx *c, LocalSet &S, double *X, const Buf<long 
 void solve_local_multi_f32(hplmm_ctx *c, LocalSet &S, float *X, const Buf<long long> &x_off, const Buf<int> &x_ld,
                            const std::vector<int> &h_ld);
 void smoother_apply(hplmm_ctx *c, LocalSet &S, const double *r_pad, double *z_pad, bool atomic);
+void smoother_apply_multi(hplmm_ctx *c, LocalSet &S, const double *R, double *Z, int k, bool atomic);
 void factor_staged(hplmm_ctx *c, float *X, const Buf<long long> &x_off, const Buf<int> &x_ld,
                    const std::vector<int> &h_ld);  // BF16 form: chunked FP32 factors + basis solves -> BF16
 void solve_local_multi_f32_subset(hplmm_ctx *c, LocalSet &S, float *X, const Buf<long long> &x_off,
@@ -441,6 +448,7 @@ void cf_analyse(hplmm_ctx *c, const std::vector<int> &gbox);
 void cf_factor(hplmm_ctx *c);
 void cf_solve(hplmm_ctx *c, double *t, double *y, double *x);
 void coarse_apply(hplmm_ctx *c, const double *r_pad, double *z_pad);
+void coarse_apply_multi(hplmm_ctx *c, const double *R, double *Z, int k);  // k vectors at stride 3 n_nodes
 void prolong_column(hplmm_ctx *c, long long col, double *out_pad);
 // apply.cu
 void precond_apply(hplmm_ctx *c, const double *r_pad, double *z_pad);
@@ -449,5 +457,7 @@ void drop_apply_graph(hplmm_ctx *c);
 void tune_local(hplmm_ctx *c);
 void smoother_stage(hplmm_ctx *c, const double *r_pad, double *z_pad);
 int fgmres(hplmm_ctx *c, const double *b_pad, double *x_pad, double tol, hplmm_stats *st);
+void precond_apply_multi(hplmm_ctx *c, const double *R, double *Z, int k);
+int fgmres_multi(hplmm_ctx *c, const double *B, double *X, int k, double tol, hplmm_stats *st);
 void check_status(hplmm_ctx *c);
 }  // namespace hp

@@ -2202,6 +2202,67 @@ void solve_local_multi_f32(hplmm_ctx *c, LocalSet &S, float *X, const Buf<long l
   solve_multi_t<float>(c, S, X, x_off, x_ld, h_ld);
 }
 
+// local right-hand-side panels of the multi-right-hand-side smoother: P[l][q] = R_q[gidx[l]] (row l of the
+// set's local vectors, k columns), and back: Z_q[gidx[l]] (+)= P[l][q]
+template <typename T>
+__global__ void k_local_gather_multi(const int *gidx, long long n, const double *R, long long L, int k, T *P) {
+  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= n * k) return;
+  const long long l = e / k;
+  const int q = (int)(e - l * k);
+  P[e] = (T)R[q * L + gidx[l]];
+}
+template <typename T>
+__global__ void k_local_scatter_multi(const int *gidx, long long n, const T *P, long long L, int k, double *Z,
+                                      int atomic) {
+  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= n * k) return;
+  const long long l = e / k;
+  const int q = (int)(e - l * k);
+  double *dst = Z + q * L + gidx[l];
+  if (atomic)
+    atomicAdd(dst, (double)P[e]);
+  else
+    *dst = (double)P[e];
+}
+
+// The smoother for k right-hand sides at stride L: each local problem's right-hand sides form an N x k panel
+// that the multi-right-hand-side banded solves (the basis solves' kernels) process with one read of the
+// factor per 32 columns.  The BF16 form keeps no FP32 factors: it applies the one-vector solve per column.
+void smoother_apply_multi(hplmm_ctx *c, LocalSet &S, const double *R, double *Z, int k, bool atomic) {
+  if (S.count == 0) return;
+  const long long L = 3LL * c->n_nodes;
+  if (S.apply_bf16) {
+    for (int q = 0; q < k; ++q) smoother_apply(c, S, R + q * L, Z + q * L, atomic);
+    return;
+  }
+  ProfScope ps(c, (&S == &c->grains) ? HPLMM_PH_APPLY_GRAINS : HPLMM_PH_APPLY_CONTACTS);
+  cudaStream_t s = c->stream;
+  const long long n = S.vec_total;
+  std::vector<long long> off(S.count);
+  for (int p = 0; p < S.count; ++p) off[p] = S.h_vec_off[p] * k;
+  Buf<long long> moff;
+  Buf<int> mld;
+  moff.upload(off, s);
+  std::vector<int> ld(S.count, k);
+  mld.upload(ld, s);
+  const unsigned grid = grid_for(n * k, 256);
+  if (S.prec == HPLMM_FP64) {
+    c->mloc64.alloc(std::max<long long>(n * k, 1));
+    k_local_gather_multi<double><<<grid, 256, 0, s>>>(S.gidx.p, n, R, L, k, c->mloc64.p);
+    HP_CHECK_LAUNCH();
+    solve_multi_t<double>(c, S, c->mloc64.p, moff, mld, ld);
+    k_local_scatter_multi<double><<<grid, 256, 0, s>>>(S.gidx.p, n, c->mloc64.p, L, k, Z, atomic ? 1 : 0);
+  } else {
+    c->mloc32.alloc(std::max<long long>(n * k, 1));
+    k_local_gather_multi<float><<<grid, 256, 0, s>>>(S.gidx.p, n, R, L, k, c->mloc32.p);
+    HP_CHECK_LAUNCH();
+    solve_multi_t<float>(c, S, c->mloc32.p, moff, mld, ld);
+    k_local_scatter_multi<float><<<grid, 256, 0, s>>>(S.gidx.p, n, c->mloc32.p, L, k, Z, atomic ? 1 : 0);
+  }
+  HP_CHECK_LAUNCH();
+}
+
 // Staged set-up of the BF16 form: the apply streams BF16 copies of the FP32 local factors, so the FP32
 // factors need not outlive the set-up.  Each set is factored in chunks of consecutive problems whose FP32
 // bands fit a scratch buffer (options.stage_mb, default STAGE_ELEMS floats); a chunk of grains serves its grains' basis solves (Eqs.
