@@ -375,26 +375,29 @@ def run_e2e(hp, problem, spec, form, steps, warmup, flush, stream, n_mortar=None
 
 
 def warm_start_eval(hp, stream, seed=0):
-    """Learned warm start of the basis solves: train the network on the exact bases of two porous32 images
-    (seeded initial weights and minibatch order drawn here and passed to the library), then solve the bases
-    of an unseen porous32 image by block-Jacobi CG from the network's guess and from zero; report the CG
-    iterations, the starting residuals and the times, next to the exact banded solve of the chosen form."""
+    """Learned warm start of the basis solves.  Training: the exact bases of the 16^3 cube (2x2x2 grains) and
+    the 64^3 porous image (4x4x4 grains) -- the first two workloads -- with seeded initial weights and
+    minibatch order drawn here and passed to the library.  Evaluation: the 64^3 corner (4x4x4 grains of 16^3
+    voxels) of an unseen 192^3 image with porosity 0.35 (seed 100), whose basis problems are solved by
+    block-Jacobi CG from the network's guess and from zero, next to the exact banded solve; CG iterations,
+    starting residuals and basis-solve times are reported."""
     import numpy as np
     import torch
     import synth
     from synth.netinit import init_params
+    from synth.voxels import _largest_component_touching_bottom
     kw = dict(METHOD, n_mortar=4, local_prec="fp32", apply_prec="fp32")
     tr = hp.Solver(**kw, keep_basis_rhs=True, stream=stream)
     n = 0
-    for s in (21, 22):
-        p = synth.make_workload("porous32", s)
+    for wl, sd in (("cube16", 0), ("porous64", 1)):
+        p = synth.make_workload(wl, sd)
         mask, E = hp.problem_to_device(p)
         tr.assemble(mask, E, p.nu, p.bcs)
         tr.setup(grains=p.grains)
         n = tr.ws_collect()
     tr.ws_set_params(init_params(7 + seed))
     rng = np.random.default_rng(8 + seed)
-    epochs = 6
+    epochs = 3
     order = np.concatenate([rng.permutation(n) for _ in range(epochs)]).astype(np.int32)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
@@ -403,11 +406,15 @@ def warm_start_eval(hp, stream, seed=0):
     t_train = time.perf_counter() - t0
     theta = tr.ws_get_params()
     tr.close()
-    p = synth.make_workload("porous32", 23)
-    out = {"train": {"samples": int(n), "epochs": epochs, "steps": int(loss.size), "batch": 8, "lr": 1e-3,
+    full = synth.make_workload("porous192", 100)
+    sub = _largest_component_touching_bottom(full.mask[:64, :64, :64].astype(bool))
+    p = synth.Problem("porous192_corner64", sub, full.E[:64, :64, :64].copy(), full.nu, (4, 4, 4), full.bcs, 4, 100)
+    out = {"train": {"images": "cube16 seed 0 and porous64 seed 1 (the first two workloads)", "samples": int(n),
+                     "epochs": epochs, "steps": int(loss.size), "batch": 8, "lr": 1e-3,
                      "loss_first_10pct": float(loss[:max(1, loss.size // 10)].mean()),
                      "loss_last_10pct": float(loss[-max(1, loss.size // 10):].mean()), "seconds": t_train},
-           "eval_image": "porous32 seed 23 (unseen)", "basis_tol": 1e-6}
+           "eval_image": "64^3 corner (4x4x4 grains) of an unseen 192^3 image, porosity 0.35, seed 100",
+           "basis_tol": 1e-6}
     for mode in ("direct", "pcg", "pcg_warm"):
         s = hp.Solver(**kw, basis_solver=mode, basis_tol=1e-6, profile=True, stream=stream)
         if mode == "pcg_warm":

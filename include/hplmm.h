@@ -81,6 +81,9 @@ typedef struct {
   int smoother_ctas;     /* CTAs per local problem in the smoother solves: 0 (default) the tuner's choice, or
                             two for a set with at most half as many problems as the GPU has SMs, else one;
                             1 or 2 force it (two: a cluster that splits each panel's far rows) */
+  int smoother_per_sm;   /* smoother solve instance: 0 (default) the tuner's choice, else one CTA per SM (the
+                            largest ring); 1 or 2 force the instance sized and compiled (at most 80
+                            registers per thread) for one or two CTAs per SM */
   int stage_mb;          /* BF16 apply form (local_prec FP32, apply_prec BF16, exact basis solves): the local
                             factors are computed in FP32 in chunks of at most this many MiB, each chunk of grains
                             used for its basis solves, then kept only as BF16 (0 = default, 6144); the result does
@@ -339,6 +342,10 @@ hplmm_status hplmm_ws_train(hplmm_ctx *ctx, const int32_t *order, long long n_or
  * float32 [n][3][D^3], grad DEVICE float32 [hplmm_ws_num_params()], loss HOST.  Synchronises. */
 hplmm_status hplmm_ws_loss_grad(hplmm_ctx *ctx, const float *in, const float *target, const float *valid, int n,
                                 int D, double *loss, float *grad);
+
+/* The network's inference path as the warm start uses it (BF16 weights and activations, FP32 products and
+ * sums): out [n][3][17^3] from in [n][5][17^3], both DEVICE float32, 1 <= n <= 4096.  Synchronises. */
+hplmm_status hplmm_ws_predict(hplmm_ctx *ctx, const float *in, float *out, int n);
 
 typedef struct {
   long long columns;          /* basis problems solved */

@@ -128,6 +128,28 @@ def forward(theta, x, channels=CHANNELS):
     return acts
 
 
+def round_bf16(a):
+    """Round to the nearest bfloat16 (8-bit significand, FP32 exponent range), ties to even: the FP32 value's
+    low 16 bits are dropped after adding half a unit of the kept part (0x7fff plus the kept part's lowest
+    bit).  Inputs are first rounded to FP32; NaN and infinities are not used here."""
+    f = np.ascontiguousarray(np.asarray(a, np.float32))
+    u = f.view(np.uint32).astype(np.uint64)
+    r = ((u + 0x7FFF + ((u >> 16) & 1)) >> 16) << 16
+    return r.astype(np.uint32).view(np.float32).astype(np.float64)
+
+
+def forward_bf16(theta, x, channels=CHANNELS):
+    """The network as its BF16 inference path defines it: weights and biases rounded to BF16, the input kept
+    in FP32, every hidden activation rounded to BF16 after its ReLU, the output kept in FP32; products and
+    sums exact here (FP64), which the GPU's FP32 accumulation approximates."""
+    a = np.asarray(np.asarray(x, np.float32), np.float64)
+    layers = unpack(np.asarray(theta, np.float64), channels)
+    for li, (W, b) in enumerate(layers):
+        z = conv3d(a, round_bf16(W), round_bf16(b), DILATIONS[li])
+        a = round_bf16(np.maximum(z, 0.0)) if li + 1 < len(layers) else np.asarray(z.astype(np.float32), np.float64)
+    return a
+
+
 def loss_and_grad(theta, x, target, valid, channels=CHANNELS):
     """Masked mean-squared error and its gradient with respect to the flat parameters."""
     acts = forward(theta, x, channels)

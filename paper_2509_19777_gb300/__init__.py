@@ -40,7 +40,7 @@ EXPORTED = [
     "hplmm_reset_profile", "hplmm_kernel_launches", "hplmm_get_costs", "hplmm_last_error", "hplmm_destroy",
     "hplmm_ws_num_params", "hplmm_ws_set_params", "hplmm_ws_get_params", "hplmm_ws_collect", "hplmm_ws_clear",
     "hplmm_ws_train", "hplmm_ws_loss_grad", "hplmm_get_basis_stats", "hplmm_ws_get_samples",
-    "hplmm_inject_alloc_failure", "hplmm_apply_multi", "hplmm_solve_multi",
+    "hplmm_inject_alloc_failure", "hplmm_apply_multi", "hplmm_solve_multi", "hplmm_ws_predict",
 ]
 PHASES = ["maps", "factor_grains", "factor_contacts", "basis_rhs", "basis_solve", "galerkin", "coarse_chol",
           "apply_coarse", "apply_contacts", "apply_grains", "spmv", "krylov", "apply_graph"]
@@ -53,7 +53,8 @@ class hplmm_options(ctypes.Structure):
                 ("use_graph", ctypes.c_int), ("verbose", ctypes.c_int), ("profile", ctypes.c_int),
                 ("autotune", ctypes.c_int), ("basis_solver", ctypes.c_int), ("basis_tol", ctypes.c_double),
                 ("basis_max_iters", ctypes.c_int), ("keep_basis_rhs", ctypes.c_int),
-                ("smoother_ctas", ctypes.c_int), ("stage_mb", ctypes.c_int), ("wait_budget_us", ctypes.c_int)]
+                ("smoother_ctas", ctypes.c_int), ("smoother_per_sm", ctypes.c_int), ("stage_mb", ctypes.c_int),
+                ("wait_budget_us", ctypes.c_int)]
 
 
 HPLMM_BASIS_DIRECT, HPLMM_BASIS_PCG, HPLMM_BASIS_PCG_WARM = 0, 1, 2
@@ -127,6 +128,7 @@ def load_library():
         "hplmm_kernel_launches": (LL, []),
         "hplmm_inject_alloc_failure": (None, [LL]),
         "hplmm_apply_multi": (I, [P, P, P, I]),
+        "hplmm_ws_predict": (I, [P, P, P, I]),
         "hplmm_solve_multi": (I, [P, P, P, I, D, ctypes.POINTER(hplmm_stats)]),
         "hplmm_get_costs": (I, [P, ctypes.POINTER(hplmm_costs)]),
         "hplmm_last_error": (ctypes.c_char_p, [P]),
@@ -320,6 +322,16 @@ def hplmm_inject_alloc_failure(after):
     load_library().hplmm_inject_alloc_failure(int(after))
 
 
+def hplmm_ws_predict(ctx, x, out=None):
+    """BF16 inference of the warm-start network on [n, 5, 17, 17, 17] float32 CUDA inputs."""
+    import torch
+    n = int(x.shape[0])
+    if out is None:
+        out = torch.empty((n, 3, 17, 17, 17), dtype=torch.float32, device=x.device)
+    _check(ctx, load_library().hplmm_ws_predict(ctx, _ptr(x), _ptr(out), n))
+    return out
+
+
 def hplmm_apply_multi(ctx, R, Z):
     """Z[q] = M^{-1} R[q] for the rows q of the [k, n_dof] float64 CUDA tensors R and Z."""
     _check(ctx, load_library().hplmm_apply_multi(ctx, _ptr(R), _ptr(Z), int(R.shape[0])))
@@ -416,7 +428,7 @@ class Solver:
     def __init__(self, n_mortar=4, beta=4.0, contact_halfwidth=2, n_st=1, local_prec="fp64", apply_prec="fp64",
                  restart=30, max_iters=300, strict_two_grain=False, use_graph=False, verbose=False, profile=False,
                  autotune=False, basis_solver="direct", basis_tol=1e-6, basis_max_iters=3000, keep_basis_rhs=False,
-                 smoother_ctas=0, stage_mb=0, wait_budget_us=0, stream=None):
+                 smoother_ctas=0, smoother_per_sm=0, stage_mb=0, wait_budget_us=0, stream=None):
         o = hplmm_default_options()
         o.n_mortar, o.beta, o.contact_halfwidth, o.n_st = n_mortar, beta, contact_halfwidth, n_st
         o.local_prec, o.apply_prec = PREC[local_prec], PREC[apply_prec]
@@ -427,6 +439,7 @@ class Solver:
         o.basis_solver, o.basis_tol, o.basis_max_iters = BASIS[basis_solver], basis_tol, basis_max_iters
         o.keep_basis_rhs = int(keep_basis_rhs)
         o.smoother_ctas = int(smoother_ctas)
+        o.smoother_per_sm = int(smoother_per_sm)
         o.stage_mb = int(stage_mb)
         o.wait_budget_us = int(wait_budget_us)
         self.options = o

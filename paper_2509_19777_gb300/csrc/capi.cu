@@ -93,6 +93,8 @@ void validate_options(const hplmm_options &o) {
   HP_REQUIRE(o.basis_tol > 0.0 && o.basis_tol < 1.0, HPLMM_ERR_INVALID, "basis_tol must lie in (0, 1)");
   HP_REQUIRE(o.basis_max_iters >= 1, HPLMM_ERR_INVALID, "basis_max_iters must be positive");
   HP_REQUIRE(o.smoother_ctas >= 0 && o.smoother_ctas <= 2, HPLMM_ERR_INVALID, "smoother_ctas must be 0, 1 or 2");
+  HP_REQUIRE(o.smoother_per_sm >= 0 && o.smoother_per_sm <= 2, HPLMM_ERR_INVALID,
+             "smoother_per_sm must be 0, 1 or 2");
   HP_REQUIRE(o.stage_mb >= 0, HPLMM_ERR_INVALID, "stage_mb must be non-negative");
   HP_REQUIRE(o.wait_budget_us >= 0, HPLMM_ERR_INVALID, "wait_budget_us must be non-negative");
 }
@@ -555,6 +557,15 @@ hplmm_status hplmm_ws_loss_grad(hplmm_ctx *c, const float *in, const float *targ
     HP_REQUIRE(n >= 1 && n <= 256 && D >= 3 && D <= 17, HPLMM_ERR_INVALID, "ws_loss_grad: need 1 <= n <= 256, 3 <= D <= 17");
     HP_REQUIRE(c->ws.has_params, HPLMM_ERR_STATE, "ws_loss_grad: set the network parameters first");
     *loss = hp::ws_loss_grad(c, c->ws.theta.p, in, target, valid, n, D, grad);
+  });
+}
+
+hplmm_status hplmm_ws_predict(hplmm_ctx *c, const float *in, float *out, int n) {
+  return guarded(c, [&] {
+    HP_REQUIRE(in && out && n >= 1 && n <= 4096, HPLMM_ERR_INVALID, "ws_predict: need inputs, outputs and 1 <= n <= 4096");
+    HP_REQUIRE(c->ws.has_params, HPLMM_ERR_STATE, "ws_predict: set the network parameters first");
+    hp::ws_infer(c, in, n, out);
+    HP_CUDA(cudaStreamSynchronize(c->stream));
   });
 }
 

@@ -143,6 +143,7 @@ struct LocalSet {
   int tuned_ring_rows = 0;   // far ring rows (0 = largest that fits) and diagonal-chunk stages
   int tuned_c0_stages = 0;
   int tuned_cluster = 0;     // CTAs per problem of the smoother solve (0 = default: 2 when the set is small)
+  int tuned_occ = 0;         // CTAs per SM the smoother solve is compiled and sized for (0 = default: 1)
   hplmm_prec prec = HPLMM_FP64;
 };
 
@@ -435,6 +436,7 @@ void ws_train(hplmm_ctx *c, const int32_t *order, long long n_order, int batch, 
 double ws_loss_grad(hplmm_ctx *c, const float *theta, const float *x, const float *tgt, const float *valid, int B,
                     int D, float *grad);
 void ws_pcg_basis(hplmm_ctx *c, bool warm);
+void ws_infer(hplmm_ctx *c, const float *x, int B, float *q);  // BF16 inference, D = 17
 int num_sms();
 // coarse.cu
 void build_coarse(hplmm_ctx *c, const double *b_pad_for_corr);  // = the three steps below

@@ -146,6 +146,12 @@ def make_workload(name, seed=0):
         E = lognormal_modulus(shape, 2.0, rng)
         p = n // 16
         return Problem(name, mask, E, 0.3, (p, p, p), bcs_clamped_traction(), 4, seed)
+    if name == "porous192":
+        # the learned warm start's evaluation images: porosity 0.35, the 64^3 recipe's filter, 12^3 grains
+        shape = (192, 192, 192)
+        mask = porous_mask(shape, 0.35, 2.0, rng)
+        E = lognormal_modulus(shape, 2.0, rng)
+        return Problem(name, mask, E, 0.3, (12, 12, 12), bcs_clamped_traction(), 4, seed)
     if name == "porous128":
         shape = (128, 128, 128)
         mask = porous_mask(shape, 0.4, 3.0, rng)
@@ -176,6 +182,7 @@ WORKLOADS = {
     "porous64": "64^3 porous block: white noise -> Gaussian sigma=2 -> porosity 0.3 -> largest 6-connected "
                 "component touching z=0; log-normal E (mu=0, sigma=1, same filter); nu=0.3; 4x4x4 subdomains",
     "porous128": "128^3 porous block, porosity 0.4, sigma=3, log-normal E, nu=0.3, 8x8x8 subdomains",
+    "porous192": "192^3 porous block, porosity 0.35, sigma=2, log-normal E, nu=0.3, 12x12x12 subdomains",
     "fractured256": "256^3 porous block (porosity 0.25, sigma=2), 64-seed Voronoi two-phase E in {1,10}, "
                     "20 planar 1-voxel slits of radius 32 with E x 1e-4, nu=0.25, 16x16x16 subdomains",
 }

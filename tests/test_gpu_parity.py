@@ -135,7 +135,7 @@ def test_mixed_precision_forms(name, local, applyp):
 def test_bf16_apply_form(name):
     # BF16 copies of the FP32 local factors, basis panels and A_hat inside the apply (FP32 arithmetic, FP64
     # coarse solve): the apply differs from the FP64 oracle by BF16 rounding (8-bit significand, unit roundoff
-    # 2^-9 ~ 2e-3) amplified by the local problems' conditioning; the outer FP64 FGMRES still reaches the FP64
+    # 2^-8 ~ 3.9e-3) amplified by the local problems' conditioning; the outer FP64 FGMRES still reaches the FP64
     # residual, and the solution matches the oracle's to the tolerance's accuracy
     p, opt, sysm, M = oracle_case(name)
     rng = np.random.default_rng(2)
@@ -149,7 +149,7 @@ def test_bf16_apply_form(name):
     # the BF16 form is the FP32 form with its stored local factors and basis panels rounded to BF16: to first
     # order the error grows with the unit roundoff at the amplification the FP32 form shows (see
     # test_gpu_smoother_forms.test_bf16_error_follows_roundoff), and the rounding is visible
-    assert e32 < e_apply <= (1.0 + 2.0 ** 15) * e32, (e_apply, e32)
+    assert e32 < e_apply <= (1.0 + 2.0 ** 16) * e32, (e_apply, e32)
     x, rc, st = s.solve(tol=1e-8)
     xn = _n(x)
     assert rc == 0

@@ -32,7 +32,7 @@ FORMS = [
     (dict(local_prec="fp32", apply_prec="fp32"), 1e-5, 5e-3),
     (dict(local_prec="fp32", apply_prec="bf16"), 1e-3, None),
 ]
-U32, U16 = 2.0 ** -24, 2.0 ** -9   # unit roundoffs of FP32 and BF16 (24- and 8-bit significands)
+U32, U16 = 2.0 ** -24, 2.0 ** -8   # unit roundoffs of FP32 and BF16 (24- and 8-bit significands)
 
 
 @pytest.mark.parametrize("name", ["cube16_n4", "porous32_n4", "tiny10_strict"])
@@ -71,6 +71,25 @@ def test_bf16_error_follows_roundoff(name):
         s.close()
     print(f"{name}: M_CG^-1 r error vs FP64 oracle: FP32 {e['fp32']:.2e}, BF16 {e['bf16']:.2e}")
     assert e["fp32"] < e["bf16"] <= (1.0 + U16 / U32) * e["fp32"]
+
+
+@pytest.mark.parametrize("name", ["porous32_n4", "porous24_g216"])
+@pytest.mark.parametrize("form", [dict(local_prec="fp64", apply_prec="fp64"),
+                                  dict(local_prec="fp32", apply_prec="fp32"),
+                                  dict(local_prec="fp32", apply_prec="bf16")])
+def test_two_ctas_per_sm_instance_agrees(name, form):
+    # the instance compiled for two CTAs per SM (at most 80 registers, smaller ring) computes the same solves
+    p, opt, sysm, M = oracle_case(name)
+    r = np.random.default_rng(23).standard_normal(sysm.n_dof)
+    out = {}
+    for per_sm in (1, 2):
+        s = gpu_solver(name, smoother_per_sm=per_sm, **form)
+        out[per_sm] = _n(s.apply_smoother(_t(r)))
+        s.close()
+    tol = 1e-12 if form["apply_prec"] == "fp64" else 1e-5
+    assert rel(out[2], out[1]) < tol
+    if form["apply_prec"] != "bf16":   # the BF16 form's bound against the oracle: test_bf16_error_follows_roundoff
+        assert rel(out[2], M.smoother.apply(r)) < (1e-10 if form["apply_prec"] == "fp64" else 5e-3)
 
 
 @pytest.mark.parametrize("ctas", [1, 2])

@@ -186,3 +186,33 @@ def test_training_and_warm_start_gain():
     assert warm["init_rel_res_mean"] < cold["init_rel_res_mean"]
     assert warm["fallback_columns"] == 0 and cold["fallback_columns"] == 0
     assert rel(sols["pcg_warm"], sols["pcg"]) < 1e-6
+
+
+def test_bf16_inference_matches_oracle_forward():
+    # The inference path rounds the weights and every hidden activation to BF16 (round to nearest even, unit
+    # roundoff 2^-8) and sums in FP32.  The oracle states that computation (forward_bf16: the same roundings,
+    # exact sums): the GPU's output must match it to FP32 accumulation accuracy, give or take an activation
+    # whose FP32 sum lands on the other side of a BF16 rounding boundary.  Against the plain FP64 forward the
+    # error is the BF16 roundings' own, the same on both sides.
+    import paper_2509_19777_gb300 as hp
+    p = synth.make_workload("porous32", 21)
+    s = hp.Solver(n_mortar=4, contact_halfwidth=2, local_prec="fp32", apply_prec="fp32", keep_basis_rhs=True)
+    mask, E = hp.problem_to_device(p)
+    s.assemble(mask, E, p.nu, p.bcs)
+    s.setup(grains=p.grains)
+    s.ws_collect()
+    xin, _, _ = hp.hplmm_ws_get_samples(s.ctx, 0, 6)
+    theta = ows.init_params(5)
+    s.ws_set_params(theta)
+    q = _n(hp.hplmm_ws_predict(s.ctx, xin)).astype(np.float64).reshape(6, 3, 17, 17, 17)
+    x = _n(xin).astype(np.float64).reshape(6, 5, 17, 17, 17)
+    ref16 = ows.forward_bf16(theta, x)
+    ref64 = ows.forward(theta.astype(np.float64), x)[-1]
+    e16 = np.linalg.norm(q - ref16) / np.linalg.norm(ref16)
+    e64 = np.linalg.norm(q - ref64) / np.linalg.norm(ref64)
+    e_def = np.linalg.norm(ref16 - ref64) / np.linalg.norm(ref64)
+    print(f"BF16 inference: vs the oracle's BF16 forward {e16:.2e}; vs its FP64 forward {e64:.2e} "
+          f"(the BF16 roundings themselves: {e_def:.2e})")
+    assert e16 < 1e-3
+    assert abs(e64 - e_def) <= 1e-3 + 0.1 * e_def
+    s.close()

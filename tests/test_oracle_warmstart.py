@@ -155,3 +155,31 @@ def test_pcg_matches_direct_solve_and_warm_start_helps():
     # the block-Jacobi operator is the inverse of the node-diagonal part
     Bd = Agg.toarray() * (node[:, None] == node[None, :])
     assert np.allclose(Dinv.toarray() @ Bd, np.eye(I.size), atol=1e-10)
+
+
+def test_round_bf16_against_its_definition():
+    # values the 8-bit significand holds exactly stay; halfway cases go to the even neighbour; others to the
+    # nearest; the result always has 16 zero low bits and is within half a unit: 2^-8 relative (the unit
+    # roundoff of an 8-bit significand)
+    assert ws.round_bf16(1.0) == 1.0 and ws.round_bf16(-3.5) == -3.5
+    assert ws.round_bf16(1.0 + 2.0 ** -8) == 1.0                       # tie: 1.0 is even
+    assert ws.round_bf16(1.0 + 3 * 2.0 ** -8) == 1.0 + 2.0 ** -6       # tie: up to the even neighbour
+    assert ws.round_bf16(1.0 + 2.0 ** -8 + 2.0 ** -20) == 1.0 + 2.0 ** -7
+    rng = np.random.default_rng(0)
+    v = rng.standard_normal(10000) * 10.0 ** rng.uniform(-5, 5, 10000)
+    r = ws.round_bf16(v)
+    bits = r.astype(np.float32).view(np.uint32)
+    assert np.all(bits & 0xFFFF == 0)
+    assert np.all(np.abs(r - v.astype(np.float32)) <= 2.0 ** -8 * np.abs(v.astype(np.float32)) * (1 + 1e-7))
+
+
+def test_forward_bf16_is_forward_of_rounded_weights_when_activations_are_exact():
+    # with weights that are already BF16 values and a one-layer network, the BF16 path equals the plain
+    # forward of those weights (rounded to FP32 at the output)
+    rng = np.random.default_rng(2)
+    ch = (2, 3)
+    theta = ws.round_bf16(rng.standard_normal(ws.n_params(ch)) * 0.1)
+    x = ws.round_bf16(rng.standard_normal((1, 2, 5, 5, 5)))
+    ref = ws.forward(theta, x, ch)[-1]
+    got = ws.forward_bf16(theta, x, ch)
+    assert np.abs(got - ref).max() <= 2.0 ** -23 * np.abs(ref).max()
