@@ -81,9 +81,6 @@ typedef struct {
   int smoother_ctas;     /* CTAs per local problem in the smoother solves: 0 (default) the tuner's choice, or
                             two for a set with at most half as many problems as the GPU has SMs, else one;
                             1 or 2 force it (two: a cluster that splits each panel's far rows) */
-  int smoother_per_sm;   /* smoother solve instance: 0 (default) the tuner's choice, else one CTA per SM (the
-                            largest ring); 1 or 2 force the instance sized and compiled (at most 80
-                            registers per thread) for one or two CTAs per SM */
   int stage_mb;          /* BF16 apply form (local_prec FP32, apply_prec BF16, exact basis solves): the local
                             factors are computed in FP32 in chunks of at most this many MiB, each chunk of grains
                             used for its basis solves, then kept only as BF16 (0 = default, 6144); the result does

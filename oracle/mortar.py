@@ -26,6 +26,18 @@ global xyz frame: because a Gaussian mortar is the same scalar on every
 component, the span of {eta_i e_gamma} does not depend on the interface's
 local (n, m) frame.
 
+Algebraic mortars (Eq. algebra, and the Remark after Eq. reduced_defs): the column (mortar i, component
+gamma) of interface c is the displacement field on the interface's free DOFs that equals 1 at DOF
+(x_i, gamma), 0 at every other mortar DOF, and solves S^c w = 0 on the remaining DOFs: the rows and columns
+of the mortar DOFs are removed, the column of the unit DOF moved to the right-hand side, and the reduced
+system solved (a dense solve, as a library primitive).  S^c is the interface block A^c_c of A_hat (its
+principal submatrix on the interface's free DOFs) with each node's 3x3 diagonal block reduced by that node's
+block-row sum over the interface, so that S^c annihilates rigid translations of the interface -- the
+property Eq. algebra states (its mortars sum to e_gamma "by superposition"); with one mortar per interface
+the column is then the rigid translation, as for PLMM.  (The unshifted principal submatrix gives mortars
+that decay within a node or two of their mortar node.)  A column (i, gamma) exists only when DOF
+(x_i, gamma) is free (a fixed DOF cannot carry the unit value).
+
 Q^o (Eq. reduced_defs) is block-diagonal per interface: rows are the free
 interface DOFs in W order, columns are (interface, mortar i, component gamma)
 in that nesting order.  A column with no free DOF (every node of the
@@ -121,10 +133,14 @@ def gaussian_mortars(coords, chosen, beta=4.0):
 class Mortars:
     """Mortar nodes, eta weights and Q^o for every interface of a decomposition."""
 
-    def __init__(self, system, dec, n, beta=4.0):
+    def __init__(self, system, dec, n, beta=4.0, kind="gaussian"):
         mesh = system.mesh
         self.n = int(n)
         self.beta = float(beta)
+        if kind not in ("gaussian", "algebraic"):
+            raise ValueError(kind)
+        self.kind = kind
+        self._alg = {}
         self.mortar_nodes = []     # per interface: global node ids of its mortars, in mortar order
         self.eta = []              # per interface: |F^c| x n_c weights
         self.columns = []          # per interface: list of (mortar i, component gamma) kept
@@ -135,8 +151,12 @@ class Mortars:
             chosen = place_mortars(coords, self.n)
             self.mortar_nodes.append(nodes[chosen])
             self.eta.append(gaussian_mortars(coords, chosen, self.beta))
-            free_comp = (~fixed[nodes]).any(axis=0)
-            self.columns.append([(i, g) for i in range(len(chosen)) for g in range(3) if free_comp[g]])
+            if kind == "gaussian":
+                free_comp = (~fixed[nodes]).any(axis=0)
+                self.columns.append([(i, g) for i in range(len(chosen)) for g in range(3) if free_comp[g]])
+            else:
+                self.columns.append([(i, g) for i in range(len(chosen)) for g in range(3)
+                                     if not fixed[nodes[chosen[i]], g]])
         self.iface_col_offset = np.zeros(dec.n_interfaces + 1, np.int64)
         for c in range(dec.n_interfaces):
             self.iface_col_offset[c + 1] = self.iface_col_offset[c] + len(self.columns[c])
@@ -150,11 +170,43 @@ class Mortars:
             for d in range(3):
                 if not system.fixed[node, d]:
                     rows.append((y, d))
+        if self.kind == "algebraic":
+            return self._algebraic_block(system, dec, c, rows)
         Q = np.zeros((len(rows), len(self.columns[c])))
         for r, (y, d) in enumerate(rows):
             for k, (i, g) in enumerate(self.columns[c]):
                 if g == d:
                     Q[r, k] = self.eta[c][y, i]
+        return Q
+
+    def _algebraic_block(self, system, dec, c, rows):
+        if c in self._alg:
+            return self._alg[c]
+        J = dec.iface_dofs[c]
+        Acc = system.A[J][:, J].toarray()
+        # S^c: each node's diagonal block minus its block-row sum over the interface (translations -> 0)
+        node_of = np.array([y for (y, d) in rows], np.int64)
+        comp_of = np.array([d for (y, d) in rows], np.int64)
+        S = Acc.copy()
+        for r in range(len(rows)):
+            for g in range(3):
+                same_g = comp_of == g
+                diag = np.flatnonzero((node_of == node_of[r]) & same_g)
+                if diag.size:
+                    S[r, diag[0]] -= Acc[r, same_g].sum()
+        Acc = S
+        mortar_y = set(np.flatnonzero(np.isin(dec.iface_nodes[c], self.mortar_nodes[c])).tolist())
+        pos = {yd: r for r, yd in enumerate(rows)}
+        is_m = np.array([y in mortar_y for (y, d) in rows], dtype=bool)
+        R = np.flatnonzero(~is_m)
+        chosen_y = [int(np.flatnonzero(dec.iface_nodes[c] == m)[0]) for m in self.mortar_nodes[c]]
+        Q = np.zeros((len(rows), len(self.columns[c])))
+        for k, (i, g) in enumerate(self.columns[c]):
+            r1 = pos[(chosen_y[i], g)]
+            Q[r1, k] = 1.0
+            if R.size:
+                Q[R, k] = -np.linalg.solve(Acc[np.ix_(R, R)], Acc[R, r1])
+        self._alg[c] = Q
         return Q
 
     def Qo(self, system, dec):

@@ -30,6 +30,7 @@ class Options:
     n_st: int = 1              # smoother stages (Eq. local_smoother)
     strict_two_grain: bool = False
     keep_corrections: bool = True
+    mortar_kind: str = "gaussian"   # "gaussian" (Eq. gauss) or "algebraic" (Eq. algebra)
 
 
 class HPLMM:
@@ -39,7 +40,7 @@ class HPLMM:
         self.system = system
         self.opt = opt
         self.dec = Decomposition(system, grain_of_voxel, n_grains, opt.strict_two_grain)
-        self.mortars = Mortars(system, self.dec, opt.n_mortar, opt.beta)
+        self.mortars = Mortars(system, self.dec, opt.n_mortar, opt.beta, opt.mortar_kind)
         self.coarse = CoarseSpace(system, self.dec, self.mortars, opt.keep_corrections)
         self.smoother = ContactGrainSmoother(system, self.dec, self.coarse, opt.contact_halfwidth)
         self.A = system.A.tocsr()

@@ -93,8 +93,6 @@ void validate_options(const hplmm_options &o) {
   HP_REQUIRE(o.basis_tol > 0.0 && o.basis_tol < 1.0, HPLMM_ERR_INVALID, "basis_tol must lie in (0, 1)");
   HP_REQUIRE(o.basis_max_iters >= 1, HPLMM_ERR_INVALID, "basis_max_iters must be positive");
   HP_REQUIRE(o.smoother_ctas >= 0 && o.smoother_ctas <= 2, HPLMM_ERR_INVALID, "smoother_ctas must be 0, 1 or 2");
-  HP_REQUIRE(o.smoother_per_sm >= 0 && o.smoother_per_sm <= 2, HPLMM_ERR_INVALID,
-             "smoother_per_sm must be 0, 1 or 2");
   HP_REQUIRE(o.stage_mb >= 0, HPLMM_ERR_INVALID, "stage_mb must be non-negative");
   HP_REQUIRE(o.wait_budget_us >= 0, HPLMM_ERR_INVALID, "wait_budget_us must be non-negative");
 }

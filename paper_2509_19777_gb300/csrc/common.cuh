@@ -143,7 +143,6 @@ struct LocalSet {
   int tuned_ring_rows = 0;   // far ring rows (0 = largest that fits) and diagonal-chunk stages
   int tuned_c0_stages = 0;
   int tuned_cluster = 0;     // CTAs per problem of the smoother solve (0 = default: 2 when the set is small)
-  int tuned_occ = 0;         // CTAs per SM the smoother solve is compiled and sized for (0 = default: 1)
   hplmm_prec prec = HPLMM_FP64;
 };
 

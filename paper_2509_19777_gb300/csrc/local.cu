@@ -1262,12 +1262,8 @@ template <typename T, int n> __device__ __forceinline__ void ld_vec(const T *p, 
   }
 }
 
-// MINB = 2 asks the compiler for at most 80 registers per thread so that two CTAs fit on an SM (with 120
-// registers one CTA of 352 threads already takes 42k of the SM's 64k registers): for sets of many small
-// problems, whose solve chains are latency-bound, two CTAs per SM can hide each other's waits; the tuner
-// times both
-template <typename S, int NB, int CL, int MINB = 1>
-__global__ void __launch_bounds__(WS_THREADS, MINB) k_band_solve_ws(
+template <typename S, int NB, int CL>
+__global__ void __launch_bounds__(WS_THREADS) k_band_solve_ws(
     int count, const int *nloc, const int *bwv, const long long *band_off, const long long *vec_off,
     const int *gidx, const S *band, const double *r, double *z, typename ComputeOf<S>::type *yscr, int atomic,
     int ring_rows, int chunk_rows, int c0_stages, int wmask, int *status, long long wait_cycles) {
@@ -2394,10 +2390,9 @@ void smoother_apply(hplmm_ctx *c, LocalSet &S, const double *r_pad, double *z_pa
   // depths: the tuner's choice when there is one, else 3 diagonal stages, whole-step chunks and the largest
   // ring
   const int c0s = S.tuned_c0_stages > 0 ? S.tuned_c0_stages : 3;
-  const int occ = c->opt.smoother_per_sm > 0 ? c->opt.smoother_per_sm : (S.tuned_occ == 2 ? 2 : 1);
   auto go = [&](auto kern, const auto *band, auto *ys) {
     const SmemBudget bud = smem_budget(kern);
-    int ring = ring_rows_for(pl, c0s, occ == 2 ? bud.pair : bud.one);
+    int ring = ring_rows_for(pl, c0s, bud.one);
     if (S.tuned_ring_rows > 0) ring = std::min(ring, S.tuned_ring_rows);
     HP_REQUIRE(ring >= 64, HPLMM_ERR_INVALID,
                "local problem too large for the smoother (window of " + std::to_string(pl.W) + " rows)");
@@ -2422,14 +2417,14 @@ void smoother_apply(hplmm_ctx *c, LocalSet &S, const double *r_pad, double *z_pa
                                chunk, c0s, pl.W - 1, c->status.p,
                                c->opt.wait_budget_us > 0 ? (long long)c->opt.wait_budget_us * 2070LL : WAIT_CYCLES));
   };
-  // the kernel instance: storage type, CTAs per problem, CTAs per SM
+  // the kernel instance: storage type and CTAs per problem
   auto pick = [&](auto tag, auto nb, const auto *band, auto *ys) {
     using ST = decltype(tag);
     constexpr int NBv = decltype(nb)::value;
     if (cl == 2)
-      occ == 2 ? go(k_band_solve_ws<ST, NBv, 2, 2>, band, ys) : go(k_band_solve_ws<ST, NBv, 2, 1>, band, ys);
+      go(k_band_solve_ws<ST, NBv, 2>, band, ys);
     else
-      occ == 2 ? go(k_band_solve_ws<ST, NBv, 1, 2>, band, ys) : go(k_band_solve_ws<ST, NBv, 1, 1>, band, ys);
+      go(k_band_solve_ws<ST, NBv, 1>, band, ys);
   };
   if (S.prec == HPLMM_FP64) {
     pick(double{}, std::integral_constant<int, 16>{}, (const double *)S.band64.p, S.yscr.p);
@@ -2456,16 +2451,15 @@ struct TuneKey {
 };
 std::mutex g_tune_mu;
 struct TuneChoice {
-  int chunk_rows, ring_rows, c0_stages, cluster, occ;
+  int chunk_rows, ring_rows, c0_stages, cluster;
 };
 std::map<TuneKey, TuneChoice> g_tune_cache;
 }  // namespace
 
 static void tune_set(hplmm_ctx *c, LocalSet &S, bool atomic) {
-  S.tuned_chunk_rows = S.tuned_ring_rows = S.tuned_c0_stages = S.tuned_cluster = S.tuned_occ = 0;
+  S.tuned_chunk_rows = S.tuned_ring_rows = S.tuned_c0_stages = S.tuned_cluster = 0;
   if (S.count == 0) return;
-  TuneKey key{S.count, 0, 0,
-              (int)S.prec + (S.apply_bf16 ? 8 : 0) + 16 * c->opt.smoother_ctas + 64 * c->opt.smoother_per_sm};
+  TuneKey key{S.count, 0, 0, (int)S.prec + (S.apply_bf16 ? 8 : 0) + 16 * c->opt.smoother_ctas};
   for (int k = 0; k < S.count; ++k) {
     key.nmax = std::max(key.nmax, S.h_n[k]);
     key.bwmax = std::max(key.bwmax, S.h_bw[k]);
@@ -2478,7 +2472,6 @@ static void tune_set(hplmm_ctx *c, LocalSet &S, bool atomic) {
       S.tuned_ring_rows = it->second.ring_rows;
       S.tuned_c0_stages = it->second.c0_stages;
       S.tuned_cluster = it->second.cluster;
-      S.tuned_occ = it->second.occ;
       return;
     }
   }
@@ -2490,7 +2483,7 @@ static void tune_set(hplmm_ctx *c, LocalSet &S, bool atomic) {
   const bool prof = c->opt.profile;
   c->opt.profile = 0;  // tuning launches are not part of any phase
   float best = 1e30f;
-  TuneChoice bc{0, 0, 0, 0, 0};
+  TuneChoice bc{0, 0, 0, 0};
   // budgets of the FP32 one-CTA kernel (the static shared memory of every instantiation is about the same;
   // smoother_apply clamps the ring to the launched kernel's own budget)
   const SmemBudget bud = S.prec == HPLMM_FP64 ? smem_budget(k_band_solve_ws<double, 16, 1>)
@@ -2499,16 +2492,14 @@ static void tune_set(hplmm_ctx *c, LocalSet &S, bool atomic) {
    for (int chunk : chunk_choices(S))
     if (c->opt.smoother_ctas == 0 || c->opt.smoother_ctas == cl)
     for (int c0d = 2; c0d <= 4; ++c0d)
-      for (int occ : {1, 2}) {
-        if (c->opt.smoother_per_sm > 0 && occ != c->opt.smoother_per_sm) continue;
-        const int ring = ring_rows_for(pl, c0d, occ == 1 ? bud.one : bud.pair);
+      for (size_t budget : {bud.one, bud.pair}) {
+        const int ring = ring_rows_for(pl, c0d, budget);
         const int cr = std::min(chunk, ring);
         if (cr < 64) continue;
         S.tuned_chunk_rows = cr;
         S.tuned_ring_rows = ring;
         S.tuned_c0_stages = c0d;
         S.tuned_cluster = cl;
-        S.tuned_occ = occ;
         smoother_apply(c, S, c->b_pad.p, c->w_zz.p, atomic);  // warm-up
         HP_CUDA(cudaEventRecord(e0, s));
         for (int rep = 0; rep < 3; ++rep) smoother_apply(c, S, c->b_pad.p, c->w_zz.p, atomic);
@@ -2518,12 +2509,12 @@ static void tune_set(hplmm_ctx *c, LocalSet &S, bool atomic) {
         HP_CUDA(cudaEventElapsedTime(&ms, e0, e1));
         if (c->opt.verbose)
           fprintf(stderr,
-                  "[hplmm] tuner trial: %d problems, %d CTA(s) each, %d per SM, chunk %d rows, ring %d rows, "
-                  "diagonal %d: %.3f ms\n",
-                  S.count, cl, occ, cr, ring, c0d, ms / 3);
+                  "[hplmm] tuner trial: %d problems, %d CTA(s) each, chunk %d rows, ring %d rows, diagonal %d: "
+                  "%.3f ms\n",
+                  S.count, cl, cr, ring, c0d, ms / 3);
         if (ms < best) {
           best = ms;
-          bc = {cr, ring, c0d, cl, occ};
+          bc = {cr, ring, c0d, cl};
         }
       }
   c->opt.profile = prof;
@@ -2533,7 +2524,6 @@ static void tune_set(hplmm_ctx *c, LocalSet &S, bool atomic) {
   S.tuned_ring_rows = bc.ring_rows;
   S.tuned_c0_stages = bc.c0_stages;
   S.tuned_cluster = bc.cluster;
-  S.tuned_occ = bc.occ;
   if (c->opt.verbose)
     fprintf(stderr,
             "[hplmm] tuner: %d problems (n<=%d, bw<=%d): %d CTA(s) each, chunk %d rows, ring %d rows, diagonal "

@@ -62,9 +62,10 @@ def test_multi_apply_matches_single_apply(form, tol):
         if form["apply_prec"] == "fp64":
             assert rel(Z[q], z1) < tol and em < 1e-10, (q, rel(Z[q], z1), em)
         else:
-            # two different FP32 computations of the same operator: each within the form's error of the
-            # FP64 oracle, so they differ by at most the sum of those errors
-            assert em < 1e-3 and rel(Z[q], z1) <= e1 + em, (q, rel(Z[q], z1), e1, em)
+            # two different FP32 computations of the same operator (the multi-vector smoother uses other
+            # kernels): each carries the form's error against the FP64 oracle, so they differ by at most the
+            # sum of those errors, and neither is more than a few times the other
+            assert rel(Z[q], z1) <= e1 + em and em <= 4 * e1, (q, rel(Z[q], z1), e1, em)
     s.close()
 
 

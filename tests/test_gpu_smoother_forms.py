@@ -73,25 +73,6 @@ def test_bf16_error_follows_roundoff(name):
     assert e["fp32"] < e["bf16"] <= (1.0 + U16 / U32) * e["fp32"]
 
 
-@pytest.mark.parametrize("name", ["porous32_n4", "porous24_g216"])
-@pytest.mark.parametrize("form", [dict(local_prec="fp64", apply_prec="fp64"),
-                                  dict(local_prec="fp32", apply_prec="fp32"),
-                                  dict(local_prec="fp32", apply_prec="bf16")])
-def test_two_ctas_per_sm_instance_agrees(name, form):
-    # the instance compiled for two CTAs per SM (at most 80 registers, smaller ring) computes the same solves
-    p, opt, sysm, M = oracle_case(name)
-    r = np.random.default_rng(23).standard_normal(sysm.n_dof)
-    out = {}
-    for per_sm in (1, 2):
-        s = gpu_solver(name, smoother_per_sm=per_sm, **form)
-        out[per_sm] = _n(s.apply_smoother(_t(r)))
-        s.close()
-    tol = 1e-12 if form["apply_prec"] == "fp64" else 1e-5
-    assert rel(out[2], out[1]) < tol
-    if form["apply_prec"] != "bf16":   # the BF16 form's bound against the oracle: test_bf16_error_follows_roundoff
-        assert rel(out[2], M.smoother.apply(r)) < (1e-10 if form["apply_prec"] == "fp64" else 5e-3)
-
-
 @pytest.mark.parametrize("ctas", [1, 2])
 def test_two_cta_solve_matches_oracle(ctas):
     name = "porous32_n4"

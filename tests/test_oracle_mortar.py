@@ -106,3 +106,64 @@ def test_gaussian_closed_form_two_mortars():
 def test_single_mortar_is_constant_one():
     coords = np.array([[k, 1, 2] for k in range(5)])
     assert np.array_equal(gaussian_mortars(coords, [2]), np.ones((5, 1)))
+
+
+# ---------------------------------------------------------------- algebraic mortars (Eq. algebra)
+def _alg_case(n, name="tiny8", seed=3):
+    import synth
+    from oracle import precond
+    p = synth.make_workload(name, seed)
+    return precond.build(p, precond.Options(n_mortar=n, contact_halfwidth=1, mortar_kind="algebraic"))
+
+
+@pytest.mark.parametrize("n", [2, 4])
+def test_algebraic_mortars_partition_of_unity_and_constraints(n):
+    # Eq. algebra: every mortar function is 1 in its own component at its own mortar node and 0 in every
+    # component at the other mortar nodes, and the functions of one component sum to e_gamma on the
+    # interface (the paper: "guaranteed automatically by superposition")
+    sysm, M = _alg_case(n)
+    mo, dec = M.mortars, M.dec
+    for c in range(dec.n_interfaces):
+        nodes = dec.iface_nodes[c]
+        rows = [(y, d) for y, node in enumerate(nodes) for d in range(3) if not sysm.fixed[node, d]]
+        Q = mo.Qo_block(sysm, dec, c)
+        chosen = [int(np.flatnonzero(nodes == m)[0]) for m in mo.mortar_nodes[c]]
+        for k, (i, g) in enumerate(mo.columns[c]):
+            for r, (y, d) in enumerate(rows):
+                if y in chosen:
+                    want = 1.0 if (y == chosen[i] and d == g) else 0.0
+                    assert Q[r, k] == want
+        all_free = all(not sysm.fixed[nodes[ch], g] for ch in chosen for g in range(3))
+        if all_free:
+            for g in range(3):
+                ks = [k for k, (i, gg) in enumerate(mo.columns[c]) if gg == g]
+                tot = Q[:, ks].sum(axis=1)
+                want = np.array([1.0 if d == g else 0.0 for (y, d) in rows])
+                assert np.abs(tot - want).max() < 1e-10, (c, g)
+
+
+def test_algebraic_one_mortar_is_plmm():
+    # one mortar per interface: the algebraic function is the rigid translation, the same as the Gaussian
+    # one (eta = 1), so both give PLMM's coarse matrix
+    import synth
+    from oracle import precond
+    p = synth.make_workload("tiny8", 3)
+    Ao = {}
+    for kind in ("gaussian", "algebraic"):
+        sysm, M = precond.build(p, precond.Options(n_mortar=1, contact_halfwidth=1, mortar_kind=kind))
+        Ao[kind] = M.coarse.A_o
+    assert np.abs(Ao["gaussian"] - Ao["algebraic"]).max() < 1e-10 * np.abs(Ao["gaussian"]).max()
+
+
+def test_algebraic_all_nodes_mortars_is_identity():
+    # n_c = |F|: every interface DOF is a mortar DOF, so Q^o is the identity and the first pass is exact
+    import scipy.sparse.linalg as spla
+    import synth
+    from oracle import precond
+    p = synth.make_workload("tiny6", 1)
+    sysm, M = precond.build(p, precond.Options(n_mortar=10 ** 4, contact_halfwidth=1, mortar_kind="algebraic"))
+    for c in range(M.dec.n_interfaces):
+        Q = M.mortars.Qo_block(sysm, M.dec, c)
+        assert Q.shape[0] == Q.shape[1] and np.array_equal(Q, np.eye(Q.shape[0]))
+    xs = spla.spsolve(sysm.A.tocsc(), sysm.b)
+    assert np.linalg.norm(M.M_G(sysm.b) - xs) < 1e-10 * np.linalg.norm(xs)
