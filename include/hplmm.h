@@ -81,6 +81,9 @@ typedef struct {
   int smoother_ctas;     /* CTAs per local problem in the smoother solves: 0 (default) the tuner's choice, or
                             two for a set with at most half as many problems as the GPU has SMs, else one;
                             1 or 2 force it (two: a cluster that splits each panel's far rows) */
+  int mortar_kind;       /* mortar functions (Section 3.3): HPLMM_MORTAR_GAUSSIAN (default, Eq. gauss, spread
+                            beta) or HPLMM_MORTAR_ALGEBRAIC (Eq. algebra: each interface's mortar functions solve
+                            its own elasticity block with unit/zero values at the mortar DOFs; no parameter) */
   int stage_mb;          /* BF16 apply form (local_prec FP32, apply_prec BF16, exact basis solves): the local
                             factors are computed in FP32 in chunks of at most this many MiB, each chunk of grains
                             used for its basis solves, then kept only as BF16 (0 = default, 6144); the result does
@@ -92,6 +95,7 @@ typedef struct {
 } hplmm_options;
 
 enum { HPLMM_BASIS_DIRECT = 0, HPLMM_BASIS_PCG = 1, HPLMM_BASIS_PCG_WARM = 2 };
+enum { HPLMM_MORTAR_GAUSSIAN = 0, HPLMM_MORTAR_ALGEBRAIC = 1 };
 
 /* Boundary conditions on the six faces of the image box, in the order
  * x=0, x=nx, y=0, y=ny, z=0, z=nz (Eq. BC).  fix[f][d] != 0 prescribes

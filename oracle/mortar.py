@@ -30,12 +30,23 @@ Algebraic mortars (Eq. algebra, and the Remark after Eq. reduced_defs): the colu
 gamma) of interface c is the displacement field on the interface's free DOFs that equals 1 at DOF
 (x_i, gamma), 0 at every other mortar DOF, and solves S^c w = 0 on the remaining DOFs: the rows and columns
 of the mortar DOFs are removed, the column of the unit DOF moved to the right-hand side, and the reduced
-system solved (a dense solve, as a library primitive).  S^c is the interface block A^c_c of A_hat (its
-principal submatrix on the interface's free DOFs) with each node's 3x3 diagonal block reduced by that node's
-block-row sum over the interface, so that S^c annihilates rigid translations of the interface -- the
-property Eq. algebra states (its mortars sum to e_gamma "by superposition"); with one mortar per interface
-the column is then the rigid translation, as for PLMM.  (The unshifted principal submatrix gives mortars
-that decay within a node or two of their mortar node.)  A column (i, gamma) exists only when DOF
+system solved (a dense solve, as a library primitive).  S^c stands for the interface's own elasticity
+operator of Eq. algebra, built from A_hat alone: for every pair of distinct interface nodes {y, y'} that
+A_hat couples, the edge term (e_y - e_y')(e_y - e_y')^T (x) B_yy', where B_yy' = |-(A_yy' + A_yy'^T)/2|
+(the matrix absolute value: eigenvectors kept, eigenvalues replaced by their magnitudes) and A_yy' is the
+3x3 block of A_hat (zero where a DOF is fixed); then ALG_SHIFT times A_hat's diagonal is added.  Without
+the shift S^c is symmetric positive semidefinite and annihilates rigid translations of the interface, so
+the mortars of one component sum to e_gamma (Eq. algebra's partition of unity "by superposition"), and
+with one mortar the column is the rigid translation, as for PLMM.  Where A_hat's coupling is attractive
+(-sym(A_yy') positive semidefinite) the edge term carries A_hat's own coupling.  The shift (1e-8 of the
+diagonal) makes S^c positive definite on interface pieces that carry no mortar node and moves the sums
+away from e_gamma by about 1e-6 at most on the tested interfaces.  Other readings and why they were
+left: the literal principal submatrix A^c_c (the Remark) gives mortars that decay within a node or two of
+their mortar node; A^c_c with each diagonal block shifted by its block-row sum is not positive definite
+where the couplings of the normal component between in-plane neighbours are positive (the normal-gradient
+part of the 3D stiffness); and clipping negative eigenvalues instead of taking magnitudes leaves the
+normal component of a planar interface coupled only along diagonals (a checkerboard of two decoupled
+halves, one without mortars).  A column (i, gamma) exists only when DOF
 (x_i, gamma) is free (a fixed DOF cannot carry the unit value).
 
 Q^o (Eq. reduced_defs) is block-diagonal per interface: rows are the free
@@ -50,6 +61,7 @@ import numpy as np
 import scipy.sparse as sp
 
 MAX_SWEEPS = 100
+ALG_SHIFT = 1e-8   # diagonal shift of the algebraic mortars' interface operator, relative to A_hat's diagonal
 
 
 def _d2(P, q):
@@ -179,22 +191,42 @@ class Mortars:
                     Q[r, k] = self.eta[c][y, i]
         return Q
 
+    def _interface_operator(self, system, dec, c, rows):
+        """S^c on the interface's free DOFs (rows in W order): a sum over coupled node pairs {y, y'} of
+        (e_y - e_y')(e_y - e_y')^T (x) B_yy', B_yy' = |-(A_yy' + A_yy'^T)/2| (matrix absolute value; A_yy'
+        the 3x3 block of A_hat, zero where a DOF is fixed), plus ALG_SHIFT times the diagonal of A_hat on
+        those DOFs."""
+        nodes = dec.iface_nodes[c]
+        F = len(nodes)
+        f2f = system.full_to_free
+        J = np.array([f2f[3 * nodes[y] + d] for (y, d) in rows], np.int64)
+        Acc = system.A[J][:, J].tocoo()
+        # the interface block on all 3F node components, zero on fixed ones
+        full_of_row = np.array([3 * y + d for (y, d) in rows], np.int64)
+        Afull = np.zeros((3 * F, 3 * F))
+        Afull[full_of_row[Acc.row], full_of_row[Acc.col]] = Acc.data
+        ny, nz = full_of_row[Acc.row] // 3, full_of_row[Acc.col] // 3
+        pairs = np.unique(np.stack([np.minimum(ny, nz), np.maximum(ny, nz)], axis=1), axis=0)
+        pairs = pairs[pairs[:, 0] != pairs[:, 1]]
+        S = np.zeros((3 * F, 3 * F))
+        if len(pairs):
+            blk = np.stack([Afull[3 * y:3 * y + 3, 3 * z:3 * z + 3] for (y, z) in pairs])
+            B = -0.5 * (blk + blk.transpose(0, 2, 1))
+            w, V = np.linalg.eigh(B)
+            P = np.einsum("kij,kj,klj->kil", V, np.abs(w), V)
+            for (y, z), Pk in zip(pairs, P):
+                S[3 * y:3 * y + 3, 3 * y:3 * y + 3] += Pk
+                S[3 * z:3 * z + 3, 3 * z:3 * z + 3] += Pk
+                S[3 * y:3 * y + 3, 3 * z:3 * z + 3] -= Pk
+                S[3 * z:3 * z + 3, 3 * y:3 * y + 3] -= Pk
+        S = S[np.ix_(full_of_row, full_of_row)]
+        S[np.diag_indices_from(S)] += ALG_SHIFT * system.A.diagonal()[J]
+        return S
+
     def _algebraic_block(self, system, dec, c, rows):
         if c in self._alg:
             return self._alg[c]
-        J = dec.iface_dofs[c]
-        Acc = system.A[J][:, J].toarray()
-        # S^c: each node's diagonal block minus its block-row sum over the interface (translations -> 0)
-        node_of = np.array([y for (y, d) in rows], np.int64)
-        comp_of = np.array([d for (y, d) in rows], np.int64)
-        S = Acc.copy()
-        for r in range(len(rows)):
-            for g in range(3):
-                same_g = comp_of == g
-                diag = np.flatnonzero((node_of == node_of[r]) & same_g)
-                if diag.size:
-                    S[r, diag[0]] -= Acc[r, same_g].sum()
-        Acc = S
+        S = self._interface_operator(system, dec, c, rows)
         mortar_y = set(np.flatnonzero(np.isin(dec.iface_nodes[c], self.mortar_nodes[c])).tolist())
         pos = {yd: r for r, yd in enumerate(rows)}
         is_m = np.array([y in mortar_y for (y, d) in rows], dtype=bool)
@@ -205,7 +237,7 @@ class Mortars:
             r1 = pos[(chosen_y[i], g)]
             Q[r1, k] = 1.0
             if R.size:
-                Q[R, k] = -np.linalg.solve(Acc[np.ix_(R, R)], Acc[R, r1])
+                Q[R, k] = -np.linalg.solve(S[np.ix_(R, R)], S[R, r1])
         self._alg[c] = Q
         return Q
 

@@ -93,6 +93,8 @@ void validate_options(const hplmm_options &o) {
   HP_REQUIRE(o.basis_tol > 0.0 && o.basis_tol < 1.0, HPLMM_ERR_INVALID, "basis_tol must lie in (0, 1)");
   HP_REQUIRE(o.basis_max_iters >= 1, HPLMM_ERR_INVALID, "basis_max_iters must be positive");
   HP_REQUIRE(o.smoother_ctas >= 0 && o.smoother_ctas <= 2, HPLMM_ERR_INVALID, "smoother_ctas must be 0, 1 or 2");
+  HP_REQUIRE(o.mortar_kind == HPLMM_MORTAR_GAUSSIAN || o.mortar_kind == HPLMM_MORTAR_ALGEBRAIC, HPLMM_ERR_INVALID,
+             "mortar_kind must be HPLMM_MORTAR_GAUSSIAN or HPLMM_MORTAR_ALGEBRAIC");
   HP_REQUIRE(o.stage_mb >= 0, HPLMM_ERR_INVALID, "stage_mb must be non-negative");
   HP_REQUIRE(o.wait_budget_us >= 0, HPLMM_ERR_INVALID, "wait_budget_us must be non-negative");
 }
@@ -210,6 +212,10 @@ hplmm_status hplmm_setup(hplmm_ctx *c, const int32_t *partition, int n_grains, i
       hp::ProfScope ps(c, HPLMM_PH_MAPS);
       hp::build_maps(c, partition);
       hp::build_mortars(c);
+      if (c->opt.mortar_kind == HPLMM_MORTAR_ALGEBRAIC) {
+        hp::build_algebraic_mortars(c);
+        hp::check_status(c);
+      }
       hp::build_local_sets(c);
     }
     double t1 = now_s(), t2, t3;

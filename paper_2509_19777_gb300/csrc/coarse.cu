@@ -32,6 +32,14 @@ __device__ __forceinline__ int colbase_of(const int *gi_off, const int *gi_iface
 
 __device__ __forceinline__ int comp_rank(int mask, int gamma) { return __popc(mask & ((1 << gamma) - 1)); }
 
+// Q^o of algebraic mortars (Eq. algebra): per interface a dense block, rows (interface slot, component),
+// columns the interface's own; q == nullptr selects the Gaussian mortars (eta_i e_gamma)
+struct QAlg {
+  const double *q;
+  const long long *qoff;
+  const int *col_off;  // first coarse column of each interface (its column count = the difference)
+};
+
 // right-hand sides of Eq. col_pk (-A^g_c Q^o e_k) and Eq. col_cg (b^g), one thread per local node
 template <typename T>
 __global__ void k_basis_rhs(int G, const long long *node_off, const int *nloc, const int *lnodes, const int *row_ptr,
@@ -39,7 +47,7 @@ __global__ void k_basis_rhs(int G, const long long *node_off, const int *nloc, c
                             const int *iface_pair, const int *mortar_off, const long long *eta_off, const double *eta,
                             const int *comp_mask, const int *gi_off, const int *gi_iface, const int *gi_colbase,
                             const int *kg, const int *corr_col, const long long *panel_off, const double *b,
-                            int strict, T *X) {
+                            int strict, T *X, QAlg qa) {
   int g = blockIdx.y;
   int cnt = nloc[g] / 3;
   int o = blockIdx.x * blockDim.x + threadIdx.x;
@@ -60,6 +68,16 @@ __global__ void k_basis_rhs(int G, const long long *node_off, const int *nloc, c
     int slot = iface_slot[m];
     const double *et = eta + eta_off[c] + (long long)slot * nc;
     const double *v = val + (long long)p * 9;
+    if (qa.q) {
+      const int ncol = qa.col_off[c + 1] - qa.col_off[c];
+      const double *qr = qa.q + qa.qoff[c] + (long long)3 * slot * ncol;
+      for (int kk = 0; kk < ncol; ++kk)
+        for (int d = 0; d < 3; ++d) {
+          const double a = v[3 * d] * qr[kk] + v[3 * d + 1] * qr[ncol + kk] + v[3 * d + 2] * qr[2 * ncol + kk];
+          if (a != 0.0) Xg[(long long)(3 * o + d) * ld + base + kk] -= (T)a;
+        }
+      continue;
+    }
     for (int i = 0; i < nc; ++i) {
       double w = et[i];
       for (int gam = 0; gam < 3; ++gam) {
@@ -100,7 +118,7 @@ __global__ void k_gal_fill(const int *gbox, const long long *gal_off, const int 
                            const uint8_t *fixed, const int *gbox_grain, const long long *node_off_g,
                            const int *lmap_g, const long long *panel_off, const T *X, const int *mortar_off,
                            const long long *eta_off, const double *eta, const int *comp_mask, const int *gi_off,
-                           const int *gi_iface, const int *gi_colbase, int g0, long long gbase, T *P) {
+                           const int *gi_iface, const int *gi_colbase, int g0, long long gbase, T *P, QAlg qa) {
   int g = g0 + blockIdx.y;
   const int *bx = gbox + 6 * g;
   int ex = bx[3], ey = bx[4], ez = bx[5];
@@ -128,6 +146,15 @@ __global__ void k_gal_fill(const int *gbox, const long long *gal_off, const int 
   if (c < 0) return;
   int base = colbase_of(gi_off, gi_iface, gi_colbase, g, c);
   if (base < 0) return;
+  if (qa.q) {
+    const int ncol = qa.col_off[c + 1] - qa.col_off[c];
+    const double *qr = qa.q + qa.qoff[c] + (long long)3 * iface_slot[n] * ncol;
+    for (int d = 0; d < 3; ++d) {
+      if (fixed[3 * n + d]) continue;
+      for (int kk = 0; kk < ncol; ++kk) Pr[(long long)d * k + base + kk] = (T)qr[d * ncol + kk];
+    }
+    return;
+  }
   int nc = mortar_off[c + 1] - mortar_off[c];
   int cm = comp_mask[c];
   int ncomp = __popc(cm);
@@ -245,7 +272,10 @@ __global__ void k_symmetrize(double *A, long long N, double *asym) {
 // t[gcol] += sum over grain rows of X_g[row][a] r_loc[row]; CTA = (grain, chunk of RCHUNK rows):
 // the chunk's residual entries are gathered once into shared memory, then each thread owns columns and
 // reads the panel rows coalesced.
-constexpr int RCHUNK = 128;
+// rows of a grain's panel per CTA of the restriction: each CTA adds its k partial sums into the coarse
+// vector atomically, so larger chunks mean fewer atomics (1,024 rows: a 12k-row grain takes 12 CTAs)
+constexpr int RCHUNK = 1024;
+constexpr int RCHUNK8 = 128;  // the same for the eight-vector restriction (its staged residuals are 8 wide)
 // largest coarse dimension for which the dense A^o is also kept (for inspection only)
 constexpr long long DENSE_COARSE_MAX = 12288;
 // elements of each of the Galerkin work arrays (P and Y on the grains' node boxes) per batch of grains
@@ -272,14 +302,19 @@ __global__ void __launch_bounds__(256) k_restrict_grain(const long long *node_of
   __syncthreads();
   const T *Xg = X + panel_off[g] + (long long)row0 * k;
   for (int a = threadIdx.x; a < k; a += blockDim.x) {
-    A s0 = 0, s1 = 0;
+    A s0 = 0, s1 = 0, s2 = 0, s3 = 0;
+    const T *xa = Xg + a;
     int rr = 0;
-    for (; rr + 1 < cnt; rr += 2) {
-      s0 += (A)Xg[(long long)rr * k + a] * rl[rr];
-      s1 += (A)Xg[(long long)(rr + 1) * k + a] * rl[rr + 1];
+    for (; rr + 3 < cnt; rr += 4) {  // four independent rows in flight per thread
+      const A x0 = (A)xa[(long long)rr * k], x1 = (A)xa[(long long)(rr + 1) * k];
+      const A x2 = (A)xa[(long long)(rr + 2) * k], x3 = (A)xa[(long long)(rr + 3) * k];
+      s0 += x0 * rl[rr];
+      s1 += x1 * rl[rr + 1];
+      s2 += x2 * rl[rr + 2];
+      s3 += x3 * rl[rr + 3];
     }
-    if (rr < cnt) s0 += (A)Xg[(long long)rr * k + a] * rl[rr];
-    atomicAdd(&t[gcol[gcol_off[g] + a]], (double)(s0 + s1));
+    for (; rr < cnt; ++rr) s0 += (A)xa[(long long)rr * k] * rl[rr];
+    atomicAdd(&t[gcol[gcol_off[g] + a]], (double)((s0 + s1) + (s2 + s3)));
   }
 }
 
@@ -287,11 +322,21 @@ __global__ void __launch_bounds__(256) k_restrict_grain(const long long *node_of
 __global__ void k_restrict_iface(const int *iface_nodes, const int *iface_of_node, long long count,
                                  const int *iface_slot, const int *mortar_off, const long long *eta_off,
                                  const double *eta, const int *comp_mask, const int *col_off, const uint8_t *fixed,
-                                 const double *r, double *t) {
+                                 const double *r, double *t, QAlg qa) {
   long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= count) return;
   int n = iface_nodes[p];
   int c = iface_of_node[n];
+  if (qa.q) {
+    const int ncol = col_off[c + 1] - col_off[c];
+    const double *qr = qa.q + qa.qoff[c] + (long long)3 * iface_slot[n] * ncol;
+    const double r0 = r[3LL * n], r1 = r[3LL * n + 1], r2 = r[3LL * n + 2];
+    for (int kk = 0; kk < ncol; ++kk) {
+      const double v = qr[kk] * r0 + qr[ncol + kk] * r1 + qr[2 * ncol + kk] * r2;
+      if (v != 0.0) atomicAdd(&t[col_off[c] + kk], v);
+    }
+    return;
+  }
   int nc = mortar_off[c + 1] - mortar_off[c];
   int cm = comp_mask[c], ncomp = __popc(cm);
   const double *et = eta + eta_off[c] + (long long)iface_slot[n] * nc;
@@ -367,11 +412,23 @@ __global__ void __launch_bounds__(256) k_prolong_grain(const long long *node_off
 __global__ void k_prolong_iface(const int *iface_nodes, const int *iface_of_node, long long count,
                                 const int *iface_slot, const int *mortar_off, const long long *eta_off,
                                 const double *eta, const int *comp_mask, const int *col_off, const uint8_t *fixed,
-                                const double *u, double *z) {
+                                const double *u, double *z, QAlg qa) {
   long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= count) return;
   int n = iface_nodes[p];
   int c = iface_of_node[n];
+  if (qa.q) {
+    const int ncol = col_off[c + 1] - col_off[c];
+    const double *qr = qa.q + qa.qoff[c] + (long long)3 * iface_slot[n] * ncol;
+    const double *uc = u + col_off[c];
+    for (int d = 0; d < 3; ++d) {
+      double sum = 0.0;
+      if (!fixed[3 * n + d])
+        for (int kk = 0; kk < ncol; ++kk) sum += qr[d * ncol + kk] * uc[kk];
+      z[3LL * n + d] = sum;
+    }
+    return;
+  }
   int nc = mortar_off[c + 1] - mortar_off[c];
   int cm = comp_mask[c], ncomp = __popc(cm);
   const double *et = eta + eta_off[c] + (long long)iface_slot[n] * nc;
@@ -391,16 +448,16 @@ __global__ void __launch_bounds__(256) k_restrict_grain8(const long long *node_o
                                                          const T *X, const int *gcol_off, const int *gcol,
                                                          const double *r, long long L, double *t, long long No,
                                                          int kc) {
-  __shared__ A rl[8][RCHUNK];
+  __shared__ A rl[8][RCHUNK8];
   const int g = blockIdx.y;
   const int N = nloc[g];
-  const int row0 = blockIdx.x * RCHUNK;
+  const int row0 = blockIdx.x * RCHUNK8;
   if (row0 >= N) return;
-  const int cnt = min(RCHUNK, N - row0);
+  const int cnt = min(RCHUNK8, N - row0);
   const int k = kg[g];
   const int *ln = lnodes + node_off[g];
-  for (int e = threadIdx.x; e < 8 * RCHUNK; e += blockDim.x) {
-    const int q = e / RCHUNK, rr = e % RCHUNK;
+  for (int e = threadIdx.x; e < 8 * RCHUNK8; e += blockDim.x) {
+    const int q = e / RCHUNK8, rr = e % RCHUNK8;
     A v = 0;
     if (q < kc && rr < cnt) {
       const int row = row0 + rr, o = row / 3, d = row - 3 * o;
@@ -463,6 +520,222 @@ __global__ void __launch_bounds__(256) k_prolong_grain8(const long long *node_of
   }
 }
 
+// ---- column-major BF16 panels of the BF16 form's apply.  Column a of grain g sits at Xc[cm_off[g] + a ld_g]
+// with ld_g = N_g rounded up to 8, so that every column starts on 16 bytes and a lane moves 8 rows (uint4) per
+// load; the padding rows hold zeros.
+__host__ __device__ inline int cm_ld(int n) { return (n + 7) & ~7; }
+
+// exact BF16 -> FP32 of the two halves of a 32-bit word
+__device__ __forceinline__ float bf_lo(uint32_t w) { return __uint_as_float(w << 16); }
+__device__ __forceinline__ float bf_hi(uint32_t w) { return __uint_as_float(w & 0xffff0000u); }
+
+__device__ __forceinline__ void bf8_to_f32(const uint4 v, float *x) {
+  x[0] = bf_lo(v.x), x[1] = bf_hi(v.x), x[2] = bf_lo(v.y), x[3] = bf_hi(v.y);
+  x[4] = bf_lo(v.z), x[5] = bf_hi(v.z), x[6] = bf_lo(v.w), x[7] = bf_hi(v.w);
+}
+
+// transpose-convert of the FP32 row-major panels (32 x 32 tiles through shared memory)
+__global__ void k_panel_bf16_cm(const int *nloc, const int *kg, const long long *panel_off, const long long *cm_off,
+                                const float *X, __nv_bfloat16 *Xc) {
+  __shared__ float tile[32][33];
+  const int g = blockIdx.z;
+  const int N = nloc[g], k = kg[g], ld = cm_ld(N);
+  const int r0 = blockIdx.x * 32, a0 = blockIdx.y * 32;
+  if (r0 >= ld || a0 >= k) return;
+  const float *Xg = X + panel_off[g];
+  __nv_bfloat16 *Cg = Xc + cm_off[g];
+  for (int i = threadIdx.y; i < 32; i += 8) {
+    const int row = r0 + i, a = a0 + threadIdx.x;
+    tile[i][threadIdx.x] = (row < N && a < k) ? Xg[(long long)row * k + a] : 0.f;
+  }
+  __syncthreads();
+  for (int j = threadIdx.y; j < 32; j += 8) {
+    const int a = a0 + j, row = r0 + threadIdx.x;
+    if (row < ld && a < k) Cg[(long long)a * ld + row] = __float2bfloat16_rn(tile[threadIdx.x][j]);
+  }
+}
+
+// Sums of 8 values over a warp (a butterfly that halves the values each lane carries at the first three levels:
+// 9 shuffles).  On return v[0] of lane l holds the sum of value 4 b4 + 2 b3 + b2 (b = the bits of l).
+__device__ __forceinline__ void warp_sum8(float *v, int lane) {
+#pragma unroll
+  for (int h = 0; h < 4; ++h) {
+    const bool up = lane & 16;
+    const float send = up ? v[h] : v[h + 4], keep = up ? v[h + 4] : v[h];
+    v[h] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
+  }
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    const bool up = lane & 8;
+    const float send = up ? v[h] : v[h + 2], keep = up ? v[h + 2] : v[h];
+    v[h] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
+  }
+  {
+    const bool up = lane & 4;
+    const float send = up ? v[0] : v[1], keep = up ? v[1] : v[0];
+    v[0] = keep + __shfl_xor_sync(0xffffffffu, send, 4);
+  }
+  v[0] += __shfl_xor_sync(0xffffffffu, v[0], 2);
+  v[0] += __shfl_xor_sync(0xffffffffu, v[0], 1);
+}
+
+constexpr int CM_ROWS = 2048;  // panel rows per CTA in the column-major restriction and prolongation (8 per thread)
+
+// restriction t_q[gcol] += sum over the grain's rows of X_g[row][a] r_q[row] on column-major BF16 panels:
+// CTA = (grain, 2,048 rows), lane = 8 consecutive rows whose residuals it keeps in registers, warps over the
+// columns.  MULTI = false: one vector, 8 columns per step (8 loads in flight); MULTI = true: kc <= 8 vectors at
+// stride L / No, one column per step.  The warp sums go to shared memory, then one atomic per column and vector.
+template <bool MULTI>
+__global__ void __launch_bounds__(256) k_restrict_grain_cm(const long long *node_off, const int *nloc,
+                                                           const int *lnodes, const int *kg, const long long *cm_off,
+                                                           const __nv_bfloat16 *Xc, const int *gcol_off,
+                                                           const int *gcol, const double *r, long long L, double *t,
+                                                           long long No, int kc) {
+  constexpr int KQ = MULTI ? 8 : 1;
+  __shared__ float colsum[KQ][512];
+  const int g = blockIdx.y;
+  const int N = nloc[g], ld = cm_ld(N), k = kg[g];
+  const int row0 = blockIdx.x * CM_ROWS;
+  if (row0 >= ld) return;
+  for (int e = threadIdx.x; e < KQ * 512; e += blockDim.x) colsum[e / 512][e % 512] = 0.f;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int *ln = lnodes + node_off[g];
+  const __nv_bfloat16 *Xg = Xc + cm_off[g];
+  // the 8 warps split the CTA's rows: warp w takes rows row0 + 256 w + 8 lane + [0, 8)
+  const int rs = row0 + 256 * wid + 8 * lane;
+  const bool live = rs < ld;
+  float rl[KQ][8];
+#pragma unroll
+  for (int q = 0; q < KQ; ++q)
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      float v = 0.f;
+      const int row = rs + j;
+      if (q < kc && row < N) {
+        const int o = row / 3, d = row - 3 * o;
+        v = (float)r[q * L + 3LL * ln[o] + d];
+      }
+      rl[q][j] = v;
+    }
+  __syncthreads();
+  const int sel = ((lane >> 4) & 1) * 4 + ((lane >> 3) & 1) * 2 + ((lane >> 2) & 1);
+  if (!MULTI) {
+    for (int a0 = 0; a0 < k; a0 += 8) {
+      float acc[8];
+      uint4 xv[8];
+#pragma unroll
+      for (int c = 0; c < 8; ++c)
+        xv[c] = (live && a0 + c < k) ? __ldg(reinterpret_cast<const uint4 *>(Xg + (long long)(a0 + c) * ld + rs))
+                                     : make_uint4(0, 0, 0, 0);
+#pragma unroll
+      for (int c = 0; c < 8; ++c) {
+        float x[8];
+        bf8_to_f32(xv[c], x);
+        float s = 0.f;
+#pragma unroll
+        for (int j = 0; j < 8; ++j) s += x[j] * rl[0][j];
+        acc[c] = s;
+      }
+      warp_sum8(acc, lane);
+      if ((lane & 3) == 0 && a0 + sel < k) atomicAdd(&colsum[0][a0 + sel], acc[0]);
+    }
+  } else {
+    for (int a = 0; a < k; ++a) {
+      const uint4 xv = live ? __ldg(reinterpret_cast<const uint4 *>(Xg + (long long)a * ld + rs))
+                            : make_uint4(0, 0, 0, 0);
+      float x[8], acc[8];
+      bf8_to_f32(xv, x);
+#pragma unroll
+      for (int q = 0; q < KQ; ++q) {
+        float s = 0.f;
+#pragma unroll
+        for (int j = 0; j < 8; ++j) s += x[j] * rl[q][j];
+        acc[q] = s;
+      }
+      warp_sum8(acc, lane);
+      if ((lane & 3) == 0 && sel < kc) atomicAdd(&colsum[sel][a], acc[0]);
+    }
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < KQ * k; e += blockDim.x) {
+    const int q = e / k, a = e % k;
+    if (q < kc) {
+      const float v = colsum[q][a];
+      if (v != 0.f) atomicAdd(&t[q * No + gcol[gcol_off[g] + a]], (double)v);
+    }
+  }
+}
+
+// prolongation z_q[row] = X_g[row][.] u_q[K_g] on column-major BF16 panels: thread = 8 consecutive rows (one
+// 16-byte load per column, coalesced over the warp), the grain's coarse values in shared memory; kc <= KQ vectors
+template <bool MULTI>
+__global__ void __launch_bounds__(256) k_prolong_grain_cm(const long long *node_off, const int *nloc,
+                                                          const int *lnodes, const int *kg, const long long *cm_off,
+                                                          const __nv_bfloat16 *Xc, const int *gcol_off,
+                                                          const int *gcol, const double *u, long long No, double *z,
+                                                          long long L, int kc) {
+  constexpr int KQ = MULTI ? 8 : 1;
+  __shared__ float ul[KQ][512];
+  const int g = blockIdx.y;
+  const int N = nloc[g], ld = cm_ld(N), k = kg[g];
+  const int row0 = blockIdx.x * CM_ROWS;
+  if (row0 >= ld) return;
+  for (int e = threadIdx.x; e < KQ * k; e += blockDim.x) {
+    const int q = e / k, a = e % k;
+    ul[q][a] = q < kc ? (float)u[q * No + gcol[gcol_off[g] + a]] : 0.f;
+  }
+  __syncthreads();
+  const int rs = row0 + 8 * threadIdx.x;
+  if (rs >= ld) return;
+  const __nv_bfloat16 *xr = Xc + cm_off[g] + rs;
+  float acc[KQ][8];
+#pragma unroll
+  for (int q = 0; q < KQ; ++q)
+#pragma unroll
+    for (int j = 0; j < 8; ++j) acc[q][j] = 0.f;
+  int a = 0;
+  if (!MULTI) {
+    for (; a + 3 < k; a += 4) {
+      uint4 xv[4];
+#pragma unroll
+      for (int c = 0; c < 4; ++c) xv[c] = __ldg(reinterpret_cast<const uint4 *>(xr + (long long)(a + c) * ld));
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        float x[8];
+        bf8_to_f32(xv[c], x);
+        const float uc = ul[0][a + c];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) acc[0][j] += x[j] * uc;
+      }
+    }
+  }
+  for (; a < k; ++a) {
+    float x[8];
+    bf8_to_f32(__ldg(reinterpret_cast<const uint4 *>(xr + (long long)a * ld)), x);
+#pragma unroll
+    for (int q = 0; q < KQ; ++q) {
+      const float uq = ul[q][a];
+#pragma unroll
+      for (int j = 0; j < 8; ++j) acc[q][j] += x[j] * uq;
+    }
+  }
+  const int *ln = lnodes + node_off[g];
+#pragma unroll
+  for (int j = 0; j < 8; ++j) {
+    const int row = rs + j;
+    if (row >= N) break;
+    const int o = row / 3, d = row - 3 * o;
+    const long long dst = 3LL * ln[o] + d;
+#pragma unroll
+    for (int q = 0; q < KQ; ++q)
+      if (q < kc) z[q * L + dst] = (double)acc[q][j];
+  }
+}
+
+QAlg qalg(const hplmm_ctx *c) {
+  return QAlg{c->opt.mortar_kind == HPLMM_MORTAR_ALGEBRAIC ? c->qblk.p : nullptr, c->qoff.p, c->col_off.p};
+}
+
 template <typename T>
 Buf<T> &gal_buf(hplmm_ctx *c);
 template <>
@@ -502,7 +775,7 @@ void galerkin(hplmm_ctx *c, const Buf<int> &gbox, const std::vector<long long> &
                                      c->iface_of_node.p, c->iface_slot.p, c->fixed.p, c->grains.box.p,
                                      c->grains.node_off.p, c->grains.lmap.p, c->panel_off.p, panel_ptr<T>(c),
                                      c->mortar_off.p, c->eta_off.p, c->eta.p, c->comp_mask.p, c->gi_off.p,
-                                     c->gi_iface.p, c->gi_colbase.p, g0, base, P);
+                                     c->gi_iface.p, c->gi_colbase.p, g0, base, P, qalg(c));
     HP_CHECK_LAUNCH();
     dim3 gy(maxvol, g1 - g0);
     k_gal_Y<T><<<gy, 128, 0, s>>>(gbox.p, gal_off.p, c->kg.p, c->vgrain.p, c->mask.p, c->E.p, c->nx, c->ny, c->nz,
@@ -565,13 +838,14 @@ void coarse_rhs(hplmm_ctx *c, const double *b_corr) {
                                              c->row_ptr.p, c->col.p, c->val64.p, c->iface_of_node.p, c->iface_slot.p,
                                              c->iface_pair.p, c->mortar_off.p, c->eta_off.p, c->eta.p,
                                              c->comp_mask.p, c->gi_off.p, c->gi_iface.p, c->gi_colbase.p, c->kg.p,
-                                             c->corr_col.p, c->panel_off.p, b_corr, c->opt.strict_two_grain, c->X64.p);
+                                             c->corr_col.p, c->panel_off.p, b_corr, c->opt.strict_two_grain, c->X64.p,
+                                             qalg(c));
   else
     k_basis_rhs<float><<<grid, 128, 0, s>>>(G, c->grains.node_off.p, c->grains.n.p, c->grains.lnodes.p, c->row_ptr.p,
                                             c->col.p, c->val64.p, c->iface_of_node.p, c->iface_slot.p,
                                             c->iface_pair.p, c->mortar_off.p, c->eta_off.p, c->eta.p, c->comp_mask.p,
                                             c->gi_off.p, c->gi_iface.p, c->gi_colbase.p, c->kg.p, c->corr_col.p,
-                                            c->panel_off.p, b_corr, c->opt.strict_two_grain, c->X32.p);
+                                            c->panel_off.p, b_corr, c->opt.strict_two_grain, c->X32.p, qalg(c));
   HP_CHECK_LAUNCH();
   }
   if (!f64 && c->opt.basis_solver == HPLMM_BASIS_DIRECT && c->opt.keep_basis_rhs) {
@@ -602,10 +876,23 @@ void coarse_finish(hplmm_ctx *c) {
   bool f64 = c->opt.local_prec == HPLMM_FP64;
   const std::vector<long long> &poff = c->h_panel_off;
   if (!f64 && c->opt.apply_prec == HPLMM_BF16) {
-    c->X16.alloc(std::max<long long>(poff[G], 1));
-    to_bf16(c->X32.p, c->X16.p, poff[G], s);
+    // the apply's BF16 panels, column-major per grain with 16-byte aligned columns
+    std::vector<long long> coff(G + 1, 0);
+    int maxld = 8, maxk = 1;
+    for (int g = 0; g < G; ++g) {
+      coff[g + 1] = coff[g] + (long long)cm_ld(c->grains.h_n[g]) * c->h_kg[g];
+      maxld = std::max(maxld, cm_ld(c->grains.h_n[g]));
+      maxk = std::max(maxk, c->h_kg[g]);
+    }
+    c->h_panel_off_cm = coff;
+    c->panel_off_cm.upload(coff, s);
+    c->X16.alloc(std::max<long long>(coff[G], 8));
+    k_panel_bf16_cm<<<dim3((maxld + 31) / 32, (maxk + 31) / 32, G), dim3(32, 8), 0, s>>>(
+        c->grains.n.p, c->kg.p, c->panel_off.p, c->panel_off_cm.p, c->X32.p, c->X16.p);
+    HP_CHECK_LAUNCH();
   } else {
     c->X16.release();
+    c->panel_off_cm.release();
   }
 
   // global column of every local panel column
@@ -708,7 +995,7 @@ void coarse_apply(hplmm_ctx *c, const double *r_pad, double *z_pad) {
   if (c->n_iface_nodes > 0) {
     k_restrict_iface<<<grid_for(c->n_iface_nodes, 128), 128, 0, s>>>(
         c->iface_nodes.p, c->iface_of_node.p, c->n_iface_nodes, c->iface_slot.p, c->mortar_off.p, c->eta_off.p,
-        c->eta.p, c->comp_mask.p, c->col_off.p, c->fixed.p, r_pad, t);
+        c->eta.p, c->comp_mask.p, c->col_off.p, c->fixed.p, r_pad, t, qalg(c));
     HP_CHECK_LAUNCH();
   }
   int nmax = 1;
@@ -720,9 +1007,9 @@ void coarse_apply(hplmm_ctx *c, const double *r_pad, double *z_pad) {
                                                         c->kg.p, c->panel_off.p, c->X64.p, c->gcol_off.p, c->gcol.p,
                                                         r_pad, t);
   else if (b16)
-    k_restrict_grain<__nv_bfloat16, float><<<gr, 256, 0, s>>>(c->grains.node_off.p, c->grains.n.p,
-                                                              c->grains.lnodes.p, c->kg.p, c->panel_off.p, c->X16.p,
-                                                              c->gcol_off.p, c->gcol.p, r_pad, t);
+    k_restrict_grain_cm<false><<<dim3((cm_ld(nmax) + CM_ROWS - 1) / CM_ROWS, G), 256, 0, s>>>(
+        c->grains.node_off.p, c->grains.n.p, c->grains.lnodes.p, c->kg.p, c->panel_off_cm.p, c->X16.p,
+        c->gcol_off.p, c->gcol.p, r_pad, 0, t, 0, 1);
   else
     k_restrict_grain<float, float><<<gr, 256, 0, s>>>(c->grains.node_off.p, c->grains.n.p, c->grains.lnodes.p,
                                                       c->kg.p, c->panel_off.p, c->X32.p, c->gcol_off.p, c->gcol.p,
@@ -738,9 +1025,9 @@ void coarse_apply(hplmm_ctx *c, const double *r_pad, double *z_pad) {
                                                        c->kg.p, c->panel_off.p, c->X64.p, c->gcol_off.p, c->gcol.p, t,
                                                        z_pad);
   else if (b16)
-    k_prolong_grain<__nv_bfloat16, float><<<gp, 256, 0, s>>>(c->grains.node_off.p, c->grains.n.p,
-                                                             c->grains.lnodes.p, c->kg.p, c->panel_off.p, c->X16.p,
-                                                             c->gcol_off.p, c->gcol.p, t, z_pad);
+    k_prolong_grain_cm<false><<<dim3((cm_ld(nmax) + CM_ROWS - 1) / CM_ROWS, G), 256, 0, s>>>(
+        c->grains.node_off.p, c->grains.n.p, c->grains.lnodes.p, c->kg.p, c->panel_off_cm.p, c->X16.p,
+        c->gcol_off.p, c->gcol.p, t, 0, z_pad, 0, 1);
   else
     k_prolong_grain<float, float><<<gp, 256, 0, s>>>(c->grains.node_off.p, c->grains.n.p, c->grains.lnodes.p,
                                                      c->kg.p, c->panel_off.p, c->X32.p, c->gcol_off.p, c->gcol.p, t,
@@ -749,7 +1036,7 @@ void coarse_apply(hplmm_ctx *c, const double *r_pad, double *z_pad) {
   if (c->n_iface_nodes > 0) {
     k_prolong_iface<<<grid_for(c->n_iface_nodes, 128), 128, 0, s>>>(
         c->iface_nodes.p, c->iface_of_node.p, c->n_iface_nodes, c->iface_slot.p, c->mortar_off.p, c->eta_off.p,
-        c->eta.p, c->comp_mask.p, c->col_off.p, c->fixed.p, t, z_pad);
+        c->eta.p, c->comp_mask.p, c->col_off.p, c->fixed.p, t, z_pad, qalg(c));
     HP_CHECK_LAUNCH();
   }
 }
@@ -773,16 +1060,15 @@ void coarse_apply_multi(hplmm_ctx *c, const double *R, double *Z, int k) {
   for (int g = 0; g < G; ++g) nmax = std::max(nmax, c->grains.h_n[g]);
   for (int q0 = 0; q0 < k; q0 += 8) {
     const int kc = std::min(8, k - q0);
-    dim3 gr((nmax + RCHUNK - 1) / RCHUNK, G);
+    dim3 gr((nmax + RCHUNK8 - 1) / RCHUNK8, G);
     if (f64)
       k_restrict_grain8<double, double><<<gr, 256, 0, s>>>(c->grains.node_off.p, c->grains.n.p, c->grains.lnodes.p,
                                                            c->kg.p, c->panel_off.p, c->X64.p, c->gcol_off.p,
                                                            c->gcol.p, R + q0 * L, L, t + q0 * No, No, kc);
     else if (b16)
-      k_restrict_grain8<__nv_bfloat16, float><<<gr, 256, 0, s>>>(c->grains.node_off.p, c->grains.n.p,
-                                                                 c->grains.lnodes.p, c->kg.p, c->panel_off.p,
-                                                                 c->X16.p, c->gcol_off.p, c->gcol.p, R + q0 * L, L,
-                                                                 t + q0 * No, No, kc);
+      k_restrict_grain_cm<true><<<dim3((cm_ld(nmax) + CM_ROWS - 1) / CM_ROWS, G), 256, 0, s>>>(
+          c->grains.node_off.p, c->grains.n.p, c->grains.lnodes.p, c->kg.p, c->panel_off_cm.p, c->X16.p,
+          c->gcol_off.p, c->gcol.p, R + q0 * L, L, t + q0 * No, No, kc);
     else
       k_restrict_grain8<float, float><<<gr, 256, 0, s>>>(c->grains.node_off.p, c->grains.n.p, c->grains.lnodes.p,
                                                          c->kg.p, c->panel_off.p, c->X32.p, c->gcol_off.p, c->gcol.p,
@@ -793,7 +1079,7 @@ void coarse_apply_multi(hplmm_ctx *c, const double *R, double *Z, int k) {
     if (c->n_iface_nodes > 0) {
       k_restrict_iface<<<grid_for(c->n_iface_nodes, 128), 128, 0, s>>>(
           c->iface_nodes.p, c->iface_of_node.p, c->n_iface_nodes, c->iface_slot.p, c->mortar_off.p, c->eta_off.p,
-          c->eta.p, c->comp_mask.p, c->col_off.p, c->fixed.p, R + q * L, t + q * No);
+          c->eta.p, c->comp_mask.p, c->col_off.p, c->fixed.p, R + q * L, t + q * No, qalg(c));
       HP_CHECK_LAUNCH();
     }
     cf_solve(c, t + q * No, c->w_coarse_y.p, u + q * No);
@@ -806,10 +1092,9 @@ void coarse_apply_multi(hplmm_ctx *c, const double *R, double *Z, int k) {
                                                           c->kg.p, c->panel_off.p, c->X64.p, c->gcol_off.p, c->gcol.p,
                                                           u + q0 * No, No, Z + q0 * L, L, kc);
     else if (b16)
-      k_prolong_grain8<__nv_bfloat16, float><<<gp, 256, 0, s>>>(c->grains.node_off.p, c->grains.n.p,
-                                                                c->grains.lnodes.p, c->kg.p, c->panel_off.p, c->X16.p,
-                                                                c->gcol_off.p, c->gcol.p, u + q0 * No, No, Z + q0 * L,
-                                                                L, kc);
+      k_prolong_grain_cm<true><<<dim3((cm_ld(nmax) + CM_ROWS - 1) / CM_ROWS, G), 256, 0, s>>>(
+          c->grains.node_off.p, c->grains.n.p, c->grains.lnodes.p, c->kg.p, c->panel_off_cm.p, c->X16.p,
+          c->gcol_off.p, c->gcol.p, u + q0 * No, No, Z + q0 * L, L, kc);
     else
       k_prolong_grain8<float, float><<<gp, 256, 0, s>>>(c->grains.node_off.p, c->grains.n.p, c->grains.lnodes.p,
                                                         c->kg.p, c->panel_off.p, c->X32.p, c->gcol_off.p, c->gcol.p,
@@ -820,7 +1105,7 @@ void coarse_apply_multi(hplmm_ctx *c, const double *R, double *Z, int k) {
     for (int q = 0; q < k; ++q) {
       k_prolong_iface<<<grid_for(c->n_iface_nodes, 128), 128, 0, s>>>(
           c->iface_nodes.p, c->iface_of_node.p, c->n_iface_nodes, c->iface_slot.p, c->mortar_off.p, c->eta_off.p,
-          c->eta.p, c->comp_mask.p, c->col_off.p, c->fixed.p, u + q * No, Z + q * L);
+          c->eta.p, c->comp_mask.p, c->col_off.p, c->fixed.p, u + q * No, Z + q * L, qalg(c));
       HP_CHECK_LAUNCH();
     }
 }
@@ -848,7 +1133,7 @@ void prolong_column(hplmm_ctx *c, long long col, double *out_pad) {
   if (c->n_iface_nodes > 0) {
     k_prolong_iface<<<grid_for(c->n_iface_nodes, 128), 128, 0, s>>>(
         c->iface_nodes.p, c->iface_of_node.p, c->n_iface_nodes, c->iface_slot.p, c->mortar_off.p, c->eta_off.p,
-        c->eta.p, c->comp_mask.p, c->col_off.p, c->fixed.p, u, out_pad);
+        c->eta.p, c->comp_mask.p, c->col_off.p, c->fixed.p, u, out_pad, qalg(c));
     HP_CHECK_LAUNCH();
   }
   HP_CUDA(cudaStreamSynchronize(s));

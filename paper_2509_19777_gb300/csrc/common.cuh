@@ -143,6 +143,7 @@ struct LocalSet {
   int tuned_ring_rows = 0;   // far ring rows (0 = largest that fits) and diagonal-chunk stages
   int tuned_c0_stages = 0;
   int tuned_cluster = 0;     // CTAs per problem of the smoother solve (0 = default: 2 when the set is small)
+  int tuned_bulk = 0;        // bulk warps per CTA of the smoother solve (0 = 8; with 4, two CTAs share an SM)
   hplmm_prec prec = HPLMM_FP64;
 };
 
@@ -284,6 +285,8 @@ struct hplmm_ctx {
   hp::Buf<int> kg;
   hp::Buf<long long> panel_off;
   std::vector<int> h_corr_col;     // coarse column of grain g's correction, or -1
+  std::vector<std::vector<int>> h_glists;  // per grain: its coupled interfaces (ascending)
+  std::vector<int> h_grain_hasb;   // per grain: b^g != 0 (a correction column is kept)
   hp::Buf<int> corr_col;
 
   // ---- mortars (Section 3.3)
@@ -300,12 +303,20 @@ struct hplmm_ctx {
 
   // ---- local problems
   hp::LocalSet grains, contacts;
+  hp::LocalSet ifsets;             // algebraic mortars: the interfaces as local problems on their own nodes
+  hp::Buf<int> mslot_of_node;      // algebraic mortars: global mortar slot of a node, or -1
+  hp::Buf<int> mfree;              // per mortar slot: bit gamma set when the mortar node's DOF gamma is free
+  hp::Buf<int> mcol;               // per mortar slot: its first column within its interface
+  hp::Buf<double> qblk;            // per interface: Q^o block, rows (slot, component) x its columns
+  hp::Buf<long long> qoff;         // offsets of the blocks
   hp::Buf<float> stage32;          // FP32 chunk of the staged BF16 set-up
 
   // ---- coarse space (Section 4.2)
   hp::Buf<double> X64;             // basis panels X_g (local DOF rows x k_g), FP64
   hp::Buf<float> X32;              // FP32 copy/compute
-  hp::Buf<__nv_bfloat16> X16;      // BF16 copy of X32 for the restriction/prolongation of the BF16 form
+  hp::Buf<__nv_bfloat16> X16;      // BF16 copy of X32 for the apply of the BF16 form, column-major per grain
+  hp::Buf<long long> panel_off_cm;  // offsets of the column-major BF16 panels (leading dimension N_g rounded to 8)
+  std::vector<long long> h_panel_off_cm;
   hp::Buf<double> Ao;              // N^o x N^o dense copy, kept only when N^o <= dense_coarse_max
   bool dense_ao = false;
   hp::Buf<double> gal64;           // Galerkin work: P and Y on the grains' node boxes (FP64 form)
@@ -407,8 +418,10 @@ void gather_free(hplmm_ctx *c, const double *pad, double *dof);
 void scatter_free(hplmm_ctx *c, const double *dof, double *pad);
 // maps.cu
 void check_anchored(hplmm_ctx *c);  // throws HPLMM_ERR_SINGULAR when a solid part has no prescribed displacement
+void layout_columns(hplmm_ctx *c);  // grain panel columns and coarse columns from the interfaces' column counts
 void build_maps(hplmm_ctx *c, const int32_t *partition);
 void build_mortars(hplmm_ctx *c);
+void build_algebraic_mortars(hplmm_ctx *c);  // local.cu: Eq. algebra mortars (options.mortar_kind = 1)
 void compute_W(hplmm_ctx *c, int64_t *W);
 // local.cu
 void build_local_sets(hplmm_ctx *c);

@@ -1262,8 +1262,8 @@ template <typename T, int n> __device__ __forceinline__ void ld_vec(const T *p, 
   }
 }
 
-template <typename S, int NB, int CL>
-__global__ void __launch_bounds__(WS_THREADS) k_band_solve_ws(
+template <typename S, int NB, int CL, int NBW>
+__global__ void __launch_bounds__((3 + NBW) * 32, NBW == WS_BULK_WARPS ? 1 : 2) k_band_solve_ws(
     int count, const int *nloc, const int *bwv, const long long *band_off, const long long *vec_off,
     const int *gidx, const S *band, const double *r, double *z, typename ComputeOf<S>::type *yscr, int atomic,
     int ring_rows, int chunk_rows, int c0_stages, int wmask, int *status, long long wait_cycles) {
@@ -1285,8 +1285,8 @@ __global__ void __launch_bounds__(WS_THREADS) k_band_solve_ws(
   __shared__ T red1[4][NB];
   // rank 1: bulk step done (every bulk warp) for its pusher warp, and its per-warp far sums (4 panels deep)
   __shared__ __align__(8) uint64_t r1done[4];
-  __shared__ T red_r1[4][WS_BULK_WARPS][NB];
-  __shared__ T red[2][WS_BULK_WARPS][NB];
+  __shared__ T red_r1[4][NBW][NB];
+  __shared__ T red[2][NBW][NB];
   __shared__ __align__(16) T lbuf[NB];  // leader: the panel's right-hand side, broadcast to its lanes
   __shared__ volatile int s_abort;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -1337,7 +1337,7 @@ __global__ void __launch_bounds__(WS_THREADS) k_band_solve_ws(
   if (threadIdx.x == 0) {
     for (int i = 0; i < WS_NSTG; ++i) {
       mbar_init(&full_far[i], 1);
-      mbar_init(&empty_far[i], WS_BULK_WARPS);
+      mbar_init(&empty_far[i], NBW);
     }
     for (int i = 0; i < c0_stages; ++i) {
       mbar_init(&full_c0[i], 32);
@@ -1347,18 +1347,18 @@ __global__ void __launch_bounds__(WS_THREADS) k_band_solve_ws(
       // rank 0: the leader's local arrival; rank 1: its armer's arrival plus the leader's st.async bytes
       mbar_init(&ydone[i], 1);
       mbar_init(&urg[i], 1);
-      mbar_init(&bdone[i], WS_BULK_WARPS);
+      mbar_init(&bdone[i], NBW);
       mbar_init(&pdone[i], 1);                   // rank 0: its armer's arrival plus the pusher's st.async bytes
-      mbar_init(&r1done[i], WS_BULK_WARPS);
+      mbar_init(&r1done[i], NBW);
     }
     s_abort = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (rank == 0) {
     // initial window: rows 0 .. min(W, N) - 1 of the right-hand side (slots of rows >= N are never read)
-    for (int l = threadIdx.x; l < min(W, N); l += WS_THREADS) v[l] = (T)r[gi[l]];
+    for (int l = threadIdx.x; l < min(W, N); l += ((3 + NBW) * 32)) v[l] = (T)r[gi[l]];
   } else {
-    for (int l = threadIdx.x; l < W; l += WS_THREADS) v[l] = (T)0;  // rank 1 accumulates its own updates
+    for (int l = threadIdx.x; l < W; l += ((3 + NBW) * 32)) v[l] = (T)0;  // rank 1 accumulates its own updates
   }
   if constexpr (CL == 2)
     cluster_sync_all();  // barriers initialised and windows set in both CTAs before any remote access
@@ -1566,7 +1566,7 @@ __global__ void __launch_bounds__(WS_THREADS) k_band_solve_ws(
           T far = 0;
           if (p + 1 < np) {
 #pragma unroll
-            for (int w = 0; w < WS_BULK_WARPS; ++w) far += red[p & 1][w][i];
+            for (int w = 0; w < NBW; ++w) far += red[p & 1][w][i];
           }
           if (CL == 2 && p <= np - 3) far += red1[p & 3][i];
           // near: L_{p+1,p}^T x_{p+1} (column i of the near block; rows past the matrix contribute nothing)
@@ -1650,7 +1650,7 @@ __global__ void __launch_bounds__(WS_THREADS) k_band_solve_ws(
         dst = peer_red1 + (uint32_t)((q & 3) * NB * sizeof(T));
         if (lane < NB) {
 #pragma unroll
-          for (int w = 0; w < WS_BULK_WARPS; ++w) val += red_r1[q & 3][w][lane];
+          for (int w = 0; w < NBW; ++w) val += red_r1[q & 3][w][lane];
         }
       }
       if (lane < NB) st_async_peer(dst + (uint32_t)(lane * sizeof(T)), val, peer_pdone + 8u * (s & 3));
@@ -1697,11 +1697,11 @@ __global__ void __launch_bounds__(WS_THREADS) k_band_solve_ws(
           const int slot = n % WS_NSTG;
           if (!fail && !mbar_wait_bounded(&full_far[slot], (uint32_t)((n / WS_NSTG) & 1), &s_abort, wait_cycles)) fail = 1;
           if (!fail) {
-            // two rows per thread per pass (t and t + WS_BULK_THREADS); the choice between the one- and the
+            // two rows per thread per pass (t and t + (NBW * 32)); the choice between the one- and the
             // two-row code is made per warp (a lane without a second row re-reads its first row, with no
             // update or a zero weight), so that no warp runs both
-            for (int t = tb; t < rows; t += 2 * WS_BULK_THREADS) {
-              const int t2 = t + WS_BULK_THREADS;
+            for (int t = tb; t < rows; t += 2 * (NBW * 32)) {
+              const int t2 = t + (NBW * 32);
               const bool two = t2 < rows;
               const bool warp_two = __any_sync(__activemask(), two);
               int rs = pos + t, rs2 = pos + t2;
@@ -2390,9 +2390,11 @@ void smoother_apply(hplmm_ctx *c, LocalSet &S, const double *r_pad, double *z_pa
   // depths: the tuner's choice when there is one, else 3 diagonal stages, whole-step chunks and the largest
   // ring
   const int c0s = S.tuned_c0_stages > 0 ? S.tuned_c0_stages : 3;
+  // bulk warps per CTA: 8 (one CTA per SM), or 4 with the ring sized for two CTAs per SM (one-CTA problems)
+  const int nbw = (cl == 1 && S.tuned_bulk == 4) ? 4 : WS_BULK_WARPS;
   auto go = [&](auto kern, const auto *band, auto *ys) {
     const SmemBudget bud = smem_budget(kern);
-    int ring = ring_rows_for(pl, c0s, bud.one);
+    int ring = ring_rows_for(pl, c0s, nbw == WS_BULK_WARPS ? bud.one : bud.pair);
     if (S.tuned_ring_rows > 0) ring = std::min(ring, S.tuned_ring_rows);
     HP_REQUIRE(ring >= 64, HPLMM_ERR_INVALID,
                "local problem too large for the smoother (window of " + std::to_string(pl.W) + " rows)");
@@ -2401,7 +2403,7 @@ void smoother_apply(hplmm_ctx *c, LocalSet &S, const double *r_pad, double *z_pa
     HP_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)(S.count * cl));
-    cfg.blockDim = dim3(WS_THREADS);
+    cfg.blockDim = dim3((unsigned)((3 + nbw) * 32));
     cfg.dynamicSmemBytes = smem;
     cfg.stream = s;
     cudaLaunchAttribute at[1];
@@ -2422,9 +2424,11 @@ void smoother_apply(hplmm_ctx *c, LocalSet &S, const double *r_pad, double *z_pa
     using ST = decltype(tag);
     constexpr int NBv = decltype(nb)::value;
     if (cl == 2)
-      go(k_band_solve_ws<ST, NBv, 2>, band, ys);
+      go(k_band_solve_ws<ST, NBv, 2, WS_BULK_WARPS>, band, ys);
+    else if (nbw == 4)
+      go(k_band_solve_ws<ST, NBv, 1, 4>, band, ys);
     else
-      go(k_band_solve_ws<ST, NBv, 1>, band, ys);
+      go(k_band_solve_ws<ST, NBv, 1, WS_BULK_WARPS>, band, ys);
   };
   if (S.prec == HPLMM_FP64) {
     pick(double{}, std::integral_constant<int, 16>{}, (const double *)S.band64.p, S.yscr.p);
@@ -2451,13 +2455,13 @@ struct TuneKey {
 };
 std::mutex g_tune_mu;
 struct TuneChoice {
-  int chunk_rows, ring_rows, c0_stages, cluster;
+  int chunk_rows, ring_rows, c0_stages, cluster, bulk;
 };
 std::map<TuneKey, TuneChoice> g_tune_cache;
 }  // namespace
 
 static void tune_set(hplmm_ctx *c, LocalSet &S, bool atomic) {
-  S.tuned_chunk_rows = S.tuned_ring_rows = S.tuned_c0_stages = S.tuned_cluster = 0;
+  S.tuned_chunk_rows = S.tuned_ring_rows = S.tuned_c0_stages = S.tuned_cluster = S.tuned_bulk = 0;
   if (S.count == 0) return;
   TuneKey key{S.count, 0, 0, (int)S.prec + (S.apply_bf16 ? 8 : 0) + 16 * c->opt.smoother_ctas};
   for (int k = 0; k < S.count; ++k) {
@@ -2472,6 +2476,7 @@ static void tune_set(hplmm_ctx *c, LocalSet &S, bool atomic) {
       S.tuned_ring_rows = it->second.ring_rows;
       S.tuned_c0_stages = it->second.c0_stages;
       S.tuned_cluster = it->second.cluster;
+      S.tuned_bulk = it->second.bulk;
       return;
     }
   }
@@ -2483,23 +2488,34 @@ static void tune_set(hplmm_ctx *c, LocalSet &S, bool atomic) {
   const bool prof = c->opt.profile;
   c->opt.profile = 0;  // tuning launches are not part of any phase
   float best = 1e30f;
-  TuneChoice bc{0, 0, 0, 0};
-  // budgets of the FP32 one-CTA kernel (the static shared memory of every instantiation is about the same;
+  TuneChoice bc{0, 0, 0, 0, 0};
+  // budgets of the FP32 one-CTA kernels (the static shared memory of every instantiation is about the same;
   // smoother_apply clamps the ring to the launched kernel's own budget)
-  const SmemBudget bud = S.prec == HPLMM_FP64 ? smem_budget(k_band_solve_ws<double, 16, 1>)
-                                              : smem_budget(k_band_solve_ws<float, 32, 1>);
-  for (int cl : {1, 2})
+  const SmemBudget bud = S.prec == HPLMM_FP64 ? smem_budget(k_band_solve_ws<double, 16, 1, WS_BULK_WARPS>)
+                                              : smem_budget(k_band_solve_ws<float, 32, 1, WS_BULK_WARPS>);
+  const SmemBudget bud4 = S.prec == HPLMM_FP64 ? smem_budget(k_band_solve_ws<double, 16, 1, 4>)
+                                               : smem_budget(k_band_solve_ws<float, 32, 1, 4>);
+  // plans: (CTAs per problem, bulk warps, shared-memory budget); the 4-warp kernel only with the two-per-SM
+  // budget, which is what it is for
+  struct Form {
+    int cl, nbw;
+    size_t budget;
+  };
+  const Form forms[] = {{1, WS_BULK_WARPS, bud.one}, {1, WS_BULK_WARPS, bud.pair}, {1, 4, bud4.pair},
+                        {2, WS_BULK_WARPS, bud.one}, {2, WS_BULK_WARPS, bud.pair}};
+  for (const Form &f : forms)
    for (int chunk : chunk_choices(S))
-    if (c->opt.smoother_ctas == 0 || c->opt.smoother_ctas == cl)
-    for (int c0d = 2; c0d <= 4; ++c0d)
-      for (size_t budget : {bud.one, bud.pair}) {
-        const int ring = ring_rows_for(pl, c0d, budget);
+    if (c->opt.smoother_ctas == 0 || c->opt.smoother_ctas == f.cl)
+    for (int c0d = 2; c0d <= 4; ++c0d) {
+        const int cl = f.cl;
+        const int ring = ring_rows_for(pl, c0d, f.budget);
         const int cr = std::min(chunk, ring);
         if (cr < 64) continue;
         S.tuned_chunk_rows = cr;
         S.tuned_ring_rows = ring;
         S.tuned_c0_stages = c0d;
         S.tuned_cluster = cl;
+        S.tuned_bulk = f.nbw;
         smoother_apply(c, S, c->b_pad.p, c->w_zz.p, atomic);  // warm-up
         HP_CUDA(cudaEventRecord(e0, s));
         for (int rep = 0; rep < 3; ++rep) smoother_apply(c, S, c->b_pad.p, c->w_zz.p, atomic);
@@ -2509,12 +2525,12 @@ static void tune_set(hplmm_ctx *c, LocalSet &S, bool atomic) {
         HP_CUDA(cudaEventElapsedTime(&ms, e0, e1));
         if (c->opt.verbose)
           fprintf(stderr,
-                  "[hplmm] tuner trial: %d problems, %d CTA(s) each, chunk %d rows, ring %d rows, diagonal %d: "
-                  "%.3f ms\n",
-                  S.count, cl, cr, ring, c0d, ms / 3);
+                  "[hplmm] tuner trial: %d problems, %d CTA(s) each, %d bulk warps, chunk %d rows, ring %d rows, "
+                  "diagonal %d: %.3f ms\n",
+                  S.count, cl, f.nbw, cr, ring, c0d, ms / 3);
         if (ms < best) {
           best = ms;
-          bc = {cr, ring, c0d, cl};
+          bc = {cr, ring, c0d, cl, f.nbw};
         }
       }
   c->opt.profile = prof;
@@ -2524,11 +2540,12 @@ static void tune_set(hplmm_ctx *c, LocalSet &S, bool atomic) {
   S.tuned_ring_rows = bc.ring_rows;
   S.tuned_c0_stages = bc.c0_stages;
   S.tuned_cluster = bc.cluster;
+  S.tuned_bulk = bc.bulk;
   if (c->opt.verbose)
     fprintf(stderr,
-            "[hplmm] tuner: %d problems (n<=%d, bw<=%d): %d CTA(s) each, chunk %d rows, ring %d rows, diagonal "
-            "stages %d, %.3f ms\n",
-            S.count, key.nmax, key.bwmax, bc.cluster, bc.chunk_rows, bc.ring_rows, bc.c0_stages, best / 3);
+            "[hplmm] tuner: %d problems (n<=%d, bw<=%d): %d CTA(s) each, %d bulk warps, chunk %d rows, ring %d "
+            "rows, diagonal stages %d, %.3f ms\n",
+            S.count, key.nmax, key.bwmax, bc.cluster, bc.bulk, bc.chunk_rows, bc.ring_rows, bc.c0_stages, best / 3);
   std::lock_guard<std::mutex> lk(g_tune_mu);
   g_tune_cache[key] = bc;
 }
@@ -2537,13 +2554,274 @@ void tune_local(hplmm_ctx *c) {
   if (!c->opt.autotune) {
     c->grains.tuned_chunk_rows = c->grains.tuned_ring_rows = c->grains.tuned_c0_stages = c->grains.tuned_cluster = 0;
     c->contacts.tuned_chunk_rows = c->contacts.tuned_ring_rows = c->contacts.tuned_c0_stages = 0;
-    c->contacts.tuned_cluster = 0;
+    c->contacts.tuned_cluster = c->grains.tuned_bulk = c->contacts.tuned_bulk = 0;
     return;
   }
   tune_set(c, c->contacts, true);
   tune_set(c, c->grains, false);
   HP_CUDA(cudaMemsetAsync(c->w_zz.p, 0, sizeof(double) * 3 * (size_t)c->n_nodes, c->stream));
   HP_CUDA(cudaStreamSynchronize(c->stream));
+}
+
+}  // namespace hp
+
+// ---------------------------------------------------------------- algebraic mortars (Eq. algebra)
+// The mortar functions of interface c solve S^c w = 0 off the mortar DOFs, with w = 1 at DOF (x_i, gamma) and
+// 0 at the other mortar DOFs (the Remark after Eq. reduced_defs).  S^c stands for the interface's elasticity
+// operator of Eq. algebra, built from A_hat: for every pair of distinct interface nodes {y, y'} that A_hat
+// couples, the edge term (e_y - e_y')(e_y - e_y')^T (x) |B_yy'| with B_yy' = -(A_yy' + A_yy'^T)/2 and |.| the
+// matrix absolute value, plus ALG_SHIFT times A_hat's diagonal.  Without the shift S^c is positive
+// semidefinite and annihilates rigid translations of the interface (so the functions of one component sum
+// to e_gamma); the shift makes it definite on interface pieces without a mortar node.  Each interface is a
+// local problem on its own nodes (the contact-grid machinery with w = 0): S^c is extracted with the mortar and
+// fixed DOFs as identity rows, factored (FP64 band), and solved for all of the interface's columns at once;
+// the right-hand side of column (i, gamma) carries the unit value at its own DOF and minus the coupling to it
+// on the other rows.
+namespace hp {
+namespace {
+
+constexpr double ALG_SHIFT = 1e-8;  // relative to A_hat's diagonal
+
+// P = |B| for B = -(V + V^T)/2, V a 3x3 block (row-major): cyclic Jacobi rotations (the symmetric Schur
+// decomposition of Golub and Van Loan, Matrix Computations, Sec. 8.5) give B = Q L Q^T, then P = Q |L| Q^T
+__device__ void abs_negsym3(const double *v, double *P) {
+  double a[3][3], q[3][3] = {{1, 0, 0}, {0, 1, 0}, {0, 0, 1}};
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) a[i][j] = -0.5 * (v[3 * i + j] + v[3 * j + i]);
+  for (int sweep = 0; sweep < 12; ++sweep) {
+    const double off = a[0][1] * a[0][1] + a[0][2] * a[0][2] + a[1][2] * a[1][2];
+    const double on = a[0][0] * a[0][0] + a[1][1] * a[1][1] + a[2][2] * a[2][2];
+    if (off <= 1e-36 * (on + off)) break;
+    for (int pq = 0; pq < 3; ++pq) {
+      const int p = pq == 2 ? 1 : 0, r = pq == 0 ? 1 : 2;
+      if (a[p][r] == 0.0) continue;
+      const double theta = (a[r][r] - a[p][p]) / (2.0 * a[p][r]);
+      const double t = (theta >= 0.0 ? 1.0 : -1.0) / (fabs(theta) + sqrt(theta * theta + 1.0));
+      const double c = 1.0 / sqrt(t * t + 1.0), sn = t * c;
+      for (int k = 0; k < 3; ++k) {  // A J
+        const double akp = a[k][p], akr = a[k][r];
+        a[k][p] = c * akp - sn * akr;
+        a[k][r] = sn * akp + c * akr;
+      }
+      for (int k = 0; k < 3; ++k) {  // J^T (A J)
+        const double apk = a[p][k], ark = a[r][k];
+        a[p][k] = c * apk - sn * ark;
+        a[r][k] = sn * apk + c * ark;
+      }
+      for (int k = 0; k < 3; ++k) {  // Q J
+        const double qkp = q[k][p], qkr = q[k][r];
+        q[k][p] = c * qkp - sn * qkr;
+        q[k][r] = sn * qkp + c * qkr;
+      }
+    }
+  }
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) {
+      double sum = 0.0;
+      for (int k = 0; k < 3; ++k) sum += q[i][k] * fabs(a[k][k]) * q[j][k];
+      P[3 * i + j] = sum;
+    }
+}
+
+// S^c of interface k into its band (lower triangle): edge terms -|B| off the diagonal, the sum of the node's
+// |B| plus the shift on it; mortar and fixed DOFs as identity rows
+__global__ void k_iface_extract(const int *box, const long long *node_off, const int *nloc, const int *bwv,
+                                const long long *band_off, const int *lmap, const int *lnodes, const int *node_ijk,
+                                const int *row_ptr, const int *col, const double *val, const uint8_t *fixed,
+                                const int *mslot_of_node, double *band) {
+  const int k = blockIdx.x;
+  const Box b = load_box(box, k);
+  const long long off = node_off[k];
+  const int cnt = nloc[k] / 3, bw = bwv[k];
+  double *B = band + band_off[k];
+  for (int o = threadIdx.x; o < cnt; o += blockDim.x) {
+    const int n = lnodes[off + o];
+    const bool mo = mslot_of_node[n] >= 0;
+    double dg[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0}, adiag[3] = {0, 0, 0};
+    for (int p = row_ptr[n]; p < row_ptr[n + 1]; ++p) {
+      const int m = col[p];
+      const int cell = box_cell(b, node_ijk[3 * m], node_ijk[3 * m + 1], node_ijk[3 * m + 2]);
+      if (cell < 0) continue;
+      const int om = lmap[off + cell];
+      if (om < 0) continue;
+      const double *v = val + (long long)p * 9;
+      if (m == n) {
+        for (int d = 0; d < 3; ++d) adiag[d] = v[4 * d];
+        continue;
+      }
+      double P[9];
+      abs_negsym3(v, P);
+#pragma unroll
+      for (int e = 0; e < 9; ++e) dg[e] += P[e];
+      if (mo || mslot_of_node[m] >= 0 || om > o) continue;
+      for (int d = 0; d < 3; ++d)
+        for (int d2 = 0; d2 < 3; ++d2)
+          if (!fixed[3 * n + d] && !fixed[3 * m + d2]) B[panel_addr(3 * o + d, 3 * om + d2, 16, bw)] = -P[3 * d + d2];
+    }
+    for (int d = 0; d < 3; ++d) {
+      const int i = 3 * o + d;
+      if (mo || fixed[3 * n + d]) {
+        B[panel_addr(i, i, 16, bw)] = 1.0;
+        continue;
+      }
+      for (int d2 = 0; d2 < d; ++d2)
+        if (!fixed[3 * n + d2]) B[panel_addr(i, 3 * o + d2, 16, bw)] = dg[3 * d + d2];
+      B[panel_addr(i, i, 16, bw)] = dg[4 * d] + ALG_SHIFT * adiag[d];
+    }
+  }
+}
+
+// right-hand sides: row (o, d) of column (i, gamma): 1 if node o is mortar i and d = gamma; 0 on other mortar
+// rows and fixed rows; otherwise minus S^c's coupling to the unit DOF, |B_{n m_i}|(d, gamma)
+__global__ void k_iface_rhs(const long long *node_off, const int *nloc, const int *lnodes, const int *row_ptr,
+                            const int *col, const double *val, const uint8_t *fixed, const int *iface_of_node,
+                            const int *mslot_of_node, const int *mcol, const int *mfree, const long long *x_off,
+                            const int *x_ld, double *X) {
+  const int k = blockIdx.x;
+  const int cnt = nloc[k] / 3;
+  const int ld = x_ld[k];
+  double *Xk = X + x_off[k];
+  for (int o = threadIdx.x; o < cnt; o += blockDim.x) {
+    const int n = lnodes[node_off[k] + o];
+    const int ms = mslot_of_node[n];
+    if (ms >= 0) {
+      for (int g = 0; g < 3; ++g)
+        if ((mfree[ms] >> g) & 1) Xk[(long long)(3 * o + g) * ld + mcol[ms] + __popc(mfree[ms] & ((1 << g) - 1))] = 1.0;
+      continue;
+    }
+    for (int p = row_ptr[n]; p < row_ptr[n + 1]; ++p) {
+      const int m = col[p];
+      const int mm = mslot_of_node[m];
+      if (mm < 0 || iface_of_node[m] != k) continue;
+      double P[9];
+      abs_negsym3(val + (long long)p * 9, P);
+      for (int g = 0; g < 3; ++g) {
+        if (!((mfree[mm] >> g) & 1)) continue;
+        const int kk = mcol[mm] + __popc(mfree[mm] & ((1 << g) - 1));
+        for (int d = 0; d < 3; ++d)
+          if (!fixed[3 * n + d]) Xk[(long long)(3 * o + d) * ld + kk] = P[3 * d + g];
+      }
+    }
+  }
+}
+
+// the solved columns into the interface's block of Q^o, rows (interface slot, component)
+__global__ void k_iface_store(const long long *node_off, const int *nloc, const int *lnodes, const int *iface_slot,
+                              const long long *x_off, const int *x_ld, const double *X, const long long *qoff,
+                              double *Q) {
+  const int k = blockIdx.x;
+  const int cnt = nloc[k] / 3;
+  const int ld = x_ld[k];
+  for (int e = threadIdx.x; e < 3 * cnt * ld; e += blockDim.x) {
+    const int row = e / ld, kk = e - row * ld;
+    const int o = row / 3, d = row - 3 * o;
+    const int slot = iface_slot[lnodes[node_off[k] + o]];
+    Q[qoff[k] + (long long)(3 * slot + d) * ld + kk] = X[x_off[k] + e];
+  }
+}
+
+__global__ void k_mortar_info(const int *mortar_nodes, int n_mortars, const uint8_t *fixed, int *mslot_of_node,
+                              int *mfree) {
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= n_mortars) return;
+  const int n = mortar_nodes[q];
+  mslot_of_node[n] = q;
+  mfree[q] = (fixed[3 * n] ? 0 : 1) | (fixed[3 * n + 1] ? 0 : 2) | (fixed[3 * n + 2] ? 0 : 4);
+}
+
+}  // namespace
+
+void build_algebraic_mortars(hplmm_ctx *c) {
+  cudaStream_t s = c->stream;
+  const int C = c->n_ifaces;
+  if (C == 0) return;
+  // columns: (mortar i, component gamma) for every free DOF of a mortar node
+  c->mslot_of_node.alloc(c->n_nodes);
+  c->mslot_of_node.fill_bytes(0xff, s);
+  c->mfree.alloc(std::max(c->n_mortars, 1));
+  k_mortar_info<<<grid_for(c->n_mortars, 256), 256, 0, s>>>(c->mortar_nodes.p, c->n_mortars, c->fixed.p,
+                                                          c->mslot_of_node.p, c->mfree.p);
+  HP_CHECK_LAUNCH();
+  const std::vector<int> hfree = c->mfree.download(s, c->n_mortars);
+  std::vector<int> hmcol(std::max(c->n_mortars, 1), 0);
+  c->h_col_off.assign(C + 1, 0);
+  for (int ci = 0; ci < C; ++ci) {
+    int kk = 0;
+    for (int q = c->h_mortar_off[ci]; q < c->h_mortar_off[ci + 1]; ++q) {
+      hmcol[q] = kk;
+      kk += __builtin_popcount(hfree[q]);
+    }
+    c->h_col_off[ci + 1] = c->h_col_off[ci] + kk;
+  }
+  c->mcol.upload(hmcol, s);
+  layout_columns(c);
+  // the interfaces as local problems on their own nodes
+  LocalSet &S = c->ifsets;
+  {
+    Buf<int> bmin, bmax;
+    bmin.alloc(3 * C);
+    bmax.alloc(3 * C);
+    bmin.fill_bytes(0x7f, s);
+    bmax.fill_bytes(0x80, s);
+    k_iface_bbox<<<grid_for(c->n_iface_nodes, 256), 256, 0, s>>>(c->iface_nodes.p, c->iface_of_node.p,
+                                                                 c->n_iface_nodes, c->node_ijk.p, bmin.p, bmax.p);
+    HP_CHECK_LAUNCH();
+    auto lo = bmin.download(s), hi = bmax.download(s);
+    S.count = C;
+    auto hbox = make_boxes(lo, hi, C, 0, c->nx, c->ny, c->nz);
+    finish_set(c, S, 1, hbox);
+    S.lmap.zero(s);
+    k_contact_mark<<<grid_for(c->n_iface_nodes, 128), 128, 0, s>>>(c->iface_nodes.p, c->iface_of_node.p,
+                                                                   c->n_iface_nodes, c->node_ijk.p, S.box.p,
+                                                                   S.node_off.p, 0, S.lmap.p);
+    HP_CHECK_LAUNCH();
+    enumerate_set(c, S, 1);
+  }
+  const int bwmax = layout_set<double>(S, s);
+  S.band64.alloc(std::max<long long>(S.h_band_off[C], 1));
+  S.band64.zero(s);
+  S.prec = HPLMM_FP64;
+  k_iface_extract<<<C, 128, 0, s>>>(S.box.p, S.node_off.p, S.n.p, S.bw.p, S.band_off.p, S.lmap.p, S.lnodes.p,
+                                    c->node_ijk.p, c->row_ptr.p, c->col.p, c->val64.p, c->fixed.p,
+                                    c->mslot_of_node.p, S.band64.p);
+  HP_CHECK_LAUNCH();
+  {
+    const size_t smem = (size_t)(16 + bwmax) * (16 + 2) * sizeof(double);
+    S.queue.alloc(1);
+    S.queue.zero(s);
+    auto kern = k_band_chol<double, 16>;
+    HP_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    kern<<<std::min(C, 2 * num_sms()), FACT_THREADS, smem, s>>>(S.order.p, C, S.queue.p, S.n.p, S.bw.p,
+                                                               S.band_off.p, S.band64.p, c->status.p, 4);
+    HP_CHECK_LAUNCH();
+  }
+  // right-hand sides, solves, and the blocks of Q^o
+  std::vector<long long> xoff(C + 1, 0), qoff(C + 1, 0);
+  std::vector<int> ld(C);
+  for (int ci = 0; ci < C; ++ci) {
+    ld[ci] = std::max(c->h_col_off[ci + 1] - c->h_col_off[ci], 1);
+    xoff[ci + 1] = xoff[ci] + (long long)S.h_n[ci] * ld[ci];
+    qoff[ci + 1] = qoff[ci] + 3LL * (c->h_iface_off[ci + 1] - c->h_iface_off[ci]) * ld[ci];
+  }
+  Buf<long long> dxoff;
+  Buf<int> dld;
+  dxoff.upload(xoff, s);
+  dld.upload(ld, s);
+  c->qoff.upload(qoff, s);
+  Buf<double> X;
+  X.alloc(std::max<long long>(xoff[C], 1));
+  X.zero(s);
+  k_iface_rhs<<<C, 128, 0, s>>>(S.node_off.p, S.n.p, S.lnodes.p, c->row_ptr.p, c->col.p, c->val64.p, c->fixed.p,
+                                c->iface_of_node.p, c->mslot_of_node.p, c->mcol.p, c->mfree.p, dxoff.p, dld.p, X.p);
+  HP_CHECK_LAUNCH();
+  solve_multi_t<double>(c, S, X.p, dxoff, dld, ld);
+  c->qblk.alloc(std::max<long long>(qoff[C], 1));
+  c->qblk.zero(s);
+  k_iface_store<<<C, 256, 0, s>>>(S.node_off.p, S.n.p, S.lnodes.p, c->iface_slot.p, dxoff.p, dld.p, X.p, c->qoff.p,
+                                  c->qblk.p);
+  HP_CHECK_LAUNCH();
+  HP_CUDA(cudaStreamSynchronize(s));
+  S.band64.release();  // the interface factors are not needed after the set-up
 }
 
 }  // namespace hp

@@ -588,19 +588,32 @@ void build_maps(hplmm_ctx *c, const int32_t *partition) {
 
   // grain -> coupled interfaces, columns per grain, kept corrections
   int G = c->n_grains;
-  c->h_gi_off.assign(G + 1, 0);
-  c->h_gi_iface.clear();
-  c->h_gi_colbase.clear();
-  std::vector<std::vector<int>> lists(G);
+  c->h_glists.assign(G, {});
   for (int ci = 0; ci < n_if; ++ci)
     for (int g = 0; g < G; ++g)
-      if (hc[(size_t)ci * G + g]) lists[g].push_back(ci);
+      if (hc[(size_t)ci * G + g]) c->h_glists[g].push_back(ci);
   Buf<int> hasb;
   hasb.alloc(G);
   hasb.zero(s);
   k_grain_has_rhs<<<grid_for(nn, 256), 256, 0, s>>>(c->node_cls.p, c->b_corr.p, nn, hasb.p);
   HP_CHECK_LAUNCH();
-  auto hb = hasb.download(s);
+  c->h_grain_hasb = hasb.download(s);
+  layout_columns(c);
+}
+
+// columns of every grain's panel from the interfaces' column counts (h_col_off): the coupled interfaces'
+// mortar columns in ascending interface order, then the grain's correction column when b^g != 0
+void layout_columns(hplmm_ctx *c) {
+  cudaStream_t s = c->stream;
+  const int G = c->n_grains;
+  const int n_if = c->n_ifaces;
+  const auto &lists = c->h_glists;
+  const auto &hb = c->h_grain_hasb;
+  c->n_mortar_cols = c->h_col_off[n_if];
+  c->col_off.upload(c->h_col_off, s);
+  c->h_gi_off.assign(G + 1, 0);
+  c->h_gi_iface.clear();
+  c->h_gi_colbase.clear();
   c->h_kg.assign(G, 0);
   c->h_corr_col.assign(G, -1);
   long long ncorr = 0;

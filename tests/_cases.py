@@ -19,6 +19,9 @@ CASES = {
     # the fractured recipe at 32^3 (2x2x2 grains): Voronoi two-phase E in {1, 10} and three one-voxel slits
     # with E x 1e-4 crossing the grains and their interfaces
     "fractured32_n2": ("fractured32", 0, dict(n_mortar=2, contact_halfwidth=2)),
+    # algebraic mortars (Eq. algebra)
+    "tiny8_alg": ("tiny8", 3, dict(n_mortar=2, contact_halfwidth=1, mortar_kind="algebraic")),
+    "porous32_alg": ("porous32", 1, dict(n_mortar=4, contact_halfwidth=2, mortar_kind="algebraic")),
     # large local sets: 216 grains of 4^3 voxels (more grains than half the SMs: one CTA per problem in the
     # factorisation) and 512 grains (more problems than two per SM: the persistent queue hands CTAs several
     # problems), both with more than 500 contact grids and a deep coarse elimination tree
@@ -40,7 +43,8 @@ def oracle_case(name):
     """(problem, options, oracle system, oracle preconditioner)."""
     p, opt = problem(name)
     o = precond.Options(n_mortar=opt["n_mortar"], contact_halfwidth=opt["contact_halfwidth"],
-                        strict_two_grain=opt.get("strict_two_grain", False))
+                        strict_two_grain=opt.get("strict_two_grain", False),
+                        mortar_kind=opt.get("mortar_kind", "gaussian"))
     sysm, M = precond.build(p, o)
     return p, opt, sysm, M
 
@@ -75,7 +79,7 @@ def gpu_solver(name, **over):
     import paper_2509_19777_gb300 as hp
     p, opt = problem(name)
     kw = dict(n_mortar=opt["n_mortar"], contact_halfwidth=opt["contact_halfwidth"],
-              strict_two_grain=opt.get("strict_two_grain", False))
+              strict_two_grain=opt.get("strict_two_grain", False), mortar_kind=opt.get("mortar_kind", "gaussian"))
     kw.update(over)
     s = hp.Solver(**kw)
     mask, E = hp.problem_to_device(p)

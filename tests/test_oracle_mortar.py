@@ -139,7 +139,8 @@ def test_algebraic_mortars_partition_of_unity_and_constraints(n):
                 ks = [k for k, (i, gg) in enumerate(mo.columns[c]) if gg == g]
                 tot = Q[:, ks].sum(axis=1)
                 want = np.array([1.0 if d == g else 0.0 for (y, d) in rows])
-                assert np.abs(tot - want).max() < 1e-10, (c, g)
+                # exact without the diagonal shift; the shift (1e-8 of the diagonal) moves the sums slightly
+                assert np.abs(tot - want).max() < 1e-5, (c, g)
 
 
 def test_algebraic_one_mortar_is_plmm():
@@ -152,7 +153,80 @@ def test_algebraic_one_mortar_is_plmm():
     for kind in ("gaussian", "algebraic"):
         sysm, M = precond.build(p, precond.Options(n_mortar=1, contact_halfwidth=1, mortar_kind=kind))
         Ao[kind] = M.coarse.A_o
-    assert np.abs(Ao["gaussian"] - Ao["algebraic"]).max() < 1e-10 * np.abs(Ao["gaussian"]).max()
+    # equal but for the diagonal shift of the interface operator (1e-8 of A_hat's diagonal)
+    assert np.abs(Ao["gaussian"] - Ao["algebraic"]).max() < 1e-5 * np.abs(Ao["gaussian"]).max()
+
+
+def _iface_operator_case(c_pick=None):
+    sysm, M = _alg_case(4)
+    mo, dec = M.mortars, M.dec
+    out = []
+    for c in range(dec.n_interfaces):
+        nodes = dec.iface_nodes[c]
+        rows = [(y, d) for y, node in enumerate(nodes) for d in range(3) if not sysm.fixed[node, d]]
+        S = mo._interface_operator(sysm, dec, c, rows)
+        f2f = sysm.full_to_free
+        J = np.array([f2f[3 * nodes[y] + d] for (y, d) in rows])
+        out.append((nodes, rows, S, J))
+    return sysm, out
+
+
+def test_algebraic_interface_operator_properties():
+    # S^c - shift annihilates every rigid translation of the interface, is symmetric positive semidefinite,
+    # and S^c itself is positive definite (so the band Cholesky of the reduced systems cannot break down)
+    from oracle import mortar
+    sysm, cases = _iface_operator_case()
+    diagA = sysm.A.diagonal()
+    for nodes, rows, S, J in cases:
+        S0 = S - np.diag(mortar.ALG_SHIFT * diagA[J])
+        scale = np.abs(S0).max()
+        assert np.abs(S0 - S0.T).max() <= 1e-14 * scale
+        for g in range(3):
+            t = np.array([1.0 if d == g else 0.0 for (y, d) in rows])
+            assert np.abs(S0 @ t).max() <= 1e-12 * scale
+        ev = np.linalg.eigvalsh(S0)
+        assert ev.min() >= -1e-12 * scale
+        assert np.linalg.eigvalsh(S).min() > 0
+
+
+def test_algebraic_interface_operator_edge_blocks():
+    # the off-diagonal block of S^c for a node pair is -|B|, B = -sym(A_yy'), checked against what fixes the
+    # matrix absolute value without computing it: |B| is the one positive semidefinite matrix whose square is
+    # B^2; where B is itself positive semidefinite (an attractive coupling) the block is sym(A_yy'), A_hat's
+    # own coupling.  Brute force over all node pairs of every interface
+    sysm, cases = _iface_operator_case()
+    A = sysm.A.toarray()
+    n_att = n_mixed = 0
+    for nodes, rows, S, J in cases:
+        pos = {yd: r for r, yd in enumerate(rows)}
+        F = len(nodes)
+        for y in range(F):
+            for z in range(F):
+                if y == z:
+                    continue
+                free = [(d, e) for d in range(3) for e in range(3) if (y, d) in pos and (z, e) in pos]
+                blk = np.zeros((3, 3))
+                for d, e in free:
+                    blk[d, e] = A[J[pos[(y, d)]], J[pos[(z, e)]]]
+                if not blk.any():
+                    continue
+                B = -0.5 * (blk + blk.T)
+                off = np.zeros((3, 3))
+                for d, e in free:
+                    off[d, e] = S[pos[(y, d)], pos[(z, e)]]
+                scale = np.abs(B).max()
+                if len(free) == 9:
+                    absB = -off
+                    assert np.abs(absB - absB.T).max() <= 1e-13 * scale
+                    assert np.linalg.eigvalsh(absB).min() >= -1e-13 * scale
+                    assert np.abs(absB @ absB - B @ B).max() <= 1e-12 * scale ** 2
+                if np.linalg.eigvalsh(B).min() >= 0:
+                    for d, e in free:
+                        assert abs(off[d, e] + B[d, e]) <= 1e-13 * scale
+                    n_att += 1
+                else:
+                    n_mixed += 1
+    assert n_att > 0 and n_mixed > 0
 
 
 def test_algebraic_all_nodes_mortars_is_identity():
