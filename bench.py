@@ -60,6 +60,12 @@ WORKLOADS = {
     "porous64": dict(image=[64, 64, 64], porosity=0.3, grains=[4, 4, 4], n_mortar=4, chosen=FP32,
                      plain_fits=True, baseline_config=2,
                      form_text="FP32 form as for porous128"),
+    # the fractured256 recipe at 64^3 and 128^3 (the same 16^3-voxel grains, so the same local problem shapes,
+    # 64 and 512 of them): profiling cases small enough for a full ncu capture, not bench lines
+    "fractured64": dict(image=[64, 64, 64], porosity=0.25, grains=[4, 4, 4], n_mortar=2, chosen=BF16,
+                        plain_fits=True, baseline_config=None, form_text="BF16 form as for fractured256"),
+    "fractured128": dict(image=[128, 128, 128], porosity=0.25, grains=[8, 8, 8], n_mortar=2, chosen=BF16,
+                         plain_fits=True, baseline_config=None, form_text="BF16 form as for fractured256"),
 }
 DEFAULT_WORKLOAD = "fractured256"
 PLAIN_WORKLOAD = "porous128"   # largest workload whose plain FP64 form fits one GPU
@@ -482,6 +488,33 @@ def _oracle_subprocess(workload, seed, n, timeout=1800):
     return json.loads(r.stdout.strip().splitlines()[-1])
 
 
+def _oracle_concurrent(workload, seed, procs, timeout=1800):
+    """The all-cores variant: `procs` single-threaded oracle processes at once, each timing the same sample;
+    returns their runs and the wall time from the first start to the last finish."""
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    code = ("import json,sys; sys.path.insert(0, %r); import bench; "
+            "print(json.dumps(bench.oracle_samples(%r, %d, 1)))") % (ROOT, workload, seed)
+    t0 = time.perf_counter()
+    ps = [subprocess.Popen([sys.executable, "-c", code], stdout=subprocess.PIPE, stderr=subprocess.PIPE, text=True,
+                           env=env) for _ in range(procs)]
+    runs = []
+    for pr in ps:
+        out, err = pr.communicate(timeout=timeout)
+        if pr.returncode != 0:
+            raise RuntimeError(err[-2000:])
+        runs.extend(json.loads(out.strip().splitlines()[-1]))
+    return runs, time.perf_counter() - t0
+
+
+def all_cores_json(runs, wall, procs):
+    return {"cores": procs, "concurrent_samples": procs, "wall_s": wall,
+            "per_sample_s": statistics.mean(r["total_s"] for r in runs),
+            "host_time_per_sample_s": wall / procs,
+            "how": (f"{procs} single-threaded oracle processes at once (one per host core), each timing the same "
+                    "sample; host_time_per_sample_s = wall time / samples, the host's throughput with every "
+                    "core busy (process start and imports included in the wall time)")}
+
+
 def cpu_baseline_json(runs, workload, full_iters=None):
     """The measured oracle time of the sample (no extrapolation in `value`); an extrapolation to the full
     image -- set-up by the grain count, solve by the grain count and the iteration ratio -- is reported
@@ -712,6 +745,9 @@ def main():
         try:
             runs = _oracle_subprocess(args.workload, args.seed, 2)
             line["cpu_baseline"] = cpu_baseline_json(runs[1:], args.workload, stc.iters)
+            procs = os.cpu_count() or 1
+            cruns, wall = _oracle_concurrent(args.workload, args.seed, procs)
+            line["cpu_baseline"]["all_cores"] = all_cores_json(cruns, wall, procs)
         except Exception as e:  # the baseline is reported, never required
             line["cpu_baseline"] = {"value": None, "error": str(e)[-300:]}
     if rank == 0:

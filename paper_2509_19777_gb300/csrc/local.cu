@@ -1263,7 +1263,7 @@ template <typename T, int n> __device__ __forceinline__ void ld_vec(const T *p, 
 }
 
 template <typename S, int NB, int CL, int NBW>
-__global__ void __launch_bounds__((3 + NBW) * 32, NBW == WS_BULK_WARPS ? 1 : 2) k_band_solve_ws(
+__global__ void __launch_bounds__((3 + NBW) * 32, NBW == WS_BULK_WARPS ? 1 : NBW == 4 ? 2 : NBW == 2 ? 3 : 4) k_band_solve_ws(
     int count, const int *nloc, const int *bwv, const long long *band_off, const long long *vec_off,
     const int *gidx, const S *band, const double *r, double *z, typename ComputeOf<S>::type *yscr, int atomic,
     int ring_rows, int chunk_rows, int c0_stages, int wmask, int *status, long long wait_cycles) {
@@ -2328,7 +2328,7 @@ struct SolvePlan {
 // kernel's static shared memory), or two CTAs per SM (half of the SM's shared memory, less the static part
 // and the per-block reservation)
 struct SmemBudget {
-  size_t one, pair;
+  size_t one, pair, third, quarter;  // dynamic shared memory for one to four CTAs per SM
 };
 template <typename K> static SmemBudget smem_budget(K kern) {
   static std::mutex mu;
@@ -2345,6 +2345,8 @@ template <typename K> static SmemBudget smem_budget(K kern) {
   SmemBudget b;
   b.one = (size_t)optin - fa.sharedSizeBytes - 256;
   b.pair = (size_t)per_sm / 2 - fa.sharedSizeBytes - 1024 - 256;
+  b.third = (size_t)per_sm / 3 - fa.sharedSizeBytes - 1024 - 256;
+  b.quarter = (size_t)per_sm / 4 - fa.sharedSizeBytes - 1024 - 256;
   cache[(const void *)kern] = b;
   return b;
 }
@@ -2390,11 +2392,16 @@ void smoother_apply(hplmm_ctx *c, LocalSet &S, const double *r_pad, double *z_pa
   // depths: the tuner's choice when there is one, else 3 diagonal stages, whole-step chunks and the largest
   // ring
   const int c0s = S.tuned_c0_stages > 0 ? S.tuned_c0_stages : 3;
-  // bulk warps per CTA: 8 (one CTA per SM), or 4 with the ring sized for two CTAs per SM (one-CTA problems)
-  const int nbw = (cl == 1 && S.tuned_bulk == 4) ? 4 : WS_BULK_WARPS;
+  // bulk warps per CTA: 8 (one CTA per SM), or, for one-CTA problems, 4, 2 or 1 with the ring sized for two,
+  // three or four CTAs per SM
+  const int nbw = (cl == 1 && (S.tuned_bulk == 4 || S.tuned_bulk == 2 || S.tuned_bulk == 1)) ? S.tuned_bulk
+                                                                                             : WS_BULK_WARPS;
   auto go = [&](auto kern, const auto *band, auto *ys) {
     const SmemBudget bud = smem_budget(kern);
-    int ring = ring_rows_for(pl, c0s, nbw == WS_BULK_WARPS ? bud.one : bud.pair);
+    int ring = ring_rows_for(pl, c0s, nbw == WS_BULK_WARPS ? bud.one
+                                      : nbw == 4            ? bud.pair
+                                      : nbw == 2            ? bud.third
+                                                            : bud.quarter);
     if (S.tuned_ring_rows > 0) ring = std::min(ring, S.tuned_ring_rows);
     HP_REQUIRE(ring >= 64, HPLMM_ERR_INVALID,
                "local problem too large for the smoother (window of " + std::to_string(pl.W) + " rows)");
@@ -2427,6 +2434,10 @@ void smoother_apply(hplmm_ctx *c, LocalSet &S, const double *r_pad, double *z_pa
       go(k_band_solve_ws<ST, NBv, 2, WS_BULK_WARPS>, band, ys);
     else if (nbw == 4)
       go(k_band_solve_ws<ST, NBv, 1, 4>, band, ys);
+    else if (nbw == 2)
+      go(k_band_solve_ws<ST, NBv, 1, 2>, band, ys);
+    else if (nbw == 1)
+      go(k_band_solve_ws<ST, NBv, 1, 1>, band, ys);
     else
       go(k_band_solve_ws<ST, NBv, 1, WS_BULK_WARPS>, band, ys);
   };
@@ -2495,13 +2506,18 @@ static void tune_set(hplmm_ctx *c, LocalSet &S, bool atomic) {
                                               : smem_budget(k_band_solve_ws<float, 32, 1, WS_BULK_WARPS>);
   const SmemBudget bud4 = S.prec == HPLMM_FP64 ? smem_budget(k_band_solve_ws<double, 16, 1, 4>)
                                                : smem_budget(k_band_solve_ws<float, 32, 1, 4>);
-  // plans: (CTAs per problem, bulk warps, shared-memory budget); the 4-warp kernel only with the two-per-SM
-  // budget, which is what it is for
+  const SmemBudget bud2 = S.prec == HPLMM_FP64 ? smem_budget(k_band_solve_ws<double, 16, 1, 2>)
+                                               : smem_budget(k_band_solve_ws<float, 32, 1, 2>);
+  const SmemBudget bud1 = S.prec == HPLMM_FP64 ? smem_budget(k_band_solve_ws<double, 16, 1, 1>)
+                                               : smem_budget(k_band_solve_ws<float, 32, 1, 1>);
+  // plans: (CTAs per problem, bulk warps, shared-memory budget); the 4-, 2- and 1-warp kernels only with the
+  // two-, three- and four-per-SM budgets, which are what they are for
   struct Form {
     int cl, nbw;
     size_t budget;
   };
-  const Form forms[] = {{1, WS_BULK_WARPS, bud.one}, {1, WS_BULK_WARPS, bud.pair}, {1, 4, bud4.pair},
+  const Form forms[] = {{1, WS_BULK_WARPS, bud.one}, {1, WS_BULK_WARPS, bud.pair}, {1, 4, bud4.pair}, {1, 2, bud2.third},
+                        {1, 1, bud1.quarter},
                         {2, WS_BULK_WARPS, bud.one}, {2, WS_BULK_WARPS, bud.pair}};
   for (const Form &f : forms)
    for (int chunk : chunk_choices(S))
