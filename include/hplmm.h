@@ -92,6 +92,10 @@ typedef struct {
                             microseconds at the nominal 2,070 MHz SM clock (0 = default, about 2 s); a wait that
                             runs out makes the launch stop and the next synchronising call return
                             HPLMM_ERR_TIMEOUT (a small value is how the tests exercise that path) */
+  int tensor_galerkin;   /* Galerkin product P_hat^T A_hat P_hat of the FP32 and BF16 forms: 1 (default) on the
+                            tensor cores (tcgen05.mma kind::tf32, three TF32 products per pair of FP32 operands,
+                            FP32 accumulation in tensor memory), 0 on the FP32 CUDA cores; the FP64 form always
+                            uses FP64 CUDA cores */
 } hplmm_options;
 
 enum { HPLMM_BASIS_DIRECT = 0, HPLMM_BASIS_PCG = 1, HPLMM_BASIS_PCG_WARM = 2 };

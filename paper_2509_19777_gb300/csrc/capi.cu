@@ -97,6 +97,7 @@ void validate_options(const hplmm_options &o) {
              "mortar_kind must be HPLMM_MORTAR_GAUSSIAN or HPLMM_MORTAR_ALGEBRAIC");
   HP_REQUIRE(o.stage_mb >= 0, HPLMM_ERR_INVALID, "stage_mb must be non-negative");
   HP_REQUIRE(o.wait_budget_us >= 0, HPLMM_ERR_INVALID, "wait_budget_us must be non-negative");
+  HP_REQUIRE(o.tensor_galerkin == 0 || o.tensor_galerkin == 1, HPLMM_ERR_INVALID, "tensor_galerkin must be 0 or 1");
 }
 
 void require_setup(hplmm_ctx *c) {
@@ -148,6 +149,7 @@ void hplmm_default_options(hplmm_options *o) {
   o->basis_max_iters = 3000;
   o->keep_basis_rhs = 0;
   o->smoother_ctas = 0;
+  o->tensor_galerkin = 1;
 }
 
 hplmm_status hplmm_create(hplmm_ctx **ctx, const hplmm_options *opt, void *cuda_stream) {

@@ -13,6 +13,7 @@
 #include "common.cuh"
 
 #include <algorithm>
+#include <type_traits>
 
 namespace hp {
 namespace {
@@ -255,6 +256,219 @@ __global__ void __launch_bounds__(256) k_gal_gemm(const int *tiles, const int *g
         if (Ao) atomicAdd(&Ao[(long long)gc[a] * No + gc[bb]], (double)acc[i][j]);
       }
     }
+}
+
+// ---- the Galerkin product on the 5th-generation tensor cores (FP32 forms): C = P^T Y per grain with
+// tcgen05.mma kind::tf32 and the accumulator in tensor memory.  FP32 accuracy from three TF32 products per
+// pair of operands (x = x_hi + x_lo with x_hi the value truncated to TF32 and x_lo = x - x_hi exact in FP32:
+// hi*hi + hi*lo + lo*hi; the dropped lo*lo term and the TF32 truncation of lo are near 2^-22 of the product).
+// CTA = (grain, 128 columns a of P, up to 256 columns b of Y): 128 threads stage 16 box rows of both operands
+// per step into shared memory in the canonical K-major layout without swizzle (8-row x 16-byte core
+// matrices; core matrices along K 128 bytes apart, 8-row groups 512 bytes apart), two stages; one thread
+// issues the 2 x 3 MMAs of a step (M = 128, N = the tile's columns rounded to 16, K = 8) and commits them to
+// the stage's mbarrier, which releases the stage for the step two later.  The 128 x N accumulator sits in
+// 256 TMEM columns (two CTAs per SM at most, by shared memory); each warp reads its 32 lanes back with
+// tcgen05.ld and adds them into the coarse fronts.
+namespace tc {
+constexpr int KC = 16;                                // box rows per stage (K of the stage)
+constexpr int A_BYTES = 128 * KC * 4;                 // one TF32 part of the A tile (8 KB)
+constexpr int B_BYTES = 256 * KC * 4;                 // one TF32 part of the B tile (16 KB)
+constexpr int STAGE_BYTES = 2 * A_BYTES + 2 * B_BYTES;  // hi and lo of both
+constexpr int SMEM_BYTES = 2 * STAGE_BYTES;           // 96 KB
+constexpr int TMEM_COLS = 256;
+constexpr long long WAIT_CYCLES = 2000000000LL;      // bounded waits: about a second of SM clock
+
+__device__ __forceinline__ uint32_t su32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+// byte offset of element (row, kk) of a tile in the K-major no-swizzle layout
+__device__ __forceinline__ int koff(int row, int kk) {
+  return (row >> 3) * 512 + (kk >> 2) * 128 + (row & 7) * 16 + (kk & 3) * 4;
+}
+
+__device__ __forceinline__ uint64_t sdesc(uint32_t addr) {
+  const uint64_t lbo = 128 >> 4, sbo = 512 >> 4;
+  return (uint64_t)((addr >> 4) & 0x3fff) | (lbo << 16) | (sbo << 32) | (1ull << 46);  // version 1, no swizzle
+}
+
+__device__ __forceinline__ uint32_t idesc_tf32(int n) {
+  return (1u << 4)                    // D: F32
+         | (2u << 7) | (2u << 10)     // A, B: TF32 (both K-major)
+         | ((uint32_t)(n >> 3) << 17) // N / 8
+         | ((uint32_t)(128 >> 4) << 24);  // M / 16
+}
+
+__device__ __forceinline__ void split_tf32(float x, float &hi, float &lo) {
+  hi = __uint_as_float(__float_as_uint(x) & 0xffffe000u);
+  lo = x - hi;
+}
+
+__device__ __forceinline__ void mma_tf32(uint32_t dtm, uint64_t a, uint64_t b, uint32_t id, int acc) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(dtm),
+      "l"(a), "l"(b), "r"(id), "r"(acc)
+      : "memory");
+}
+
+__device__ __forceinline__ bool bar_wait(uint64_t *bar, uint32_t parity) {
+  const long long t0 = clock64();
+  for (;;) {
+    uint32_t done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.b32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(su32(bar)), "r"(parity)
+        : "memory");
+    if (done) return true;
+    if (clock64() - t0 > WAIT_CYCLES) return false;
+  }
+}
+}  // namespace tc
+
+__global__ void __launch_bounds__(128) k_gal_gemm_tc(const int *tiles, const int *gbox, const long long *gal_off,
+                                                     const int *kg, const int *gcol_off, const int *gcol,
+                                                     const float *P, const float *Y, long long gbase, CFView cf,
+                                                     double *Ao, long long No, int *status) {
+  extern __shared__ __align__(1024) unsigned char tsm[];
+  __shared__ __align__(8) uint64_t bar[2];
+  __shared__ uint32_t tmem_base;
+  const int tid = threadIdx.x, wid = tid >> 5, lane = tid & 31;
+  // tile: grain, first column of P, first column of Y, and the range [c_beg, c_end) of 16-row chunks of the
+  // box (split-K: the partial products of one output tile are added into the fronts atomically)
+  const int *tl = tiles + 5 * blockIdx.x;
+  const int g = tl[0], a0 = tl[1], b0 = tl[2], c_beg = tl[3], c_end = tl[4];
+  const int *bx = gbox + 6 * g;
+  const long long M = 3LL * bx[3] * bx[4] * bx[5];
+  const int k = kg[g];
+  const int nb = min(256, k - b0);
+  const int N = (nb + 15) & ~15;
+  const float *Pg = P + (gal_off[g] - gbase);
+  const float *Yg = Y + (gal_off[g] - gbase);
+  if (wid == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(tc::su32(&tmem_base)),
+                 "r"(tc::TMEM_COLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  if (tid == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(tc::su32(&bar[0])) : "memory");
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(tc::su32(&bar[1])) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t dtm = tmem_base;
+  const uint32_t id = tc::idesc_tf32(N);
+  const int nchunks = c_end - c_beg;
+  // this thread's values of one chunk: column a0 + tid of P, columns b0 + tid and b0 + tid + 128 of Y
+  float ra[tc::KC], rb[2][tc::KC];
+  auto fetch = [&](int ch) {
+    const long long r0 = (long long)(c_beg + ch) * tc::KC;
+#pragma unroll
+    for (int e = 0; e < tc::KC; ++e) {
+      const long long r = r0 + e;
+      ra[e] = (r < M && a0 + tid < k) ? __ldg(Pg + r * k + a0 + tid) : 0.f;
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int j = tid + 128 * h;
+        rb[h][e] = (r < M && j < nb) ? __ldg(Yg + r * k + b0 + j) : 0.f;
+      }
+    }
+  };
+  if (nchunks > 0) fetch(0);
+  bool ok = true;
+  for (int ch = 0; ch < nchunks; ++ch) {
+    const int st = ch & 1;
+    // the stage's previous MMAs (step ch - 2) must have read it
+    if (ch >= 2 && ok && !tc::bar_wait(&bar[st], (uint32_t)(((ch - 2) >> 1) & 1))) ok = false;
+    unsigned char *base = tsm + st * tc::STAGE_BYTES;
+    unsigned char *Ahi = base, *Alo = base + tc::A_BYTES;
+    unsigned char *Bhi = base + 2 * tc::A_BYTES, *Blo = Bhi + tc::B_BYTES;
+    // store this chunk (four consecutive box rows per 16-byte store), split into TF32 hi and lo
+#pragma unroll
+    for (int q = 0; q < tc::KC; q += 4) {
+      float4 h, l;
+      tc::split_tf32(ra[q], h.x, l.x);
+      tc::split_tf32(ra[q + 1], h.y, l.y);
+      tc::split_tf32(ra[q + 2], h.z, l.z);
+      tc::split_tf32(ra[q + 3], h.w, l.w);
+      *reinterpret_cast<float4 *>(Ahi + tc::koff(tid, q)) = h;
+      *reinterpret_cast<float4 *>(Alo + tc::koff(tid, q)) = l;
+#pragma unroll
+      for (int hh = 0; hh < 2; ++hh) {
+        const int j = tid + 128 * hh;
+        if (j < N) {
+          float4 bh, bl;
+          tc::split_tf32(rb[hh][q], bh.x, bl.x);
+          tc::split_tf32(rb[hh][q + 1], bh.y, bl.y);
+          tc::split_tf32(rb[hh][q + 2], bh.z, bl.z);
+          tc::split_tf32(rb[hh][q + 3], bh.w, bl.w);
+          *reinterpret_cast<float4 *>(Bhi + tc::koff(j, q)) = bh;
+          *reinterpret_cast<float4 *>(Blo + tc::koff(j, q)) = bl;
+        }
+      }
+    }
+    // the next chunk's loads are in flight while this one is handed to the tensor cores
+    if (ch + 1 < nchunks) fetch(ch + 1);
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    __syncthreads();
+    // every step is committed (with or without MMAs), so that the last commit always arrives
+    if (tid == 0) {
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+#pragma unroll
+      for (int ks = 0; ks < tc::KC / 8; ++ks) {
+        if (!ok) break;
+        const uint32_t off = (uint32_t)ks * 256u;  // two core matrices along K per MMA
+        const uint64_t ah = tc::sdesc(tc::su32(Ahi) + off), al = tc::sdesc(tc::su32(Alo) + off);
+        const uint64_t bh = tc::sdesc(tc::su32(Bhi) + off), bl = tc::sdesc(tc::su32(Blo) + off);
+        tc::mma_tf32(dtm, ah, bh, id, (ch > 0 || ks > 0) ? 1 : 0);
+        tc::mma_tf32(dtm, ah, bl, id, 1);
+        tc::mma_tf32(dtm, al, bh, id, 1);
+      }
+      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                       tc::su32(&bar[st]))
+                   : "memory");
+    }
+  }
+  // the last commit covers every MMA issued before it (an empty box issues none and adds nothing)
+  const int last = nchunks - 1;
+  if (nchunks == 0) ok = false;
+  else if (ok && !tc::bar_wait(&bar[last & 1], (uint32_t)((last >> 1) & 1))) ok = false;
+  if (!ok && nchunks > 0) {
+    atomicCAS(status, 0, (int)HPLMM_ERR_TIMEOUT);
+    // the MMAs must not outlive the tensor memory: wait for the last commit once more before freeing it
+    tc::bar_wait(&bar[last & 1], (uint32_t)((last >> 1) & 1));
+  }
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const int a = a0 + 32 * wid + lane;
+  const int *gc = gcol + gcol_off[g];
+  for (int c0 = 0; c0 < N; c0 += 16) {
+    uint32_t v[16];
+    const uint32_t taddr = dtm + ((uint32_t)(32 * wid) << 16) + (uint32_t)c0;
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+        : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+          "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+        : "r"(taddr)
+        : "memory");
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+    if (ok && a < k) {
+#pragma unroll
+      for (int i = 0; i < 16; ++i) {
+        const int bb = b0 + c0 + i;
+        if (c0 + i < nb) {
+          const double val = (double)__uint_as_float(v[i]);
+          cf_add(cf, gc[a], gc[bb], val);
+          if (Ao) atomicAdd(&Ao[(long long)gc[a] * No + gc[bb]], val);
+        }
+      }
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (wid == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(dtm), "r"(tc::TMEM_COLS) : "memory");
 }
 
 __global__ void k_symmetrize(double *A, long long N, double *asym) {
@@ -781,23 +995,48 @@ void galerkin(hplmm_ctx *c, const Buf<int> &gbox, const std::vector<long long> &
     k_gal_Y<T><<<gy, 128, 0, s>>>(gbox.p, gal_off.p, c->kg.p, c->vgrain.p, c->mask.p, c->E.p, c->nx, c->ny, c->nz,
                                   c->Kref.p, c->fixed.p, c->grid_to_node.p, g0, base, P, Y);
     HP_CHECK_LAUNCH();
+    // output tiles: 128 x 256 on the tensor cores (each split along the box rows into enough pieces for
+    // about four CTAs per SM over the batch), 32 x 32 on the CUDA cores
+    const bool tensor = std::is_same<T, float>::value && c->opt.tensor_galerkin;
+    const int ta = tensor ? 128 : 32, tb = tensor ? 256 : 32;
     std::vector<int> tiles;
+    int ntile = 0;
+    for (int g = g0; g < g1; ++g) ntile += ((c->h_kg[g] + ta - 1) / ta) * ((c->h_kg[g] + tb - 1) / tb);
+    const int want = 4 * num_sms();
     for (int g = g0; g < g1; ++g) {
       int k = c->h_kg[g];
-      for (int a0 = 0; a0 < k; a0 += 32)
-        for (int b0 = 0; b0 < k; b0 += 32) {
-          tiles.push_back(g);
-          tiles.push_back(a0);
-          tiles.push_back(b0);
-        }
+      const long long nch = ((hgal[g + 1] - hgal[g]) / std::max(k, 1) + 15) / 16;  // 16-row chunks of the box
+      const int split = tensor ? (int)std::max<long long>(1, std::min<long long>(nch / 32, (want + ntile - 1) / std::max(ntile, 1))) : 1;
+      for (int a0 = 0; a0 < k; a0 += ta)
+        for (int b0 = 0; b0 < k; b0 += tb)
+          for (int q = 0; q < split; ++q) {
+            tiles.push_back(g);
+            tiles.push_back(a0);
+            tiles.push_back(b0);
+            if (tensor) {
+              tiles.push_back((int)(nch * q / split));
+              tiles.push_back((int)(nch * (q + 1) / split));
+            }
+          }
     }
     if (!tiles.empty()) {
       HP_CUDA(cudaStreamSynchronize(s));  // the previous batch's tile list is still read until here
       tl.upload(tiles, s);
-      k_gal_gemm<T><<<(unsigned)(tiles.size() / 3), 256, 0, s>>>(tl.p, gbox.p, gal_off.p, c->kg.p, gcol_off.p,
-                                                                 gcol.p, P, Y, base, cv,
-                                                                 c->dense_ao ? c->Ao.p : nullptr, c->n_coarse);
-      HP_CHECK_LAUNCH();
+      if constexpr (std::is_same<T, float>::value) {
+        if (tensor) {
+          HP_CUDA(cudaFuncSetAttribute(k_gal_gemm_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, tc::SMEM_BYTES));
+          k_gal_gemm_tc<<<(unsigned)(tiles.size() / 5), 128, tc::SMEM_BYTES, s>>>(
+              tl.p, gbox.p, gal_off.p, c->kg.p, gcol_off.p, gcol.p, P, Y, base, cv, c->dense_ao ? c->Ao.p : nullptr,
+              c->n_coarse, c->status.p);
+          HP_CHECK_LAUNCH();
+        }
+      }
+      if (!tensor) {
+        k_gal_gemm<T><<<(unsigned)(tiles.size() / 3), 256, 0, s>>>(tl.p, gbox.p, gal_off.p, c->kg.p, gcol_off.p,
+                                                                   gcol.p, P, Y, base, cv,
+                                                                   c->dense_ao ? c->Ao.p : nullptr, c->n_coarse);
+        HP_CHECK_LAUNCH();
+      }
     }
     g0 = g1;
   }
