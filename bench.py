@@ -48,7 +48,7 @@ PLAIN = dict(local_prec="fp64", apply_prec="fp64")
 FP64_TUNED = dict(local_prec="fp64", apply_prec="fp64", use_graph=True, autotune=True)
 
 WORKLOADS = {
-    "fractured256": dict(image=[256, 256, 256], porosity=0.25, grains=[16, 16, 16], n_mortar=2, chosen=BF16,
+    "fractured256": dict(image=[256, 256, 256], porosity=0.25, grains=[16, 16, 16], n_mortar=4, chosen=BF16,
                          plain_fits=False, baseline_config=4,
                          form_text=("BF16 local factors and basis panels (FP32 factorisation in chunks), FP32 "
                                     "residual updates and arithmetic, FP64 sparse coarse Cholesky and FGMRES; "

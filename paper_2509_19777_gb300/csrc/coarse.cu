@@ -259,9 +259,10 @@ __global__ void __launch_bounds__(256) k_gal_gemm(const int *tiles, const int *g
 }
 
 // ---- the Galerkin product on the 5th-generation tensor cores (FP32 forms): C = P^T Y per grain with
-// tcgen05.mma kind::tf32 and the accumulator in tensor memory.  FP32 accuracy from three TF32 products per
-// pair of operands (x = x_hi + x_lo with x_hi the value truncated to TF32 and x_lo = x - x_hi exact in FP32:
-// hi*hi + hi*lo + lo*hi; the dropped lo*lo term and the TF32 truncation of lo are near 2^-22 of the product).
+// tcgen05.mma kind::tf32 and the accumulator in tensor memory.  Near-FP32 accuracy from three TF32 products
+// per pair of operands (x = x_hi + x_lo with x_hi the value rounded to TF32 and x_lo = x - x_hi exact in
+// FP32: hi*hi + hi*lo + lo*hi; the dropped lo*lo term and the TF32 truncation of lo are below 2^-22 of the
+// product).
 // CTA = (grain, 128 columns a of P, up to 256 columns b of Y): 128 threads stage 16 box rows of both operands
 // per step into shared memory in the canonical K-major layout without swizzle (8-row x 16-byte core
 // matrices; core matrices along K 128 bytes apart, 8-row groups 512 bytes apart), two stages; one thread
@@ -297,8 +298,12 @@ __device__ __forceinline__ uint32_t idesc_tf32(int n) {
          | ((uint32_t)(128 >> 4) << 24);  // M / 16
 }
 
+// x = hi + lo exactly, hi = x rounded to the nearest TF32 value (|lo| <= 2^-12 |x|); the tensor core then
+// truncates lo to TF32, an error of at most 2^-23 |x|
 __device__ __forceinline__ void split_tf32(float x, float &hi, float &lo) {
-  hi = __uint_as_float(__float_as_uint(x) & 0xffffe000u);
+  uint32_t h;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(h) : "f"(x));
+  hi = __uint_as_float(h);
   lo = x - hi;
 }
 
@@ -1213,6 +1218,10 @@ void coarse_finish(hplmm_ctx *c) {
     cf_factor(c);
   }
   HP_CUDA(cudaStreamSynchronize(s));
+  // BF16 form: after the Galerkin product (the last reader of the FP32 panels) the apply and the inspection
+  // calls read only the BF16 copy; the FP32 panels stay only when the warm-start collection will read them
+  // as training targets
+  if (c->X16.p && !c->opt.keep_basis_rhs) c->X32.release();
 }
 
 void build_coarse(hplmm_ctx *c, const double *b_corr) {
@@ -1360,10 +1369,16 @@ void prolong_column(hplmm_ctx *c, long long col, double *out_pad) {
   double one = 1.0;
   HP_CUDA(cudaMemcpyAsync(u + col, &one, sizeof(double), cudaMemcpyHostToDevice, s));
   dim3 gp(64, G);
+  int nmax = 1;
+  for (int g = 0; g < G; ++g) nmax = std::max(nmax, c->grains.h_n[g]);
   if (f64)
     k_prolong_grain<double, double><<<gp, 256, 0, s>>>(c->grains.node_off.p, c->grains.n.p, c->grains.lnodes.p,
                                                        c->kg.p, c->panel_off.p, c->X64.p, c->gcol_off.p, c->gcol.p, u,
                                                        out_pad);
+  else if (c->X16.p)
+    k_prolong_grain_cm<false><<<dim3((cm_ld(nmax) + CM_ROWS - 1) / CM_ROWS, G), 256, 0, s>>>(
+        c->grains.node_off.p, c->grains.n.p, c->grains.lnodes.p, c->kg.p, c->panel_off_cm.p, c->X16.p,
+        c->gcol_off.p, c->gcol.p, u, 0, out_pad, 0, 1);
   else
     k_prolong_grain<float, float><<<gp, 256, 0, s>>>(c->grains.node_off.p, c->grains.n.p, c->grains.lnodes.p,
                                                      c->kg.p, c->panel_off.p, c->X32.p, c->gcol_off.p, c->gcol.p, u,

@@ -656,8 +656,8 @@ static void ws_fill(hplmm_ctx *c, long long j0, int B, const float *rhs_panel, c
 long long ws_collect(hplmm_ctx *c) {
   auto &w = c->ws;
   HP_REQUIRE(c->setup_done, HPLMM_ERR_STATE, "call hplmm_setup first");
-  HP_REQUIRE(c->opt.local_prec == HPLMM_FP32 && c->Xrhs.n > 1, HPLMM_ERR_STATE,
-             "collecting warm-start samples needs a set-up with local_prec = FP32 and warm_start_keep = 1");
+  HP_REQUIRE(c->opt.local_prec == HPLMM_FP32 && c->Xrhs.n > 1 && c->X32.p != nullptr, HPLMM_ERR_STATE,
+             "collecting warm-start samples needs a set-up with local_prec = FP32 and keep_basis_rhs = 1");
   ws_prepare(c, c->Xrhs.p, c->X32.p);
   if (w.S == 0) return w.n_samples;
   const long long S5 = 5LL * WS_D3, S3 = 3LL * WS_D3;
