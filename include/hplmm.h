@@ -96,6 +96,10 @@ typedef struct {
                             tensor cores (tcgen05.mma kind::tf32, three TF32 products per pair of FP32 operands,
                             FP32 accumulation in tensor memory), 0 on the FP32 CUDA cores; the FP64 form always
                             uses FP64 CUDA cores */
+  int tensor_coarse;     /* Schur updates of the coarse multifrontal Cholesky: 1 (default) on the tensor cores in
+                            FP64 by the Ozaki splitting scheme (each row cut to 56-bit fixed point in seven BF16
+                            digits, digit products exact in FP32, FP64 recombination; FP64-accurate), 0 on the
+                            FP64 CUDA cores */
 } hplmm_options;
 
 enum { HPLMM_BASIS_DIRECT = 0, HPLMM_BASIS_PCG = 1, HPLMM_BASIS_PCG_WARM = 2 };

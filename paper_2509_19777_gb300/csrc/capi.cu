@@ -98,6 +98,7 @@ void validate_options(const hplmm_options &o) {
   HP_REQUIRE(o.stage_mb >= 0, HPLMM_ERR_INVALID, "stage_mb must be non-negative");
   HP_REQUIRE(o.wait_budget_us >= 0, HPLMM_ERR_INVALID, "wait_budget_us must be non-negative");
   HP_REQUIRE(o.tensor_galerkin == 0 || o.tensor_galerkin == 1, HPLMM_ERR_INVALID, "tensor_galerkin must be 0 or 1");
+  HP_REQUIRE(o.tensor_coarse == 0 || o.tensor_coarse == 1, HPLMM_ERR_INVALID, "tensor_coarse must be 0 or 1");
 }
 
 void require_setup(hplmm_ctx *c) {
@@ -150,6 +151,7 @@ void hplmm_default_options(hplmm_options *o) {
   o->keep_basis_rhs = 0;
   o->smoother_ctas = 0;
   o->tensor_galerkin = 1;
+  o->tensor_coarse = 1;
 }
 
 hplmm_status hplmm_create(hplmm_ctx **ctx, const hplmm_options *opt, void *cuda_stream) {

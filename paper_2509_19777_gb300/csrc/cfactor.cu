@@ -28,7 +28,10 @@ namespace {
 constexpr int CT = 64;        // tile edge of the front factorisation
 constexpr int CF_AMIN = 64;   // fronts with fewer pivot columns are merged into their parents
 
-enum Kind { K_POTRF = 0, K_TRSM, K_SYRK, K_TRINV_SCALE, K_TRINV_UPDATE, K_EXTEND, K_FWD_Y, K_FWD_B, K_BWD_B, K_BWD_Y };
+enum Kind {
+  K_POTRF = 0, K_TRSM, K_SYRK, K_TRINV_SCALE, K_TRINV_UPDATE, K_EXTEND, K_FWD_Y, K_FWD_B, K_BWD_B, K_BWD_Y,
+  K_OZ_SLICE, K_OZ_SYRK
+};
 
 inline long long rup(long long a, long long b) { return (a + b - 1) / b * b; }
 
@@ -249,6 +252,238 @@ __global__ void __launch_bounds__(256) k_cf_syrk(const FTask *tasks, const long 
       const int r = ty + 16 * u, cc = tx + 16 * v;
       if (r < nbi && cc < nbj && (tk.b != tk.c || cc <= r)) A[(long long)(i0 + r) * N + j0 + cc] -= acc[u][v];
     }
+}
+
+// ---- the Schur update on the tensor cores, FP64 by the Ozaki splitting scheme (Ozaki, Ogita, Oishi and Rump,
+// "Error-free transformations of matrix multiplication by using fast routines of matrix multiplication and
+// its applications", Numer. Algorithms 59, 2012).  Each row r of the panel column block kt is scaled by
+// 2^-e_r with 2^e_r above the row's largest magnitude and cut to a 56-bit fixed-point integer M (truncated:
+// an error below 2^-56 of the row's largest entry), written in base 256 as M = sum_p d_p 256^(6-p) with
+// d_0 in [-256, 255] and d_1 .. d_6 in [0, 255]: every digit is exact in BF16.  A digit product summed over
+// the tile's 64 columns is below 2^22 in magnitude, so tcgen05.mma kind::f16 (BF16 operands, FP32
+// accumulation) computes it exactly; the products of one group g = p + q are accumulated in the same 64 TMEM
+// columns (exact up to g = 3; from g = 4 on the FP32 rounding lies below 2^-52 of the leading group), and
+// the groups g <= 6 are kept (the dropped ones lie below 2^-53 of |L_i||L_j|).  Then
+// (L_i L_j^T)_ab = 2^(e_a + e_b - 64) sum_g 256^(6-g) D_g, recombined in FP64 by Horner's rule.
+// CTA = 128 rows (two tiles of the column below the diagonal) x one 64-column tile, 128 threads: all seven
+// digits of both operands are staged at once in the canonical K-major no-swizzle layout (168 KB), one
+// thread issues the 28 x 4 MMAs (M = 128, N = 64, K = 16), one commit; each thread then reads its row's
+// seven accumulators back with tcgen05.ld.
+namespace oz {
+constexpr int ND = 7;                         // base-256 digits per value
+constexpr int A_BYTES = 128 * CT * 2;         // one digit of the 128-row operand (16 KB)
+constexpr int B_BYTES = CT * CT * 2;          // one digit of the 64-row operand (8 KB)
+constexpr int SMEM = ND * (A_BYTES + B_BYTES);  // 168 KB
+constexpr int TMEM_COLS = 512;                // 7 groups x 64 columns
+constexpr long long WAIT_CYCLES = 2000000000LL;
+
+__device__ __forceinline__ uint32_t su32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+// byte offset of BF16 element (row, k), k a multiple of 8, in a K-major no-swizzle tile of 64 columns:
+// 8-row x 16-byte core matrices, 128 bytes apart along K, 8-row groups 1024 bytes apart
+__device__ __forceinline__ int off8(int row, int k) { return (row >> 3) * 1024 + (k >> 3) * 128 + (row & 7) * 16; }
+__device__ __forceinline__ uint64_t sdesc(uint32_t addr) {
+  const uint64_t lbo = 128 >> 4, sbo = 1024 >> 4;
+  return (uint64_t)((addr >> 4) & 0x3fff) | (lbo << 16) | (sbo << 32) | (1ull << 46);
+}
+// kind::f16 instruction descriptor: D F32, A and B BF16 (K-major), N = 64, M = 128
+__device__ __forceinline__ uint32_t idesc() {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(64 >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
+}
+__device__ __forceinline__ void mma(uint32_t dtm, uint64_t a, uint64_t b, uint32_t id, int acc) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(dtm),
+      "l"(a), "l"(b), "r"(id), "r"(acc)
+      : "memory");
+}
+}  // namespace oz
+
+// digits of the 64 rows of panel tile (it, kt) of a front (TRSM task {f, kt, it}): slot = the task's index,
+// S[slot][digit][row][64 columns] and E[slot][row]
+__global__ void __launch_bounds__(256) k_cf_oz_slice(const FTask *tasks, const long long *foff, const int *mv,
+                                                     const double *Fr, __nv_bfloat16 *S, int *E) {
+  const FTask tk = tasks[blockIdx.x];
+  const long long m = mv[tk.f];
+  const double *A = Fr + foff[tk.f];
+  const int i0 = tk.b * CT, k0 = tk.a * CT;
+  const int r = threadIdx.x >> 2, q = threadIdx.x & 3;  // row, quarter of its 64 columns
+  const long long row = i0 + r;
+  double v[16];
+  double mx = 0.0;
+#pragma unroll
+  for (int e = 0; e < 16; ++e) {
+    v[e] = row < m ? A[row * m + k0 + 16 * q + e] : 0.0;
+    mx = fmax(mx, fabs(v[e]));
+  }
+  mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, 1));
+  mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, 2));
+  int ex = 0;
+  if (mx > 0.0) frexp(mx, &ex);  // mx < 2^ex
+  if (q == 0) E[(long long)blockIdx.x * CT + r] = ex;
+  __nv_bfloat16 *Sd = S + (long long)blockIdx.x * oz::ND * CT * CT;
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    long long M[8];
+#pragma unroll
+    for (int e = 0; e < 8; ++e) M[e] = __double2ll_rz(ldexp(v[8 * h + e], 56 - ex));
+#pragma unroll
+    for (int d = 0; d < oz::ND; ++d) {
+      __align__(16) __nv_bfloat16 o[8];
+#pragma unroll
+      for (int e = 0; e < 8; ++e) {
+        const int dig = d == 0 ? (int)(M[e] >> 48) : (int)((M[e] >> (8 * (6 - d))) & 255);
+        o[e] = __int2bfloat16_rn(dig);
+      }
+      *reinterpret_cast<uint4 *>(Sd + ((long long)d * CT + r) * CT + 16 * q + 8 * h) = *reinterpret_cast<uint4 *>(o);
+    }
+  }
+}
+
+// F[rows of tiles it, it+1][tile jt] -= L L^T on the tensor cores (task {f, kt, it, jt, slot(it), slot(jt)});
+// 256 threads: all stage (eight 16-byte loads in flight per thread), warp w reads TMEM lanes 32 (w mod 4)
+// .. + 31 and columns 32 (w / 4) .. + 31 of every group.  The groups are recombined in 64-bit integers:
+// sum_{g<=5} D_g 256^(5-g) + floor(D_6 / 256) stays below 2^63 (|D_0| < 2^22), and the dropped fraction is
+// below 2^-62 of it; one conversion to FP64 and a scaling by 2^(e_a + e_b - 56) follow.
+constexpr int OZ_THREADS = 256;
+__global__ void __launch_bounds__(OZ_THREADS) k_cf_oz_syrk(const int *otask, const long long *foff, const int *mv,
+                                                           double *Fr, const __nv_bfloat16 *S, const int *E,
+                                                           int *status) {
+  extern __shared__ __align__(1024) unsigned char osm[];
+  __shared__ __align__(8) uint64_t bar;
+  __shared__ uint32_t tmem_base;
+  const int tid = threadIdx.x, wid = tid >> 5, lane = tid & 31;
+  const int *t = otask + 6LL * blockIdx.x;
+  const int f = t[0], it = t[2], jt = t[3], si = t[4], sj = t[5];
+  const long long m = mv[f];
+  double *A = Fr + foff[f];
+  const int Tf = (int)((m + CT - 1) / CT);
+  const bool two = it + 1 < Tf;
+  if (wid == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(oz::su32(&tmem_base)),
+                 "r"(oz::TMEM_COLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  if (tid == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(oz::su32(&bar)) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  // stage the digits: A rows 0..63 from slot si, 64..127 from slot si + 1 (zero rows past the front), then B
+  constexpr int NA = oz::ND * 128 * 8, NBC = oz::ND * 64 * 8;  // 16-byte chunks
+  unsigned char *Bs = osm + oz::ND * oz::A_BYTES;
+  for (int c0 = tid; c0 < NA + NBC; c0 += 8 * OZ_THREADS) {
+    uint4 v[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int c = c0 + u * OZ_THREADS;
+      v[u] = make_uint4(0u, 0u, 0u, 0u);
+      if (c < NA) {
+        const int d = c >> 10, row = (c >> 3) & 127, kc = c & 7;
+        if (row < 64 || two) {
+          const int slot = row < 64 ? si : si + 1;
+          v[u] = __ldg(reinterpret_cast<const uint4 *>(S + (((long long)slot * oz::ND + d) * CT + (row & 63)) * CT +
+                                                      8 * kc));
+        }
+      } else if (c < NA + NBC) {
+        const int cb = c - NA, d = cb >> 9, row = (cb >> 3) & 63, kc = cb & 7;
+        v[u] = __ldg(reinterpret_cast<const uint4 *>(S + (((long long)sj * oz::ND + d) * CT + row) * CT + 8 * kc));
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int c = c0 + u * OZ_THREADS;
+      if (c < NA) {
+        const int d = c >> 10, row = (c >> 3) & 127, kc = c & 7;
+        *reinterpret_cast<uint4 *>(osm + d * oz::A_BYTES + oz::off8(row, 8 * kc)) = v[u];
+      } else if (c < NA + NBC) {
+        const int cb = c - NA, d = cb >> 9, row = (cb >> 3) & 63, kc = cb & 7;
+        *reinterpret_cast<uint4 *>(Bs + d * oz::B_BYTES + oz::off8(row, 8 * kc)) = v[u];
+      }
+    }
+  }
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t dtm = tmem_base;
+  if (tid == 0) {
+    const uint32_t id = oz::idesc();
+    const uint32_t abase = oz::su32(osm), bbase = oz::su32(Bs);
+    for (int p = 0; p < oz::ND; ++p)
+      for (int q = 0; p + q < oz::ND; ++q) {
+        const int g = p + q;
+        for (int ks = 0; ks < CT / 16; ++ks) {
+          const uint64_t ad = oz::sdesc(abase + p * oz::A_BYTES + ks * 256);
+          const uint64_t bd = oz::sdesc(bbase + q * oz::B_BYTES + ks * 256);
+          // the loop meets every group first at p = 0, which starts its accumulator
+          oz::mma(dtm + (uint32_t)(g * 64), ad, bd, id, (p > 0 || ks > 0) ? 1 : 0);
+        }
+      }
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(oz::su32(&bar))
+                 : "memory");
+  }
+  bool ok = true;
+  for (int attempt = 0; attempt < 2; ++attempt) {
+    // the second (longer) wait only after a timeout: the MMAs must not outlive the tensor memory
+    const long long t0 = clock64(), budget = (attempt + 1) * oz::WAIT_CYCLES;
+    bool done = false;
+    for (;;) {
+      uint32_t d;
+      asm volatile(
+          "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], 0;\n selp.b32 %0, 1, 0, p;\n}\n"
+          : "=r"(d)
+          : "r"(oz::su32(&bar))
+          : "memory");
+      if (d) {
+        done = true;
+        break;
+      }
+      if (clock64() - t0 > budget) break;
+    }
+    if (done) break;
+    if (ok) atomicCAS(status, 0, (int)HPLMM_ERR_TIMEOUT);
+    ok = false;
+  }
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const int r = 32 * (wid & 3) + lane;            // row of the 128-row block
+  const int ch = wid >> 2;                         // column half
+  const long long grow = (long long)it * CT + r;   // row in the front
+  const int rtile = it + (r >> 6);
+  const int ei = E[(long long)(r < 64 ? si : si + 1) * CT + (r & 63)];
+  for (int c0 = 32 * ch; c0 < 32 * ch + 32; c0 += 16) {
+    long long acc[16];
+#pragma unroll
+    for (int i = 0; i < 16; ++i) acc[i] = 0;
+    for (int g = 0; g < oz::ND; ++g) {
+      uint32_t u[16];
+      const uint32_t taddr = dtm + ((uint32_t)(32 * (wid & 3)) << 16) + (uint32_t)(g * 64 + c0);
+      asm volatile(
+          "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+          : "=r"(u[0]), "=r"(u[1]), "=r"(u[2]), "=r"(u[3]), "=r"(u[4]), "=r"(u[5]), "=r"(u[6]), "=r"(u[7]),
+            "=r"(u[8]), "=r"(u[9]), "=r"(u[10]), "=r"(u[11]), "=r"(u[12]), "=r"(u[13]), "=r"(u[14]), "=r"(u[15])
+          : "r"(taddr)
+          : "memory");
+      asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+      for (int i = 0; i < 16; ++i) {
+        const long long v = (long long)__float2int_rn(__uint_as_float(u[i]));  // an integer below 2^26
+        acc[i] += g < 6 ? (v << (8 * (5 - g))) : (v >> 8);
+      }
+    }
+    if (ok && grow < m) {
+#pragma unroll
+      for (int i = 0; i < 16; ++i) {
+        const int cc = c0 + i;
+        const long long col = (long long)jt * CT + cc;
+        if (col < m && (rtile != jt || cc <= (r & 63)) && acc[i] != 0)
+          A[grow * m + col] -= ldexp((double)acc[i], ei + E[(long long)sj * CT + cc] - 56);
+      }
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (wid == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(dtm), "r"(oz::TMEM_COLS) : "memory");
 }
 
 // Explicit inverse of the pivot block, Y = inv(L_pp) (P x P, row-major), by right-looking block
@@ -775,7 +1010,9 @@ void cf_analyse(hplmm_ctx *c, const std::vector<int> &gbox) {
   // diagonal tile, panel tiles below it, Schur update of the trailing tiles, inverse steps; then the
   // extend-add of the level's update blocks into their parents.
   std::vector<FTask> tk;
+  std::vector<int> ot;  // tensor-core Schur update tasks, six ints each
   F.fact.clear();
+  F.oz_slots = 0;
   auto push = [&](std::vector<FLaunch> &L, int kind, int kt, long long off) {
     const int cnt = (int)((long long)tk.size() - off);
     if (cnt > 0) L.push_back({kind, kt, off, cnt});
@@ -796,15 +1033,40 @@ void cf_analyse(hplmm_ctx *c, const std::vector<int> &gbox) {
         const int Tf = (int)((F.h_m[f] + CT - 1) / CT);
         for (int it = kt + 1; it < Tf; ++it) tk.push_back({f, kt, it, 0});
       }
+      const long long o_trsm = o;
       push(F.fact, K_TRSM, kt, o);
-      o = (long long)tk.size();
-      for (int f : lev[h]) {
-        if (F.h_P[f] / CT <= kt) continue;
-        const int Tf = (int)((F.h_m[f] + CT - 1) / CT);
-        for (int it = kt + 1; it < Tf; ++it)
-          for (int jt = kt + 1; jt <= it; ++jt) tk.push_back({f, kt, it, jt});
+      if (c->opt.tensor_coarse) {
+        // the Schur update on the tensor cores: digits of the panel tiles (one slot per TRSM task, in the same
+        // order), then one task per (pair of row tiles it, it + 1; column tile jt)
+        const int nslot = (int)((long long)tk.size() - o_trsm);
+        if (nslot > 0) {
+          F.fact.push_back({K_OZ_SLICE, kt, o_trsm, nslot});
+          F.oz_slots = std::max<long long>(F.oz_slots, nslot);
+          const long long ot0 = (long long)ot.size() / 6;
+          int base = 0;
+          for (int f : lev[h]) {
+            if (F.h_P[f] / CT <= kt) continue;
+            const int Tf = (int)((F.h_m[f] + CT - 1) / CT);
+            for (int jt = kt + 1; jt < Tf; ++jt)
+              for (int it = jt; it < Tf; it += 2) {
+                const int tsk[6] = {f, kt, it, jt, base + it - kt - 1, base + jt - kt - 1};
+                ot.insert(ot.end(), tsk, tsk + 6);
+              }
+            base += Tf - kt - 1;
+          }
+          const int cnt = (int)((long long)ot.size() / 6 - ot0);
+          if (cnt > 0) F.fact.push_back({K_OZ_SYRK, kt, ot0, cnt});
+        }
+      } else {
+        o = (long long)tk.size();
+        for (int f : lev[h]) {
+          if (F.h_P[f] / CT <= kt) continue;
+          const int Tf = (int)((F.h_m[f] + CT - 1) / CT);
+          for (int it = kt + 1; it < Tf; ++it)
+            for (int jt = kt + 1; jt <= it; ++jt) tk.push_back({f, kt, it, jt});
+        }
+        push(F.fact, K_SYRK, kt, o);
       }
-      push(F.fact, K_SYRK, kt, o);
       o = (long long)tk.size();
       for (int f : lev[h]) {
         if (F.h_P[f] / CT <= kt) continue;
@@ -855,6 +1117,15 @@ void cf_analyse(hplmm_ctx *c, const std::vector<int> &gbox) {
   }
   if (tk.empty()) tk.push_back({0, 0, 0, 0});
   F.tasks.upload(tk, s);
+  if (ot.empty()) ot.assign(6, 0);
+  F.otask.upload(ot, s);
+  if (F.oz_slots > 0) {
+    F.oz_S.alloc((size_t)F.oz_slots * 7 * CT * CT);
+    F.oz_E.alloc((size_t)F.oz_slots * CT);
+  } else {
+    F.oz_S.release();
+    F.oz_E.release();
+  }
   HP_CUDA(cudaStreamSynchronize(s));
 }
 
@@ -895,6 +1166,14 @@ void cf_factor(hplmm_ctx *c) {
       case K_EXTEND:
         k_cf_extend<<<L.count, 256, 0, s>>>(t, F.m.p, F.P.p, F.bdev(), F.parent.p,
                                             F.foff.p, F.roff.p, F.rel.p, F.F.p);
+        break;
+      case K_OZ_SLICE:
+        k_cf_oz_slice<<<L.count, 256, 0, s>>>(t, F.foff.p, F.m.p, F.F.p, F.oz_S.p, F.oz_E.p);
+        break;
+      case K_OZ_SYRK:
+        HP_CUDA(cudaFuncSetAttribute(k_cf_oz_syrk, cudaFuncAttributeMaxDynamicSharedMemorySize, oz::SMEM));
+        k_cf_oz_syrk<<<L.count, OZ_THREADS, oz::SMEM, s>>>(F.otask.p + 6 * L.off, F.foff.p, F.m.p, F.F.p, F.oz_S.p,
+                                                     F.oz_E.p, c->status.p);
         break;
       default:
         throw Error(HPLMM_ERR_INVALID, "coarse factor: bad launch kind");

@@ -180,6 +180,10 @@ struct CoarseFactor {
   Buf<double> Y;    // per front: inv(L_pp), P x P row-major
   Buf<double> D;    // per front: inverses of the 64 x 64 diagonal tiles of L_pp
   Buf<FTask> tasks;
+  Buf<int> otask;                       // tensor-core Schur update tasks: f, kt, it, jt, slot(it), slot(jt)
+  Buf<__nv_bfloat16> oz_S;              // base-256 digits of one step's panel tiles (7 per value)
+  Buf<int> oz_E;                        // their per-row exponents
+  long long oz_slots = 0;
   std::vector<FLaunch> fact;            // factorisation launches, in order
   std::vector<std::vector<FLaunch>> fwd, bwd;  // solve launches per level (forward ascending, backward
                                                // descending levels)
