@@ -216,6 +216,21 @@ hplmm_status hplmm_solve(hplmm_ctx *ctx, const double *b, double *x, double tol,
 hplmm_status hplmm_apply_multi(hplmm_ctx *ctx, const double *R, double *Z, int k);
 hplmm_status hplmm_solve_multi(hplmm_ctx *ctx, const double *B, double *X, int k, double tol, hplmm_stats *st);
 
+/* Saving and reloading a set-up (the set-up is built once and reused, Sections 1, 6.3 and 7.4).
+ * hplmm_save_setup writes everything hplmm_setup computed -- decomposition and maps, mortars, local factors
+ * and layouts, basis panels, the coarse factor and its schedules, the tuner's plans -- to the file at path
+ * (HOST, NUL-terminated; overwritten), after a header with the set-up options and a fingerprint of the
+ * assembled system.  hplmm_load_setup reads such a file into a context that has been assembled on the same
+ * system with the same set-up options (n_mortar, beta, contact_halfwidth, n_st, local_prec, apply_prec,
+ * strict_two_grain, basis_solver, mortar_kind): apply and solve then behave as on the saved context, and
+ * no hplmm_setup is needed.  Errors: HPLMM_ERR_STATE (no set-up to save; not assembled before a load),
+ * HPLMM_ERR_INVALID (file unreadable, unwritable or of another format, or saved for another system or
+ * other options; the context's previous set-up is then gone and hplmm_setup or a good load must follow),
+ * HPLMM_ERR_OOM.  Both synchronise.  The file holds the factors in their stored precision (about the
+ * device memory the set-up uses). */
+hplmm_status hplmm_save_setup(hplmm_ctx *ctx, const char *path);
+hplmm_status hplmm_load_setup(hplmm_ctx *ctx, const char *path);
+
 /* Sizes of the index maps, for hplmm_get_maps.  HOST outputs. */
 typedef struct {
   long long n_nodes;        /* existing fine nodes */

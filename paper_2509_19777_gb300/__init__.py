@@ -41,6 +41,7 @@ EXPORTED = [
     "hplmm_ws_num_params", "hplmm_ws_set_params", "hplmm_ws_get_params", "hplmm_ws_collect", "hplmm_ws_clear",
     "hplmm_ws_train", "hplmm_ws_loss_grad", "hplmm_get_basis_stats", "hplmm_ws_get_samples",
     "hplmm_inject_alloc_failure", "hplmm_apply_multi", "hplmm_solve_multi", "hplmm_ws_predict",
+    "hplmm_save_setup", "hplmm_load_setup",
 ]
 PHASES = ["maps", "factor_grains", "factor_contacts", "basis_rhs", "basis_solve", "galerkin", "coarse_chol",
           "apply_coarse", "apply_contacts", "apply_grains", "spmv", "krylov", "apply_graph"]
@@ -131,6 +132,8 @@ def load_library():
         "hplmm_kernel_launches": (LL, []),
         "hplmm_inject_alloc_failure": (None, [LL]),
         "hplmm_apply_multi": (I, [P, P, P, I]),
+        "hplmm_save_setup": (I, [P, ctypes.c_char_p]),
+        "hplmm_load_setup": (I, [P, ctypes.c_char_p]),
         "hplmm_ws_predict": (I, [P, P, P, I]),
         "hplmm_solve_multi": (I, [P, P, P, I, D, ctypes.POINTER(hplmm_stats)]),
         "hplmm_get_costs": (I, [P, ctypes.POINTER(hplmm_costs)]),
@@ -335,6 +338,16 @@ def hplmm_ws_predict(ctx, x, out=None):
     return out
 
 
+def hplmm_save_setup(ctx, path):
+    """Write the context's set-up to the file at path."""
+    _check(ctx, load_library().hplmm_save_setup(ctx, os.fsencode(path)))
+
+
+def hplmm_load_setup(ctx, path):
+    """Read a saved set-up into a context assembled on the same system with the same set-up options."""
+    _check(ctx, load_library().hplmm_load_setup(ctx, os.fsencode(path)))
+
+
 def hplmm_apply_multi(ctx, R, Z):
     """Z[q] = M^{-1} R[q] for the rows q of the [k, n_dof] float64 CUDA tensors R and Z."""
     _check(ctx, load_library().hplmm_apply_multi(ctx, _ptr(R), _ptr(Z), int(R.shape[0])))
@@ -502,6 +515,12 @@ class Solver:
         x = torch.empty(self.n_dof, dtype=torch.float64, device="cuda") if x is None else x
         rc, st = hplmm_solve(self.ctx, b, x, tol)
         return x, rc, st
+
+    def save_setup(self, path):
+        hplmm_save_setup(self.ctx, path)
+
+    def load_setup(self, path):
+        hplmm_load_setup(self.ctx, path)
 
     def apply_multi(self, R, Z=None):
         import torch

@@ -332,6 +332,22 @@ hplmm_status hplmm_solve(hplmm_ctx *c, const double *b, double *x, double tol, h
   return g != HPLMM_OK ? g : rc;
 }
 
+hplmm_status hplmm_save_setup(hplmm_ctx *c, const char *path) {
+  return guarded(c, [&] {
+    require_setup(c);
+    hp::save_setup(c, path);
+  });
+}
+
+hplmm_status hplmm_load_setup(hplmm_ctx *c, const char *path) {
+  return guarded(c, [&] {
+    HP_REQUIRE(c->assembled, HPLMM_ERR_STATE, "call hplmm_assemble first");
+    hp::load_setup(c, path);
+    alloc_work(c);
+    c->setup_done = true;
+  });
+}
+
 hplmm_status hplmm_apply_multi(hplmm_ctx *c, const double *R, double *Z, int k) {
   return guarded(c, [&] {
     require_setup(c);

@@ -25,6 +25,7 @@ struct Error : public std::runtime_error {
   do {                                                                                     \
     cudaError_t e_ = (call);                                                               \
     if (e_ != cudaSuccess) {                                                               \
+      (void)cudaGetLastError(); /* a non-sticky error must not resurface at a later check */ \
       throw ::hp::Error(e_ == cudaErrorMemoryAllocation ? HPLMM_ERR_OOM : HPLMM_ERR_CUDA,  \
                         std::string(#call) + ": " + cudaGetErrorString(e_) + " at " +      \
                             __FILE__ + ":" + std::to_string(__LINE__));                    \
@@ -472,6 +473,9 @@ void prolong_column(hplmm_ctx *c, long long col, double *out_pad);
 void precond_apply(hplmm_ctx *c, const double *r_pad, double *z_pad);
 void precond_apply_any(hplmm_ctx *c, const double *r_pad, double *z_pad);  // graph replay when use_graph
 void drop_apply_graph(hplmm_ctx *c);
+// checkpoint.cu: the set-up's state to a file and back (the context must be assembled on the same system)
+void save_setup(hplmm_ctx *c, const char *path);
+void load_setup(hplmm_ctx *c, const char *path);
 void tune_local(hplmm_ctx *c);
 void smoother_stage(hplmm_ctx *c, const double *r_pad, double *z_pad);
 int fgmres(hplmm_ctx *c, const double *b_pad, double *x_pad, double tol, hplmm_stats *st);

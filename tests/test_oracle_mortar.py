@@ -241,3 +241,37 @@ def test_algebraic_all_nodes_mortars_is_identity():
         assert Q.shape[0] == Q.shape[1] and np.array_equal(Q, np.eye(Q.shape[0]))
     xs = spla.spsolve(sysm.A.tocsc(), sysm.b)
     assert np.linalg.norm(M.M_G(sysm.b) - xs) < 1e-10 * np.linalg.norm(xs)
+
+
+# ---------------------------------------------------------------- the spread beta (Appendix A)
+def test_gaussian_mortars_beta_limits():
+    # Eq. gauss as beta -> infinity: every exponent tends to 0, so the mortars flatten to 1/n_c on the whole
+    # interface (linearly dependent columns); as beta -> 0 each node belongs to the mortar with the smallest
+    # d^2 / dmin^2 (with a symmetric layout, the nearest mortar): indicator functions
+    coords = np.array([[0, y, z] for y in range(7) for z in range(7)])
+    chosen = [0, 6, 42, 48]                        # the four corners: equal nearest-mortar distances
+    eta_inf = gaussian_mortars(coords, chosen, beta=1e12)
+    assert np.abs(eta_inf - 0.25).max() < 1e-10
+    eta_0 = gaussian_mortars(coords, chosen, beta=1e-3)
+    X = coords[chosen]
+    d2 = ((coords[:, None, :] - X[None, :, :]) ** 2).sum(axis=2)
+    for y in range(len(coords)):
+        order = np.sort(d2[y])
+        if order[0] < order[1]:                    # a unique nearest mortar
+            want = np.zeros(4)
+            want[np.argmin(d2[y])] = 1.0
+            assert np.abs(eta_0[y] - want).max() < 1e-12, y
+
+
+def test_coarse_conditioning_grows_with_beta():
+    # Appendix A: the larger beta, the more adjacent mortars overlap and the worse A^o is conditioned
+    import synth
+    from oracle import precond
+    p = synth.make_workload("tiny8", 3)
+    kappa = []
+    for beta in (0.25, 1.0, 4.0, 16.0, 64.0):
+        sysm, M = precond.build(p, precond.Options(n_mortar=2, contact_halfwidth=1, beta=beta))
+        ev = np.linalg.eigvalsh(M.coarse.A_o)
+        assert ev[0] > 0
+        kappa.append(ev[-1] / ev[0])
+    assert all(b > a for a, b in zip(kappa, kappa[1:])), kappa
