@@ -609,28 +609,51 @@ __global__ void __launch_bounds__(256) k_cf_extend(const FTask *tasks, const int
 }
 
 // ---------------------------------------------------------------- coarse solve kernels
-// forward, pivot rows: y[idx_i] = sum_{j <= i} Y[i][j] t[idx_j]; CTA = 32 rows of one front, warp per row
+// Forward kernels: CTA = 32 rows of one front, warp w the rows w, w + 8, w + 16, w + 24 of the block.  The
+// gathered right-hand side (t or y at the front's pivot columns) is staged in shared memory in chunks of
+// FW_CH values, so that each row is a contiguous stream against shared memory, the four rows' loads of a
+// lane are independent (four in flight), and no load waits on an index load.
+constexpr int FW_CH = 2048;
+
+// forward, pivot rows: y[idx_i] = sum_{j <= i} Y[i][j] t[idx_j]
 __global__ void __launch_bounds__(256) k_cf_fwd_y(const FTask *tasks, const int *pv, const int *Pv,
                                                   const long long *yoff, const long long *ioff, const int *idx,
                                                   const double *Yr, const double *t, double *y) {
+  __shared__ double tl[FW_CH];
   const FTask tk = tasks[blockIdx.x];
   const int p = pv[tk.f];
   const long long P = Pv[tk.f];
   const double *Y = Yr + yoff[tk.f];
   const int *ix = idx + ioff[tk.f];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  for (int r = tk.a + wid; r < min(tk.a + 32, p); r += 8) {
-    const double *yr = Y + r * P;
-    double s0 = 0.0, s1 = 0.0;
-    int j = lane;
-    for (; j + 32 <= r; j += 64) {
-      s0 += yr[j] * t[ix[j]];
-      s1 += yr[j + 32] * t[ix[j + 32]];
+  const int rend = min(tk.a + 32, p);
+  double acc[4] = {0.0, 0.0, 0.0, 0.0};
+  for (int j0 = 0; j0 < rend; j0 += FW_CH) {
+    const int jn = min(FW_CH, rend - j0);
+    __syncthreads();
+    for (int j = threadIdx.x; j < jn; j += blockDim.x) tl[j] = t[ix[j0 + j]];
+    __syncthreads();
+    const double *yr[4];
+    int lim[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int r = tk.a + wid + 8 * u;
+      lim[u] = r < rend ? min(jn, r - j0 + 1) : 0;  // row r reads columns j <= r
+      yr[u] = Y + (long long)(r < rend ? r : tk.a) * P + j0;
     }
-    if (j <= r) s0 += yr[j] * t[ix[j]];
-    double s = s0 + s1;
-    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
-    if (lane == 0) y[ix[r]] = s;
+    for (int j = lane; j < lim[0] || j < lim[1] || j < lim[2] || j < lim[3]; j += 32) {
+      const double tv = tl[j];
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+        if (j < lim[u]) acc[u] = fma(yr[u][j], tv, acc[u]);
+    }
+  }
+#pragma unroll
+  for (int u = 0; u < 4; ++u) {
+    double sum = acc[u];
+    for (int o = 16; o > 0; o >>= 1) sum += __shfl_down_sync(0xffffffffu, sum, o);
+    const int r = tk.a + wid + 8 * u;
+    if (lane == 0 && r < rend) y[ix[r]] = sum;
   }
 }
 
@@ -639,24 +662,41 @@ __global__ void __launch_bounds__(256) k_cf_fwd_y(const FTask *tasks, const int 
 __global__ void __launch_bounds__(256) k_cf_fwd_b(const FTask *tasks, const int *pv, const int *Pv, const int *bv,
                                                   const int *mv, const long long *foff, const long long *ioff,
                                                   const int *idx, const double *Fr, const double *y, double *t) {
+  __shared__ double yl[FW_CH];
   const FTask tk = tasks[blockIdx.x];
   const int p = pv[tk.f], b = bv[tk.f];
   const long long P = Pv[tk.f], m = mv[tk.f];
   const double *L = Fr + foff[tk.f];
   const int *ix = idx + ioff[tk.f];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  for (int r = tk.a + wid; r < min(tk.a + 32, b); r += 8) {
-    const double *lr = L + (P + r) * m;
-    double s0 = 0.0, s1 = 0.0;
-    int j = lane;
-    for (; j + 32 < p; j += 64) {
-      s0 += lr[j] * y[ix[j]];
-      s1 += lr[j + 32] * y[ix[j + 32]];
+  const int rend = min(tk.a + 32, b);
+  double acc[4] = {0.0, 0.0, 0.0, 0.0};
+  for (int j0 = 0; j0 < p; j0 += FW_CH) {
+    const int jn = min(FW_CH, p - j0);
+    __syncthreads();
+    for (int j = threadIdx.x; j < jn; j += blockDim.x) yl[j] = y[ix[j0 + j]];
+    __syncthreads();
+    const double *lr[4];
+    int lim[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int r = tk.a + wid + 8 * u;
+      lim[u] = r < rend ? jn : 0;
+      lr[u] = L + (P + (r < rend ? r : tk.a)) * m + j0;
     }
-    if (j < p) s0 += lr[j] * y[ix[j]];
-    double s = s0 + s1;
-    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
-    if (lane == 0 && s != 0.0) atomicAdd(&t[ix[P + r]], -s);
+    for (int j = lane; j < lim[0]; j += 32) {  // lim[0] is the largest
+      const double yv = yl[j];
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+        if (j < lim[u]) acc[u] = fma(lr[u][j], yv, acc[u]);
+    }
+  }
+#pragma unroll
+  for (int u = 0; u < 4; ++u) {
+    double sum = acc[u];
+    for (int o = 16; o > 0; o >>= 1) sum += __shfl_down_sync(0xffffffffu, sum, o);
+    const int r = tk.a + wid + 8 * u;
+    if (lane == 0 && r < rend && sum != 0.0) atomicAdd(&t[ix[P + r]], -sum);
   }
 }
 
