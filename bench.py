@@ -254,7 +254,11 @@ def apply_bytes(costs, form):
     fb = {"fp64": 8, "fp32": 4, "bf16": 2}[form["apply_prec"]]      # local factors and panels
     ab = 8 if form["apply_prec"] == "fp64" else 4                    # A_hat of the residual updates
     vb = 8 if form["apply_prec"] == "fp64" else 4                    # local vectors of the smoother
-    spmv = 2 * (costs["nnzb"] * (9 * ab + 4) + 3 * n3 * 8)
+    if form["apply_prec"] != "fp64" and costs.get("matrix_free_updates"):
+        # element by element: the vectors (x, sub, y), the moduli and mask, the node map and coordinates
+        spmv = 2 * (3 * n3 * 8 + 5 * costs["n_voxels"] + 4 * costs["n_grid"] + 12 * costs["n_nodes"] + n3)
+    else:
+        spmv = 2 * (costs["nnzb"] * (9 * ab + 4) + 3 * n3 * 8)
     coarse = 2 * costs["panel_elems"] * fb + costs["coarse_solve_bytes"] + 2 * n3 * 8
     local = 2 * (costs["grain_band_elems"] + costs["contact_band_elems"]) * fb
     local += (costs["grain_dofs"] + costs["contact_dofs"]) * (8 + 8 + 4 + 2 * vb)

@@ -100,6 +100,10 @@ typedef struct {
                             FP64 by the Ozaki splitting scheme (each row cut to 56-bit fixed point in seven BF16
                             digits, digit products exact in FP32, FP64 recombination; FP64-accurate), 0 on the
                             FP64 CUDA cores */
+  int matrix_free_updates; /* residual updates r - A_hat z inside the apply of the FP32 and BF16 forms: 1
+                            (default) element by element from the voxel moduli and the reference stiffness, in
+                            FP32 (no matrix read), 0 from the FP32 copy of A_hat (sliced ELL); the FP64 form
+                            and the Krylov products always use the assembled FP64 A_hat */
 } hplmm_options;
 
 enum { HPLMM_BASIS_DIRECT = 0, HPLMM_BASIS_PCG = 1, HPLMM_BASIS_PCG_WARM = 2 };
@@ -320,6 +324,9 @@ typedef struct {
   double coarse_factor_flops;     /* flops of the multifrontal coarse Cholesky (pivot blocks, panels, updates) */
   long long coarse_fronts;        /* fronts of the coarse factor */
   long long coarse_front_bytes;   /* device bytes of the fronts (dense, m x m each) */
+  long long n_voxels;             /* voxels of the image (nx ny nz) */
+  long long n_grid;               /* grid points (nx+1)(ny+1)(nz+1) */
+  int matrix_free_updates;        /* the apply's residual updates are element by element (options) */
 } hplmm_costs;
 
 hplmm_status hplmm_get_costs(hplmm_ctx *ctx, hplmm_costs *out);

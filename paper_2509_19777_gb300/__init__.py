@@ -56,7 +56,7 @@ class hplmm_options(ctypes.Structure):
                 ("basis_max_iters", ctypes.c_int), ("keep_basis_rhs", ctypes.c_int),
                 ("smoother_ctas", ctypes.c_int), ("mortar_kind", ctypes.c_int), ("stage_mb", ctypes.c_int),
                 ("wait_budget_us", ctypes.c_int), ("tensor_galerkin", ctypes.c_int),
-                ("tensor_coarse", ctypes.c_int)]
+                ("tensor_coarse", ctypes.c_int), ("matrix_free_updates", ctypes.c_int)]
 
 
 HPLMM_BASIS_DIRECT, HPLMM_BASIS_PCG, HPLMM_BASIS_PCG_WARM = 0, 1, 2
@@ -96,7 +96,8 @@ class hplmm_costs(ctypes.Structure):
                 ("panel_elems", ctypes.c_longlong), ("local_elem_bytes", ctypes.c_int),
                 ("n_nodes", ctypes.c_longlong), ("sell_blocks", ctypes.c_longlong),
                 ("coarse_solve_bytes", ctypes.c_longlong), ("coarse_factor_flops", ctypes.c_double),
-                ("coarse_fronts", ctypes.c_longlong), ("coarse_front_bytes", ctypes.c_longlong)]
+                ("coarse_fronts", ctypes.c_longlong), ("coarse_front_bytes", ctypes.c_longlong),
+                ("n_voxels", ctypes.c_longlong), ("n_grid", ctypes.c_longlong), ("matrix_free_updates", ctypes.c_int)]
 
 
 _lib = None
@@ -445,7 +446,7 @@ class Solver:
                  restart=30, max_iters=300, strict_two_grain=False, use_graph=False, verbose=False, profile=False,
                  autotune=False, basis_solver="direct", basis_tol=1e-6, basis_max_iters=3000, keep_basis_rhs=False,
                  smoother_ctas=0, mortar_kind="gaussian", stage_mb=0, wait_budget_us=0, tensor_galerkin=True,
-                 tensor_coarse=True, stream=None):
+                 tensor_coarse=True, matrix_free_updates=True, stream=None):
         o = hplmm_default_options()
         o.n_mortar, o.beta, o.contact_halfwidth, o.n_st = n_mortar, beta, contact_halfwidth, n_st
         o.local_prec, o.apply_prec = PREC[local_prec], PREC[apply_prec]
@@ -461,6 +462,7 @@ class Solver:
         o.wait_budget_us = int(wait_budget_us)
         o.tensor_galerkin = int(tensor_galerkin)
         o.tensor_coarse = int(tensor_coarse)
+        o.matrix_free_updates = int(matrix_free_updates)
         self.options = o
         self.ctx = hplmm_create(o, stream)
         self.n_dof = 0

@@ -369,6 +369,78 @@ __global__ void k_spmv_sell(const int *slice_off, const int *scol, const T *sval
   }
 }
 
+// y = A_hat x (or sub - A_hat x) element by element, in FP32 (the residual updates of the FP32 and BF16
+// apply forms): A_hat = sum over solid voxels e of E_e K_ref, so the row block of node n is rebuilt from the
+// moduli of its (up to) eight voxels and the 24 x 24 reference stiffness, which the kernel receives as a
+// parameter (constant memory, read with compile-time offsets).  Thread per node: the 27 neighbours' values
+// into registers (absent neighbours as zeros), then per voxel t = K_ref[corner of n][.] x_voxel and
+// y += E_e t.  Vectors are zero on fixed slots (the columns of fixed DOFs drop out) and the rows of fixed
+// DOFs are zero, as in the assembled A_hat.  It reads the moduli, the node map and the vectors instead of
+// A_hat's 36 bytes per block.
+struct KRef32 {
+  float k[576];
+};
+
+// FP32 copy of a vector: each value is converted once (a node's 27 neighbours would otherwise convert it
+// 27 times, and FP64 -> FP32 conversions run at the FP64 rate)
+__global__ void k_vec_to_f32(const double *x, float *xf, long long n) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) xf[i] = (float)x[i];
+}
+
+__global__ void __launch_bounds__(256) k_spmv_ebe32(const int *node_ijk, int n_nodes, const int *g2n,
+                                                    const uint8_t *mask, const float *E, int nx, int ny, int nz,
+                                                    const __grid_constant__ KRef32 K, const uint8_t *fixed,
+                                                    const float *x, double *y, const double *sub) {
+  const int n = blockIdx.x * blockDim.x + threadIdx.x;
+  if (n >= n_nodes) return;
+  const int i = node_ijk[3 * n], j = node_ijk[3 * n + 1], k = node_ijk[3 * n + 2];
+  const long long NX = nx + 1, NY = ny + 1;
+  float xv[27][3];
+#pragma unroll
+  for (int q = 0; q < 27; ++q) {
+    const int dx = q % 3 - 1, dy = (q / 3) % 3 - 1, dz = q / 9 - 1;
+    const int ii = i + dx, jj = j + dy, kk = k + dz;
+    int m = -1;
+    if (ii >= 0 && jj >= 0 && kk >= 0 && ii <= nx && jj <= ny && kk <= nz) m = g2n[((long long)kk * NY + jj) * NX + ii];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) xv[q][d] = m >= 0 ? x[3LL * m + d] : 0.f;
+  }
+  float acc[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+  for (int oz = 0; oz < 2; ++oz)
+#pragma unroll
+    for (int oy = 0; oy < 2; ++oy)
+#pragma unroll
+      for (int ox = 0; ox < 2; ++ox) {
+        // voxel (i - 1 + ox, j - 1 + oy, k - 1 + oz); node n is its corner (1 - ox, 1 - oy, 1 - oz)
+        const int vx = i - 1 + ox, vy = j - 1 + oy, vz = k - 1 + oz;
+        if (vx < 0 || vy < 0 || vz < 0 || vx >= nx || vy >= ny || vz >= nz) continue;
+        const long long v = ((long long)vz * ny + vy) * nx + vx;
+        if (!mask[v]) continue;
+        const float e = E[v];
+        const int a = (1 - ox) + 2 * (1 - oy) + 4 * (1 - oz);
+        float t[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+        for (int bb = 0; bb < 8; ++bb) {
+          const int cx = bb & 1, cy = (bb >> 1) & 1, cz = bb >> 2;
+          const int q = (ox - 1 + cx + 1) + 3 * (oy - 1 + cy + 1) + 9 * (oz - 1 + cz + 1);
+#pragma unroll
+          for (int d = 0; d < 3; ++d)
+#pragma unroll
+            for (int d2 = 0; d2 < 3; ++d2) t[d] = fmaf(K.k[(3 * a + d) * 24 + 3 * bb + d2], xv[q][d2], t[d]);
+        }
+#pragma unroll
+        for (int d = 0; d < 3; ++d) acc[d] = fmaf(e, t[d], acc[d]);
+      }
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    const long long r = 3LL * n + d;
+    const double av = fixed[r] ? 0.0 : (double)acc[d];
+    y[r] = sub ? sub[r] - av : av;
+  }
+}
+
 // Y_q = A X_q (or SUB_q - A X_q) for up to four vectors q < kc, at stride L: the matrix is read once for the
 // group (the multi-right-hand-side solve shares one preconditioner over several load cases)
 template <typename T>
@@ -482,6 +554,10 @@ void assemble(hplmm_ctx *c, const uint8_t *mask, int nx, int ny, int nz, const f
   c->Kref.alloc(576);
   k_kref<<<1, 576, 0, s>>>(nu, c->Kref.p);
   HP_CHECK_LAUNCH();
+  {
+    const std::vector<double> kh = c->Kref.download(s);
+    c->h_kref32.assign(kh.begin(), kh.end());  // FP32 copy for the element-by-element residual updates
+  }
 
   BCDev bc;
   for (int f = 0; f < 6; ++f)
@@ -571,10 +647,21 @@ void spmv(hplmm_ctx *c, const double *x_pad, double *y_pad, hplmm_prec prec, con
   // the BF16 form keeps A_hat in FP32: its residual updates r - A_hat z subtract nearly equal vectors, and
   // A_hat rounded to BF16 (8-bit significand) left errors of the size of the difference on stiffness
   // contrasts of 1e4 (measured: 300 instead of 178 FGMRES iterations on a fractured 128^3 block)
-  if (prec == HPLMM_FP64)
+  if (prec == HPLMM_FP64) {
     k_spmv_sell<double><<<grid, 64, 0, c->stream>>>(off, col, c->sell_val64.p, perm, x_pad, y_pad, sub, c->n_nodes);
-  else
+  } else if (c->opt.matrix_free_updates) {
+    KRef32 K;
+    for (int e = 0; e < 576; ++e) K.k[e] = c->h_kref32[e];
+    const long long L = 3LL * c->n_nodes;
+    if ((long long)c->w_x32.n < L) c->w_x32.alloc(L);
+    k_vec_to_f32<<<grid_for(L, 256), 256, 0, c->stream>>>(x_pad, c->w_x32.p, L);
+    HP_CHECK_LAUNCH();
+    k_spmv_ebe32<<<grid_for(c->n_nodes, 256), 256, 0, c->stream>>>(c->node_ijk.p, c->n_nodes, c->grid_to_node.p,
+                                                                    c->mask.p, c->E.p, c->nx, c->ny, c->nz, K,
+                                                                    c->fixed.p, c->w_x32.p, y_pad, sub);
+  } else {
     k_spmv_sell<float><<<grid, 64, 0, c->stream>>>(off, col, c->sell_val32.p, perm, x_pad, y_pad, sub, c->n_nodes);
+  }
   HP_CHECK_LAUNCH();
 }
 

@@ -99,6 +99,8 @@ void validate_options(const hplmm_options &o) {
   HP_REQUIRE(o.wait_budget_us >= 0, HPLMM_ERR_INVALID, "wait_budget_us must be non-negative");
   HP_REQUIRE(o.tensor_galerkin == 0 || o.tensor_galerkin == 1, HPLMM_ERR_INVALID, "tensor_galerkin must be 0 or 1");
   HP_REQUIRE(o.tensor_coarse == 0 || o.tensor_coarse == 1, HPLMM_ERR_INVALID, "tensor_coarse must be 0 or 1");
+  HP_REQUIRE(o.matrix_free_updates == 0 || o.matrix_free_updates == 1, HPLMM_ERR_INVALID,
+             "matrix_free_updates must be 0 or 1");
 }
 
 void require_setup(hplmm_ctx *c) {
@@ -114,6 +116,7 @@ void alloc_work(hplmm_ctx *c) {
   c->w_coarse_t.alloc(No);
   c->w_coarse_u.alloc(No);
   c->w_coarse_y.alloc(No);
+  c->w_x32.alloc(L);  // allocated before any graph capture reads it
   int m = c->opt.restart;
   c->V.alloc((size_t)(m + 1) * L);
   c->Z.alloc((size_t)m * L);
@@ -152,6 +155,7 @@ void hplmm_default_options(hplmm_options *o) {
   o->smoother_ctas = 0;
   o->tensor_galerkin = 1;
   o->tensor_coarse = 1;
+  o->matrix_free_updates = 1;
 }
 
 hplmm_status hplmm_create(hplmm_ctx **ctx, const hplmm_options *opt, void *cuda_stream) {
@@ -510,6 +514,9 @@ hplmm_status hplmm_get_costs(hplmm_ctx *c, hplmm_costs *out) {
     out->coarse_factor_flops = c->cf.flops;
     out->coarse_fronts = c->cf.nf;
     out->coarse_front_bytes = 8LL * c->cf.F_total;
+    out->n_voxels = (long long)c->nx * c->ny * c->nz;
+    out->n_grid = c->n_grid;
+    out->matrix_free_updates = c->opt.matrix_free_updates;
   });
 }
 

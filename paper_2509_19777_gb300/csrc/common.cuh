@@ -257,6 +257,7 @@ struct hplmm_ctx {
   hp::Buf<int> free_index;         // n_nodes*3 -> free DOF or -1
   hp::Buf<int> dof_slot;           // n_dof -> node*3+d
   hp::Buf<double> Kref;            // 24x24 reference element stiffness (E = 1)
+  std::vector<float> h_kref32;     // its FP32 copy (host), for the element-by-element residual updates
   hp::Buf<int> row_ptr, col;       // BSR over nodes, 3x3 blocks
   long long nnzb = 0;
   hp::Buf<double> val64;           // nnzb*9, fixed rows/cols zeroed
@@ -340,6 +341,7 @@ struct hplmm_ctx {
   hp::Buf<double> w_loc64;         // local vectors for smoother
   hp::Buf<float> w_loc32;
   hp::Buf<double> w_in, w_out;     // padded copies of API vectors
+  hp::Buf<float> w_x32;            // FP32 copy of the vector of an element-by-element residual update
   hp::Buf<double> V, Z, w_dots, w_h;
   int gmres_cap = 0;
   hp::Buf<double> w_partial;
