@@ -322,7 +322,7 @@ __global__ void k_sell_fill(const int *row_ptr, const int *col, const double *va
       double v = (j < len) ? val[(long long)(b + j) * 9 + e] : 0.0;
       long long at = (base + (long long)j * 32) * 9 + (long long)e * 32 + lane;
       sval64[at] = v;
-      sval32[at] = (float)v;
+      if (sval32) sval32[at] = (float)v;
     }
   }
 }
@@ -615,7 +615,11 @@ void assemble(hplmm_ctx *c, const uint8_t *mask, int nx, int ny, int nz, const f
     HP_REQUIRE(nent < (1LL << 31), HPLMM_ERR_INVALID, "assemble: too many blocks for 32-bit SpMV offsets");
     c->sell_col.alloc(nent);
     c->sell_val64.alloc(nent * 9);
-    c->sell_val32.alloc(nent * 9);
+    // the FP32 copy serves only the assembled FP32 residual updates (matrix_free_updates = 0)
+    if (c->opt.matrix_free_updates)
+      c->sell_val32.release();
+    else
+      c->sell_val32.alloc(nent * 9);
     k_sell_fill<<<grid_for((long long)nsl * 32, 128), 128, 0, s>>>(c->row_ptr.p, c->col.p, c->val64.p,
                                                                    c->sell_perm.p, c->n_nodes, c->sell_off.p,
                                                                    c->sell_col.p, c->sell_val64.p, c->sell_val32.p);
@@ -666,6 +670,12 @@ void spmv(hplmm_ctx *c, const double *x_pad, double *y_pad, hplmm_prec prec, con
 }
 
 void spmv_multi(hplmm_ctx *c, const double *X, double *Y, int k, hplmm_prec prec, const double *SUB) {
+  if (prec != HPLMM_FP64 && c->opt.matrix_free_updates) {
+    // element by element there is no matrix to share between the vectors: one product per vector
+    const long long L = 3LL * c->n_nodes;
+    for (int q = 0; q < k; ++q) spmv(c, X + q * L, Y + q * L, prec, SUB ? SUB + q * L : nullptr);
+    return;
+  }
   ProfScope ps(c, HPLMM_PH_SPMV);
   const unsigned grid = grid_for(c->n_nodes, 64);
   const long long L = 3LL * c->n_nodes;
