@@ -49,23 +49,25 @@ FP64_TUNED = dict(local_prec="fp64", apply_prec="fp64", use_graph=True, autotune
 
 WORKLOADS = {
     "fractured256": dict(image=[256, 256, 256], porosity=0.25, grains=[16, 16, 16], n_mortar=4, chosen=BF16,
-                         plain_fits=False, baseline_config=4,
-                         form_text=("BF16 local factors and basis panels (FP32 factorisation in chunks), FP32 "
-                                    "residual updates and arithmetic, FP64 sparse coarse Cholesky and FGMRES; "
-                                    "apply replayed from a CUDA graph; smoother plans tuned at set-up")),
+                         plain_fits=False,
+                         form_text=("BF16 local factors and basis panels (FP32 factorisation in chunks), "
+                                    "element-by-element FP32 residual updates, FP32 arithmetic, FP64 sparse coarse "
+                                    "Cholesky (Schur updates on tcgen05 by the Ozaki scheme) and FGMRES; Galerkin "
+                                    "GEMM on tcgen05; apply replayed from a CUDA graph; smoother plans tuned at "
+                                    "set-up")),
     "porous128": dict(image=[128, 128, 128], porosity=0.4, grains=[8, 8, 8], n_mortar=4, chosen=FP32,
-                      plain_fits=True, baseline_config=3,
+                      plain_fits=True,
                       form_text=("FP32 local factors, basis panels and residual updates, FP64 sparse coarse "
                                  "Cholesky and FGMRES; apply replayed from a CUDA graph; smoother plans tuned")),
     "porous64": dict(image=[64, 64, 64], porosity=0.3, grains=[4, 4, 4], n_mortar=4, chosen=FP32,
-                     plain_fits=True, baseline_config=2,
+                     plain_fits=True,
                      form_text="FP32 form as for porous128"),
     # the fractured256 recipe at 64^3 and 128^3 (the same 16^3-voxel grains, so the same local problem shapes,
     # 64 and 512 of them): profiling cases small enough for a full ncu capture, not bench lines
     "fractured64": dict(image=[64, 64, 64], porosity=0.25, grains=[4, 4, 4], n_mortar=2, chosen=BF16,
-                        plain_fits=True, baseline_config=None, form_text="BF16 form as for fractured256"),
+                        plain_fits=True, form_text="BF16 form as for fractured256"),
     "fractured128": dict(image=[128, 128, 128], porosity=0.25, grains=[8, 8, 8], n_mortar=2, chosen=BF16,
-                         plain_fits=True, baseline_config=None, form_text="BF16 form as for fractured256"),
+                         plain_fits=True, form_text="BF16 form as for fractured256"),
 }
 DEFAULT_WORKLOAD = "fractured256"
 PLAIN_WORKLOAD = "porous128"   # largest workload whose plain FP64 form fits one GPU
@@ -699,7 +701,7 @@ def main():
         "vs_baseline": None,
         "dtype": "bf16+f32+f64" if form["apply_prec"] == "bf16" else ("f32+f64" if form["apply_prec"] == "fp32" else "f64"),
         "data": "synthetic",
-        "config": {"workload": args.workload, "baseline_config": spec["baseline_config"], "image": spec["image"],
+        "config": {"workload": args.workload, "image": spec["image"],
                    "porosity": spec["porosity"], "grains": spec["grains"], "n_mortar": nm,
                    "contact_halfwidth": METHOD["contact_halfwidth"], "restart": METHOD["restart"], "tol": TOL,
                    "n_dof": sizes["n_dof"], "n_coarse": sizes["n_coarse"], "n_interfaces": sizes["n_interfaces"],
