@@ -104,6 +104,10 @@ typedef struct {
                             (default) element by element from the voxel moduli and the reference stiffness, in
                             FP32 (no matrix read), 0 from the FP32 copy of A_hat (sliced ELL); the FP64 form
                             and the Krylov products always use the assembled FP64 A_hat */
+  int smoother_bulk_warps; /* warps per CTA that stream the far rows in the smoother solves: 0 (default) the
+                            tuner's choice, else 8; 8, 4, 2 or 1 force it (4, 2 and 1 run one CTA per local
+                            problem, with a ring sized for two, three or four CTAs per SM, and so exclude
+                            smoother_ctas = 2); the result does not depend on it beyond the order of additions */
 } hplmm_options;
 
 enum { HPLMM_BASIS_DIRECT = 0, HPLMM_BASIS_PCG = 1, HPLMM_BASIS_PCG_WARM = 2 };

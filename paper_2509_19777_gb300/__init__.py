@@ -56,7 +56,8 @@ class hplmm_options(ctypes.Structure):
                 ("basis_max_iters", ctypes.c_int), ("keep_basis_rhs", ctypes.c_int),
                 ("smoother_ctas", ctypes.c_int), ("mortar_kind", ctypes.c_int), ("stage_mb", ctypes.c_int),
                 ("wait_budget_us", ctypes.c_int), ("tensor_galerkin", ctypes.c_int),
-                ("tensor_coarse", ctypes.c_int), ("matrix_free_updates", ctypes.c_int)]
+                ("tensor_coarse", ctypes.c_int), ("matrix_free_updates", ctypes.c_int),
+                ("smoother_bulk_warps", ctypes.c_int)]
 
 
 HPLMM_BASIS_DIRECT, HPLMM_BASIS_PCG, HPLMM_BASIS_PCG_WARM = 0, 1, 2
@@ -446,7 +447,7 @@ class Solver:
                  restart=30, max_iters=300, strict_two_grain=False, use_graph=False, verbose=False, profile=False,
                  autotune=False, basis_solver="direct", basis_tol=1e-6, basis_max_iters=3000, keep_basis_rhs=False,
                  smoother_ctas=0, mortar_kind="gaussian", stage_mb=0, wait_budget_us=0, tensor_galerkin=True,
-                 tensor_coarse=True, matrix_free_updates=True, stream=None):
+                 tensor_coarse=True, matrix_free_updates=True, smoother_bulk_warps=0, stream=None):
         o = hplmm_default_options()
         o.n_mortar, o.beta, o.contact_halfwidth, o.n_st = n_mortar, beta, contact_halfwidth, n_st
         o.local_prec, o.apply_prec = PREC[local_prec], PREC[apply_prec]
@@ -463,6 +464,7 @@ class Solver:
         o.tensor_galerkin = int(tensor_galerkin)
         o.tensor_coarse = int(tensor_coarse)
         o.matrix_free_updates = int(matrix_free_updates)
+        o.smoother_bulk_warps = int(smoother_bulk_warps)
         self.options = o
         self.ctx = hplmm_create(o, stream)
         self.n_dof = 0

@@ -101,6 +101,11 @@ void validate_options(const hplmm_options &o) {
   HP_REQUIRE(o.tensor_coarse == 0 || o.tensor_coarse == 1, HPLMM_ERR_INVALID, "tensor_coarse must be 0 or 1");
   HP_REQUIRE(o.matrix_free_updates == 0 || o.matrix_free_updates == 1, HPLMM_ERR_INVALID,
              "matrix_free_updates must be 0 or 1");
+  HP_REQUIRE(o.smoother_bulk_warps == 0 || o.smoother_bulk_warps == 1 || o.smoother_bulk_warps == 2 ||
+                 o.smoother_bulk_warps == 4 || o.smoother_bulk_warps == 8,
+             HPLMM_ERR_INVALID, "smoother_bulk_warps must be 0, 1, 2, 4 or 8");
+  HP_REQUIRE(o.smoother_bulk_warps == 0 || o.smoother_bulk_warps == 8 || o.smoother_ctas != 2, HPLMM_ERR_INVALID,
+             "smoother_bulk_warps 1, 2 or 4 runs one CTA per local problem: it excludes smoother_ctas = 2");
 }
 
 void require_setup(hplmm_ctx *c) {
@@ -156,6 +161,7 @@ void hplmm_default_options(hplmm_options *o) {
   o->tensor_galerkin = 1;
   o->tensor_coarse = 1;
   o->matrix_free_updates = 1;
+  o->smoother_bulk_warps = 0;
 }
 
 hplmm_status hplmm_create(hplmm_ctx **ctx, const hplmm_options *opt, void *cuda_stream) {

@@ -2387,15 +2387,18 @@ void smoother_apply(hplmm_ctx *c, LocalSet &S, const double *r_pad, double *z_pa
   ProfScope ps(c, (&S == &c->grains) ? HPLMM_PH_APPLY_GRAINS : HPLMM_PH_APPLY_CONTACTS);
   cudaStream_t s = c->stream;
   const SolvePlan pl = solve_plan(S);
-  const int cl = c->opt.smoother_ctas > 0 ? c->opt.smoother_ctas
-                 : (S.tuned_cluster > 0 ? S.tuned_cluster : default_cluster(S));
+  const int fb = c->opt.smoother_bulk_warps;  // forced bulk warps, 0 if none
+  const int cl = (fb > 0 && fb < WS_BULK_WARPS) ? 1
+                 : c->opt.smoother_ctas > 0     ? c->opt.smoother_ctas
+                                                : (S.tuned_cluster > 0 ? S.tuned_cluster : default_cluster(S));
   // depths: the tuner's choice when there is one, else 3 diagonal stages, whole-step chunks and the largest
   // ring
   const int c0s = S.tuned_c0_stages > 0 ? S.tuned_c0_stages : 3;
   // bulk warps per CTA: 8 (one CTA per SM), or, for one-CTA problems, 4, 2 or 1 with the ring sized for two,
-  // three or four CTAs per SM
-  const int nbw = (cl == 1 && (S.tuned_bulk == 4 || S.tuned_bulk == 2 || S.tuned_bulk == 1)) ? S.tuned_bulk
-                                                                                             : WS_BULK_WARPS;
+  // three or four CTAs per SM (forced, or the tuner's choice)
+  const int nbw = fb > 0 ? fb
+                  : (cl == 1 && (S.tuned_bulk == 4 || S.tuned_bulk == 2 || S.tuned_bulk == 1)) ? S.tuned_bulk
+                                                                                               : WS_BULK_WARPS;
   auto go = [&](auto kern, const auto *band, auto *ys) {
     const SmemBudget bud = smem_budget(kern);
     int ring = ring_rows_for(pl, c0s, nbw == WS_BULK_WARPS ? bud.one
@@ -2474,7 +2477,8 @@ std::map<TuneKey, TuneChoice> g_tune_cache;
 static void tune_set(hplmm_ctx *c, LocalSet &S, bool atomic) {
   S.tuned_chunk_rows = S.tuned_ring_rows = S.tuned_c0_stages = S.tuned_cluster = S.tuned_bulk = 0;
   if (S.count == 0) return;
-  TuneKey key{S.count, 0, 0, (int)S.prec + (S.apply_bf16 ? 8 : 0) + 16 * c->opt.smoother_ctas};
+  TuneKey key{S.count, 0, 0,
+              (int)S.prec + (S.apply_bf16 ? 8 : 0) + 16 * c->opt.smoother_ctas + 64 * c->opt.smoother_bulk_warps};
   for (int k = 0; k < S.count; ++k) {
     key.nmax = std::max(key.nmax, S.h_n[k]);
     key.bwmax = std::max(key.bwmax, S.h_bw[k]);
@@ -2521,7 +2525,8 @@ static void tune_set(hplmm_ctx *c, LocalSet &S, bool atomic) {
                         {2, WS_BULK_WARPS, bud.one}, {2, WS_BULK_WARPS, bud.pair}};
   for (const Form &f : forms)
    for (int chunk : chunk_choices(S))
-    if (c->opt.smoother_ctas == 0 || c->opt.smoother_ctas == f.cl)
+    if ((c->opt.smoother_ctas == 0 || c->opt.smoother_ctas == f.cl) &&
+        (c->opt.smoother_bulk_warps == 0 || c->opt.smoother_bulk_warps == f.nbw))
     for (int c0d = 2; c0d <= 4; ++c0d) {
         const int cl = f.cl;
         const int ring = ring_rows_for(pl, c0d, f.budget);

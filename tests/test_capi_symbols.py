@@ -32,15 +32,34 @@ def test_default_options_and_struct_sizes():
     assert o.local_prec == hp.HPLMM_FP64 and o.apply_prec == hp.HPLMM_FP64
 
 
-def test_missing_library_fails_loudly(monkeypatch, tmp_path):
+def test_missing_library_fails_loudly(tmp_path):
     import importlib
-    monkeypatch.setattr(hp, "LIB_PATH", str(tmp_path / "absent.so"))
-    monkeypatch.setattr(hp, "_lib", None)
+    import pytest
+    # the patches are undone before the module is reloaded, so later tests see the library with its
+    # argument types bound to the reloaded module's classes
     try:
-        hp.load_library()
-    except RuntimeError as e:
-        assert "no CPU fallback" in str(e)
-    else:
-        raise AssertionError("load_library must raise when the library is missing")
+        with pytest.MonkeyPatch.context() as mp:
+            mp.setattr(hp, "LIB_PATH", str(tmp_path / "absent.so"))
+            mp.setattr(hp, "_lib", None)
+            with pytest.raises(RuntimeError, match="no CPU fallback"):
+                hp.load_library()
     finally:
         importlib.reload(hp)
+
+
+def test_invalid_options_rejected_before_any_device_call():
+    # hplmm_create validates the options first and returns HPLMM_ERR_INVALID without touching a device, so
+    # this runs on a machine without a GPU
+    import ctypes
+    lib = hp.load_library()
+    bad = [dict(smoother_bulk_warps=3), dict(smoother_bulk_warps=4, smoother_ctas=2),
+           dict(smoother_bulk_warps=1, smoother_ctas=2), dict(smoother_ctas=3), dict(restart=0),
+           dict(matrix_free_updates=2)]
+    for over in bad:
+        o = hp.hplmm_default_options()
+        for k, v in over.items():
+            setattr(o, k, v)
+        ctx = ctypes.c_void_p()
+        assert lib.hplmm_create(ctypes.byref(ctx), ctypes.byref(o), None) == hp.HPLMM_ERR_INVALID, over
+        assert not ctx.value
+    assert hp.hplmm_default_options().smoother_bulk_warps == 0

@@ -54,6 +54,42 @@ def test_one_and_two_cta_smoothers_agree(name, form, tol_forms, tol_oracle):
 
 
 @pytest.mark.parametrize("name", ["cube16_n4", "porous32_n4", "fractured32_n2"])
+@pytest.mark.parametrize("form,tol_forms,tol_oracle", FORMS)
+def test_bulk_warp_forms_agree(name, form, tol_forms, tol_oracle):
+    # the one-CTA smoother with 8, 4, 2 or 1 warps streaming the far rows (ring sized for one, two, three or
+    # four CTAs per SM): the same operator, summed in another order
+    p, opt, sysm, M = oracle_case(name)
+    r = np.random.default_rng(23).standard_normal(sysm.n_dof)
+    z_ref = M.smoother.apply(r)
+    out = {}
+    for nbw in (8, 4, 2, 1):
+        s = gpu_solver(name, smoother_ctas=1, smoother_bulk_warps=nbw, **form)
+        out[nbw] = _n(s.apply_smoother(_t(r)))
+        s.close()
+    for nbw in (4, 2, 1):
+        assert rel(out[nbw], out[8]) < tol_forms, nbw
+    if tol_oracle is not None:
+        for nbw in out:
+            assert rel(out[nbw], z_ref) < tol_oracle, nbw
+
+
+@pytest.mark.parametrize("nbw", [4, 1])
+def test_bulk_warp_solve_matches_oracle(nbw):
+    # the headline's smoother forms (4 bulk warps for the grains, 1 for the contact grids) inside FGMRES with
+    # the graph replay
+    name = "porous32_n4"
+    x_ref, _ = oracle_solution(name)
+    p, opt, sysm, M = oracle_case(name)
+    s = gpu_solver(name, smoother_bulk_warps=nbw, local_prec="fp32", apply_prec="bf16", use_graph=True)
+    x, rc, st = s.solve(tol=1e-10)
+    xn = _n(x)
+    assert rc == 0
+    assert np.linalg.norm(sysm.b - sysm.A @ xn) / np.linalg.norm(sysm.b) <= 1e-10 * 1.001
+    assert rel(xn, x_ref) < 1e-6
+    s.close()
+
+
+@pytest.mark.parametrize("name", ["cube16_n4", "porous32_n4", "fractured32_n2"])
 def test_bf16_error_follows_roundoff(name):
     # The BF16 form computes exactly like the FP32 form (FP32 factorisation, FP32 arithmetic) and then stores
     # the factors rounded to BF16, each element with relative error at most U16.  To first order an error in
@@ -107,3 +143,5 @@ def test_smoother_ctas_validated():
     import paper_2509_19777_gb300 as hp
     with pytest.raises(hp.HplmmError):
         hp.Solver(smoother_ctas=3)
+    with pytest.raises(hp.HplmmError):
+        hp.Solver(smoother_bulk_warps=4, smoother_ctas=2)
