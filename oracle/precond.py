@@ -5,9 +5,10 @@ ORACLE -- test infrastructure only (see oracle/__init__.py).
 
 * Eq. multi_precond: M^{-1} = M_G^{-1} + M_L^{-1} (I - A_hat M_G^{-1}); M_G first.
 * Eq. local_smoother: M_L^{-1} = sum_{i=1}^{n_st} M_l^{-1} prod_{j<i} (I - A_hat M_l^{-1})
-  with base smoother M_l = M_CG (n_st = 1 in the paper's runs).
+  with base smoother M_l = M_CG (n_st = 1 in the paper's runs) or, for the paper's smoother comparison,
+  M_l = M_ILU(0) (oracle/ilu.py; n_st = 6 there).
 Applied to r this is: z1 = M_G^{-1} r; r1 = r - A_hat z1; then n_st stages of
-t = M_CG^{-1} res, s += t, res -= A_hat t; return z1 + s.
+t = M_l^{-1} res, s += t, res -= A_hat t; return z1 + s.
 """
 from __future__ import annotations
 
@@ -18,6 +19,7 @@ import numpy as np
 from . import fem
 from .coarse import CoarseSpace
 from .decomposition import Decomposition, cartesian_partition
+from .ilu import ILU0Smoother
 from .mortar import Mortars
 from .smoother import ContactGrainSmoother
 
@@ -31,6 +33,7 @@ class Options:
     strict_two_grain: bool = False
     keep_corrections: bool = True
     mortar_kind: str = "gaussian"   # "gaussian" (Eq. gauss) or "algebraic" (Eq. algebra)
+    smoother: str = "contact_grain"  # base smoother M_l: "contact_grain" (M_CG) or "ilu0" (M_ILU(0))
 
 
 class HPLMM:
@@ -42,7 +45,10 @@ class HPLMM:
         self.dec = Decomposition(system, grain_of_voxel, n_grains, opt.strict_two_grain)
         self.mortars = Mortars(system, self.dec, opt.n_mortar, opt.beta, opt.mortar_kind)
         self.coarse = CoarseSpace(system, self.dec, self.mortars, opt.keep_corrections)
-        self.smoother = ContactGrainSmoother(system, self.dec, self.coarse, opt.contact_halfwidth)
+        if opt.smoother == "ilu0":
+            self.smoother = ILU0Smoother(system)
+        else:
+            self.smoother = ContactGrainSmoother(system, self.dec, self.coarse, opt.contact_halfwidth)
         self.A = system.A.tocsr()
 
     def M_G(self, r):
