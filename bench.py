@@ -185,7 +185,8 @@ class ClockSampler:
 
 # ------------------------------------------------------------------ the GPU arm
 def make_solver(hp, spec, form, stream, profile=False, n_mortar=None):
-    return hp.Solver(n_mortar=n_mortar or spec["n_mortar"], **METHOD, **form, profile=profile, stream=stream)
+    # a form may override the method's defaults (the ILU(0) smoother runs n_st = 6 stages)
+    return hp.Solver(n_mortar=n_mortar or spec["n_mortar"], **{**METHOD, **form}, profile=profile, stream=stream)
 
 
 def run_form(hp, problem, spec, form, steps, warmup, flush, stream, profile=False, n_mortar=None, keep=False):
@@ -583,6 +584,30 @@ def compare_forms(hp, np, torch, synth, spec_name, flush, stream, seed):
     return out
 
 
+def smoother_comparison(hp, np, synth, spec_name, flush, stream, seed):
+    """The paper's smoother comparison (Section 5): hPLMM with the contact-grain smoother M_CG (n_st = 1)
+    against the black-box ILU(0) base smoother (n_st = 6), same coarse space, FP64 form with graph replay."""
+    spec = WORKLOADS[spec_name]
+    problem = synth.make_workload(spec_name, seed)
+    out = {"workload": spec_name, "n_mortar": spec["n_mortar"], "form": FP64_TUNED}
+    xs = {}
+    for name, over in (("contact_grain_nst1", {}), ("ilu0_nst6", dict(smoother="ilu0", n_st=6))):
+        form = dict(FP64_TUNED, **over)
+        _, x, t, st, prof, costs, _, launches = run_form(hp, problem, spec, form, 1, 1, flush, stream)
+        xs[name] = x.cpu().numpy()
+        out[name] = {"value": t[0] / 1e3, "unit": "s", "iters": st.iters, "rel_res_true": st.rel_res_true,
+                     "t_setup_ml": st.t_setup_ml, "t_setup_mg": st.t_setup_mg, "t_solve": st.t_solve,
+                     "ms_per_iteration": 1e3 * st.t_solve / max(1, st.iters), "gpu_launches": int(launches)}
+        if over:
+            out[name]["ilu_levels"] = costs["ilu_levels"]
+        del x
+    a, b = xs["contact_grain_nst1"], xs["ilu0_nst6"]
+    out["ilu0_nst6"]["rel_diff_vs_contact_grain"] = float(np.linalg.norm(b - a) / np.linalg.norm(a))
+    out["time_ratio_ilu0_over_contact_grain"] = out["ilu0_nst6"]["value"] / out["contact_grain_nst1"]["value"]
+    out["iteration_ratio_ilu0_over_contact_grain"] = out["ilu0_nst6"]["iters"] / out["contact_grain_nst1"]["iters"]
+    return out
+
+
 def multi_load_eval(hp, torch, synth, spec_name, flush, stream, seed, k=4):
     """Load-step reuse: one set-up, then k load cases (top-face tractions in z, x, y and a combination) solved
     one at a time and all together in lockstep (hplmm_solve_multi), against k separate set-up + solve steps."""
@@ -742,6 +767,10 @@ def main():
             line["multi_load"] = multi_load_eval(hp, torch, synth, PLAIN_WORKLOAD, flush, stream, args.seed)
         except Exception as e:
             line["multi_load"] = {"error": str(e)[-300:]}
+        try:
+            line["smoother_comparison"] = smoother_comparison(hp, np, synth, "porous64", flush, stream, args.seed)
+        except Exception as e:
+            line["smoother_comparison"] = {"error": str(e)[-300:]}
     if rank == 0 and not args.no_ws:
         try:
             line["warm_start"] = warm_start_eval(hp, stream)

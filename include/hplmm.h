@@ -108,10 +108,17 @@ typedef struct {
                             tuner's choice, else 8; 8, 4, 2 or 1 force it (4, 2 and 1 run one CTA per local
                             problem, with a ring sized for two, three or four CTAs per SM, and so exclude
                             smoother_ctas = 2); the result does not depend on it beyond the order of additions */
+  int smoother_kind;     /* base smoother M_l of Eq. local_smoother: HPLMM_SMOOTHER_CONTACT_GRAIN (default, M_CG of
+                            Section 4.3) or HPLMM_SMOOTHER_ILU0 (M_ILU(0), the black-box smoother of the paper's
+                            smoother comparison, Sections 4.1 and 5; use it with n_st = 6 as the paper does):
+                            ILU(0) of A_hat in FP64 on its structural pattern (DOFs coupled when their nodes share
+                            a solid voxel), rows eliminated in free-DOF order; the contact grids are then not built,
+                            and the set-up fails with HPLMM_ERR_SINGULAR on a zero pivot */
 } hplmm_options;
 
 enum { HPLMM_BASIS_DIRECT = 0, HPLMM_BASIS_PCG = 1, HPLMM_BASIS_PCG_WARM = 2 };
 enum { HPLMM_MORTAR_GAUSSIAN = 0, HPLMM_MORTAR_ALGEBRAIC = 1 };
+enum { HPLMM_SMOOTHER_CONTACT_GRAIN = 0, HPLMM_SMOOTHER_ILU0 = 1 };
 
 /* Boundary conditions on the six faces of the image box, in the order
  * x=0, x=nx, y=0, y=ny, z=0, z=nz (Eq. BC).  fix[f][d] != 0 prescribes
@@ -292,6 +299,8 @@ typedef enum {
   HPLMM_PH_SPMV,              /* every A_hat x product */
   HPLMM_PH_KRYLOV,            /* FGMRES vector work (CGS2 products, updates) */
   HPLMM_PH_APPLY_GRAPH,       /* whole preconditioner applies replayed from a captured CUDA graph (use_graph) */
+  HPLMM_PH_FACTOR_ILU,        /* ILU(0) factorisation of A_hat (smoother_kind = HPLMM_SMOOTHER_ILU0) */
+  HPLMM_PH_APPLY_ILU,         /* M_ILU(0)^{-1}: the two level-scheduled triangular solves */
   HPLMM_PH_COUNT
 } hplmm_phase;
 
@@ -331,6 +340,8 @@ typedef struct {
   long long n_voxels;             /* voxels of the image (nx ny nz) */
   long long n_grid;               /* grid points (nx+1)(ny+1)(nz+1) */
   int matrix_free_updates;        /* the apply's residual updates are element by element (options) */
+  long long ilu_levels;           /* non-empty node levels of the ILU(0) factor and solves (0 without it); each
+                                     triangular solve is one launch per level and reads nnzb 3x3 blocks in all */
 } hplmm_costs;
 
 hplmm_status hplmm_get_costs(hplmm_ctx *ctx, hplmm_costs *out);

@@ -44,7 +44,8 @@ EXPORTED = [
     "hplmm_save_setup", "hplmm_load_setup",
 ]
 PHASES = ["maps", "factor_grains", "factor_contacts", "basis_rhs", "basis_solve", "galerkin", "coarse_chol",
-          "apply_coarse", "apply_contacts", "apply_grains", "spmv", "krylov", "apply_graph"]
+          "apply_coarse", "apply_contacts", "apply_grains", "spmv", "krylov", "apply_graph", "factor_ilu",
+          "apply_ilu"]
 
 
 class hplmm_options(ctypes.Structure):
@@ -57,13 +58,15 @@ class hplmm_options(ctypes.Structure):
                 ("smoother_ctas", ctypes.c_int), ("mortar_kind", ctypes.c_int), ("stage_mb", ctypes.c_int),
                 ("wait_budget_us", ctypes.c_int), ("tensor_galerkin", ctypes.c_int),
                 ("tensor_coarse", ctypes.c_int), ("matrix_free_updates", ctypes.c_int),
-                ("smoother_bulk_warps", ctypes.c_int)]
+                ("smoother_bulk_warps", ctypes.c_int), ("smoother_kind", ctypes.c_int)]
 
 
 HPLMM_BASIS_DIRECT, HPLMM_BASIS_PCG, HPLMM_BASIS_PCG_WARM = 0, 1, 2
 BASIS = {"direct": HPLMM_BASIS_DIRECT, "pcg": HPLMM_BASIS_PCG, "pcg_warm": HPLMM_BASIS_PCG_WARM}
 HPLMM_MORTAR_GAUSSIAN, HPLMM_MORTAR_ALGEBRAIC = 0, 1
 MORTAR = {"gaussian": HPLMM_MORTAR_GAUSSIAN, "algebraic": HPLMM_MORTAR_ALGEBRAIC}
+HPLMM_SMOOTHER_CONTACT_GRAIN, HPLMM_SMOOTHER_ILU0 = 0, 1
+SMOOTHER = {"contact_grain": HPLMM_SMOOTHER_CONTACT_GRAIN, "ilu0": HPLMM_SMOOTHER_ILU0}
 
 
 class hplmm_basis_stats(ctypes.Structure):
@@ -98,7 +101,8 @@ class hplmm_costs(ctypes.Structure):
                 ("n_nodes", ctypes.c_longlong), ("sell_blocks", ctypes.c_longlong),
                 ("coarse_solve_bytes", ctypes.c_longlong), ("coarse_factor_flops", ctypes.c_double),
                 ("coarse_fronts", ctypes.c_longlong), ("coarse_front_bytes", ctypes.c_longlong),
-                ("n_voxels", ctypes.c_longlong), ("n_grid", ctypes.c_longlong), ("matrix_free_updates", ctypes.c_int)]
+                ("n_voxels", ctypes.c_longlong), ("n_grid", ctypes.c_longlong), ("matrix_free_updates", ctypes.c_int),
+                ("ilu_levels", ctypes.c_longlong)]
 
 
 _lib = None
@@ -447,7 +451,8 @@ class Solver:
                  restart=30, max_iters=300, strict_two_grain=False, use_graph=False, verbose=False, profile=False,
                  autotune=False, basis_solver="direct", basis_tol=1e-6, basis_max_iters=3000, keep_basis_rhs=False,
                  smoother_ctas=0, mortar_kind="gaussian", stage_mb=0, wait_budget_us=0, tensor_galerkin=True,
-                 tensor_coarse=True, matrix_free_updates=True, smoother_bulk_warps=0, stream=None):
+                 tensor_coarse=True, matrix_free_updates=True, smoother_bulk_warps=0, smoother="contact_grain",
+                 stream=None):
         o = hplmm_default_options()
         o.n_mortar, o.beta, o.contact_halfwidth, o.n_st = n_mortar, beta, contact_halfwidth, n_st
         o.local_prec, o.apply_prec = PREC[local_prec], PREC[apply_prec]
@@ -465,6 +470,7 @@ class Solver:
         o.tensor_coarse = int(tensor_coarse)
         o.matrix_free_updates = int(matrix_free_updates)
         o.smoother_bulk_warps = int(smoother_bulk_warps)
+        o.smoother_kind = SMOOTHER[smoother]
         self.options = o
         self.ctx = hplmm_create(o, stream)
         self.n_dof = 0

@@ -20,7 +20,7 @@ OUT = os.path.join(HERE, "libhplmm.so")
 STAMP = OUT + ".sha256"
 BUILD_DIR = os.path.join(HERE, "_build")
 SOURCES = ["prims.cu", "assemble.cu", "maps.cu", "local.cu", "coarse.cu", "cfactor.cu", "apply.cu", "capi.cu", "static_spmv.cu",
-           "checkpoint.cu",
+           "checkpoint.cu", "ilu.cu",
            "ws.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr"]

@@ -259,6 +259,9 @@ void check_status(hplmm_ctx *c) {
   int st = w[0];
   if (st != 0) {
     hplmm_status code = (hplmm_status)st;
+    if (code == HPLMM_ERR_SINGULAR && w[1] == 5)
+      throw Error(code, "zero or non-finite pivot in the ILU(0) factorisation (node " + std::to_string(w[2]) +
+                            ", component " + std::to_string(w[3]) + ")");
     if (code == HPLMM_ERR_SINGULAR) {
       static const char *where[] = {"?", "grain-grid", "contact-grid", "coarse"};
       throw Error(code, std::string("non-positive pivot in the ") + where[(w[1] >= 1 && w[1] <= 3) ? w[1] : 0] +
@@ -274,6 +277,10 @@ void check_status(hplmm_ctx *c) {
 }
 
 void smoother_stage(hplmm_ctx *c, const double *r_pad, double *z_pad) {
+  if (c->opt.smoother_kind == HPLMM_SMOOTHER_ILU0) {
+    ilu_stage(c, r_pad, z_pad);
+    return;
+  }
   cudaStream_t s = c->stream;
   long long L = 3LL * c->n_nodes;
   // z_zeta = M_zeta^{-1} r
@@ -315,6 +322,11 @@ void precond_apply(hplmm_ctx *c, const double *r_pad, double *z_pad) {
 void precond_apply_multi(hplmm_ctx *c, const double *R, double *Z, int k) {
   cudaStream_t s = c->stream;
   const long long L = 3LL * c->n_nodes, LK = L * k;
+  if (c->opt.smoother_kind == HPLMM_SMOOTHER_ILU0) {
+    // the level-scheduled ILU(0) solves have no multi-vector form: one vector at a time
+    for (int v = 0; v < k; ++v) precond_apply(c, R + v * L, Z + v * L);
+    return;
+  }
   for (auto *b : {&c->mw_r1, &c->mw_r2, &c->mw_z1, &c->mw_zz, &c->mw_zg, &c->mw_t}) b->alloc(LK);
   coarse_apply_multi(c, R, c->mw_z1.p, k);
   spmv_multi(c, c->mw_z1.p, c->mw_r1.p, k, c->opt.apply_prec, R);

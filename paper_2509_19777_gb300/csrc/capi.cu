@@ -106,6 +106,8 @@ void validate_options(const hplmm_options &o) {
              HPLMM_ERR_INVALID, "smoother_bulk_warps must be 0, 1, 2, 4 or 8");
   HP_REQUIRE(o.smoother_bulk_warps == 0 || o.smoother_bulk_warps == 8 || o.smoother_ctas != 2, HPLMM_ERR_INVALID,
              "smoother_bulk_warps 1, 2 or 4 runs one CTA per local problem: it excludes smoother_ctas = 2");
+  HP_REQUIRE(o.smoother_kind == HPLMM_SMOOTHER_CONTACT_GRAIN || o.smoother_kind == HPLMM_SMOOTHER_ILU0,
+             HPLMM_ERR_INVALID, "smoother_kind must be HPLMM_SMOOTHER_CONTACT_GRAIN or HPLMM_SMOOTHER_ILU0");
 }
 
 void require_setup(hplmm_ctx *c) {
@@ -162,6 +164,7 @@ void hplmm_default_options(hplmm_options *o) {
   o->tensor_coarse = 1;
   o->matrix_free_updates = 1;
   o->smoother_bulk_warps = 0;
+  o->smoother_kind = HPLMM_SMOOTHER_CONTACT_GRAIN;
 }
 
 hplmm_status hplmm_create(hplmm_ctx **ctx, const hplmm_options *opt, void *cuda_stream) {
@@ -254,8 +257,14 @@ hplmm_status hplmm_setup(hplmm_ctx *c, const int32_t *partition, int n_grains, i
     alloc_work(c);
     hp::check_status(c);
     t3 = now_s();
-    // pipeline depths of the smoother solves (part of the smoother build)
-    hp::tune_local(c);
+    // the ILU(0) smoother's factorisation, or the pipeline depths of the contact-grain smoother's solves (both
+    // part of the smoother build)
+    if (c->opt.smoother_kind == HPLMM_SMOOTHER_ILU0) {
+      hp::ilu_setup(c);
+      hp::check_status(c);
+    } else {
+      hp::tune_local(c);
+    }
     double t4 = now_s();
     t2 += t4 - t3;
     t3 = t4;
@@ -354,6 +363,11 @@ hplmm_status hplmm_load_setup(hplmm_ctx *c, const char *path) {
     HP_REQUIRE(c->assembled, HPLMM_ERR_STATE, "call hplmm_assemble first");
     hp::load_setup(c, path);
     alloc_work(c);
+    // the ILU(0) factor is not stored: it is recomputed from A_hat
+    if (c->opt.smoother_kind == HPLMM_SMOOTHER_ILU0) {
+      hp::ilu_setup(c);
+      hp::check_status(c);
+    }
     c->setup_done = true;
   });
 }
@@ -523,6 +537,7 @@ hplmm_status hplmm_get_costs(hplmm_ctx *c, hplmm_costs *out) {
     out->n_voxels = (long long)c->nx * c->ny * c->nz;
     out->n_grid = c->n_grid;
     out->matrix_free_updates = c->opt.matrix_free_updates;
+    out->ilu_levels = c->opt.smoother_kind == HPLMM_SMOOTHER_ILU0 ? (long long)c->h_ilu_off.size() - 1 : 0;
   });
 }
 

@@ -38,6 +38,7 @@ void get(FILE *f, void *p, size_t bytes) {
 // the options that shape the set-up (the others only steer how it runs)
 struct SetupKey {
   int n_mortar, contact_halfwidth, n_st, local_prec, apply_prec, strict_two_grain, basis_solver, mortar_kind;
+  int smoother_kind, pad_;
   double beta;
   int nx, ny, nz, n_nodes;
   long long n_dof, nnzb;
@@ -54,6 +55,7 @@ SetupKey key_of(const hplmm_ctx *c) {
   k.strict_two_grain = c->opt.strict_two_grain;
   k.basis_solver = c->opt.basis_solver;
   k.mortar_kind = c->opt.mortar_kind;
+  k.smoother_kind = c->opt.smoother_kind;
   k.beta = c->opt.beta;
   k.nx = c->nx;
   k.ny = c->ny;
@@ -375,7 +377,7 @@ void load_setup(hplmm_ctx *c, const char *path) {
   get(fh.f, &k, sizeof(k));
   HP_REQUIRE(std::memcmp(&k, &mine, sizeof(k)) == 0, HPLMM_ERR_INVALID,
              "load_setup: the file was saved for another system or other set-up options (image, n_mortar, "
-             "beta, contact_halfwidth, n_st, precisions, basis solver, mortar kind must match)");
+             "beta, contact_halfwidth, n_st, precisions, basis solver, mortar kind, smoother kind must match)");
   c->setup_done = false;
   drop_apply_graph(c);
   Loader ld{fh.f, c->stream, {}, {}};

@@ -331,6 +331,12 @@ struct hplmm_ctx {
   hp::Buf<int> gcol_off, gcol;     // global coarse column of each panel column
   hp::Buf<int> status;             // device error word
 
+  // ---- ILU(0) base smoother (smoother_kind = HPLMM_SMOOTHER_ILU0)
+  hp::Buf<double> ilu_val;         // L and U in A_hat's block storage (nnzb x 9)
+  hp::Buf<int> ilu_diag;           // position of each node row's diagonal block
+  hp::Buf<int> ilu_nodes;          // nodes ordered by level
+  std::vector<int> h_ilu_off;      // first entry of each non-empty level in ilu_nodes, then n_nodes
+
   // ---- apply / GMRES work vectors (padded n_nodes*3)
   hp::Buf<double> w_r1, w_r2, w_z1, w_zz, w_zg, w_t, w_w;
   hp::Buf<double> w_coarse_t, w_coarse_u, w_coarse_y;
@@ -480,6 +486,8 @@ void save_setup(hplmm_ctx *c, const char *path);
 void load_setup(hplmm_ctx *c, const char *path);
 void tune_local(hplmm_ctx *c);
 void smoother_stage(hplmm_ctx *c, const double *r_pad, double *z_pad);
+void ilu_setup(hplmm_ctx *c);
+void ilu_stage(hplmm_ctx *c, const double *r_pad, double *z_pad);
 int fgmres(hplmm_ctx *c, const double *b_pad, double *x_pad, double tol, hplmm_stats *st);
 void precond_apply_multi(hplmm_ctx *c, const double *R, double *Z, int k);
 int fgmres_multi(hplmm_ctx *c, const double *B, double *X, int k, double tol, hplmm_stats *st);

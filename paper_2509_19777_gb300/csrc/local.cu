@@ -2053,7 +2053,8 @@ void build_local_sets(hplmm_ctx *c) {
   }
   // contact grids
   {
-    int C = c->n_ifaces;
+    // the ILU(0) base smoother replaces the contact-grain smoother: no contact grids then
+    int C = c->opt.smoother_kind == HPLMM_SMOOTHER_ILU0 ? 0 : c->n_ifaces;
     c->contacts.count = C;
     if (C > 0) {
       Buf<int> bmin, bmax;

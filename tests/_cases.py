@@ -27,6 +27,10 @@ CASES = {
     # problems), both with more than 500 contact grids and a deep coarse elimination tree
     "porous24_g216": ("porous24", 1, dict(n_mortar=1, contact_halfwidth=1, grains=(6, 6, 6))),
     "porous32_g512": ("porous32", 1, dict(n_mortar=1, contact_halfwidth=1, grains=(8, 8, 8))),
+    # the ILU(0) base smoother with the paper's six stages (its smoother comparison, Section 5)
+    "tiny8_ilu": ("tiny8", 3, dict(n_mortar=2, contact_halfwidth=1, smoother="ilu0", n_st=6)),
+    "cube16_ilu": ("cube16", 0, dict(n_mortar=4, contact_halfwidth=1, smoother="ilu0", n_st=6)),
+    "porous32_ilu": ("porous32", 1, dict(n_mortar=4, contact_halfwidth=2, smoother="ilu0", n_st=6)),
 }
 
 
@@ -44,7 +48,8 @@ def oracle_case(name):
     p, opt = problem(name)
     o = precond.Options(n_mortar=opt["n_mortar"], contact_halfwidth=opt["contact_halfwidth"],
                         strict_two_grain=opt.get("strict_two_grain", False),
-                        mortar_kind=opt.get("mortar_kind", "gaussian"))
+                        mortar_kind=opt.get("mortar_kind", "gaussian"),
+                        smoother=opt.get("smoother", "contact_grain"), n_st=opt.get("n_st", 1))
     sysm, M = precond.build(p, o)
     return p, opt, sysm, M
 
@@ -79,7 +84,8 @@ def gpu_solver(name, **over):
     import paper_2509_19777_gb300 as hp
     p, opt = problem(name)
     kw = dict(n_mortar=opt["n_mortar"], contact_halfwidth=opt["contact_halfwidth"],
-              strict_two_grain=opt.get("strict_two_grain", False), mortar_kind=opt.get("mortar_kind", "gaussian"))
+              strict_two_grain=opt.get("strict_two_grain", False), mortar_kind=opt.get("mortar_kind", "gaussian"),
+              smoother=opt.get("smoother", "contact_grain"), n_st=opt.get("n_st", 1))
     kw.update(over)
     s = hp.Solver(**kw)
     mask, E = hp.problem_to_device(p)
