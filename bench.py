@@ -278,16 +278,21 @@ def measured_peaks():
     return 6800.0, 2070.0, "fallback"
 
 
-# the sources the smoother solve's translation unit is compiled from: its recorded DRAM traffic stays valid
-# while these are unchanged
-SMOOTHER_SOURCES = ("paper_2509_19777_gb300/csrc/local.cu", "paper_2509_19777_gb300/csrc/common.cuh",
-                    "include/hplmm.h")
+# the smoother solve's device source: the device helpers at the head of local.cu (up to its first section of
+# kernels) and the section that holds k_band_solve_ws.  Its recorded DRAM traffic stays valid while these are
+# unchanged; host code (launch dispatch, tuner, options) does not change what a launch reads or writes.
+SMOOTHER_FILE = "paper_2509_19777_gb300/csrc/local.cu"
+SMOOTHER_REGIONS = ((None, "// ---------------------------------------------------------------- boxes"),
+                    ("// ---------------------------------------------------------------- single-RHS smoother solves",
+                     "int num_sms() {"))
 
 
 def kernel_source_hash():
+    txt = open(os.path.join(ROOT, SMOOTHER_FILE)).read()
     h = hashlib.sha256()
-    for f in SMOOTHER_SOURCES:
-        h.update(open(os.path.join(ROOT, f), "rb").read())
+    for start, end in SMOOTHER_REGIONS:
+        a = txt.index(start) if start else 0
+        h.update(txt[a:txt.index(end, a)].encode())
     return h.hexdigest()[:16]
 
 
