@@ -15,6 +15,7 @@ Modules, in the paper's order:
   smoother      Section 4.3, Eqs. local_smoother_CG and Mg_Mz: contact-grain additive-Schwarz smoother
   precond       Section 4.1, Eqs. multi_precond and local_smoother: the multiplicative two-level M
   ilu           Sections 4.1 and 5: the ILU(0) base smoother of the paper's smoother comparison
+  spectral      Section 3.1: spectral k-way partition of a gray-scale image into grain grids
   gmres         Section 5: right-preconditioned restarted GMRES
   accuracy      Eq. err_metric: first-pass L2 errors of displacement and maximum shear stress
   warmstart     learned warm start of the local basis solves (3-D convolutional network, Adam) and the
