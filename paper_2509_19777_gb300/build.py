@@ -79,7 +79,8 @@ def build_library(verbose=False, ptxas_info=False, force=False):
             if log.strip():
                 print(f"== {os.path.basename(obj)}\n{log}", file=sys.stderr)
     tmp = OUT + ".tmp"
-    cmd = [nvcc(), *ARCH, "-shared", "-o", tmp, *[o for o, _ in results]]
+    # -ldl: the NVTX 3 header loads a profiler's injection library with dlopen (in libc from glibc 2.34 on)
+    cmd = [nvcc(), *ARCH, "-shared", "-o", tmp, *[o for o, _ in results], "-ldl"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")

@@ -13,6 +13,15 @@
 
 #include "../../include/hplmm.h"
 
+// NVTX ranges around the library's phases (header-only NVTX 3: free unless a profiler is attached); left out
+// where the toolkit has no NVTX headers
+#if defined(__has_include)
+#if __has_include(<nvtx3/nvToolsExt.h>)
+#include <nvtx3/nvToolsExt.h>
+#define HP_HAVE_NVTX 1
+#endif
+#endif
+
 namespace hp {
 
 // ---------------------------------------------------------------- errors
@@ -402,18 +411,35 @@ cudaEvent_t prof_event(hplmm_ctx *c);
 void prof_harvest(hplmm_ctx *c);
 
 // times the kernels queued on the context's stream between construction and destruction
+inline const char *phase_name(int ph) {
+  static const char *const names[] = {"hplmm:maps",         "hplmm:factor_grains", "hplmm:factor_contacts",
+                                      "hplmm:basis_rhs",    "hplmm:basis_solve",   "hplmm:galerkin",
+                                      "hplmm:coarse_chol",  "hplmm:apply_coarse",  "hplmm:apply_contacts",
+                                      "hplmm:apply_grains", "hplmm:spmv",          "hplmm:krylov",
+                                      "hplmm:apply_graph",  "hplmm:factor_ilu",    "hplmm:apply_ilu"};
+  static_assert(sizeof(names) / sizeof(names[0]) == HPLMM_PH_COUNT, "one name per phase");
+  return (ph >= 0 && ph < HPLMM_PH_COUNT) ? names[ph] : "hplmm:?";
+}
+
+// a phase: an NVTX range always, CUDA events on the context's stream when options.profile is set
 struct ProfScope {
   hplmm_ctx *c;
   int ph;
   cudaEvent_t e0 = nullptr;
   long long l0 = 0;
   ProfScope(hplmm_ctx *ctx, int phase) : c(ctx), ph(phase) {
+#ifdef HP_HAVE_NVTX
+    nvtxRangePushA(phase_name(ph));
+#endif
     if (!c->opt.profile || c->capturing) return;
     e0 = prof_event(c);
     cudaEventRecord(e0, c->stream);
     l0 = launch_count();
   }
   ~ProfScope() {
+#ifdef HP_HAVE_NVTX
+    nvtxRangePop();
+#endif
     if (!c->opt.profile || !e0) return;
     cudaEvent_t e1 = prof_event(c);
     cudaEventRecord(e1, c->stream);
