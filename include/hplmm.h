@@ -69,7 +69,8 @@ typedef struct {
   int verbose;           /* 1: print phase timings to stderr */
   int profile;           /* 1: time every phase with CUDA events on the context's stream (hplmm_get_profile) */
   int autotune;          /* 1: at set-up, time the smoother solve's pipeline depths on this problem's local
-                            problems and keep the fastest (cached per problem-size bucket for the process) */
+                            problems and keep the fastest (cached per problem-size bucket for the process);
+                            no effect with the ILU(0) smoother */
   int basis_solver;      /* local basis solves (Eqs. col_pk, col_cg): HPLMM_BASIS_DIRECT (default, the exact
                             banded Cholesky solve), HPLMM_BASIS_PCG (block-Jacobi CG from a zero guess) or
                             HPLMM_BASIS_PCG_WARM (CG from the learned warm start); the iterative forms need
@@ -177,7 +178,8 @@ hplmm_status hplmm_setup(hplmm_ctx *ctx, const int32_t *partition, int n_grains,
                          int px, int py, int pz, const double *b);
 
 /* z = M^{-1} r, the full multiplicative preconditioner of Eq. multi_precond
- * (M_G first, then n_st stages of M_CG).  r, z: DEVICE float64 [n_dof];
+ * (M_G first, then n_st stages of the base smoother: M_CG, or M_ILU(0) with
+ * options.smoother_kind).  r, z: DEVICE float64 [n_dof];
  * they may not alias.  Asynchronous on the context's stream. */
 hplmm_status hplmm_apply(hplmm_ctx *ctx, const double *r, double *z);
 
@@ -185,8 +187,9 @@ hplmm_status hplmm_apply(hplmm_ctx *ctx, const double *r, double *z);
  * this is the first-pass solution of Section 6.1.  DEVICE float64 [n_dof]. */
 hplmm_status hplmm_apply_coarse(hplmm_ctx *ctx, const double *r, double *z);
 
-/* z = M_CG^{-1} r, one stage of the contact-grain smoother (Eq.
- * local_smoother_CG).  DEVICE float64 [n_dof]. */
+/* z = M_l^{-1} r, one stage of the base smoother: the contact-grain smoother
+ * M_CG (Eq. local_smoother_CG), or M_ILU(0) = U^{-1} L^{-1} with
+ * options.smoother_kind = HPLMM_SMOOTHER_ILU0.  DEVICE float64 [n_dof]. */
 hplmm_status hplmm_apply_smoother(hplmm_ctx *ctx, const double *r, double *z);
 
 /* y = A_hat x in FP64.  DEVICE float64 [n_dof]. */
